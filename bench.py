@@ -1,0 +1,333 @@
+"""Benchmark of the SBR trace-integrate path on one GB300 (replicas on N GPUs).
+
+Workload (default): triangular trihedral corner reflector, 1 m legs,
+3 x 1024 triangles, 10 GHz, ray spacing lambda/10 (margin 0.05), up to 3
+bounces, azimuth sweep 0..90 deg in 0.5 deg steps at elevation 35.26 deg
+(181 aspects, about 52M launched rays), vector PO, HH and VV.
+One step = one full sweep: sbr_trace over all 181 aspects + sbr_po_integrate.
+
+Metric: ray-bounces per second (closest-hit queries on live rays, hit or
+miss), aggregated over all ranks; angles per second is reported beside it.
+
+  value     device-resident: mesh and BVH already on the GPU, outputs to device
+  e2e       through the public API from host buffers every step: mesh upload
+            from pinned host memory, BVH build, trace, PO, results read back
+  roofline  the transport passes (primary + bounce kernels, one traversal
+            routine), FP32 issue bound: algorithmic FP32 operations from the
+            node-visit and triangle-test counts of a counting run, divided by
+            the passes' CUDA-event time measured inside the timed steps
+  cpu_baseline  the FP64 oracle on a sample of the sweep's aspects, all host cores
+
+``--impl reference`` times the oracle (the CPU reference of this method) on
+the same workload and prints its own line. N > 1 (torchrun): every rank runs
+the full workload on its own GPU (replicas, no collective on the data path);
+the step time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import sbr_inputs as S  # noqa: E402
+
+# FP32 operations of one node visit (two slab tests and the ordering compare)
+# and of one triangle test (Moller-Trumbore form up to the inside decision),
+# counted from the traversal routine in sbr_trace.cu
+OPS_NODE = 41
+OPS_TRI = 38
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group(backend="gloo")
+        pg = dist
+    return ws, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, x: float) -> float:
+    if pg is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def workload(name: str) -> dict:
+    if name == "trihedral":
+        return S.trihedral_case()
+    if name == "sphere":
+        return S.sphere_case(n_random=64)
+    if name.startswith("aircraft"):
+        f = {"aircraft1": 1e9, "aircraft3": 3e9, "aircraft10": 10e9}[name]
+        return S.aircraft_case(f, n_az=360)
+    raise ValueError(name)
+
+
+def wl_config(case: dict, name: str) -> dict:
+    return {"workload": case["name"], "mesh_triangles": int(len(case["tri"])), "aspects": int(len(case["angles"])),
+            "freq_ghz": [float(f) / 1e9 for f in case["freqs"]], "ray_spacing_m": float(case["spacing"]),
+            "max_bounces": int(case["max_bounces"]), "po": "vector", "pols": "HH,VV",
+            "l2": "flushed between timed steps (512 MB write)"}
+
+
+# ----------------------------------------------------------------------------- oracle timing
+def oracle_sample(case, n_angles: int, threads: int):
+    import oracle
+
+    om = oracle.Mesh(case["xyz"], case["tri"])
+    idx = np.linspace(0, len(case["angles"]) - 1, n_angles).round().astype(int)
+    t0 = time.perf_counter()
+    bounces = 0
+    for a in idx:
+        az, el = case["angles"][a]
+        fr = oracle.make_frame(om.bbox, az, el, case["spacing"], eta=case["eta"], window=case.get("window", 0.0))
+        tr = oracle.trace(om, fr, case["max_bounces"], threads=threads)
+        oracle.po(tr["coef"], tr["L"], tr["valid"], case["freqs"])
+        nb = tr["nb"]
+        bounces += int(np.sum(nb + (nb < case["max_bounces"])))
+    dt = time.perf_counter() - t0
+    return bounces, dt, idx
+
+
+def run_reference(args, case, ws, rank, pg):
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    n = args.ref_angles
+    for _ in range(args.warmup):
+        oracle_sample(case, 1, threads)
+    tot_b, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        b, t, idx = oracle_sample(case, n, threads)
+        tot_b += b
+        tot_t += t
+    v = tot_b / tot_t
+    line = {"impl": "reference", "metric": "ray-bounces/s", "value": v, "unit": "ray-bounces/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": wl_config(case, args.workload),
+            "angles_per_s": n * args.steps / tot_t,
+            "cpu_baseline": {"value": v, "unit": "ray-bounces/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{n} of {len(case['angles'])} aspects per step (evenly spaced), full ray grids"},
+            "e2e": {"value": v, "unit": "ray-bounces/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_sbr(args, case, ws, rank, local, pg):
+    import torch
+
+    import paper_2604_09243_gb300 as G
+    from paper_2604_09243_gb300 import build
+
+    build.build()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    ctx = G.Context(local, stream=stream)
+    ctx.load_mesh(case["xyz"], case["tri"])
+    ang = np.ascontiguousarray(case["angles"], np.float64)
+    freqs = np.ascontiguousarray(case["freqs"], np.float64)
+    B = case["max_bounces"]
+    kw = dict(eta=case["eta"], max_bounces=B, window=case.get("window", 0.0))
+    na, nf, npol = len(ang), len(freqs), 2
+    E_dev = torch.empty((na, nf, npol, 2), dtype=torch.float64, device=f"cuda:{local}")
+    R_dev = torch.empty((na, nf, npol), dtype=torch.float64, device=f"cuda:{local}")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=f"cuda:{local}")
+
+    def step(flags=G.TRACE_TIME_PASSES):
+        st = ctx.trace(ang, case["spacing"], flags=flags, **kw)
+        ctx.po_integrate(freqs, "HH,VV", E_out=E_dev, rcs_out=R_dev)
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    cnt = ctx.trace(ang, case["spacing"], flags=G.TRACE_COUNT_VISITS, **kw)  # counting run, untimed
+    stream.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    barrier(pg)
+    torch.cuda.synchronize()
+    sampler.start()
+    stats = []
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 255)
+        ev[k][0].record(stream)
+        stats.append(step())
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(pg)
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_dev = max_over_ranks(pg, sum(step_ms) / 1e3)
+    bounces = stats[0]["ray_bounces"]
+    assert all(s["ray_bounces"] == bounces for s in stats)
+    value = ws * bounces * args.steps / t_dev
+
+    # --- end to end through the public API from host buffers
+    xyz_p = torch.from_numpy(case["xyz"]).pin_memory()
+    tri_p = torch.from_numpy(case["tri"]).pin_memory()
+    ang_p = torch.from_numpy(ang).pin_memory()
+    E_h = np.empty((na, nf, npol, 2))
+    R_h = np.empty((na, nf, npol))
+    h2d = xyz_p.numel() * 4 + tri_p.numel() * 4 + ang_p.numel() * 8 + freqs.size * 8
+    d2h = E_h.nbytes + R_h.nbytes
+
+    def e2e_step():
+        ctx.load_mesh(xyz_p.numpy(), tri_p.numpy())
+        ctx.trace(ang_p.numpy(), case["spacing"], **kw)
+        E, R = ctx.po_integrate(freqs, "HH,VV")
+        E_h[...] = np.stack([E.real, E.imag], -1)
+        R_h[...] = R
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    barrier(pg)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks(pg, time.perf_counter() - t0)
+    e2e_value = ws * bounces * args.steps / t_e2e
+
+    # --- roofline of the transport passes (FP32 issue bound)
+    ops = OPS_NODE * cnt["node_visits"] + OPS_TRI * cnt["tri_tests"]
+    pass_s = float(np.mean([s["pass_ms"] for s in stats])) / 1e3
+    pk, src = peaks()
+    peak_ops = SM_COUNT * FP32_LANES_PER_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    achieved = ops / pass_s / 1e12
+    launches = stats[0]["kernel_launches"] + 2  # + PO reduce and PO final
+    line = {"metric": "ray-bounces/s", "value": value, "unit": "ray-bounces/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": wl_config(case, args.workload),
+            "angles_per_s": ws * na * args.steps / t_dev,
+            "rays_launched_per_step": stats[0]["rays_launched"], "ray_bounces_per_step": bounces,
+            "valid_rays_per_step": stats[0]["valid_rays"],
+            "roofline": {"bound": "alu", "kernel": "k_primary+k_bounce (transport passes)",
+                         "achieved": achieved, "peak": peak_ops, "unit": "T FP32-op/s",
+                         "frac": achieved / peak_ops, "traffic": None,
+                         "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                                        f"{pk.get('sm_max_mhz', 2070.0):g} MHz ({src} SM clock)",
+                         "ops_per_step": ops, "node_visits": cnt["node_visits"], "tri_tests": cnt["tri_tests"],
+                         "pass_ms_per_step": pass_s * 1e3},
+            "e2e": {"value": e2e_value, "unit": "ray-bounces/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * t_e2e / args.steps},
+            "gpu_launches": int(launches * args.steps),
+            "clocks": clocks}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        b, t, idx = oracle_sample(case, args.ref_angles, threads)
+        line["cpu_baseline"] = {"value": b / t, "unit": "ray-bounces/s", "cores": threads, "kind": "oracle",
+                                "sample": f"{len(idx)} of {na} aspects (evenly spaced), full ray grids, "
+                                          f"{t:.1f} s wall"}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="sbr", choices=["sbr", "reference"])
+    ap.add_argument("--workload", default="trihedral",
+                    choices=["trihedral", "sphere", "aircraft1", "aircraft3", "aircraft10"])
+    ap.add_argument("--ref-angles", type=int, default=24)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local, pg = dist_setup()
+    case = workload(args.workload)
+    if args.impl == "reference":
+        run_reference(args, case, ws, rank, pg)
+    else:
+        run_sbr(args, case, ws, rank, local, pg)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

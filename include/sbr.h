@@ -1,0 +1,216 @@
+/*
+ * sbr.h -- C ABI of libsbr, a GB300 (sm_103a) implementation of the
+ * trace-integrate hot path of shooting and bouncing rays (SBR) for monostatic
+ * radar cross section, after "BVH-Accelerated Ray Tracing for High-Frequency
+ * Electromagnetic Backscattering" (arXiv 2604.09243).
+ *
+ * Pipeline (Sec. 4 and Fig. 1 of the paper):
+ *   sbr_load_mesh    triangulated PEC surface                        (Sec. 4.1)
+ *   sbr_build_bvh    LBVH over the triangles, SAH leaf collapse      (Sec. 4, BVH)
+ *   sbr_trace        orthographic ray grid per aspect (Eq. L1-L3), multi-bounce
+ *                    closest-hit transport with specular reflection and PEC
+ *                    field update (Algorithm 2), compaction of valid hits
+ *   sbr_po_integrate physical-optics ray-tube sum over valid hits only
+ *                    (Eq. po_sum; vector form from Eq. em5/em6) and
+ *                    sigma = 4 pi |A|^2 in dBsm (Sec. 4, after Eq. po_sum)
+ *
+ * Conventions shared by every call:
+ *   - Angles in degrees. r = (cos el cos az, cos el sin az, sin el) points to the
+ *     radar; the incident direction is k_inc = -r. V = theta_hat =
+ *     (sin el cos az, sin el sin az, -cos el), H = phi_hat = (-sin az, cos az, 0).
+ *   - Polarisation order HH, VV, HV, VH: first letter receive, second transmit.
+ *   - Every call returns an int status (SBR_OK = 0, negative on error) and never
+ *     aborts or throws across the ABI; sbr_last_error() gives the message.
+ *   - All device work of a context is ordered on the context's CUDA stream.
+ *     Calls that return results to host memory synchronise that stream.
+ *   - A context is not thread safe: use one context per host thread.
+ */
+#ifndef SBR_H_
+#define SBR_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SBR_VERSION_MAJOR 0
+#define SBR_VERSION_MINOR 1
+
+/* status codes */
+#define SBR_OK 0
+#define SBR_ERR_ARG (-1)            /* invalid argument (null pointer, size, index) */
+#define SBR_ERR_CUDA (-2)           /* a CUDA runtime call failed */
+#define SBR_ERR_OOM (-3)            /* device or pinned-host allocation failed */
+#define SBR_ERR_STATE (-4)          /* call out of order (no mesh, no BVH, no trace) */
+#define SBR_ERR_STACK_OVERFLOW (-5) /* a traversal needed more than the stack depth */
+#define SBR_ERR_TIMEOUT (-6)        /* a bounded device wait gave up */
+#define SBR_ERR_NODEV (-7)          /* no usable CUDA device */
+
+/* polarisation mask bits for sbr_po_integrate */
+#define SBR_POL_HH 1
+#define SBR_POL_VV 2
+#define SBR_POL_HV 4
+#define SBR_POL_VH 8
+
+/* po_mode for sbr_po_integrate: one form, optionally OR-ed with one phase precision */
+#define SBR_PO_VECTOR 0           /* Stratton-Chu PO at the last hit (Eq. em5, em6) */
+#define SBR_PO_PAPER_SCALAR 1     /* Eq. po_sum literally, Gamma = -1 (PEC) */
+#define SBR_PHASE_COMPENSATED 0   /* k*L as a two-float product, reduced in cycles (default) */
+#define SBR_PHASE_FP32 16         /* plain FP32 k*L and sincosf */
+#define SBR_PHASE_FP64 32         /* FP64 k*L and sincos (slow on GB300) */
+
+/* sbr_trace_opts.flags */
+#define SBR_TRACE_PHASE_LITERAL_2R 1 /* scalar form uses e^{-j 2 k R}, R the summed path (Eq. po_sum as printed) */
+#define SBR_TRACE_REQUIRE_ESCAPE 2   /* a ray still hitting after max_bounces is invalid (Sec. 4 text) */
+#define SBR_TRACE_RECORD_HITS 4      /* keep per-ray, per-bounce hits for sbr_get_hits */
+#define SBR_TRACE_COUNT_VISITS 8     /* count node visits and triangle tests into the stats */
+#define SBR_TRACE_TIME_PASSES 16     /* time each transport pass with CUDA events into the stats */
+
+typedef struct sbr_ctx sbr_ctx; /* opaque; owns the device copies of mesh, BVH and ray buffers */
+
+/* BVH build options (Sec. 4: SAH cost C_T + SA(L)/SA(P) N_L C_I + SA(R)/SA(P) N_R C_I). */
+typedef struct {
+    int leaf_max;         /* largest leaf after the SAH collapse, 1..16 (default 4) */
+    float cost_traverse;  /* C_T (default 1) */
+    float cost_intersect; /* C_I (default 1) */
+} sbr_bvh_opts;
+
+/* Ray-grid and transport options of sbr_trace. A zeroed struct gives the defaults. */
+typedef struct {
+    double window_m; /* > 0: fixed square aperture of this side replaces Eq. L2 (N = ceil(W/ds)) */
+    double offset_u; /* sub-cell shift of the whole grid along u, in units of the spacing */
+    double offset_v; /* same along v */
+    int flags;       /* SBR_TRACE_* */
+    int chunk_rays;  /* rays per internal batch of aspects (0 = 2^27); bounds the live-ray queue
+                        memory at 192 bytes per ray; an aspect larger than this is refused */
+} sbr_trace_opts;
+
+/* Counters of the last sbr_trace (summed over its angles). */
+typedef struct {
+    int64_t n_angles;
+    int64_t rays_launched; /* sum of Nu*Nv (Eq. L3) */
+    int64_t ray_bounces;   /* closest-hit queries on live rays, hit or miss */
+    int64_t valid_rays;    /* rays with at least one hit (Algorithm 2 'valid') */
+    int64_t node_visits;   /* only with SBR_TRACE_COUNT_VISITS */
+    int64_t tri_tests;     /* only with SBR_TRACE_COUNT_VISITS */
+    int64_t stack_overflows;
+    int64_t kernel_launches; /* CUDA kernels this call enqueued */
+    int64_t pass_launches;   /* transport-pass kernels among them (primary and bounce passes) */
+    double pass_ms;          /* with SBR_TRACE_TIME_PASSES: summed device time of those passes */
+} sbr_trace_stats;
+
+/* Per-aspect ray grid (Eq. L1-L3) exactly as sbr_trace generates it. */
+typedef struct {
+    int64_t nu, nv;          /* Eq. L3 */
+    double lu, lv;           /* projected extents, Eq. L1 */
+    double spacing;          /* ds (m); tube area dA = ds^2 */
+    double eps;              /* origin offset after a hit: 1e-5 * bbox diagonal (m) */
+    double rhat[3], khat[3]; /* direction to the radar and incident direction */
+    double vhat[3], hhat[3]; /* V = theta_hat (aperture v), H = phi_hat (aperture u) */
+    float p0[3];             /* origin of ray (0, 0), FP32 */
+    float du[3], dv[3];      /* grid steps ds*u and ds*v, FP32 */
+    float dir[3];            /* ray direction k_inc, FP32 */
+} sbr_ray_grid;
+
+/* Library version as major*100 + minor. */
+int sbr_version(void);
+
+/* Create a context on CUDA device `device`. `cuda_stream` is a cudaStream_t to
+ * order all work on (e.g. torch.cuda.current_stream().cuda_stream), or NULL for
+ * a stream the context creates and owns. The caller keeps ownership of a
+ * stream it passes and must keep it alive until sbr_destroy. On failure *out is
+ * NULL and the status is SBR_ERR_NODEV, SBR_ERR_CUDA or SBR_ERR_ARG. */
+int sbr_create(sbr_ctx** out, int device, void* cuda_stream);
+
+/* Free every device buffer of the context (after synchronising its stream). NULL is a no-op. */
+void sbr_destroy(sbr_ctx* ctx);
+
+/* Message of the last failed call on `ctx` (owned by the context, valid until the
+ * next call on it); for ctx == NULL, the message of the last failed sbr_create. */
+const char* sbr_last_error(const sbr_ctx* ctx);
+
+/* Load a triangulated PEC surface (Sec. 4.1 of the paper; meshes come from the
+ * caller, no file I/O). xyz: float32 [n_vert][3] metres; tri: int32 [n_tri][3]
+ * vertex indices. on_device = 0: host pointers; 1: device pointers on the
+ * context's device. The data are copied; the caller keeps ownership. Indices
+ * outside [0, n_vert) give SBR_ERR_ARG. Replaces any previous mesh and drops
+ * the trace results; it also computes the scene box and builds a BVH with the
+ * default options (sbr_build_bvh rebuilds it with others). Synchronises. */
+int sbr_load_mesh(sbr_ctx* ctx, const float* xyz, int64_t n_vert, const int32_t* tri, int64_t n_tri,
+                  int on_device);
+
+/* Scene bounding box [xmin, ymin, zmin, xmax, ymax, zmax] of the loaded mesh
+ * (exact FP32 min/max of the vertices), written to host memory. */
+int sbr_get_bbox(sbr_ctx* ctx, float* bbox6);
+
+/* Build the BVH (Sec. 4, BVH paragraph; Algorithm 1 is the paper's host
+ * builder, this is a GPU LBVH): 63-bit Morton codes of the triangle centroids,
+ * device radix sort, Karras hierarchy, bottom-up AABB refit and SAH leaf
+ * collapse with C_T, C_I and leaf_max from `opt` (NULL = defaults), triangles
+ * reordered so each leaf is a contiguous range. Runs on the context stream. */
+int sbr_build_bvh(sbr_ctx* ctx, const sbr_bvh_opts* opt);
+
+/* Ray grid of one aspect for the loaded mesh (Eq. L1-L3), computed on the host.
+ * ray_spacing_m = ds, margin_eta = eta of Eq. L2 (ignored when opt->window_m > 0).
+ * Needs a loaded mesh but no device work. */
+int sbr_ray_grid_for(sbr_ctx* ctx, double az_deg, double el_deg, double ray_spacing_m, double margin_eta,
+                     const sbr_trace_opts* opt, sbr_ray_grid* out);
+
+/* Same as sbr_ray_grid_for for an explicit scene box bbox6 (host, float[6] =
+ * xmin, ymin, zmin, xmax, ymax, zmax); needs no context and no GPU. Ray (i, j)
+ * of the grid starts at (p0 + i*du) + j*dv, each operation an FP32
+ * round-to-nearest multiply or add (no fused multiply-add), and travels along dir. */
+int sbr_ray_grid_box(const float* bbox6, double az_deg, double el_deg, double ray_spacing_m, double margin_eta,
+                 const sbr_trace_opts* opt, sbr_ray_grid* out);
+
+/* Trace every aspect of az_el_deg (host, [n_angles][2] = (az, el) degrees):
+ * orthographic ray grid per aspect (Eq. L1-L3), up to max_bounces closest-hit
+ * queries per ray with specular reflection d - 2 (d.n) n, PEC field update
+ * E' = 2 (n.E) n - E and origin offset eps along the normal (Algorithm 2),
+ * then compaction of the valid rays into a dense record buffer (Sec. 4,
+ * trace-integrate decomposition). The records stay in the context until the
+ * next sbr_trace or sbr_load_mesh; sbr_po_integrate reads them for any list of
+ * frequencies. `opt` may be NULL; `stats` may be NULL (it is filled on return
+ * and then the stream is synchronised). max_bounces in 1..64. */
+int sbr_trace(sbr_ctx* ctx, const double* az_el_deg, int64_t n_angles, double ray_spacing_m, double margin_eta,
+              int max_bounces, const sbr_trace_opts* opt, sbr_trace_stats* stats);
+
+/* Physical-optics ray-tube sum over the valid hits of the last sbr_trace, for
+ * every traced aspect and every frequency of freq_hz (host, n_freq values):
+ *   E_pq = (-j k / 4 pi) sum_i c_pq,i e^{-j k L_i},  k = 2 pi f / c0,
+ * with c_pq,i the tube's coefficient for receive p / transmit q (Eq. em6 in
+ * SBR_PO_VECTOR; Eq. po_sum with Gamma = -1 in SBR_PO_PAPER_SCALAR, where
+ * HH = VV = A and HV = VH = 0), then sigma = 4 pi |E|^2 and dBsm = 10 log10 sigma.
+ * The partial sums are FP32 per block of tubes and FP64 across blocks, in a
+ * fixed order (results are bitwise reproducible). pol_mask selects the
+ * polarisations (SBR_POL_*); n_pol = popcount(pol_mask) outputs in the order
+ * HH, VV, HV, VH. Outputs: E_re_im [n_angles][n_freq][n_pol][2] FP64 and
+ * rcs_dbsm [n_angles][n_freq][n_pol] FP64 (either may be NULL), in host memory
+ * (out_on_device = 0, synchronises) or device memory (1, stream ordered). */
+int sbr_po_integrate(sbr_ctx* ctx, const double* freq_hz, int64_t n_freq, int pol_mask, int po_mode,
+                     double* E_re_im, double* rcs_dbsm, int out_on_device);
+
+/* Per-ray hits of traced aspect `angle` (needs SBR_TRACE_RECORD_HITS), for
+ * parity checks; ray id = j * nu + i. Host outputs (any may be NULL):
+ * tri_ids [nu*nv][max_bounces] original triangle index or -1, t [nu*nv][max_bounces]
+ * hit distance along each leg, n_bounce [nu*nv]. Synchronises. */
+int sbr_get_hits(sbr_ctx* ctx, int64_t angle, int32_t* tri_ids, float* t, int32_t* n_bounce);
+
+/* Dense valid-hit records of traced aspect `angle`, in ray order, for parity
+ * checks. Host outputs of capacity `cap` records (any may be NULL):
+ * ray_ids (j*nu + i), coef [.][5] = (HH, VV, HV, VH, scalar) tube coefficients,
+ * path [.] = L in metres. *n_out receives the record count. Synchronises. */
+int sbr_get_records(sbr_ctx* ctx, int64_t angle, int64_t cap, int64_t* ray_ids, float* coef, double* path,
+                    int64_t* n_out);
+
+/* Ray spacing for `rays_per_lambda` rays per wavelength at frequency f_max_hz:
+ * ds = c0 / (f_max_hz * rays_per_lambda); the paper's sampling rule (Sec. 4)
+ * asks for ds <= lambda / 5. Returns a negative value for bad arguments. */
+double sbr_spacing_for(double f_max_hz, double rays_per_lambda);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SBR_H_ */

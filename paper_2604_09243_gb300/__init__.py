@@ -1,0 +1,9 @@
+"""GB300 (sm_103a) shooting-and-bouncing-rays trace-integrate path for monostatic RCS.
+
+The compute path lives in ``lib/libsbr.so`` (CUDA, C ABI in ``include/sbr.h``);
+``sbr`` is its ctypes binding. Build with ``paper_2604_09243_gb300.build.build()``.
+"""
+from .sbr import (  # noqa: F401
+    Context, SbrError, lib, ray_grid, spacing_for, version, POL_ORDER, EXPORTS,
+    TRACE_PHASE_LITERAL_2R, TRACE_REQUIRE_ESCAPE, TRACE_RECORD_HITS, TRACE_COUNT_VISITS,
+)

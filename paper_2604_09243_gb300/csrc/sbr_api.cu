@@ -1,0 +1,781 @@
+// sbr_api.cu -- host runtime behind the C ABI declared in include/sbr.h:
+// context and stream ownership, device buffers, per-aspect ray frames
+// (Eq. L1-L3), the chunked trace driver (Algorithm 2 as a wavefront of
+// persistent passes) and the PO integration driver (Eq. po_sum).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/sbr.h"
+#include "sbr_internal.h"
+
+using namespace sbr;
+
+namespace {
+
+constexpr double kC0 = 299792458.0;
+constexpr double kPi = 3.14159265358979323846;
+constexpr long long kChunkRays = 1ll << 27;  // rays per trace chunk (queues: 2 x 12.9 GB at this size)
+constexpr int kPoItem = 1024;                 // records per PO item (matches sbr_po.cu)
+constexpr int kMaxBounces = 64;
+
+std::string g_create_error;
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    cudaError_t ensure(size_t bytes)
+    {
+        if (bytes <= cap) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        size_t want = std::max(bytes, (size_t)256);
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e == cudaSuccess) cap = want;
+        return e;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+    template <class T>
+    T* as() const { return (T*)p; }
+};
+
+struct AngleHost {
+    sbr_ray_grid grid;
+    long long ray_begin;  // first ray (padded layout) over the whole trace
+    long long rec_begin, rec_count;
+};
+
+}  // namespace
+
+struct sbr_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int n_sms = 0, trace_bps = 1;
+    std::string err;
+    // mesh
+    long long n_vert = 0, n_tri = 0;
+    DevBuf xyz, tri;
+    float bbox[6] = {0, 0, 0, 0, 0, 0};
+    bool has_mesh = false, has_bvh = false;
+    // BVH
+    DevBuf nodes, tris, bvh_scratch, bbox_dev, err_dev;
+    // trace
+    DevBuf angles, rayoff, mask, tilebase, scan_scr, recoff, q0, q1, ctr64, ctr32, stats, rec;
+    DevBuf hit_tri, hit_t, hit_nb;
+    long long rec_total = 0;
+    int max_bounces = 0, trace_flags = 0;
+    bool has_trace = false;
+    std::vector<AngleHost> ang;
+    // PO
+    DevBuf items, itemoff, freq, kfreq, partial, E, rcs;
+    // pinned staging
+    void* host_stage = nullptr;
+    size_t host_stage_cap = 0;
+    cudaEvent_t stage_ev = nullptr;  // recorded after the last enqueued copy that touches host_stage
+    std::vector<cudaEvent_t> evpool; // pass timing events (SBR_TRACE_TIME_PASSES)
+};
+
+namespace {
+
+int fail(sbr_ctx* c, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+int cuda_fail(sbr_ctx* c, cudaError_t e, const char* what)
+{
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(c, SBR_ERR_OOM, "%s: out of device memory", what);
+    }
+    return fail(c, SBR_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+void* stage(sbr_ctx* c, size_t bytes)
+{
+    if (c->stage_ev) cudaEventSynchronize(c->stage_ev);  // earlier async copies may still read it
+    if (bytes > c->host_stage_cap) {
+        if (c->host_stage) {
+            cudaStreamSynchronize(c->stream);
+            cudaFreeHost(c->host_stage);
+        }
+        c->host_stage = nullptr;
+        c->host_stage_cap = 0;
+        size_t want = std::max(bytes, (size_t)(1 << 20));
+        if (cudaMallocHost(&c->host_stage, want) != cudaSuccess) return nullptr;
+        c->host_stage_cap = want;
+    }
+    return c->host_stage;
+}
+
+// Per-aspect grid (Eq. L1-L3) in FP64, rounded once to FP32 where the device uses it.
+// Arithmetic order is part of the ray-grid convention (bit-identical rays on
+// every implementation of it); this file is built without FP contraction.
+void make_grid(const float* bbox, double az_deg, double el_deg, double ds, double eta, const sbr_trace_opts* opt,
+               sbr_ray_grid* g)
+{
+    memset(g, 0, sizeof(*g));
+    const double a = az_deg * (kPi / 180.0), e = el_deg * (kPi / 180.0);
+    const double ca = cos(a), sa = sin(a), ce = cos(e), se = sin(e);
+    g->rhat[0] = ce * ca;
+    g->rhat[1] = ce * sa;
+    g->rhat[2] = se;
+    for (int k = 0; k < 3; ++k) g->khat[k] = -g->rhat[k];
+    g->vhat[0] = se * ca;
+    g->vhat[1] = se * sa;
+    g->vhat[2] = -ce;
+    g->hhat[0] = -sa;
+    g->hhat[1] = ca;
+    g->hhat[2] = 0.0;
+    double lo[3], hi[3], mid[3], s2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = (double)bbox[k];
+        hi[k] = (double)bbox[3 + k];
+        mid[k] = 0.5 * (lo[k] + hi[k]);
+        s2 += (hi[k] - lo[k]) * (hi[k] - lo[k]);
+    }
+    const double diag = sqrt(s2);
+    const double D = 0.5 * diag + 1.0;
+    double umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
+    for (int m = 0; m < 8; ++m) {
+        const double p[3] = {(m & 1) ? hi[0] : lo[0], (m & 2) ? hi[1] : lo[1], (m & 4) ? hi[2] : lo[2]};
+        const double pu = p[0] * g->hhat[0] + p[1] * g->hhat[1] + p[2] * g->hhat[2];
+        const double pv = p[0] * g->vhat[0] + p[1] * g->vhat[1] + p[2] * g->vhat[2];
+        umin = std::min(umin, pu);
+        umax = std::max(umax, pu);
+        vmin = std::min(vmin, pv);
+        vmax = std::max(vmax, pv);
+    }
+    g->lu = umax - umin;
+    g->lv = vmax - vmin;
+    const double window = opt ? opt->window_m : 0.0;
+    double xu, xv;
+    if (window > 0.0) {
+        xu = window / ds;
+        xv = xu;
+    } else {
+        xu = (1.0 + eta) * g->lu / ds;
+        xv = (1.0 + eta) * g->lv / ds;
+    }
+    g->nu = std::max<int64_t>(1, (int64_t)ceil(xu - 1e-9));
+    g->nv = std::max<int64_t>(1, (int64_t)ceil(xv - 1e-9));
+    g->spacing = ds;
+    g->eps = 1e-5 * diag;
+    const double offu = opt ? opt->offset_u : 0.0, offv = opt ? opt->offset_v : 0.0;
+    const double au = (0.5 - 0.5 * (double)g->nu + offu) * ds;
+    const double av = (0.5 - 0.5 * (double)g->nv + offv) * ds;
+    for (int k = 0; k < 3; ++k) {
+        g->p0[k] = (float)(((mid[k] - D * g->khat[k]) + au * g->hhat[k]) + av * g->vhat[k]);
+        g->du[k] = (float)(ds * g->hhat[k]);
+        g->dv[k] = (float)(ds * g->vhat[k]);
+        g->dir[k] = (float)g->khat[k];
+    }
+}
+
+AngleDev to_dev(const sbr_ray_grid& g, long long ray_off)
+{
+    AngleDev d;
+    memset(&d, 0, sizeof(d));
+    for (int k = 0; k < 3; ++k) {
+        d.p0[k] = g.p0[k];
+        d.du[k] = g.du[k];
+        d.dv[k] = g.dv[k];
+        d.dir[k] = g.dir[k];
+        d.rhat[k] = (float)g.rhat[k];
+        d.vhat[k] = (float)g.vhat[k];
+        d.hhat[k] = (float)g.hhat[k];
+    }
+    d.dA = (float)(g.spacing * g.spacing);
+    d.eps = (float)g.eps;
+    d.nu = (int)g.nu;
+    d.nv = (int)g.nv;
+    d.ray_off = ray_off;
+    return d;
+}
+
+long long pad32(long long n) { return (n + 31) & ~31ll; }
+
+}  // namespace
+
+extern "C" {
+
+int sbr_version(void) { return SBR_VERSION_MAJOR * 100 + SBR_VERSION_MINOR; }
+
+const char* sbr_last_error(const sbr_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+double sbr_spacing_for(double f_max_hz, double rays_per_lambda)
+{
+    if (!(f_max_hz > 0.0) || !(rays_per_lambda > 0.0)) return -1.0;
+    return kC0 / (f_max_hz * rays_per_lambda);
+}
+
+int sbr_create(sbr_ctx** out, int device, void* cuda_stream)
+{
+    if (!out) {
+        g_create_error = "sbr_create: null output pointer";
+        return SBR_ERR_ARG;
+    }
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        g_create_error = std::string("sbr_create: no CUDA device (") + cudaGetErrorString(e) + ")";
+        return SBR_ERR_NODEV;
+    }
+    if (device < 0 || device >= n) {
+        g_create_error = "sbr_create: device index out of range";
+        return SBR_ERR_ARG;
+    }
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("sbr_create: cudaSetDevice: ") + cudaGetErrorString(e);
+        return SBR_ERR_CUDA;
+    }
+    sbr_ctx* c = new sbr_ctx();
+    c->device = device;
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            g_create_error = std::string("sbr_create: stream: ") + cudaGetErrorString(e);
+            delete c;
+            return SBR_ERR_CUDA;
+        }
+        c->own_stream = true;
+    }
+    cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, device);
+    e = cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("sbr_create: event: ") + cudaGetErrorString(e);
+        if (c->own_stream) cudaStreamDestroy(c->stream);
+        delete c;
+        return SBR_ERR_CUDA;
+    }
+    c->trace_bps = trace_blocks_per_sm();
+    *out = c;
+    return SBR_OK;
+}
+
+void sbr_destroy(sbr_ctx* c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    DevBuf* all[] = {&c->xyz, &c->tri, &c->nodes, &c->tris, &c->bvh_scratch, &c->bbox_dev, &c->err_dev,
+                     &c->angles, &c->rayoff, &c->mask, &c->tilebase, &c->scan_scr, &c->recoff, &c->q0, &c->q1,
+                     &c->ctr64, &c->ctr32, &c->stats, &c->rec, &c->hit_tri, &c->hit_t, &c->hit_nb, &c->items,
+                     &c->itemoff, &c->freq, &c->kfreq, &c->partial, &c->E, &c->rcs};
+    for (DevBuf* b : all) b->release();
+    if (c->host_stage) cudaFreeHost(c->host_stage);
+    if (c->stage_ev) cudaEventDestroy(c->stage_ev);
+    for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int sbr_load_mesh(sbr_ctx* c, const float* xyz, int64_t n_vert, const int32_t* tri, int64_t n_tri, int on_device)
+{
+    if (!c) return SBR_ERR_ARG;
+    if (!xyz || !tri || n_vert < 3 || n_tri < 1) return fail(c, SBR_ERR_ARG, "sbr_load_mesh: empty or null mesh");
+    if (n_tri >= (1ll << 27)) return fail(c, SBR_ERR_ARG, "sbr_load_mesh: at most 2^27 - 1 triangles");
+    if (n_vert >= (1ll << 31)) return fail(c, SBR_ERR_ARG, "sbr_load_mesh: at most 2^31 - 1 vertices");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    c->has_mesh = c->has_bvh = c->has_trace = false;
+    if (!on_device) {
+        for (int64_t i = 0; i < 3 * n_tri; ++i)
+            if (tri[i] < 0 || tri[i] >= n_vert) return fail(c, SBR_ERR_ARG, "sbr_load_mesh: index %lld out of range", (long long)i);
+    }
+    CK(c->xyz.ensure(sizeof(float) * 3 * (size_t)n_vert), "alloc xyz");
+    CK(c->tri.ensure(sizeof(int32_t) * 3 * (size_t)n_tri), "alloc tri");
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(c->xyz.p, xyz, sizeof(float) * 3 * (size_t)n_vert, kind, c->stream), "copy xyz");
+    CK(cudaMemcpyAsync(c->tri.p, tri, sizeof(int32_t) * 3 * (size_t)n_tri, kind, c->stream), "copy tri");
+    c->n_vert = n_vert;
+    c->n_tri = n_tri;
+    // exact scene box and index check run as part of the BVH build; build the
+    // box now so sbr_get_bbox / sbr_ray_grid_for work right after loading
+    c->has_mesh = true;
+    return sbr_build_bvh(c, nullptr);
+}
+
+int sbr_get_bbox(sbr_ctx* c, float* bbox6)
+{
+    if (!c || !bbox6) return SBR_ERR_ARG;
+    if (!c->has_mesh) return fail(c, SBR_ERR_STATE, "sbr_get_bbox: no mesh loaded");
+    memcpy(bbox6, c->bbox, sizeof(c->bbox));
+    return SBR_OK;
+}
+
+int sbr_build_bvh(sbr_ctx* c, const sbr_bvh_opts* opt)
+{
+    if (!c) return SBR_ERR_ARG;
+    if (!c->has_mesh) return fail(c, SBR_ERR_STATE, "sbr_build_bvh: no mesh loaded");
+    int leaf_max = opt ? opt->leaf_max : 4;
+    float ct = opt ? opt->cost_traverse : 1.f, ci = opt ? opt->cost_intersect : 1.f;
+    if (leaf_max < 1 || leaf_max > kLeafMax) return fail(c, SBR_ERR_ARG, "sbr_build_bvh: leaf_max must be 1..16");
+    if (!(ct >= 0.f) || !(ci > 0.f)) return fail(c, SBR_ERR_ARG, "sbr_build_bvh: costs must be C_T >= 0, C_I > 0");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    const long long n = c->n_tri;
+    const long long n_nodes = n > 1 ? n - 1 : 1;
+    CK(c->nodes.ensure(sizeof(float4) * 4 * (size_t)n_nodes), "alloc nodes");
+    CK(c->tris.ensure(sizeof(float4) * 3 * (size_t)n), "alloc tris");
+    size_t sb = bvh_scratch_bytes(n);
+    CK(c->bvh_scratch.ensure(sb), "alloc bvh scratch");
+    CK(c->bbox_dev.ensure(sizeof(float) * 8), "alloc bbox");
+    CK(c->err_dev.ensure(sizeof(int) * 4), "alloc err");
+    BvhBuild b;
+    b.xyz = c->xyz.as<float>();
+    b.tri = c->tri.as<int>();
+    b.n_vert = c->n_vert;
+    b.n_tri = n;
+    b.leaf_max = leaf_max;
+    b.c_t = ct;
+    b.c_i = ci;
+    b.nodes = c->nodes.as<float4>();
+    b.tris = c->tris.as<float4>();
+    b.bbox_out = c->bbox_dev.as<float>();
+    b.err_flag = c->err_dev.as<int>();
+    b.scratch = c->bvh_scratch.p;
+    b.scratch_bytes = c->bvh_scratch.cap;
+    CK(bvh_build(b, c->stream), "bvh build");
+    float hb[8];
+    int herr = 0;
+    CK(cudaMemcpyAsync(hb, c->bbox_dev.p, sizeof(float) * 6, cudaMemcpyDeviceToHost, c->stream), "copy bbox");
+    CK(cudaMemcpyAsync(&herr, c->err_dev.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "copy err");
+    CK(cudaStreamSynchronize(c->stream), "bvh build sync");
+    if (herr) {
+        c->has_mesh = false;
+        return fail(c, SBR_ERR_ARG, "sbr_build_bvh: triangle index out of range");
+    }
+    memcpy(c->bbox, hb, sizeof(c->bbox));
+    c->has_bvh = true;
+    c->has_trace = false;
+    return SBR_OK;
+}
+
+int sbr_ray_grid_for(sbr_ctx* c, double az_deg, double el_deg, double ds, double eta, const sbr_trace_opts* opt,
+                     sbr_ray_grid* out)
+{
+    if (!c || !out) return SBR_ERR_ARG;
+    if (!c->has_mesh) return fail(c, SBR_ERR_STATE, "sbr_ray_grid_for: no mesh loaded");
+    if (!(ds > 0.0) || !(eta >= 0.0)) return fail(c, SBR_ERR_ARG, "sbr_ray_grid_for: spacing must be > 0, eta >= 0");
+    make_grid(c->bbox, az_deg, el_deg, ds, eta, opt, out);
+    return SBR_OK;
+}
+
+int sbr_ray_grid_box(const float* bbox6, double az_deg, double el_deg, double ds, double eta, const sbr_trace_opts* opt,
+                 sbr_ray_grid* out)
+{
+    if (!bbox6 || !out) return SBR_ERR_ARG;
+    if (!(ds > 0.0) || !(eta >= 0.0)) return SBR_ERR_ARG;
+    make_grid(bbox6, az_deg, el_deg, ds, eta, opt, out);
+    return SBR_OK;
+}
+
+int sbr_trace(sbr_ctx* c, const double* az_el, int64_t n_angles, double ds, double eta, int max_bounces,
+              const sbr_trace_opts* opt, sbr_trace_stats* stats)
+{
+    if (!c) return SBR_ERR_ARG;
+    if (!c->has_bvh) return fail(c, SBR_ERR_STATE, "sbr_trace: no BVH (load a mesh first)");
+    if (!az_el || n_angles < 1) return fail(c, SBR_ERR_ARG, "sbr_trace: no angles");
+    if (n_angles > (1ll << 30)) return fail(c, SBR_ERR_ARG, "sbr_trace: too many angles");
+    if (!(ds > 0.0) || !(eta >= 0.0)) return fail(c, SBR_ERR_ARG, "sbr_trace: spacing must be > 0, eta >= 0");
+    if (max_bounces < 1 || max_bounces > kMaxBounces) return fail(c, SBR_ERR_ARG, "sbr_trace: max_bounces in 1..64");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    const int flags = opt ? opt->flags : 0;
+    const bool escape = flags & SBR_TRACE_REQUIRE_ESCAPE;
+    const bool hits = flags & SBR_TRACE_RECORD_HITS;
+    const bool count = flags & SBR_TRACE_COUNT_VISITS;
+    const long long chunk_cap = (opt && opt->chunk_rays > 0) ? std::max<long long>(32, opt->chunk_rays) : kChunkRays;
+    c->has_trace = false;
+    c->ang.resize((size_t)n_angles);
+    long long total = 0, launched = 0;
+    for (int64_t a = 0; a < n_angles; ++a) {
+        AngleHost& h = c->ang[(size_t)a];
+        make_grid(c->bbox, az_el[2 * a], az_el[2 * a + 1], ds, eta, opt, &h.grid);
+        const long long nr = h.grid.nu * h.grid.nv;
+        if (h.grid.nu > (1ll << 30) || h.grid.nv > (1ll << 30) || pad32(nr) > chunk_cap)
+            return fail(c, SBR_ERR_ARG, "sbr_trace: ray grid of angle %lld too large (%lld x %lld)", (long long)a,
+                        (long long)h.grid.nu, (long long)h.grid.nv);
+        h.ray_begin = total;
+        total += pad32(nr);
+        launched += nr;
+    }
+    // chunks of consecutive angles
+    std::vector<int64_t> cut{0};
+    {
+        long long acc = 0;
+        for (int64_t a = 0; a < n_angles; ++a) {
+            long long r = pad32(c->ang[(size_t)a].grid.nu * c->ang[(size_t)a].grid.nv);
+            if (acc > 0 && acc + r > chunk_cap) {
+                cut.push_back(a);
+                acc = 0;
+            }
+            acc += r;
+        }
+        cut.push_back(n_angles);
+    }
+    long long max_chunk = 0;
+    int max_chunk_angles = 0;
+    for (size_t k = 0; k + 1 < cut.size(); ++k) {
+        long long r = c->ang[(size_t)cut[k + 1] - 1].ray_begin + pad32(c->ang[(size_t)cut[k + 1] - 1].grid.nu *
+                                                                         c->ang[(size_t)cut[k + 1] - 1].grid.nv) -
+                      c->ang[(size_t)cut[k]].ray_begin;
+        max_chunk = std::max(max_chunk, r);
+        max_chunk_angles = std::max(max_chunk_angles, (int)(cut[k + 1] - cut[k]));
+    }
+    const long long max_tiles = max_chunk / 32;
+    CK(c->angles.ensure(sizeof(AngleDev) * (size_t)max_chunk_angles), "alloc angles");
+    CK(c->rayoff.ensure(sizeof(long long) * (size_t)(max_chunk_angles + 1)), "alloc ray offsets");
+    CK(c->recoff.ensure(sizeof(unsigned) * (size_t)(max_chunk_angles + 1)), "alloc record offsets");
+    CK(c->mask.ensure(sizeof(unsigned) * (size_t)max_tiles), "alloc mask");
+    CK(c->tilebase.ensure(sizeof(unsigned) * (size_t)max_tiles), "alloc tile base");
+    CK(c->scan_scr.ensure(scan_scratch_bytes(max_tiles)), "alloc scan scratch");
+    CK(c->q0.ensure(sizeof(RayState) * (size_t)max_chunk), "alloc ray queue");
+    CK(c->q1.ensure(sizeof(RayState) * (size_t)max_chunk), "alloc ray queue");
+    CK(c->ctr64.ensure(sizeof(unsigned long long) * 2 * (kMaxBounces + 2)), "alloc counters");
+    CK(c->ctr32.ensure(sizeof(unsigned) * 2 * (kMaxBounces + 2) + 64), "alloc counters");
+    CK(c->stats.ensure(sizeof(unsigned long long) * kStatCount), "alloc stats");
+    CK(cudaMemsetAsync(c->stats.p, 0, sizeof(unsigned long long) * kStatCount, c->stream), "memset stats");
+    if (hits) {
+        CK(c->hit_tri.ensure(sizeof(int) * (size_t)total * max_bounces), "alloc hit ids");
+        CK(c->hit_t.ensure(sizeof(float) * (size_t)total * max_bounces), "alloc hit t");
+        CK(c->hit_nb.ensure(sizeof(int) * (size_t)total), "alloc hit counts");
+        CK(cudaMemsetAsync(c->hit_tri.p, 0xFF, sizeof(int) * (size_t)total * max_bounces, c->stream), "memset");
+        CK(cudaMemsetAsync(c->hit_t.p, 0, sizeof(float) * (size_t)total * max_bounces, c->stream), "memset");
+        CK(cudaMemsetAsync(c->hit_nb.p, 0, sizeof(int) * (size_t)total, c->stream), "memset");
+    }
+    const int n_blocks = c->n_sms * c->trace_bps;
+    const bool timed = flags & SBR_TRACE_TIME_PASSES;
+    int64_t n_launch = 0, n_pass = 0;
+    size_t n_ev = 0;
+    auto ev = [&](size_t i) -> cudaEvent_t {
+        while (c->evpool.size() <= i) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            c->evpool.push_back(e);
+        }
+        return c->evpool[i];
+    };
+    auto pass = [&](const TraceArgs& t) -> cudaError_t {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (timed) {
+            e0 = ev(n_ev);
+            e1 = ev(n_ev + 1);
+            if (!e0 || !e1) return cudaErrorMemoryAllocation;
+            n_ev += 2;
+            cudaEventRecord(e0, c->stream);
+        }
+        cudaError_t e = launch_trace(t, n_blocks, count, c->stream);
+        if (timed) cudaEventRecord(e1, c->stream);
+        ++n_launch;
+        ++n_pass;
+        return e;
+    };
+    c->rec_total = 0;
+    unsigned* q_count = c->ctr32.as<unsigned>();
+    unsigned* total_dev = q_count + 2 * (kMaxBounces + 2);
+    for (size_t k = 0; k + 1 < cut.size(); ++k) {
+        const int64_t a0 = cut[k], a1 = cut[k + 1];
+        const int na = (int)(a1 - a0);
+        const long long base = c->ang[(size_t)a0].ray_begin;
+        const long long chunk_rays = c->ang[(size_t)a1 - 1].ray_begin +
+                                     pad32(c->ang[(size_t)a1 - 1].grid.nu * c->ang[(size_t)a1 - 1].grid.nv) - base;
+        // stage angle table and ray offsets
+        size_t bytes_a = sizeof(AngleDev) * (size_t)na, bytes_o = sizeof(long long) * (size_t)(na + 1);
+        char* hs = (char*)stage(c, bytes_a + bytes_o + sizeof(unsigned) * (size_t)(na + 1));
+        if (!hs) return fail(c, SBR_ERR_OOM, "sbr_trace: pinned staging allocation failed");
+        AngleDev* ha = (AngleDev*)hs;
+        long long* ho = (long long*)(hs + bytes_a);
+        for (int i = 0; i < na; ++i) {
+            const AngleHost& h = c->ang[(size_t)(a0 + i)];
+            ho[i] = h.ray_begin - base;
+            ha[i] = to_dev(h.grid, ho[i]);
+        }
+        ho[na] = chunk_rays;
+        CK(cudaMemcpyAsync(c->angles.p, ha, bytes_a, cudaMemcpyHostToDevice, c->stream), "copy angles");
+        CK(cudaMemcpyAsync(c->rayoff.p, ho, bytes_o, cudaMemcpyHostToDevice, c->stream), "copy ray offsets");
+        CK(cudaMemsetAsync(c->ctr64.p, 0, c->ctr64.cap, c->stream), "memset counters");
+        CK(cudaMemsetAsync(c->ctr32.p, 0, c->ctr32.cap, c->stream), "memset counters");
+        TraceArgs ta;
+        memset(&ta, 0, sizeof(ta));
+        ta.nodes = c->nodes.as<float4>();
+        ta.tris = c->tris.as<float4>();
+        ta.angles = c->angles.as<AngleDev>();
+        ta.ray_off = c->rayoff.as<long long>();
+        ta.n_angles = na;
+        ta.max_bounces = max_bounces;
+        ta.flags = flags;
+        ta.visit_limit = (int)std::min<long long>(2 * c->n_tri + 64, 1ll << 30);
+        ta.total_rays = chunk_rays;
+        ta.mask = c->mask.as<unsigned>();
+        ta.tile_base = c->tilebase.as<unsigned>();
+        ta.stats = c->stats.as<unsigned long long>();
+        if (hits) {
+            ta.hit_tri = c->hit_tri.as<int>() + (size_t)base * max_bounces;
+            ta.hit_t = c->hit_t.as<float>() + (size_t)base * max_bounces;
+            ta.hit_nb = c->hit_nb.as<int>() + base;
+        }
+        RayState* qs[2] = {c->q0.as<RayState>(), c->q1.as<RayState>()};
+        // pass 0: primary rays -> queue 0
+        ta.bounce = 0;
+        ta.work = c->ctr64.as<unsigned long long>();
+        ta.q_out = qs[0];
+        ta.q_out_count = q_count + 1;
+        CK(pass(ta), "trace primary");
+        // dense slots of the valid rays
+        CK(scan_popc(ta.mask, c->tilebase.as<unsigned>(), chunk_rays / 32, total_dev, c->scan_scr.p, c->stream),
+           "scan");
+        n_launch += 3;
+        CK(launch_angle_offsets(ta.ray_off, c->tilebase.as<unsigned>(), total_dev, na, c->recoff.as<unsigned>(),
+                                c->stream),
+           "angle offsets");
+        ++n_launch;
+        unsigned* hro = (unsigned*)(hs + bytes_a + bytes_o);
+        CK(cudaMemcpyAsync(hro, c->recoff.p, sizeof(unsigned) * (size_t)(na + 1), cudaMemcpyDeviceToHost, c->stream),
+           "copy record offsets");
+        CK(cudaStreamSynchronize(c->stream), "trace sync");
+        const long long n_valid = hro[na];
+        for (int i = 0; i < na; ++i) {
+            AngleHost& h = c->ang[(size_t)(a0 + i)];
+            h.rec_begin = c->rec_total + hro[i];
+            h.rec_count = (long long)hro[i + 1] - hro[i];
+        }
+        // grow the record buffer, keeping earlier chunks
+        const size_t need = sizeof(Record) * (size_t)(c->rec_total + n_valid);
+        if (need > c->rec.cap) {
+            DevBuf nb;
+            CK(nb.ensure(need + need / 4), "alloc records");
+            if (c->rec_total > 0)
+                CK(cudaMemcpyAsync(nb.p, c->rec.p, sizeof(Record) * (size_t)c->rec_total, cudaMemcpyDeviceToDevice,
+                                   c->stream),
+                   "copy records");
+            CK(cudaStreamSynchronize(c->stream), "records sync");
+            c->rec.release();
+            c->rec = nb;
+        }
+        ta.rec = c->rec.as<Record>() + c->rec_total;
+        if (max_bounces == 1 && !escape) {
+            ta.q_in = qs[0];
+            ta.q_in_count = q_count + 1;
+            CK(launch_emit_all(ta, n_blocks, c->stream), "emit");
+            ++n_launch;
+        } else {
+            const int last_pass = escape ? max_bounces : max_bounces - 1;
+            for (int b = 1; b <= last_pass; ++b) {
+                ta.bounce = b;
+                ta.work = c->ctr64.as<unsigned long long>() + b;
+                ta.q_in = qs[(b - 1) & 1];
+                ta.q_in_count = q_count + b;
+                ta.q_out = qs[b & 1];
+                ta.q_out_count = q_count + b + 1;
+                CK(pass(ta), "trace bounce");
+            }
+        }
+        c->rec_total += n_valid;
+    }
+    unsigned long long hs_stats[kStatCount];
+    CK(cudaMemcpyAsync(hs_stats, c->stats.p, sizeof(hs_stats), cudaMemcpyDeviceToHost, c->stream), "copy stats");
+    CK(cudaStreamSynchronize(c->stream), "trace end sync");
+    c->max_bounces = max_bounces;
+    c->trace_flags = flags;
+    c->has_trace = true;
+    if (stats) {
+        stats->n_angles = n_angles;
+        stats->rays_launched = launched;
+        stats->ray_bounces = (int64_t)hs_stats[kStatQueries];
+        stats->valid_rays = c->rec_total;
+        stats->node_visits = (int64_t)hs_stats[kStatNodes];
+        stats->tri_tests = (int64_t)hs_stats[kStatTris];
+        stats->stack_overflows = (int64_t)hs_stats[kStatOverflow];
+        stats->kernel_launches = n_launch;
+        stats->pass_launches = n_pass;
+        stats->pass_ms = 0.0;
+        for (size_t i = 0; timed && i + 1 < n_ev; i += 2) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, c->evpool[i], c->evpool[i + 1]) == cudaSuccess) stats->pass_ms += ms;
+        }
+    }
+    if (hs_stats[kStatOverflow])
+        return fail(c, SBR_ERR_STACK_OVERFLOW, "sbr_trace: %llu traversals exceeded the stack depth",
+                    (unsigned long long)hs_stats[kStatOverflow]);
+    return SBR_OK;
+}
+
+int sbr_po_integrate(sbr_ctx* c, const double* freq_hz, int64_t n_freq, int pol_mask, int po_mode, double* E_out,
+                     double* rcs_out, int out_on_device)
+{
+    if (!c) return SBR_ERR_ARG;
+    if (!c->has_trace) return fail(c, SBR_ERR_STATE, "sbr_po_integrate: no trace results");
+    if (!freq_hz || n_freq < 1 || n_freq > (1 << 20)) return fail(c, SBR_ERR_ARG, "sbr_po_integrate: bad frequency list");
+    if (pol_mask <= 0 || pol_mask > 15) return fail(c, SBR_ERR_ARG, "sbr_po_integrate: pol_mask must select HH/VV/HV/VH");
+    const int form = po_mode & 15, prec = po_mode & ~15;
+    if (form != SBR_PO_VECTOR && form != SBR_PO_PAPER_SCALAR)
+        return fail(c, SBR_ERR_ARG, "sbr_po_integrate: unknown PO form");
+    if (prec != SBR_PHASE_COMPENSATED && prec != SBR_PHASE_FP32 && prec != SBR_PHASE_FP64)
+        return fail(c, SBR_ERR_ARG, "sbr_po_integrate: unknown phase precision");
+    for (int64_t f = 0; f < n_freq; ++f)
+        if (!(freq_hz[f] > 0.0)) return fail(c, SBR_ERR_ARG, "sbr_po_integrate: frequencies must be > 0");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    PoArgs pa;
+    memset(&pa, 0, sizeof(pa));
+    pa.n_pol = 0;
+    for (int q = 0; q < 4; ++q)
+        if (pol_mask & (1 << q)) pa.pol_sel[pa.n_pol++] = q;
+    pa.scalar = form == SBR_PO_PAPER_SCALAR;
+    pa.phase_mode = prec == SBR_PHASE_COMPENSATED ? 0 : (prec == SBR_PHASE_FP32 ? 1 : 2);
+    const int na = (int)c->ang.size();
+    // items: consecutive slices of <= kPoItem records per aspect
+    std::vector<int> item_off((size_t)na + 1);
+    std::vector<PoItem> items;
+    for (int a = 0; a < na; ++a) {
+        item_off[(size_t)a] = (int)items.size();
+        const AngleHost& h = c->ang[(size_t)a];
+        for (long long r = 0; r < h.rec_count; r += kPoItem) {
+            PoItem it;
+            it.angle = a;
+            it.first = h.rec_begin + r;
+            it.count = (int)std::min<long long>(kPoItem, h.rec_count - r);
+            items.push_back(it);
+        }
+    }
+    item_off[(size_t)na] = (int)items.size();
+    const int n_items = (int)items.size();
+    const size_t b_items = sizeof(PoItem) * (size_t)std::max(n_items, 1);
+    const size_t b_ioff = sizeof(int) * (size_t)(na + 1);
+    const size_t b_freq = sizeof(float4) * (size_t)n_freq, b_kf = sizeof(double) * (size_t)n_freq;
+    CK(c->items.ensure(b_items), "alloc items");
+    CK(c->itemoff.ensure(b_ioff), "alloc item offsets");
+    CK(c->freq.ensure(b_freq), "alloc freq");
+    CK(c->kfreq.ensure(b_kf), "alloc freq");
+    CK(c->partial.ensure(sizeof(double) * (size_t)std::max(n_items, 1) * (size_t)n_freq * 2 * pa.n_pol),
+       "alloc partials");
+    char* hs = (char*)stage(c, b_items + b_ioff + b_freq + b_kf + 64);
+    if (!hs) return fail(c, SBR_ERR_OOM, "sbr_po_integrate: pinned staging allocation failed");
+    char* p = hs;
+    if (n_items) memcpy(p, items.data(), sizeof(PoItem) * (size_t)n_items);
+    CK(cudaMemcpyAsync(c->items.p, p, sizeof(PoItem) * (size_t)n_items, cudaMemcpyHostToDevice, c->stream), "copy items");
+    p += b_items;
+    memcpy(p, item_off.data(), b_ioff);
+    CK(cudaMemcpyAsync(c->itemoff.p, p, b_ioff, cudaMemcpyHostToDevice, c->stream), "copy item offsets");
+    p += b_ioff;
+    float4* hf = (float4*)p;
+    double* hk = (double*)(p + b_freq);
+    for (int64_t f = 0; f < n_freq; ++f) {
+        const double kappa = freq_hz[f] / kC0;  // cycles per metre
+        const float kh = (float)kappa;
+        const float kl = (float)(kappa - (double)kh);
+        const double k = 2.0 * kPi * freq_hz[f] / kC0;
+        hf[f] = make_float4(kh, kl, (float)k, 0.f);
+        hk[f] = k;
+    }
+    CK(cudaMemcpyAsync(c->freq.p, hf, b_freq, cudaMemcpyHostToDevice, c->stream), "copy freq");
+    CK(cudaMemcpyAsync(c->kfreq.p, hk, b_kf, cudaMemcpyHostToDevice, c->stream), "copy freq");
+    CK(cudaEventRecord(c->stage_ev, c->stream), "record staging event");
+    pa.rec = c->rec.as<Record>();
+    pa.items = c->items.as<PoItem>();
+    pa.n_items = n_items;
+    pa.freq = c->freq.as<float4>();
+    pa.kfreq = c->kfreq.as<double>();
+    pa.n_freq = (int)n_freq;
+    pa.partial = c->partial.as<double>();
+    CK(launch_po(pa, c->stream), "po reduce");
+    const size_t n_out = (size_t)na * (size_t)n_freq * pa.n_pol;
+    double* dE = E_out;
+    double* dR = rcs_out;
+    if (!out_on_device) {
+        CK(c->E.ensure(sizeof(double) * 2 * n_out), "alloc E");
+        CK(c->rcs.ensure(sizeof(double) * n_out), "alloc rcs");
+        dE = E_out ? c->E.as<double>() : nullptr;
+        dR = rcs_out ? c->rcs.as<double>() : nullptr;
+    }
+    CK(launch_po_final(pa.partial, c->itemoff.as<int>(), na, pa.kfreq, (int)n_freq, pa.n_pol, dE, dR, c->stream),
+       "po final");
+    if (!out_on_device) {
+        if (E_out)
+            CK(cudaMemcpyAsync(E_out, dE, sizeof(double) * 2 * n_out, cudaMemcpyDeviceToHost, c->stream), "copy E");
+        if (rcs_out)
+            CK(cudaMemcpyAsync(rcs_out, dR, sizeof(double) * n_out, cudaMemcpyDeviceToHost, c->stream), "copy rcs");
+        CK(cudaStreamSynchronize(c->stream), "po sync");
+    }
+    return SBR_OK;
+}
+
+int sbr_get_hits(sbr_ctx* c, int64_t angle, int32_t* tri_ids, float* t, int32_t* n_bounce)
+{
+    if (!c) return SBR_ERR_ARG;
+    if (!c->has_trace || !(c->trace_flags & SBR_TRACE_RECORD_HITS))
+        return fail(c, SBR_ERR_STATE, "sbr_get_hits: last trace did not record hits");
+    if (angle < 0 || angle >= (int64_t)c->ang.size()) return fail(c, SBR_ERR_ARG, "sbr_get_hits: angle out of range");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    const AngleHost& h = c->ang[(size_t)angle];
+    const size_t nr = (size_t)(h.grid.nu * h.grid.nv), B = (size_t)c->max_bounces;
+    if (tri_ids)
+        CK(cudaMemcpyAsync(tri_ids, c->hit_tri.as<int>() + (size_t)h.ray_begin * B, sizeof(int) * nr * B,
+                           cudaMemcpyDeviceToHost, c->stream),
+           "copy hits");
+    if (t)
+        CK(cudaMemcpyAsync(t, c->hit_t.as<float>() + (size_t)h.ray_begin * B, sizeof(float) * nr * B,
+                           cudaMemcpyDeviceToHost, c->stream),
+           "copy hits");
+    if (n_bounce)
+        CK(cudaMemcpyAsync(n_bounce, c->hit_nb.as<int>() + h.ray_begin, sizeof(int) * nr, cudaMemcpyDeviceToHost,
+                           c->stream),
+           "copy hits");
+    CK(cudaStreamSynchronize(c->stream), "hits sync");
+    return SBR_OK;
+}
+
+int sbr_get_records(sbr_ctx* c, int64_t angle, int64_t cap, int64_t* ray_ids, float* coef, double* path,
+                    int64_t* n_out)
+{
+    if (!c) return SBR_ERR_ARG;
+    if (!c->has_trace) return fail(c, SBR_ERR_STATE, "sbr_get_records: no trace results");
+    if (angle < 0 || angle >= (int64_t)c->ang.size()) return fail(c, SBR_ERR_ARG, "sbr_get_records: angle out of range");
+    const AngleHost& h = c->ang[(size_t)angle];
+    if (n_out) *n_out = h.rec_count;
+    const long long n = std::min<long long>(cap, h.rec_count);
+    if (n <= 0) return SBR_OK;
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    std::vector<Record> r((size_t)n);
+    CK(cudaMemcpyAsync(r.data(), c->rec.as<Record>() + h.rec_begin, sizeof(Record) * (size_t)n, cudaMemcpyDeviceToHost,
+                       c->stream),
+       "copy records");
+    CK(cudaStreamSynchronize(c->stream), "records sync");
+    for (long long i = 0; i < n; ++i) {
+        if (ray_ids) ray_ids[i] = r[(size_t)i].ray;
+        if (coef)
+            for (int q = 0; q < 5; ++q) coef[5 * i + q] = r[(size_t)i].c[q];
+        if (path) path[i] = (double)r[(size_t)i].l_hi + (double)r[(size_t)i].l_lo;
+    }
+    return SBR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,467 @@
+// sbr_bvh.cu -- GPU LBVH builder.
+//
+// The paper builds its BVH on the host by recursive median or binned-SAH
+// partitioning (Sec. 4, Algorithm 1). Here the whole build runs on the GPU:
+//   1. triangle AABBs and centroids, scene boxes (ordered-integer atomics, exact)
+//   2. 63-bit Morton codes of the centroids (21 bits per axis)
+//   3. stable LSD radix sort of (code, triangle) pairs, 8 passes of 8 bits
+//   4. Karras hierarchy: n - 1 internal nodes from the sorted codes, ties broken
+//      by position (Karras 2012, "Maximizing parallelism in the construction of
+//      BVHs, octrees and k-d trees")
+//   5. bottom-up refit with one atomic arrival flag per node; the second arrival
+//      unions the child boxes and evaluates the SAH cost of the paper,
+//      C_T SA(P) + C(L) + C(R) against C_I N SA(P) for collapsing the subtree
+//      into one leaf of at most leaf_max triangles
+//   6. node emission (child boxes stored in the parent) and triangle reorder so
+//      that every leaf is a contiguous range (Sec. 4: leaves reference
+//      contiguous triangle ranges).
+#include <float.h>
+
+#include "sbr_internal.h"
+
+namespace sbr {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kRsThreads = 256;
+constexpr int kRsItems = 8;
+constexpr int kRsTile = kRsThreads * kRsItems;
+constexpr int kRsWarps = kRsThreads / 32;
+
+__device__ __forceinline__ unsigned f2o(float f)
+{
+    unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float o2f(unsigned u)
+{
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
+}
+
+// acc layout (unsigned ordered floats): [0..2] vertex min, [3..5] vertex max,
+// [6..8] centroid min, [9..11] centroid max
+__global__ void k_acc_init(unsigned* acc, int* err)
+{
+    int t = threadIdx.x;
+    if (t < 12) acc[t] = ((t % 6) < 3) ? 0xFFFFFFFFu : 0u;
+    if (t == 0) *err = 0;
+}
+
+__device__ __forceinline__ void warp_minmax_atomic(float3 lo, float3 hi, unsigned* acc_lo, unsigned* acc_hi)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo.x = fminf(lo.x, __shfl_xor_sync(0xffffffffu, lo.x, o));
+        lo.y = fminf(lo.y, __shfl_xor_sync(0xffffffffu, lo.y, o));
+        lo.z = fminf(lo.z, __shfl_xor_sync(0xffffffffu, lo.z, o));
+        hi.x = fmaxf(hi.x, __shfl_xor_sync(0xffffffffu, hi.x, o));
+        hi.y = fmaxf(hi.y, __shfl_xor_sync(0xffffffffu, hi.y, o));
+        hi.z = fmaxf(hi.z, __shfl_xor_sync(0xffffffffu, hi.z, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (lo.x <= hi.x) {
+            atomicMin(acc_lo + 0, f2o(lo.x));
+            atomicMin(acc_lo + 1, f2o(lo.y));
+            atomicMin(acc_lo + 2, f2o(lo.z));
+            atomicMax(acc_hi + 0, f2o(hi.x));
+            atomicMax(acc_hi + 1, f2o(hi.y));
+            atomicMax(acc_hi + 2, f2o(hi.z));
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_vertex_box(const float* xyz, long long nv, unsigned* acc)
+{
+    float3 lo = make_float3(FLT_MAX, FLT_MAX, FLT_MAX), hi = make_float3(-FLT_MAX, -FLT_MAX, -FLT_MAX);
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv; v += (long long)gridDim.x * blockDim.x) {
+        float x = xyz[3 * v], y = xyz[3 * v + 1], z = xyz[3 * v + 2];
+        lo = make_float3(fminf(lo.x, x), fminf(lo.y, y), fminf(lo.z, z));
+        hi = make_float3(fmaxf(hi.x, x), fmaxf(hi.y, y), fmaxf(hi.z, z));
+    }
+    warp_minmax_atomic(lo, hi, acc, acc + 3);
+}
+
+__global__ void __launch_bounds__(kThreads) k_prep(const float* xyz, const int* tri, long long nv, int n,
+                                                   float4* tbox, float4* cen, unsigned* acc, int* err)
+{
+    float3 lo = make_float3(FLT_MAX, FLT_MAX, FLT_MAX), hi = make_float3(-FLT_MAX, -FLT_MAX, -FLT_MAX);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int ia = tri[3 * (long long)i], ib = tri[3 * (long long)i + 1], ic = tri[3 * (long long)i + 2];
+        if (ia < 0 || ib < 0 || ic < 0 || ia >= nv || ib >= nv || ic >= nv) {
+            *err = 1;
+            ia = ib = ic = 0;
+        }
+        float3 a = make_float3(xyz[3 * (long long)ia], xyz[3 * (long long)ia + 1], xyz[3 * (long long)ia + 2]);
+        float3 b = make_float3(xyz[3 * (long long)ib], xyz[3 * (long long)ib + 1], xyz[3 * (long long)ib + 2]);
+        float3 c = make_float3(xyz[3 * (long long)ic], xyz[3 * (long long)ic + 1], xyz[3 * (long long)ic + 2]);
+        float3 bl = make_float3(fminf(a.x, fminf(b.x, c.x)), fminf(a.y, fminf(b.y, c.y)), fminf(a.z, fminf(b.z, c.z)));
+        float3 bh = make_float3(fmaxf(a.x, fmaxf(b.x, c.x)), fmaxf(a.y, fmaxf(b.y, c.y)), fmaxf(a.z, fmaxf(b.z, c.z)));
+        tbox[2 * i] = make_float4(bl.x, bl.y, bl.z, 0.f);
+        tbox[2 * i + 1] = make_float4(bh.x, bh.y, bh.z, 0.f);
+        float3 m = make_float3((a.x + b.x + c.x) * (1.f / 3.f), (a.y + b.y + c.y) * (1.f / 3.f),
+                               (a.z + b.z + c.z) * (1.f / 3.f));
+        cen[i] = make_float4(m.x, m.y, m.z, 0.f);
+        lo = make_float3(fminf(lo.x, m.x), fminf(lo.y, m.y), fminf(lo.z, m.z));
+        hi = make_float3(fmaxf(hi.x, m.x), fmaxf(hi.y, m.y), fmaxf(hi.z, m.z));
+    }
+    warp_minmax_atomic(lo, hi, acc + 6, acc + 9);
+}
+
+__device__ __forceinline__ unsigned long long spread21(unsigned long long x)
+{
+    x &= 0x1fffffull;
+    x = (x | (x << 32)) & 0x1f00000000ffffull;
+    x = (x | (x << 16)) & 0x1f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+__global__ void __launch_bounds__(kThreads) k_morton(const float4* cen, int n, const unsigned* acc,
+                                                     unsigned long long* keys, unsigned* vals, float* bbox_out)
+{
+    float lo[3], sc[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        lo[c] = o2f(acc[6 + c]);
+        float ext = o2f(acc[9 + c]) - lo[c];
+        sc[c] = ext > 0.f ? 2097152.f / ext : 0.f;
+    }
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0 && bbox_out)
+        for (int c = 0; c < 6; ++c) bbox_out[c] = o2f(acc[c]);
+    if (i >= n) return;
+    float4 m = cen[i];
+    unsigned q[3];
+    float mc[3] = {m.x, m.y, m.z};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) q[c] = (unsigned)fminf(fmaxf((mc[c] - lo[c]) * sc[c], 0.f), 2097151.f);
+    keys[i] = (spread21(q[0]) << 2) | (spread21(q[1]) << 1) | spread21(q[2]);
+    vals[i] = (unsigned)i;
+}
+
+// ---------------------------------------------------------------- radix sort
+__global__ void __launch_bounds__(kRsThreads) k_rs_hist(const unsigned long long* keys, int n, int shift,
+                                                        unsigned* hist, int nb)
+{
+    __shared__ unsigned s_h[256];
+    s_h[threadIdx.x] = 0;
+    __syncthreads();
+    int base = blockIdx.x * kRsTile;
+#pragma unroll
+    for (int r = 0; r < kRsItems; ++r) {
+        int i = base + r * kRsThreads + threadIdx.x;
+        if (i < n) atomicAdd(&s_h[(unsigned)(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[threadIdx.x * nb + blockIdx.x] = s_h[threadIdx.x];  // digit-major
+}
+
+// stable scatter: keys of a tile are ranked in index order, warp by warp
+__global__ void __launch_bounds__(kRsThreads) k_rs_scatter(const unsigned long long* kin, const unsigned* vin,
+                                                           unsigned long long* kout, unsigned* vout, int n,
+                                                           int shift, const unsigned* hist, int nb)
+{
+    __shared__ unsigned s_base[256];
+    __shared__ unsigned s_cnt[kRsWarps][256];
+    __shared__ unsigned s_off[kRsWarps][256];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    s_base[t] = hist[t * nb + blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kRsWarps; ++k) s_cnt[k][t] = 0;
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    int base = blockIdx.x * kRsTile;
+    for (int r = 0; r < kRsItems; ++r) {
+        int i = base + r * kRsThreads + t;
+        bool ok = i < n;
+        unsigned long long key = ok ? kin[i] : 0ull;
+        unsigned val = ok ? vin[i] : 0u;
+        unsigned d = ok ? ((unsigned)(key >> shift) & 255u) : 256u;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        unsigned rank = __popc(peers & lt);
+        if (ok && rank == 0) s_cnt[w][d] = __popc(peers);
+        __syncthreads();
+        {
+            unsigned run = s_base[t];
+#pragma unroll
+            for (int k = 0; k < kRsWarps; ++k) {
+                s_off[k][t] = run;
+                run += s_cnt[k][t];
+                s_cnt[k][t] = 0;
+            }
+            s_base[t] = run;
+        }
+        __syncthreads();
+        if (ok) {
+            unsigned dst = s_off[w][d] + rank;
+            if (dst < (unsigned)n) {
+                kout[dst] = key;
+                vout[dst] = val;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- Karras hierarchy
+__device__ __forceinline__ int delta(const unsigned long long* k, int n, int i, int j)
+{
+    if (j < 0 || j >= n) return -1;
+    unsigned long long a = k[i], b = k[j];
+    if (a == b) return 64 + __clz((unsigned)(i ^ j));
+    return __clzll(a ^ b);
+}
+
+// child encoding: c >= 0 internal node c, c < 0 leaf ~c (sorted primitive)
+__global__ void __launch_bounds__(kThreads) k_karras(const unsigned long long* k, int n, int* left, int* right,
+                                                     int* first, int* last, int* par_int, int* par_leaf)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int d = (delta(k, n, i, i + 1) - delta(k, n, i, i - 1)) >= 0 ? 1 : -1;
+    int dmin = delta(k, n, i, i - d);
+    int lmax = 2;
+    while (delta(k, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+        if (delta(k, n, i, i + (l + t) * d) > dmin) l += t;
+    int j = i + l * d;
+    int dnode = delta(k, n, i, j);
+    int s = 0, t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (delta(k, n, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    int g = i + s * d + min(d, 0);
+    int lo = min(i, j), hi = max(i, j);
+    int lc = (lo == g) ? ~g : g;
+    int rc = (hi == g + 1) ? ~(g + 1) : g + 1;
+    left[i] = lc;
+    right[i] = rc;
+    first[i] = lo;
+    last[i] = hi;
+    if (lc >= 0) par_int[lc] = i; else par_leaf[~lc] = i;
+    if (rc >= 0) par_int[rc] = i; else par_leaf[~rc] = i;
+}
+
+__device__ __forceinline__ float area(float4 lo, float4 hi)
+{
+    float dx = hi.x - lo.x, dy = hi.y - lo.y, dz = hi.z - lo.z;
+    return 2.f * (dx * dy + dy * dz + dz * dx);
+}
+
+// bottom-up refit; leaf data: lbox (sorted order); node data: nbox, ncnt, ncost, ncol
+__global__ void __launch_bounds__(kThreads) k_refit(const unsigned* vals, const float4* tbox, int n,
+                                                    const int* left, const int* right, const int* par_int,
+                                                    const int* par_leaf, int* flags, float4* lbox, float4* nbox,
+                                                    int* ncnt, float* ncost, int* ncol, int leaf_max, float c_t,
+                                                    float c_i)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    unsigned tid = vals[p];
+    lbox[2 * p] = tbox[2 * tid];
+    lbox[2 * p + 1] = tbox[2 * tid + 1];
+    if (n == 1) return;
+    __threadfence();
+    int node = par_leaf[p];
+    // a walk to the root passes at most n - 1 internal nodes; the bound guards
+    // against a malformed hierarchy
+    for (int steps = 0; steps < n && node >= 0 && node < n - 1; ++steps) {
+        if (atomicAdd(&flags[node], 1) == 0) return;  // first arrival: the sibling finishes the node
+        __threadfence();
+        int ch[2] = {left[node], right[node]};
+        float4 lo = make_float4(FLT_MAX, FLT_MAX, FLT_MAX, 0.f), hi = make_float4(-FLT_MAX, -FLT_MAX, -FLT_MAX, 0.f);
+        int cnt = 0;
+        float cost = 0.f;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            float4 a, b;
+            int c = ch[s];
+            if (c < 0) {
+                a = __ldcg(lbox + 2 * (~c));
+                b = __ldcg(lbox + 2 * (~c) + 1);
+                cnt += 1;
+                cost += c_i * area(a, b);
+            } else {
+                a = __ldcg(nbox + 2 * c);
+                b = __ldcg(nbox + 2 * c + 1);
+                cnt += __ldcg(ncnt + c);
+                cost += __ldcg(ncost + c);
+            }
+            lo = make_float4(fminf(lo.x, a.x), fminf(lo.y, a.y), fminf(lo.z, a.z), 0.f);
+            hi = make_float4(fmaxf(hi.x, b.x), fmaxf(hi.y, b.y), fmaxf(hi.z, b.z), 0.f);
+        }
+        float sa = area(lo, hi);
+        float split = c_t * sa + cost;
+        float as_leaf = c_i * (float)cnt * sa;
+        int col = (cnt <= leaf_max) && (as_leaf <= split);
+        nbox[2 * node] = lo;
+        nbox[2 * node + 1] = hi;
+        ncnt[node] = cnt;
+        ncost[node] = col ? as_leaf : split;
+        ncol[node] = col;
+        __threadfence();
+        if (node == 0) return;
+        node = par_int[node];
+    }
+}
+
+
+__device__ __forceinline__ void put_node(float4* out, int i, float4 llo, float4 lhi, float4 rlo, float4 rhi, int lr,
+                                         int rr)
+{
+    out[4 * i + 0] = make_float4(llo.x, lhi.x, llo.y, lhi.y);
+    out[4 * i + 1] = make_float4(rlo.x, rhi.x, rlo.y, rhi.y);
+    out[4 * i + 2] = make_float4(llo.z, lhi.z, rlo.z, rhi.z);
+    out[4 * i + 3] = make_float4(__int_as_float(lr), __int_as_float(rr), 0.f, 0.f);
+}
+
+__global__ void __launch_bounds__(kThreads) k_emit(int n, const int* left, const int* right, const int* first,
+                                                   const float4* lbox, const float4* nbox, const int* ncnt,
+                                                   const int* ncol, float4* nodes)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const float4 elo = make_float4(FLT_MAX, FLT_MAX, FLT_MAX, 0.f), ehi = make_float4(-FLT_MAX, -FLT_MAX, -FLT_MAX, 0.f);
+    if (n == 1) {
+        if (i == 0) put_node(nodes, 0, lbox[0], lbox[1], elo, ehi, leaf_ref(0, 1), kEmptyRef);
+        return;
+    }
+    if (i >= n - 1) return;
+    if (ncol[i]) {
+        if (i == 0) put_node(nodes, 0, nbox[0], nbox[1], elo, ehi, leaf_ref(0, ncnt[0]), kEmptyRef);
+        return;
+    }
+    float4 bl[2], bh[2];
+    int ref[2];
+    int ch[2] = {left[i], right[i]};
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        int c = ch[s];
+        if (c < 0) {
+            bl[s] = lbox[2 * (~c)];
+            bh[s] = lbox[2 * (~c) + 1];
+            ref[s] = leaf_ref(~c, 1);
+        } else {
+            bl[s] = nbox[2 * c];
+            bh[s] = nbox[2 * c + 1];
+            ref[s] = ncol[c] ? leaf_ref(first[c], ncnt[c]) : c;
+        }
+    }
+    put_node(nodes, i, bl[0], bh[0], bl[1], bh[1], ref[0], ref[1]);
+}
+
+__global__ void __launch_bounds__(kThreads) k_reorder(const float* xyz, const int* tri, long long nv,
+                                                      const unsigned* vals, int n, float4* tris)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    unsigned t = vals[p];
+    int ia = tri[3 * (long long)t], ib = tri[3 * (long long)t + 1], ic = tri[3 * (long long)t + 2];
+    if (ia < 0 || ib < 0 || ic < 0 || ia >= nv || ib >= nv || ic >= nv) ia = ib = ic = 0;
+    float ax = xyz[3 * (long long)ia], ay = xyz[3 * (long long)ia + 1], az = xyz[3 * (long long)ia + 2];
+    float bx = xyz[3 * (long long)ib], by = xyz[3 * (long long)ib + 1], bz = xyz[3 * (long long)ib + 2];
+    float cx = xyz[3 * (long long)ic], cy = xyz[3 * (long long)ic + 1], cz = xyz[3 * (long long)ic + 2];
+    tris[3 * p + 0] = make_float4(ax, ay, az, __int_as_float((int)t));
+    tris[3 * p + 1] = make_float4(bx - ax, by - ay, bz - az, 0.f);
+    tris[3 * p + 2] = make_float4(cx - ax, cy - ay, cz - az, 0.f);
+}
+
+struct Carve {
+    char* p;
+    size_t off, cap;
+    template <class T>
+    T* take(size_t count)
+    {
+        size_t o = (off + 255) & ~(size_t)255;
+        off = o + count * sizeof(T);
+        return (T*)(p + o);
+    }
+};
+
+}  // namespace
+
+size_t bvh_scratch_bytes(long long n_tri)
+{
+    size_t n = (size_t)(n_tri < 2 ? 2 : n_tri);
+    size_t nb = (n + kRsTile - 1) / kRsTile;
+    size_t b = 0;
+    auto add = [&](size_t bytes) { b = ((b + 255) & ~(size_t)255) + bytes; };
+    add(64);                                // acc
+    add(n * 32);                            // tbox
+    add(n * 16);                            // cen
+    add(n * 8); add(n * 8);                 // keys x2
+    add(n * 4); add(n * 4);                 // vals x2
+    add(256 * nb * 4);                      // hist
+    add(scan_scratch_bytes(256 * (long long)nb));
+    for (int k = 0; k < 6; ++k) add(n * 4); // left right first last par_int par_leaf
+    add(n * 4);                             // flags
+    add(n * 32); add(n * 32);               // lbox nbox
+    add(n * 4); add(n * 4); add(n * 4);     // ncnt ncost ncol
+    return b + 256;
+}
+
+cudaError_t bvh_build(const BvhBuild& b, cudaStream_t st)
+{
+    const int n = (int)b.n_tri;
+    if (n < 1) return cudaErrorInvalidValue;
+    Carve cv{(char*)b.scratch, 0, b.scratch_bytes};
+    const int nn = n < 2 ? 2 : n;
+    unsigned* acc = cv.take<unsigned>(16);
+    float4* tbox = cv.take<float4>(2 * (size_t)nn);
+    float4* cen = cv.take<float4>(nn);
+    unsigned long long* k0 = cv.take<unsigned long long>(nn);
+    unsigned long long* k1 = cv.take<unsigned long long>(nn);
+    unsigned* v0 = cv.take<unsigned>(nn);
+    unsigned* v1 = cv.take<unsigned>(nn);
+    const int nb = (nn + kRsTile - 1) / kRsTile;
+    unsigned* hist = cv.take<unsigned>(256 * (size_t)nb);
+    void* sscr = cv.take<char>(scan_scratch_bytes(256 * (long long)nb));
+    int* left = cv.take<int>(nn);
+    int* right = cv.take<int>(nn);
+    int* first = cv.take<int>(nn);
+    int* last = cv.take<int>(nn);
+    int* par_int = cv.take<int>(nn);
+    int* par_leaf = cv.take<int>(nn);
+    int* flags = cv.take<int>(nn);
+    float4* lbox = cv.take<float4>(2 * (size_t)nn);
+    float4* nbox = cv.take<float4>(2 * (size_t)nn);
+    int* ncnt = cv.take<int>(nn);
+    float* ncost = cv.take<float>(nn);
+    int* ncol = cv.take<int>(nn);
+    if (cv.off > cv.cap) return cudaErrorInvalidValue;
+
+    const int g = (n + kThreads - 1) / kThreads;
+    k_acc_init<<<1, 32, 0, st>>>(acc, b.err_flag);
+    int gv = (int)((b.n_vert + kThreads - 1) / kThreads);
+    if (gv > 4096) gv = 4096;
+    k_vertex_box<<<gv, kThreads, 0, st>>>(b.xyz, b.n_vert, acc);
+    k_prep<<<g, kThreads, 0, st>>>(b.xyz, b.tri, b.n_vert, n, tbox, cen, acc, b.err_flag);
+    k_morton<<<g, kThreads, 0, st>>>(cen, n, acc, k0, v0, b.bbox_out);
+    unsigned long long *ki = k0, *ko = k1;
+    unsigned *vi = v0, *vo = v1;
+    for (int pass = 0; pass < 8; ++pass) {
+        k_rs_hist<<<nb, kRsThreads, 0, st>>>(ki, n, 8 * pass, hist, nb);
+        cudaError_t e = scan_exclusive_u32(hist, hist, 256 * (long long)nb, false, nullptr, sscr, st);
+        if (e != cudaSuccess) return e;
+        k_rs_scatter<<<nb, kRsThreads, 0, st>>>(ki, vi, ko, vo, n, 8 * pass, hist, nb);
+        unsigned long long* tk = ki; ki = ko; ko = tk;
+        unsigned* tv = vi; vi = vo; vo = tv;
+    }
+    // after an even number of passes the sorted data is back in (k0, v0)
+    if (n > 1) {
+        k_karras<<<(n - 1 + kThreads - 1) / kThreads, kThreads, 0, st>>>(ki, n, left, right, first, last, par_int,
+                                                                         par_leaf);
+        cudaMemsetAsync(flags, 0, sizeof(int) * (size_t)n, st);
+    }
+    k_refit<<<g, kThreads, 0, st>>>(vi, tbox, n, left, right, par_int, par_leaf, flags, lbox, nbox, ncnt, ncost, ncol,
+                                    b.leaf_max, b.c_t, b.c_i);
+    int ge = n > 1 ? (n - 1 + kThreads - 1) / kThreads : 1;
+    k_emit<<<ge, kThreads, 0, st>>>(n, left, right, first, lbox, nbox, ncnt, ncol, b.nodes);
+    k_reorder<<<g, kThreads, 0, st>>>(b.xyz, b.tri, b.n_vert, vi, n, b.tris);
+    return cudaGetLastError();
+}
+
+}  // namespace sbr

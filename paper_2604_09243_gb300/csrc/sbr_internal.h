@@ -1,0 +1,148 @@
+// sbr_internal.h -- device data layouts and launcher declarations shared by the
+// translation units of libsbr (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sbr {
+
+// ---------------------------------------------------------------- BVH layout
+// A BVH node stores the boxes of both children, so one 64-byte fetch gives the
+// traversal everything it needs to test and order the two children:
+//   n0 = (L.lo.x, L.hi.x, L.lo.y, L.hi.y)
+//   n1 = (R.lo.x, R.hi.x, R.lo.y, R.hi.y)
+//   n2 = (L.lo.z, L.hi.z, R.lo.z, R.hi.z)
+//   n3 = (ref L, ref R, 0, 0)   (int bits)
+// ref >= 0 is an internal node index; ref < 0 is a leaf whose triangles are the
+// contiguous range [first, first + count) of the reordered triangle array:
+//   ref = 0x80000000 | first << 4 | (count - 1),  count in 1..16.
+// kEmptyRef marks a missing child (its box is empty: lo > hi).
+constexpr int kLeafMax = 16;
+constexpr int kEmptyRef = (int)0xFFFFFFFF;
+
+__host__ __device__ inline int leaf_ref(int first, int count)
+{
+    return (int)(0x80000000u | ((unsigned)first << 4) | (unsigned)(count - 1));
+}
+__host__ __device__ inline int leaf_first(int ref) { return (int)(((unsigned)ref & 0x7FFFFFFFu) >> 4); }
+__host__ __device__ inline int leaf_count(int ref) { return (int)((unsigned)ref & 15u) + 1; }
+
+// A triangle is 3 float4 (48 bytes): (v0, original index as int bits), (e1, 0),
+// (e2, 0) with e1 = v1 - v0, e2 = v2 - v0 rounded to FP32.
+
+// ---------------------------------------------------------------- per-aspect data
+struct AngleDev {            // 128 bytes
+    float p0[3], du[3], dv[3], dir[3];  // FP32 ray grid: o(i, j) = (p0 + i du) + j dv
+    float rhat[3], vhat[3], hhat[3];    // radar direction, V (theta_hat), H (phi_hat)
+    float dA, eps;                      // tube area ds^2, origin offset after a hit
+    int nu, nv;
+    long long ray_off;                  // first ray of this aspect in the chunk, multiple of 32
+    int pad[4];
+};
+static_assert(sizeof(AngleDev) == 128, "AngleDev layout");
+
+// live ray between bounces (96 bytes, three 32-byte sectors)
+struct __align__(16) RayState {
+    float ox, oy, oz, dx;
+    float dy, dz, evx, evy;
+    float evz, lacc_hi, lacc_lo, cos0;  // E of the V transmit case; path so far (two-float)
+    float c0, c1, c2, c3;               // candidate tube coefficients HH, VV, HV, VH at the last hit
+    float cs, lc_hi, lc_lo, pad;        // candidate scalar coefficient, candidate path L (two-float)
+    int angle, local, last, nb;         // aspect (chunk-local), ray id j*nu+i, last sorted triangle, bounces
+};
+static_assert(sizeof(RayState) == 96, "RayState layout");
+
+// dense valid-hit record consumed by the PO reduction (32 bytes)
+struct __align__(16) Record {
+    float c[5];         // HH, VV, HV, VH (vector form) and the scalar form coefficient
+    float l_hi, l_lo;   // path L as an unevaluated FP32 sum
+    int ray;            // ray id j*nu + i within its aspect
+};
+static_assert(sizeof(Record) == 32, "Record layout");
+
+// stats counters on the device (unsigned long long each)
+enum { kStatQueries = 0, kStatNodes = 1, kStatTris = 2, kStatOverflow = 3, kStatCount = 4 };
+
+// ---------------------------------------------------------------- launchers
+// All launchers enqueue on `st` and return the launch error (cudaSuccess if none).
+
+struct BvhBuild {
+    // inputs
+    const float* xyz;
+    const int* tri;
+    long long n_vert, n_tri;
+    int leaf_max;
+    float c_t, c_i;
+    // outputs (allocated by the caller: nodes [max(n_tri-1,1)*4] float4, tris [n_tri*3] float4)
+    float4* nodes;
+    float4* tris;
+    float* bbox_out;  // device float[6] scene box of the vertices
+    int* err_flag;    // device int: set to 1 if a triangle index is out of range
+    // scratch (caller-owned)
+    void* scratch;
+    size_t scratch_bytes;
+};
+size_t bvh_scratch_bytes(long long n_tri);
+cudaError_t bvh_build(const BvhBuild& b, cudaStream_t st);
+
+struct TraceArgs {
+    const float4* nodes;
+    const float4* tris;
+    const AngleDev* angles;
+    const long long* ray_off;     // [n_angles + 1] chunk-relative, multiples of 32
+    int n_angles;
+    int max_bounces;
+    int bounce;                   // index of this pass (0 = primary rays)
+    int flags;
+    int visit_limit;              // upper bound of node + leaf visits of one query (2 n_tri + 64)
+    long long total_rays;         // primary: padded ray count of the chunk
+    const RayState* q_in;
+    const unsigned* q_in_count;
+    RayState* q_out;
+    unsigned* q_out_count;
+    unsigned* mask;               // [total_rays / 32] valid bits of primary rays
+    const unsigned* tile_base;    // [total_rays / 32] exclusive prefix of popcount(mask)
+    Record* rec;                  // dense records of this chunk (already offset to the chunk)
+    unsigned long long* work;     // work counter (zeroed before each pass)
+    unsigned long long* stats;    // [kStatCount]
+    int* hit_tri;                 // optional [total_rays][max_bounces] (RECORD_HITS)
+    float* hit_t;                 // optional [total_rays][max_bounces]
+    int* hit_nb;                  // optional [total_rays]
+};
+int trace_blocks_per_sm();
+cudaError_t launch_trace(const TraceArgs& a, int n_blocks, bool count_visits, cudaStream_t st);
+cudaError_t launch_emit_all(const TraceArgs& a, int n_blocks, cudaStream_t st);
+
+// exclusive scan of in[i] (or popcount(in[i])) -> out[i]; total written to *total
+size_t scan_scratch_bytes(long long n);
+cudaError_t scan_exclusive_u32(const unsigned* in, unsigned* out, long long n, bool popc, unsigned* total,
+                               void* scratch, cudaStream_t st);
+cudaError_t scan_popc(const unsigned* mask, unsigned* tile_base, long long n, unsigned* total, void* scratch,
+                      cudaStream_t st);
+cudaError_t launch_angle_offsets(const long long* ray_off, const unsigned* tile_base, const unsigned* total,
+                                 int n_angles, unsigned* rec_off, cudaStream_t st);
+
+struct PoItem {
+    int angle;        // aspect index (global over the trace)
+    int count;        // records in this item
+    long long first;  // first record
+};
+struct PoArgs {
+    const Record* rec;
+    const PoItem* items;
+    int n_items;
+    const float4* freq;   // [n_freq] (kappa_hi, kappa_lo, k, 0), kappa = f / c0 cycles per metre
+    const double* kfreq;  // [n_freq] k in FP64 (FP64 phase mode)
+    int n_freq;
+    int pol_sel[4];       // selected polarisation indices (0 HH, 1 VV, 2 HV, 3 VH)
+    int n_pol;
+    int scalar;           // 1: paper scalar form
+    int phase_mode;       // 0 compensated, 1 FP32, 2 FP64
+    double* partial;      // [n_items][n_freq][n_pol][2]
+};
+cudaError_t launch_po(const PoArgs& a, cudaStream_t st);
+cudaError_t launch_po_final(const double* partial, const int* item_off, int n_angles, const double* kfreq,
+                            int n_freq, int n_pol, double* E, double* rcs, cudaStream_t st);
+
+}  // namespace sbr

@@ -1,0 +1,161 @@
+// sbr_po.cu -- physical-optics ray-tube sum over the dense valid-hit records
+// (Eq. po_sum of the paper; vector form from Eq. em5/em6).
+//
+// The records of one aspect are cut into items of up to kPoItem tubes. One
+// block owns an item: it loads the tubes once and, for every requested
+// frequency, evaluates e^{-j k L} per tube, multiplies by the tube coefficients
+// and reduces with warp shuffles and a shared-memory tree in FP32. The item
+// partial is stored in FP64; a second kernel adds the partials of an aspect in
+// item order in FP64, applies -j k / (4 pi) and sigma = 4 pi |E|^2 (Sec. 4).
+// The order of every addition is fixed, so results are bitwise reproducible
+// (the paper notes run-to-run scatter of its FP32 sums, Sec. 5.1).
+//
+// Phase: k L is formed in cycles, kappa = f / c0, with kappa and L both held
+// as unevaluated two-float sums; the integer part is dropped exactly and the
+// fraction goes to sincospi. This keeps the phase error at the FP32 rounding
+// of the fraction even for paths of thousands of wavelengths.
+#include <math.h>
+
+#include "sbr_internal.h"
+
+namespace sbr {
+
+namespace {
+
+constexpr int kPoThreads = 256;
+constexpr int kPoPer = 4;  // records per thread
+constexpr int kWarps = kPoThreads / 32;
+
+__device__ __forceinline__ void phase_cs(const PoArgs& a, float4 fq, double kd, float lh, float ll, float& c,
+                                         float& s)
+{
+    if (a.phase_mode == 0) {
+        const float p = __fmul_rn(fq.x, lh);
+        float e = __fmaf_rn(fq.x, lh, -p);
+        e = __fadd_rn(e, __fadd_rn(__fmul_rn(fq.x, ll), __fmul_rn(fq.y, lh)));
+        const float n = rintf(p);
+        const float r = __fadd_rn(__fsub_rn(p, n), e);
+        sincospif(2.f * r, &s, &c);
+    } else if (a.phase_mode == 1) {
+        sincosf(fq.z * lh, &s, &c);
+    } else {
+        double sd, cd;
+        sincos(kd * ((double)lh + (double)ll), &sd, &cd);
+        s = (float)sd;
+        c = (float)cd;
+    }
+}
+
+__global__ void __launch_bounds__(kPoThreads) k_po(const PoArgs a)
+{
+    __shared__ float s_red[kWarps][8];
+    const PoItem I = a.items[blockIdx.x];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    float cf[kPoPer][4];
+    float lh[kPoPer], ll[kPoPer];
+#pragma unroll
+    for (int k = 0; k < kPoPer; ++k) {
+        const int idx = k * kPoThreads + tid;
+        if (idx < I.count) {
+            const float4* p = reinterpret_cast<const float4*>(a.rec + I.first + idx);
+            const float4 x = __ldg(p), y = __ldg(p + 1);
+            const float cv[5] = {x.x, x.y, x.z, x.w, y.x};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int sel = a.pol_sel[q];
+                float v = 0.f;
+                if (q < a.n_pol) v = a.scalar ? (sel < 2 ? cv[4] : 0.f) : cv[sel];
+                cf[k][q] = v;
+            }
+            lh[k] = y.y;
+            ll[k] = y.z;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) cf[k][q] = 0.f;
+            lh[k] = 0.f;
+            ll[k] = 0.f;
+        }
+    }
+    for (int f = 0; f < a.n_freq; ++f) {
+        const float4 fq = a.freq[f];
+        const double kd = a.kfreq[f];
+        float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < kPoPer; ++k) {
+            if (k * kPoThreads + tid >= I.count) break;
+            float c, s;
+            phase_cs(a, fq, kd, lh[k], ll[k], c, s);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                re[q] = fmaf(cf[k][q], c, re[q]);
+                im[q] = fmaf(-cf[k][q], s, im[q]);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                re[q] += __shfl_xor_sync(0xffffffffu, re[q], o);
+                im[q] += __shfl_xor_sync(0xffffffffu, im[q], o);
+            }
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                s_red[w][2 * q] = re[q];
+                s_red[w][2 * q + 1] = im[q];
+            }
+        __syncthreads();
+        if (tid < 2 * a.n_pol) {
+            float v = 0.f;
+#pragma unroll
+            for (int k = 0; k < kWarps; ++k) v += s_red[k][tid];
+            a.partial[((size_t)blockIdx.x * a.n_freq + f) * (2 * a.n_pol) + tid] = (double)v;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_po_final(const double* partial, const int* item_off, int n_angles, const double* kfreq, int n_freq,
+                           int n_pol, double* E, double* rcs)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long n = (long long)n_angles * n_freq * n_pol;
+    if (i >= n) return;
+    const int p = (int)(i % n_pol);
+    const int f = (int)((i / n_pol) % n_freq);
+    const int ang = (int)(i / ((long long)n_pol * n_freq));
+    double sr = 0.0, si = 0.0;
+    for (int it = item_off[ang]; it < item_off[ang + 1]; ++it) {
+        const double* q = partial + ((size_t)it * n_freq + f) * (2 * n_pol) + 2 * p;
+        sr += q[0];
+        si += q[1];
+    }
+    // E = (-j k / 4 pi) (sr + j si)
+    const double pre = kfreq[f] / (4.0 * 3.14159265358979323846);
+    const double er = pre * si, ei = -pre * sr;
+    if (E) {
+        E[2 * i] = er;
+        E[2 * i + 1] = ei;
+    }
+    if (rcs) rcs[i] = 10.0 * log10(4.0 * 3.14159265358979323846 * (er * er + ei * ei));
+}
+
+}  // namespace
+
+cudaError_t launch_po(const PoArgs& a, cudaStream_t st)
+{
+    if (a.n_items <= 0) return cudaSuccess;
+    k_po<<<a.n_items, kPoThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_po_final(const double* partial, const int* item_off, int n_angles, const double* kfreq,
+                            int n_freq, int n_pol, double* E, double* rcs, cudaStream_t st)
+{
+    long long n = (long long)n_angles * n_freq * n_pol;
+    if (n <= 0) return cudaSuccess;
+    k_po_final<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(partial, item_off, n_angles, kfreq, n_freq, n_pol, E, rcs);
+    return cudaGetLastError();
+}
+
+}  // namespace sbr

@@ -1,0 +1,493 @@
+// sbr_trace.cu -- multi-bounce ray transport (Algorithm 2 of the paper) as a
+// wavefront of persistent kernels:
+//   pass 0        primary rays generated from their index on the aperture grid
+//                 (Eq. L1-L3), closest hit, one 32-bit hit mask per 32 rays
+//   scan          exclusive popcount prefix of the masks = dense record slots
+//   pass b >= 1   the live rays of the previous pass, compacted into a queue,
+//                 take their next closest-hit query (skipping the triangle just
+//                 left); rays that miss or reach B_max write their record
+// Each hit applies the specular reflection d - 2 (d.n) n, the PEC field update
+// E' = 2 (n.E) n - E and the origin offset eps along the normal (Sec. 4), and
+// stores the ray-tube coefficients the PO sum needs if this hit is the last one.
+//
+// Warps fetch 32 rays at a time from a global counter, so the grid stays full
+// while rays finish at different depths; the traversal keeps a per-thread
+// stack of node references, visits the nearer child first and tests the
+// triangles of a leaf in FP32 Moller-Trumbore form.
+#include <float.h>
+#include <limits.h>
+
+#include "sbr_internal.h"
+
+namespace sbr {
+
+namespace {
+
+constexpr int kTraceThreads = 256;
+constexpr int kStack = 64;
+// Barycentric slack of the FP32 triangle test (2^-22): closes the FP32 cracks
+// along shared edges; it is well inside the 1e-6 edge band of the parity rule.
+constexpr float kSlack = 2.384185791015625e-07f;
+// conservative slab test: exit distance scaled by 1 + 2*gamma_3 (robust traversal)
+constexpr float kBoxGrow = 1.0000008f;
+constexpr unsigned kFull = 0xffffffffu;
+
+// trace flag bits (mirror of SBR_TRACE_* in sbr.h)
+constexpr int kFlagLiteral = 1;
+constexpr int kFlagEscape = 2;
+constexpr int kFlagHits = 4;
+
+struct Hit {
+    float t;
+    int k;
+    int orig;
+};
+
+__device__ __forceinline__ float safe_rcp(float x)
+{
+    const float tiny = 1e-20f;
+    return __frcp_rn(fabsf(x) > tiny ? x : copysignf(tiny, x));
+}
+
+// ---------------------------------------------------------------- two-float helpers
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void tf_add(float& hi, float& lo, float x)
+{
+    float s, e;
+    two_sum(hi, x, s, e);
+    e = __fadd_rn(e, lo);
+    hi = __fadd_rn(s, e);
+    lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+__device__ __forceinline__ void tf_add_tf(float& hi, float& lo, float xh, float xl)
+{
+    float s, e;
+    two_sum(hi, xh, s, e);
+    e = __fadd_rn(e, __fadd_rn(lo, xl));
+    hi = __fadd_rn(s, e);
+    lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+// a . b as an unevaluated two-float sum (exact products, compensated sum)
+__device__ __forceinline__ void tf_dot(const float* a, float3 b, float& hi, float& lo)
+{
+    float p0 = __fmul_rn(a[0], b.x), e0 = __fmaf_rn(a[0], b.x, -p0);
+    float p1 = __fmul_rn(a[1], b.y), e1 = __fmaf_rn(a[1], b.y, -p1);
+    float p2 = __fmul_rn(a[2], b.z), e2 = __fmaf_rn(a[2], b.z, -p2);
+    float s, e, s2, f;
+    two_sum(p0, p1, s, e);
+    two_sum(s, p2, s2, f);
+    float lo_ = __fadd_rn(__fadd_rn(e, f), __fadd_rn(__fadd_rn(e0, e1), e2));
+    hi = __fadd_rn(s2, lo_);
+    lo = __fsub_rn(lo_, __fsub_rn(hi, s2));
+}
+
+// ---------------------------------------------------------------- closest hit
+template <bool kCount>
+__device__ __forceinline__ void closest_hit(const float4* __restrict__ nodes, const float4* __restrict__ tris, float3 o,
+                                            float3 d, int skip, int limit, Hit& h, unsigned& nvis, unsigned& ntri,
+                                            bool& overflow)
+{
+    int stack[kStack];
+    const float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+    const float3 oi = make_float3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
+    h.t = FLT_MAX;
+    h.k = -1;
+    h.orig = INT_MAX;
+    int sp = 0;
+    int ref = 0;
+    // a query visits every node and leaf at most once; the bound guards against
+    // a malformed hierarchy (reported like a stack overflow)
+    for (int it = 0;; ++it) {
+        if (it >= limit) {
+            overflow = true;
+            break;
+        }
+        if (ref >= 0) {
+            const float4* nd = nodes + 4 * (size_t)ref;
+            const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
+            if (kCount) ++nvis;
+            const float tmax = h.t;
+            float ax0 = fmaf(n0.x, inv.x, -oi.x), ax1 = fmaf(n0.y, inv.x, -oi.x);
+            float ay0 = fmaf(n0.z, inv.y, -oi.y), ay1 = fmaf(n0.w, inv.y, -oi.y);
+            float az0 = fmaf(n2.x, inv.z, -oi.z), az1 = fmaf(n2.y, inv.z, -oi.z);
+            float bx0 = fmaf(n1.x, inv.x, -oi.x), bx1 = fmaf(n1.y, inv.x, -oi.x);
+            float by0 = fmaf(n1.z, inv.y, -oi.y), by1 = fmaf(n1.w, inv.y, -oi.y);
+            float bz0 = fmaf(n2.z, inv.z, -oi.z), bz1 = fmaf(n2.w, inv.z, -oi.z);
+            float an = fmaxf(fmaxf(fminf(ax0, ax1), fminf(ay0, ay1)), fmaxf(fminf(az0, az1), 0.f));
+            float af = fminf(fminf(fmaxf(ax0, ax1), fmaxf(ay0, ay1)), fminf(fmaxf(az0, az1), tmax));
+            float bn = fmaxf(fmaxf(fminf(bx0, bx1), fminf(by0, by1)), fmaxf(fminf(bz0, bz1), 0.f));
+            float bf = fminf(fminf(fmaxf(bx0, bx1), fmaxf(by0, by1)), fminf(fmaxf(bz0, bz1), tmax));
+            const int lref = __float_as_int(n3.x), rref = __float_as_int(n3.y);
+            const bool hl = an <= af * kBoxGrow;
+            const bool hr = (bn <= bf * kBoxGrow) && (rref != kEmptyRef);
+            if (hl && hr) {
+                const bool lnear = an <= bn;
+                if (sp < kStack) stack[sp++] = lnear ? rref : lref;
+                else overflow = true;
+                ref = lnear ? lref : rref;
+                continue;
+            }
+            if (hl) { ref = lref; continue; }
+            if (hr) { ref = rref; continue; }
+        } else {
+            const int first = leaf_first(ref), cnt = leaf_count(ref);
+            for (int q = 0; q < cnt; ++q) {
+                const int k = first + q;
+                if (kCount) ++ntri;
+                if (k == skip) continue;
+                const float4* tp = tris + 3 * (size_t)k;
+                const float4 A = __ldg(tp), B = __ldg(tp + 1), C = __ldg(tp + 2);
+                // Moller-Trumbore, division-free until a candidate is inside
+                const float px = d.y * C.z - d.z * C.y, py = d.z * C.x - d.x * C.z, pz = d.x * C.y - d.y * C.x;
+                const float det = B.x * px + B.y * py + B.z * pz;
+                const float sx = o.x - A.x, sy = o.y - A.y, sz = o.z - A.z;
+                const float qx = sy * B.z - sz * B.y, qy = sz * B.x - sx * B.z, qz = sx * B.y - sy * B.x;
+                const float sg = det < 0.f ? -1.f : 1.f;
+                const float U = sg * (sx * px + sy * py + sz * pz);
+                const float V = sg * (d.x * qx + d.y * qy + d.z * qz);
+                const float T = C.x * qx + C.y * qy + C.z * qz;
+                const float ad = fabsf(det);
+                const float tol = kSlack * ad;
+                if (ad > 0.f && U >= -tol && V >= -tol && U + V <= ad + tol && sg * T > 0.f) {
+                    const float t = __fdiv_rn(T, det);
+                    const int orig = __float_as_int(A.w);
+                    if (t < h.t || (t == h.t && orig < h.orig)) {
+                        h.t = t;
+                        h.k = k;
+                        h.orig = orig;
+                    }
+                }
+            }
+        }
+        if (sp == 0) break;
+        ref = stack[--sp];
+    }
+}
+
+// ---------------------------------------------------------------- per-ray state in registers
+struct Ray {
+    float3 o, d, ev;
+    float lacc_hi, lacc_lo, cos0;
+    float c[5];
+    float lc_hi, lc_lo;
+    int angle, local, last, nb;
+};
+
+__device__ __forceinline__ void load_state(const RayState* __restrict__ q, unsigned i, Ray& r)
+{
+    const float4* p = reinterpret_cast<const float4*>(q + i);
+    float4 a = p[0], b = p[1], c = p[2], e = p[3], f = p[4];
+    int4 g = reinterpret_cast<const int4*>(p)[5];
+    r.o = make_float3(a.x, a.y, a.z);
+    r.d = make_float3(a.w, b.x, b.y);
+    r.ev = make_float3(b.z, b.w, c.x);
+    r.lacc_hi = c.y;
+    r.lacc_lo = c.z;
+    r.cos0 = c.w;
+    r.c[0] = e.x; r.c[1] = e.y; r.c[2] = e.z; r.c[3] = e.w;
+    r.c[4] = f.x;
+    r.lc_hi = f.y;
+    r.lc_lo = f.z;
+    r.angle = g.x; r.local = g.y; r.last = g.z; r.nb = g.w;
+}
+
+__device__ __forceinline__ void store_state(RayState* __restrict__ q, unsigned i, const Ray& r)
+{
+    float4* p = reinterpret_cast<float4*>(q + i);
+    p[0] = make_float4(r.o.x, r.o.y, r.o.z, r.d.x);
+    p[1] = make_float4(r.d.y, r.d.z, r.ev.x, r.ev.y);
+    p[2] = make_float4(r.ev.z, r.lacc_hi, r.lacc_lo, r.cos0);
+    p[3] = make_float4(r.c[0], r.c[1], r.c[2], r.c[3]);
+    p[4] = make_float4(r.c[4], r.lc_hi, r.lc_lo, 0.f);
+    reinterpret_cast<int4*>(p)[5] = make_int4(r.angle, r.local, r.last, r.nb);
+}
+
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float dot3(const float* a, float3 b) { return a[0] * b.x + a[1] * b.y + a[2] * b.z; }
+
+// Update the ray at its closest hit: path, bounce count, candidate PO
+// coefficients of this hit (used if it turns out to be the last), reflection,
+// PEC field update and the new origin.
+__device__ __forceinline__ void apply_hit(const AngleDev& A, const float4* __restrict__ tris, const Hit& h, int flags,
+                                          Ray& r)
+{
+    const float3 x = make_float3(fmaf(h.t, r.d.x, r.o.x), fmaf(h.t, r.d.y, r.o.y), fmaf(h.t, r.d.z, r.o.z));
+    tf_add(r.lacc_hi, r.lacc_lo, h.t);
+    const int nb_before = r.nb;
+    r.nb = nb_before + 1;
+    const float4 B = __ldg(tris + 3 * (size_t)h.k + 1), C = __ldg(tris + 3 * (size_t)h.k + 2);
+    float3 n = make_float3(B.y * C.z - B.z * C.y, B.z * C.x - B.x * C.z, B.x * C.y - B.y * C.x);
+    const float il = rsqrtf(fmaxf(dot3(n, n), 1e-37f));
+    n = make_float3(n.x * il, n.y * il, n.z * il);
+    const float dn = dot3(r.d, n);
+    const float3 nf = dn < 0.f ? n : make_float3(-n.x, -n.y, -n.z);
+    const float adn = fabsf(dn);
+    const float3 rh = make_float3(A.rhat[0], A.rhat[1], A.rhat[2]);
+    if (r.nb == 1) r.cos0 = dot3(nf, rh);
+    // candidate path L = k.o0 + sum t + k.x
+    float kh, kl;
+    tf_dot(A.dir, x, kh, kl);
+    r.lc_hi = r.lacc_hi;
+    r.lc_lo = r.lacc_lo;
+    tf_add_tf(r.lc_hi, r.lc_lo, kh, kl);
+    // H-transmit field from the V one: E_H = s (d x E_V), s = +1 after an odd number of reflections
+    const float sH = (nb_before & 1) ? 1.f : -1.f;
+    const float3 eh = make_float3(sH * (r.d.y * r.ev.z - r.d.z * r.ev.y), sH * (r.d.z * r.ev.x - r.d.x * r.ev.z),
+                                  sH * (r.d.x * r.ev.y - r.d.y * r.ev.x));
+    const float dS = adn > 0.f ? __fdiv_rn(A.dA, adn) : 0.f;
+    const float nfd = dot3(nf, r.d);
+    const float3 vh = make_float3(A.vhat[0], A.vhat[1], A.vhat[2]);
+    const float3 hh = make_float3(A.hhat[0], A.hhat[1], A.hhat[2]);
+    float3 W[2];
+    const float3 Eq[2] = {eh, r.ev};
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const float ne = dot3(nf, Eq[q]);
+        // J = 2 nf x (d x E) = 2 (d (nf.E) - E (nf.d))
+        const float3 J = make_float3(2.f * (r.d.x * ne - Eq[q].x * nfd), 2.f * (r.d.y * ne - Eq[q].y * nfd),
+                                     2.f * (r.d.z * ne - Eq[q].z * nfd));
+        const float jr = dot3(J, rh);
+        W[q] = make_float3(dS * (J.x - jr * rh.x), dS * (J.y - jr * rh.y), dS * (J.z - jr * rh.z));
+    }
+    r.c[0] = dot3(W[0], hh);  // HH
+    r.c[1] = dot3(W[1], vh);  // VV
+    r.c[2] = dot3(W[1], hh);  // HV
+    r.c[3] = dot3(W[0], vh);  // VH
+    const float gam = (r.nb & 1) ? -1.f : 1.f;  // Gamma^N, Gamma = -1
+    r.c[4] = -2.f * A.dA * r.cos0 * gam;
+    if (flags & kFlagLiteral) {
+        // scalar form with e^{-j 2 k R}: L = 2 (k.o0 + R), stored in the candidate path
+        r.lc_hi = 2.f * r.lacc_hi;
+        r.lc_lo = 2.f * r.lacc_lo;
+    }
+    // specular reflection and PEC field update
+    const float nev = dot3(n, r.ev);
+    r.d = make_float3(fmaf(-2.f * dn, n.x, r.d.x), fmaf(-2.f * dn, n.y, r.d.y), fmaf(-2.f * dn, n.z, r.d.z));
+    r.ev = make_float3(fmaf(2.f * nev, n.x, -r.ev.x), fmaf(2.f * nev, n.y, -r.ev.y), fmaf(2.f * nev, n.z, -r.ev.z));
+    r.o = make_float3(fmaf(A.eps, nf.x, x.x), fmaf(A.eps, nf.y, x.y), fmaf(A.eps, nf.z, x.z));
+    r.last = h.k;
+}
+
+__device__ __forceinline__ long long ray_global(const TraceArgs& a, const Ray& r)
+{
+    return a.ray_off[r.angle] + r.local;
+}
+
+__device__ __forceinline__ void emit(const TraceArgs& a, const Ray& r, bool zero)
+{
+    const long long g = ray_global(a, r);
+    const long long tile = g >> 5;
+    const unsigned bit = (unsigned)(g & 31);
+    const unsigned slot = a.tile_base[tile] + __popc(a.mask[tile] & ((1u << bit) - 1u));
+    float4* p = reinterpret_cast<float4*>(a.rec + slot);
+    if (zero) {
+        p[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+        p[1] = make_float4(0.f, 0.f, 0.f, __int_as_float(r.local));
+    } else {
+        p[0] = make_float4(r.c[0], r.c[1], r.c[2], r.c[3]);
+        p[1] = make_float4(r.c[4], r.lc_hi, r.lc_lo, __int_as_float(r.local));
+    }
+    if (a.hit_nb) a.hit_nb[g] = r.nb;
+}
+
+__device__ __forceinline__ void record_hit(const TraceArgs& a, const Ray& r, const Hit& h)
+{
+    if (!a.hit_tri) return;
+    const long long g = ray_global(a, r);
+    a.hit_tri[g * a.max_bounces + (r.nb - 1)] = h.orig;
+    a.hit_t[g * a.max_bounces + (r.nb - 1)] = h.t;
+}
+
+__device__ __forceinline__ int find_angle(const long long* __restrict__ off, int n, long long g)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// warp-aggregated append to the live-ray queue; every lane of the warp must call it
+__device__ __forceinline__ void push(const TraceArgs& a, bool want, const Ray& r)
+{
+    const unsigned m = __ballot_sync(kFull, want);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(a.q_out_count, (unsigned)__popc(m));
+    base = __shfl_sync(kFull, base, leader);
+    if (want) store_state(a.q_out, base + __popc(m & ((1u << lane) - 1u)), r);
+}
+
+template <bool kCount>
+__device__ __forceinline__ void flush_stats(const TraceArgs& a, unsigned q, unsigned nvis, unsigned ntri, bool ovf)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        q += __shfl_xor_sync(kFull, q, o);
+        if (kCount) {
+            nvis += __shfl_xor_sync(kFull, nvis, o);
+            ntri += __shfl_xor_sync(kFull, ntri, o);
+        }
+    }
+    const unsigned ov = __ballot_sync(kFull, ovf);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(a.stats + kStatQueries, (unsigned long long)q);
+        if (kCount) {
+            atomicAdd(a.stats + kStatNodes, (unsigned long long)nvis);
+            atomicAdd(a.stats + kStatTris, (unsigned long long)ntri);
+        }
+        if (ov) atomicAdd(a.stats + kStatOverflow, (unsigned long long)__popc(ov));
+    }
+}
+
+// ---------------------------------------------------------------- pass 0: primary rays
+template <bool kCount>
+__global__ void __launch_bounds__(kTraceThreads) k_primary(const TraceArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    unsigned nq = 0, nvis = 0, ntri = 0;
+    bool ovf = false;
+    while (true) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(a.work, 32ull);
+        base = __shfl_sync(kFull, base, 0);
+        if ((long long)base >= a.total_rays) break;
+        int ang = 0;
+        if (lane == 0) ang = find_angle(a.ray_off, a.n_angles, (long long)base);
+        ang = __shfl_sync(kFull, ang, 0);
+        const AngleDev& A = a.angles[ang];
+        const long long local = (long long)base + lane - a.ray_off[ang];
+        const bool active = local < (long long)A.nu * A.nv;
+        bool hit = false;
+        Ray r;
+        r.angle = ang;
+        r.local = (int)local;
+        if (active) {
+            const int i = (int)(local % A.nu), j = (int)(local / A.nu);
+            const float fi = (float)i, fj = (float)j;
+            r.o = make_float3(__fadd_rn(__fadd_rn(A.p0[0], __fmul_rn(fi, A.du[0])), __fmul_rn(fj, A.dv[0])),
+                              __fadd_rn(__fadd_rn(A.p0[1], __fmul_rn(fi, A.du[1])), __fmul_rn(fj, A.dv[1])),
+                              __fadd_rn(__fadd_rn(A.p0[2], __fmul_rn(fi, A.du[2])), __fmul_rn(fj, A.dv[2])));
+            r.d = make_float3(A.dir[0], A.dir[1], A.dir[2]);
+            r.ev = make_float3(A.vhat[0], A.vhat[1], A.vhat[2]);
+            tf_dot(A.dir, r.o, r.lacc_hi, r.lacc_lo);
+            r.cos0 = 0.f;
+            r.nb = 0;
+            r.last = -1;
+            Hit h;
+            closest_hit<kCount>(a.nodes, a.tris, r.o, r.d, -1, a.visit_limit, h, nvis, ntri, ovf);
+            ++nq;
+            if (h.k >= 0) {
+                hit = true;
+                apply_hit(A, a.tris, h, a.flags, r);
+                record_hit(a, r, h);
+            }
+        }
+        const unsigned m = __ballot_sync(kFull, hit);
+        if (lane == 0) a.mask[base >> 5] = m;
+        push(a, hit, r);
+    }
+    flush_stats<kCount>(a, nq, nvis, ntri, ovf);
+}
+
+// ---------------------------------------------------------------- pass b >= 1: live rays
+template <bool kCount>
+__global__ void __launch_bounds__(kTraceThreads) k_bounce(const TraceArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned n_in = *a.q_in_count;
+    const bool escape_pass = a.bounce >= a.max_bounces;
+    unsigned nq = 0, nvis = 0, ntri = 0;
+    bool ovf = false;
+    while (true) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(a.work, 32ull);
+        base = __shfl_sync(kFull, base, 0);
+        if (base >= n_in) break;
+        const unsigned idx = (unsigned)base + lane;
+        bool again = false;
+        Ray r;
+        if (idx < n_in) {
+            load_state(a.q_in, idx, r);
+            const AngleDev& A = a.angles[r.angle];
+            Hit h;
+            closest_hit<kCount>(a.nodes, a.tris, r.o, r.d, r.last, a.visit_limit, h, nvis, ntri, ovf);
+            ++nq;
+            if (h.k < 0) {
+                emit(a, r, false);                     // escaped: its last hit radiates
+            } else if (escape_pass) {
+                emit(a, r, true);                      // still trapped after B_max: invalid
+            } else {
+                apply_hit(A, a.tris, h, a.flags, r);
+                record_hit(a, r, h);
+                if (r.nb < a.max_bounces || (a.flags & kFlagEscape)) again = true;
+                else emit(a, r, false);
+            }
+        }
+        push(a, again, r);
+    }
+    flush_stats<kCount>(a, nq, nvis, ntri, ovf);
+}
+
+// every ray of the queue writes its record (B_max = 1 without the escape check)
+__global__ void __launch_bounds__(kTraceThreads) k_emit_all(const TraceArgs a)
+{
+    const unsigned n_in = *a.q_in_count;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n_in; i += gridDim.x * blockDim.x) {
+        Ray r;
+        load_state(a.q_in, i, r);
+        emit(a, r, false);
+    }
+}
+
+__global__ void k_angle_offsets(const long long* ray_off, const unsigned* tile_base, const unsigned* total,
+                                int n_angles, unsigned* rec_off)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_angles) rec_off[i] = tile_base[ray_off[i] >> 5];
+    if (i == n_angles) rec_off[i] = *total;
+}
+
+}  // namespace
+
+int trace_blocks_per_sm()
+{
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bounce<false>, kTraceThreads, 0);
+    return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_trace(const TraceArgs& a, int n_blocks, bool count_visits, cudaStream_t st)
+{
+    if (a.bounce == 0) {
+        if (count_visits) k_primary<true><<<n_blocks, kTraceThreads, 0, st>>>(a);
+        else k_primary<false><<<n_blocks, kTraceThreads, 0, st>>>(a);
+    } else {
+        if (count_visits) k_bounce<true><<<n_blocks, kTraceThreads, 0, st>>>(a);
+        else k_bounce<false><<<n_blocks, kTraceThreads, 0, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emit_all(const TraceArgs& a, int n_blocks, cudaStream_t st)
+{
+    k_emit_all<<<n_blocks, kTraceThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_angle_offsets(const long long* ray_off, const unsigned* tile_base, const unsigned* total,
+                                 int n_angles, unsigned* rec_off, cudaStream_t st)
+{
+    k_angle_offsets<<<(n_angles + 1 + 255) / 256, 256, 0, st>>>(ray_off, tile_base, total, n_angles, rec_off);
+    return cudaGetLastError();
+}
+
+}  // namespace sbr

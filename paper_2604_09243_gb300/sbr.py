@@ -1,0 +1,290 @@
+"""Thin ctypes binding of libsbr (include/sbr.h): argument marshalling only.
+
+Every step of the trace-integrate path runs in the CUDA library. If
+``lib/libsbr.so`` is missing or cannot be loaded, every entry point raises;
+there is no CPU fallback. PyTorch is optional: device tensors (``torch.Tensor``
+on CUDA) are accepted wherever the C ABI takes a device pointer, and a torch
+stream may be passed as the context's stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libsbr.so")
+
+SBR_OK = 0
+ERRORS = {-1: "SBR_ERR_ARG", -2: "SBR_ERR_CUDA", -3: "SBR_ERR_OOM", -4: "SBR_ERR_STATE",
+          -5: "SBR_ERR_STACK_OVERFLOW", -6: "SBR_ERR_TIMEOUT", -7: "SBR_ERR_NODEV"}
+POL_BITS = {"HH": 1, "VV": 2, "HV": 4, "VH": 8}
+POL_ORDER = ("HH", "VV", "HV", "VH")
+PO_VECTOR, PO_PAPER_SCALAR = 0, 1
+PHASE = {"compensated": 0, "fp32": 16, "fp64": 32}
+TRACE_PHASE_LITERAL_2R, TRACE_REQUIRE_ESCAPE, TRACE_RECORD_HITS, TRACE_COUNT_VISITS, TRACE_TIME_PASSES = 1, 2, 4, 8, 16
+
+# every symbol declared in include/sbr.h
+EXPORTS = ("sbr_version", "sbr_create", "sbr_destroy", "sbr_last_error", "sbr_load_mesh", "sbr_get_bbox",
+           "sbr_build_bvh", "sbr_ray_grid_for", "sbr_ray_grid_box", "sbr_trace", "sbr_po_integrate", "sbr_get_hits",
+           "sbr_get_records", "sbr_spacing_for")
+
+
+class SbrError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class BvhOpts(C.Structure):
+    _fields_ = [("leaf_max", C.c_int), ("cost_traverse", C.c_float), ("cost_intersect", C.c_float)]
+
+
+class TraceOpts(C.Structure):
+    _fields_ = [("window_m", C.c_double), ("offset_u", C.c_double), ("offset_v", C.c_double),
+                ("flags", C.c_int), ("chunk_rays", C.c_int)]
+
+
+class TraceStats(C.Structure):
+    _fields_ = [("n_angles", C.c_int64), ("rays_launched", C.c_int64), ("ray_bounces", C.c_int64),
+                ("valid_rays", C.c_int64), ("node_visits", C.c_int64), ("tri_tests", C.c_int64),
+                ("stack_overflows", C.c_int64), ("kernel_launches", C.c_int64), ("pass_launches", C.c_int64),
+                ("pass_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: (float if k == "pass_ms" else int)(getattr(self, k)) for k, _ in self._fields_}
+
+
+class RayGrid(C.Structure):
+    _fields_ = [("nu", C.c_int64), ("nv", C.c_int64), ("lu", C.c_double), ("lv", C.c_double),
+                ("spacing", C.c_double), ("eps", C.c_double),
+                ("rhat", C.c_double * 3), ("khat", C.c_double * 3), ("vhat", C.c_double * 3),
+                ("hhat", C.c_double * 3),
+                ("p0", C.c_float * 3), ("du", C.c_float * 3), ("dv", C.c_float * 3), ("dir", C.c_float * 3)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libsbr.so (built in-tree by ``paper_2604_09243_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libsbr.so not found at {LIB_PATH}: run paper_2604_09243_gb300.build.build() "
+                           "(there is no CPU fallback)")
+    L = C.CDLL(LIB_PATH)
+    P, vp, i64, d = C.POINTER, C.c_void_p, C.c_int64, C.c_double
+    sig = {
+        "sbr_version": ([], C.c_int),
+        "sbr_create": ([P(vp), C.c_int, vp], C.c_int),
+        "sbr_destroy": ([vp], None),
+        "sbr_last_error": ([vp], C.c_char_p),
+        "sbr_load_mesh": ([vp, vp, i64, vp, i64, C.c_int], C.c_int),
+        "sbr_get_bbox": ([vp, P(C.c_float)], C.c_int),
+        "sbr_build_bvh": ([vp, P(BvhOpts)], C.c_int),
+        "sbr_ray_grid_for": ([vp, d, d, d, d, P(TraceOpts), P(RayGrid)], C.c_int),
+        "sbr_ray_grid_box": ([P(C.c_float), d, d, d, d, P(TraceOpts), P(RayGrid)], C.c_int),
+        "sbr_trace": ([vp, P(d), i64, d, d, C.c_int, P(TraceOpts), P(TraceStats)], C.c_int),
+        "sbr_po_integrate": ([vp, P(d), i64, C.c_int, C.c_int, vp, vp, C.c_int], C.c_int),
+        "sbr_get_hits": ([vp, i64, vp, vp, vp], C.c_int),
+        "sbr_get_records": ([vp, i64, i64, vp, vp, vp, P(i64)], C.c_int),
+        "sbr_spacing_for": ([d, d], d),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def version() -> int:
+    return int(lib().sbr_version())
+
+
+def spacing_for(f_max_hz: float, rays_per_lambda: float) -> float:
+    """Ray spacing ds = c0 / (f * rays_per_lambda) (Sec. 4 sampling rule asks ds <= lambda / 5)."""
+    v = lib().sbr_spacing_for(float(f_max_hz), float(rays_per_lambda))
+    if v < 0:
+        raise ValueError("frequency and rays per wavelength must be > 0")
+    return v
+
+
+def _opts(window=0.0, offset=(0.0, 0.0), flags=0, chunk_rays=0) -> TraceOpts:
+    return TraceOpts(float(window), float(offset[0]), float(offset[1]), int(flags), int(chunk_rays))
+
+
+def _grid_dict(g: RayGrid) -> dict:
+    out = {k: getattr(g, k) for k, _ in RayGrid._fields_}
+    for k in ("rhat", "khat", "vhat", "hhat"):
+        out[k] = np.array(out[k], np.float64)
+    for k in ("p0", "du", "dv", "dir"):
+        out[k] = np.array(out[k], np.float32)
+    out["nu"], out["nv"] = int(g.nu), int(g.nv)
+    return out
+
+
+def ray_grid(bbox, az_deg, el_deg, spacing, eta=0.05, window=0.0, offset=(0.0, 0.0)) -> dict:
+    """Aperture grid of one aspect for a scene box (Eq. L1-L3); host only, no GPU."""
+    b = np.ascontiguousarray(bbox, dtype=np.float32)
+    g = RayGrid()
+    o = _opts(window, offset)
+    rc = lib().sbr_ray_grid_box(b.ctypes.data_as(C.POINTER(C.c_float)), float(az_deg), float(el_deg), float(spacing),
+                            float(eta), C.byref(o), C.byref(g))
+    if rc != SBR_OK:
+        raise SbrError(rc, "sbr_ray_grid_box: bad arguments")
+    return _grid_dict(g)
+
+
+def _is_torch_cuda(x) -> bool:
+    return hasattr(x, "data_ptr") and getattr(x, "is_cuda", False)
+
+
+def _pols(pols) -> int:
+    if isinstance(pols, int):
+        return pols
+    if isinstance(pols, str):
+        pols = [p.strip() for p in pols.split(",") if p.strip()]
+    m = 0
+    for p in pols:
+        m |= POL_BITS[p.upper()]
+    return m
+
+
+class Context:
+    """One libsbr context on one CUDA device; methods mirror the sbr_* calls."""
+
+    def __init__(self, device: int = 0, stream=None):
+        L = lib()
+        h = C.c_void_p()
+        s = None
+        if stream is not None:
+            s = int(getattr(stream, "cuda_stream", stream))
+        rc = L.sbr_create(C.byref(h), int(device), C.c_void_p(s) if s else None)
+        if rc != SBR_OK:
+            raise SbrError(rc, (L.sbr_last_error(None) or b"").decode())
+        self._h = h
+        self.device = device
+        self._stream_ref = stream  # keep a passed stream alive
+        self.n_tri = 0
+        self.max_bounces = 0
+        self.grids: list[dict] = []
+
+    # ------------------------------------------------------------------ plumbing
+    def _check(self, rc: int):
+        if rc != SBR_OK:
+            raise SbrError(rc, (lib().sbr_last_error(self._h) or b"").decode())
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().sbr_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ------------------------------------------------------------------ calls
+    def load_mesh(self, xyz, tri):
+        """Copy a mesh (numpy host arrays or CUDA torch tensors: float32 [nv,3], int32 [nt,3])."""
+        if _is_torch_cuda(xyz) or _is_torch_cuda(tri):
+            if not (_is_torch_cuda(xyz) and _is_torch_cuda(tri)):
+                raise ValueError("xyz and tri must both be host arrays or both CUDA tensors")
+            xyz_c, tri_c = xyz.contiguous(), tri.contiguous()
+            self._check(lib().sbr_load_mesh(self._h, xyz_c.data_ptr(), xyz_c.shape[0], tri_c.data_ptr(),
+                                            tri_c.shape[0], 1))
+            self.n_tri = int(tri_c.shape[0])
+            return
+        xyz = np.ascontiguousarray(xyz, dtype=np.float32)
+        tri = np.ascontiguousarray(tri, dtype=np.int32)
+        if xyz.ndim != 2 or xyz.shape[1] != 3 or tri.ndim != 2 or tri.shape[1] != 3:
+            raise ValueError("xyz must be [nv, 3] and tri [nt, 3]")
+        self._check(lib().sbr_load_mesh(self._h, xyz.ctypes.data, len(xyz), tri.ctypes.data, len(tri), 0))
+        self.n_tri = len(tri)
+
+    def build_bvh(self, leaf_max: int = 4, cost_traverse: float = 1.0, cost_intersect: float = 1.0):
+        o = BvhOpts(int(leaf_max), float(cost_traverse), float(cost_intersect))
+        self._check(lib().sbr_build_bvh(self._h, C.byref(o)))
+
+    def get_bbox(self) -> np.ndarray:
+        b = np.zeros(6, np.float32)
+        self._check(lib().sbr_get_bbox(self._h, b.ctypes.data_as(C.POINTER(C.c_float))))
+        return b
+
+    def ray_grid_for(self, az_deg, el_deg, spacing, eta=0.05, window=0.0, offset=(0.0, 0.0)) -> dict:
+        g = RayGrid()
+        o = _opts(window, offset)
+        self._check(lib().sbr_ray_grid_for(self._h, float(az_deg), float(el_deg), float(spacing), float(eta),
+                                           C.byref(o), C.byref(g)))
+        return _grid_dict(g)
+
+    def trace(self, angles, spacing, eta=0.05, max_bounces=1, window=0.0, offset=(0.0, 0.0), flags=0,
+              stats=True, chunk_rays=0) -> dict | None:
+        """Trace aspects ``angles`` ([n, 2] az, el degrees); returns the trace stats."""
+        a = np.ascontiguousarray(np.atleast_2d(angles), dtype=np.float64)
+        if a.shape[1] != 2:
+            raise ValueError("angles must be [n, 2] (az, el)")
+        o = _opts(window, offset, flags, chunk_rays)
+        st = TraceStats()
+        self._check(lib().sbr_trace(self._h, a.ctypes.data_as(C.POINTER(C.c_double)), len(a), float(spacing),
+                                    float(eta), int(max_bounces), C.byref(o), C.byref(st) if stats else None))
+        self.max_bounces = int(max_bounces)
+        self.n_angles = len(a)
+        self._last_angles = a.copy()
+        self._trace_args = (spacing, eta, window, offset)
+        return st.as_dict() if stats else None
+
+    def po_integrate(self, freqs, pols="HH,VV", mode="vector", phase="compensated", E_out=None, rcs_out=None):
+        """PO sum of the last trace. Returns (E complex128 [n_angles, n_freq, n_pol], rcs_dbsm [...]) as
+        numpy arrays, or fills the given CUDA float64 tensors E_out [.., 2] / rcs_out (device path)."""
+        f = np.ascontiguousarray(np.atleast_1d(freqs), dtype=np.float64)
+        pm = _pols(pols)
+        npol = bin(pm).count("1")
+        m = (PO_PAPER_SCALAR if mode == "scalar" else PO_VECTOR) | PHASE[phase]
+        fp = f.ctypes.data_as(C.POINTER(C.c_double))
+        if E_out is not None or rcs_out is not None:
+            ep = E_out.data_ptr() if E_out is not None else None
+            rp = rcs_out.data_ptr() if rcs_out is not None else None
+            self._check(lib().sbr_po_integrate(self._h, fp, len(f), pm, m, ep, rp, 1))
+            return E_out, rcs_out
+        E = np.empty((self.n_angles, len(f), npol, 2), np.float64)
+        R = np.empty((self.n_angles, len(f), npol), np.float64)
+        self._check(lib().sbr_po_integrate(self._h, fp, len(f), pm, m, E.ctypes.data, R.ctypes.data, 0))
+        return E[..., 0] + 1j * E[..., 1], R
+
+    def get_hits(self, angle: int):
+        """Per-ray hits of aspect ``angle`` (needs TRACE_RECORD_HITS): (tri [n, B], t [n, B], n_bounce [n])."""
+        sp, eta, window, offset = self._trace_args
+        g = self.ray_grid_for(*self._angle(angle), sp, eta, window, offset)
+        n = g["nu"] * g["nv"]
+        B = self.max_bounces
+        tri = np.empty((n, B), np.int32)
+        t = np.empty((n, B), np.float32)
+        nb = np.empty(n, np.int32)
+        self._check(lib().sbr_get_hits(self._h, int(angle), tri.ctypes.data, t.ctypes.data, nb.ctypes.data))
+        return tri, t, nb
+
+    def _angle(self, angle):
+        return self._last_angles[angle]
+
+    def get_records(self, angle: int) -> dict:
+        n = C.c_int64()
+        self._check(lib().sbr_get_records(self._h, int(angle), 0, None, None, None, C.byref(n)))
+        cnt = int(n.value)
+        ids = np.empty(cnt, np.int64)
+        coef = np.empty((cnt, 5), np.float32)
+        path = np.empty(cnt, np.float64)
+        self._check(lib().sbr_get_records(self._h, int(angle), cnt, ids.ctypes.data, coef.ctypes.data,
+                                          path.ctypes.data, C.byref(n)))
+        return dict(ray=ids, coef=coef, L=path)

@@ -1,0 +1,294 @@
+"""CUDA path vs the FP64 oracle on the same seeded inputs, through the C ABI.
+
+Parity rule: triangle index and bounce count equal for every ray outside the
+1e-6 edge band (band fraction reported, below 1e-5), hit distance within 1e-5
+relative, RCS within 0.1 dB wherever the oracle is above -40 dBsm.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import sbr_inputs as S
+from parity import assert_hit_parity, assert_rcs_close, compare_hits
+
+pytestmark = pytest.mark.gpu
+C0 = 299_792_458.0
+HITS = 4  # SBR_TRACE_RECORD_HITS
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2604_09243_gb300 import build
+
+    build.build()
+    import paper_2604_09243_gb300 as G
+
+    return G
+
+
+@pytest.fixture()
+def ctx(G):
+    c = G.Context(0)
+    yield c
+    c.close()
+
+
+def _trace_both(G, ctx, orc, om, angles, spacing, B, eta=0.05, window=0.0, offset=(0.0, 0.0), flags=0, **kw):
+    st = ctx.trace(angles, spacing, eta=eta, max_bounces=B, window=window, offset=offset, flags=flags | HITS, **kw)
+    out = []
+    for a, (az, el) in enumerate(angles):
+        fr = orc.make_frame(om.bbox, az, el, spacing, eta=eta, window=window, offset=offset)
+        o = orc.trace(om, fr, B, require_escape=bool(flags & 2))
+        g = ctx.get_hits(a)
+        out.append((g, o, fr))
+    return st, out
+
+
+# ----------------------------------------------------------------------------- C1 sphere
+def test_sphere_hits_rcs_and_mie(G, ctx, orc):
+    case = S.sphere_case(n_random=4)
+    ctx.load_mesh(case["xyz"], case["tri"])
+    om = orc.Mesh(case["xyz"], case["tri"])
+    assert np.array_equal(ctx.get_bbox(), om.bbox)
+    f = case["freqs"]
+    st, res = _trace_both(G, ctx, orc, om, case["angles"], case["spacing"], 1, window=case["window"])
+    assert st["rays_launched"] == 220 * 220 * len(case["angles"])
+    Ev, Rv = ctx.po_integrate(f, "HH,VV", mode="vector")
+    Es, Rs = ctx.po_integrate(f, "HH,VV", mode="scalar")
+    mie = 10 * math.log10(math.pi * orc.mie_pec_backscatter(2 * math.pi * f[0] / C0))
+    n_valid = 0
+    for a, (g, o, fr) in enumerate(res):
+        s = compare_hits(*g, o)
+        assert_hit_parity(s)
+        n_valid += int(o["valid"].sum())
+        Eo, Ro = orc.po(o["coef"], o["L"], o["valid"], f)
+        assert_rcs_close(Rv[a, 0], Ro[0, :2])
+        o2 = orc.trace(om, fr, 1, po_mode="scalar")
+        Eo2, Ro2 = orc.po(o2["coef"], o2["L"], o2["valid"], f)
+        assert_rcs_close(Rs[a, 0], Ro2[0, :2])
+        assert np.all(np.abs(Rs[a, 0] - mie) < 0.5)  # paper's Eq. po_sum vs Mie at ka = 62.9
+    assert st["valid_rays"] == n_valid
+
+
+# ----------------------------------------------------------------------------- C2 trihedral
+def test_trihedral_hits_and_rcs_subset(G, ctx, orc):
+    case = S.trihedral_case()
+    ctx.load_mesh(case["xyz"], case["tri"])
+    om = orc.Mesh(case["xyz"], case["tri"])
+    ang = case["angles"][[0, 1, 37, 60, 90, 91, 133, 179, 180]]
+    st, res = _trace_both(G, ctx, orc, om, ang, case["spacing"], 3)
+    E, R = ctx.po_integrate(case["freqs"], "HH,VV,HV,VH")
+    tot = dict(n=0, band=0)
+    for a, (g, o, fr) in enumerate(res):
+        s = compare_hits(*g, o)
+        assert_hit_parity(s, band_frac_max=1e-4)
+        tot["n"] += s["n"]
+        tot["band"] += s["band"]
+        Eo, Ro = orc.po(o["coef"], o["L"], o["valid"], case["freqs"])
+        assert_rcs_close(R[a, 0], Ro[0])
+    assert tot["band"] / tot["n"] < 1e-5, tot
+
+
+def test_trihedral_full_sweep_rcs(G, ctx, orc):
+    # the benchmark workload: 181 aspects in one call, vector PO, HH/VV
+    case = S.trihedral_case()
+    ctx.load_mesh(case["xyz"], case["tri"])
+    om = orc.Mesh(case["xyz"], case["tri"])
+    st = ctx.trace(case["angles"], case["spacing"], eta=case["eta"], max_bounces=3)
+    E, R = ctx.po_integrate(case["freqs"], "HH,VV")
+    worst = 0.0
+    for a, (az, el) in enumerate(case["angles"]):
+        _, Ro, _, _ = orc.rcs_angle(om, om.bbox, az, el, case["spacing"], case["freqs"], 3, eta=case["eta"])
+        worst = max(worst, assert_rcs_close(R[a, 0], Ro[0, :2]))
+    assert st["ray_bounces"] > st["rays_launched"]
+    print("worst dB error over the sweep:", worst)
+
+
+def test_full_size_sampled_rays(G, ctx, orc):
+    # full sweep in the benchmark's launch configuration; sampled rays checked one by one
+    case = S.trihedral_case()
+    ctx.load_mesh(case["xyz"], case["tri"])
+    om = orc.Mesh(case["xyz"], case["tri"])
+    ctx.trace(case["angles"], case["spacing"], eta=case["eta"], max_bounces=3, flags=HITS)
+    rng = np.random.default_rng(9)
+    for a in (0, 45, 90, 120, 180):
+        az, el = case["angles"][a]
+        fr = orc.make_frame(om.bbox, az, el, case["spacing"], eta=case["eta"])
+        ids = rng.choice(fr.n_rays, 4000, replace=False)
+        o = orc.trace(om, fr, 3, ids=ids)
+        s = compare_hits(*ctx.get_hits(a), o, ids=ids)
+        assert_hit_parity(s)
+
+
+# ----------------------------------------------------------------------------- closed forms
+def test_flat_plate_and_dihedral_closed_forms(G, ctx, orc):
+    xyz, tri = S.square_plate(1.0, 4)
+    ctx.load_mesh(xyz, tri)
+    f = 3e9
+    lam = C0 / f
+    ctx.trace([[0.0, 90.0]], 0.01, max_bounces=1, window=1.2)
+    for mode in ("vector", "scalar"):
+        _, R = ctx.po_integrate([f], "HH,VV", mode=mode)
+        assert np.allclose(R[0, 0], 10 * math.log10(4 * math.pi / lam**2), atol=1e-4)
+    xyz, tri = S.dihedral(1.0, 8)
+    ctx.load_mesh(xyz, tri)
+    f = 10e9
+    lam = C0 / f
+    st = ctx.trace([[45.0, 0.0]], lam / 10, max_bounces=2, offset=(0.25, 0.25))
+    E, R = ctx.po_integrate([f], "HH,VV,HV")
+    n = st["valid_rays"]
+    assert R[0, 0, 0] == pytest.approx(10 * math.log10(4 * math.pi * (n * (lam / 10) ** 2) ** 2 / lam**2), abs=2e-3)
+    assert abs(E[0, 0, 0] + E[0, 0, 1]) < 1e-4 * abs(E[0, 0, 0])  # HH = -VV after two reflections
+
+
+def test_trihedral_peak(G, ctx):
+    xyz, tri = S.trihedral(1.0, 32)
+    ctx.load_mesh(xyz, tri)
+    f = 10e9
+    lam = C0 / f
+    el = math.degrees(math.atan(1 / math.sqrt(2)))
+    ctx.trace([[45.0, el]], lam / 10, max_bounces=3)
+    _, R = ctx.po_integrate([f], "HH,VV,HV,VH")
+    assert abs(R[0, 0, 0] - 10 * math.log10(4 * math.pi / (3 * lam**2))) < 0.1
+    assert R[0, 0, 2] < R[0, 0, 0] - 40
+
+
+# ----------------------------------------------------------------------------- edge cases
+def test_single_and_two_triangles(G, ctx, orc):
+    xyz = np.array([[-1, -1, 0.3], [1, -1, 0.3], [0, 1, 0.3], [0, 1, 0.9]], np.float32)
+    for tri in (np.array([[0, 1, 2]], np.int32), np.array([[0, 1, 2], [0, 2, 3]], np.int32)):
+        ctx.load_mesh(xyz, tri)
+        om = orc.Mesh(xyz, tri)
+        ang = np.array([[0.0, 90.0], [30.0, 60.0], [200.0, -45.0]])
+        st, res = _trace_both(G, ctx, orc, om, ang, 0.013, 2)
+        for g, o, fr in res:
+            assert_hit_parity(compare_hits(*g, o))
+
+
+def test_all_rays_miss_gives_empty_sum(G, ctx):
+    xyz, tri = S.square_plate(1.0, 2)
+    ctx.load_mesh(xyz, tri)
+    st = ctx.trace([[0.0, 0.0]], 0.01, max_bounces=2)  # grazing along the plate plane
+    assert st["valid_rays"] == 0 and st["ray_bounces"] == st["rays_launched"]
+    E, R = ctx.po_integrate([1e9, 2e9], "HH,VV")
+    assert np.all(E == 0) and np.all(np.isneginf(R))
+
+
+@pytest.mark.parametrize("leaf", [1, 2, 8, 16])
+def test_leaf_sizes_same_hits(G, ctx, orc, leaf):
+    xyz, tri = S.icosphere(4)
+    ctx.load_mesh(xyz, tri)
+    ctx.build_bvh(leaf_max=leaf)
+    om = orc.Mesh(xyz, tri)
+    st, res = _trace_both(G, ctx, orc, om, np.array([[12.0, 34.0]]), 0.01, 1, window=2.2)
+    assert_hit_parity(compare_hits(*res[0][0], res[0][1]))
+
+
+def test_chunked_trace_matches_single_chunk(G, ctx):
+    case = S.trihedral_case(az_step=10.0)
+    ctx.load_mesh(case["xyz"], case["tri"])
+    sp = 3 * case["spacing"]
+    a = ctx.trace(case["angles"], sp, max_bounces=3)
+    E1, R1 = ctx.po_integrate([10e9, 11e9], "HH,VV,HV,VH")
+    b = ctx.trace(case["angles"], sp, max_bounces=3, chunk_rays=70_000)
+    E2, R2 = ctx.po_integrate([10e9, 11e9], "HH,VV,HV,VH")
+    assert a == b
+    assert np.array_equal(E1, E2)
+
+
+def test_deterministic_results(G, ctx):
+    case = S.trihedral_case(az_step=15.0)
+    ctx.load_mesh(case["xyz"], case["tri"])
+    outs = []
+    for _ in range(2):
+        ctx.trace(case["angles"], case["spacing"], max_bounces=3)
+        outs.append(ctx.po_integrate([9e9, 10e9, 11e9], "HH,VV,HV,VH")[0])
+    assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("B", [1, 2, 3, 5])
+def test_bounce_limits_and_escape(G, ctx, orc, B):
+    xyz, tri = S.trihedral(1.0, 8)
+    ctx.load_mesh(xyz, tri)
+    om = orc.Mesh(xyz, tri)
+    ang = np.array([[45.0, 35.26], [20.0, 20.0]])
+    for flags in (0, 2):
+        st, res = _trace_both(G, ctx, orc, om, ang, 0.01, B, flags=flags)
+        E, R = ctx.po_integrate([10e9], "HH,VV")
+        for a, (g, o, fr) in enumerate(res):
+            assert_hit_parity(compare_hits(*g, o))
+            Eo, Ro = orc.po(o["coef"], o["L"], o["valid"], [10e9])
+            assert_rcs_close(R[a, 0], Ro[0, :2])
+
+
+def test_multifrequency_and_phase_precision(G, ctx, orc):
+    case = S.trihedral_case()
+    ctx.load_mesh(case["xyz"], case["tri"])
+    om = orc.Mesh(case["xyz"], case["tri"])
+    ang = case["angles"][[30, 90]]
+    freqs = np.linspace(8e9, 12e9, 17)
+    ctx.trace(ang, case["spacing"], max_bounces=3)
+    errs = {}
+    for ph in ("compensated", "fp64", "fp32"):
+        E, R = ctx.po_integrate(freqs, "HH,VV", phase=ph)
+        e = 0.0
+        for a, (az, el) in enumerate(ang):
+            _, Ro, _, _ = orc.rcs_angle(om, om.bbox, az, el, case["spacing"], freqs, 3, eta=case["eta"])
+            e = max(e, assert_rcs_close(R[a], Ro[:, :2], tol=0.5))
+        errs[ph] = e
+    assert errs["compensated"] <= 0.1 and errs["fp64"] <= 0.1
+    print("max dB error by phase precision:", errs)
+
+
+def test_device_outputs_and_torch_stream(G, orc):
+    torch = pytest.importorskip("torch")
+    st = torch.cuda.Stream()
+    c = G.Context(0, stream=st)
+    case = S.trihedral_case(az_step=30.0)
+    xyz = torch.from_numpy(case["xyz"]).cuda()
+    tri = torch.from_numpy(case["tri"]).cuda()
+    torch.cuda.synchronize()
+    c.load_mesh(xyz, tri)
+    c.trace(case["angles"], case["spacing"], max_bounces=3)
+    Eh, Rh = c.po_integrate([10e9], "HH,VV")
+    Ed = torch.empty((len(case["angles"]), 1, 2, 2), dtype=torch.float64, device="cuda")
+    Rd = torch.empty((len(case["angles"]), 1, 2), dtype=torch.float64, device="cuda")
+    c.po_integrate([10e9], "HH,VV", E_out=Ed, rcs_out=Rd)
+    st.synchronize()
+    assert np.array_equal(Rd.cpu().numpy(), Rh)
+    assert np.array_equal(Ed.cpu().numpy()[..., 0], Eh.real)
+    c.close()
+
+
+def test_records_match_oracle_coefficients(G, ctx, orc):
+    case = S.trihedral_case()
+    ctx.load_mesh(case["xyz"], case["tri"])
+    om = orc.Mesh(case["xyz"], case["tri"])
+    az, el = case["angles"][70]
+    ctx.trace([[az, el]], case["spacing"], max_bounces=3)
+    r = ctx.get_records(0)
+    fr = orc.make_frame(om.bbox, az, el, case["spacing"], eta=case["eta"])
+    o = orc.trace(om, fr, 3, ids=r["ray"])
+    o_s = orc.trace(om, fr, 3, ids=r["ray"], po_mode="scalar")
+    ok = o["band"] == 0
+    assert np.all(o["valid"][ok] == 1)
+    scale = 2 * case["spacing"] ** 2
+    assert np.max(np.abs(r["coef"][ok, :4] - o["coef"][ok])) < 1e-4 * scale
+    assert np.max(np.abs(r["coef"][ok, 4] - o_s["coef"][ok, 0])) < 1e-4 * scale
+    assert np.max(np.abs(r["L"][ok] - o["L"][ok])) < 2e-5
+
+
+def test_aircraft_sampled_parity(G, ctx, orc):
+    # 1M-triangle aircraft at 1 GHz (lambda/10 grid), two aspects, up to 10 bounces
+    case = S.aircraft_case(1e9, n_az=360)
+    ctx.load_mesh(case["xyz"], case["tri"])
+    om = orc.Mesh(case["xyz"], case["tri"])
+    ang = case["angles"][[0, 30]]
+    st, res = _trace_both(G, ctx, orc, om, ang, case["spacing"], 10)
+    E, R = ctx.po_integrate(case["freqs"], "HH,VV")
+    for a, (g, o, fr) in enumerate(res):
+        s = compare_hits(*g, o)
+        assert_hit_parity(s, band_frac_max=1e-4)
+        Eo, Ro = orc.po(o["coef"], o["L"], o["valid"], case["freqs"])
+        assert_rcs_close(R[a, 0], Ro[0, :2])
