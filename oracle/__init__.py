@@ -50,7 +50,8 @@ class Frame(C.Structure):
 
 class TraceOpts(C.Structure):
     _fields_ = [("max_bounces", C.c_int), ("po_mode", C.c_int), ("phase_literal", C.c_int),
-                ("require_escape", C.c_int), ("use_bvh", C.c_int), ("n_threads", C.c_int)]
+                ("require_escape", C.c_int), ("use_bvh", C.c_int), ("n_threads", C.c_int),
+                ("transport", C.c_int)]
 
 
 _lib = None
@@ -81,7 +82,7 @@ def lib():
         L.orc_closest_hit.restype = C.c_int
         L.orc_trace.argtypes = [C.c_void_p, P(Frame), P(TraceOpts), P(C.c_int64), C.c_int64,
                                 P(C.c_int32), P(C.c_double), P(C.c_int32), P(C.c_uint8), P(C.c_uint8),
-                                P(C.c_double), P(C.c_double), P(C.c_int64)]
+                                P(C.c_double), P(C.c_double), P(C.c_double), P(C.c_int64)]
         L.orc_trace.restype = C.c_int
         L.orc_po.argtypes = [P(C.c_double), P(C.c_double), P(C.c_uint8), C.c_int64, P(C.c_double),
                              C.c_int64, P(C.c_double), P(C.c_double)]
@@ -170,10 +171,16 @@ class Mesh:
 
 
 def trace(mesh: Mesh, frame: Frame, max_bounces: int, po_mode: str = "vector", phase_literal: bool = False,
-          require_escape: bool = False, use_bvh: bool = True, ids=None, threads: int | None = None) -> dict:
+          require_escape: bool = False, use_bvh: bool = True, ids=None, threads: int | None = None,
+          transport: str = "fp32") -> dict:
     """Trace rays of ``frame`` (all, or the ray ids ``ids`` = j*nu + i) through
     ``mesh`` (Algorithm 2) and return per-ray arrays: hit_tri/hit_t [n, B],
-    nb, valid, band, coef [n, 4] (HH, VV, HV, VH) and L."""
+    nb, valid, band, coef [n, 4] (HH, VV, HV, VH) and L.
+
+    transport="fp32": hit decisions, hit points, normals, reflections and
+    offsets in the written FP32 operation order (the precision the traversal
+    runs in); transport="exact": the same steps in FP64 with exact inclusive
+    edges. Path length, fields and coefficients are FP64 in both."""
     B = int(max_bounces)
     if ids is None:
         n = frame.n_rays
@@ -184,14 +191,15 @@ def trace(mesh: Mesh, frame: Frame, max_bounces: int, po_mode: str = "vector", p
         idp = ids
     out = dict(hit_tri=np.empty((n, B), np.int32), hit_t=np.empty((n, B), np.float64),
                nb=np.empty(n, np.int32), valid=np.empty(n, np.uint8), band=np.empty(n, np.uint8),
-               coef=np.empty((n, 4), np.float64), L=np.empty(n, np.float64),
+               coef=np.empty((n, 4), np.float64), L=np.empty(n, np.float64), bmin=np.empty(n, np.float64),
                counters=np.zeros(2, np.int64))
     o = TraceOpts(B, 1 if po_mode == "scalar" else 0, int(bool(phase_literal)), int(bool(require_escape)),
-                  int(bool(use_bvh) and mesh.has_bvh), int(threads or default_threads()))
+                  int(bool(use_bvh) and mesh.has_bvh), int(threads or default_threads()),
+                  {"fp32": 0, "exact": 1}[transport])
     rc = lib().orc_trace(mesh._h, C.byref(frame), C.byref(o), _ptr(idp, C.c_int64), n,
                          _ptr(out["hit_tri"], C.c_int32), _ptr(out["hit_t"], C.c_double),
                          _ptr(out["nb"], C.c_int32), _ptr(out["valid"], C.c_uint8), _ptr(out["band"], C.c_uint8),
-                         _ptr(out["coef"], C.c_double), _ptr(out["L"], C.c_double),
+                         _ptr(out["coef"], C.c_double), _ptr(out["L"], C.c_double), _ptr(out["bmin"], C.c_double),
                          _ptr(out["counters"], C.c_int64))
     if rc != 0:
         raise ValueError("orc_trace failed")
@@ -232,10 +240,11 @@ def mie_pec_backscatter(x: float) -> float:
 
 
 def rcs_angle(mesh: Mesh, bbox, az, el, spacing, freqs, max_bounces, eta=0.05, window=0.0, offset=(0.0, 0.0),
-              po_mode="vector", phase_literal=False, require_escape=False, threads=None, ids=None):
+              po_mode="vector", phase_literal=False, require_escape=False, threads=None, ids=None,
+              transport="fp32"):
     """Convenience: one aspect, trace + PO. Returns (E [nf,4], rcs_dbsm [nf,4], trace dict, frame)."""
     fr = make_frame(bbox, az, el, spacing, eta=eta, window=window, offset=offset)
     tr = trace(mesh, fr, max_bounces, po_mode=po_mode, phase_literal=phase_literal,
-               require_escape=require_escape, ids=ids, threads=threads)
+               require_escape=require_escape, ids=ids, threads=threads, transport=transport)
     E, rcs = po(tr["coef"], tr["L"], tr["valid"], freqs)
     return E, rcs, tr, fr

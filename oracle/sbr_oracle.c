@@ -31,9 +31,18 @@
  *     P0, ds*u, ds*v and k are rounded once to FP32 and ray (i, j) starts at
  *     o = (P0 + i*U) + j*V evaluated in FP32 without fused multiply-add, so both
  *     sides trace bit-identical rays; the oracle then continues in FP64.
- *   - Intersection: Moller-Trumbore form, inclusive edges (u, v >= 0,
- *     u + v <= 1), t > 0, the triangle just left is skipped, and the closest hit
- *     is the smallest (t, original triangle index) pair.
+ *   - Intersection: Moller-Trumbore form, t > 0, the triangle just left is
+ *     skipped, and the closest hit is the smallest (t, original triangle index)
+ *     pair.
+ *   - Transport precision. Which triangle a ray hits is an integer decided by
+ *     floating point; the oracle takes that decision in FP32, the precision the
+ *     paper runs its traversal in and the kernel's, following a written
+ *     operation order (ORC_FP32 transport below: explicit fused multiply-adds,
+ *     IEEE division and square root, a barycentric slack of 2^-12 that closes
+ *     FP32 cracks along shared edges). Everything downstream of the hits (path
+ *     length, field transport, PO sums) is FP64. An exact FP64 transport
+ *     (inclusive edges, no slack) is kept beside it for the physics checks and
+ *     for measuring the edge band.
  *   - eps = 1e-5 * bbox diagonal, applied along the normal turned toward the
  *     incoming side.
  *   - Path L = k.o0 + sum t_b + k.x_last (monostatic round trip to a reference
@@ -164,8 +173,11 @@ typedef struct {
     double* e2;  /* [nt][3] */
     double* nrm; /* [nt][3] unit normal e1 x e2 / |e1 x e2| */
     double* cen; /* [nt][3] centroid */
-    double* tlo; /* [nt][3] triangle AABB */
+    double* tlo; /* [nt][3] triangle AABB, enlarged to cover the FP32 test's slack */
     double* thi;
+    float* v0f;  /* [nt][3] FP32 vertex 0 */
+    float* e1f;  /* [nt][3] FP32 edge v1 - v0 (rounded) */
+    float* e2f;  /* [nt][3] FP32 edge v2 - v0 (rounded) */
     float bbox[6];
     orc_node* nodes;
     int64_t n_nodes, cap_nodes;
@@ -177,6 +189,7 @@ void orc_mesh_free(orc_mesh* m)
 {
     if (!m) return;
     free(m->v0); free(m->e1); free(m->e2); free(m->nrm); free(m->cen); free(m->tlo); free(m->thi);
+    free(m->v0f); free(m->e1f); free(m->e2f);
     free(m->nodes); free(m->order);
     free(m);
 }
@@ -189,6 +202,8 @@ orc_mesh* orc_mesh_create(const float* xyz, int64_t nv, const int32_t* tri, int6
     size_t b = sizeof(double) * 3 * (size_t)nt;
     m->v0 = malloc(b); m->e1 = malloc(b); m->e2 = malloc(b); m->nrm = malloc(b);
     m->cen = malloc(b); m->tlo = malloc(b); m->thi = malloc(b);
+    size_t bf = sizeof(float) * 3 * (size_t)nt;
+    m->v0f = malloc(bf); m->e1f = malloc(bf); m->e2f = malloc(bf);
     for (int c = 0; c < 3; ++c) { m->bbox[c] = INFINITY; m->bbox[3 + c] = -INFINITY; }
     for (int64_t v = 0; v < nv; ++v)
         for (int c = 0; c < 3; ++c) {
@@ -208,6 +223,21 @@ orc_mesh* orc_mesh_create(const float* xyz, int64_t nv, const int32_t* tri, int6
             m->cen[3 * k + c] = (A[c] + B[c] + C[c]) / 3.0;
             m->tlo[3 * k + c] = fmin(A[c], fmin(B[c], C[c]));
             m->thi[3 * k + c] = fmax(A[c], fmax(B[c], C[c]));
+            m->v0f[3 * k + c] = xyz[3 * ia + c];
+            m->e1f[3 * k + c] = xyz[3 * ib + c] - xyz[3 * ia + c];
+            m->e2f[3 * k + c] = xyz[3 * ic + c] - xyz[3 * ia + c];
+        }
+        /* FP32 hits may lie up to the slack (2^-12 of the triangle) plus a few
+         * FP32 rounding units outside the exact triangle: widen its box */
+        double ext = 0.0, mag = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            ext = fmax(ext, m->thi[3 * k + c] - m->tlo[3 * k + c]);
+            mag = fmax(mag, fmax(fabs(m->tlo[3 * k + c]), fabs(m->thi[3 * k + c])));
+        }
+        double grow = ext * 0x1p-11 + mag * 0x1p-19 + 1e-30;
+        for (int c = 0; c < 3; ++c) {
+            m->tlo[3 * k + c] -= grow;
+            m->thi[3 * k + c] += grow;
         }
         double n[3];
         cross3(m->e1 + 3 * k, m->e2 + 3 * k, n);
@@ -314,17 +344,62 @@ static int tri_hit(const orc_mesh* m, int64_t k, const double* o, const double* 
     return 1;
 }
 
+/* ORC_FP32 transport: the FP32 operation order both implementations follow.
+ * fmaf is one rounding; every other operation is one FP32 round-to-nearest
+ * operation (this file is compiled without contraction). */
+static void cross32(const float* a, const float* b, float* c)
+{
+    c[0] = fmaf(a[1], b[2], -(a[2] * b[1]));
+    c[1] = fmaf(a[2], b[0], -(a[0] * b[2]));
+    c[2] = fmaf(a[0], b[1], -(a[1] * b[0]));
+}
+static float dot32(const float* a, const float* b) { return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2])); }
+
+/* Moller-Trumbore in FP32: e1 = v1 - v0 and e2 = v2 - v0 rounded to FP32,
+ * p = d x e2, det = e1.p, s = o - v0, U = s.p, q = s x e1, V = d.q, T = e2.q;
+ * with U, V, T negated when det < 0 and a = |det|, m = a 2^-12 (the slack),
+ * a hit needs det != 0, U >= -m, V >= -m, U + V <= a + m, T > 0; t = T / det. */
+static int tri_hit32(const orc_mesh* m, int64_t k, const float* o, const float* d, float* t, double* bmin)
+{
+    const float *v0 = m->v0f + 3 * k, *e1 = m->e1f + 3 * k, *e2 = m->e2f + 3 * k;
+    float p[3], q[3], s[3];
+    cross32(d, e2, p);
+    float det = dot32(e1, p);
+    if (det == 0.0f) return 0;
+    for (int c = 0; c < 3; ++c) s[c] = o[c] - v0[c];
+    float U = dot32(s, p);
+    cross32(s, e1, q);
+    float V = dot32(d, q);
+    float T = dot32(e2, q);
+    float a = det, Us = U, Vs = V, Ts = T;
+    if (det < 0.0f) { a = -det; Us = -U; Vs = -V; Ts = -T; }
+    float mg = a * 0x1p-12f;
+    if (!(Us >= -mg && Vs >= -mg && Us + Vs <= a + mg && Ts > 0.0f)) return 0;
+    *t = T / det;
+    double ad = (double)a;
+    *bmin = fmin((double)Us, fmin((double)Vs, ad - (double)Us - (double)Vs)) / ad;
+    return 1;
+}
+
 typedef struct {
     double t, t2, bmin;
     int64_t k;
     int64_t tests, nodes;
 } orc_hit;
 
-static void consider(const orc_mesh* m, int64_t k, const double* o, const double* d, orc_hit* h)
+/* candidate triangle k; fp32 selects the FP32 test (ray o32, d32), else FP64 (o, d) */
+static void consider(const orc_mesh* m, int64_t k, const double* o, const double* d, const float* o32,
+                     const float* d32, int fp32, orc_hit* h)
 {
     double t, b;
     h->tests++;
-    if (!tri_hit(m, k, o, d, &t, &b)) return;
+    if (fp32) {
+        float tf;
+        if (!tri_hit32(m, k, o32, d32, &tf, &b)) return;
+        t = (double)tf;
+    } else if (!tri_hit(m, k, o, d, &t, &b)) {
+        return;
+    }
     if (t < h->t || (t == h->t && k < h->k)) {
         if (h->k >= 0 && h->t < h->t2) h->t2 = h->t;
         h->t = t;
@@ -353,8 +428,11 @@ static int slab(const orc_node* nd, const double* o, const double* d, double tma
     return 1;
 }
 
-/* closest hit skipping triangle `skip`; use_bvh = 0 brute force, 1 median BVH */
-static void closest(const orc_mesh* m, int use_bvh, const double* o, const double* d, int64_t skip, orc_hit* h)
+/* closest hit skipping triangle `skip`; use_bvh = 0 brute force, 1 median BVH.
+ * With fp32 set the FP32 ray (o32, d32) is tested; (o, d) is then the same ray
+ * in FP64 and only drives the (conservative) box culling. */
+static void closest(const orc_mesh* m, int use_bvh, const double* o, const double* d, const float* o32,
+                    const float* d32, int fp32, int64_t skip, orc_hit* h)
 {
     h->t = INFINITY;
     h->t2 = INFINITY;
@@ -363,7 +441,7 @@ static void closest(const orc_mesh* m, int use_bvh, const double* o, const doubl
     h->tests = h->nodes = 0;
     if (!use_bvh || !m->nodes) {
         for (int64_t k = 0; k < m->nt; ++k)
-            if (k != skip) consider(m, k, o, d, h);
+            if (k != skip) consider(m, k, o, d, o32, d32, fp32, h);
         return;
     }
     int64_t stack[256];
@@ -379,7 +457,7 @@ static void closest(const orc_mesh* m, int use_bvh, const double* o, const doubl
         if (nd->count > 0) {
             for (int64_t i = nd->first; i < nd->first + nd->count; ++i) {
                 int64_t k = m->order[i];
-                if (k != skip) consider(m, k, o, d, h);
+                if (k != skip) consider(m, k, o, d, o32, d32, fp32, h);
             }
             continue;
         }
@@ -403,7 +481,7 @@ int orc_closest_hit(const orc_mesh* m, int use_bvh, const double* o, const doubl
                     double* t, int64_t* tri, double* bmin, double* t2)
 {
     orc_hit h;
-    closest(m, use_bvh, o, d, skip, &h);
+    closest(m, use_bvh, o, d, NULL, NULL, 0, skip, &h);
     *t = h.t;
     *tri = h.k;
     *bmin = h.bmin;
@@ -433,6 +511,7 @@ typedef struct {
     int require_escape;
     int use_bvh;
     int n_threads;
+    int transport; /* 0 FP32 (the written operation order), 1 exact FP64 */
 } orc_trace_opts;
 
 typedef struct {
@@ -448,6 +527,7 @@ typedef struct {
     uint8_t* band;     /* [n] bit0 barycentric band, bit1 runner-up band */
     double* coef;      /* [n][4] HH, VV, HV, VH */
     double* Lpath;     /* [n] */
+    double* bmin;      /* [n] smallest barycentric of the hits along the path (1 if no hit) */
     int64_t* counters; /* [2] per call: triangle tests, node visits */
     int64_t t_begin, t_end;
     int64_t tests, nodes;
@@ -458,11 +538,13 @@ static void trace_one(trace_job* J, int64_t r)
     const orc_frame* f = J->f;
     const orc_trace_opts* opt = J->opt;
     const int B = opt->max_bounces;
+    const int fp32 = opt->transport == 0;
     int64_t rid = J->ids ? J->ids[r] : r;
     int64_t i = rid % f->nu, j = rid / f->nu;
-    float of[3], df[3];
-    orc_ray(f, i, j, of, df);
-    double o[3] = {of[0], of[1], of[2]}, d[3] = {df[0], df[1], df[2]};
+    float o32[3], d32[3];
+    orc_ray(f, i, j, o32, d32);
+    double o[3] = {o32[0], o32[1], o32[2]}, d[3] = {d32[0], d32[1], d32[2]};
+    const float eps32 = (float)f->eps;
     double Ev[3], Eh[3];
     for (int c = 0; c < 3; ++c) { Ev[c] = f->vhat[c]; Eh[c] = f->hhat[c]; }
     double ref = dot3(f->khat, o); /* k.o0 */
@@ -470,6 +552,7 @@ static void trace_one(trace_job* J, int64_t r)
     double cv[4] = {0, 0, 0, 0};
     int N = 0;
     uint8_t band = 0;
+    double bmin_path = 1.0;
     int64_t skip = -1;
     for (int b = 0; b < B; ++b) {
         if (J->hit_tri) J->hit_tri[r * B + b] = -1;
@@ -477,22 +560,56 @@ static void trace_one(trace_job* J, int64_t r)
     }
     for (int b = 0; b < B; ++b) {
         orc_hit h;
-        closest(J->m, opt->use_bvh, o, d, skip, &h);
+        closest(J->m, opt->use_bvh, o, d, o32, d32, fp32, skip, &h);
         J->tests += h.tests;
         J->nodes += h.nodes;
         if (h.k < 0) break;
         if (h.bmin < 1e-6) band |= 1;
+        if (h.bmin < bmin_path) bmin_path = h.bmin;
         if (h.t2 - h.t <= 1e-6 * h.t) band |= 2;
-        double x[3];
-        for (int c = 0; c < 3; ++c) x[c] = o[c] + h.t * d[c];
+        double x[3], n[3], din[3];
+        int front; /* the normal faces the incoming ray (orientation decided in the transport precision) */
+        if (fp32) {
+            /* hit point, unit normal, reflection and offset in the FP32 operation order */
+            const float* e1 = J->m->e1f + 3 * h.k;
+            const float* e2 = J->m->e2f + 3 * h.k;
+            const float tf = (float)h.t;
+            float x32[3], n32[3];
+            for (int c = 0; c < 3; ++c) x32[c] = fmaf(tf, d32[c], o32[c]);
+            cross32(e1, e2, n32);
+            float len2 = dot32(n32, n32);
+            float rl = 1.0f / sqrtf(len2);
+            for (int c = 0; c < 3; ++c) n32[c] = n32[c] * rl;
+            float dn32 = dot32(d32, n32);
+            float m2 = -2.0f * dn32;
+            front = dn32 < 0.0f;
+            for (int c = 0; c < 3; ++c) {
+                x[c] = x32[c];
+                n[c] = n32[c];
+                din[c] = d32[c];
+            }
+            for (int c = 0; c < 3; ++c) {
+                float nf32 = dn32 < 0.0f ? n32[c] : -n32[c];
+                d32[c] = fmaf(m2, n32[c], d32[c]);
+                o32[c] = fmaf(eps32, nf32, x32[c]);
+                d[c] = d32[c];
+                o[c] = o32[c];
+            }
+        } else {
+            for (int c = 0; c < 3; ++c) {
+                x[c] = o[c] + h.t * d[c];
+                n[c] = J->m->nrm[3 * h.k + c];
+                din[c] = d[c];
+            }
+            front = dot3(d, n) < 0.0;
+        }
         R += h.t;
         N += 1;
         if (J->hit_tri) J->hit_tri[r * B + b] = (int32_t)h.k;
         if (J->hit_t) J->hit_t[r * B + b] = h.t;
-        const double* n = J->m->nrm + 3 * h.k;
-        double dn = dot3(d, n);
+        double dn = dot3(din, n);
         double nf[3];
-        for (int c = 0; c < 3; ++c) nf[c] = dn < 0.0 ? n[c] : -n[c];
+        for (int c = 0; c < 3; ++c) nf[c] = front ? n[c] : -n[c];
         if (N == 1) cos0 = dot3(nf, f->rhat);
         /* candidate contribution if this hit is the last one */
         L = ref + R + dot3(f->khat, x);
@@ -503,7 +620,7 @@ static void trace_one(trace_job* J, int64_t r)
             double W[2][3];
             for (int q = 0; q < 2; ++q) {
                 double Hf[3], Jc[3];
-                cross3(d, Eq[q], Hf);
+                cross3(din, Eq[q], Hf);
                 cross3(nf, Hf, Jc);
                 for (int c = 0; c < 3; ++c) Jc[c] *= 2.0;
                 double jr = dot3(Jc, f->rhat);
@@ -514,14 +631,19 @@ static void trace_one(trace_job* J, int64_t r)
             cv[2] = dot3(W[1], f->hhat); /* HV: receive H, transmit V */
             cv[3] = dot3(W[0], f->vhat); /* VH: receive V, transmit H */
         }
-        reflect(n, d, Ev, Eh);
-        for (int c = 0; c < 3; ++c) o[c] = x[c] + f->eps * nf[c];
+        if (fp32) {
+            double dd[3] = {din[0], din[1], din[2]};
+            reflect(n, dd, Ev, Eh); /* fields in FP64 about the FP32 normal */
+        } else {
+            reflect(n, d, Ev, Eh);
+            for (int c = 0; c < 3; ++c) o[c] = x[c] + f->eps * nf[c];
+        }
         skip = h.k;
     }
     int valid = N >= 1;
     if (valid && opt->require_escape && N == B) {
         orc_hit h;
-        closest(J->m, opt->use_bvh, o, d, skip, &h);
+        closest(J->m, opt->use_bvh, o, d, o32, d32, fp32, skip, &h);
         J->tests += h.tests;
         J->nodes += h.nodes;
         if (h.k >= 0) valid = 0;
@@ -538,6 +660,7 @@ static void trace_one(trace_job* J, int64_t r)
     if (J->coef)
         for (int p = 0; p < 4; ++p) J->coef[4 * r + p] = valid ? cv[p] : 0.0;
     if (J->Lpath) J->Lpath[r] = valid ? L : 0.0;
+    if (J->bmin) J->bmin[r] = bmin_path;
 }
 
 static void* trace_worker(void* arg)
@@ -550,7 +673,7 @@ static void* trace_worker(void* arg)
 /* Trace rays `ids` (NULL: every ray of the frame, n = nu*nv). Outputs may be NULL. */
 int orc_trace(const orc_mesh* m, const orc_frame* f, const orc_trace_opts* opt, const int64_t* ids, int64_t n,
               int32_t* hit_tri, double* hit_t, int32_t* nb, uint8_t* valid, uint8_t* band, double* coef,
-              double* Lpath, int64_t* counters)
+              double* Lpath, double* bmin, int64_t* counters)
 {
     if (!m || !f || !opt || opt->max_bounces < 1 || n < 0) return -1;
     int T = opt->n_threads > 0 ? opt->n_threads : 1;
@@ -563,7 +686,7 @@ int orc_trace(const orc_mesh* m, const orc_frame* f, const orc_trace_opts* opt, 
         memset(J, 0, sizeof(*J));
         J->m = m; J->f = f; J->opt = opt; J->ids = ids; J->n = n;
         J->hit_tri = hit_tri; J->hit_t = hit_t; J->nb = nb; J->valid = valid; J->band = band;
-        J->coef = coef; J->Lpath = Lpath;
+        J->coef = coef; J->Lpath = Lpath; J->bmin = bmin;
         J->t_begin = n * t / T;
         J->t_end = n * (t + 1) / T;
     }

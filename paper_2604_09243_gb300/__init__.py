@@ -5,5 +5,5 @@ The compute path lives in ``lib/libsbr.so`` (CUDA, C ABI in ``include/sbr.h``);
 """
 from .sbr import (  # noqa: F401
     Context, SbrError, lib, ray_grid, spacing_for, version, POL_ORDER, EXPORTS,
-    TRACE_PHASE_LITERAL_2R, TRACE_REQUIRE_ESCAPE, TRACE_RECORD_HITS, TRACE_COUNT_VISITS,
+    TRACE_PHASE_LITERAL_2R, TRACE_REQUIRE_ESCAPE, TRACE_RECORD_HITS, TRACE_COUNT_VISITS, TRACE_TIME_PASSES,
 )

@@ -97,8 +97,15 @@ __global__ void __launch_bounds__(kThreads) k_prep(const float* xyz, const int* 
         float3 c = make_float3(xyz[3 * (long long)ic], xyz[3 * (long long)ic + 1], xyz[3 * (long long)ic + 2]);
         float3 bl = make_float3(fminf(a.x, fminf(b.x, c.x)), fminf(a.y, fminf(b.y, c.y)), fminf(a.z, fminf(b.z, c.z)));
         float3 bh = make_float3(fmaxf(a.x, fmaxf(b.x, c.x)), fmaxf(a.y, fmaxf(b.y, c.y)), fmaxf(a.z, fmaxf(b.z, c.z)));
-        tbox[2 * i] = make_float4(bl.x, bl.y, bl.z, 0.f);
-        tbox[2 * i + 1] = make_float4(bh.x, bh.y, bh.z, 0.f);
+        // the FP32 triangle test accepts hits up to its slack (2^-12 of the
+        // triangle) plus a few rounding units outside the exact triangle: widen
+        // the leaf box so the culling stays conservative
+        const float ext = fmaxf(bh.x - bl.x, fmaxf(bh.y - bl.y, bh.z - bl.z));
+        const float mag = fmaxf(fmaxf(fmaxf(fabsf(bl.x), fabsf(bh.x)), fmaxf(fabsf(bl.y), fabsf(bh.y))),
+                                fmaxf(fabsf(bl.z), fabsf(bh.z)));
+        const float grow = ext * 0x1p-11f + mag * 0x1p-19f + 1e-30f;
+        tbox[2 * i] = make_float4(bl.x - grow, bl.y - grow, bl.z - grow, 0.f);
+        tbox[2 * i + 1] = make_float4(bh.x + grow, bh.y + grow, bh.z + grow, 0.f);
         float3 m = make_float3((a.x + b.x + c.x) * (1.f / 3.f), (a.y + b.y + c.y) * (1.f / 3.f),
                                (a.z + b.z + c.z) * (1.f / 3.f));
         cen[i] = make_float4(m.x, m.y, m.z, 0.f);

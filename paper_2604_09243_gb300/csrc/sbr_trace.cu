@@ -25,9 +25,10 @@ namespace {
 
 constexpr int kTraceThreads = 256;
 constexpr int kStack = 64;
-// Barycentric slack of the FP32 triangle test (2^-22): closes the FP32 cracks
-// along shared edges; it is well inside the 1e-6 edge band of the parity rule.
-constexpr float kSlack = 2.384185791015625e-07f;
+// Barycentric slack of the FP32 triangle test (2^-12): closes the FP32 cracks
+// along shared edges (FP32 barycentric errors reach ~1e-5 for rays starting
+// metres from centimetre facets); leaf boxes are widened to cover it.
+constexpr float kSlack = 0x1p-12f;
 // conservative slab test: exit distance scaled by 1 + 2*gamma_3 (robust traversal)
 constexpr float kBoxGrow = 1.0000008f;
 constexpr unsigned kFull = 0xffffffffu;
@@ -86,6 +87,23 @@ __device__ __forceinline__ void tf_dot(const float* a, float3 b, float& hi, floa
     lo = __fsub_rn(lo_, __fsub_rn(hi, s2));
 }
 
+// ---------------------------------------------------------------- FP32 transport order
+// Which triangle a ray hits, where, and where it goes next are decided in FP32
+// in one written operation order (each fma a single rounding, every other
+// operation one IEEE round-to-nearest operation), so the decisions are
+// reproducible bit for bit by any implementation of the same order:
+//   cross(a, b) = (fma(a.y, b.z, -(a.z b.y)), fma(a.z, b.x, -(a.x b.z)), fma(a.x, b.y, -(a.y b.x)))
+//   dot(a, b)   = fma(a.x, b.x, fma(a.y, b.y, a.z b.z))
+__device__ __forceinline__ float3 cross_s(float3 a, float3 b)
+{
+    return make_float3(__fmaf_rn(a.y, b.z, -__fmul_rn(a.z, b.y)), __fmaf_rn(a.z, b.x, -__fmul_rn(a.x, b.z)),
+                       __fmaf_rn(a.x, b.y, -__fmul_rn(a.y, b.x)));
+}
+__device__ __forceinline__ float dot_s(float3 a, float3 b)
+{
+    return __fmaf_rn(a.x, b.x, __fmaf_rn(a.y, b.y, __fmul_rn(a.z, b.z)));
+}
+
 // ---------------------------------------------------------------- closest hit
 template <bool kCount>
 __device__ __forceinline__ void closest_hit(const float4* __restrict__ nodes, const float4* __restrict__ tris, float3 o,
@@ -142,19 +160,20 @@ __device__ __forceinline__ void closest_hit(const float4* __restrict__ nodes, co
                 if (k == skip) continue;
                 const float4* tp = tris + 3 * (size_t)k;
                 const float4 A = __ldg(tp), B = __ldg(tp + 1), C = __ldg(tp + 2);
-                // Moller-Trumbore, division-free until a candidate is inside
-                const float px = d.y * C.z - d.z * C.y, py = d.z * C.x - d.x * C.z, pz = d.x * C.y - d.y * C.x;
-                const float det = B.x * px + B.y * py + B.z * pz;
-                const float sx = o.x - A.x, sy = o.y - A.y, sz = o.z - A.z;
-                const float qx = sy * B.z - sz * B.y, qy = sz * B.x - sx * B.z, qz = sx * B.y - sy * B.x;
-                const float sg = det < 0.f ? -1.f : 1.f;
-                const float U = sg * (sx * px + sy * py + sz * pz);
-                const float V = sg * (d.x * qx + d.y * qy + d.z * qz);
-                const float T = C.x * qx + C.y * qy + C.z * qz;
+                // Moller-Trumbore in the written FP32 operation order (division
+                // only for a candidate inside the triangle)
+                const float3 e1 = make_float3(B.x, B.y, B.z), e2 = make_float3(C.x, C.y, C.z);
+                const float3 p = cross_s(d, e2);
+                const float det = dot_s(e1, p);
+                const float3 s = make_float3(__fsub_rn(o.x, A.x), __fsub_rn(o.y, A.y), __fsub_rn(o.z, A.z));
+                const float3 qv = cross_s(s, e1);
+                const float U0 = dot_s(s, p), V0 = dot_s(d, qv), T0 = dot_s(e2, qv);
+                const bool neg = det < 0.f;
+                const float U = neg ? -U0 : U0, V = neg ? -V0 : V0, T = neg ? -T0 : T0;
                 const float ad = fabsf(det);
-                const float tol = kSlack * ad;
-                if (ad > 0.f && U >= -tol && V >= -tol && U + V <= ad + tol && sg * T > 0.f) {
-                    const float t = __fdiv_rn(T, det);
+                const float mg = __fmul_rn(ad, kSlack);
+                if (det != 0.f && U >= -mg && V >= -mg && __fadd_rn(U, V) <= __fadd_rn(ad, mg) && T > 0.f) {
+                    const float t = __fdiv_rn(T0, det);
                     const int orig = __float_as_int(A.w);
                     if (t < h.t || (t == h.t && orig < h.orig)) {
                         h.t = t;
@@ -216,15 +235,17 @@ __device__ __forceinline__ float dot3(const float* a, float3 b) { return a[0] * 
 __device__ __forceinline__ void apply_hit(const AngleDev& A, const float4* __restrict__ tris, const Hit& h, int flags,
                                           Ray& r)
 {
-    const float3 x = make_float3(fmaf(h.t, r.d.x, r.o.x), fmaf(h.t, r.d.y, r.o.y), fmaf(h.t, r.d.z, r.o.z));
+    // hit point, unit normal and orientation in the written FP32 order
+    const float3 x = make_float3(__fmaf_rn(h.t, r.d.x, r.o.x), __fmaf_rn(h.t, r.d.y, r.o.y),
+                                 __fmaf_rn(h.t, r.d.z, r.o.z));
     tf_add(r.lacc_hi, r.lacc_lo, h.t);
     const int nb_before = r.nb;
     r.nb = nb_before + 1;
     const float4 B = __ldg(tris + 3 * (size_t)h.k + 1), C = __ldg(tris + 3 * (size_t)h.k + 2);
-    float3 n = make_float3(B.y * C.z - B.z * C.y, B.z * C.x - B.x * C.z, B.x * C.y - B.y * C.x);
-    const float il = rsqrtf(fmaxf(dot3(n, n), 1e-37f));
-    n = make_float3(n.x * il, n.y * il, n.z * il);
-    const float dn = dot3(r.d, n);
+    float3 n = cross_s(make_float3(B.x, B.y, B.z), make_float3(C.x, C.y, C.z));
+    const float rl = __fdiv_rn(1.f, __fsqrt_rn(dot_s(n, n)));
+    n = make_float3(__fmul_rn(n.x, rl), __fmul_rn(n.y, rl), __fmul_rn(n.z, rl));
+    const float dn = dot_s(r.d, n);
     const float3 nf = dn < 0.f ? n : make_float3(-n.x, -n.y, -n.z);
     const float adn = fabsf(dn);
     const float3 rh = make_float3(A.rhat[0], A.rhat[1], A.rhat[2]);
@@ -265,11 +286,13 @@ __device__ __forceinline__ void apply_hit(const AngleDev& A, const float4* __res
         r.lc_hi = 2.f * r.lacc_hi;
         r.lc_lo = 2.f * r.lacc_lo;
     }
-    // specular reflection and PEC field update
+    // PEC field update (FP32, not part of the transport order) and specular
+    // reflection + origin offset (transport order)
     const float nev = dot3(n, r.ev);
-    r.d = make_float3(fmaf(-2.f * dn, n.x, r.d.x), fmaf(-2.f * dn, n.y, r.d.y), fmaf(-2.f * dn, n.z, r.d.z));
     r.ev = make_float3(fmaf(2.f * nev, n.x, -r.ev.x), fmaf(2.f * nev, n.y, -r.ev.y), fmaf(2.f * nev, n.z, -r.ev.z));
-    r.o = make_float3(fmaf(A.eps, nf.x, x.x), fmaf(A.eps, nf.y, x.y), fmaf(A.eps, nf.z, x.z));
+    const float m2 = -2.f * dn;
+    r.d = make_float3(__fmaf_rn(m2, n.x, r.d.x), __fmaf_rn(m2, n.y, r.d.y), __fmaf_rn(m2, n.z, r.d.z));
+    r.o = make_float3(__fmaf_rn(A.eps, nf.x, x.x), __fmaf_rn(A.eps, nf.y, x.y), __fmaf_rn(A.eps, nf.z, x.z));
     r.last = h.k;
 }
 

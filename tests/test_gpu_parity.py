@@ -1,8 +1,11 @@
-"""CUDA path vs the FP64 oracle on the same seeded inputs, through the C ABI.
+"""CUDA path vs the oracle on the same seeded inputs, through the C ABI.
 
-Parity rule: triangle index and bounce count equal for every ray outside the
-1e-6 edge band (band fraction reported, below 1e-5), hit distance within 1e-5
-relative, RCS within 0.1 dB wherever the oracle is above -40 dBsm.
+Parity rule: hit decisions are taken by both sides in FP32 in one written
+operation order, so triangle index, bounce count and hit distance must agree
+bit for bit for every ray; RCS (FP64 oracle sums vs FP32/FP64 kernel sums)
+within 0.1 dB wherever the oracle is above -40 dBsm. The edge band (exact FP64
+hit within 1e-6 barycentric of an edge, or a runner-up within 1e-6 in t) is
+measured with the oracle's exact transport, reported, and must stay below 1e-5.
 """
 import math
 
@@ -82,11 +85,16 @@ def test_trihedral_hits_and_rcs_subset(G, ctx, orc):
     tot = dict(n=0, band=0)
     for a, (g, o, fr) in enumerate(res):
         s = compare_hits(*g, o)
-        assert_hit_parity(s, band_frac_max=1e-4)
-        tot["n"] += s["n"]
-        tot["band"] += s["band"]
+        assert_hit_parity(s)
         Eo, Ro = orc.po(o["coef"], o["L"], o["valid"], case["freqs"])
         assert_rcs_close(R[a, 0], Ro[0])
+        # edge band of the exact FP64 transport, and how often FP32 decides differently
+        ox = orc.trace(om, fr, 3, transport="exact")
+        tot["n"] += s["n"]
+        tot["band"] += int((ox["band"] != 0).sum())
+        tot.setdefault("fp32_vs_exact", 0)
+        tot["fp32_vs_exact"] += int((np.any(ox["hit_tri"] != o["hit_tri"], axis=1)).sum())
+    print("edge band and FP32-vs-exact decisions:", tot)
     assert tot["band"] / tot["n"] < 1e-5, tot
 
 
@@ -271,12 +279,11 @@ def test_records_match_oracle_coefficients(G, ctx, orc):
     fr = orc.make_frame(om.bbox, az, el, case["spacing"], eta=case["eta"])
     o = orc.trace(om, fr, 3, ids=r["ray"])
     o_s = orc.trace(om, fr, 3, ids=r["ray"], po_mode="scalar")
-    ok = o["band"] == 0
-    assert np.all(o["valid"][ok] == 1)
+    assert np.all(o["valid"] == 1)
     scale = 2 * case["spacing"] ** 2
-    assert np.max(np.abs(r["coef"][ok, :4] - o["coef"][ok])) < 1e-4 * scale
-    assert np.max(np.abs(r["coef"][ok, 4] - o_s["coef"][ok, 0])) < 1e-4 * scale
-    assert np.max(np.abs(r["L"][ok] - o["L"][ok])) < 2e-5
+    assert np.max(np.abs(r["coef"][:, :4] - o["coef"])) < 1e-4 * scale
+    assert np.max(np.abs(r["coef"][:, 4] - o_s["coef"][:, 0])) < 1e-4 * scale
+    assert np.max(np.abs(r["L"] - o["L"])) < 2e-6
 
 
 def test_aircraft_sampled_parity(G, ctx, orc):
@@ -289,6 +296,6 @@ def test_aircraft_sampled_parity(G, ctx, orc):
     E, R = ctx.po_integrate(case["freqs"], "HH,VV")
     for a, (g, o, fr) in enumerate(res):
         s = compare_hits(*g, o)
-        assert_hit_parity(s, band_frac_max=1e-4)
+        assert_hit_parity(s)
         Eo, Ro = orc.po(o["coef"], o["L"], o["valid"], case["freqs"])
         assert_rcs_close(R[a, 0], Ro[0, :2])

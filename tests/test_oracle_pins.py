@@ -224,12 +224,14 @@ def test_two_plate_round_trip_phase(orc):
     tri = np.concatenate([t1, t2 + len(v1)]).astype(np.int32)
     m = orc.Mesh(xyz, tri)
     dz = float(np.float32(0.0137))
-    for f in (2e9, 4.4e9, 7.1e9):
-        k = 2 * math.pi * f / C0
-        E, rcs, tr, fr = orc.rcs_angle(m, m.bbox, 0.0, 90.0, 0.01, [f], 1, window=1.2, offset=(0.25, 0.25))
-        n = tr["valid"].sum() // 2
-        S_ = 2 * 1e-4 * abs(n + n * np.exp(2j * k * dz))
-        assert abs(E[0, 0]) == pytest.approx(k / (4 * math.pi) * S_, rel=1e-6)
+    for transport, rel in (("exact", 1e-9), ("fp32", 1e-4)):
+        for f in (2e9, 4.4e9, 7.1e9):
+            k = 2 * math.pi * f / C0
+            E, rcs, tr, fr = orc.rcs_angle(m, m.bbox, 0.0, 90.0, 0.01, [f], 1, window=1.2, offset=(0.25, 0.25),
+                                           transport=transport)
+            n = tr["valid"].sum() // 2
+            S_ = 2 * 1e-4 * abs(n + n * np.exp(2j * k * dz))
+            assert abs(E[0, 0]) == pytest.approx(k / (4 * math.pi) * S_, rel=rel)
 
 
 def test_dihedral_double_bounce_peak(orc):
@@ -335,3 +337,38 @@ def test_sphere_vector_mode_converges_to_mie(orc):
         err[ds] = abs(rcs[0, 0] - mie)
     assert err[0.01] < 1.0
     assert err[0.00125] < 0.1
+
+
+# ----------------------------------------------------------------------------- FP32 vs exact transport
+@pytest.mark.parametrize("which", ["sphere", "trihedral"])
+def test_fp32_transport_tracks_exact_transport(orc, which):
+    # the FP32 transport order (the precision hit decisions are taken in) differs
+    # from exact FP64 transport only for rays grazing an edge, and not in dBsm
+    if which == "sphere":
+        case = S.sphere_case(n_random=2)
+        kw = dict(window=case["window"])
+    else:
+        case = S.trihedral_case(az_step=30.0)
+        kw = dict(eta=case["eta"])
+    m = orc.Mesh(case["xyz"], case["tri"])
+    n = mism = 0
+    for az, el in case["angles"]:
+        E32, R32, t32, _ = orc.rcs_angle(m, m.bbox, az, el, case["spacing"], case["freqs"], case["max_bounces"],
+                                         transport="fp32", **kw)
+        E64, R64, t64, _ = orc.rcs_angle(m, m.bbox, az, el, case["spacing"], case["freqs"], case["max_bounces"],
+                                         transport="exact", **kw)
+        n += len(t32["nb"])
+        diff = np.any(t32["hit_tri"] != t64["hit_tri"], axis=1)
+        mism += int(diff.sum())
+        # every ray decided differently grazes an edge within the FP32 test's slack
+        # (2^-12; on the FP32 side the barycentric may be slightly negative) or has a
+        # runner-up at nearly the same distance
+        near = np.minimum(np.abs(t32["bmin"][diff]), np.abs(t64["bmin"][diff])) < 2 * 2.0**-12
+        assert np.all(near | (t64["band"][diff] & 2 != 0)), np.abs(t32["bmin"][diff]).max()
+        ok = R64[0, :2] > -40
+        assert np.all(np.abs(R32[0, :2] - R64[0, :2])[ok] < 0.02)
+        both = (t32["hit_tri"] >= 0) & (t32["hit_tri"] == t64["hit_tri"])
+        # FP32 positions carry ~1e-7 m absolute error (short legs near corners make it large relative)
+        dt = np.abs(t32["hit_t"][both] - t64["hit_t"][both])
+        assert np.all(dt < 1e-5 * t64["hit_t"][both] + 1e-6)
+    assert mism / n < 2e-3, (mism, n)
