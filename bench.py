@@ -147,7 +147,8 @@ def workload(name: str) -> dict:
 def wl_config(case: dict, name: str) -> dict:
     return {"workload": case["name"], "mesh_triangles": int(len(case["tri"])), "aspects": int(len(case["angles"])),
             "freq_ghz": [float(f) / 1e9 for f in case["freqs"]], "ray_spacing_m": float(case["spacing"]),
-            "max_bounces": int(case["max_bounces"]), "po": "vector", "pols": "HH,VV",
+            "max_bounces": int(case["max_bounces"]), "grid_offset": list(case.get("offset", (0.0, 0.0))),
+            "po": "vector", "pols": "HH,VV",
             "l2": "flushed between timed steps (512 MB write)"}
 
 
@@ -161,7 +162,8 @@ def oracle_sample(case, n_angles: int, threads: int):
     bounces = 0
     for a in idx:
         az, el = case["angles"][a]
-        fr = oracle.make_frame(om.bbox, az, el, case["spacing"], eta=case["eta"], window=case.get("window", 0.0))
+        fr = oracle.make_frame(om.bbox, az, el, case["spacing"], eta=case["eta"], window=case.get("window", 0.0),
+                               offset=case.get("offset", (0.0, 0.0)))
         tr = oracle.trace(om, fr, case["max_bounces"], threads=threads)
         oracle.po(tr["coef"], tr["L"], tr["valid"], case["freqs"])
         nb = tr["nb"]
@@ -209,7 +211,7 @@ def run_sbr(args, case, ws, rank, local, pg):
     ang = np.ascontiguousarray(case["angles"], np.float64)
     freqs = np.ascontiguousarray(case["freqs"], np.float64)
     B = case["max_bounces"]
-    kw = dict(eta=case["eta"], max_bounces=B, window=case.get("window", 0.0))
+    kw = dict(eta=case["eta"], max_bounces=B, window=case.get("window", 0.0), offset=case.get("offset", (0.0, 0.0)))
     na, nf, npol = len(ang), len(freqs), 2
     E_dev = torch.empty((na, nf, npol, 2), dtype=torch.float64, device=f"cuda:{local}")
     R_dev = torch.empty((na, nf, npol), dtype=torch.float64, device=f"cuda:{local}")
@@ -317,10 +319,17 @@ def main():
     ap.add_argument("--workload", default="trihedral",
                     choices=["trihedral", "sphere", "aircraft1", "aircraft3", "aircraft10"])
     ap.add_argument("--ref-angles", type=int, default=24)
+    ap.add_argument("--aspects", type=int, default=0,
+                    help="use this many evenly spaced aspects of the sweep (small profiling cases); 0 = all")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     ws, rank, local, pg = dist_setup()
     case = workload(args.workload)
+    if args.aspects > 0:
+        idx = np.linspace(0, len(case["angles"]) - 1, args.aspects).round().astype(int)
+        case["angles"] = case["angles"][idx]
+        case["name"] += f"_{args.aspects}aspects"
+        args.ref_angles = min(args.ref_angles, args.aspects)
     if args.impl == "reference":
         run_reference(args, case, ws, rank, pg)
     else:

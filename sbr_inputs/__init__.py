@@ -7,6 +7,6 @@ consume it without sharing any of the method's code.
 """
 from .meshes import icosphere, trihedral, square_plate, dihedral, aircraft, mesh_bbox  # noqa: F401
 from .workloads import (  # noqa: F401
-    C0, spacing_for, sphere_case, trihedral_case, aircraft_case, batched_requests,
+    C0, spacing_for, grid_offset, sphere_case, trihedral_case, aircraft_case, batched_requests,
     surrogate_samples,
 )

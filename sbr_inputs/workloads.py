@@ -20,6 +20,14 @@ def spacing_for(freq_hz: float, rays_per_lambda: float) -> float:
     return C0 / (freq_hz * rays_per_lambda)
 
 
+def grid_offset(seed: int) -> tuple:
+    """Seeded sub-cell shift (du, dv) of the aperture grid, in units of the ray
+    spacing, drawn U[0, 1)^2. It keeps a regular grid from lining up with the
+    edges of a regular mesh (whole rows of rays on edges otherwise)."""
+    rng = np.random.default_rng(seed)
+    return tuple(float(x) for x in rng.uniform(0.0, 1.0, 2))
+
+
 def _random_aspects(n: int, seed: int) -> np.ndarray:
     """``n`` aspects uniform over the unit sphere, as (az, el) degrees."""
     rng = np.random.default_rng(seed)
@@ -36,18 +44,21 @@ def sphere_case(n_random: int = 64, seed: int = 11) -> dict:
     xyz, tri = meshes.icosphere(5, 1.0)
     ang = np.concatenate([[[0.0, 0.0]], _random_aspects(n_random, seed)])
     return dict(name="sphere_r1m_ico5_3GHz", xyz=xyz, tri=tri, freqs=np.array([3.0e9]),
-                angles=ang, spacing=0.01, eta=0.0, window=2.2, max_bounces=1, radius=1.0)
+                angles=ang, spacing=0.01, eta=0.0, window=2.2, max_bounces=1, radius=1.0, offset=(0.0, 0.0))
 
 
 def trihedral_case(az_step: float = 0.5, el: float = 35.26) -> dict:
     """Triangular trihedral (1 m legs, 3 x 1024 triangles), 10 GHz, spacing
     lambda/10, aperture margin 0.05, up to 3 bounces, azimuth 0..90 deg in
-    ``az_step`` steps at elevation ``el`` (181 angles for 0.5 deg)."""
+    ``az_step`` steps at elevation ``el`` (181 angles for 0.5 deg); grid offset
+    from seed 5 (the axis-aligned plates would otherwise put whole rows of rays
+    on edges at 0 and 90 deg)."""
     xyz, tri = meshes.trihedral(1.0, 32)
     az = np.arange(0.0, 90.0 + 1e-9, az_step)
     ang = np.stack([az, np.full_like(az, el)], axis=1)
     return dict(name="trihedral_1m_10GHz_sweep", xyz=xyz, tri=tri, freqs=np.array([10.0e9]),
-                angles=ang, spacing=spacing_for(10.0e9, 10.0), eta=0.05, window=0.0, max_bounces=3)
+                angles=ang, spacing=spacing_for(10.0e9, 10.0), eta=0.05, window=0.0, max_bounces=3,
+                offset=grid_offset(5))
 
 
 def aircraft_case(freq_hz: float = 1.0e9, n_az: int = 360, target_tris: int = 1_000_000,
@@ -58,7 +69,8 @@ def aircraft_case(freq_hz: float = 1.0e9, n_az: int = 360, target_tris: int = 1_
     az = np.arange(n_az) * (360.0 / n_az)
     ang = np.stack([az, np.zeros_like(az)], axis=1)
     return dict(name=f"aircraft_{freq_hz / 1e9:g}GHz", xyz=xyz, tri=tri, freqs=np.array([freq_hz]),
-                angles=ang, spacing=spacing_for(freq_hz, 10.0), eta=0.05, window=0.0, max_bounces=10)
+                angles=ang, spacing=spacing_for(freq_hz, 10.0), eta=0.05, window=0.0, max_bounces=10,
+                offset=grid_offset(6))
 
 
 def batched_requests(n: int = 4096, seed: int = 2, n_meshes: int = 3) -> list:

@@ -80,7 +80,7 @@ def test_trihedral_hits_and_rcs_subset(G, ctx, orc):
     ctx.load_mesh(case["xyz"], case["tri"])
     om = orc.Mesh(case["xyz"], case["tri"])
     ang = case["angles"][[0, 1, 37, 60, 90, 91, 133, 179, 180]]
-    st, res = _trace_both(G, ctx, orc, om, ang, case["spacing"], 3)
+    st, res = _trace_both(G, ctx, orc, om, ang, case["spacing"], 3, eta=case["eta"], offset=case["offset"])
     E, R = ctx.po_integrate(case["freqs"], "HH,VV,HV,VH")
     tot = dict(n=0, band=0)
     for a, (g, o, fr) in enumerate(res):
@@ -103,11 +103,12 @@ def test_trihedral_full_sweep_rcs(G, ctx, orc):
     case = S.trihedral_case()
     ctx.load_mesh(case["xyz"], case["tri"])
     om = orc.Mesh(case["xyz"], case["tri"])
-    st = ctx.trace(case["angles"], case["spacing"], eta=case["eta"], max_bounces=3)
+    st = ctx.trace(case["angles"], case["spacing"], eta=case["eta"], max_bounces=3, offset=case["offset"])
     E, R = ctx.po_integrate(case["freqs"], "HH,VV")
     worst = 0.0
     for a, (az, el) in enumerate(case["angles"]):
-        _, Ro, _, _ = orc.rcs_angle(om, om.bbox, az, el, case["spacing"], case["freqs"], 3, eta=case["eta"])
+        _, Ro, _, _ = orc.rcs_angle(om, om.bbox, az, el, case["spacing"], case["freqs"], 3, eta=case["eta"],
+                                    offset=case["offset"])
         worst = max(worst, assert_rcs_close(R[a, 0], Ro[0, :2]))
     assert st["ray_bounces"] > st["rays_launched"]
     print("worst dB error over the sweep:", worst)
@@ -118,11 +119,11 @@ def test_full_size_sampled_rays(G, ctx, orc):
     case = S.trihedral_case()
     ctx.load_mesh(case["xyz"], case["tri"])
     om = orc.Mesh(case["xyz"], case["tri"])
-    ctx.trace(case["angles"], case["spacing"], eta=case["eta"], max_bounces=3, flags=HITS)
+    ctx.trace(case["angles"], case["spacing"], eta=case["eta"], max_bounces=3, flags=HITS, offset=case["offset"])
     rng = np.random.default_rng(9)
     for a in (0, 45, 90, 120, 180):
         az, el = case["angles"][a]
-        fr = orc.make_frame(om.bbox, az, el, case["spacing"], eta=case["eta"])
+        fr = orc.make_frame(om.bbox, az, el, case["spacing"], eta=case["eta"], offset=case["offset"])
         ids = rng.choice(fr.n_rays, 4000, replace=False)
         o = orc.trace(om, fr, 3, ids=ids)
         s = compare_hits(*ctx.get_hits(a), o, ids=ids)
@@ -236,13 +237,14 @@ def test_multifrequency_and_phase_precision(G, ctx, orc):
     om = orc.Mesh(case["xyz"], case["tri"])
     ang = case["angles"][[30, 90]]
     freqs = np.linspace(8e9, 12e9, 17)
-    ctx.trace(ang, case["spacing"], max_bounces=3)
+    ctx.trace(ang, case["spacing"], max_bounces=3, offset=case["offset"])
     errs = {}
     for ph in ("compensated", "fp64", "fp32"):
         E, R = ctx.po_integrate(freqs, "HH,VV", phase=ph)
         e = 0.0
         for a, (az, el) in enumerate(ang):
-            _, Ro, _, _ = orc.rcs_angle(om, om.bbox, az, el, case["spacing"], freqs, 3, eta=case["eta"])
+            _, Ro, _, _ = orc.rcs_angle(om, om.bbox, az, el, case["spacing"], freqs, 3, eta=case["eta"],
+                                        offset=case["offset"])
             e = max(e, assert_rcs_close(R[a], Ro[:, :2], tol=0.5))
         errs[ph] = e
     assert errs["compensated"] <= 0.1 and errs["fp64"] <= 0.1
@@ -274,9 +276,9 @@ def test_records_match_oracle_coefficients(G, ctx, orc):
     ctx.load_mesh(case["xyz"], case["tri"])
     om = orc.Mesh(case["xyz"], case["tri"])
     az, el = case["angles"][70]
-    ctx.trace([[az, el]], case["spacing"], max_bounces=3)
+    ctx.trace([[az, el]], case["spacing"], max_bounces=3, offset=case["offset"])
     r = ctx.get_records(0)
-    fr = orc.make_frame(om.bbox, az, el, case["spacing"], eta=case["eta"])
+    fr = orc.make_frame(om.bbox, az, el, case["spacing"], eta=case["eta"], offset=case["offset"])
     o = orc.trace(om, fr, 3, ids=r["ray"])
     o_s = orc.trace(om, fr, 3, ids=r["ray"], po_mode="scalar")
     assert np.all(o["valid"] == 1)
@@ -292,7 +294,7 @@ def test_aircraft_sampled_parity(G, ctx, orc):
     ctx.load_mesh(case["xyz"], case["tri"])
     om = orc.Mesh(case["xyz"], case["tri"])
     ang = case["angles"][[0, 30]]
-    st, res = _trace_both(G, ctx, orc, om, ang, case["spacing"], 10)
+    st, res = _trace_both(G, ctx, orc, om, ang, case["spacing"], 10, eta=case["eta"], offset=case["offset"])
     E, R = ctx.po_integrate(case["freqs"], "HH,VV")
     for a, (g, o, fr) in enumerate(res):
         s = compare_hits(*g, o)
