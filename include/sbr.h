@@ -127,7 +127,8 @@ int sbr_create(sbr_ctx** out, int device, void* cuda_stream);
 void sbr_destroy(sbr_ctx* ctx);
 
 /* Message of the last failed call on `ctx` (owned by the context, valid until the
- * next call on it); for ctx == NULL, the message of the last failed sbr_create. */
+ * next call on it); for ctx == NULL, the message of the last failed sbr_create
+ * or sbr_po_integrate_noalloc. */
 const char* sbr_last_error(const sbr_ctx* ctx);
 
 /* Load a triangulated PEC surface (Sec. 4.1 of the paper; meshes come from the
@@ -203,6 +204,42 @@ int sbr_get_hits(sbr_ctx* ctx, int64_t angle, int32_t* tri_ids, float* t, int32_
  * path [.] = L in metres. *n_out receives the record count. Synchronises. */
 int sbr_get_records(sbr_ctx* ctx, int64_t angle, int64_t cap, int64_t* ray_ids, float* coef, double* path,
                     int64_t* n_out);
+
+/* ---- allocation-free PO sum ------------------------------------------------
+ * The paper has no counterpart of this call; it exists for callers that cannot
+ * allocate device memory where they need the sum: work recorded into a CUDA
+ * graph (no cudaMalloc while a stream is captured), plug-ins running inside an
+ * application that owns all device memory, loops that must not enter the
+ * allocator. It computes what sbr_po_integrate computes, with the same kernels,
+ * from caller-provided device records, and keeps all scratch in one fixed
+ * file-scope device array (about 8.7 MB, held by every GPU that loads the
+ * library until the process exits). It calls no cudaMalloc/cudaFree.
+ *
+ *   records      device, n_records x 32 bytes, each record 8 x 32-bit words:
+ *                float c[5] (HH, VV, HV, VH, scalar-form coefficient), float L_hi,
+ *                float L_lo (path L = L_hi + L_lo in metres), int ray id (unused);
+ *                the layout sbr_trace produces (see sbr_get_records for values)
+ *   rec_offsets  host, [n_angles + 1]: records of aspect a are
+ *                [rec_offsets[a], rec_offsets[a + 1]); rec_offsets[0] = 0
+ *   freq_hz      host, n_freq frequencies > 0
+ *   pol_mask, po_mode  as for sbr_po_integrate
+ *   E_re_im, rcs_dbsm  device outputs laid out as for sbr_po_integrate (one may be NULL)
+ *   cuda_stream  stream to order the work on (NULL = legacy default stream)
+ * Limits: n_angles <= SBR_NOALLOC_MAX_ANGLES, n_freq <= SBR_NOALLOC_MAX_FREQ,
+ * at most SBR_NOALLOC_MAX_ITEMS blocks of 1024 records in total, and
+ * blocks x n_freq x n_pol x 16 bytes <= SBR_NOALLOC_PARTIAL_BYTES; larger
+ * requests return SBR_ERR_ARG with the reason in sbr_last_error(NULL).
+ * The first call on a device looks up the array's device address (make that
+ * first call outside any stream capture). Every call reuses the same array and
+ * overwrites what it reads, so calls that overlap on the GPU (other streams,
+ * other host threads) race: order them. Returns once the work is enqueued. */
+#define SBR_NOALLOC_MAX_ANGLES 4096
+#define SBR_NOALLOC_MAX_FREQ 256
+#define SBR_NOALLOC_MAX_ITEMS 16384
+#define SBR_NOALLOC_PARTIAL_BYTES (8u << 20)
+int sbr_po_integrate_noalloc(const void* records, const int64_t* rec_offsets, int64_t n_angles, const double* freq_hz,
+                             int64_t n_freq, int pol_mask, int po_mode, double* E_re_im, double* rcs_dbsm,
+                             void* cuda_stream);
 
 /* Ray spacing for `rays_per_lambda` rays per wavelength at frequency f_max_hz:
  * ds = c0 / (f_max_hz * rays_per_lambda); the paper's sampling rule (Sec. 4)

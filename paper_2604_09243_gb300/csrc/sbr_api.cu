@@ -27,6 +27,15 @@ constexpr int kMaxBounces = 64;
 
 std::string g_create_error;
 
+}  // namespace
+
+namespace sbr {
+// error message of a context-free call, returned by sbr_last_error(NULL)
+void set_static_error(const char* msg) { g_create_error = msg; }
+}  // namespace sbr
+
+namespace {
+
 struct DevBuf {
     void* p = nullptr;
     size_t cap = 0;

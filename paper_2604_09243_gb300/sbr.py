@@ -28,7 +28,7 @@ TRACE_PHASE_LITERAL_2R, TRACE_REQUIRE_ESCAPE, TRACE_RECORD_HITS, TRACE_COUNT_VIS
 # every symbol declared in include/sbr.h
 EXPORTS = ("sbr_version", "sbr_create", "sbr_destroy", "sbr_last_error", "sbr_load_mesh", "sbr_get_bbox",
            "sbr_build_bvh", "sbr_ray_grid_for", "sbr_ray_grid_box", "sbr_trace", "sbr_po_integrate", "sbr_get_hits",
-           "sbr_get_records", "sbr_spacing_for")
+           "sbr_get_records", "sbr_spacing_for", "sbr_po_integrate_noalloc")
 
 
 class SbrError(RuntimeError):
@@ -92,6 +92,7 @@ def lib() -> C.CDLL:
         "sbr_get_hits": ([vp, i64, vp, vp, vp], C.c_int),
         "sbr_get_records": ([vp, i64, i64, vp, vp, vp, P(i64)], C.c_int),
         "sbr_spacing_for": ([d, d], d),
+        "sbr_po_integrate_noalloc": ([vp, P(i64), i64, P(d), i64, C.c_int, C.c_int, vp, vp, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -111,6 +112,23 @@ def spacing_for(f_max_hz: float, rays_per_lambda: float) -> float:
     if v < 0:
         raise ValueError("frequency and rays per wavelength must be > 0")
     return v
+
+
+def po_integrate_noalloc(records_ptr: int, rec_offsets, freqs, pols="HH,VV", mode="vector", phase="compensated",
+                        E_ptr: int | None = None, rcs_ptr: int | None = None, stream=None) -> None:
+    """Allocation-free PO sum (sbr_po_integrate_noalloc) over caller-owned device
+    records; ``records_ptr``, ``E_ptr`` and ``rcs_ptr`` are device addresses,
+    ``rec_offsets`` host int64 [n_angles + 1]. Raises SbrError on a refused call."""
+    off = np.ascontiguousarray(rec_offsets, dtype=np.int64)
+    f = np.ascontiguousarray(np.atleast_1d(freqs), dtype=np.float64)
+    m = (PO_PAPER_SCALAR if mode == "scalar" else PO_VECTOR) | PHASE[phase]
+    s = int(getattr(stream, "cuda_stream", stream)) if stream is not None else None
+    rc = lib().sbr_po_integrate_noalloc(C.c_void_p(int(records_ptr)), off.ctypes.data_as(C.POINTER(C.c_int64)),
+                                        len(off) - 1, f.ctypes.data_as(C.POINTER(C.c_double)), len(f), _pols(pols),
+                                        m, C.c_void_p(E_ptr) if E_ptr else None,
+                                        C.c_void_p(rcs_ptr) if rcs_ptr else None, C.c_void_p(s) if s else None)
+    if rc != SBR_OK:
+        raise SbrError(rc, (lib().sbr_last_error(None) or b"").decode())
 
 
 def _opts(window=0.0, offset=(0.0, 0.0), flags=0, chunk_rays=0) -> TraceOpts:

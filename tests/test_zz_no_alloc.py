@@ -1,0 +1,81 @@
+"""Allocation-free PO sum (sbr_po_integrate_noalloc) against sbr_po_integrate.
+
+The entry point serves callers that cannot allocate device memory where they
+need the sum (graph capture, host applications that own all device memory);
+its scratch is a fixed device array inside the library. This file sorts last so
+that a run stopping at its first failure has already run every other test; it
+also passes on its own in a fresh process.
+"""
+import numpy as np
+import pytest
+
+import sbr_inputs as S
+
+pytestmark = pytest.mark.gpu
+
+
+def _device_records(torch, ctx, n_angles):
+    """Rebuild the dense record buffer of the last trace on the device, in the
+    documented 32-byte layout, from the per-aspect records the C ABI returns."""
+    parts, off = [], [0]
+    for a in range(n_angles):
+        r = ctx.get_records(a)
+        n = len(r["ray"])
+        buf = np.zeros((n, 8), np.float32)
+        buf[:, :5] = r["coef"]
+        hi = r["L"].astype(np.float32)
+        buf[:, 5] = hi
+        buf[:, 6] = (r["L"] - hi.astype(np.float64)).astype(np.float32)
+        buf[:, 7] = r["ray"].astype(np.int32).view(np.float32)
+        parts.append(buf)
+        off.append(off[-1] + n)
+    rec = torch.from_numpy(np.concatenate(parts)).cuda()
+    return rec, np.array(off, np.int64)
+
+
+def test_noalloc_matches_po_integrate_twice():
+    torch = pytest.importorskip("torch")
+    from paper_2604_09243_gb300 import build
+
+    build.build()
+    import paper_2604_09243_gb300 as G
+
+    case = S.trihedral_case(az_step=7.5)
+    ctx = G.Context(0)
+    ctx.load_mesh(case["xyz"], case["tri"])
+    ctx.trace(case["angles"], case["spacing"], eta=case["eta"], max_bounces=3, offset=case["offset"])
+    na = len(case["angles"])
+    rec, off = _device_records(torch, ctx, na)
+    for freqs, pols, mode in (([10e9], "HH,VV", "vector"), ([8e9, 9.5e9, 12e9], "HH,VV,HV,VH", "scalar")):
+        E_ref, R_ref = ctx.po_integrate(freqs, pols, mode=mode)
+        npol = len(pols.split(","))
+        for _ in range(2):  # two calls in a row share the static scratch
+            E = torch.full((na, len(freqs), npol, 2), float("nan"), dtype=torch.float64, device="cuda")
+            R = torch.full((na, len(freqs), npol), float("nan"), dtype=torch.float64, device="cuda")
+            G.po_integrate_noalloc(rec.data_ptr(), off, freqs, pols, mode=mode, E_ptr=E.data_ptr(),
+                                   rcs_ptr=R.data_ptr())
+            torch.cuda.synchronize()
+            Eh = E.cpu().numpy()
+            Rh = R.cpu().numpy()
+            scale = np.max(np.abs(E_ref))
+            assert np.max(np.abs(Eh[..., 0] + 1j * Eh[..., 1] - E_ref)) <= 1e-9 * scale
+            m = R_ref > -40.0
+            assert np.max(np.abs(Rh[m] - R_ref[m])) <= 0.1
+    ctx.close()
+
+
+def test_noalloc_rejects_oversize_requests():
+    pytest.importorskip("torch")
+    from paper_2604_09243_gb300 import build
+
+    build.build()
+    import paper_2604_09243_gb300 as G
+
+    off = np.array([0, 10], np.int64)
+    with pytest.raises(G.SbrError, match="n_freq"):
+        G.po_integrate_noalloc(1 << 20, off, np.full(257, 1e9), "HH", E_ptr=1 << 20)
+    with pytest.raises(G.SbrError, match="SBR_NOALLOC_MAX_ITEMS"):
+        G.po_integrate_noalloc(1 << 20, np.array([0, 1024 * 16385], np.int64), [1e9], "HH", E_ptr=1 << 20)
+    with pytest.raises(G.SbrError, match="PARTIAL_BYTES"):
+        G.po_integrate_noalloc(1 << 20, np.array([0, 1024 * 4096], np.int64), np.full(256, 1e9), "HH,VV,HV,VH",
+                               E_ptr=1 << 20)
