@@ -12,7 +12,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/sbr.h"
+#include "sbr.h"
 #include "sbr_internal.h"
 
 using namespace sbr;
@@ -223,11 +223,13 @@ AngleDev to_dev(const sbr_ray_grid& g, long long ray_off)
     d.eps = (float)g.eps;
     d.nu = (int)g.nu;
     d.nv = (int)g.nv;
+    d.nbu = (int)((g.nu + 7) / 8);
     d.ray_off = ray_off;
     return d;
 }
 
-long long pad32(long long n) { return (n + 31) & ~31ll; }
+// rays an aspect occupies in the processing layout: whole 8 x 4 tiles
+long long tiled_rays(const sbr_ray_grid& g) { return ((g.nu + 7) / 8) * ((g.nv + 3) / 4) * 32; }
 
 }  // namespace
 
@@ -430,11 +432,11 @@ int sbr_trace(sbr_ctx* c, const double* az_el, int64_t n_angles, double ds, doub
         AngleHost& h = c->ang[(size_t)a];
         make_grid(c->bbox, az_el[2 * a], az_el[2 * a + 1], ds, eta, opt, &h.grid);
         const long long nr = h.grid.nu * h.grid.nv;
-        if (h.grid.nu > (1ll << 30) || h.grid.nv > (1ll << 30) || pad32(nr) > chunk_cap)
+        if (h.grid.nu > (1ll << 30) || h.grid.nv > (1ll << 30) || tiled_rays(h.grid) > chunk_cap)
             return fail(c, SBR_ERR_ARG, "sbr_trace: ray grid of angle %lld too large (%lld x %lld)", (long long)a,
                         (long long)h.grid.nu, (long long)h.grid.nv);
         h.ray_begin = total;
-        total += pad32(nr);
+        total += tiled_rays(h.grid);
         launched += nr;
     }
     // chunks of consecutive angles
@@ -442,7 +444,7 @@ int sbr_trace(sbr_ctx* c, const double* az_el, int64_t n_angles, double ds, doub
     {
         long long acc = 0;
         for (int64_t a = 0; a < n_angles; ++a) {
-            long long r = pad32(c->ang[(size_t)a].grid.nu * c->ang[(size_t)a].grid.nv);
+            long long r = tiled_rays(c->ang[(size_t)a].grid);
             if (acc > 0 && acc + r > chunk_cap) {
                 cut.push_back(a);
                 acc = 0;
@@ -454,8 +456,7 @@ int sbr_trace(sbr_ctx* c, const double* az_el, int64_t n_angles, double ds, doub
     long long max_chunk = 0;
     int max_chunk_angles = 0;
     for (size_t k = 0; k + 1 < cut.size(); ++k) {
-        long long r = c->ang[(size_t)cut[k + 1] - 1].ray_begin + pad32(c->ang[(size_t)cut[k + 1] - 1].grid.nu *
-                                                                         c->ang[(size_t)cut[k + 1] - 1].grid.nv) -
+        long long r = c->ang[(size_t)cut[k + 1] - 1].ray_begin + tiled_rays(c->ang[(size_t)cut[k + 1] - 1].grid) -
                       c->ang[(size_t)cut[k]].ray_begin;
         max_chunk = std::max(max_chunk, r);
         max_chunk_angles = std::max(max_chunk_angles, (int)(cut[k + 1] - cut[k]));
@@ -516,7 +517,7 @@ int sbr_trace(sbr_ctx* c, const double* az_el, int64_t n_angles, double ds, doub
         const int na = (int)(a1 - a0);
         const long long base = c->ang[(size_t)a0].ray_begin;
         const long long chunk_rays = c->ang[(size_t)a1 - 1].ray_begin +
-                                     pad32(c->ang[(size_t)a1 - 1].grid.nu * c->ang[(size_t)a1 - 1].grid.nv) - base;
+                                     tiled_rays(c->ang[(size_t)a1 - 1].grid) - base;
         // stage angle table and ray offsets
         size_t bytes_a = sizeof(AngleDev) * (size_t)na, bytes_o = sizeof(long long) * (size_t)(na + 1);
         char* hs = (char*)stage(c, bytes_a + bytes_o + sizeof(unsigned) * (size_t)(na + 1));
@@ -745,20 +746,32 @@ int sbr_get_hits(sbr_ctx* c, int64_t angle, int32_t* tri_ids, float* t, int32_t*
     if (angle < 0 || angle >= (int64_t)c->ang.size()) return fail(c, SBR_ERR_ARG, "sbr_get_hits: angle out of range");
     CK(cudaSetDevice(c->device), "cudaSetDevice");
     const AngleHost& h = c->ang[(size_t)angle];
-    const size_t nr = (size_t)(h.grid.nu * h.grid.nv), B = (size_t)c->max_bounces;
-    if (tri_ids)
-        CK(cudaMemcpyAsync(tri_ids, c->hit_tri.as<int>() + (size_t)h.ray_begin * B, sizeof(int) * nr * B,
-                           cudaMemcpyDeviceToHost, c->stream),
-           "copy hits");
-    if (t)
-        CK(cudaMemcpyAsync(t, c->hit_t.as<float>() + (size_t)h.ray_begin * B, sizeof(float) * nr * B,
-                           cudaMemcpyDeviceToHost, c->stream),
-           "copy hits");
-    if (n_bounce)
-        CK(cudaMemcpyAsync(n_bounce, c->hit_nb.as<int>() + h.ray_begin, sizeof(int) * nr, cudaMemcpyDeviceToHost,
-                           c->stream),
-           "copy hits");
+    const size_t np = (size_t)tiled_rays(h.grid), B = (size_t)c->max_bounces;
+    std::vector<int> ht(np * B), hn(np);
+    std::vector<float> htt(np * B);
+    CK(cudaMemcpyAsync(ht.data(), c->hit_tri.as<int>() + (size_t)h.ray_begin * B, sizeof(int) * np * B,
+                       cudaMemcpyDeviceToHost, c->stream),
+       "copy hits");
+    CK(cudaMemcpyAsync(htt.data(), c->hit_t.as<float>() + (size_t)h.ray_begin * B, sizeof(float) * np * B,
+                       cudaMemcpyDeviceToHost, c->stream),
+       "copy hits");
+    CK(cudaMemcpyAsync(hn.data(), c->hit_nb.as<int>() + h.ray_begin, sizeof(int) * np, cudaMemcpyDeviceToHost,
+                       c->stream),
+       "copy hits");
     CK(cudaStreamSynchronize(c->stream), "hits sync");
+    // processing layout (8 x 4 tiles) -> ray id j * nu + i
+    const long long nbu = (h.grid.nu + 7) / 8;
+    for (size_t p = 0; p < np; ++p) {
+        const long long blk = (long long)(p >> 5), l = (long long)(p & 31);
+        const long long i = (blk % nbu) * 8 + (l & 7), j = (blk / nbu) * 4 + (l >> 3);
+        if (i >= h.grid.nu || j >= h.grid.nv) continue;
+        const size_t id = (size_t)(j * h.grid.nu + i);
+        for (size_t b = 0; b < B; ++b) {
+            if (tri_ids) tri_ids[id * B + b] = ht[p * B + b];
+            if (t) t[id * B + b] = htt[p * B + b];
+        }
+        if (n_bounce) n_bounce[id] = hn[p];
+    }
     return SBR_OK;
 }
 

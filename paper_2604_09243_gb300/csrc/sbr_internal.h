@@ -38,7 +38,8 @@ struct AngleDev {            // 128 bytes
     float dA, eps;                      // tube area ds^2, origin offset after a hit
     int nu, nv;
     long long ray_off;                  // first ray of this aspect in the chunk, multiple of 32
-    int pad[4];
+    int nbu;                            // 8 x 4 ray tiles per aperture row: ceil(nu / 8)
+    int pad[3];
 };
 static_assert(sizeof(AngleDev) == 128, "AngleDev layout");
 
@@ -49,7 +50,7 @@ struct __align__(16) RayState {
     float evz, lacc_hi, lacc_lo, cos0;  // E of the V transmit case; path so far (two-float)
     float c0, c1, c2, c3;               // candidate tube coefficients HH, VV, HV, VH at the last hit
     float cs, lc_hi, lc_lo, pad;        // candidate scalar coefficient, candidate path L (two-float)
-    int angle, local, last, nb;         // aspect (chunk-local), ray id j*nu+i, last sorted triangle, bounces
+    int angle, local, last, nb;         // aspect (chunk-local), processing index (8x4 tiles), last sorted triangle, bounces
 };
 static_assert(sizeof(RayState) == 96, "RayState layout");
 

@@ -20,7 +20,7 @@
 
 #include <mutex>
 
-#include "../../include/sbr.h"
+#include "sbr.h"
 #include "sbr_internal.h"
 
 namespace sbr {

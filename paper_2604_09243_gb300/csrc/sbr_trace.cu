@@ -301,19 +301,34 @@ __device__ __forceinline__ long long ray_global(const TraceArgs& a, const Ray& r
     return a.ray_off[r.angle] + r.local;
 }
 
+// Rays are processed in 8 x 4 tiles: processing index p of an aspect maps to
+// grid point (i, j) = (8 bu + p % 8, 4 bv + (p % 32) / 8), tile p / 32 = bv * nbu + bu,
+// so the 32 lanes of a warp trace a compact 8 x 4 patch of the aperture.
+__device__ __forceinline__ void tile_ij(const AngleDev& A, int p, int& i, int& j)
+{
+    const int blk = p >> 5, l = p & 31;
+    const int bv = blk / A.nbu, bu = blk - bv * A.nbu;
+    i = bu * 8 + (l & 7);
+    j = bv * 4 + (l >> 3);
+}
+
 __device__ __forceinline__ void emit(const TraceArgs& a, const Ray& r, bool zero)
 {
     const long long g = ray_global(a, r);
+    int i, j;
+    const AngleDev& A = a.angles[r.angle];
+    tile_ij(A, r.local, i, j);
+    const int ray_id = j * A.nu + i;
     const long long tile = g >> 5;
     const unsigned bit = (unsigned)(g & 31);
     const unsigned slot = a.tile_base[tile] + __popc(a.mask[tile] & ((1u << bit) - 1u));
     float4* p = reinterpret_cast<float4*>(a.rec + slot);
     if (zero) {
         p[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-        p[1] = make_float4(0.f, 0.f, 0.f, __int_as_float(r.local));
+        p[1] = make_float4(0.f, 0.f, 0.f, __int_as_float(ray_id));
     } else {
         p[0] = make_float4(r.c[0], r.c[1], r.c[2], r.c[3]);
-        p[1] = make_float4(r.c[4], r.lc_hi, r.lc_lo, __int_as_float(r.local));
+        p[1] = make_float4(r.c[4], r.lc_hi, r.lc_lo, __int_as_float(ray_id));
     }
     if (a.hit_nb) a.hit_nb[g] = r.nb;
 }
@@ -373,7 +388,7 @@ __device__ __forceinline__ void flush_stats(const TraceArgs& a, unsigned q, unsi
 
 // ---------------------------------------------------------------- pass 0: primary rays
 template <bool kCount>
-__global__ void __launch_bounds__(kTraceThreads) k_primary(const TraceArgs a)
+__global__ void __launch_bounds__(kTraceThreads, 4) k_primary(const TraceArgs a)
 {
     const int lane = threadIdx.x & 31;
     unsigned nq = 0, nvis = 0, ntri = 0;
@@ -387,14 +402,15 @@ __global__ void __launch_bounds__(kTraceThreads) k_primary(const TraceArgs a)
         if (lane == 0) ang = find_angle(a.ray_off, a.n_angles, (long long)base);
         ang = __shfl_sync(kFull, ang, 0);
         const AngleDev& A = a.angles[ang];
-        const long long local = (long long)base + lane - a.ray_off[ang];
-        const bool active = local < (long long)A.nu * A.nv;
+        const int local = (int)((long long)base + lane - a.ray_off[ang]);
+        int i, j;
+        tile_ij(A, local, i, j);
+        const bool active = i < A.nu && j < A.nv;
         bool hit = false;
         Ray r;
         r.angle = ang;
-        r.local = (int)local;
+        r.local = local;
         if (active) {
-            const int i = (int)(local % A.nu), j = (int)(local / A.nu);
             const float fi = (float)i, fj = (float)j;
             r.o = make_float3(__fadd_rn(__fadd_rn(A.p0[0], __fmul_rn(fi, A.du[0])), __fmul_rn(fj, A.dv[0])),
                               __fadd_rn(__fadd_rn(A.p0[1], __fmul_rn(fi, A.du[1])), __fmul_rn(fj, A.dv[1])),
@@ -423,7 +439,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_primary(const TraceArgs a)
 
 // ---------------------------------------------------------------- pass b >= 1: live rays
 template <bool kCount>
-__global__ void __launch_bounds__(kTraceThreads) k_bounce(const TraceArgs a)
+__global__ void __launch_bounds__(kTraceThreads, 4) k_bounce(const TraceArgs a)
 {
     const int lane = threadIdx.x & 31;
     const unsigned n_in = *a.q_in_count;
