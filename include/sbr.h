@@ -192,6 +192,32 @@ int sbr_trace(sbr_ctx* ctx, const double* az_el_deg, int64_t n_angles, double ra
 int sbr_po_integrate(sbr_ctx* ctx, const double* freq_hz, int64_t n_freq, int pol_mask, int po_mode,
                      double* E_re_im, double* rcs_dbsm, int out_on_device);
 
+/* One request of a batch: an aspect with its own ray spacing and its own list
+ * of frequencies (entries freq_offset .. freq_offset + n_freq - 1 of the
+ * batch's frequency array). */
+typedef struct {
+    double az_deg, el_deg;
+    double ray_spacing_m;  /* ds of this request (e.g. sbr_spacing_for(its highest frequency, rays/lambda)) */
+    int64_t freq_offset;
+    int32_t n_freq;
+    int32_t reserved;
+} sbr_request;
+
+/* Batched trace-integrate (the paper's angular sweep, Sec. 4 last paragraph,
+ * done inside one GPU): every request is traced once (Algorithm 2, Eq. L1-L3
+ * with its own spacing) and its frequency-independent ray paths are integrated
+ * for all of its frequencies (Eq. po_sum / em6), requests of uneven ray counts
+ * packed into chunks of persistent-kernel passes. Chunks are integrated as soon
+ * as they are traced, so record memory stays bounded by the chunk size
+ * (opt->chunk_rays). Output row r0 + q (r0 = sum of n_freq over the earlier
+ * requests) holds frequency q of a request: E_re_im [rows][n_pol][2],
+ * rcs_dbsm [rows][n_pol], host (out_on_device = 0) or device (1) memory.
+ * The call synchronises; it leaves no trace results behind (sbr_po_integrate
+ * and sbr_get_records need sbr_trace). SBR_TRACE_RECORD_HITS is refused. */
+int sbr_run_batch(sbr_ctx* ctx, const sbr_request* req, int64_t n_req, const double* freq_hz, int64_t n_freq_total,
+                  double margin_eta, int max_bounces, int pol_mask, int po_mode, const sbr_trace_opts* opt,
+                  double* E_re_im, double* rcs_dbsm, int out_on_device, sbr_trace_stats* stats);
+
 /* Per-ray hits of traced aspect `angle` (needs SBR_TRACE_RECORD_HITS), for
  * parity checks; ray id = j * nu + i. Host outputs (any may be NULL):
  * tri_ids [nu*nv][max_bounces] original triangle index or -1, t [nu*nv][max_bounces]
@@ -212,7 +238,7 @@ int sbr_get_records(sbr_ctx* ctx, int64_t angle, int64_t cap, int64_t* ray_ids, 
  * application that owns all device memory, loops that must not enter the
  * allocator. It computes what sbr_po_integrate computes, with the same kernels,
  * from caller-provided device records, and keeps all scratch in one fixed
- * file-scope device array (about 8.7 MB, held by every GPU that loads the
+ * file-scope device array (about 9 MB, held by every GPU that loads the
  * library until the process exits). It calls no cudaMalloc/cudaFree.
  *
  *   records      device, n_records x 32 bytes, each record 8 x 32-bit words:

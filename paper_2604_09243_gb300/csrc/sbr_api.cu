@@ -410,6 +410,336 @@ int sbr_ray_grid_box(const float* bbox6, double az_deg, double el_deg, double ds
     return SBR_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// per-call state of a trace (sbr_trace or sbr_run_batch)
+struct TraceRun {
+    int flags = 0, max_bounces = 1;
+    bool escape = false, hits = false, count = false, timed = false;
+    long long chunk_cap = kChunkRays;
+    int n_blocks = 0;
+    int64_t n_launch = 0, n_pass = 0;
+    size_t n_ev = 0;
+};
+
+// Lay out the aspects c->ang[0..n) (grids filled) in processing order, cut them
+// into chunks of at most chunk_cap rays and size the per-chunk buffers.
+int plan_chunks(sbr_ctx* c, TraceRun& R, std::vector<int64_t>& cut, long long* total_out, long long* launched_out)
+{
+    const int64_t n = (int64_t)c->ang.size();
+    long long total = 0, launched = 0;
+    for (int64_t a = 0; a < n; ++a) {
+        AngleHost& h = c->ang[(size_t)a];
+        if (h.grid.nu > (1ll << 30) || h.grid.nv > (1ll << 30) || tiled_rays(h.grid) > R.chunk_cap)
+            return fail(c, SBR_ERR_ARG, "ray grid of aspect %lld too large (%lld x %lld) for a chunk of %lld rays",
+                        (long long)a, (long long)h.grid.nu, (long long)h.grid.nv, R.chunk_cap);
+        h.ray_begin = total;
+        h.rec_begin = h.rec_count = 0;
+        total += tiled_rays(h.grid);
+        launched += h.grid.nu * h.grid.nv;
+    }
+    cut.assign(1, 0);
+    long long acc = 0;
+    for (int64_t a = 0; a < n; ++a) {
+        const long long r = tiled_rays(c->ang[(size_t)a].grid);
+        if (acc > 0 && acc + r > R.chunk_cap) {
+            cut.push_back(a);
+            acc = 0;
+        }
+        acc += r;
+    }
+    cut.push_back(n);
+    long long max_chunk = 0;
+    int max_angles = 0;
+    for (size_t k = 0; k + 1 < cut.size(); ++k) {
+        const AngleHost& last = c->ang[(size_t)cut[k + 1] - 1];
+        max_chunk = std::max(max_chunk, last.ray_begin + tiled_rays(last.grid) - c->ang[(size_t)cut[k]].ray_begin);
+        max_angles = std::max(max_angles, (int)(cut[k + 1] - cut[k]));
+    }
+    const long long max_tiles = max_chunk / 32;
+    CK(c->angles.ensure(sizeof(AngleDev) * (size_t)max_angles), "alloc angles");
+    CK(c->rayoff.ensure(sizeof(long long) * (size_t)(max_angles + 1)), "alloc ray offsets");
+    CK(c->recoff.ensure(sizeof(unsigned) * (size_t)(max_angles + 1)), "alloc record offsets");
+    CK(c->mask.ensure(sizeof(unsigned) * (size_t)max_tiles), "alloc mask");
+    CK(c->tilebase.ensure(sizeof(unsigned) * (size_t)max_tiles), "alloc tile base");
+    CK(c->scan_scr.ensure(scan_scratch_bytes(max_tiles)), "alloc scan scratch");
+    CK(c->q0.ensure(sizeof(RayState) * (size_t)max_chunk), "alloc ray queue");
+    CK(c->q1.ensure(sizeof(RayState) * (size_t)max_chunk), "alloc ray queue");
+    CK(c->ctr64.ensure(sizeof(unsigned long long) * 2 * (kMaxBounces + 2)), "alloc counters");
+    CK(c->ctr32.ensure(sizeof(unsigned) * 2 * (kMaxBounces + 2) + 64), "alloc counters");
+    CK(c->stats.ensure(sizeof(unsigned long long) * kStatCount), "alloc stats");
+    CK(cudaMemsetAsync(c->stats.p, 0, sizeof(unsigned long long) * kStatCount, c->stream), "memset stats");
+    if (R.hits) {
+        const size_t B = (size_t)R.max_bounces;
+        CK(c->hit_tri.ensure(sizeof(int) * (size_t)total * B), "alloc hit ids");
+        CK(c->hit_t.ensure(sizeof(float) * (size_t)total * B), "alloc hit t");
+        CK(c->hit_nb.ensure(sizeof(int) * (size_t)total), "alloc hit counts");
+        CK(cudaMemsetAsync(c->hit_tri.p, 0xFF, sizeof(int) * (size_t)total * B, c->stream), "memset");
+        CK(cudaMemsetAsync(c->hit_t.p, 0, sizeof(float) * (size_t)total * B, c->stream), "memset");
+        CK(cudaMemsetAsync(c->hit_nb.p, 0, sizeof(int) * (size_t)total, c->stream), "memset");
+    }
+    R.n_blocks = c->n_sms * c->trace_bps;
+    *total_out = total;
+    *launched_out = launched;
+    return SBR_OK;
+}
+
+cudaEvent_t pool_event(sbr_ctx* c, size_t i)
+{
+    while (c->evpool.size() <= i) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        c->evpool.push_back(e);
+    }
+    return c->evpool[i];
+}
+
+// Trace the aspects [a0, a1) (one chunk): primary pass, popcount scan of the
+// hit masks (one synchronisation to learn the record counts), bounce passes.
+// Records go to c->rec from index rec_base on; earlier records are kept.
+int trace_chunk(sbr_ctx* c, TraceRun& R, int64_t a0, int64_t a1, long long rec_base, long long* n_valid_out)
+{
+    const int na = (int)(a1 - a0);
+    const long long base = c->ang[(size_t)a0].ray_begin;
+    const long long chunk_rays = c->ang[(size_t)a1 - 1].ray_begin + tiled_rays(c->ang[(size_t)a1 - 1].grid) - base;
+    unsigned* q_count = c->ctr32.as<unsigned>();
+    unsigned* total_dev = q_count + 2 * (kMaxBounces + 2);
+    auto pass = [&](const TraceArgs& t) -> cudaError_t {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (R.timed) {
+            e0 = pool_event(c, R.n_ev);
+            e1 = pool_event(c, R.n_ev + 1);
+            if (!e0 || !e1) return cudaErrorMemoryAllocation;
+            R.n_ev += 2;
+            cudaEventRecord(e0, c->stream);
+        }
+        cudaError_t e = launch_trace(t, R.n_blocks, R.count, c->stream);
+        if (R.timed) cudaEventRecord(e1, c->stream);
+        ++R.n_launch;
+        ++R.n_pass;
+        return e;
+    };
+    // stage angle table and ray offsets
+    const size_t bytes_a = sizeof(AngleDev) * (size_t)na, bytes_o = sizeof(long long) * (size_t)(na + 1);
+    char* hs = (char*)stage(c, bytes_a + bytes_o + sizeof(unsigned) * (size_t)(na + 1));
+    if (!hs) return fail(c, SBR_ERR_OOM, "pinned staging allocation failed");
+    AngleDev* ha = (AngleDev*)hs;
+    long long* ho = (long long*)(hs + bytes_a);
+    for (int i = 0; i < na; ++i) {
+        const AngleHost& h = c->ang[(size_t)(a0 + i)];
+        ho[i] = h.ray_begin - base;
+        ha[i] = to_dev(h.grid, ho[i]);
+    }
+    ho[na] = chunk_rays;
+    CK(cudaMemcpyAsync(c->angles.p, ha, bytes_a, cudaMemcpyHostToDevice, c->stream), "copy angles");
+    CK(cudaMemcpyAsync(c->rayoff.p, ho, bytes_o, cudaMemcpyHostToDevice, c->stream), "copy ray offsets");
+    CK(cudaMemsetAsync(c->ctr64.p, 0, c->ctr64.cap, c->stream), "memset counters");
+    CK(cudaMemsetAsync(c->ctr32.p, 0, c->ctr32.cap, c->stream), "memset counters");
+    TraceArgs ta;
+    memset(&ta, 0, sizeof(ta));
+    ta.nodes = c->nodes.as<float4>();
+    ta.tris = c->tris.as<float4>();
+    ta.angles = c->angles.as<AngleDev>();
+    ta.ray_off = c->rayoff.as<long long>();
+    ta.n_angles = na;
+    ta.max_bounces = R.max_bounces;
+    ta.flags = R.flags;
+    ta.visit_limit = (int)std::min<long long>(2 * c->n_tri + 64, 1ll << 30);
+    ta.total_rays = chunk_rays;
+    ta.mask = c->mask.as<unsigned>();
+    ta.tile_base = c->tilebase.as<unsigned>();
+    ta.stats = c->stats.as<unsigned long long>();
+    if (R.hits) {
+        ta.hit_tri = c->hit_tri.as<int>() + (size_t)base * R.max_bounces;
+        ta.hit_t = c->hit_t.as<float>() + (size_t)base * R.max_bounces;
+        ta.hit_nb = c->hit_nb.as<int>() + base;
+    }
+    RayState* qs[2] = {c->q0.as<RayState>(), c->q1.as<RayState>()};
+    ta.bounce = 0;  // pass 0: primary rays -> queue 0
+    ta.work = c->ctr64.as<unsigned long long>();
+    ta.q_out = qs[0];
+    ta.q_out_count = q_count + 1;
+    CK(pass(ta), "trace primary");
+    CK(scan_popc(ta.mask, c->tilebase.as<unsigned>(), chunk_rays / 32, total_dev, c->scan_scr.p, c->stream), "scan");
+    R.n_launch += 3;
+    CK(launch_angle_offsets(ta.ray_off, c->tilebase.as<unsigned>(), total_dev, na, c->recoff.as<unsigned>(), c->stream),
+       "angle offsets");
+    ++R.n_launch;
+    unsigned* hro = (unsigned*)(hs + bytes_a + bytes_o);
+    CK(cudaMemcpyAsync(hro, c->recoff.p, sizeof(unsigned) * (size_t)(na + 1), cudaMemcpyDeviceToHost, c->stream),
+       "copy record offsets");
+    CK(cudaStreamSynchronize(c->stream), "trace sync");
+    const long long n_valid = hro[na];
+    for (int i = 0; i < na; ++i) {
+        AngleHost& h = c->ang[(size_t)(a0 + i)];
+        h.rec_begin = rec_base + hro[i];
+        h.rec_count = (long long)hro[i + 1] - hro[i];
+    }
+    // grow the record buffer, keeping the records below rec_base
+    const size_t need = sizeof(Record) * (size_t)(rec_base + n_valid);
+    if (need > c->rec.cap) {
+        DevBuf nb;
+        CK(nb.ensure(need + need / 4), "alloc records");
+        if (rec_base > 0)
+            CK(cudaMemcpyAsync(nb.p, c->rec.p, sizeof(Record) * (size_t)rec_base, cudaMemcpyDeviceToDevice, c->stream),
+               "copy records");
+        CK(cudaStreamSynchronize(c->stream), "records sync");
+        c->rec.release();
+        c->rec = nb;
+    }
+    ta.rec = c->rec.as<Record>() + rec_base;
+    if (R.max_bounces == 1 && !R.escape) {
+        ta.q_in = qs[0];
+        ta.q_in_count = q_count + 1;
+        CK(launch_emit_all(ta, R.n_blocks, c->stream), "emit");
+        ++R.n_launch;
+    } else {
+        const int last_pass = R.escape ? R.max_bounces : R.max_bounces - 1;
+        for (int b = 1; b <= last_pass; ++b) {
+            ta.bounce = b;
+            ta.work = c->ctr64.as<unsigned long long>() + b;
+            ta.q_in = qs[(b - 1) & 1];
+            ta.q_in_count = q_count + b;
+            ta.q_out = qs[b & 1];
+            ta.q_out_count = q_count + b + 1;
+            CK(pass(ta), "trace bounce");
+        }
+    }
+    *n_valid_out = n_valid;
+    return SBR_OK;
+}
+
+// read the device counters into stats (synchronises); SBR_ERR_STACK_OVERFLOW if any traversal overflowed
+int finish_stats(sbr_ctx* c, const TraceRun& R, int64_t n_angles, long long launched, long long valid,
+                 sbr_trace_stats* stats)
+{
+    unsigned long long hs_stats[kStatCount];
+    CK(cudaMemcpyAsync(hs_stats, c->stats.p, sizeof(hs_stats), cudaMemcpyDeviceToHost, c->stream), "copy stats");
+    CK(cudaStreamSynchronize(c->stream), "trace end sync");
+    if (stats) {
+        stats->n_angles = n_angles;
+        stats->rays_launched = launched;
+        stats->ray_bounces = (int64_t)hs_stats[kStatQueries];
+        stats->valid_rays = valid;
+        stats->node_visits = (int64_t)hs_stats[kStatNodes];
+        stats->tri_tests = (int64_t)hs_stats[kStatTris];
+        stats->stack_overflows = (int64_t)hs_stats[kStatOverflow];
+        stats->kernel_launches = R.n_launch;
+        stats->pass_launches = R.n_pass;
+        stats->pass_ms = 0.0;
+        for (size_t i = 0; R.timed && i + 1 < R.n_ev; i += 2) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, c->evpool[i], c->evpool[i + 1]) == cudaSuccess) stats->pass_ms += ms;
+        }
+    }
+    if (hs_stats[kStatOverflow])
+        return fail(c, SBR_ERR_STACK_OVERFLOW, "%llu traversals exceeded the stack depth",
+                    (unsigned long long)hs_stats[kStatOverflow]);
+    return SBR_OK;
+}
+
+int check_po_mode(sbr_ctx* c, int pol_mask, int po_mode, PoArgs& pa)
+{
+    if (pol_mask <= 0 || pol_mask > 15) return fail(c, SBR_ERR_ARG, "pol_mask must select HH/VV/HV/VH");
+    const int form = po_mode & 15, prec = po_mode & ~15;
+    if (form != SBR_PO_VECTOR && form != SBR_PO_PAPER_SCALAR) return fail(c, SBR_ERR_ARG, "unknown PO form");
+    if (prec != SBR_PHASE_COMPENSATED && prec != SBR_PHASE_FP32 && prec != SBR_PHASE_FP64)
+        return fail(c, SBR_ERR_ARG, "unknown phase precision");
+    memset(&pa, 0, sizeof(pa));
+    for (int q = 0; q < 4; ++q)
+        if (pol_mask & (1 << q)) pa.pol_sel[pa.n_pol++] = q;
+    pa.scalar = form == SBR_PO_PAPER_SCALAR;
+    pa.phase_mode = prec == SBR_PHASE_COMPENSATED ? 0 : (prec == SBR_PHASE_FP32 ? 1 : 2);
+    return SBR_OK;
+}
+
+// upload the frequency table: (kappa_hi, kappa_lo, k) per frequency, kappa = f / c0
+int upload_freqs(sbr_ctx* c, const double* freq_hz, int64_t n_freq)
+{
+    for (int64_t f = 0; f < n_freq; ++f)
+        if (!(freq_hz[f] > 0.0)) return fail(c, SBR_ERR_ARG, "frequencies must be > 0");
+    const size_t b_freq = sizeof(float4) * (size_t)n_freq, b_kf = sizeof(double) * (size_t)n_freq;
+    CK(c->freq.ensure(b_freq), "alloc freq");
+    CK(c->kfreq.ensure(b_kf), "alloc freq");
+    char* hs = (char*)stage(c, b_freq + b_kf + 64);
+    if (!hs) return fail(c, SBR_ERR_OOM, "pinned staging allocation failed");
+    float4* hf = (float4*)hs;
+    double* hk = (double*)(hs + b_freq);
+    for (int64_t f = 0; f < n_freq; ++f) {
+        const double kappa = freq_hz[f] / kC0;  // cycles per metre
+        const float kh = (float)kappa;
+        const double k = 2.0 * kPi * freq_hz[f] / kC0;
+        hf[f] = make_float4(kh, (float)(kappa - (double)kh), (float)k, 0.f);
+        hk[f] = k;
+    }
+    CK(cudaMemcpyAsync(c->freq.p, hf, b_freq, cudaMemcpyHostToDevice, c->stream), "copy freq");
+    CK(cudaMemcpyAsync(c->kfreq.p, hk, b_kf, cudaMemcpyHostToDevice, c->stream), "copy freq");
+    CK(cudaEventRecord(c->stage_ev, c->stream), "record staging event");
+    return SBR_OK;
+}
+
+// PO sum of the aspects [a0, a1) of c->ang over their records; aspect a uses
+// frequencies [f0[a], f0[a] + nf[a]) of the uploaded table and writes rows
+// out_row[a] .. of the device outputs dE / dR.
+int po_run(sbr_ctx* c, PoArgs pa, int64_t a0, int64_t a1, const std::vector<int>& f0, const std::vector<int>& nf,
+           const std::vector<long long>& out_row, double* dE, double* dR, int64_t* n_launch)
+{
+    const int na = (int)(a1 - a0);
+    std::vector<PoItem> items;
+    std::vector<PoAngle> pang((size_t)na);
+    long long part = 0;
+    for (int i = 0; i < na; ++i) {
+        const AngleHost& h = c->ang[(size_t)(a0 + i)];
+        PoAngle& A = pang[(size_t)i];
+        A.item_begin = (int)items.size();
+        A.f0 = f0[(size_t)(a0 + i)];
+        A.nf = nf[(size_t)(a0 + i)];
+        A.out_row = out_row[(size_t)(a0 + i)];
+        A.pad = 0;
+        for (long long r = 0; r < h.rec_count; r += kPoItem) {
+            PoItem it;
+            it.angle = i;
+            it.first = h.rec_begin + r;
+            it.count = (int)std::min<long long>(kPoItem, h.rec_count - r);
+            it.f0 = A.f0;
+            it.nf = A.nf;
+            it.part = part;
+            part += (long long)A.nf * 2 * pa.n_pol;
+            items.push_back(it);
+        }
+        A.item_end = (int)items.size();
+    }
+    const int n_items = (int)items.size();
+    const size_t b_items = sizeof(PoItem) * (size_t)n_items, b_ang = sizeof(PoAngle) * (size_t)na;
+    CK(c->items.ensure(std::max(b_items, (size_t)32)), "alloc items");
+    CK(c->itemoff.ensure(b_ang), "alloc aspect table");
+    CK(c->partial.ensure(sizeof(double) * (size_t)std::max(part, 1ll)), "alloc partials");
+    char* hs = (char*)stage(c, b_items + b_ang + 64);
+    if (!hs) return fail(c, SBR_ERR_OOM, "pinned staging allocation failed");
+    if (n_items) memcpy(hs, items.data(), b_items);
+    memcpy(hs + b_items, pang.data(), b_ang);
+    if (n_items) CK(cudaMemcpyAsync(c->items.p, hs, b_items, cudaMemcpyHostToDevice, c->stream), "copy items");
+    CK(cudaMemcpyAsync(c->itemoff.p, hs + b_items, b_ang, cudaMemcpyHostToDevice, c->stream), "copy aspect table");
+    CK(cudaEventRecord(c->stage_ev, c->stream), "record staging event");
+    pa.rec = c->rec.as<Record>();
+    pa.items = c->items.as<PoItem>();
+    pa.n_items = n_items;
+    pa.freq = c->freq.as<float4>();
+    pa.kfreq = c->kfreq.as<double>();
+    pa.partial = c->partial.as<double>();
+    CK(launch_po(pa, c->stream), "po reduce");
+    CK(launch_po_final(pa.partial, pa.items, c->itemoff.as<PoAngle>(), na, pa.kfreq, pa.n_pol, dE, dR, c->stream),
+       "po final");
+    if (n_launch) *n_launch += (n_items > 0 ? 1 : 0) + 1;
+    return SBR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int sbr_trace(sbr_ctx* c, const double* az_el, int64_t n_angles, double ds, double eta, int max_bounces,
               const sbr_trace_opts* opt, sbr_trace_stats* stats)
 {
@@ -420,223 +750,33 @@ int sbr_trace(sbr_ctx* c, const double* az_el, int64_t n_angles, double ds, doub
     if (!(ds > 0.0) || !(eta >= 0.0)) return fail(c, SBR_ERR_ARG, "sbr_trace: spacing must be > 0, eta >= 0");
     if (max_bounces < 1 || max_bounces > kMaxBounces) return fail(c, SBR_ERR_ARG, "sbr_trace: max_bounces in 1..64");
     CK(cudaSetDevice(c->device), "cudaSetDevice");
-    const int flags = opt ? opt->flags : 0;
-    const bool escape = flags & SBR_TRACE_REQUIRE_ESCAPE;
-    const bool hits = flags & SBR_TRACE_RECORD_HITS;
-    const bool count = flags & SBR_TRACE_COUNT_VISITS;
-    const long long chunk_cap = (opt && opt->chunk_rays > 0) ? std::max<long long>(32, opt->chunk_rays) : kChunkRays;
+    TraceRun R;
+    R.flags = opt ? opt->flags : 0;
+    R.max_bounces = max_bounces;
+    R.escape = R.flags & SBR_TRACE_REQUIRE_ESCAPE;
+    R.hits = R.flags & SBR_TRACE_RECORD_HITS;
+    R.count = R.flags & SBR_TRACE_COUNT_VISITS;
+    R.timed = R.flags & SBR_TRACE_TIME_PASSES;
+    R.chunk_cap = (opt && opt->chunk_rays > 0) ? std::max<long long>(32, opt->chunk_rays) : kChunkRays;
     c->has_trace = false;
     c->ang.resize((size_t)n_angles);
+    for (int64_t a = 0; a < n_angles; ++a) make_grid(c->bbox, az_el[2 * a], az_el[2 * a + 1], ds, eta, opt, &c->ang[(size_t)a].grid);
+    std::vector<int64_t> cut;
     long long total = 0, launched = 0;
-    for (int64_t a = 0; a < n_angles; ++a) {
-        AngleHost& h = c->ang[(size_t)a];
-        make_grid(c->bbox, az_el[2 * a], az_el[2 * a + 1], ds, eta, opt, &h.grid);
-        const long long nr = h.grid.nu * h.grid.nv;
-        if (h.grid.nu > (1ll << 30) || h.grid.nv > (1ll << 30) || tiled_rays(h.grid) > chunk_cap)
-            return fail(c, SBR_ERR_ARG, "sbr_trace: ray grid of angle %lld too large (%lld x %lld)", (long long)a,
-                        (long long)h.grid.nu, (long long)h.grid.nv);
-        h.ray_begin = total;
-        total += tiled_rays(h.grid);
-        launched += nr;
-    }
-    // chunks of consecutive angles
-    std::vector<int64_t> cut{0};
-    {
-        long long acc = 0;
-        for (int64_t a = 0; a < n_angles; ++a) {
-            long long r = tiled_rays(c->ang[(size_t)a].grid);
-            if (acc > 0 && acc + r > chunk_cap) {
-                cut.push_back(a);
-                acc = 0;
-            }
-            acc += r;
-        }
-        cut.push_back(n_angles);
-    }
-    long long max_chunk = 0;
-    int max_chunk_angles = 0;
-    for (size_t k = 0; k + 1 < cut.size(); ++k) {
-        long long r = c->ang[(size_t)cut[k + 1] - 1].ray_begin + tiled_rays(c->ang[(size_t)cut[k + 1] - 1].grid) -
-                      c->ang[(size_t)cut[k]].ray_begin;
-        max_chunk = std::max(max_chunk, r);
-        max_chunk_angles = std::max(max_chunk_angles, (int)(cut[k + 1] - cut[k]));
-    }
-    const long long max_tiles = max_chunk / 32;
-    CK(c->angles.ensure(sizeof(AngleDev) * (size_t)max_chunk_angles), "alloc angles");
-    CK(c->rayoff.ensure(sizeof(long long) * (size_t)(max_chunk_angles + 1)), "alloc ray offsets");
-    CK(c->recoff.ensure(sizeof(unsigned) * (size_t)(max_chunk_angles + 1)), "alloc record offsets");
-    CK(c->mask.ensure(sizeof(unsigned) * (size_t)max_tiles), "alloc mask");
-    CK(c->tilebase.ensure(sizeof(unsigned) * (size_t)max_tiles), "alloc tile base");
-    CK(c->scan_scr.ensure(scan_scratch_bytes(max_tiles)), "alloc scan scratch");
-    CK(c->q0.ensure(sizeof(RayState) * (size_t)max_chunk), "alloc ray queue");
-    CK(c->q1.ensure(sizeof(RayState) * (size_t)max_chunk), "alloc ray queue");
-    CK(c->ctr64.ensure(sizeof(unsigned long long) * 2 * (kMaxBounces + 2)), "alloc counters");
-    CK(c->ctr32.ensure(sizeof(unsigned) * 2 * (kMaxBounces + 2) + 64), "alloc counters");
-    CK(c->stats.ensure(sizeof(unsigned long long) * kStatCount), "alloc stats");
-    CK(cudaMemsetAsync(c->stats.p, 0, sizeof(unsigned long long) * kStatCount, c->stream), "memset stats");
-    if (hits) {
-        CK(c->hit_tri.ensure(sizeof(int) * (size_t)total * max_bounces), "alloc hit ids");
-        CK(c->hit_t.ensure(sizeof(float) * (size_t)total * max_bounces), "alloc hit t");
-        CK(c->hit_nb.ensure(sizeof(int) * (size_t)total), "alloc hit counts");
-        CK(cudaMemsetAsync(c->hit_tri.p, 0xFF, sizeof(int) * (size_t)total * max_bounces, c->stream), "memset");
-        CK(cudaMemsetAsync(c->hit_t.p, 0, sizeof(float) * (size_t)total * max_bounces, c->stream), "memset");
-        CK(cudaMemsetAsync(c->hit_nb.p, 0, sizeof(int) * (size_t)total, c->stream), "memset");
-    }
-    const int n_blocks = c->n_sms * c->trace_bps;
-    const bool timed = flags & SBR_TRACE_TIME_PASSES;
-    int64_t n_launch = 0, n_pass = 0;
-    size_t n_ev = 0;
-    auto ev = [&](size_t i) -> cudaEvent_t {
-        while (c->evpool.size() <= i) {
-            cudaEvent_t e;
-            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
-            c->evpool.push_back(e);
-        }
-        return c->evpool[i];
-    };
-    auto pass = [&](const TraceArgs& t) -> cudaError_t {
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (timed) {
-            e0 = ev(n_ev);
-            e1 = ev(n_ev + 1);
-            if (!e0 || !e1) return cudaErrorMemoryAllocation;
-            n_ev += 2;
-            cudaEventRecord(e0, c->stream);
-        }
-        cudaError_t e = launch_trace(t, n_blocks, count, c->stream);
-        if (timed) cudaEventRecord(e1, c->stream);
-        ++n_launch;
-        ++n_pass;
-        return e;
-    };
+    int rc = plan_chunks(c, R, cut, &total, &launched);
+    if (rc != SBR_OK) return rc;
     c->rec_total = 0;
-    unsigned* q_count = c->ctr32.as<unsigned>();
-    unsigned* total_dev = q_count + 2 * (kMaxBounces + 2);
     for (size_t k = 0; k + 1 < cut.size(); ++k) {
-        const int64_t a0 = cut[k], a1 = cut[k + 1];
-        const int na = (int)(a1 - a0);
-        const long long base = c->ang[(size_t)a0].ray_begin;
-        const long long chunk_rays = c->ang[(size_t)a1 - 1].ray_begin +
-                                     tiled_rays(c->ang[(size_t)a1 - 1].grid) - base;
-        // stage angle table and ray offsets
-        size_t bytes_a = sizeof(AngleDev) * (size_t)na, bytes_o = sizeof(long long) * (size_t)(na + 1);
-        char* hs = (char*)stage(c, bytes_a + bytes_o + sizeof(unsigned) * (size_t)(na + 1));
-        if (!hs) return fail(c, SBR_ERR_OOM, "sbr_trace: pinned staging allocation failed");
-        AngleDev* ha = (AngleDev*)hs;
-        long long* ho = (long long*)(hs + bytes_a);
-        for (int i = 0; i < na; ++i) {
-            const AngleHost& h = c->ang[(size_t)(a0 + i)];
-            ho[i] = h.ray_begin - base;
-            ha[i] = to_dev(h.grid, ho[i]);
-        }
-        ho[na] = chunk_rays;
-        CK(cudaMemcpyAsync(c->angles.p, ha, bytes_a, cudaMemcpyHostToDevice, c->stream), "copy angles");
-        CK(cudaMemcpyAsync(c->rayoff.p, ho, bytes_o, cudaMemcpyHostToDevice, c->stream), "copy ray offsets");
-        CK(cudaMemsetAsync(c->ctr64.p, 0, c->ctr64.cap, c->stream), "memset counters");
-        CK(cudaMemsetAsync(c->ctr32.p, 0, c->ctr32.cap, c->stream), "memset counters");
-        TraceArgs ta;
-        memset(&ta, 0, sizeof(ta));
-        ta.nodes = c->nodes.as<float4>();
-        ta.tris = c->tris.as<float4>();
-        ta.angles = c->angles.as<AngleDev>();
-        ta.ray_off = c->rayoff.as<long long>();
-        ta.n_angles = na;
-        ta.max_bounces = max_bounces;
-        ta.flags = flags;
-        ta.visit_limit = (int)std::min<long long>(2 * c->n_tri + 64, 1ll << 30);
-        ta.total_rays = chunk_rays;
-        ta.mask = c->mask.as<unsigned>();
-        ta.tile_base = c->tilebase.as<unsigned>();
-        ta.stats = c->stats.as<unsigned long long>();
-        if (hits) {
-            ta.hit_tri = c->hit_tri.as<int>() + (size_t)base * max_bounces;
-            ta.hit_t = c->hit_t.as<float>() + (size_t)base * max_bounces;
-            ta.hit_nb = c->hit_nb.as<int>() + base;
-        }
-        RayState* qs[2] = {c->q0.as<RayState>(), c->q1.as<RayState>()};
-        // pass 0: primary rays -> queue 0
-        ta.bounce = 0;
-        ta.work = c->ctr64.as<unsigned long long>();
-        ta.q_out = qs[0];
-        ta.q_out_count = q_count + 1;
-        CK(pass(ta), "trace primary");
-        // dense slots of the valid rays
-        CK(scan_popc(ta.mask, c->tilebase.as<unsigned>(), chunk_rays / 32, total_dev, c->scan_scr.p, c->stream),
-           "scan");
-        n_launch += 3;
-        CK(launch_angle_offsets(ta.ray_off, c->tilebase.as<unsigned>(), total_dev, na, c->recoff.as<unsigned>(),
-                                c->stream),
-           "angle offsets");
-        ++n_launch;
-        unsigned* hro = (unsigned*)(hs + bytes_a + bytes_o);
-        CK(cudaMemcpyAsync(hro, c->recoff.p, sizeof(unsigned) * (size_t)(na + 1), cudaMemcpyDeviceToHost, c->stream),
-           "copy record offsets");
-        CK(cudaStreamSynchronize(c->stream), "trace sync");
-        const long long n_valid = hro[na];
-        for (int i = 0; i < na; ++i) {
-            AngleHost& h = c->ang[(size_t)(a0 + i)];
-            h.rec_begin = c->rec_total + hro[i];
-            h.rec_count = (long long)hro[i + 1] - hro[i];
-        }
-        // grow the record buffer, keeping earlier chunks
-        const size_t need = sizeof(Record) * (size_t)(c->rec_total + n_valid);
-        if (need > c->rec.cap) {
-            DevBuf nb;
-            CK(nb.ensure(need + need / 4), "alloc records");
-            if (c->rec_total > 0)
-                CK(cudaMemcpyAsync(nb.p, c->rec.p, sizeof(Record) * (size_t)c->rec_total, cudaMemcpyDeviceToDevice,
-                                   c->stream),
-                   "copy records");
-            CK(cudaStreamSynchronize(c->stream), "records sync");
-            c->rec.release();
-            c->rec = nb;
-        }
-        ta.rec = c->rec.as<Record>() + c->rec_total;
-        if (max_bounces == 1 && !escape) {
-            ta.q_in = qs[0];
-            ta.q_in_count = q_count + 1;
-            CK(launch_emit_all(ta, n_blocks, c->stream), "emit");
-            ++n_launch;
-        } else {
-            const int last_pass = escape ? max_bounces : max_bounces - 1;
-            for (int b = 1; b <= last_pass; ++b) {
-                ta.bounce = b;
-                ta.work = c->ctr64.as<unsigned long long>() + b;
-                ta.q_in = qs[(b - 1) & 1];
-                ta.q_in_count = q_count + b;
-                ta.q_out = qs[b & 1];
-                ta.q_out_count = q_count + b + 1;
-                CK(pass(ta), "trace bounce");
-            }
-        }
+        long long n_valid = 0;
+        rc = trace_chunk(c, R, cut[k], cut[k + 1], c->rec_total, &n_valid);
+        if (rc != SBR_OK) return rc;
         c->rec_total += n_valid;
     }
-    unsigned long long hs_stats[kStatCount];
-    CK(cudaMemcpyAsync(hs_stats, c->stats.p, sizeof(hs_stats), cudaMemcpyDeviceToHost, c->stream), "copy stats");
-    CK(cudaStreamSynchronize(c->stream), "trace end sync");
+    rc = finish_stats(c, R, n_angles, launched, c->rec_total, stats);
     c->max_bounces = max_bounces;
-    c->trace_flags = flags;
-    c->has_trace = true;
-    if (stats) {
-        stats->n_angles = n_angles;
-        stats->rays_launched = launched;
-        stats->ray_bounces = (int64_t)hs_stats[kStatQueries];
-        stats->valid_rays = c->rec_total;
-        stats->node_visits = (int64_t)hs_stats[kStatNodes];
-        stats->tri_tests = (int64_t)hs_stats[kStatTris];
-        stats->stack_overflows = (int64_t)hs_stats[kStatOverflow];
-        stats->kernel_launches = n_launch;
-        stats->pass_launches = n_pass;
-        stats->pass_ms = 0.0;
-        for (size_t i = 0; timed && i + 1 < n_ev; i += 2) {
-            float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, c->evpool[i], c->evpool[i + 1]) == cudaSuccess) stats->pass_ms += ms;
-        }
-    }
-    if (hs_stats[kStatOverflow])
-        return fail(c, SBR_ERR_STACK_OVERFLOW, "sbr_trace: %llu traversals exceeded the stack depth",
-                    (unsigned long long)hs_stats[kStatOverflow]);
-    return SBR_OK;
+    c->trace_flags = R.flags;
+    c->has_trace = rc == SBR_OK;
+    return rc;
 }
 
 int sbr_po_integrate(sbr_ctx* c, const double* freq_hz, int64_t n_freq, int pol_mask, int po_mode, double* E_out,
@@ -645,78 +785,17 @@ int sbr_po_integrate(sbr_ctx* c, const double* freq_hz, int64_t n_freq, int pol_
     if (!c) return SBR_ERR_ARG;
     if (!c->has_trace) return fail(c, SBR_ERR_STATE, "sbr_po_integrate: no trace results");
     if (!freq_hz || n_freq < 1 || n_freq > (1 << 20)) return fail(c, SBR_ERR_ARG, "sbr_po_integrate: bad frequency list");
-    if (pol_mask <= 0 || pol_mask > 15) return fail(c, SBR_ERR_ARG, "sbr_po_integrate: pol_mask must select HH/VV/HV/VH");
-    const int form = po_mode & 15, prec = po_mode & ~15;
-    if (form != SBR_PO_VECTOR && form != SBR_PO_PAPER_SCALAR)
-        return fail(c, SBR_ERR_ARG, "sbr_po_integrate: unknown PO form");
-    if (prec != SBR_PHASE_COMPENSATED && prec != SBR_PHASE_FP32 && prec != SBR_PHASE_FP64)
-        return fail(c, SBR_ERR_ARG, "sbr_po_integrate: unknown phase precision");
-    for (int64_t f = 0; f < n_freq; ++f)
-        if (!(freq_hz[f] > 0.0)) return fail(c, SBR_ERR_ARG, "sbr_po_integrate: frequencies must be > 0");
-    CK(cudaSetDevice(c->device), "cudaSetDevice");
     PoArgs pa;
-    memset(&pa, 0, sizeof(pa));
-    pa.n_pol = 0;
-    for (int q = 0; q < 4; ++q)
-        if (pol_mask & (1 << q)) pa.pol_sel[pa.n_pol++] = q;
-    pa.scalar = form == SBR_PO_PAPER_SCALAR;
-    pa.phase_mode = prec == SBR_PHASE_COMPENSATED ? 0 : (prec == SBR_PHASE_FP32 ? 1 : 2);
-    const int na = (int)c->ang.size();
-    // items: consecutive slices of <= kPoItem records per aspect
-    std::vector<int> item_off((size_t)na + 1);
-    std::vector<PoItem> items;
-    for (int a = 0; a < na; ++a) {
-        item_off[(size_t)a] = (int)items.size();
-        const AngleHost& h = c->ang[(size_t)a];
-        for (long long r = 0; r < h.rec_count; r += kPoItem) {
-            PoItem it;
-            it.angle = a;
-            it.first = h.rec_begin + r;
-            it.count = (int)std::min<long long>(kPoItem, h.rec_count - r);
-            items.push_back(it);
-        }
-    }
-    item_off[(size_t)na] = (int)items.size();
-    const int n_items = (int)items.size();
-    const size_t b_items = sizeof(PoItem) * (size_t)std::max(n_items, 1);
-    const size_t b_ioff = sizeof(int) * (size_t)(na + 1);
-    const size_t b_freq = sizeof(float4) * (size_t)n_freq, b_kf = sizeof(double) * (size_t)n_freq;
-    CK(c->items.ensure(b_items), "alloc items");
-    CK(c->itemoff.ensure(b_ioff), "alloc item offsets");
-    CK(c->freq.ensure(b_freq), "alloc freq");
-    CK(c->kfreq.ensure(b_kf), "alloc freq");
-    CK(c->partial.ensure(sizeof(double) * (size_t)std::max(n_items, 1) * (size_t)n_freq * 2 * pa.n_pol),
-       "alloc partials");
-    char* hs = (char*)stage(c, b_items + b_ioff + b_freq + b_kf + 64);
-    if (!hs) return fail(c, SBR_ERR_OOM, "sbr_po_integrate: pinned staging allocation failed");
-    char* p = hs;
-    if (n_items) memcpy(p, items.data(), sizeof(PoItem) * (size_t)n_items);
-    CK(cudaMemcpyAsync(c->items.p, p, sizeof(PoItem) * (size_t)n_items, cudaMemcpyHostToDevice, c->stream), "copy items");
-    p += b_items;
-    memcpy(p, item_off.data(), b_ioff);
-    CK(cudaMemcpyAsync(c->itemoff.p, p, b_ioff, cudaMemcpyHostToDevice, c->stream), "copy item offsets");
-    p += b_ioff;
-    float4* hf = (float4*)p;
-    double* hk = (double*)(p + b_freq);
-    for (int64_t f = 0; f < n_freq; ++f) {
-        const double kappa = freq_hz[f] / kC0;  // cycles per metre
-        const float kh = (float)kappa;
-        const float kl = (float)(kappa - (double)kh);
-        const double k = 2.0 * kPi * freq_hz[f] / kC0;
-        hf[f] = make_float4(kh, kl, (float)k, 0.f);
-        hk[f] = k;
-    }
-    CK(cudaMemcpyAsync(c->freq.p, hf, b_freq, cudaMemcpyHostToDevice, c->stream), "copy freq");
-    CK(cudaMemcpyAsync(c->kfreq.p, hk, b_kf, cudaMemcpyHostToDevice, c->stream), "copy freq");
-    CK(cudaEventRecord(c->stage_ev, c->stream), "record staging event");
-    pa.rec = c->rec.as<Record>();
-    pa.items = c->items.as<PoItem>();
-    pa.n_items = n_items;
-    pa.freq = c->freq.as<float4>();
-    pa.kfreq = c->kfreq.as<double>();
+    int rc = check_po_mode(c, pol_mask, po_mode, pa);
+    if (rc != SBR_OK) return rc;
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    rc = upload_freqs(c, freq_hz, n_freq);
+    if (rc != SBR_OK) return rc;
     pa.n_freq = (int)n_freq;
-    pa.partial = c->partial.as<double>();
-    CK(launch_po(pa, c->stream), "po reduce");
+    const int64_t na = (int64_t)c->ang.size();
+    std::vector<int> f0((size_t)na, 0), nf((size_t)na, (int)n_freq);
+    std::vector<long long> row((size_t)na);
+    for (int64_t a = 0; a < na; ++a) row[(size_t)a] = a * n_freq;
     const size_t n_out = (size_t)na * (size_t)n_freq * pa.n_pol;
     double* dE = E_out;
     double* dR = rcs_out;
@@ -726,8 +805,8 @@ int sbr_po_integrate(sbr_ctx* c, const double* freq_hz, int64_t n_freq, int pol_
         dE = E_out ? c->E.as<double>() : nullptr;
         dR = rcs_out ? c->rcs.as<double>() : nullptr;
     }
-    CK(launch_po_final(pa.partial, c->itemoff.as<int>(), na, pa.kfreq, (int)n_freq, pa.n_pol, dE, dR, c->stream),
-       "po final");
+    rc = po_run(c, pa, 0, na, f0, nf, row, dE, dR, nullptr);
+    if (rc != SBR_OK) return rc;
     if (!out_on_device) {
         if (E_out)
             CK(cudaMemcpyAsync(E_out, dE, sizeof(double) * 2 * n_out, cudaMemcpyDeviceToHost, c->stream), "copy E");
@@ -736,6 +815,83 @@ int sbr_po_integrate(sbr_ctx* c, const double* freq_hz, int64_t n_freq, int pol_
         CK(cudaStreamSynchronize(c->stream), "po sync");
     }
     return SBR_OK;
+}
+
+int sbr_run_batch(sbr_ctx* c, const sbr_request* req, int64_t n_req, const double* freq_hz, int64_t n_freq_total,
+                  double eta, int max_bounces, int pol_mask, int po_mode, const sbr_trace_opts* opt, double* E_out,
+                  double* rcs_out, int out_on_device, sbr_trace_stats* stats)
+{
+    if (!c) return SBR_ERR_ARG;
+    if (!c->has_bvh) return fail(c, SBR_ERR_STATE, "sbr_run_batch: no BVH (load a mesh first)");
+    if (!req || n_req < 1 || n_req > (1ll << 30)) return fail(c, SBR_ERR_ARG, "sbr_run_batch: no requests");
+    if (!freq_hz || n_freq_total < 1 || n_freq_total > (1ll << 30))
+        return fail(c, SBR_ERR_ARG, "sbr_run_batch: bad frequency array");
+    if (!(eta >= 0.0)) return fail(c, SBR_ERR_ARG, "sbr_run_batch: eta >= 0");
+    if (max_bounces < 1 || max_bounces > kMaxBounces) return fail(c, SBR_ERR_ARG, "sbr_run_batch: max_bounces in 1..64");
+    if (opt && (opt->flags & SBR_TRACE_RECORD_HITS))
+        return fail(c, SBR_ERR_ARG, "sbr_run_batch: SBR_TRACE_RECORD_HITS is for sbr_trace");
+    PoArgs pa;
+    int rc = check_po_mode(c, pol_mask, po_mode, pa);
+    if (rc != SBR_OK) return rc;
+    std::vector<int> f0((size_t)n_req), nf((size_t)n_req);
+    std::vector<long long> row((size_t)n_req);
+    long long rows = 0;
+    for (int64_t r = 0; r < n_req; ++r) {
+        const sbr_request& q = req[r];
+        if (!(q.ray_spacing_m > 0.0)) return fail(c, SBR_ERR_ARG, "sbr_run_batch: request %lld: spacing must be > 0", (long long)r);
+        if (q.n_freq < 1 || q.freq_offset < 0 || q.freq_offset + q.n_freq > n_freq_total)
+            return fail(c, SBR_ERR_ARG, "sbr_run_batch: request %lld: frequency range outside the array", (long long)r);
+        f0[(size_t)r] = (int)q.freq_offset;
+        nf[(size_t)r] = q.n_freq;
+        row[(size_t)r] = rows;
+        rows += q.n_freq;
+    }
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    TraceRun R;
+    R.flags = opt ? opt->flags : 0;
+    R.max_bounces = max_bounces;
+    R.escape = R.flags & SBR_TRACE_REQUIRE_ESCAPE;
+    R.count = R.flags & SBR_TRACE_COUNT_VISITS;
+    R.timed = R.flags & SBR_TRACE_TIME_PASSES;
+    R.chunk_cap = (opt && opt->chunk_rays > 0) ? std::max<long long>(32, opt->chunk_rays) : kChunkRays;
+    c->has_trace = false;
+    c->ang.resize((size_t)n_req);
+    for (int64_t r = 0; r < n_req; ++r)
+        make_grid(c->bbox, req[r].az_deg, req[r].el_deg, req[r].ray_spacing_m, eta, opt, &c->ang[(size_t)r].grid);
+    std::vector<int64_t> cut;
+    long long total = 0, launched = 0;
+    rc = plan_chunks(c, R, cut, &total, &launched);
+    if (rc != SBR_OK) return rc;
+    rc = upload_freqs(c, freq_hz, n_freq_total);
+    if (rc != SBR_OK) return rc;
+    pa.n_freq = (int)n_freq_total;
+    const size_t n_out = (size_t)rows * pa.n_pol;
+    double* dE = E_out;
+    double* dR = rcs_out;
+    if (!out_on_device) {
+        CK(c->E.ensure(sizeof(double) * 2 * n_out), "alloc E");
+        CK(c->rcs.ensure(sizeof(double) * n_out), "alloc rcs");
+        dE = E_out ? c->E.as<double>() : nullptr;
+        dR = rcs_out ? c->rcs.as<double>() : nullptr;
+    }
+    // each chunk is traced once and integrated for all its requests' frequencies
+    // before the next chunk reuses the record buffer
+    long long valid = 0;
+    for (size_t k = 0; k + 1 < cut.size(); ++k) {
+        long long n_valid = 0;
+        rc = trace_chunk(c, R, cut[k], cut[k + 1], 0, &n_valid);
+        if (rc != SBR_OK) return rc;
+        valid += n_valid;
+        rc = po_run(c, pa, cut[k], cut[k + 1], f0, nf, row, dE, dR, &R.n_launch);
+        if (rc != SBR_OK) return rc;
+    }
+    if (!out_on_device) {
+        if (E_out)
+            CK(cudaMemcpyAsync(E_out, dE, sizeof(double) * 2 * n_out, cudaMemcpyDeviceToHost, c->stream), "copy E");
+        if (rcs_out)
+            CK(cudaMemcpyAsync(rcs_out, dR, sizeof(double) * n_out, cudaMemcpyDeviceToHost, c->stream), "copy rcs");
+    }
+    return finish_stats(c, R, n_req, launched, valid, stats);
 }
 
 int sbr_get_hits(sbr_ctx* c, int64_t angle, int32_t* tri_ids, float* t, int32_t* n_bounce)

@@ -125,25 +125,37 @@ cudaError_t launch_angle_offsets(const long long* ray_off, const unsigned* tile_
                                  int n_angles, unsigned* rec_off, cudaStream_t st);
 
 struct PoItem {
-    int angle;        // aspect index (global over the trace)
-    int count;        // records in this item
+    int angle;        // aspect index within the call
+    int count;        // records in this item (at most kPoItem)
     long long first;  // first record
+    int f0, nf;       // frequencies [f0, f0 + nf) of the frequency table
+    long long part;   // first FP64 partial of this item: nf x n_pol x (re, im)
 };
+static_assert(sizeof(PoItem) == 32, "PoItem layout");
+// per-aspect view of the items and of the output rows
+struct PoAngle {
+    int item_begin, item_end;  // items of this aspect
+    int f0, nf;                // its frequencies in the frequency table
+    long long out_row;         // first output row: row out_row + q holds frequency f0 + q
+    long long pad;
+};
+static_assert(sizeof(PoAngle) == 32, "PoAngle layout");
 struct PoArgs {
     const Record* rec;
     const PoItem* items;
     int n_items;
     const float4* freq;   // [n_freq] (kappa_hi, kappa_lo, k, 0), kappa = f / c0 cycles per metre
     const double* kfreq;  // [n_freq] k in FP64 (FP64 phase mode)
-    int n_freq;
+    int n_freq;           // entries of the frequency table
     int pol_sel[4];       // selected polarisation indices (0 HH, 1 VV, 2 HV, 3 VH)
     int n_pol;
     int scalar;           // 1: paper scalar form
     int phase_mode;       // 0 compensated, 1 FP32, 2 FP64
-    double* partial;      // [n_items][n_freq][n_pol][2]
+    double* partial;      // FP64 partials, item i at items[i].part
 };
 cudaError_t launch_po(const PoArgs& a, cudaStream_t st);
-cudaError_t launch_po_final(const double* partial, const int* item_off, int n_angles, const double* kfreq,
-                            int n_freq, int n_pol, double* E, double* rcs, cudaStream_t st);
+// E[row][n_pol][2] and rcs[row][n_pol] for every aspect's rows (fixed-order FP64 sums of the partials)
+cudaError_t launch_po_final(const double* partial, const PoItem* items, const PoAngle* angles, int n_angles,
+                            const double* kfreq, int n_pol, double* E, double* rcs, cudaStream_t st);
 
 }  // namespace sbr

@@ -38,7 +38,7 @@ constexpr int kMaxDevices = 64;
 
 // layout of the static scratch (bytes)
 constexpr size_t kItemsBytes = sizeof(PoItem) * SBR_NOALLOC_MAX_ITEMS;
-constexpr size_t kOffBytes = sizeof(int) * (SBR_NOALLOC_MAX_ANGLES + 1);
+constexpr size_t kOffBytes = sizeof(PoAngle) * SBR_NOALLOC_MAX_ANGLES;
 constexpr size_t kFreqBytes = sizeof(float4) * SBR_NOALLOC_MAX_FREQ;
 constexpr size_t kKfBytes = sizeof(double) * SBR_NOALLOC_MAX_FREQ;
 constexpr size_t kPartialBytes = SBR_NOALLOC_PARTIAL_BYTES;
@@ -56,7 +56,7 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 std::mutex g_mu;
 void* g_addr[kMaxDevices] = {nullptr};
 PoItem g_items[SBR_NOALLOC_MAX_ITEMS];
-int g_item_off[SBR_NOALLOC_MAX_ANGLES + 1];
+PoAngle g_angles[SBR_NOALLOC_MAX_ANGLES];
 float4 g_freq[SBR_NOALLOC_MAX_FREQ];
 double g_kf[SBR_NOALLOC_MAX_FREQ];
 
@@ -112,15 +112,23 @@ extern "C" int sbr_po_integrate_noalloc(const void* records, const int64_t* rec_
                       "sbr_po_integrate_noalloc: blocks x n_freq x n_pol x 16 B exceeds SBR_NOALLOC_PARTIAL_BYTES");
     int ni = 0;
     for (int64_t a = 0; a < n_angles; ++a) {
-        g_item_off[a] = ni;
+        PoAngle& A = g_angles[a];
+        A.item_begin = ni;
+        A.f0 = 0;
+        A.nf = (int)n_freq;
+        A.out_row = a * n_freq;
+        A.pad = 0;
         for (long long r = rec_offsets[a]; r < rec_offsets[a + 1]; r += kItem) {
             g_items[ni].angle = (int)a;
             g_items[ni].first = r;
             g_items[ni].count = (int)(rec_offsets[a + 1] - r < kItem ? rec_offsets[a + 1] - r : kItem);
+            g_items[ni].f0 = 0;
+            g_items[ni].nf = (int)n_freq;
+            g_items[ni].part = (long long)ni * n_freq * 2 * pa.n_pol;
             ++ni;
         }
+        A.item_end = ni;
     }
-    g_item_off[n_angles] = ni;
     for (int64_t f = 0; f < n_freq; ++f) {
         const double kappa = freq_hz[f] / kC0;
         const float kh = (float)kappa;
@@ -147,7 +155,7 @@ extern "C" int sbr_po_integrate_noalloc(const void* records, const int64_t* rec_
     // host tables can be refilled by the next call
     if (ni > 0) e = cudaMemcpyAsync(base + kOffItems, g_items, sizeof(PoItem) * (size_t)ni, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(base + kOffOff, g_item_off, sizeof(int) * (size_t)(n_angles + 1), cudaMemcpyHostToDevice, st);
+        e = cudaMemcpyAsync(base + kOffOff, g_angles, sizeof(PoAngle) * (size_t)n_angles, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(base + kOffFreq, g_freq, sizeof(float4) * (size_t)n_freq, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
@@ -163,7 +171,7 @@ extern "C" int sbr_po_integrate_noalloc(const void* records, const int64_t* rec_
     pa.partial = (double*)(base + kOffPartial);  // every entry read below is written by this call first
     e = launch_po(pa, st);
     if (e == cudaSuccess)
-        e = launch_po_final(pa.partial, (const int*)(base + kOffOff), (int)n_angles, pa.kfreq, (int)n_freq, pa.n_pol,
+        e = launch_po_final(pa.partial, pa.items, (const PoAngle*)(base + kOffOff), (int)n_angles, pa.kfreq, pa.n_pol,
                             E_re_im, rcs_dbsm, st);
     if (e != cudaSuccess) return reject(SBR_ERR_CUDA, "sbr_po_integrate_noalloc: kernel launch failed");
     return SBR_OK;

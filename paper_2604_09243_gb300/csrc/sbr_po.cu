@@ -76,9 +76,9 @@ __global__ void __launch_bounds__(kPoThreads) k_po(const PoArgs a)
             ll[k] = 0.f;
         }
     }
-    for (int f = 0; f < a.n_freq; ++f) {
-        const float4 fq = a.freq[f];
-        const double kd = a.kfreq[f];
+    for (int fi = 0; fi < I.nf; ++fi) {
+        const float4 fq = a.freq[I.f0 + fi];
+        const double kd = a.kfreq[I.f0 + fi];
         float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int k = 0; k < kPoPer; ++k) {
@@ -109,35 +109,35 @@ __global__ void __launch_bounds__(kPoThreads) k_po(const PoArgs a)
             float v = 0.f;
 #pragma unroll
             for (int k = 0; k < kWarps; ++k) v += s_red[k][tid];
-            a.partial[((size_t)blockIdx.x * a.n_freq + f) * (2 * a.n_pol) + tid] = (double)v;
+            a.partial[I.part + (size_t)fi * (2 * a.n_pol) + tid] = (double)v;
         }
         __syncthreads();
     }
 }
 
-__global__ void k_po_final(const double* partial, const int* item_off, int n_angles, const double* kfreq, int n_freq,
+// one block per aspect; its threads stride over (frequency, polarisation) outputs
+__global__ void k_po_final(const double* partial, const PoItem* items, const PoAngle* angles, const double* kfreq,
                            int n_pol, double* E, double* rcs)
 {
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long n = (long long)n_angles * n_freq * n_pol;
-    if (i >= n) return;
-    const int p = (int)(i % n_pol);
-    const int f = (int)((i / n_pol) % n_freq);
-    const int ang = (int)(i / ((long long)n_pol * n_freq));
-    double sr = 0.0, si = 0.0;
-    for (int it = item_off[ang]; it < item_off[ang + 1]; ++it) {
-        const double* q = partial + ((size_t)it * n_freq + f) * (2 * n_pol) + 2 * p;
-        sr += q[0];
-        si += q[1];
+    const PoAngle A = angles[blockIdx.x];
+    for (int o = threadIdx.x; o < A.nf * n_pol; o += blockDim.x) {
+        const int q = o / n_pol, p = o - q * n_pol;
+        double sr = 0.0, si = 0.0;
+        for (int it = A.item_begin; it < A.item_end; ++it) {
+            const double* v = partial + items[it].part + (size_t)q * (2 * n_pol) + 2 * p;
+            sr += v[0];
+            si += v[1];
+        }
+        // E = (-j k / 4 pi) (sr + j si)
+        const double pre = kfreq[A.f0 + q] / (4.0 * 3.14159265358979323846);
+        const double er = pre * si, ei = -pre * sr;
+        const long long i = (A.out_row + q) * n_pol + p;
+        if (E) {
+            E[2 * i] = er;
+            E[2 * i + 1] = ei;
+        }
+        if (rcs) rcs[i] = 10.0 * log10(4.0 * 3.14159265358979323846 * (er * er + ei * ei));
     }
-    // E = (-j k / 4 pi) (sr + j si)
-    const double pre = kfreq[f] / (4.0 * 3.14159265358979323846);
-    const double er = pre * si, ei = -pre * sr;
-    if (E) {
-        E[2 * i] = er;
-        E[2 * i + 1] = ei;
-    }
-    if (rcs) rcs[i] = 10.0 * log10(4.0 * 3.14159265358979323846 * (er * er + ei * ei));
 }
 
 }  // namespace
@@ -149,12 +149,11 @@ cudaError_t launch_po(const PoArgs& a, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_po_final(const double* partial, const int* item_off, int n_angles, const double* kfreq,
-                            int n_freq, int n_pol, double* E, double* rcs, cudaStream_t st)
+cudaError_t launch_po_final(const double* partial, const PoItem* items, const PoAngle* angles, int n_angles,
+                            const double* kfreq, int n_pol, double* E, double* rcs, cudaStream_t st)
 {
-    long long n = (long long)n_angles * n_freq * n_pol;
-    if (n <= 0) return cudaSuccess;
-    k_po_final<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(partial, item_off, n_angles, kfreq, n_freq, n_pol, E, rcs);
+    if (n_angles <= 0) return cudaSuccess;
+    k_po_final<<<n_angles, 128, 0, st>>>(partial, items, angles, kfreq, n_pol, E, rcs);
     return cudaGetLastError();
 }
 

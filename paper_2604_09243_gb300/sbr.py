@@ -28,7 +28,7 @@ TRACE_PHASE_LITERAL_2R, TRACE_REQUIRE_ESCAPE, TRACE_RECORD_HITS, TRACE_COUNT_VIS
 # every symbol declared in include/sbr.h
 EXPORTS = ("sbr_version", "sbr_create", "sbr_destroy", "sbr_last_error", "sbr_load_mesh", "sbr_get_bbox",
            "sbr_build_bvh", "sbr_ray_grid_for", "sbr_ray_grid_box", "sbr_trace", "sbr_po_integrate", "sbr_get_hits",
-           "sbr_get_records", "sbr_spacing_for", "sbr_po_integrate_noalloc")
+           "sbr_get_records", "sbr_spacing_for", "sbr_po_integrate_noalloc", "sbr_run_batch")
 
 
 class SbrError(RuntimeError):
@@ -54,6 +54,11 @@ class TraceStats(C.Structure):
 
     def as_dict(self):
         return {k: (float if k == "pass_ms" else int)(getattr(self, k)) for k, _ in self._fields_}
+
+
+class Request(C.Structure):
+    _fields_ = [("az_deg", C.c_double), ("el_deg", C.c_double), ("ray_spacing_m", C.c_double),
+                ("freq_offset", C.c_int64), ("n_freq", C.c_int32), ("reserved", C.c_int32)]
 
 
 class RayGrid(C.Structure):
@@ -92,6 +97,8 @@ def lib() -> C.CDLL:
         "sbr_get_hits": ([vp, i64, vp, vp, vp], C.c_int),
         "sbr_get_records": ([vp, i64, i64, vp, vp, vp, P(i64)], C.c_int),
         "sbr_spacing_for": ([d, d], d),
+        "sbr_run_batch": ([vp, P(Request), i64, P(d), i64, d, C.c_int, C.c_int, C.c_int, P(TraceOpts), vp, vp,
+                           C.c_int, P(TraceStats)], C.c_int),
         "sbr_po_integrate_noalloc": ([vp, P(i64), i64, P(d), i64, C.c_int, C.c_int, vp, vp, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
@@ -262,6 +269,38 @@ class Context:
         self._last_angles = a.copy()
         self._trace_args = (spacing, eta, window, offset)
         return st.as_dict() if stats else None
+
+    def run_batch(self, requests, eta=0.05, max_bounces=1, pols="HH,VV", mode="vector", phase="compensated",
+                  flags=0, chunk_rays=0, window=0.0, offset=(0.0, 0.0)):
+        """Batched trace + PO (sbr_run_batch). ``requests``: iterable of dicts with az, el,
+        spacing and freqs (array). Returns (list of E [n_freq, n_pol] complex, list of
+        rcs [n_freq, n_pol], stats)."""
+        reqs = list(requests)
+        freqs = np.concatenate([np.atleast_1d(np.asarray(r["freqs"], np.float64)) for r in reqs])
+        arr = (Request * len(reqs))()
+        off = 0
+        for k, r in enumerate(reqs):
+            nf = len(np.atleast_1d(r["freqs"]))
+            arr[k] = Request(float(r["az"]), float(r["el"]), float(r["spacing"]), off, nf, 0)
+            off += nf
+        pm = _pols(pols)
+        npol = bin(pm).count("1")
+        m = (PO_PAPER_SCALAR if mode == "scalar" else PO_VECTOR) | PHASE[phase]
+        E = np.empty((len(freqs), npol, 2), np.float64)
+        R = np.empty((len(freqs), npol), np.float64)
+        o = _opts(window, offset, flags, chunk_rays)
+        st = TraceStats()
+        self._check(lib().sbr_run_batch(self._h, arr, len(reqs), freqs.ctypes.data_as(C.POINTER(C.c_double)),
+                                        len(freqs), float(eta), int(max_bounces), pm, m, C.byref(o), E.ctypes.data,
+                                        R.ctypes.data, 0, C.byref(st)))
+        Ec = E[..., 0] + 1j * E[..., 1]
+        outE, outR, off = [], [], 0
+        for k in range(len(reqs)):
+            nf = arr[k].n_freq
+            outE.append(Ec[off:off + nf])
+            outR.append(R[off:off + nf])
+            off += nf
+        return outE, outR, st.as_dict()
 
     def po_integrate(self, freqs, pols="HH,VV", mode="vector", phase="compensated", E_out=None, rcs_out=None):
         """PO sum of the last trace. Returns (E complex128 [n_angles, n_freq, n_pol], rcs_dbsm [...]) as
