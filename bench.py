@@ -197,6 +197,56 @@ def run_reference(args, case, ws, rank, pg):
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def batched_vs_plain(G, torch, dev, n_req):
+    """Batched form against plain per-request SBR on the first ``n_req`` requests
+    of the mixed-request workload (4096 requests, seed 2, over the sphere,
+    trihedral and aircraft meshes): requests (= aspects) per second, same
+    requests, same outputs (HH, VV for every requested frequency)."""
+    import time as _t
+
+    reqs = S.batched_requests(4096, seed=2)[:n_req]
+    meshes = [S.icosphere(5), S.trihedral(1.0, 32), S.aircraft(seed=1)]
+    offs = [(0.0, 0.0), S.grid_offset(5), S.grid_offset(6)]
+    bounces = [1, 3, 10]
+    ctxs = []
+    for xyz, tri in meshes:
+        c = G.Context(dev)
+        c.load_mesh(xyz, tri)
+        ctxs.append(c)
+    groups = [[r for r in reqs if r["mesh"] == m] for m in range(3)]
+
+    def batched():
+        rb = 0
+        for m in range(3):
+            if groups[m]:
+                rb += ctxs[m].run_batch(groups[m], eta=0.05, max_bounces=bounces[m], offset=offs[m])[2]["ray_bounces"]
+        torch.cuda.synchronize()
+        return rb
+
+    def plain():
+        for m in range(3):
+            for r in groups[m]:
+                ctxs[m].trace([[r["az"], r["el"]]], r["spacing"], eta=0.05, max_bounces=bounces[m], offset=offs[m],
+                              stats=False)
+                ctxs[m].po_integrate(r["freqs"], "HH,VV")
+        torch.cuda.synchronize()
+
+    batched()
+    plain()
+    t0 = _t.perf_counter()
+    rb = batched()
+    tb = _t.perf_counter() - t0
+    t0 = _t.perf_counter()
+    plain()
+    tp = _t.perf_counter() - t0
+    for c in ctxs:
+        c.close()
+    return {"requests": n_req, "meshes": "icosphere5 / trihedral / aircraft (1M)",
+            "frequencies": int(sum(len(r["freqs"]) for r in reqs)),
+            "batched_requests_per_s": n_req / tb, "plain_requests_per_s": n_req / tp, "speedup": tp / tb,
+            "batched_ray_bounces_per_s": rb / tb, "timing": "host wall clock, one pass each after one warm-up pass"}
+
+
 def run_sbr(args, case, ws, rank, local, pg):
     import torch
 
@@ -299,6 +349,8 @@ def run_sbr(args, case, ws, rank, local, pg):
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * t_e2e / args.steps},
             "gpu_launches": int(launches * args.steps),
             "clocks": clocks}
+    if args.batch_requests > 0:
+        line["batched_vs_plain"] = batched_vs_plain(G, torch, local, args.batch_requests)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         b, t, idx = oracle_sample(case, args.ref_angles, threads)
@@ -319,6 +371,8 @@ def main():
     ap.add_argument("--workload", default="trihedral",
                     choices=["trihedral", "sphere", "aircraft1", "aircraft3", "aircraft10"])
     ap.add_argument("--ref-angles", type=int, default=24)
+    ap.add_argument("--batch-requests", type=int, default=256,
+                    help="mixed requests for the batched-vs-plain comparison (0 = skip)")
     ap.add_argument("--aspects", type=int, default=0,
                     help="use this many evenly spaced aspects of the sweep (small profiling cases); 0 = all")
     ap.add_argument("--no-cpu-baseline", action="store_true")
