@@ -247,6 +247,137 @@ def batched_vs_plain(G, torch, dev, n_req):
             "batched_ray_bounces_per_s": rb / tb, "timing": "host wall clock, one pass each after one warm-up pass"}
 
 
+def surrogate_eval(G, torch, dev, n_aspects=2000, f_per=100, n_heldout=10000, n_query=1_000_000, epochs=60,
+                   spread_db=1.0, sigmas=(1.0, 2.0, 4.0, 8.0, 16.0)):
+    """Learned surrogate on the aircraft mesh against plain SBR.
+
+    Training data: ``n_aspects`` aspects (az U[0, 360), el U[-30, 30], seed 3),
+    each with ``f_per`` frequencies log-uniform in [1, 12] GHz, traced once at
+    10 rays per wavelength of its highest frequency (batched form) -> samples
+    (az, el, f) -> (Re, Im of HH and VV). Held out: ``n_heldout`` points
+    (seed 4), each its own aspect and frequency, computed by SBR. The ensemble
+    answers a point when its spread is <= ``spread_db``; otherwise SBR does."""
+    import time as _t
+
+    xyz, tri = S.aircraft(seed=1)
+    off = S.grid_offset(6)
+    ctx = G.Context(dev)
+    ctx.load_mesh(xyz, tri)
+    rng = np.random.default_rng(3)
+    reqs = []
+    for _ in range(n_aspects):
+        f = np.sort(np.exp(rng.uniform(np.log(1e9), np.log(12e9), f_per)))
+        reqs.append(dict(az=float(rng.uniform(0, 360)), el=float(rng.uniform(-30, 30)), freqs=f,
+                         spacing=S.spacing_for(float(f[-1]), 10.0)))
+    torch.cuda.synchronize()
+    t0 = _t.perf_counter()
+    E, R, st = ctx.run_batch(reqs, eta=0.05, max_bounces=10, offset=off)
+    t_data = _t.perf_counter() - t0
+    x = np.concatenate([np.stack([np.full(len(r["freqs"]), r["az"]), np.full(len(r["freqs"]), r["el"]), r["freqs"]], 1)
+                        for r in reqs])
+    Ec = np.concatenate(E)
+    y = np.stack([Ec[:, 0].real, Ec[:, 0].imag, Ec[:, 1].real, Ec[:, 1].imag], 1)
+    # Fourier scale sigma_B tuned on a 90/10 split of the training samples (one member, short runs)
+    t0 = _t.perf_counter()
+    perm = np.random.default_rng(5).permutation(len(x))
+    cut = (int(0.9 * len(x)) // 128) * 128
+    tr, va = perm[:cut], perm[cut:]
+    tune = {}
+    for sig in sigmas:
+        m = G.Surrogate(dev, n_members=1, width=512, depth=6, n_fourier=256, fourier_sigma=sig, seed=11)
+        m.train(x[tr], y[tr], epochs=max(1, epochs // 4), batch=8192, lr=1e-3)
+        yv, _ = m.predict(x[va])
+        m.close()
+        tune[sig] = float(np.sqrt(np.mean((yv - y[va]) ** 2)) / np.sqrt(np.mean(y[va] ** 2)))
+    sigma = min(tune, key=tune.get)
+    t_tune = _t.perf_counter() - t0
+    sur = G.Surrogate(dev, n_members=4, width=512, depth=6, n_fourier=256, fourier_sigma=sigma, seed=1)
+    t0 = _t.perf_counter()
+    loss = sur.train(x, y, epochs=epochs, batch=8192, lr=1e-3)
+    t_train = _t.perf_counter() - t0
+    # held-out points, plain SBR (batched, one frequency per aspect)
+    rng = np.random.default_rng(4)
+    hx = np.stack([rng.uniform(0, 360, n_heldout), rng.uniform(-30, 30, n_heldout),
+                   np.exp(rng.uniform(np.log(1e9), np.log(12e9), n_heldout))], 1)
+    hreq = [dict(az=a, el=e, freqs=np.array([f]), spacing=S.spacing_for(f, 10.0)) for a, e, f in hx]
+    torch.cuda.synchronize()
+    t0 = _t.perf_counter()
+    _, Rh, _ = ctx.run_batch(hreq, eta=0.05, max_bounces=10, offset=off)
+    t_sbr = _t.perf_counter() - t0
+    Rh = np.concatenate(Rh)  # [n, 2] dBsm HH, VV
+    t0 = _t.perf_counter()
+    ym, spread = sur.predict(hx)
+    t_pred = _t.perf_counter() - t0
+    with np.errstate(divide="ignore"):
+        Rp = 10 * np.log10(4 * np.pi * np.stack([ym[:, 0] ** 2 + ym[:, 1] ** 2, ym[:, 2] ** 2 + ym[:, 3] ** 2], 1))
+    err = np.max(np.abs(Rp - Rh), axis=1)
+    above = np.min(Rh, axis=1) > -40.0
+    served = spread <= spread_db
+    # hybrid: surrogate for served points, SBR for the rest (timed)
+    fb = [hreq[i] for i in np.nonzero(~served)[0]]
+    t0 = _t.perf_counter()
+    if fb:
+        ctx.run_batch(fb, eta=0.05, max_bounces=10, offset=off)
+    t_fb = _t.perf_counter() - t0
+    # dense lattice query
+    naz, nel = 500, 40
+    nfq = max(1, n_query // (naz * nel))
+    A, El, F = np.meshgrid(np.linspace(0, 360, naz, endpoint=False), np.linspace(-30, 30, nel),
+                           np.exp(np.linspace(np.log(1e9), np.log(12e9), nfq)), indexing="ij")
+    q = np.stack([A.ravel(), El.ravel(), F.ravel()], 1)
+    t0 = _t.perf_counter()
+    _, qs = sur.predict(q)
+    t_q = _t.perf_counter() - t0
+    bands = {}
+    for lo, hi in ((1e9, 3e9), (3e9, 6e9), (6e9, 12.01e9)):
+        m = (hx[:, 2] >= lo) & (hx[:, 2] < hi)
+        sm = m & served
+        bands[f"{lo / 1e9:g}-{min(hi, 12e9) / 1e9:g} GHz"] = {
+            "points": int(m.sum()), "served_fraction": float(sm.sum() / max(1, m.sum())),
+            "served_median_db_error": float(np.median(err[sm])) if sm.any() else None,
+            "served_within_0.5dB": float(np.mean(err[sm] <= 0.5)) if sm.any() else None,
+            "all_median_db_error": float(np.median(err[m])) if m.any() else None}
+    sur.close()
+    ctx.close()
+    return {"training_samples": int(len(x)), "training_aspects": n_aspects, "data_gen_s": t_data,
+            "data_ray_bounces": st["ray_bounces"], "sigma_validation_rel_rms": {str(k): v for k, v in tune.items()},
+            "fourier_sigma": sigma, "tune_s": t_tune, "train_s": t_train, "epochs": epochs,
+            "final_loss_per_member": [float(v) for v in loss[:, -1]],
+            "heldout_points": n_heldout, "plain_sbr_points_per_s": n_heldout / t_sbr,
+            "surrogate_points_per_s": n_heldout / t_pred,
+            "served_fraction": float(served.mean()), "spread_threshold_db": spread_db,
+            "served_median_db_error": float(np.median(err[served])) if served.any() else None,
+            "served_within_0.5dB": float(np.mean(err[served] <= 0.5)) if served.any() else None,
+            "served_above_m40dBsm_within_0.5dB": float(np.mean(err[served & above] <= 0.5))
+            if (served & above).any() else None,
+            "all_median_db_error": float(np.median(err)),
+            "hybrid_points_per_s": n_heldout / (t_pred + t_fb), "hybrid_vs_plain": t_sbr / (t_pred + t_fb),
+            "dense_query_points": int(len(q)), "dense_query_s": t_q,
+            "dense_query_served_fraction": float(np.mean(qs <= spread_db)), "bands": bands}
+
+
+def run_surrogate(args, ws, rank, local, pg):
+    """Surrogate-with-fallback against plain SBR on the aircraft (one replica per rank)."""
+    import torch
+    import paper_2604_09243_gb300 as G
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "the surrogate has no oracle counterpart; "
+                              "its judge is the plain SBR path"}))
+        return
+    torch.cuda.set_device(local)
+    r = surrogate_eval(G, torch, local, n_aspects=args.sur_aspects, n_heldout=args.sur_heldout,
+                       epochs=args.sur_epochs)
+    if rank == 0:
+        print(json.dumps({"metric": "RCS points/s, surrogate with SBR fallback (spread > 1 dB)",
+                          "value": r["hybrid_points_per_s"] * ws, "unit": "points/s", "n_gpus": ws,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+                          "data": "synthetic", "config": {"workload": "aircraft_surrogate", "mesh": "aircraft seed 1",
+                                                          "parallelism": f"replicas{ws}"},
+                          "surrogate": r}))
+
+
 def run_sbr(args, case, ws, rank, local, pg):
     import torch
 
@@ -369,15 +500,23 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sbr", choices=["sbr", "reference"])
     ap.add_argument("--workload", default="trihedral",
-                    choices=["trihedral", "sphere", "aircraft1", "aircraft3", "aircraft10"])
+                    choices=["trihedral", "sphere", "aircraft1", "aircraft3", "aircraft10", "surrogate"])
     ap.add_argument("--ref-angles", type=int, default=24)
     ap.add_argument("--batch-requests", type=int, default=256,
                     help="mixed requests for the batched-vs-plain comparison (0 = skip)")
     ap.add_argument("--aspects", type=int, default=0,
                     help="use this many evenly spaced aspects of the sweep (small profiling cases); 0 = all")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sur-aspects", type=int, default=2000, help="surrogate: training aspects (100 frequencies each)")
+    ap.add_argument("--sur-heldout", type=int, default=10000, help="surrogate: held-out points judged by plain SBR")
+    ap.add_argument("--sur-epochs", type=int, default=60)
     args = ap.parse_args()
     ws, rank, local, pg = dist_setup()
+    if args.workload == "surrogate":
+        run_surrogate(args, ws, rank, local, pg)
+        if pg is not None:
+            pg.destroy_process_group()
+        return
     case = workload(args.workload)
     if args.aspects > 0:
         idx = np.linspace(0, len(case["angles"]) - 1, args.aspects).round().astype(int)

@@ -231,6 +231,61 @@ int sbr_get_hits(sbr_ctx* ctx, int64_t angle, int32_t* tri_ids, float* t, int32_
 int sbr_get_records(sbr_ctx* ctx, int64_t angle, int64_t cap, int64_t* ray_ids, float* coef, double* path,
                     int64_t* n_out);
 
+/* ---- learned surrogate ------------------------------------------------------
+ * A Fourier-feature MLP that learns the complex HH/VV field from SBR samples
+ * (its training data come from sbr_trace/sbr_po_integrate or sbr_run_batch):
+ * inputs (az, el, f) -> (sin az, cos az, el / 30 deg, log f mapped from
+ * [1, 12] GHz to [-1, 1]) -> n_fourier features [sin 2 pi B x, cos 2 pi B x],
+ * B ~ N(0, fourier_sigma^2) -> depth GELU layers of `width` -> 4 outputs
+ * (Re HH, Im HH, Re VV, Im VV). Hidden layers run in BF16 with FP32
+ * accumulation on the tcgen05 tensor-core GEMM (forward and backward); FP32
+ * master weights, Adam, mean-squared error on targets divided by their RMS.
+ * n_members independently initialised networks form an ensemble; the spread
+ * of their |E|^2 in dB marks points where the caller should fall back to SBR. */
+typedef struct sbr_surrogate sbr_surrogate;
+typedef struct {
+    int n_members;       /* ensemble size (default 4) */
+    int width;           /* hidden width, a multiple of 128 (default 512) */
+    int depth;           /* hidden GELU layers, 1..16 (default 6) */
+    int n_fourier;       /* Fourier features, a multiple of 128 (default 256) */
+    float fourier_sigma; /* standard deviation of the Fourier matrix (default 4) */
+    uint64_t seed;       /* initialisation and shuffling seed (default 1) */
+} sbr_surrogate_opts;
+
+/* Create on CUDA device `device`, work ordered on cuda_stream (NULL: own stream); opt NULL = defaults. */
+int sbr_surrogate_create(sbr_surrogate** out, int device, void* cuda_stream, const sbr_surrogate_opts* opt);
+void sbr_surrogate_destroy(sbr_surrogate* s);
+const char* sbr_surrogate_last_error(const sbr_surrogate* s);
+/* Parameters per member: [W_0 (width x n_fourier), b_0, W_1 (width x width), b_1, ..., W_head (4 x width),
+ * b_head (4)], FP32, row-major [out][in]. */
+int64_t sbr_surrogate_num_params(const sbr_surrogate* s);
+/* Copy member `member`'s parameters out to host `get` and/or in from host `set` (either may be NULL). */
+int sbr_surrogate_params(sbr_surrogate* s, int member, float* get, const float* set);
+/* Member `member`'s Fourier matrix B, host float [n_fourier / 2][4]. */
+int sbr_surrogate_fourier(sbr_surrogate* s, int member, float* B);
+/* Train every member for `epochs` epochs of shuffled mini-batches of `batch` samples (a multiple of 128;
+ * an incomplete last batch of an epoch is dropped). x: host double [n][3] = (az deg, el deg, f Hz);
+ * y: host double [n][4] = (Re HH, Im HH, Re VV, Im VV). loss_per_epoch: host float [n_members][epochs]
+ * (mean squared error of the scaled targets) or NULL. Synchronises. */
+int sbr_surrogate_train(sbr_surrogate* s, const double* x, const double* y, int64_t n, int epochs, int batch,
+                        float lr, float* loss_per_epoch);
+/* Loss and parameter gradients of member `member` on one batch (n a multiple of 128), parameters unchanged;
+ * for gradient checks. grads: host float [num_params] in the parameter layout. Targets are divided by
+ * the scale of the last sbr_surrogate_train (1 before any training). */
+int sbr_surrogate_grads(sbr_surrogate* s, int member, const double* x, const double* y, int64_t n, double* loss,
+                        float* grads);
+/* Ensemble prediction at n points x (host double [n][3]): y_mean host double [n][4] (mean over members, in
+ * the units of the training targets) and spread_db host float [n] (over HH and VV, the largest range across
+ * members of 10 log10 |E|^2). Either output may be NULL. Synchronises. */
+int sbr_surrogate_predict(sbr_surrogate* s, const double* x, int64_t n, double* y_mean, float* spread_db);
+
+/* The tensor-core GEMM the surrogate runs on (tcgen05, TMA, FP32 accumulation in tensor memory):
+ * C [M x N] (FP32, device, row stride ldc) = A [M x K] B^T, A and B BF16 on the device with K contiguous
+ * (row strides lda, ldb, multiples of 8). M and N multiples of 128, K a multiple of 64. Synchronises
+ * the stream; SBR_ERR_TIMEOUT if a bounded wait inside the kernel gave up. */
+int sbr_gemm_bf16_tn(const void* A, int lda, const void* B, int ldb, int M, int N, int K, float* C, int ldc,
+                     void* cuda_stream);
+
 /* ---- allocation-free PO sum ------------------------------------------------
  * The paper has no counterpart of this call; it exists for callers that cannot
  * allocate device memory where they need the sum: work recorded into a CUDA

@@ -4,6 +4,7 @@ The compute path lives in ``lib/libsbr.so`` (CUDA, C ABI in ``include/sbr.h``);
 ``sbr`` is its ctypes binding. Build with ``paper_2604_09243_gb300.build.build()``.
 """
 from .sbr import (  # noqa: F401
-    Context, SbrError, lib, ray_grid, spacing_for, version, POL_ORDER, EXPORTS, po_integrate_noalloc,
+    Context, SbrError, Surrogate, gemm_bf16_tn, lib, ray_grid, spacing_for, version, POL_ORDER, EXPORTS,
+    po_integrate_noalloc,
     TRACE_PHASE_LITERAL_2R, TRACE_REQUIRE_ESCAPE, TRACE_RECORD_HITS, TRACE_COUNT_VISITS, TRACE_TIME_PASSES,
 )

@@ -2,6 +2,7 @@
 // translation units of libsbr (not part of the public ABI).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -157,5 +158,24 @@ cudaError_t launch_po(const PoArgs& a, cudaStream_t st);
 // E[row][n_pol][2] and rcs[row][n_pol] for every aspect's rows (fixed-order FP64 sums of the partials)
 cudaError_t launch_po_final(const double* partial, const PoItem* items, const PoAngle* angles, int n_angles,
                             const double* kfreq, int n_pol, double* E, double* rcs, cudaStream_t st);
+
+// ---------------------------------------------------------------- tensor-core GEMM (surrogate)
+// C = A B^T, A [M x K] and B [N x K] BF16 with K contiguous; M, N multiples of
+// 128 and K a multiple of 64. The epilogue is fused:
+enum { kEpiF32 = 0, kEpiBiasGelu = 1, kEpiGeluGrad = 2 };
+struct GemmEpi {
+    int mode;                 // kEpi*
+    int M;                    // rows of C
+    float* c_f32;             // kEpiF32: C; kEpiBiasGelu: z = acc + bias  (row stride ldc)
+    int ldc;
+    __nv_bfloat16* out_bf16;  // kEpiBiasGelu: gelu(z); kEpiGeluGrad: acc * gelu'(z)  (row stride ldo)
+    int ldo;
+    const float* bias;        // kEpiBiasGelu: [N]
+    const float* z;           // kEpiGeluGrad: pre-activation [M x N] (row stride ldz)
+    int ldz;
+};
+bool gemm_shape_ok(int M, int N, int K);
+cudaError_t gemm_bf16_tn(const void* A, int lda, const void* B, int ldb, int M, int N, int K, const GemmEpi& ep,
+                         int* err, cudaStream_t st);
 
 }  // namespace sbr

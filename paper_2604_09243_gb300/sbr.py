@@ -28,7 +28,10 @@ TRACE_PHASE_LITERAL_2R, TRACE_REQUIRE_ESCAPE, TRACE_RECORD_HITS, TRACE_COUNT_VIS
 # every symbol declared in include/sbr.h
 EXPORTS = ("sbr_version", "sbr_create", "sbr_destroy", "sbr_last_error", "sbr_load_mesh", "sbr_get_bbox",
            "sbr_build_bvh", "sbr_ray_grid_for", "sbr_ray_grid_box", "sbr_trace", "sbr_po_integrate", "sbr_get_hits",
-           "sbr_get_records", "sbr_spacing_for", "sbr_po_integrate_noalloc", "sbr_run_batch")
+           "sbr_get_records", "sbr_spacing_for", "sbr_po_integrate_noalloc", "sbr_run_batch",
+           "sbr_surrogate_create", "sbr_surrogate_destroy", "sbr_surrogate_last_error", "sbr_surrogate_num_params",
+           "sbr_surrogate_params", "sbr_surrogate_fourier", "sbr_surrogate_train", "sbr_surrogate_grads",
+           "sbr_surrogate_predict", "sbr_gemm_bf16_tn")
 
 
 class SbrError(RuntimeError):
@@ -345,3 +348,111 @@ class Context:
         self._check(lib().sbr_get_records(self._h, int(angle), cnt, ids.ctypes.data, coef.ctypes.data,
                                           path.ctypes.data, C.byref(n)))
         return dict(ray=ids, coef=coef, L=path)
+
+
+# ---------------------------------------------------------------------------- surrogate
+class SurrogateOpts(C.Structure):
+    _fields_ = [("n_members", C.c_int), ("width", C.c_int), ("depth", C.c_int), ("n_fourier", C.c_int),
+                ("fourier_sigma", C.c_float), ("seed", C.c_uint64)]
+
+
+def _surrogate_sigs(L):
+    P, vp, i64, d = C.POINTER, C.c_void_p, C.c_int64, C.c_double
+    sig = {
+        "sbr_surrogate_create": ([P(vp), C.c_int, vp, P(SurrogateOpts)], C.c_int),
+        "sbr_surrogate_destroy": ([vp], None),
+        "sbr_surrogate_last_error": ([vp], C.c_char_p),
+        "sbr_surrogate_num_params": ([vp], i64),
+        "sbr_surrogate_params": ([vp, C.c_int, vp, vp], C.c_int),
+        "sbr_surrogate_fourier": ([vp, C.c_int, vp], C.c_int),
+        "sbr_surrogate_train": ([vp, vp, vp, i64, C.c_int, C.c_int, C.c_float, vp], C.c_int),
+        "sbr_surrogate_grads": ([vp, C.c_int, vp, vp, i64, P(d), vp], C.c_int),
+        "sbr_surrogate_predict": ([vp, vp, i64, vp, vp], C.c_int),
+        "sbr_gemm_bf16_tn": ([vp, C.c_int, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_int, vp], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    return L
+
+
+def gemm_bf16_tn(A_ptr: int, lda: int, B_ptr: int, ldb: int, M: int, N: int, K: int, C_ptr: int, ldc: int,
+                 stream=None) -> None:
+    """C [M x N] FP32 = A [M x K] B^T on the tensor cores (device pointers; BF16 inputs, K contiguous)."""
+    L = _surrogate_sigs(lib())
+    s = int(getattr(stream, "cuda_stream", stream)) if stream is not None else None
+    rc = L.sbr_gemm_bf16_tn(A_ptr, lda, B_ptr, ldb, M, N, K, C_ptr, ldc, C.c_void_p(s) if s else None)
+    if rc != SBR_OK:
+        raise SbrError(rc, "sbr_gemm_bf16_tn failed")
+
+
+class Surrogate:
+    """Fourier-feature MLP ensemble trained on SBR samples (sbr_surrogate_*)."""
+
+    def __init__(self, device=0, stream=None, n_members=4, width=512, depth=6, n_fourier=256, fourier_sigma=4.0,
+                 seed=1):
+        L = _surrogate_sigs(lib())
+        o = SurrogateOpts(n_members, width, depth, n_fourier, fourier_sigma, seed)
+        h = C.c_void_p()
+        s = int(getattr(stream, "cuda_stream", stream)) if stream is not None else None
+        rc = L.sbr_surrogate_create(C.byref(h), int(device), C.c_void_p(s) if s else None, C.byref(o))
+        if rc != SBR_OK:
+            raise SbrError(rc, "sbr_surrogate_create failed")
+        self._h = h
+        self._stream_ref = stream
+        self.n_members, self.width, self.depth, self.n_fourier = n_members, width, depth, n_fourier
+        self.n_params = int(L.sbr_surrogate_num_params(h))
+
+    def _check(self, rc):
+        if rc != SBR_OK:
+            raise SbrError(rc, (lib().sbr_surrogate_last_error(self._h) or b"").decode())
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().sbr_surrogate_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self, member=0, set_to=None):
+        out = np.empty(self.n_params, np.float32)
+        if set_to is not None:
+            set_to = np.ascontiguousarray(set_to, dtype=np.float32)
+            assert set_to.size == self.n_params
+        self._check(lib().sbr_surrogate_params(self._h, member, out.ctypes.data,
+                                               None if set_to is None else set_to.ctypes.data))
+        return out
+
+    def fourier(self, member=0):
+        B = np.empty((self.n_fourier // 2, 4), np.float32)
+        self._check(lib().sbr_surrogate_fourier(self._h, member, B.ctypes.data))
+        return B
+
+    def train(self, x, y, epochs=10, batch=8192, lr=1e-3):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        loss = np.zeros((self.n_members, epochs), np.float32)
+        self._check(lib().sbr_surrogate_train(self._h, x.ctypes.data, y.ctypes.data, len(x), int(epochs),
+                                              int(batch), float(lr), loss.ctypes.data))
+        return loss
+
+    def grads(self, x, y, member=0):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        g = np.empty(self.n_params, np.float32)
+        loss = C.c_double()
+        self._check(lib().sbr_surrogate_grads(self._h, member, x.ctypes.data, y.ctypes.data, len(x),
+                                              C.byref(loss), g.ctypes.data))
+        return float(loss.value), g
+
+    def predict(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        ym = np.empty((len(x), 4), np.float64)
+        sp = np.empty(len(x), np.float32)
+        self._check(lib().sbr_surrogate_predict(self._h, x.ctypes.data, len(x), ym.ctypes.data, sp.ctypes.data))
+        return ym, sp

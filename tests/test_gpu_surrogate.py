@@ -1,0 +1,80 @@
+"""Learned surrogate: tensor-core GEMM against FP64 numpy, network gradients
+against the FP64 reference network, training and ensemble prediction."""
+import numpy as np
+import pytest
+
+from oracle import mlp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2604_09243_gb300 import build
+
+    build.build()
+    import paper_2604_09243_gb300 as G
+
+    return G
+
+
+@pytest.mark.parametrize("M,N,K,pad", [(128, 128, 64, 0), (256, 384, 512, 0), (1024, 512, 256, 8), (8192, 512, 512, 0)])
+def test_tensor_core_gemm(G, M, N, K, pad):
+    torch = pytest.importorskip("torch")
+    g = torch.Generator().manual_seed(M + N + K)
+    A = torch.randn(M, K + pad, generator=g).to(torch.bfloat16).cuda()
+    B = torch.randn(N, K + pad, generator=g).to(torch.bfloat16).cuda()
+    C = torch.full((M, N), float("nan"), device="cuda")
+    G.gemm_bf16_tn(A.data_ptr(), K + pad, B.data_ptr(), K + pad, M, N, K, C.data_ptr(), N)
+    ref = A[:, :K].double().cpu().numpy() @ B[:, :K].double().cpu().numpy().T
+    got = C.cpu().numpy()
+    assert not np.isnan(got).any()
+    # exact BF16 products, FP32 accumulation
+    assert np.max(np.abs(got - ref)) <= 2e-6 * np.sqrt(K) * np.abs(ref).max()
+
+
+def _samples(n, seed):
+    rng = np.random.default_rng(seed)
+    x = np.stack([rng.uniform(0, 360, n), rng.uniform(-30, 30, n), np.exp(rng.uniform(np.log(1e9), np.log(12e9), n))], 1)
+    return rng, x
+
+
+@pytest.mark.parametrize("width,depth,nf", [(128, 2, 128), (512, 6, 256)])
+def test_gradients_against_fp64_reference(G, width, depth, nf):
+    s = G.Surrogate(0, n_members=1, width=width, depth=depth, n_fourier=nf, fourier_sigma=2.0, seed=3)
+    rng, x = _samples(512, 4)
+    t = rng.normal(0, 1, (512, 4))
+    p = s.params(0).astype(np.float64)
+    B = s.fourier(0).astype(np.float64)
+    loss_g, g = s.grads(x, t)
+    loss_o, go, _ = mlp.loss_and_grads(p, B, x, t, width, depth, nf)
+    assert abs(loss_g - loss_o) <= 0.02 * loss_o
+    lay, n = mlp.layout(width, depth, nf)
+    assert n == s.n_params
+    for l, (o, shp, ob, nb) in enumerate(lay):
+        for a, b in ((o, o + shp[0] * shp[1]), (ob, ob + nb)):
+            u, v = g[a:b].astype(np.float64), go[a:b]
+            cos = np.dot(u, v) / (np.linalg.norm(u) * np.linalg.norm(v) + 1e-300)
+            assert cos > 0.99, (l, cos)
+            assert abs(np.linalg.norm(u) / np.linalg.norm(v) - 1) < 0.05, l
+    s.close()
+
+
+def test_training_reduces_loss_and_ensemble_spread(G):
+    rng, x = _samples(8192, 5)
+    az, el = np.radians(x[:, 0]), np.radians(x[:, 1])
+    lf = np.log(x[:, 2] / 1e9)
+    y = np.stack([np.cos(az) * np.cos(el), np.sin(2 * az), 0.5 * lf * np.cos(az), np.sin(el + az)], 1)
+    s = G.Surrogate(0, n_members=2, width=256, depth=3, n_fourier=128, fourier_sigma=0.3, seed=7)
+    loss = s.train(x, y, epochs=100, batch=1024, lr=2e-3)
+    assert np.all(loss[:, -1] < 0.05 * loss[:, 0]), loss[:, [0, -1]]
+    _, xq = _samples(3000, 6)
+    m1, sp1 = s.predict(xq)
+    m2, sp2 = s.predict(xq)
+    assert np.array_equal(m1, m2) and np.array_equal(sp1, sp2)
+    assert np.all(sp1 >= 0) and np.isfinite(m1).all()
+    azq, elq = np.radians(xq[:, 0]), np.radians(xq[:, 1])
+    yq = np.stack([np.cos(azq) * np.cos(elq), np.sin(2 * azq), 0.5 * np.log(xq[:, 2] / 1e9) * np.cos(azq),
+                   np.sin(elq + azq)], 1)
+    assert np.sqrt(np.mean((m1 - yq) ** 2)) < 0.1 * np.sqrt(np.mean(yq ** 2))
+    s.close()
