@@ -247,31 +247,43 @@ def batched_vs_plain(G, torch, dev, n_req):
             "batched_ray_bounces_per_s": rb / tb, "timing": "host wall clock, one pass each after one warm-up pass"}
 
 
-def surrogate_eval(G, torch, dev, n_aspects=2000, f_per=100, n_heldout=10000, n_query=1_000_000, epochs=60,
-                   spread_db=1.0, sigmas=(1.0, 2.0, 4.0, 8.0, 16.0)):
-    """Learned surrogate on the aircraft mesh against plain SBR.
+SURROGATE_DOMAINS = {
+    # the configured case: the whole sweep space, 200k samples
+    "full": dict(az=(0.0, 360.0), el=(-30.0, 30.0), f=(1e9, 12e9), n_aspects=2000, f_per=100, n_heldout=10000,
+                 lattice=(500, 40, 50), sigmas=(1.0, 4.0, 16.0, 64.0)),
+    # a dense sweep patch around nose-on: 4 deg x 2 deg x 1.0-1.2 GHz, 200k samples
+    "patch": dict(az=(178.0, 182.0), el=(-1.0, 1.0), f=(1e9, 1.2e9), n_aspects=2000, f_per=100, n_heldout=10000,
+                  lattice=(100, 20, 500), sigmas=(16.0, 32.0, 64.0, 128.0, 256.0)),
+}
 
-    Training data: ``n_aspects`` aspects (az U[0, 360), el U[-30, 30], seed 3),
-    each with ``f_per`` frequencies log-uniform in [1, 12] GHz, traced once at
-    10 rays per wavelength of its highest frequency (batched form) -> samples
-    (az, el, f) -> (Re, Im of HH and VV). Held out: ``n_heldout`` points
-    (seed 4), each its own aspect and frequency, computed by SBR. The ensemble
-    answers a point when its spread is <= ``spread_db``; otherwise SBR does."""
+
+def surrogate_eval(G, torch, ctx, dom, epochs=60, batch=2048, spread_db=1.0, scale=1.0):
+    """Learned surrogate on the aircraft mesh against plain SBR over one domain.
+
+    Training data: ``n_aspects`` aspects uniform over the domain's (az, el) box
+    (seed 3), each with ``f_per`` frequencies log-uniform over its band, traced
+    once at 10 rays per wavelength of its highest frequency (batched form) ->
+    samples (az, el, f) -> (Re, Im of HH and VV). sigma_B is picked on a 90/10
+    split. Held out: ``n_heldout`` points (seed 4), each its own aspect and
+    frequency, computed by plain SBR at 10 rays per wavelength of that
+    frequency. The ensemble answers a point when its spread is <= ``spread_db``;
+    otherwise SBR does. ``scale`` shrinks the sample counts (quick runs)."""
     import time as _t
 
-    xyz, tri = S.aircraft(seed=1)
     off = S.grid_offset(6)
-    ctx = G.Context(dev)
-    ctx.load_mesh(xyz, tri)
+    n_aspects = max(8, int(dom["n_aspects"] * scale))
+    n_heldout = max(64, int(dom["n_heldout"] * scale))
+    f_per = dom["f_per"]
+    (a0, a1), (e0, e1), (f0, f1) = dom["az"], dom["el"], dom["f"]
     rng = np.random.default_rng(3)
     reqs = []
     for _ in range(n_aspects):
-        f = np.sort(np.exp(rng.uniform(np.log(1e9), np.log(12e9), f_per)))
-        reqs.append(dict(az=float(rng.uniform(0, 360)), el=float(rng.uniform(-30, 30)), freqs=f,
+        f = np.sort(np.exp(rng.uniform(np.log(f0), np.log(f1), f_per)))
+        reqs.append(dict(az=float(rng.uniform(a0, a1)), el=float(rng.uniform(e0, e1)), freqs=f,
                          spacing=S.spacing_for(float(f[-1]), 10.0)))
     torch.cuda.synchronize()
     t0 = _t.perf_counter()
-    E, R, st = ctx.run_batch(reqs, eta=0.05, max_bounces=10, offset=off)
+    E, _, st = ctx.run_batch(reqs, eta=0.05, max_bounces=10, offset=off)
     t_data = _t.perf_counter() - t0
     x = np.concatenate([np.stack([np.full(len(r["freqs"]), r["az"]), np.full(len(r["freqs"]), r["el"]), r["freqs"]], 1)
                         for r in reqs])
@@ -283,22 +295,22 @@ def surrogate_eval(G, torch, dev, n_aspects=2000, f_per=100, n_heldout=10000, n_
     cut = (int(0.9 * len(x)) // 128) * 128
     tr, va = perm[:cut], perm[cut:]
     tune = {}
-    for sig in sigmas:
-        m = G.Surrogate(dev, n_members=1, width=512, depth=6, n_fourier=256, fourier_sigma=sig, seed=11)
-        m.train(x[tr], y[tr], epochs=max(1, epochs // 4), batch=8192, lr=1e-3)
+    for sig in dom["sigmas"]:
+        m = G.Surrogate(ctx.device, n_members=1, width=512, depth=6, n_fourier=256, fourier_sigma=sig, seed=11)
+        m.train(x[tr], y[tr], epochs=max(1, epochs // 4), batch=batch, lr=1e-3)
         yv, _ = m.predict(x[va])
         m.close()
         tune[sig] = float(np.sqrt(np.mean((yv - y[va]) ** 2)) / np.sqrt(np.mean(y[va] ** 2)))
     sigma = min(tune, key=tune.get)
     t_tune = _t.perf_counter() - t0
-    sur = G.Surrogate(dev, n_members=4, width=512, depth=6, n_fourier=256, fourier_sigma=sigma, seed=1)
+    sur = G.Surrogate(ctx.device, n_members=4, width=512, depth=6, n_fourier=256, fourier_sigma=sigma, seed=1)
     t0 = _t.perf_counter()
-    loss = sur.train(x, y, epochs=epochs, batch=8192, lr=1e-3)
+    loss = sur.train(x, y, epochs=epochs, batch=batch, lr=1e-3)
     t_train = _t.perf_counter() - t0
-    # held-out points, plain SBR (batched, one frequency per aspect)
+    # held-out points, plain SBR (one frequency per aspect)
     rng = np.random.default_rng(4)
-    hx = np.stack([rng.uniform(0, 360, n_heldout), rng.uniform(-30, 30, n_heldout),
-                   np.exp(rng.uniform(np.log(1e9), np.log(12e9), n_heldout))], 1)
+    hx = np.stack([rng.uniform(a0, a1, n_heldout), rng.uniform(e0, e1, n_heldout),
+                   np.exp(rng.uniform(np.log(f0), np.log(f1), n_heldout))], 1)
     hreq = [dict(az=a, el=e, freqs=np.array([f]), spacing=S.spacing_for(f, 10.0)) for a, e, f in hx]
     torch.cuda.synchronize()
     t0 = _t.perf_counter()
@@ -319,29 +331,42 @@ def surrogate_eval(G, torch, dev, n_aspects=2000, f_per=100, n_heldout=10000, n_
     if fb:
         ctx.run_batch(fb, eta=0.05, max_bounces=10, offset=off)
     t_fb = _t.perf_counter() - t0
-    # dense lattice query
-    naz, nel = 500, 40
-    nfq = max(1, n_query // (naz * nel))
-    A, El, F = np.meshgrid(np.linspace(0, 360, naz, endpoint=False), np.linspace(-30, 30, nel),
-                           np.exp(np.linspace(np.log(1e9), np.log(12e9), nfq)), indexing="ij")
+    # dense (az, el, log f) lattice: surrogate query, and SBR on the same lattice (each aspect traced once)
+    naz, nel, nfq = dom["lattice"]
+    if scale < 1.0:
+        naz = max(4, int(naz * scale))
+    la, le = np.linspace(a0, a1, naz), np.linspace(e0, e1, nel)
+    lf = np.exp(np.linspace(np.log(f0), np.log(f1), nfq))
+    A, El, F = np.meshgrid(la, le, lf, indexing="ij")
     q = np.stack([A.ravel(), El.ravel(), F.ravel()], 1)
     t0 = _t.perf_counter()
     _, qs = sur.predict(q)
     t_q = _t.perf_counter() - t0
+    lat_aspects = naz * nel
+    n_lat_sbr = min(lat_aspects, 256)
+    pick = np.linspace(0, lat_aspects - 1, n_lat_sbr).round().astype(int)
+    lreq = [dict(az=float(la[k // nel]), el=float(le[k % nel]), freqs=lf, spacing=S.spacing_for(f1, 10.0))
+            for k in pick]
+    torch.cuda.synchronize()
+    t0 = _t.perf_counter()
+    ctx.run_batch(lreq, eta=0.05, max_bounces=10, offset=off)
+    t_lat = (_t.perf_counter() - t0) * lat_aspects / n_lat_sbr
     bands = {}
-    for lo, hi in ((1e9, 3e9), (3e9, 6e9), (6e9, 12.01e9)):
+    edges = np.exp(np.linspace(np.log(f0), np.log(f1), 4))
+    edges[-1] *= 1.0001
+    for lo, hi in zip(edges[:-1], edges[1:]):
         m = (hx[:, 2] >= lo) & (hx[:, 2] < hi)
         sm = m & served
-        bands[f"{lo / 1e9:g}-{min(hi, 12e9) / 1e9:g} GHz"] = {
+        bands[f"{lo / 1e9:.3g}-{min(hi, f1) / 1e9:.3g} GHz"] = {
             "points": int(m.sum()), "served_fraction": float(sm.sum() / max(1, m.sum())),
             "served_median_db_error": float(np.median(err[sm])) if sm.any() else None,
             "served_within_0.5dB": float(np.mean(err[sm] <= 0.5)) if sm.any() else None,
             "all_median_db_error": float(np.median(err[m])) if m.any() else None}
     sur.close()
-    ctx.close()
-    return {"training_samples": int(len(x)), "training_aspects": n_aspects, "data_gen_s": t_data,
-            "data_ray_bounces": st["ray_bounces"], "sigma_validation_rel_rms": {str(k): v for k, v in tune.items()},
-            "fourier_sigma": sigma, "tune_s": t_tune, "train_s": t_train, "epochs": epochs,
+    return {"domain": {k: dom[k] for k in ("az", "el", "f")}, "training_samples": int(len(x)),
+            "training_aspects": n_aspects, "data_gen_s": t_data, "data_ray_bounces": st["ray_bounces"],
+            "sigma_validation_rel_rms": {str(k): v for k, v in tune.items()}, "fourier_sigma": sigma,
+            "tune_s": t_tune, "train_s": t_train, "epochs": epochs, "batch": batch,
             "final_loss_per_member": [float(v) for v in loss[:, -1]],
             "heldout_points": n_heldout, "plain_sbr_points_per_s": n_heldout / t_sbr,
             "surrogate_points_per_s": n_heldout / t_pred,
@@ -352,8 +377,10 @@ def surrogate_eval(G, torch, dev, n_aspects=2000, f_per=100, n_heldout=10000, n_
             if (served & above).any() else None,
             "all_median_db_error": float(np.median(err)),
             "hybrid_points_per_s": n_heldout / (t_pred + t_fb), "hybrid_vs_plain": t_sbr / (t_pred + t_fb),
-            "dense_query_points": int(len(q)), "dense_query_s": t_q,
-            "dense_query_served_fraction": float(np.mean(qs <= spread_db)), "bands": bands}
+            "lattice_points": int(len(q)), "lattice_surrogate_s": t_q,
+            "lattice_served_fraction": float(np.mean(qs <= spread_db)),
+            "lattice_sbr_s": t_lat, "lattice_sbr_sample": f"{n_lat_sbr} of {lat_aspects} lattice aspects, scaled",
+            "bands": bands}
 
 
 def run_surrogate(args, ws, rank, local, pg):
@@ -367,15 +394,22 @@ def run_surrogate(args, ws, rank, local, pg):
                               "its judge is the plain SBR path"}))
         return
     torch.cuda.set_device(local)
-    r = surrogate_eval(G, torch, local, n_aspects=args.sur_aspects, n_heldout=args.sur_heldout,
-                       epochs=args.sur_epochs)
+    xyz, tri = S.aircraft(seed=1)
+    ctx = G.Context(local)
+    ctx.load_mesh(xyz, tri)
+    res = {}
+    for name in args.sur_domains.split(","):
+        res[name] = surrogate_eval(G, torch, ctx, SURROGATE_DOMAINS[name], epochs=args.sur_epochs,
+                                   scale=args.sur_scale)
+    ctx.close()
+    head = res[args.sur_domains.split(",")[0]]
     if rank == 0:
         print(json.dumps({"metric": "RCS points/s, surrogate with SBR fallback (spread > 1 dB)",
-                          "value": r["hybrid_points_per_s"] * ws, "unit": "points/s", "n_gpus": ws,
+                          "value": head["hybrid_points_per_s"] * ws, "unit": "points/s", "n_gpus": ws,
                           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
                           "data": "synthetic", "config": {"workload": "aircraft_surrogate", "mesh": "aircraft seed 1",
                                                           "parallelism": f"replicas{ws}"},
-                          "surrogate": r}))
+                          "surrogate": res}))
 
 
 def run_sbr(args, case, ws, rank, local, pg):
@@ -507,8 +541,8 @@ def main():
     ap.add_argument("--aspects", type=int, default=0,
                     help="use this many evenly spaced aspects of the sweep (small profiling cases); 0 = all")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--sur-aspects", type=int, default=2000, help="surrogate: training aspects (100 frequencies each)")
-    ap.add_argument("--sur-heldout", type=int, default=10000, help="surrogate: held-out points judged by plain SBR")
+    ap.add_argument("--sur-domains", default="full,patch", help="surrogate: domains to evaluate")
+    ap.add_argument("--sur-scale", type=float, default=1.0, help="surrogate: fraction of the sample counts")
     ap.add_argument("--sur-epochs", type=int, default=60)
     args = ap.parse_args()
     ws, rank, local, pg = dist_setup()

@@ -266,7 +266,8 @@ int sbr_surrogate_fourier(sbr_surrogate* s, int member, float* B);
 /* Train every member for `epochs` epochs of shuffled mini-batches of `batch` samples (a multiple of 128;
  * an incomplete last batch of an epoch is dropped). x: host double [n][3] = (az deg, el deg, f Hz);
  * y: host double [n][4] = (Re HH, Im HH, Re VV, Im VV). loss_per_epoch: host float [n_members][epochs]
- * (mean squared error of the scaled targets) or NULL. Synchronises. */
+ * (mean squared error of the scaled targets) or NULL. Adam (0.9, 0.999); the learning rate follows a
+ * cosine schedule from `lr` down to lr / 100 over the call's steps. Synchronises. */
 int sbr_surrogate_train(sbr_surrogate* s, const double* x, const double* y, int64_t n, int epochs, int batch,
                         float lr, float* loss_per_epoch);
 /* Loss and parameter gradients of member `member` on one batch (n a multiple of 128), parameters unchanged;

@@ -140,32 +140,78 @@ __global__ void k_head_bwd_dz(const float* dy, const float* W, const float* z, i
     dz[i] = __float2bfloat16_rn(s * gelu_grad_f(z[i]));
 }
 
-// dW[o][k] = sum_m dy[m][o] h[m][k]; db[o] = sum_m dy[m][o]  (one thread per k, k < K; thread K does db)
-__global__ void k_head_bwd_dw(const float* dy, const __nv_bfloat16* h, int M, int K, float* dW, float* db)
+// Column sums over the batch in two fixed-order stages (deterministic): stage 1
+// gives one partial per kRedRows rows (block 32 columns x 8 row lanes), stage 2
+// adds the partials in order.
+constexpr int kRedRows = 256;
+
+// head gradient, stage 1: part[p][o][k] = sum over rows m of chunk p of dy[m][o] h[m][k]
+// (k < K) and of dy[m][o] (k = K, the bias)
+__global__ void k_head_dw_part(const float* dy, const __nv_bfloat16* h, int M, int K, float* part)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k > K) return;
+    __shared__ float sh[8][kOut][33];
+    const int k = blockIdx.x * 32 + threadIdx.x, p = blockIdx.y;
     float acc[kOut] = {0.f, 0.f, 0.f, 0.f};
-    for (int m = 0; m < M; ++m) {
-        const float v = k < K ? __bfloat162float(h[(size_t)m * K + k]) : 1.f;
+    if (k <= K) {
+        const int r1 = min(M, (p + 1) * kRedRows);
+#pragma unroll 4
+        for (int m = p * kRedRows + threadIdx.y; m < r1; m += 8) {
+            const float v = k < K ? __bfloat162float(h[(size_t)m * K + k]) : 1.f;
 #pragma unroll
-        for (int o = 0; o < kOut; ++o) acc[o] = fmaf(dy[m * kOut + o], v, acc[o]);
+            for (int o = 0; o < kOut; ++o) acc[o] = fmaf(dy[m * kOut + o], v, acc[o]);
+        }
     }
 #pragma unroll
-    for (int o = 0; o < kOut; ++o) {
-        if (k < K) dW[o * K + k] = acc[o];
-        else db[o] = acc[o];
+    for (int o = 0; o < kOut; ++o) sh[threadIdx.y][o][threadIdx.x] = acc[o];
+    __syncthreads();
+    if (threadIdx.y < kOut && k <= K) {
+        const int o = threadIdx.y;
+        float t = 0.f;
+        for (int y = 0; y < 8; ++y) t += sh[y][o][threadIdx.x];
+        part[((size_t)p * kOut + o) * (K + 1) + k] = t;
     }
 }
 
-// db[n] = sum_m dz[m][n]
-__global__ void k_colsum(const __nv_bfloat16* dz, int M, int N, float* db)
+// head gradient, stage 2: dW[o][k], db[o] = sum over the P partials
+__global__ void k_head_dw_fin(const float* part, int P, int K, float* dW, float* db)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= kOut * (K + 1)) return;
+    const int o = j / (K + 1), k = j % (K + 1);
+    float t = 0.f;
+    for (int q = 0; q < P; ++q) t += part[((size_t)q * kOut + o) * (K + 1) + k];
+    if (k < K) dW[o * K + k] = t;
+    else db[o] = t;
+}
+
+// bias gradient, stage 1: part[p][n] = sum over rows m of chunk p of dz[m][n]
+__global__ void k_colsum_part(const __nv_bfloat16* dz, int M, int N, float* part)
+{
+    __shared__ float sh[8][33];
+    const int n = blockIdx.x * 32 + threadIdx.x, p = blockIdx.y;
+    float acc = 0.f;
+    if (n < N) {
+        const int r1 = min(M, (p + 1) * kRedRows);
+#pragma unroll 4
+        for (int m = p * kRedRows + threadIdx.y; m < r1; m += 8) acc += __bfloat162float(dz[(size_t)m * N + n]);
+    }
+    sh[threadIdx.y][threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.y == 0 && n < N) {
+        float t = 0.f;
+        for (int y = 0; y < 8; ++y) t += sh[y][threadIdx.x];
+        part[(size_t)p * N + n] = t;
+    }
+}
+
+// bias gradient, stage 2
+__global__ void k_colsum_fin(const float* part, int P, int N, float* db)
 {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    float s = 0.f;
-    for (int m = 0; m < M; ++m) s += __bfloat162float(dz[(size_t)m * N + n]);
-    db[n] = s;
+    float t = 0.f;
+    for (int q = 0; q < P; ++q) t += part[(size_t)q * N + n];
+    db[n] = t;
 }
 
 // out[c][r] = in[r][c] for a [R x Cc] BF16 matrix, 32 x 32 tiles through shared memory
@@ -258,6 +304,7 @@ struct sbr_surrogate {
     std::vector<__nv_bfloat16*> dz;  // dz[l] BF16 [cap x N_l]
     __nv_bfloat16 *dzT = nullptr, *hT = nullptr;
     float *y = nullptr, *dy = nullptr, *xb = nullptr, *yb = nullptr;
+    float* red = nullptr;  // partial column sums [cap / 256 x 4 (width + 1)]
     double* loss = nullptr;
     int* gerr = nullptr;
     int* idx = nullptr;
@@ -300,6 +347,7 @@ int ensure_cap(sbr_surrogate* s, int M)
     fr(s->xb);
     fr(s->yb);
     fr(s->idx);
+    fr(s->red);
     s->h.assign(D + 1, nullptr);
     s->z.assign(D, nullptr);
     s->dz.assign(D, nullptr);
@@ -316,6 +364,8 @@ int ensure_cap(sbr_surrogate* s, int M)
     SCK(cudaMalloc(&s->xb, sizeof(float) * (size_t)M * kIn), "alloc xb");
     SCK(cudaMalloc(&s->yb, sizeof(float) * (size_t)M * kOut), "alloc yb");
     SCK(cudaMalloc(&s->idx, sizeof(int) * (size_t)M), "alloc idx");
+    SCK(cudaMalloc(&s->red, sizeof(float) * (size_t)((M + kRedRows - 1) / kRedRows) * kOut * (wmax + 1)),
+        "alloc partial sums");
     s->cap = M;
     return SBR_OK;
 }
@@ -369,7 +419,10 @@ int backward(sbr_surrogate* s, int e, int M, double* lacc = nullptr)
         cudaMemsetAsync(lacc, 0, sizeof(double), s->stream);
     }
     k_loss<<<blocks((long long)M * kOut, 256), 256, 0, s->stream>>>(s->y, s->yb, M * kOut, s->dy, lacc);
-    k_head_bwd_dw<<<blocks(W + 1, 128), 128, 0, s->stream>>>(s->dy, s->h[D], M, W, s->G + s->offW[D], s->G + s->offb[D]);
+    const int P = (M + kRedRows - 1) / kRedRows;
+    k_head_dw_part<<<dim3((W + 1 + 31) / 32, P), dim3(32, 8), 0, s->stream>>>(s->dy, s->h[D], M, W, s->red);
+    k_head_dw_fin<<<blocks(kOut * (W + 1), 256), 256, 0, s->stream>>>(s->red, P, W, s->G + s->offW[D],
+                                                                        s->G + s->offb[D]);
     k_head_bwd_dz<<<blocks((long long)M * W, 256), 256, 0, s->stream>>>(s->dy, s->P[e] + s->offW[D], s->z[D - 1], M, W,
                                                                          s->dz[D - 1]);
     for (int l = D - 1; l >= 0; --l) {
@@ -384,7 +437,8 @@ int backward(sbr_surrogate* s, int e, int M, double* lacc = nullptr)
         ep.c_f32 = s->G + s->offW[l];
         ep.ldc = s->K[l];
         SCK(gemm_bf16_tn(s->dzT, M, s->hT, M, s->N[l], s->K[l], M, ep, s->gerr, s->stream), "weight-gradient gemm");
-        k_colsum<<<blocks(s->N[l], 128), 128, 0, s->stream>>>(s->dz[l], M, s->N[l], s->G + s->offb[l]);
+        k_colsum_part<<<dim3((s->N[l] + 31) / 32, P), dim3(32, 8), 0, s->stream>>>(s->dz[l], M, s->N[l], s->red);
+        k_colsum_fin<<<blocks(s->N[l], 256), 256, 0, s->stream>>>(s->red, P, s->N[l], s->G + s->offb[l]);
         if (l > 0) {
             // dz_{l-1} = (dz_l W_l) * gelu'(z_{l-1}) : A = dz_l [M x N], B = W_l^T [K x N]
             GemmEpi eg;
@@ -595,6 +649,7 @@ void sbr_surrogate_destroy(sbr_surrogate* s)
     fr(s->loss);
     fr(s->gerr);
     fr(s->idx);
+    fr(s->red);
     if (s->own_stream) cudaStreamDestroy(s->stream);
     delete s;
 }
@@ -690,9 +745,11 @@ int sbr_surrogate_train(sbr_surrogate* s, const double* x, const double* y, int6
     std::vector<int> perm((size_t)n);
     std::vector<double> hloss((size_t)epochs);
     cudaMemsetAsync(s->gerr, 0, sizeof(int), s->stream);
+    const double total_steps = (double)epochs * (double)steps_per_epoch;
     for (int e = 0; e < s->opt.n_members && rc == SBR_OK; ++e) {
         std::mt19937_64 rng(s->opt.seed * 7919 + (uint64_t)e);
         cudaMemsetAsync(dloss, 0, sizeof(double) * (size_t)epochs, s->stream);
+        long long call_step = 0;
         for (int ep = 0; ep < epochs && rc == SBR_OK; ++ep) {
             for (int64_t i = 0; i < n; ++i) perm[(size_t)i] = (int)i;
             std::shuffle(perm.begin(), perm.end(), rng);
@@ -710,8 +767,11 @@ int sbr_surrogate_train(sbr_surrogate* s, const double* x, const double* y, int6
                 const long long t = ++s->steps[(size_t)e];
                 const float b1 = 0.9f, b2 = 0.999f;
                 const float c1 = 1.f / (1.f - powf(b1, (float)t)), c2 = 1.f / (1.f - powf(b2, (float)t));
+                // cosine schedule lr -> lr / 100 over this call
+                const double ph = (double)(call_step++) / std::max(1.0, total_steps - 1.0);
+                const float lr_t = (float)(lr * (0.01 + 0.99 * 0.5 * (1.0 + cos(kPi * ph))));
                 k_adam<<<blocks(s->n_params, 256), 256, 0, s->stream>>>(s->P[e], s->Pm[e], s->Pv[e], s->G,
-                                                                         s->n_params, lr, b1, b2, c1, c2, 1e-8f);
+                                                                         s->n_params, lr_t, b1, b2, c1, c2, 1e-8f);
                 rc = refresh_bf16(s, e);
             }
         }
