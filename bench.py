@@ -231,20 +231,43 @@ def batched_vs_plain(G, torch, dev, n_req):
                 ctxs[m].po_integrate(r["freqs"], "HH,VV")
         torch.cuda.synchronize()
 
+    rows = [sum(len(r["freqs"]) for r in groups[m]) for m in range(3)]
+    outs = [torch.zeros((max(1, rows[m]), 2), dtype=torch.float64, device=f"cuda:{dev}") for m in range(3)]
+    torch.cuda.synchronize()
+
+    def graphed():
+        # one asynchronous submission per mesh (each context has its own stream), then wait for all
+        for m in range(3):
+            if groups[m]:
+                ctxs[m].submit_batch(groups[m], None, outs[m], eta=0.05, max_bounces=bounces[m], offset=offs[m])
+        return sum(ctxs[m].sync()["ray_bounces"] for m in range(3) if groups[m])
+
     batched()
     plain()
+    graphed()
     t0 = _t.perf_counter()
     rb = batched()
     tb = _t.perf_counter() - t0
     t0 = _t.perf_counter()
     plain()
     tp = _t.perf_counter() - t0
+    t0 = _t.perf_counter()
+    rg = graphed()
+    tg = _t.perf_counter() - t0
+    same = True
+    for m in range(3):
+        if groups[m]:
+            _, Rb, _ = ctxs[m].run_batch(groups[m], eta=0.05, max_bounces=bounces[m], offset=offs[m])
+            same = same and bool(np.array_equal(outs[m][:rows[m]].cpu().numpy(), np.concatenate(Rb)))
     for c in ctxs:
         c.close()
     return {"requests": n_req, "meshes": "icosphere5 / trihedral / aircraft (1M)",
             "frequencies": int(sum(len(r["freqs"]) for r in reqs)),
             "batched_requests_per_s": n_req / tb, "plain_requests_per_s": n_req / tp, "speedup": tp / tb,
-            "batched_ray_bounces_per_s": rb / tb, "timing": "host wall clock, one pass each after one warm-up pass"}
+            "graph_requests_per_s": n_req / tg, "graph_speedup": tp / tg, "graph_equals_batched": same,
+            "batched_ray_bounces_per_s": rb / tb, "graph_ray_bounces_per_s": rg / tg,
+            "timing": "host wall clock, one pass each after one warm-up pass; graph = sbr_submit_batch replay "
+                      "(one CUDA graph per mesh, three streams) + sbr_sync"}
 
 
 SURROGATE_DOMAINS = {

@@ -66,6 +66,7 @@ extern "C" {
 #define SBR_TRACE_RECORD_HITS 4      /* keep per-ray, per-bounce hits for sbr_get_hits */
 #define SBR_TRACE_COUNT_VISITS 8     /* count node visits and triangle tests into the stats */
 #define SBR_TRACE_TIME_PASSES 16     /* time each transport pass with CUDA events into the stats */
+#define SBR_TRACE_NO_GRAPH 32        /* sbr_submit_batch: enqueue the kernels directly, no CUDA graph */
 
 typedef struct sbr_ctx sbr_ctx; /* opaque; owns the device copies of mesh, BVH and ray buffers */
 
@@ -217,6 +218,33 @@ typedef struct {
 int sbr_run_batch(sbr_ctx* ctx, const sbr_request* req, int64_t n_req, const double* freq_hz, int64_t n_freq_total,
                   double margin_eta, int max_bounces, int pol_mask, int po_mode, const sbr_trace_opts* opt,
                   double* E_re_im, double* rcs_dbsm, int out_on_device, sbr_trace_stats* stats);
+
+/* Batched trace-integrate, asynchronous (same requests, frequency array,
+ * options and output layout as sbr_run_batch, and the same results bit for
+ * bit). The PO work lists are built on the device from the record counts, so
+ * the whole batch runs with no host synchronisation: it is captured once as
+ * one CUDA graph and launched on the ctx stream, and the call returns without
+ * waiting. Submitting the same arguments again (requests, frequencies, eta,
+ * bounces, polarisations, mode, options and output pointers) on the same mesh
+ * replays the captured graph without planning again.
+ *   E_dev, rcs_dev: DEVICE memory (either may be NULL) laid out as in
+ *   sbr_run_batch; written when the ctx stream reaches the end of the graph.
+ *   opt->flags: SBR_TRACE_REQUIRE_ESCAPE, SBR_TRACE_COUNT_VISITS as for
+ *   sbr_trace; SBR_TRACE_NO_GRAPH enqueues the kernels directly each time;
+ *   SBR_TRACE_RECORD_HITS and SBR_TRACE_TIME_PASSES are refused.
+ * The plan owns its device buffers (ray queues for its largest chunk, record
+ * and partial buffers sized for every ray being valid) until a submit with
+ * other arguments or sbr_destroy; sbr_trace results are left untouched.
+ * Errors found while planning are returned here; kernel-side conditions
+ * (stack overflow) by sbr_sync. No counterpart in the paper: the paper's
+ * sweep is a host loop over aspects. */
+int sbr_submit_batch(sbr_ctx* ctx, const sbr_request* req, int64_t n_req, const double* freq_hz,
+                     int64_t n_freq_total, double margin_eta, int max_bounces, int pol_mask, int po_mode,
+                     const sbr_trace_opts* opt, double* E_dev, double* rcs_dev);
+/* Wait for the last submitted batch and report its statistics as
+ * sbr_run_batch does (kernel_launches: kernels per run of the batch).
+ * SBR_ERR_STATE if nothing was submitted. */
+int sbr_sync(sbr_ctx* ctx, sbr_trace_stats* stats);
 
 /* Per-ray hits of traced aspect `angle` (needs SBR_TRACE_RECORD_HITS), for
  * parity checks; ray id = j * nu + i. Host outputs (any may be NULL):

@@ -7,4 +7,5 @@ from .sbr import (  # noqa: F401
     Context, SbrError, Surrogate, gemm_bf16_tn, lib, ray_grid, spacing_for, version, POL_ORDER, EXPORTS,
     po_integrate_noalloc,
     TRACE_PHASE_LITERAL_2R, TRACE_REQUIRE_ESCAPE, TRACE_RECORD_HITS, TRACE_COUNT_VISITS, TRACE_TIME_PASSES,
+    TRACE_NO_GRAPH,
 )

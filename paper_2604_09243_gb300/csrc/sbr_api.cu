@@ -22,7 +22,6 @@ namespace {
 constexpr double kC0 = 299792458.0;
 constexpr double kPi = 3.14159265358979323846;
 constexpr long long kChunkRays = 1ll << 27;  // rays per trace chunk (queues: 2 x 12.9 GB at this size)
-constexpr int kPoItem = 1024;                 // records per PO item (matches sbr_po.cu)
 constexpr int kMaxBounces = 64;
 
 std::string g_create_error;
@@ -66,6 +65,9 @@ struct AngleHost {
     long long rec_begin, rec_count;
 };
 
+struct BatchPlan;
+void free_plan(BatchPlan* p);
+
 }  // namespace
 
 struct sbr_ctx {
@@ -95,6 +97,10 @@ struct sbr_ctx {
     size_t host_stage_cap = 0;
     cudaEvent_t stage_ev = nullptr;  // recorded after the last enqueued copy that touches host_stage
     std::vector<cudaEvent_t> evpool; // pass timing events (SBR_TRACE_TIME_PASSES)
+    // asynchronous batches (sbr_submit_batch)
+    long long mesh_gen = 0;  // bumped whenever the BVH buffers change
+    BatchPlan* plan = nullptr;
+    bool plan_pending = false;
 };
 
 namespace {
@@ -307,6 +313,7 @@ void sbr_destroy(sbr_ctx* c)
     if (c->host_stage) cudaFreeHost(c->host_stage);
     if (c->stage_ev) cudaEventDestroy(c->stage_ev);
     for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
+    free_plan(c->plan);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -353,6 +360,7 @@ int sbr_build_bvh(sbr_ctx* c, const sbr_bvh_opts* opt)
     if (leaf_max < 1 || leaf_max > kLeafMax) return fail(c, SBR_ERR_ARG, "sbr_build_bvh: leaf_max must be 1..16");
     if (!(ct >= 0.f) || !(ci > 0.f)) return fail(c, SBR_ERR_ARG, "sbr_build_bvh: costs must be C_T >= 0, C_I > 0");
     CK(cudaSetDevice(c->device), "cudaSetDevice");
+    ++c->mesh_gen;  // captured batch graphs hold the node and triangle pointers
     const long long n = c->n_tri;
     const long long n_nodes = n > 1 ? n - 1 : 1;
     CK(c->nodes.ensure(sizeof(float4) * 4 * (size_t)n_nodes), "alloc nodes");
@@ -697,12 +705,12 @@ int po_run(sbr_ctx* c, PoArgs pa, int64_t a0, int64_t a1, const std::vector<int>
         A.f0 = f0[(size_t)(a0 + i)];
         A.nf = nf[(size_t)(a0 + i)];
         A.out_row = out_row[(size_t)(a0 + i)];
-        A.pad = 0;
-        for (long long r = 0; r < h.rec_count; r += kPoItem) {
+        A.part = 0;
+        for (long long r = 0; r < h.rec_count; r += kPoItemRecords) {
             PoItem it;
             it.angle = i;
             it.first = h.rec_begin + r;
-            it.count = (int)std::min<long long>(kPoItem, h.rec_count - r);
+            it.count = (int)std::min<long long>(kPoItemRecords, h.rec_count - r);
             it.f0 = A.f0;
             it.nf = A.nf;
             it.part = part;
@@ -733,6 +741,263 @@ int po_run(sbr_ctx* c, PoArgs pa, int64_t a0, int64_t a1, const std::vector<int>
     CK(launch_po_final(pa.partial, pa.items, c->itemoff.as<PoAngle>(), na, pa.kfreq, pa.n_pol, dE, dR, c->stream),
        "po final");
     if (n_launch) *n_launch += (n_items > 0 ? 1 : 0) + 1;
+    return SBR_OK;
+}
+
+// ---------------------------------------------------------------- asynchronous batches
+// A plan holds one submitted batch: its ray grids cut into chunks, device
+// tables uploaded once, buffers sized for the worst case (every ray valid) and
+// the captured CUDA graph of the whole batch.
+struct BatchPlan {
+    // identity of the submission
+    std::vector<sbr_request> req;
+    std::vector<double> freq;
+    double eta = 0.0;
+    int max_bounces = 0, pol_mask = 0, po_mode = 0, flags = 0, trace_bps = 0;
+    sbr_trace_opts opt;
+    double* E = nullptr;
+    double* R = nullptr;
+    long long mesh_gen = -1;
+    // chunks of aspects [cut[k], cut[k + 1])
+    std::vector<int64_t> cut;
+    std::vector<long long> chunk_rays, items_bound;
+    long long launched = 0;
+    int64_t n_launch = 0, n_pass = 0;
+    bool count = false;
+    PoArgs pa;
+    // device buffers
+    DevBuf angles, rayoff, pang, recoff, mask, tilebase, scan_scr, q0, q1, ctr64, ctr32, stats, rec, items, nitems,
+        valid, freq_t, kfreq, partial;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+void free_plan(BatchPlan* p)
+{
+    if (!p) return;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->cap) cudaStreamDestroy(p->cap);
+    DevBuf* all[] = {&p->angles, &p->rayoff, &p->pang,   &p->recoff, &p->mask,   &p->tilebase, &p->scan_scr,
+                     &p->q0,     &p->q1,     &p->ctr64,  &p->ctr32,  &p->stats,  &p->rec,      &p->items,
+                     &p->nitems, &p->valid,  &p->freq_t, &p->kfreq,  &p->partial};
+    for (DevBuf* b : all) b->release();
+    delete p;
+}
+
+bool same_submission(const BatchPlan& P, const sbr_ctx* c, const sbr_request* req, int64_t n_req, const double* freq,
+                     int64_t n_freq, double eta, int max_bounces, int pol_mask, int po_mode, const sbr_trace_opts& o,
+                     double* E, double* R)
+{
+    return P.mesh_gen == c->mesh_gen && P.trace_bps == c->trace_bps && (int64_t)P.req.size() == n_req &&
+           (int64_t)P.freq.size() == n_freq && P.eta == eta && P.max_bounces == max_bounces &&
+           P.pol_mask == pol_mask && P.po_mode == po_mode && P.E == E && P.R == R &&
+           memcmp(&P.opt, &o, sizeof(o)) == 0 && memcmp(P.req.data(), req, sizeof(sbr_request) * (size_t)n_req) == 0 &&
+           memcmp(P.freq.data(), freq, sizeof(double) * (size_t)n_freq) == 0;
+}
+
+// Enqueue the whole batch on stream st: per chunk the transport passes, the
+// record scan, the device-built PO work list, the PO sums and the final sums.
+cudaError_t enqueue_plan(const sbr_ctx* c, BatchPlan& P, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(P.stats.p, 0, sizeof(unsigned long long) * kStatCount, st);
+    unsigned* q_count = P.ctr32.as<unsigned>();
+    unsigned* total_dev = q_count + 2 * (kMaxBounces + 2);
+    RayState* qs[2] = {P.q0.as<RayState>(), P.q1.as<RayState>()};
+    const int n_blocks = c->n_sms * c->trace_bps;
+    const bool escape = P.flags & SBR_TRACE_REQUIRE_ESCAPE;
+    for (size_t k = 0; e == cudaSuccess && k + 1 < P.cut.size(); ++k) {
+        const int64_t a0 = P.cut[k];
+        const int na = (int)(P.cut[k + 1] - a0);
+        const long long rays = P.chunk_rays[k];
+        e = cudaMemsetAsync(P.ctr64.p, 0, P.ctr64.cap, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(P.ctr32.p, 0, P.ctr32.cap, st);
+        if (e != cudaSuccess) break;
+        TraceArgs ta;
+        memset(&ta, 0, sizeof(ta));
+        ta.nodes = c->nodes.as<float4>();
+        ta.tris = c->tris.as<float4>();
+        ta.angles = P.angles.as<AngleDev>() + a0;
+        ta.ray_off = P.rayoff.as<long long>() + a0 + (int64_t)k;  // chunk k's table has na + 1 entries
+        ta.n_angles = na;
+        ta.max_bounces = P.max_bounces;
+        ta.flags = P.flags;
+        ta.visit_limit = (int)std::min<long long>(2 * c->n_tri + 64, 1ll << 30);
+        ta.total_rays = rays;
+        ta.mask = P.mask.as<unsigned>();
+        ta.tile_base = P.tilebase.as<unsigned>();
+        ta.stats = P.stats.as<unsigned long long>();
+        ta.bounce = 0;
+        ta.work = P.ctr64.as<unsigned long long>();
+        ta.q_out = qs[0];
+        ta.q_out_count = q_count + 1;
+        e = launch_trace(ta, n_blocks, P.count, st);
+        if (e == cudaSuccess) e = scan_popc(ta.mask, P.tilebase.as<unsigned>(), rays / 32, total_dev, P.scan_scr.p, st);
+        if (e == cudaSuccess)
+            e = launch_angle_offsets(ta.ray_off, ta.tile_base, total_dev, na, P.recoff.as<unsigned>(), st);
+        if (e != cudaSuccess) break;
+        ta.rec = P.rec.as<Record>();
+        if (P.max_bounces == 1 && !escape) {
+            ta.q_in = qs[0];
+            ta.q_in_count = q_count + 1;
+            e = launch_emit_all(ta, n_blocks, st);
+        } else {
+            const int last_pass = escape ? P.max_bounces : P.max_bounces - 1;
+            for (int b = 1; b <= last_pass && e == cudaSuccess; ++b) {
+                ta.bounce = b;
+                ta.work = P.ctr64.as<unsigned long long>() + b;
+                ta.q_in = qs[(b - 1) & 1];
+                ta.q_in_count = q_count + b;
+                ta.q_out = qs[b & 1];
+                ta.q_out_count = q_count + b + 1;
+                e = launch_trace(ta, n_blocks, P.count, st);
+            }
+        }
+        PoAngle* pang = P.pang.as<PoAngle>() + a0;
+        if (e == cudaSuccess)
+            e = launch_po_items(P.recoff.as<unsigned>(), pang, na, P.pa.n_pol, P.items.as<PoItem>(), P.nitems.as<int>(),
+                                P.valid.as<long long>() + k, st);
+        if (e == cudaSuccess && P.items_bound[k] > 0) {
+            PoArgs pa = P.pa;
+            pa.rec = P.rec.as<Record>();
+            pa.items = P.items.as<PoItem>();
+            pa.n_items = 0;
+            pa.n_items_dev = P.nitems.as<int>();
+            pa.freq = P.freq_t.as<float4>();
+            pa.kfreq = P.kfreq.as<double>();
+            pa.partial = P.partial.as<double>();
+            e = launch_po(pa, st, (int)std::min<long long>(P.items_bound[k], (long long)c->n_sms * 8));
+        }
+        if (e == cudaSuccess)
+            e = launch_po_final(P.partial.as<double>(), P.items.as<PoItem>(), pang, na, P.kfreq.as<double>(),
+                                P.pa.n_pol, P.E, P.R, st);
+    }
+    return e;
+}
+
+// Build a plan (tables uploaded, buffers sized); the graph is captured by the caller.
+int build_plan(sbr_ctx* c, BatchPlan& P)
+{
+    const int64_t n = (int64_t)P.req.size();
+    std::vector<sbr_ray_grid> g((size_t)n);
+    std::vector<long long> begin((size_t)n);
+    long long total = 0;
+    for (int64_t a = 0; a < n; ++a) {
+        make_grid(c->bbox, P.req[(size_t)a].az_deg, P.req[(size_t)a].el_deg, P.req[(size_t)a].ray_spacing_m, P.eta,
+                  &P.opt, &g[(size_t)a]);
+        const long long cap = P.opt.chunk_rays > 0 ? std::max<long long>(32, P.opt.chunk_rays) : kChunkRays;
+        if (g[(size_t)a].nu > (1ll << 30) || g[(size_t)a].nv > (1ll << 30) || tiled_rays(g[(size_t)a]) > cap)
+            return fail(c, SBR_ERR_ARG, "ray grid of request %lld too large (%lld x %lld) for a chunk of %lld rays",
+                        (long long)a, (long long)g[(size_t)a].nu, (long long)g[(size_t)a].nv, cap);
+        begin[(size_t)a] = total;
+        total += tiled_rays(g[(size_t)a]);
+        P.launched += g[(size_t)a].nu * g[(size_t)a].nv;
+    }
+    const long long cap = P.opt.chunk_rays > 0 ? std::max<long long>(32, P.opt.chunk_rays) : kChunkRays;
+    P.cut.assign(1, 0);
+    long long acc = 0;
+    for (int64_t a = 0; a < n; ++a) {
+        const long long r = tiled_rays(g[(size_t)a]);
+        if (acc > 0 && acc + r > cap) {
+            P.cut.push_back(a);
+            acc = 0;
+        }
+        acc += r;
+    }
+    P.cut.push_back(n);
+    const size_t nc = P.cut.size() - 1;
+    long long max_rays = 0, max_rec = 0, max_items = 0, max_part = 0;
+    int max_angles = 0;
+    P.chunk_rays.assign(nc, 0);
+    P.items_bound.assign(nc, 0);
+    for (size_t k = 0; k < nc; ++k) {
+        long long rays = 0, rec = 0, items = 0, part = 0;
+        for (int64_t a = P.cut[k]; a < P.cut[k + 1]; ++a) {
+            const sbr_ray_grid& G = g[(size_t)a];
+            rays += tiled_rays(G);
+            rec += G.nu * G.nv;
+            const long long ni = (G.nu * G.nv + kPoItemRecords - 1) / kPoItemRecords;
+            items += ni;
+            part += ni * P.req[(size_t)a].n_freq * 2 * P.pa.n_pol;
+        }
+        P.chunk_rays[k] = rays;
+        P.items_bound[k] = items;
+        max_rays = std::max(max_rays, rays);
+        max_rec = std::max(max_rec, rec);
+        max_items = std::max(max_items, items);
+        max_part = std::max(max_part, part);
+        max_angles = std::max(max_angles, (int)(P.cut[k + 1] - P.cut[k]));
+    }
+    if (max_items >= (1ll << 31)) return fail(c, SBR_ERR_ARG, "sbr_submit_batch: chunk too large for the PO work list");
+    const long long max_tiles = max_rays / 32;
+    CK(P.angles.ensure(sizeof(AngleDev) * (size_t)n), "alloc angles");
+    CK(P.rayoff.ensure(sizeof(long long) * (size_t)(n + nc)), "alloc ray offsets");
+    CK(P.pang.ensure(sizeof(PoAngle) * (size_t)n), "alloc aspect table");
+    CK(P.recoff.ensure(sizeof(unsigned) * (size_t)(max_angles + 1)), "alloc record offsets");
+    CK(P.mask.ensure(sizeof(unsigned) * (size_t)max_tiles), "alloc mask");
+    CK(P.tilebase.ensure(sizeof(unsigned) * (size_t)max_tiles), "alloc tile base");
+    CK(P.scan_scr.ensure(scan_scratch_bytes(max_tiles)), "alloc scan scratch");
+    CK(P.q0.ensure(sizeof(RayState) * (size_t)max_rays), "alloc ray queue");
+    CK(P.q1.ensure(sizeof(RayState) * (size_t)max_rays), "alloc ray queue");
+    CK(P.ctr64.ensure(sizeof(unsigned long long) * 2 * (kMaxBounces + 2)), "alloc counters");
+    CK(P.ctr32.ensure(sizeof(unsigned) * 2 * (kMaxBounces + 2) + 64), "alloc counters");
+    CK(P.stats.ensure(sizeof(unsigned long long) * kStatCount), "alloc stats");
+    CK(P.rec.ensure(sizeof(Record) * (size_t)std::max(max_rec, 1ll)), "alloc records");
+    CK(P.items.ensure(sizeof(PoItem) * (size_t)std::max(max_items, 1ll)), "alloc items");
+    CK(P.nitems.ensure(sizeof(int)), "alloc item count");
+    CK(P.valid.ensure(sizeof(long long) * nc), "alloc valid counts");
+    CK(P.partial.ensure(sizeof(double) * (size_t)std::max(max_part, 1ll)), "alloc partials");
+    CK(P.freq_t.ensure(sizeof(float4) * P.freq.size()), "alloc freq");
+    CK(P.kfreq.ensure(sizeof(double) * P.freq.size()), "alloc freq");
+    // tables: angles, per-chunk ray offsets, aspect rows, frequencies (one synchronous upload)
+    const size_t b_a = sizeof(AngleDev) * (size_t)n, b_o = sizeof(long long) * (size_t)(n + nc),
+                 b_p = sizeof(PoAngle) * (size_t)n, b_f = sizeof(float4) * P.freq.size(),
+                 b_k = sizeof(double) * P.freq.size();
+    char* hs = (char*)stage(c, b_a + b_o + b_p + b_f + b_k + 256);
+    if (!hs) return fail(c, SBR_ERR_OOM, "pinned staging allocation failed");
+    AngleDev* ha = (AngleDev*)hs;
+    long long* ho = (long long*)(hs + b_a);
+    PoAngle* hp = (PoAngle*)(hs + b_a + b_o);
+    float4* hf = (float4*)(hs + b_a + b_o + b_p);
+    double* hk = (double*)(hs + b_a + b_o + b_p + b_f);
+    long long row = 0;
+    for (int64_t a = 0; a < n; ++a) {
+        PoAngle& A = hp[a];
+        memset(&A, 0, sizeof(A));
+        A.f0 = (int)P.req[(size_t)a].freq_offset;
+        A.nf = P.req[(size_t)a].n_freq;
+        A.out_row = row;
+        row += A.nf;
+    }
+    for (size_t k = 0; k < nc; ++k) {
+        const long long base = begin[(size_t)P.cut[k]];
+        for (int64_t a = P.cut[k]; a < P.cut[k + 1]; ++a) {
+            ho[a + (int64_t)k] = begin[(size_t)a] - base;
+            ha[a] = to_dev(g[(size_t)a], begin[(size_t)a] - base);
+        }
+        ho[P.cut[k + 1] + (int64_t)k] = P.chunk_rays[k];
+    }
+    for (size_t f = 0; f < P.freq.size(); ++f) {
+        const double kappa = P.freq[f] / kC0;
+        const float kh = (float)kappa;
+        const double kk = 2.0 * kPi * P.freq[f] / kC0;
+        hf[f] = make_float4(kh, (float)(kappa - (double)kh), (float)kk, 0.f);
+        hk[f] = kk;
+    }
+    CK(cudaMemcpyAsync(P.angles.p, ha, b_a, cudaMemcpyHostToDevice, c->stream), "copy angles");
+    CK(cudaMemcpyAsync(P.rayoff.p, ho, b_o, cudaMemcpyHostToDevice, c->stream), "copy ray offsets");
+    CK(cudaMemcpyAsync(P.pang.p, hp, b_p, cudaMemcpyHostToDevice, c->stream), "copy aspect table");
+    CK(cudaMemcpyAsync(P.freq_t.p, hf, b_f, cudaMemcpyHostToDevice, c->stream), "copy freq");
+    CK(cudaMemcpyAsync(P.kfreq.p, hk, b_k, cudaMemcpyHostToDevice, c->stream), "copy freq");
+    CK(cudaStreamSynchronize(c->stream), "plan upload sync");
+    // kernels per run: stats memset excluded; per chunk trace passes, 3 scan, offsets, 2 work list, PO, final
+    const bool escape = P.flags & SBR_TRACE_REQUIRE_ESCAPE;
+    const int passes = (P.max_bounces == 1 && !escape) ? 1 : 1 + (escape ? P.max_bounces : P.max_bounces - 1);
+    P.n_pass = (int64_t)nc * passes;
+    P.n_launch = 0;
+    for (size_t k = 0; k < nc; ++k)
+        P.n_launch += passes + ((P.max_bounces == 1 && !escape) ? 1 : 0) + 3 + 1 + 2 + (P.items_bound[k] > 0 ? 1 : 0) + 1;
     return SBR_OK;
 }
 
@@ -892,6 +1157,125 @@ int sbr_run_batch(sbr_ctx* c, const sbr_request* req, int64_t n_req, const doubl
             CK(cudaMemcpyAsync(rcs_out, dR, sizeof(double) * n_out, cudaMemcpyDeviceToHost, c->stream), "copy rcs");
     }
     return finish_stats(c, R, n_req, launched, valid, stats);
+}
+
+int sbr_submit_batch(sbr_ctx* c, const sbr_request* req, int64_t n_req, const double* freq_hz, int64_t n_freq_total,
+                     double eta, int max_bounces, int pol_mask, int po_mode, const sbr_trace_opts* opt, double* E_dev,
+                     double* rcs_dev)
+{
+    if (!c) return SBR_ERR_ARG;
+    if (!c->has_bvh) return fail(c, SBR_ERR_STATE, "sbr_submit_batch: no BVH (load a mesh first)");
+    if (!req || n_req < 1 || n_req > (1ll << 30)) return fail(c, SBR_ERR_ARG, "sbr_submit_batch: no requests");
+    if (!freq_hz || n_freq_total < 1 || n_freq_total > (1ll << 30))
+        return fail(c, SBR_ERR_ARG, "sbr_submit_batch: bad frequency array");
+    if (!(eta >= 0.0)) return fail(c, SBR_ERR_ARG, "sbr_submit_batch: eta >= 0");
+    if (max_bounces < 1 || max_bounces > kMaxBounces)
+        return fail(c, SBR_ERR_ARG, "sbr_submit_batch: max_bounces in 1..64");
+    sbr_trace_opts o;
+    memset(&o, 0, sizeof(o));
+    if (opt) o = *opt;
+    if (o.flags & (SBR_TRACE_RECORD_HITS | SBR_TRACE_TIME_PASSES))
+        return fail(c, SBR_ERR_ARG, "sbr_submit_batch: SBR_TRACE_RECORD_HITS / SBR_TRACE_TIME_PASSES are refused");
+    for (int64_t f = 0; f < n_freq_total; ++f)
+        if (!(freq_hz[f] > 0.0)) return fail(c, SBR_ERR_ARG, "sbr_submit_batch: frequencies must be > 0");
+    for (int64_t r = 0; r < n_req; ++r) {
+        const sbr_request& q = req[r];
+        if (!(q.ray_spacing_m > 0.0))
+            return fail(c, SBR_ERR_ARG, "sbr_submit_batch: request %lld: spacing must be > 0", (long long)r);
+        if (q.n_freq < 1 || q.freq_offset < 0 || q.freq_offset + q.n_freq > n_freq_total)
+            return fail(c, SBR_ERR_ARG, "sbr_submit_batch: request %lld: frequency range outside the array",
+                        (long long)r);
+    }
+    PoArgs pa;
+    int rc = check_po_mode(c, pol_mask, po_mode, pa);
+    if (rc != SBR_OK) return rc;
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    const bool graph = !(o.flags & SBR_TRACE_NO_GRAPH);
+    o.flags &= ~SBR_TRACE_NO_GRAPH;
+    if (!(c->plan && same_submission(*c->plan, c, req, n_req, freq_hz, n_freq_total, eta, max_bounces, pol_mask,
+                                     po_mode, o, E_dev, rcs_dev))) {
+        if (c->plan) CK(cudaStreamSynchronize(c->stream), "wait for the previous batch");
+        free_plan(c->plan);
+        c->plan = nullptr;
+        c->plan_pending = false;
+        BatchPlan* P = new BatchPlan();
+        P->req.assign(req, req + n_req);
+        P->freq.assign(freq_hz, freq_hz + n_freq_total);
+        P->eta = eta;
+        P->max_bounces = max_bounces;
+        P->pol_mask = pol_mask;
+        P->po_mode = po_mode;
+        P->opt = o;
+        P->flags = o.flags;
+        P->count = o.flags & SBR_TRACE_COUNT_VISITS;
+        P->trace_bps = c->trace_bps;
+        P->E = E_dev;
+        P->R = rcs_dev;
+        P->mesh_gen = c->mesh_gen;
+        P->pa = pa;
+        rc = build_plan(c, *P);
+        if (rc != SBR_OK) {
+            free_plan(P);
+            return rc;
+        }
+        c->plan = P;
+    }
+    BatchPlan& P = *c->plan;
+    if (!graph) {
+        CK(enqueue_plan(c, P, c->stream), "enqueue batch");
+    } else {
+        if (!P.exec) {
+            if (!P.cap) CK(cudaStreamCreateWithFlags(&P.cap, cudaStreamNonBlocking), "capture stream");
+            CK(cudaStreamBeginCapture(P.cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+            cudaError_t e = enqueue_plan(c, P, P.cap);
+            cudaGraph_t gr = nullptr;
+            const cudaError_t e2 = cudaStreamEndCapture(P.cap, &gr);
+            if (e == cudaSuccess) e = e2;
+            if (e != cudaSuccess) {
+                if (gr) cudaGraphDestroy(gr);
+                cudaGetLastError();
+                return cuda_fail(c, e, "capture batch graph");
+            }
+            P.graph = gr;
+            CK(cudaGraphInstantiate(&P.exec, P.graph, 0), "instantiate batch graph");
+        }
+        CK(cudaGraphLaunch(P.exec, c->stream), "launch batch graph");
+    }
+    c->plan_pending = true;
+    return SBR_OK;
+}
+
+int sbr_sync(sbr_ctx* c, sbr_trace_stats* stats)
+{
+    if (!c) return SBR_ERR_ARG;
+    if (!c->plan || !c->plan_pending) return fail(c, SBR_ERR_STATE, "sbr_sync: no submitted batch");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    BatchPlan& P = *c->plan;
+    const size_t nc = P.cut.size() - 1;
+    unsigned long long hs[kStatCount];
+    std::vector<long long> hv(nc);
+    CK(cudaStreamSynchronize(c->stream), "batch sync");
+    CK(cudaMemcpy(hs, P.stats.p, sizeof(hs), cudaMemcpyDeviceToHost), "copy stats");
+    CK(cudaMemcpy(hv.data(), P.valid.p, sizeof(long long) * nc, cudaMemcpyDeviceToHost), "copy valid counts");
+    c->plan_pending = false;
+    long long valid = 0;
+    for (long long v : hv) valid += v;
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->n_angles = (int64_t)P.req.size();
+        stats->rays_launched = P.launched;
+        stats->ray_bounces = (int64_t)hs[kStatQueries];
+        stats->valid_rays = valid;
+        stats->node_visits = (int64_t)hs[kStatNodes];
+        stats->tri_tests = (int64_t)hs[kStatTris];
+        stats->stack_overflows = (int64_t)hs[kStatOverflow];
+        stats->kernel_launches = P.n_launch;
+        stats->pass_launches = P.n_pass;
+    }
+    if (hs[kStatOverflow])
+        return fail(c, SBR_ERR_STACK_OVERFLOW, "%llu traversals exceeded the stack depth",
+                    (unsigned long long)hs[kStatOverflow]);
+    return SBR_OK;
 }
 
 int sbr_get_hits(sbr_ctx* c, int64_t angle, int32_t* tri_ids, float* t, int32_t* n_bounce)

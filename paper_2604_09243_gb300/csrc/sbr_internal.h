@@ -138,13 +138,14 @@ struct PoAngle {
     int item_begin, item_end;  // items of this aspect
     int f0, nf;                // its frequencies in the frequency table
     long long out_row;         // first output row: row out_row + q holds frequency f0 + q
-    long long pad;
+    long long part;            // first partial of its items (device-built work lists)
 };
 static_assert(sizeof(PoAngle) == 32, "PoAngle layout");
 struct PoArgs {
     const Record* rec;
     const PoItem* items;
     int n_items;
+    const int* n_items_dev;  // when set, the item count is read here (device-built work lists)
     const float4* freq;   // [n_freq] (kappa_hi, kappa_lo, k, 0), kappa = f / c0 cycles per metre
     const double* kfreq;  // [n_freq] k in FP64 (FP64 phase mode)
     int n_freq;           // entries of the frequency table
@@ -154,7 +155,15 @@ struct PoArgs {
     int phase_mode;       // 0 compensated, 1 FP32, 2 FP64
     double* partial;      // FP64 partials, item i at items[i].part
 };
-cudaError_t launch_po(const PoArgs& a, cudaStream_t st);
+// n_blocks > 0: persistent grid of that many blocks looping over the items
+cudaError_t launch_po(const PoArgs& a, cudaStream_t st, int n_blocks = 0);
+// Device-built PO work list of one traced chunk: aspect a owns the records
+// [recoff[a], recoff[a + 1]) of the chunk, cut into items of kPoItemRecords.
+// Fills angles[a].item_begin / item_end / part (f0, nf, out_row are inputs),
+// items[] and *n_items; *valid = recoff[n_angles] (may be null).
+constexpr int kPoItemRecords = 1024;
+cudaError_t launch_po_items(const unsigned* recoff, PoAngle* angles, int n_angles, int n_pol, PoItem* items,
+                            int* n_items, long long* valid, cudaStream_t st);
 // E[row][n_pol][2] and rcs[row][n_pol] for every aspect's rows (fixed-order FP64 sums of the partials)
 cudaError_t launch_po_final(const double* partial, const PoItem* items, const PoAngle* angles, int n_angles,
                             const double* kfreq, int n_pol, double* E, double* rcs, cudaStream_t st);

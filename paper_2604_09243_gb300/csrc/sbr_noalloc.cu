@@ -117,7 +117,7 @@ extern "C" int sbr_po_integrate_noalloc(const void* records, const int64_t* rec_
         A.f0 = 0;
         A.nf = (int)n_freq;
         A.out_row = a * n_freq;
-        A.pad = 0;
+        A.part = 0;
         for (long long r = rec_offsets[a]; r < rec_offsets[a + 1]; r += kItem) {
             g_items[ni].angle = (int)a;
             g_items[ni].first = r;

@@ -1,7 +1,7 @@
 // sbr_po.cu -- physical-optics ray-tube sum over the dense valid-hit records
 // (Eq. po_sum of the paper; vector form from Eq. em5/em6).
 //
-// The records of one aspect are cut into items of up to kPoItem tubes. One
+// The records of one aspect are cut into items of up to kPoItemRecords tubes. One
 // block owns an item: it loads the tubes once and, for every requested
 // frequency, evaluates e^{-j k L} per tube, multiplies by the tube coefficients
 // and reduces with warp shuffles and a shared-memory tree in FP32. The item
@@ -15,6 +15,8 @@
 // fraction goes to sincospi. This keeps the phase error at the FP32 rounding
 // of the fraction even for paths of thousands of wavelengths.
 #include <math.h>
+
+#include <algorithm>
 
 #include "sbr_internal.h"
 
@@ -49,69 +51,151 @@ __device__ __forceinline__ void phase_cs(const PoArgs& a, float4 fq, double kd, 
 __global__ void __launch_bounds__(kPoThreads) k_po(const PoArgs a)
 {
     __shared__ float s_red[kWarps][8];
-    const PoItem I = a.items[blockIdx.x];
+    const int n_items = a.n_items_dev ? *a.n_items_dev : a.n_items;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    float cf[kPoPer][4];
-    float lh[kPoPer], ll[kPoPer];
-#pragma unroll
-    for (int k = 0; k < kPoPer; ++k) {
-        const int idx = k * kPoThreads + tid;
-        if (idx < I.count) {
-            const float4* p = reinterpret_cast<const float4*>(a.rec + I.first + idx);
-            const float4 x = __ldg(p), y = __ldg(p + 1);
-            const float cv[5] = {x.x, x.y, x.z, x.w, y.x};
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int sel = a.pol_sel[q];
-                float v = 0.f;
-                if (q < a.n_pol) v = a.scalar ? (sel < 2 ? cv[4] : 0.f) : cv[sel];
-                cf[k][q] = v;
-            }
-            lh[k] = y.y;
-            ll[k] = y.z;
-        } else {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) cf[k][q] = 0.f;
-            lh[k] = 0.f;
-            ll[k] = 0.f;
-        }
-    }
-    for (int fi = 0; fi < I.nf; ++fi) {
-        const float4 fq = a.freq[I.f0 + fi];
-        const double kd = a.kfreq[I.f0 + fi];
-        float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const PoItem I = a.items[item];
+        float cf[kPoPer][4];
+        float lh[kPoPer], ll[kPoPer];
 #pragma unroll
         for (int k = 0; k < kPoPer; ++k) {
-            if (k * kPoThreads + tid >= I.count) break;
-            float c, s;
-            phase_cs(a, fq, kd, lh[k], ll[k], c, s);
+            const int idx = k * kPoThreads + tid;
+            if (idx < I.count) {
+                const float4* p = reinterpret_cast<const float4*>(a.rec + I.first + idx);
+                const float4 x = __ldg(p), y = __ldg(p + 1);
+                const float cv[5] = {x.x, x.y, x.z, x.w, y.x};
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                re[q] = fmaf(cf[k][q], c, re[q]);
-                im[q] = fmaf(-cf[k][q], s, im[q]);
+                for (int q = 0; q < 4; ++q) {
+                    const int sel = a.pol_sel[q];
+                    float v = 0.f;
+                    if (q < a.n_pol) v = a.scalar ? (sel < 2 ? cv[4] : 0.f) : cv[sel];
+                    cf[k][q] = v;
+                }
+                lh[k] = y.y;
+                ll[k] = y.z;
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) cf[k][q] = 0.f;
+                lh[k] = 0.f;
+                ll[k] = 0.f;
             }
         }
+        for (int fi = 0; fi < I.nf; ++fi) {
+            const float4 fq = a.freq[I.f0 + fi];
+            const double kd = a.kfreq[I.f0 + fi];
+            float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
+            for (int k = 0; k < kPoPer; ++k) {
+                if (k * kPoThreads + tid >= I.count) break;
+                float c, s;
+                phase_cs(a, fq, kd, lh[k], ll[k], c, s);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                re[q] += __shfl_xor_sync(0xffffffffu, re[q], o);
-                im[q] += __shfl_xor_sync(0xffffffffu, im[q], o);
+                for (int q = 0; q < 4; ++q) {
+                    re[q] = fmaf(cf[k][q], c, re[q]);
+                    im[q] = fmaf(-cf[k][q], s, im[q]);
+                }
             }
-        if (lane == 0)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                s_red[w][2 * q] = re[q];
-                s_red[w][2 * q + 1] = im[q];
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    re[q] += __shfl_xor_sync(0xffffffffu, re[q], o);
+                    im[q] += __shfl_xor_sync(0xffffffffu, im[q], o);
+                }
+            if (lane == 0)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    s_red[w][2 * q] = re[q];
+                    s_red[w][2 * q + 1] = im[q];
+                }
+            __syncthreads();
+            if (tid < 2 * a.n_pol) {
+                float v = 0.f;
+#pragma unroll
+                for (int k = 0; k < kWarps; ++k) v += s_red[k][tid];
+                a.partial[I.part + (size_t)fi * (2 * a.n_pol) + tid] = (double)v;
             }
-        __syncthreads();
-        if (tid < 2 * a.n_pol) {
-            float v = 0.f;
+            __syncthreads();
+        }
+    }
+}
+
+static_assert(kPoItemRecords == kPoPer * kPoThreads, "PO item size");
+
+// Work list, stage 1 (one block): 64-bit exclusive scans over the aspects of
+// their item counts and partial sizes, in tiles of the block size.
+__global__ void k_po_items_scan(const unsigned* recoff, PoAngle* angles, int na, int n_pol, int* n_items,
+                                long long* valid)
+{
+    __shared__ long long s_ni[32], s_np[32];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
+    long long base_i = 0, base_p = 0;
+    for (int t0 = 0; t0 < na; t0 += blockDim.x) {
+        const int a = t0 + tid;
+        long long ni = 0, np = 0;
+        if (a < na) {
+            const unsigned rc = recoff[a + 1] - recoff[a];
+            ni = (rc + kPoItemRecords - 1) / kPoItemRecords;
+            np = ni * (long long)angles[a].nf * 2 * n_pol;
+        }
+        // inclusive warp scans, then across warps
+        long long xi = ni, xp = np;
 #pragma unroll
-            for (int k = 0; k < kWarps; ++k) v += s_red[k][tid];
-            a.partial[I.part + (size_t)fi * (2 * a.n_pol) + tid] = (double)v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long yi = __shfl_up_sync(0xffffffffu, xi, o), yp = __shfl_up_sync(0xffffffffu, xp, o);
+            if (lane >= o) {
+                xi += yi;
+                xp += yp;
+            }
+        }
+        if (lane == 31) {
+            s_ni[w] = xi;
+            s_np[w] = xp;
         }
         __syncthreads();
+        long long wi = 0, wp = 0, ti = 0, tp = 0;
+        for (int k = 0; k < nw; ++k) {
+            if (k < w) {
+                wi += s_ni[k];
+                wp += s_np[k];
+            }
+            ti += s_ni[k];
+            tp += s_np[k];
+        }
+        if (a < na) {
+            PoAngle& A = angles[a];
+            A.item_begin = (int)(base_i + wi + xi - ni);
+            A.item_end = (int)(base_i + wi + xi);
+            A.part = base_p + wp + xp - np;
+        }
+        base_i += ti;
+        base_p += tp;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        *n_items = (int)base_i;
+        if (valid) *valid = recoff[na];
+    }
+}
+
+// Work list, stage 2: one warp per aspect writes its items.
+__global__ void k_po_items_fill(const unsigned* recoff, const PoAngle* angles, int na, int n_pol, PoItem* items)
+{
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; a < na; a += nwarps) {
+        const PoAngle A = angles[a];
+        const unsigned r0 = recoff[a], rc = recoff[a + 1] - r0;
+        for (int r = lane; r < A.item_end - A.item_begin; r += 32) {
+            PoItem it;
+            it.angle = a;
+            it.count = (int)min((unsigned)kPoItemRecords, rc - (unsigned)r * kPoItemRecords);
+            it.first = (long long)r0 + (long long)r * kPoItemRecords;
+            it.f0 = A.f0;
+            it.nf = A.nf;
+            it.part = A.part + (long long)r * A.nf * 2 * n_pol;
+            items[A.item_begin + r] = it;
+        }
     }
 }
 
@@ -142,10 +226,21 @@ __global__ void k_po_final(const double* partial, const PoItem* items, const PoA
 
 }  // namespace
 
-cudaError_t launch_po(const PoArgs& a, cudaStream_t st)
+cudaError_t launch_po(const PoArgs& a, cudaStream_t st, int n_blocks)
 {
-    if (a.n_items <= 0) return cudaSuccess;
-    k_po<<<a.n_items, kPoThreads, 0, st>>>(a);
+    const int grid = n_blocks > 0 ? n_blocks : a.n_items;
+    if (grid <= 0) return cudaSuccess;
+    k_po<<<grid, kPoThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_po_items(const unsigned* recoff, PoAngle* angles, int n_angles, int n_pol, PoItem* items,
+                            int* n_items, long long* valid, cudaStream_t st)
+{
+    if (n_angles <= 0) return cudaErrorInvalidValue;
+    k_po_items_scan<<<1, 1024, 0, st>>>(recoff, angles, n_angles, n_pol, n_items, valid);
+    const int blocks = (int)std::min<long long>(((long long)n_angles * 32 + 255) / 256, 4096);
+    k_po_items_fill<<<blocks, 256, 0, st>>>(recoff, angles, n_angles, n_pol, items);
     return cudaGetLastError();
 }
 

@@ -24,11 +24,13 @@ POL_ORDER = ("HH", "VV", "HV", "VH")
 PO_VECTOR, PO_PAPER_SCALAR = 0, 1
 PHASE = {"compensated": 0, "fp32": 16, "fp64": 32}
 TRACE_PHASE_LITERAL_2R, TRACE_REQUIRE_ESCAPE, TRACE_RECORD_HITS, TRACE_COUNT_VISITS, TRACE_TIME_PASSES = 1, 2, 4, 8, 16
+TRACE_NO_GRAPH = 32
 
 # every symbol declared in include/sbr.h
 EXPORTS = ("sbr_version", "sbr_create", "sbr_destroy", "sbr_last_error", "sbr_load_mesh", "sbr_get_bbox",
            "sbr_build_bvh", "sbr_ray_grid_for", "sbr_ray_grid_box", "sbr_trace", "sbr_po_integrate", "sbr_get_hits",
-           "sbr_get_records", "sbr_spacing_for", "sbr_po_integrate_noalloc", "sbr_run_batch",
+           "sbr_get_records", "sbr_spacing_for", "sbr_po_integrate_noalloc", "sbr_run_batch", "sbr_submit_batch",
+           "sbr_sync",
            "sbr_surrogate_create", "sbr_surrogate_destroy", "sbr_surrogate_last_error", "sbr_surrogate_num_params",
            "sbr_surrogate_params", "sbr_surrogate_fourier", "sbr_surrogate_train", "sbr_surrogate_grads",
            "sbr_surrogate_predict", "sbr_gemm_bf16_tn")
@@ -103,6 +105,9 @@ def lib() -> C.CDLL:
         "sbr_run_batch": ([vp, P(Request), i64, P(d), i64, d, C.c_int, C.c_int, C.c_int, P(TraceOpts), vp, vp,
                            C.c_int, P(TraceStats)], C.c_int),
         "sbr_po_integrate_noalloc": ([vp, P(i64), i64, P(d), i64, C.c_int, C.c_int, vp, vp, vp], C.c_int),
+        "sbr_submit_batch": ([vp, P(Request), i64, P(d), i64, d, C.c_int, C.c_int, C.c_int, P(TraceOpts), vp, vp],
+                             C.c_int),
+        "sbr_sync": ([vp, P(TraceStats)], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -278,14 +283,7 @@ class Context:
         """Batched trace + PO (sbr_run_batch). ``requests``: iterable of dicts with az, el,
         spacing and freqs (array). Returns (list of E [n_freq, n_pol] complex, list of
         rcs [n_freq, n_pol], stats)."""
-        reqs = list(requests)
-        freqs = np.concatenate([np.atleast_1d(np.asarray(r["freqs"], np.float64)) for r in reqs])
-        arr = (Request * len(reqs))()
-        off = 0
-        for k, r in enumerate(reqs):
-            nf = len(np.atleast_1d(r["freqs"]))
-            arr[k] = Request(float(r["az"]), float(r["el"]), float(r["spacing"]), off, nf, 0)
-            off += nf
+        reqs, arr, freqs = _requests(requests)
         pm = _pols(pols)
         npol = bin(pm).count("1")
         m = (PO_PAPER_SCALAR if mode == "scalar" else PO_VECTOR) | PHASE[phase]
@@ -304,6 +302,28 @@ class Context:
             outR.append(R[off:off + nf])
             off += nf
         return outE, outR, st.as_dict()
+
+    def submit_batch(self, requests, E_out=None, rcs_out=None, eta=0.05, max_bounces=1, pols="HH,VV",
+                     mode="vector", phase="compensated", flags=0, chunk_rays=0, window=0.0, offset=(0.0, 0.0)):
+        """Asynchronous batch (sbr_submit_batch): enqueue the batch as a CUDA graph on the context's stream
+        and return at once. ``E_out`` / ``rcs_out``: CUDA float64 tensors [rows, n_pol, 2] / [rows, n_pol]
+        (rows = total frequencies), written when the stream gets there; ``sync()`` waits. Submitting the
+        same requests, options and tensors again replays the captured graph."""
+        reqs, arr, freqs = _requests(requests)
+        self._submit_keep = (arr, freqs)
+        pm = _pols(pols)
+        m = (PO_PAPER_SCALAR if mode == "scalar" else PO_VECTOR) | PHASE[phase]
+        o = _opts(window, offset, flags, chunk_rays)
+        ep = E_out.data_ptr() if E_out is not None else None
+        rp = rcs_out.data_ptr() if rcs_out is not None else None
+        self._check(lib().sbr_submit_batch(self._h, arr, len(reqs), freqs.ctypes.data_as(C.POINTER(C.c_double)),
+                                           len(freqs), float(eta), int(max_bounces), pm, m, C.byref(o), ep, rp))
+
+    def sync(self) -> dict:
+        """Wait for the last submitted batch; its statistics."""
+        st = TraceStats()
+        self._check(lib().sbr_sync(self._h, C.byref(st)))
+        return st.as_dict()
 
     def po_integrate(self, freqs, pols="HH,VV", mode="vector", phase="compensated", E_out=None, rcs_out=None):
         """PO sum of the last trace. Returns (E complex128 [n_angles, n_freq, n_pol], rcs_dbsm [...]) as
@@ -351,6 +371,19 @@ class Context:
 
 
 # ---------------------------------------------------------------------------- surrogate
+def _requests(requests):
+    """(list of request dicts, sbr_request array, concatenated frequency array)."""
+    reqs = list(requests)
+    freqs = np.ascontiguousarray(np.concatenate([np.atleast_1d(np.asarray(r["freqs"], np.float64)) for r in reqs]))
+    arr = (Request * len(reqs))()
+    off = 0
+    for k, r in enumerate(reqs):
+        nf = len(np.atleast_1d(r["freqs"]))
+        arr[k] = Request(float(r["az"]), float(r["el"]), float(r["spacing"]), off, nf, 0)
+        off += nf
+    return reqs, arr, freqs
+
+
 class SurrogateOpts(C.Structure):
     _fields_ = [("n_members", C.c_int), ("width", C.c_int), ("depth", C.c_int), ("n_fourier", C.c_int),
                 ("fourier_sigma", C.c_float), ("seed", C.c_uint64)]

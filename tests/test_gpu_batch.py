@@ -62,3 +62,67 @@ def test_batch_against_oracle_sphere(G, orc):
     for k, r in enumerate(reqs):
         _, Ro, _, _ = orc.rcs_angle(om, om.bbox, r["az"], r["el"], r["spacing"], r["freqs"], 1, eta=0.05)
         assert_rcs_close(Rb[k], Ro[:, :2])
+
+
+@pytest.mark.parametrize("chunk,no_graph", [(0, False), (200_000, False), (200_000, True)])
+def test_submitted_batch_equals_run_batch(G, chunk, no_graph):
+    """sbr_submit_batch (device-built PO work lists, CUDA graph replay) gives the
+    run_batch results bit for bit, on the first launch and on replays."""
+    torch = pytest.importorskip("torch")
+    case = S.trihedral_case()
+    reqs = _requests(24, 7, fmax=6e9)
+    rows = sum(len(r["freqs"]) for r in reqs)
+    flags = G.TRACE_NO_GRAPH if no_graph else 0
+    with G.Context(0) as c:
+        c.load_mesh(case["xyz"], case["tri"])
+        Eb, Rb, st = c.run_batch(reqs, eta=0.05, max_bounces=3, pols="HH,VV,HV,VH", chunk_rays=chunk,
+                                 offset=case["offset"])
+        Eb, Rb = np.concatenate(Eb), np.concatenate(Rb)
+        E = torch.full((rows, 4, 2), float("nan"), dtype=torch.float64, device="cuda")
+        R = torch.full((rows, 4), float("nan"), dtype=torch.float64, device="cuda")
+        for rep in range(3):
+            E.fill_(float("nan"))
+            R.fill_(float("nan"))
+            torch.cuda.synchronize()  # the context runs on its own stream
+            c.submit_batch(reqs, E, R, eta=0.05, max_bounces=3, pols="HH,VV,HV,VH", chunk_rays=chunk,
+                           offset=case["offset"], flags=flags)
+            ss = c.sync()
+            Eg = E.cpu().numpy()
+            assert np.array_equal(Eg[..., 0] + 1j * Eg[..., 1], Eb), rep
+            assert np.array_equal(R.cpu().numpy(), Rb), rep
+            for k in ("ray_bounces", "valid_rays", "rays_launched", "n_angles"):
+                assert ss[k] == st[k], (k, ss[k], st[k])
+        if chunk:
+            assert ss["kernel_launches"] > 8 * 2
+
+
+def test_submitted_batch_replans_on_change_and_refuses_bad_flags(G):
+    torch = pytest.importorskip("torch")
+    case = S.trihedral_case()
+    reqs = _requests(5, 9, fmax=6e9)
+    rows = sum(len(r["freqs"]) for r in reqs)
+    with G.Context(0) as c:
+        c.load_mesh(case["xyz"], case["tri"])
+        with pytest.raises(G.SbrError):
+            c.sync()  # nothing submitted
+        R = torch.zeros((rows, 2), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()  # the context runs on its own stream
+        c.submit_batch(reqs, None, R, max_bounces=2, offset=case["offset"])
+        c.sync()
+        r1 = R.cpu().numpy().copy()
+        # another bounce limit: a new plan, results of run_batch with that limit
+        c.submit_batch(reqs, None, R, max_bounces=1, offset=case["offset"])
+        c.sync()
+        _, Rb, _ = c.run_batch(reqs, eta=0.05, max_bounces=1, offset=case["offset"])
+        assert np.array_equal(R.cpu().numpy(), np.concatenate(Rb))
+        assert not np.array_equal(R.cpu().numpy(), r1)
+        for bad in (G.TRACE_RECORD_HITS, G.TRACE_TIME_PASSES):
+            with pytest.raises(G.SbrError):
+                c.submit_batch(reqs, None, R, flags=bad)
+        # a new mesh invalidates the captured graph
+        sph = S.sphere_case(n_random=0)
+        c.load_mesh(sph["xyz"], sph["tri"])
+        c.submit_batch(reqs, None, R, max_bounces=1, offset=case["offset"])
+        c.sync()
+        _, Rs, _ = c.run_batch(reqs, eta=0.05, max_bounces=1, offset=case["offset"])
+        assert np.array_equal(R.cpu().numpy(), np.concatenate(Rs))
