@@ -460,6 +460,18 @@ def run_sbr(args, case, ws, rank, local, pg):
         ctx.po_integrate(freqs, "HH,VV", E_out=E_dev, rcs_out=R_dev)
         return st
 
+    tune = None
+    if not args.no_autotune:
+        # untimed: the autotuner picks blocks per SM, ray tile, stack depth, PO item and chunk size on an
+        # evenly spaced sample of the workload's aspects
+        pick = np.linspace(0, na - 1, min(na, args.tune_aspects)).round().astype(int)
+        sample = [dict(az=float(ang[i, 0]), el=float(ang[i, 1]), freqs=freqs, spacing=case["spacing"]) for i in pick]
+        best, best_ms, trials = ctx.autotune(sample, reps=3, **kw)
+        tune = {"best": best, "start": {k: trials[0][k] for k in best}, "start_ms": trials[0]["ms"],
+                "best_ms": best_ms, "trials": len(trials),
+                "refused": sum(1 for t in trials if t["status"] != 0),
+                "sample": f"{len(pick)} of {na} aspects, mean of 3 runs per setting"}
+
     for _ in range(args.warmup):
         step()
     cnt = ctx.trace(ang, case["spacing"], flags=G.TRACE_COUNT_VISITS, **kw)  # counting run, untimed
@@ -536,6 +548,7 @@ def run_sbr(args, case, ws, rank, local, pg):
             "e2e": {"value": e2e_value, "unit": "ray-bounces/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * t_e2e / args.steps},
             "gpu_launches": int(launches * args.steps),
+            "autotune": tune,
             "clocks": clocks}
     if args.batch_requests > 0:
         line["batched_vs_plain"] = batched_vs_plain(G, torch, local, args.batch_requests)
@@ -564,6 +577,8 @@ def main():
     ap.add_argument("--aspects", type=int, default=0,
                     help="use this many evenly spaced aspects of the sweep (small profiling cases); 0 = all")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default tuning")
+    ap.add_argument("--tune-aspects", type=int, default=24, help="aspects in the autotuner's sample")
     ap.add_argument("--sur-domains", default="full,patch", help="surrogate: domains to evaluate")
     ap.add_argument("--sur-scale", type=float, default=1.0, help="surrogate: fraction of the sample counts")
     ap.add_argument("--sur-epochs", type=int, default=60)

@@ -246,6 +246,48 @@ int sbr_submit_batch(sbr_ctx* ctx, const sbr_request* req, int64_t n_req, const 
  * SBR_ERR_STATE if nothing was submitted. */
 int sbr_sync(sbr_ctx* ctx, sbr_trace_stats* stats);
 
+/* ---- tuning ------------------------------------------------------------------
+ * Launch and layout parameters of the trace-integrate path. None of them
+ * changes any ray's hits or records; the ray tile and the PO item size change
+ * the order of the FP32 partial sums, so fields agree to rounding across
+ * settings and bit for bit between runs with the same setting. */
+typedef struct {
+    int tile_w;          /* rays of a warp form a tile_w x (32 / tile_w) patch; 1, 2, 4, 8, 16, 32 (default 8) */
+    int blocks_per_sm;   /* resident 256-thread transport blocks per SM, 1..4 (default: occupancy limit) */
+    int stack_depth;     /* traversal stack entries: 32, 64 or 128 (default 64); a query that needs more is
+                            reported as a stack overflow (SBR_ERR_STACK_OVERFLOW) */
+    int chunk_rays_log2; /* rays per chunk when opt->chunk_rays is 0: 2^20 .. 2^27 (default 27) */
+    int po_item;         /* records per PO block: 512, 1024 or 2048 (default 1024) */
+} sbr_tuning;
+int sbr_get_tuning(const sbr_ctx* ctx, sbr_tuning* out);
+/* SBR_ERR_ARG for a value outside the ranges above. */
+int sbr_set_tuning(sbr_ctx* ctx, const sbr_tuning* t);
+
+/* One configuration tried by sbr_autotune: its mean time per run of the
+ * sample batch (host wall clock of sbr_run_batch) and status: 0 accepted,
+ * 1 refused because its dBsm differ from the starting configuration's by more
+ * than 0.01 dB where those are above -40 dBsm, < 0 the error code of the run
+ * (e.g. SBR_ERR_STACK_OVERFLOW for a stack too shallow for the mesh). */
+typedef struct {
+    sbr_tuning tuning;
+    double ms;
+    int status;
+    int reserved;
+} sbr_tune_trial;
+
+/* Autotuner: times sbr_run_batch on the given sample batch (arguments as for
+ * sbr_run_batch) under the current setting and then, one parameter at a
+ * time (blocks per SM, ray tile, stack depth, PO item, chunk size), under
+ * each alternative value, keeping a change when it is faster and its results
+ * agree (see sbr_tune_trial). Each timing is the mean of `reps` runs after one
+ * warm-up run. Leaves the fastest accepted setting on the ctx and returns it
+ * in *best (and its time in *best_ms). trials: host array of capacity
+ * trial_cap (may be NULL); *n_trials receives the number of runs tried.
+ * Synchronises; takes about (2 + reps) x 16 runs of the sample. */
+int sbr_autotune(sbr_ctx* ctx, const sbr_request* req, int64_t n_req, const double* freq_hz, int64_t n_freq_total,
+                 double margin_eta, int max_bounces, int pol_mask, int po_mode, const sbr_trace_opts* opt, int reps,
+                 sbr_tune_trial* trials, int trial_cap, int* n_trials, sbr_tuning* best, double* best_ms);
+
 /* Per-ray hits of traced aspect `angle` (needs SBR_TRACE_RECORD_HITS), for
  * parity checks; ray id = j * nu + i. Host outputs (any may be NULL):
  * tri_ids [nu*nv][max_bounces] original triangle index or -1, t [nu*nv][max_bounces]

@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <string>
 #include <vector>
 
@@ -21,7 +22,6 @@ namespace {
 
 constexpr double kC0 = 299792458.0;
 constexpr double kPi = 3.14159265358979323846;
-constexpr long long kChunkRays = 1ll << 27;  // rays per trace chunk (queues: 2 x 12.9 GB at this size)
 constexpr int kMaxBounces = 64;
 
 std::string g_create_error;
@@ -61,6 +61,7 @@ struct DevBuf {
 
 struct AngleHost {
     sbr_ray_grid grid;
+    int tw;               // ray tile width log2 used for this trace
     long long ray_begin;  // first ray (padded layout) over the whole trace
     long long rec_begin, rec_count;
 };
@@ -74,7 +75,8 @@ struct sbr_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    int n_sms = 0, trace_bps = 1;
+    int n_sms = 0;
+    sbr_tuning tune;  // launch and layout parameters (sbr_set_tuning / sbr_autotune)
     std::string err;
     // mesh
     long long n_vert = 0, n_tri = 0;
@@ -212,7 +214,7 @@ void make_grid(const float* bbox, double az_deg, double el_deg, double ds, doubl
     }
 }
 
-AngleDev to_dev(const sbr_ray_grid& g, long long ray_off)
+AngleDev to_dev(const sbr_ray_grid& g, long long ray_off, int tw)
 {
     AngleDev d;
     memset(&d, 0, sizeof(d));
@@ -229,13 +231,33 @@ AngleDev to_dev(const sbr_ray_grid& g, long long ray_off)
     d.eps = (float)g.eps;
     d.nu = (int)g.nu;
     d.nv = (int)g.nv;
-    d.nbu = (int)((g.nu + 7) / 8);
+    d.nbu = (int)((g.nu + (1 << tw) - 1) >> tw);
+    d.tw_log2 = tw;
     d.ray_off = ray_off;
     return d;
 }
 
-// rays an aspect occupies in the processing layout: whole 8 x 4 tiles
-long long tiled_rays(const sbr_ray_grid& g) { return ((g.nu + 7) / 8) * ((g.nv + 3) / 4) * 32; }
+// rays an aspect occupies in the processing layout: whole tiles of 2^tw x 32 / 2^tw
+long long tiled_rays(const sbr_ray_grid& g, int tw)
+{
+    const long long th = 32 >> tw;
+    return ((g.nu + (1ll << tw) - 1) >> tw) * ((g.nv + th - 1) / th) * 32;
+}
+
+int log2i(int v)
+{
+    int k = 0;
+    while ((1 << (k + 1)) <= v) ++k;
+    return k;
+}
+
+bool tuning_ok(const sbr_tuning& t)
+{
+    const bool tile = t.tile_w >= 1 && t.tile_w <= 32 && (t.tile_w & (t.tile_w - 1)) == 0;
+    return tile && t.blocks_per_sm >= 1 && t.blocks_per_sm <= 4 &&
+           (t.stack_depth == 32 || t.stack_depth == 64 || t.stack_depth == 128) && t.chunk_rays_log2 >= 20 &&
+           t.chunk_rays_log2 <= 27 && (t.po_item == 512 || t.po_item == 1024 || t.po_item == 2048);
+}
 
 }  // namespace
 
@@ -295,7 +317,11 @@ int sbr_create(sbr_ctx** out, int device, void* cuda_stream)
         delete c;
         return SBR_ERR_CUDA;
     }
-    c->trace_bps = trace_blocks_per_sm();
+    c->tune.tile_w = 8;
+    c->tune.blocks_per_sm = std::min(4, trace_blocks_per_sm());
+    c->tune.stack_depth = 64;
+    c->tune.chunk_rays_log2 = 27;
+    c->tune.po_item = kPoItemRecords;
     *out = c;
     return SBR_OK;
 }
@@ -426,7 +452,7 @@ namespace {
 struct TraceRun {
     int flags = 0, max_bounces = 1;
     bool escape = false, hits = false, count = false, timed = false;
-    long long chunk_cap = kChunkRays;
+    long long chunk_cap = 1ll << 27;
     int n_blocks = 0;
     int64_t n_launch = 0, n_pass = 0;
     size_t n_ev = 0;
@@ -440,18 +466,18 @@ int plan_chunks(sbr_ctx* c, TraceRun& R, std::vector<int64_t>& cut, long long* t
     long long total = 0, launched = 0;
     for (int64_t a = 0; a < n; ++a) {
         AngleHost& h = c->ang[(size_t)a];
-        if (h.grid.nu > (1ll << 30) || h.grid.nv > (1ll << 30) || tiled_rays(h.grid) > R.chunk_cap)
+        if (h.grid.nu > (1ll << 30) || h.grid.nv > (1ll << 30) || tiled_rays(h.grid, h.tw) > R.chunk_cap)
             return fail(c, SBR_ERR_ARG, "ray grid of aspect %lld too large (%lld x %lld) for a chunk of %lld rays",
                         (long long)a, (long long)h.grid.nu, (long long)h.grid.nv, R.chunk_cap);
         h.ray_begin = total;
         h.rec_begin = h.rec_count = 0;
-        total += tiled_rays(h.grid);
+        total += tiled_rays(h.grid, h.tw);
         launched += h.grid.nu * h.grid.nv;
     }
     cut.assign(1, 0);
     long long acc = 0;
     for (int64_t a = 0; a < n; ++a) {
-        const long long r = tiled_rays(c->ang[(size_t)a].grid);
+        const long long r = tiled_rays(c->ang[(size_t)a].grid, c->ang[(size_t)a].tw);
         if (acc > 0 && acc + r > R.chunk_cap) {
             cut.push_back(a);
             acc = 0;
@@ -463,7 +489,7 @@ int plan_chunks(sbr_ctx* c, TraceRun& R, std::vector<int64_t>& cut, long long* t
     int max_angles = 0;
     for (size_t k = 0; k + 1 < cut.size(); ++k) {
         const AngleHost& last = c->ang[(size_t)cut[k + 1] - 1];
-        max_chunk = std::max(max_chunk, last.ray_begin + tiled_rays(last.grid) - c->ang[(size_t)cut[k]].ray_begin);
+        max_chunk = std::max(max_chunk, last.ray_begin + tiled_rays(last.grid, last.tw) - c->ang[(size_t)cut[k]].ray_begin);
         max_angles = std::max(max_angles, (int)(cut[k + 1] - cut[k]));
     }
     const long long max_tiles = max_chunk / 32;
@@ -488,7 +514,7 @@ int plan_chunks(sbr_ctx* c, TraceRun& R, std::vector<int64_t>& cut, long long* t
         CK(cudaMemsetAsync(c->hit_t.p, 0, sizeof(float) * (size_t)total * B, c->stream), "memset");
         CK(cudaMemsetAsync(c->hit_nb.p, 0, sizeof(int) * (size_t)total, c->stream), "memset");
     }
-    R.n_blocks = c->n_sms * c->trace_bps;
+    R.n_blocks = c->n_sms * c->tune.blocks_per_sm;
     *total_out = total;
     *launched_out = launched;
     return SBR_OK;
@@ -511,7 +537,8 @@ int trace_chunk(sbr_ctx* c, TraceRun& R, int64_t a0, int64_t a1, long long rec_b
 {
     const int na = (int)(a1 - a0);
     const long long base = c->ang[(size_t)a0].ray_begin;
-    const long long chunk_rays = c->ang[(size_t)a1 - 1].ray_begin + tiled_rays(c->ang[(size_t)a1 - 1].grid) - base;
+    const long long chunk_rays = c->ang[(size_t)a1 - 1].ray_begin +
+                                 tiled_rays(c->ang[(size_t)a1 - 1].grid, c->ang[(size_t)a1 - 1].tw) - base;
     unsigned* q_count = c->ctr32.as<unsigned>();
     unsigned* total_dev = q_count + 2 * (kMaxBounces + 2);
     auto pass = [&](const TraceArgs& t) -> cudaError_t {
@@ -523,7 +550,7 @@ int trace_chunk(sbr_ctx* c, TraceRun& R, int64_t a0, int64_t a1, long long rec_b
             R.n_ev += 2;
             cudaEventRecord(e0, c->stream);
         }
-        cudaError_t e = launch_trace(t, R.n_blocks, R.count, c->stream);
+        cudaError_t e = launch_trace(t, R.n_blocks, R.count, c->tune.stack_depth, c->stream);
         if (R.timed) cudaEventRecord(e1, c->stream);
         ++R.n_launch;
         ++R.n_pass;
@@ -538,7 +565,7 @@ int trace_chunk(sbr_ctx* c, TraceRun& R, int64_t a0, int64_t a1, long long rec_b
     for (int i = 0; i < na; ++i) {
         const AngleHost& h = c->ang[(size_t)(a0 + i)];
         ho[i] = h.ray_begin - base;
-        ha[i] = to_dev(h.grid, ho[i]);
+        ha[i] = to_dev(h.grid, ho[i], h.tw);
     }
     ho[na] = chunk_rays;
     CK(cudaMemcpyAsync(c->angles.p, ha, bytes_a, cudaMemcpyHostToDevice, c->stream), "copy angles");
@@ -706,11 +733,11 @@ int po_run(sbr_ctx* c, PoArgs pa, int64_t a0, int64_t a1, const std::vector<int>
         A.nf = nf[(size_t)(a0 + i)];
         A.out_row = out_row[(size_t)(a0 + i)];
         A.part = 0;
-        for (long long r = 0; r < h.rec_count; r += kPoItemRecords) {
+        for (long long r = 0; r < h.rec_count; r += c->tune.po_item) {
             PoItem it;
             it.angle = i;
             it.first = h.rec_begin + r;
-            it.count = (int)std::min<long long>(kPoItemRecords, h.rec_count - r);
+            it.count = (int)std::min<long long>(c->tune.po_item, h.rec_count - r);
             it.f0 = A.f0;
             it.nf = A.nf;
             it.part = part;
@@ -737,6 +764,7 @@ int po_run(sbr_ctx* c, PoArgs pa, int64_t a0, int64_t a1, const std::vector<int>
     pa.freq = c->freq.as<float4>();
     pa.kfreq = c->kfreq.as<double>();
     pa.partial = c->partial.as<double>();
+    pa.item_records = c->tune.po_item;
     CK(launch_po(pa, c->stream), "po reduce");
     CK(launch_po_final(pa.partial, pa.items, c->itemoff.as<PoAngle>(), na, pa.kfreq, pa.n_pol, dE, dR, c->stream),
        "po final");
@@ -753,7 +781,8 @@ struct BatchPlan {
     std::vector<sbr_request> req;
     std::vector<double> freq;
     double eta = 0.0;
-    int max_bounces = 0, pol_mask = 0, po_mode = 0, flags = 0, trace_bps = 0;
+    int max_bounces = 0, pol_mask = 0, po_mode = 0, flags = 0;
+    sbr_tuning tune;
     sbr_trace_opts opt;
     double* E = nullptr;
     double* R = nullptr;
@@ -790,7 +819,8 @@ bool same_submission(const BatchPlan& P, const sbr_ctx* c, const sbr_request* re
                      int64_t n_freq, double eta, int max_bounces, int pol_mask, int po_mode, const sbr_trace_opts& o,
                      double* E, double* R)
 {
-    return P.mesh_gen == c->mesh_gen && P.trace_bps == c->trace_bps && (int64_t)P.req.size() == n_req &&
+    return P.mesh_gen == c->mesh_gen && memcmp(&P.tune, &c->tune, sizeof(sbr_tuning)) == 0 &&
+           (int64_t)P.req.size() == n_req &&
            (int64_t)P.freq.size() == n_freq && P.eta == eta && P.max_bounces == max_bounces &&
            P.pol_mask == pol_mask && P.po_mode == po_mode && P.E == E && P.R == R &&
            memcmp(&P.opt, &o, sizeof(o)) == 0 && memcmp(P.req.data(), req, sizeof(sbr_request) * (size_t)n_req) == 0 &&
@@ -805,7 +835,7 @@ cudaError_t enqueue_plan(const sbr_ctx* c, BatchPlan& P, cudaStream_t st)
     unsigned* q_count = P.ctr32.as<unsigned>();
     unsigned* total_dev = q_count + 2 * (kMaxBounces + 2);
     RayState* qs[2] = {P.q0.as<RayState>(), P.q1.as<RayState>()};
-    const int n_blocks = c->n_sms * c->trace_bps;
+    const int n_blocks = c->n_sms * P.tune.blocks_per_sm;
     const bool escape = P.flags & SBR_TRACE_REQUIRE_ESCAPE;
     for (size_t k = 0; e == cudaSuccess && k + 1 < P.cut.size(); ++k) {
         const int64_t a0 = P.cut[k];
@@ -832,7 +862,7 @@ cudaError_t enqueue_plan(const sbr_ctx* c, BatchPlan& P, cudaStream_t st)
         ta.work = P.ctr64.as<unsigned long long>();
         ta.q_out = qs[0];
         ta.q_out_count = q_count + 1;
-        e = launch_trace(ta, n_blocks, P.count, st);
+        e = launch_trace(ta, n_blocks, P.count, P.tune.stack_depth, st);
         if (e == cudaSuccess) e = scan_popc(ta.mask, P.tilebase.as<unsigned>(), rays / 32, total_dev, P.scan_scr.p, st);
         if (e == cudaSuccess)
             e = launch_angle_offsets(ta.ray_off, ta.tile_base, total_dev, na, P.recoff.as<unsigned>(), st);
@@ -851,13 +881,13 @@ cudaError_t enqueue_plan(const sbr_ctx* c, BatchPlan& P, cudaStream_t st)
                 ta.q_in_count = q_count + b;
                 ta.q_out = qs[b & 1];
                 ta.q_out_count = q_count + b + 1;
-                e = launch_trace(ta, n_blocks, P.count, st);
+                e = launch_trace(ta, n_blocks, P.count, P.tune.stack_depth, st);
             }
         }
         PoAngle* pang = P.pang.as<PoAngle>() + a0;
         if (e == cudaSuccess)
-            e = launch_po_items(P.recoff.as<unsigned>(), pang, na, P.pa.n_pol, P.items.as<PoItem>(), P.nitems.as<int>(),
-                                P.valid.as<long long>() + k, st);
+            e = launch_po_items(P.recoff.as<unsigned>(), pang, na, P.pa.n_pol, P.tune.po_item, P.items.as<PoItem>(),
+                                P.nitems.as<int>(), P.valid.as<long long>() + k, st);
         if (e == cudaSuccess && P.items_bound[k] > 0) {
             PoArgs pa = P.pa;
             pa.rec = P.rec.as<Record>();
@@ -867,6 +897,7 @@ cudaError_t enqueue_plan(const sbr_ctx* c, BatchPlan& P, cudaStream_t st)
             pa.freq = P.freq_t.as<float4>();
             pa.kfreq = P.kfreq.as<double>();
             pa.partial = P.partial.as<double>();
+            pa.item_records = P.tune.po_item;
             e = launch_po(pa, st, (int)std::min<long long>(P.items_bound[k], (long long)c->n_sms * 8));
         }
         if (e == cudaSuccess)
@@ -880,25 +911,26 @@ cudaError_t enqueue_plan(const sbr_ctx* c, BatchPlan& P, cudaStream_t st)
 int build_plan(sbr_ctx* c, BatchPlan& P)
 {
     const int64_t n = (int64_t)P.req.size();
+    const int tw = log2i(P.tune.tile_w);
     std::vector<sbr_ray_grid> g((size_t)n);
     std::vector<long long> begin((size_t)n);
     long long total = 0;
     for (int64_t a = 0; a < n; ++a) {
         make_grid(c->bbox, P.req[(size_t)a].az_deg, P.req[(size_t)a].el_deg, P.req[(size_t)a].ray_spacing_m, P.eta,
                   &P.opt, &g[(size_t)a]);
-        const long long cap = P.opt.chunk_rays > 0 ? std::max<long long>(32, P.opt.chunk_rays) : kChunkRays;
-        if (g[(size_t)a].nu > (1ll << 30) || g[(size_t)a].nv > (1ll << 30) || tiled_rays(g[(size_t)a]) > cap)
+        const long long cap = P.opt.chunk_rays > 0 ? std::max<long long>(32, P.opt.chunk_rays) : (1ll << P.tune.chunk_rays_log2);
+        if (g[(size_t)a].nu > (1ll << 30) || g[(size_t)a].nv > (1ll << 30) || tiled_rays(g[(size_t)a], tw) > cap)
             return fail(c, SBR_ERR_ARG, "ray grid of request %lld too large (%lld x %lld) for a chunk of %lld rays",
                         (long long)a, (long long)g[(size_t)a].nu, (long long)g[(size_t)a].nv, cap);
         begin[(size_t)a] = total;
-        total += tiled_rays(g[(size_t)a]);
+        total += tiled_rays(g[(size_t)a], tw);
         P.launched += g[(size_t)a].nu * g[(size_t)a].nv;
     }
-    const long long cap = P.opt.chunk_rays > 0 ? std::max<long long>(32, P.opt.chunk_rays) : kChunkRays;
+    const long long cap = P.opt.chunk_rays > 0 ? std::max<long long>(32, P.opt.chunk_rays) : (1ll << P.tune.chunk_rays_log2);
     P.cut.assign(1, 0);
     long long acc = 0;
     for (int64_t a = 0; a < n; ++a) {
-        const long long r = tiled_rays(g[(size_t)a]);
+        const long long r = tiled_rays(g[(size_t)a], tw);
         if (acc > 0 && acc + r > cap) {
             P.cut.push_back(a);
             acc = 0;
@@ -915,9 +947,9 @@ int build_plan(sbr_ctx* c, BatchPlan& P)
         long long rays = 0, rec = 0, items = 0, part = 0;
         for (int64_t a = P.cut[k]; a < P.cut[k + 1]; ++a) {
             const sbr_ray_grid& G = g[(size_t)a];
-            rays += tiled_rays(G);
+            rays += tiled_rays(G, tw);
             rec += G.nu * G.nv;
-            const long long ni = (G.nu * G.nv + kPoItemRecords - 1) / kPoItemRecords;
+            const long long ni = (G.nu * G.nv + P.tune.po_item - 1) / P.tune.po_item;
             items += ni;
             part += ni * P.req[(size_t)a].n_freq * 2 * P.pa.n_pol;
         }
@@ -974,7 +1006,7 @@ int build_plan(sbr_ctx* c, BatchPlan& P)
         const long long base = begin[(size_t)P.cut[k]];
         for (int64_t a = P.cut[k]; a < P.cut[k + 1]; ++a) {
             ho[a + (int64_t)k] = begin[(size_t)a] - base;
-            ha[a] = to_dev(g[(size_t)a], begin[(size_t)a] - base);
+            ha[a] = to_dev(g[(size_t)a], begin[(size_t)a] - base, tw);
         }
         ho[P.cut[k + 1] + (int64_t)k] = P.chunk_rays[k];
     }
@@ -1022,10 +1054,14 @@ int sbr_trace(sbr_ctx* c, const double* az_el, int64_t n_angles, double ds, doub
     R.hits = R.flags & SBR_TRACE_RECORD_HITS;
     R.count = R.flags & SBR_TRACE_COUNT_VISITS;
     R.timed = R.flags & SBR_TRACE_TIME_PASSES;
-    R.chunk_cap = (opt && opt->chunk_rays > 0) ? std::max<long long>(32, opt->chunk_rays) : kChunkRays;
+    R.chunk_cap = (opt && opt->chunk_rays > 0) ? std::max<long long>(32, opt->chunk_rays)
+                                                : (1ll << c->tune.chunk_rays_log2);
     c->has_trace = false;
     c->ang.resize((size_t)n_angles);
-    for (int64_t a = 0; a < n_angles; ++a) make_grid(c->bbox, az_el[2 * a], az_el[2 * a + 1], ds, eta, opt, &c->ang[(size_t)a].grid);
+    for (int64_t a = 0; a < n_angles; ++a) {
+        make_grid(c->bbox, az_el[2 * a], az_el[2 * a + 1], ds, eta, opt, &c->ang[(size_t)a].grid);
+        c->ang[(size_t)a].tw = log2i(c->tune.tile_w);
+    }
     std::vector<int64_t> cut;
     long long total = 0, launched = 0;
     int rc = plan_chunks(c, R, cut, &total, &launched);
@@ -1118,11 +1154,14 @@ int sbr_run_batch(sbr_ctx* c, const sbr_request* req, int64_t n_req, const doubl
     R.escape = R.flags & SBR_TRACE_REQUIRE_ESCAPE;
     R.count = R.flags & SBR_TRACE_COUNT_VISITS;
     R.timed = R.flags & SBR_TRACE_TIME_PASSES;
-    R.chunk_cap = (opt && opt->chunk_rays > 0) ? std::max<long long>(32, opt->chunk_rays) : kChunkRays;
+    R.chunk_cap = (opt && opt->chunk_rays > 0) ? std::max<long long>(32, opt->chunk_rays)
+                                                : (1ll << c->tune.chunk_rays_log2);
     c->has_trace = false;
     c->ang.resize((size_t)n_req);
-    for (int64_t r = 0; r < n_req; ++r)
+    for (int64_t r = 0; r < n_req; ++r) {
         make_grid(c->bbox, req[r].az_deg, req[r].el_deg, req[r].ray_spacing_m, eta, opt, &c->ang[(size_t)r].grid);
+        c->ang[(size_t)r].tw = log2i(c->tune.tile_w);
+    }
     std::vector<int64_t> cut;
     long long total = 0, launched = 0;
     rc = plan_chunks(c, R, cut, &total, &launched);
@@ -1208,7 +1247,7 @@ int sbr_submit_batch(sbr_ctx* c, const sbr_request* req, int64_t n_req, const do
         P->opt = o;
         P->flags = o.flags;
         P->count = o.flags & SBR_TRACE_COUNT_VISITS;
-        P->trace_bps = c->trace_bps;
+        P->tune = c->tune;
         P->E = E_dev;
         P->R = rcs_dev;
         P->mesh_gen = c->mesh_gen;
@@ -1278,6 +1317,112 @@ int sbr_sync(sbr_ctx* c, sbr_trace_stats* stats)
     return SBR_OK;
 }
 
+int sbr_get_tuning(const sbr_ctx* c, sbr_tuning* out)
+{
+    if (!c || !out) return SBR_ERR_ARG;
+    *out = c->tune;
+    return SBR_OK;
+}
+
+int sbr_set_tuning(sbr_ctx* c, const sbr_tuning* t)
+{
+    if (!c || !t) return SBR_ERR_ARG;
+    if (!tuning_ok(*t)) return fail(c, SBR_ERR_ARG, "sbr_set_tuning: value out of range");
+    c->tune = *t;
+    return SBR_OK;
+}
+
+int sbr_autotune(sbr_ctx* c, const sbr_request* req, int64_t n_req, const double* freq_hz, int64_t n_freq_total,
+                 double eta, int max_bounces, int pol_mask, int po_mode, const sbr_trace_opts* opt, int reps,
+                 sbr_tune_trial* trials, int trial_cap, int* n_trials, sbr_tuning* best, double* best_ms)
+{
+    if (!c) return SBR_ERR_ARG;
+    if (!req || n_req < 1 || !freq_hz || n_freq_total < 1 || pol_mask <= 0 || pol_mask > 15)
+        return fail(c, SBR_ERR_ARG, "sbr_autotune: empty sample batch");
+    if (n_trials) *n_trials = 0;
+    reps = std::max(1, std::min(reps, 100));
+    int n_pol = 0;
+    for (int q = 0; q < 4; ++q) n_pol += (pol_mask >> q) & 1;
+    long long rows = 0;
+    for (int64_t r = 0; r < n_req; ++r) rows += std::max(0, req[r].n_freq);
+    DevBuf dR;
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    CK(dR.ensure(sizeof(double) * (size_t)std::max(1ll, rows * n_pol)), "alloc autotune output");
+    const sbr_tuning start = c->tune;
+    std::vector<double> ref((size_t)(rows * n_pol)), cur(ref.size());
+    int nt = 0;
+    auto run = [&](const sbr_tuning& t, std::vector<double>& rcs, double* ms) -> int {
+        c->tune = t;
+        int rc = sbr_run_batch(c, req, n_req, freq_hz, n_freq_total, eta, max_bounces, pol_mask, po_mode, opt,
+                               nullptr, dR.as<double>(), 1, nullptr);
+        if (rc != SBR_OK) return rc;
+        if (cudaMemcpy(rcs.data(), dR.p, sizeof(double) * rcs.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return fail(c, SBR_ERR_CUDA, "sbr_autotune: copy results");
+        const auto t0 = std::chrono::steady_clock::now();
+        for (int k = 0; k < reps && rc == SBR_OK; ++k)
+            rc = sbr_run_batch(c, req, n_req, freq_hz, n_freq_total, eta, max_bounces, pol_mask, po_mode, opt,
+                               nullptr, dR.as<double>(), 1, nullptr);
+        if (cudaDeviceSynchronize() != cudaSuccess) return fail(c, SBR_ERR_CUDA, "sbr_autotune: sync");
+        *ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() / reps;
+        return rc;
+    };
+    auto note = [&](const sbr_tuning& t, double ms, int status) {
+        if (trials && nt < trial_cap) {
+            trials[nt].tuning = t;
+            trials[nt].ms = ms;
+            trials[nt].status = status;
+            trials[nt].reserved = 0;
+        }
+        ++nt;
+    };
+    double cur_ms = 0.0;
+    int rc = run(start, ref, &cur_ms);
+    note(start, cur_ms, rc);
+    if (rc != SBR_OK) {
+        c->tune = start;
+        if (n_trials) *n_trials = nt;
+        return rc;
+    }
+    sbr_tuning bestt = start;
+    const int occ = std::min(4, std::max(1, trace_blocks_per_sm()));
+    for (int p = 0; p < 5; ++p) {
+        std::vector<int> vals;
+        if (p == 0)
+            for (int v = 1; v <= occ; ++v) vals.push_back(v);
+        if (p == 1) vals = {32, 16, 8, 4};
+        if (p == 2) vals = {32, 64, 128};
+        if (p == 3) vals = {512, 1024, 2048};
+        if (p == 4) vals = {22, 24, 25, 26, 27};
+        for (int v : vals) {
+            sbr_tuning t = bestt;
+            int* field = p == 0 ? &t.blocks_per_sm
+                                : p == 1 ? &t.tile_w : p == 2 ? &t.stack_depth : p == 3 ? &t.po_item : &t.chunk_rays_log2;
+            if (*field == v) continue;
+            *field = v;
+            double ms = 0.0;
+            int st = run(t, cur, &ms);
+            if (st == SBR_OK) {
+                for (size_t i = 0; i < ref.size(); ++i)
+                    if (ref[i] > -40.0 && !(fabs(cur[i] - ref[i]) <= 0.01)) {
+                        st = 1;
+                        break;
+                    }
+            }
+            note(t, ms, st);
+            if (st == SBR_OK && ms < cur_ms) {
+                cur_ms = ms;
+                bestt = t;
+            }
+        }
+    }
+    c->tune = bestt;
+    c->err.clear();
+    if (n_trials) *n_trials = nt;
+    if (best) *best = bestt;
+    if (best_ms) *best_ms = cur_ms;
+    return SBR_OK;
+}
+
 int sbr_get_hits(sbr_ctx* c, int64_t angle, int32_t* tri_ids, float* t, int32_t* n_bounce)
 {
     if (!c) return SBR_ERR_ARG;
@@ -1286,7 +1431,7 @@ int sbr_get_hits(sbr_ctx* c, int64_t angle, int32_t* tri_ids, float* t, int32_t*
     if (angle < 0 || angle >= (int64_t)c->ang.size()) return fail(c, SBR_ERR_ARG, "sbr_get_hits: angle out of range");
     CK(cudaSetDevice(c->device), "cudaSetDevice");
     const AngleHost& h = c->ang[(size_t)angle];
-    const size_t np = (size_t)tiled_rays(h.grid), B = (size_t)c->max_bounces;
+    const size_t np = (size_t)tiled_rays(h.grid, h.tw), B = (size_t)c->max_bounces;
     std::vector<int> ht(np * B), hn(np);
     std::vector<float> htt(np * B);
     CK(cudaMemcpyAsync(ht.data(), c->hit_tri.as<int>() + (size_t)h.ray_begin * B, sizeof(int) * np * B,
@@ -1299,11 +1444,11 @@ int sbr_get_hits(sbr_ctx* c, int64_t angle, int32_t* tri_ids, float* t, int32_t*
                        c->stream),
        "copy hits");
     CK(cudaStreamSynchronize(c->stream), "hits sync");
-    // processing layout (8 x 4 tiles) -> ray id j * nu + i
-    const long long nbu = (h.grid.nu + 7) / 8;
+    // processing layout (tiles of W x 32 / W) -> ray id j * nu + i
+    const long long W = 1ll << h.tw, nbu = (h.grid.nu + W - 1) / W;
     for (size_t p = 0; p < np; ++p) {
         const long long blk = (long long)(p >> 5), l = (long long)(p & 31);
-        const long long i = (blk % nbu) * 8 + (l & 7), j = (blk / nbu) * 4 + (l >> 3);
+        const long long i = (blk % nbu) * W + (l & (W - 1)), j = (blk / nbu) * (32 / W) + (l >> h.tw);
         if (i >= h.grid.nu || j >= h.grid.nv) continue;
         const size_t id = (size_t)(j * h.grid.nu + i);
         for (size_t b = 0; b < B; ++b) {

@@ -39,8 +39,9 @@ struct AngleDev {            // 128 bytes
     float dA, eps;                      // tube area ds^2, origin offset after a hit
     int nu, nv;
     long long ray_off;                  // first ray of this aspect in the chunk, multiple of 32
-    int nbu;                            // 8 x 4 ray tiles per aperture row: ceil(nu / 8)
-    int pad[3];
+    int nbu;                            // ray tiles per aperture row: ceil(nu / tile width)
+    int tw_log2;                        // tile width 2^tw_log2 (height 32 / width): one warp per tile
+    int pad[2];
 };
 static_assert(sizeof(AngleDev) == 128, "AngleDev layout");
 
@@ -113,7 +114,8 @@ struct TraceArgs {
     int* hit_nb;                  // optional [total_rays]
 };
 int trace_blocks_per_sm();
-cudaError_t launch_trace(const TraceArgs& a, int n_blocks, bool count_visits, cudaStream_t st);
+// stack_depth: 32, 64 or 128 entries of the traversal stack (other values: 64)
+cudaError_t launch_trace(const TraceArgs& a, int n_blocks, bool count_visits, int stack_depth, cudaStream_t st);
 cudaError_t launch_emit_all(const TraceArgs& a, int n_blocks, cudaStream_t st);
 
 // exclusive scan of in[i] (or popcount(in[i])) -> out[i]; total written to *total
@@ -146,6 +148,7 @@ struct PoArgs {
     const PoItem* items;
     int n_items;
     const int* n_items_dev;  // when set, the item count is read here (device-built work lists)
+    int item_records;        // records per item: 512, 1024 or 2048 (kPoItemRecords when 0)
     const float4* freq;   // [n_freq] (kappa_hi, kappa_lo, k, 0), kappa = f / c0 cycles per metre
     const double* kfreq;  // [n_freq] k in FP64 (FP64 phase mode)
     int n_freq;           // entries of the frequency table
@@ -158,12 +161,12 @@ struct PoArgs {
 // n_blocks > 0: persistent grid of that many blocks looping over the items
 cudaError_t launch_po(const PoArgs& a, cudaStream_t st, int n_blocks = 0);
 // Device-built PO work list of one traced chunk: aspect a owns the records
-// [recoff[a], recoff[a + 1]) of the chunk, cut into items of kPoItemRecords.
+// [recoff[a], recoff[a + 1]) of the chunk, cut into items of item_records.
 // Fills angles[a].item_begin / item_end / part (f0, nf, out_row are inputs),
 // items[] and *n_items; *valid = recoff[n_angles] (may be null).
 constexpr int kPoItemRecords = 1024;
-cudaError_t launch_po_items(const unsigned* recoff, PoAngle* angles, int n_angles, int n_pol, PoItem* items,
-                            int* n_items, long long* valid, cudaStream_t st);
+cudaError_t launch_po_items(const unsigned* recoff, PoAngle* angles, int n_angles, int n_pol, int item_records,
+                            PoItem* items, int* n_items, long long* valid, cudaStream_t st);
 // E[row][n_pol][2] and rcs[row][n_pol] for every aspect's rows (fixed-order FP64 sums of the partials)
 cudaError_t launch_po_final(const double* partial, const PoItem* items, const PoAngle* angles, int n_angles,
                             const double* kfreq, int n_pol, double* E, double* rcs, cudaStream_t st);

@@ -25,7 +25,6 @@ namespace sbr {
 namespace {
 
 constexpr int kPoThreads = 256;
-constexpr int kPoPer = 4;  // records per thread
 constexpr int kWarps = kPoThreads / 32;
 
 __device__ __forceinline__ void phase_cs(const PoArgs& a, float4 fq, double kd, float lh, float ll, float& c,
@@ -48,6 +47,8 @@ __device__ __forceinline__ void phase_cs(const PoArgs& a, float4 fq, double kd, 
     }
 }
 
+// kPoPer records per thread: items of kPoPer * kPoThreads records
+template <int kPoPer>
 __global__ void __launch_bounds__(kPoThreads) k_po(const PoArgs a)
 {
     __shared__ float s_red[kWarps][8];
@@ -120,12 +121,12 @@ __global__ void __launch_bounds__(kPoThreads) k_po(const PoArgs a)
     }
 }
 
-static_assert(kPoItemRecords == kPoPer * kPoThreads, "PO item size");
+static_assert(kPoItemRecords == 4 * kPoThreads, "PO item size");
 
 // Work list, stage 1 (one block): 64-bit exclusive scans over the aspects of
 // their item counts and partial sizes, in tiles of the block size.
-__global__ void k_po_items_scan(const unsigned* recoff, PoAngle* angles, int na, int n_pol, int* n_items,
-                                long long* valid)
+__global__ void k_po_items_scan(const unsigned* recoff, PoAngle* angles, int na, int n_pol, int item_records,
+                                int* n_items, long long* valid)
 {
     __shared__ long long s_ni[32], s_np[32];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
@@ -135,7 +136,7 @@ __global__ void k_po_items_scan(const unsigned* recoff, PoAngle* angles, int na,
         long long ni = 0, np = 0;
         if (a < na) {
             const unsigned rc = recoff[a + 1] - recoff[a];
-            ni = (rc + kPoItemRecords - 1) / kPoItemRecords;
+            ni = (rc + item_records - 1) / item_records;
             np = ni * (long long)angles[a].nf * 2 * n_pol;
         }
         // inclusive warp scans, then across warps
@@ -179,7 +180,8 @@ __global__ void k_po_items_scan(const unsigned* recoff, PoAngle* angles, int na,
 }
 
 // Work list, stage 2: one warp per aspect writes its items.
-__global__ void k_po_items_fill(const unsigned* recoff, const PoAngle* angles, int na, int n_pol, PoItem* items)
+__global__ void k_po_items_fill(const unsigned* recoff, const PoAngle* angles, int na, int n_pol, int item_records,
+                                PoItem* items)
 {
     const int lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -189,8 +191,8 @@ __global__ void k_po_items_fill(const unsigned* recoff, const PoAngle* angles, i
         for (int r = lane; r < A.item_end - A.item_begin; r += 32) {
             PoItem it;
             it.angle = a;
-            it.count = (int)min((unsigned)kPoItemRecords, rc - (unsigned)r * kPoItemRecords);
-            it.first = (long long)r0 + (long long)r * kPoItemRecords;
+            it.count = (int)min((unsigned)item_records, rc - (unsigned)r * item_records);
+            it.first = (long long)r0 + (long long)r * item_records;
             it.f0 = A.f0;
             it.nf = A.nf;
             it.part = A.part + (long long)r * A.nf * 2 * n_pol;
@@ -230,17 +232,21 @@ cudaError_t launch_po(const PoArgs& a, cudaStream_t st, int n_blocks)
 {
     const int grid = n_blocks > 0 ? n_blocks : a.n_items;
     if (grid <= 0) return cudaSuccess;
-    k_po<<<grid, kPoThreads, 0, st>>>(a);
+    const int per = (a.item_records > 0 ? a.item_records : kPoItemRecords) / kPoThreads;
+    if (per == 2) k_po<2><<<grid, kPoThreads, 0, st>>>(a);
+    else if (per == 8) k_po<8><<<grid, kPoThreads, 0, st>>>(a);
+    else if (per == 4) k_po<4><<<grid, kPoThreads, 0, st>>>(a);
+    else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
-cudaError_t launch_po_items(const unsigned* recoff, PoAngle* angles, int n_angles, int n_pol, PoItem* items,
-                            int* n_items, long long* valid, cudaStream_t st)
+cudaError_t launch_po_items(const unsigned* recoff, PoAngle* angles, int n_angles, int n_pol, int item_records,
+                            PoItem* items, int* n_items, long long* valid, cudaStream_t st)
 {
-    if (n_angles <= 0) return cudaErrorInvalidValue;
-    k_po_items_scan<<<1, 1024, 0, st>>>(recoff, angles, n_angles, n_pol, n_items, valid);
+    if (n_angles <= 0 || item_records <= 0) return cudaErrorInvalidValue;
+    k_po_items_scan<<<1, 1024, 0, st>>>(recoff, angles, n_angles, n_pol, item_records, n_items, valid);
     const int blocks = (int)std::min<long long>(((long long)n_angles * 32 + 255) / 256, 4096);
-    k_po_items_fill<<<blocks, 256, 0, st>>>(recoff, angles, n_angles, n_pol, items);
+    k_po_items_fill<<<blocks, 256, 0, st>>>(recoff, angles, n_angles, n_pol, item_records, items);
     return cudaGetLastError();
 }
 

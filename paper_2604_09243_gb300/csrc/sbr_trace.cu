@@ -24,7 +24,6 @@ namespace sbr {
 namespace {
 
 constexpr int kTraceThreads = 256;
-constexpr int kStack = 64;
 // Barycentric slack of the FP32 triangle test (2^-12): closes the FP32 cracks
 // along shared edges (FP32 barycentric errors reach ~1e-5 for rays starting
 // metres from centimetre facets); leaf boxes are widened to cover it.
@@ -105,7 +104,7 @@ __device__ __forceinline__ float dot_s(float3 a, float3 b)
 }
 
 // ---------------------------------------------------------------- closest hit
-template <bool kCount>
+template <bool kCount, int kStack>
 __device__ __forceinline__ void closest_hit(const float4* __restrict__ nodes, const float4* __restrict__ tris, float3 o,
                                             float3 d, int skip, int limit, Hit& h, unsigned& nvis, unsigned& ntri,
                                             bool& overflow)
@@ -301,15 +300,16 @@ __device__ __forceinline__ long long ray_global(const TraceArgs& a, const Ray& r
     return a.ray_off[r.angle] + r.local;
 }
 
-// Rays are processed in 8 x 4 tiles: processing index p of an aspect maps to
-// grid point (i, j) = (8 bu + p % 8, 4 bv + (p % 32) / 8), tile p / 32 = bv * nbu + bu,
-// so the 32 lanes of a warp trace a compact 8 x 4 patch of the aperture.
+// Rays are processed in tiles of W x H = 32 grid points (W = 2^tw_log2, 8 x 4
+// by default): processing index p of an aspect maps to grid point
+// (i, j) = (W bu + p % W, H bv + (p % 32) / W), tile p / 32 = bv * nbu + bu,
+// so the 32 lanes of a warp trace a compact patch of the aperture.
 __device__ __forceinline__ void tile_ij(const AngleDev& A, int p, int& i, int& j)
 {
-    const int blk = p >> 5, l = p & 31;
+    const int blk = p >> 5, l = p & 31, tw = A.tw_log2;
     const int bv = blk / A.nbu, bu = blk - bv * A.nbu;
-    i = bu * 8 + (l & 7);
-    j = bv * 4 + (l >> 3);
+    i = (bu << tw) + (l & ((1 << tw) - 1));
+    j = bv * (32 >> tw) + (l >> tw);
 }
 
 __device__ __forceinline__ void emit(const TraceArgs& a, const Ray& r, bool zero)
@@ -387,7 +387,7 @@ __device__ __forceinline__ void flush_stats(const TraceArgs& a, unsigned q, unsi
 }
 
 // ---------------------------------------------------------------- pass 0: primary rays
-template <bool kCount>
+template <bool kCount, int kStack>
 __global__ void __launch_bounds__(kTraceThreads, 4) k_primary(const TraceArgs a)
 {
     const int lane = threadIdx.x & 31;
@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_primary(const TraceArgs a)
             r.nb = 0;
             r.last = -1;
             Hit h;
-            closest_hit<kCount>(a.nodes, a.tris, r.o, r.d, -1, a.visit_limit, h, nvis, ntri, ovf);
+            closest_hit<kCount, kStack>(a.nodes, a.tris, r.o, r.d, -1, a.visit_limit, h, nvis, ntri, ovf);
             ++nq;
             if (h.k >= 0) {
                 hit = true;
@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_primary(const TraceArgs a)
 }
 
 // ---------------------------------------------------------------- pass b >= 1: live rays
-template <bool kCount>
+template <bool kCount, int kStack>
 __global__ void __launch_bounds__(kTraceThreads, 4) k_bounce(const TraceArgs a)
 {
     const int lane = threadIdx.x & 31;
@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_bounce(const TraceArgs a)
             load_state(a.q_in, idx, r);
             const AngleDev& A = a.angles[r.angle];
             Hit h;
-            closest_hit<kCount>(a.nodes, a.tris, r.o, r.d, r.last, a.visit_limit, h, nvis, ntri, ovf);
+            closest_hit<kCount, kStack>(a.nodes, a.tris, r.o, r.d, r.last, a.visit_limit, h, nvis, ntri, ovf);
             ++nq;
             if (h.k < 0) {
                 emit(a, r, false);                     // escaped: its last hit radiates
@@ -500,19 +500,27 @@ __global__ void k_angle_offsets(const long long* ray_off, const unsigned* tile_b
 int trace_blocks_per_sm()
 {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bounce<false>, kTraceThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bounce<false, 64>, kTraceThreads, 0);
     return nb > 0 ? nb : 1;
 }
 
-cudaError_t launch_trace(const TraceArgs& a, int n_blocks, bool count_visits, cudaStream_t st)
+template <int kStack>
+void launch_trace_s(const TraceArgs& a, int n_blocks, bool count_visits, cudaStream_t st)
 {
     if (a.bounce == 0) {
-        if (count_visits) k_primary<true><<<n_blocks, kTraceThreads, 0, st>>>(a);
-        else k_primary<false><<<n_blocks, kTraceThreads, 0, st>>>(a);
+        if (count_visits) k_primary<true, kStack><<<n_blocks, kTraceThreads, 0, st>>>(a);
+        else k_primary<false, kStack><<<n_blocks, kTraceThreads, 0, st>>>(a);
     } else {
-        if (count_visits) k_bounce<true><<<n_blocks, kTraceThreads, 0, st>>>(a);
-        else k_bounce<false><<<n_blocks, kTraceThreads, 0, st>>>(a);
+        if (count_visits) k_bounce<true, kStack><<<n_blocks, kTraceThreads, 0, st>>>(a);
+        else k_bounce<false, kStack><<<n_blocks, kTraceThreads, 0, st>>>(a);
     }
+}
+
+cudaError_t launch_trace(const TraceArgs& a, int n_blocks, bool count_visits, int stack_depth, cudaStream_t st)
+{
+    if (stack_depth == 32) launch_trace_s<32>(a, n_blocks, count_visits, st);
+    else if (stack_depth == 128) launch_trace_s<128>(a, n_blocks, count_visits, st);
+    else launch_trace_s<64>(a, n_blocks, count_visits, st);
     return cudaGetLastError();
 }
 

@@ -30,7 +30,7 @@ TRACE_NO_GRAPH = 32
 EXPORTS = ("sbr_version", "sbr_create", "sbr_destroy", "sbr_last_error", "sbr_load_mesh", "sbr_get_bbox",
            "sbr_build_bvh", "sbr_ray_grid_for", "sbr_ray_grid_box", "sbr_trace", "sbr_po_integrate", "sbr_get_hits",
            "sbr_get_records", "sbr_spacing_for", "sbr_po_integrate_noalloc", "sbr_run_batch", "sbr_submit_batch",
-           "sbr_sync",
+           "sbr_sync", "sbr_get_tuning", "sbr_set_tuning", "sbr_autotune",
            "sbr_surrogate_create", "sbr_surrogate_destroy", "sbr_surrogate_last_error", "sbr_surrogate_num_params",
            "sbr_surrogate_params", "sbr_surrogate_fourier", "sbr_surrogate_train", "sbr_surrogate_grads",
            "sbr_surrogate_predict", "sbr_gemm_bf16_tn")
@@ -49,6 +49,18 @@ class BvhOpts(C.Structure):
 class TraceOpts(C.Structure):
     _fields_ = [("window_m", C.c_double), ("offset_u", C.c_double), ("offset_v", C.c_double),
                 ("flags", C.c_int), ("chunk_rays", C.c_int)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("tile_w", C.c_int), ("blocks_per_sm", C.c_int), ("stack_depth", C.c_int),
+                ("chunk_rays_log2", C.c_int), ("po_item", C.c_int)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class TuneTrial(C.Structure):
+    _fields_ = [("tuning", Tuning), ("ms", C.c_double), ("status", C.c_int), ("reserved", C.c_int)]
 
 
 class TraceStats(C.Structure):
@@ -108,6 +120,10 @@ def lib() -> C.CDLL:
         "sbr_submit_batch": ([vp, P(Request), i64, P(d), i64, d, C.c_int, C.c_int, C.c_int, P(TraceOpts), vp, vp],
                              C.c_int),
         "sbr_sync": ([vp, P(TraceStats)], C.c_int),
+        "sbr_get_tuning": ([vp, P(Tuning)], C.c_int),
+        "sbr_set_tuning": ([vp, P(Tuning)], C.c_int),
+        "sbr_autotune": ([vp, P(Request), i64, P(d), i64, d, C.c_int, C.c_int, C.c_int, P(TraceOpts), C.c_int,
+                          P(TuneTrial), C.c_int, P(C.c_int), P(Tuning), P(d)], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -318,6 +334,35 @@ class Context:
         rp = rcs_out.data_ptr() if rcs_out is not None else None
         self._check(lib().sbr_submit_batch(self._h, arr, len(reqs), freqs.ctypes.data_as(C.POINTER(C.c_double)),
                                            len(freqs), float(eta), int(max_bounces), pm, m, C.byref(o), ep, rp))
+
+    def tuning(self) -> dict:
+        t = Tuning()
+        self._check(lib().sbr_get_tuning(self._h, C.byref(t)))
+        return t.as_dict()
+
+    def set_tuning(self, **kw):
+        """Change some tuning fields (tile_w, blocks_per_sm, stack_depth, chunk_rays_log2, po_item)."""
+        t = Tuning(**{**self.tuning(), **kw})
+        self._check(lib().sbr_set_tuning(self._h, C.byref(t)))
+
+    def autotune(self, requests, eta=0.05, max_bounces=1, pols="HH,VV", mode="vector", phase="compensated",
+                 flags=0, chunk_rays=0, window=0.0, offset=(0.0, 0.0), reps=3):
+        """sbr_autotune on a sample batch; returns (best tuning dict, best ms, list of trials)."""
+        reqs, arr, freqs = _requests(requests)
+        pm = _pols(pols)
+        m = (PO_PAPER_SCALAR if mode == "scalar" else PO_VECTOR) | PHASE[phase]
+        o = _opts(window, offset, flags, chunk_rays)
+        cap = 64
+        tr = (TuneTrial * cap)()
+        n = C.c_int()
+        best = Tuning()
+        ms = C.c_double()
+        self._check(lib().sbr_autotune(self._h, arr, len(reqs), freqs.ctypes.data_as(C.POINTER(C.c_double)),
+                                       len(freqs), float(eta), int(max_bounces), pm, m, C.byref(o), int(reps), tr, cap,
+                                       C.byref(n), C.byref(best), C.byref(ms)))
+        trials = [dict(tr[k].tuning.as_dict(), ms=float(tr[k].ms), status=int(tr[k].status))
+                  for k in range(min(n.value, cap))]
+        return best.as_dict(), float(ms.value), trials
 
     def sync(self) -> dict:
         """Wait for the last submitted batch; its statistics."""

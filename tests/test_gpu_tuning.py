@@ -1,0 +1,98 @@
+"""Tuning parameters (ray tile, stack depth, blocks per SM, PO item, chunk size)
+and the autotuner: hits are the same under every setting, fields agree to
+rounding, and the autotuner keeps only settings whose results agree."""
+import numpy as np
+import pytest
+
+import sbr_inputs as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2604_09243_gb300 import build
+
+    build.build()
+    import paper_2604_09243_gb300 as G
+
+    return G
+
+
+@pytest.fixture(scope="module")
+def tri_case():
+    return S.trihedral_case()
+
+
+def _trace(c, case, angles, **kw):
+    c.trace(angles, case["spacing"], eta=case["eta"], max_bounces=case["max_bounces"], offset=case["offset"],
+            flags=kw.pop("flags", 0), **kw)
+
+
+@pytest.mark.parametrize("setting", [dict(tile_w=1), dict(tile_w=4), dict(tile_w=32), dict(stack_depth=32),
+                                     dict(stack_depth=128), dict(blocks_per_sm=1), dict(po_item=512),
+                                     dict(po_item=2048), dict(chunk_rays_log2=20)])
+def test_setting_keeps_hits_and_fields(G, tri_case, setting):
+    case = tri_case
+    angles = case["angles"][[0, 45, 90, 135, 180]]
+    out = []
+    for s in ({}, setting):
+        with G.Context(0) as c:
+            c.load_mesh(case["xyz"], case["tri"])
+            if s:
+                c.set_tuning(**s)
+                assert all(c.tuning()[k] == v for k, v in s.items())
+            _trace(c, case, angles, flags=G.TRACE_RECORD_HITS)
+            hits = [c.get_hits(a) for a in range(len(angles))]
+            E, R = c.po_integrate([10e9, 7e9], "HH,VV")
+            out.append((hits, E, R))
+    (h0, E0, R0), (h1, E1, R1) = out
+    for a, b in zip(h0, h1):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+    assert np.max(np.abs(E1 - E0)) <= 1e-5 * np.max(np.abs(E0))
+    big = R0 > -40
+    assert np.max(np.abs(R1[big] - R0[big])) < 1e-3
+
+
+def test_bad_settings_refused(G):
+    with G.Context(0) as c:
+        before = c.tuning()
+        for bad in (dict(tile_w=3), dict(tile_w=64), dict(blocks_per_sm=0), dict(blocks_per_sm=5),
+                    dict(stack_depth=48), dict(po_item=300), dict(chunk_rays_log2=19), dict(chunk_rays_log2=28)):
+            with pytest.raises(G.SbrError):
+                c.set_tuning(**bad)
+        assert c.tuning() == before
+
+
+def test_submitted_batch_follows_tuning(G, tri_case):
+    torch = pytest.importorskip("torch")
+    case = tri_case
+    rng = np.random.default_rng(3)
+    reqs = [dict(az=float(rng.uniform(0, 90)), el=35.26, freqs=np.array([6e9, 10e9]),
+                 spacing=S.spacing_for(10e9, 6.0)) for _ in range(6)]
+    with G.Context(0) as c:
+        c.load_mesh(case["xyz"], case["tri"])
+        c.set_tuning(tile_w=16, po_item=512, stack_depth=32)
+        _, Rb, _ = c.run_batch(reqs, max_bounces=3, offset=case["offset"])
+        R = torch.zeros((12, 2), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        c.submit_batch(reqs, None, R, max_bounces=3, offset=case["offset"])
+        c.sync()
+        assert np.array_equal(R.cpu().numpy(), np.concatenate(Rb))
+
+
+def test_autotune_keeps_an_accepted_setting(G, tri_case):
+    case = tri_case
+    rng = np.random.default_rng(4)
+    reqs = [dict(az=float(rng.uniform(0, 90)), el=35.26, freqs=np.array([10e9]), spacing=case["spacing"])
+            for _ in range(8)]
+    with G.Context(0) as c:
+        c.load_mesh(case["xyz"], case["tri"])
+        best, ms, trials = c.autotune(reqs, max_bounces=3, offset=case["offset"], reps=2)
+        assert c.tuning() == best
+        assert len(trials) >= 10 and ms > 0
+        ok = [t for t in trials if t["status"] == 0]
+        assert ok[0]["ms"] >= ms  # the starting setting is never faster than the kept one
+        assert any(all(t[k] == best[k] for k in best) for t in ok)
+        assert ms == min(t["ms"] for t in ok if all(t[k] == best[k] for k in best))
