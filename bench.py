@@ -42,10 +42,14 @@ if ROOT not in sys.path:
 
 import sbr_inputs as S  # noqa: E402
 
-# FP32 operations of one node visit (two slab tests and the ordering compare)
-# and of one triangle test (Moller-Trumbore form up to the inside decision),
-# counted from the traversal routine in sbr_trace.cu
+# FP32 operations of one node visit and of one triangle test (Moller-Trumbore
+# form up to the inside decision), counted from the traversal routines in
+# sbr_trace.cu. Binary node: two slab tests (6 FMA, 12 min/max, 1 scale, 1
+# compare each) and the ordering compare. 4-wide node: four slab tests with
+# the near/far slabs picked per ray (6 FMA, 6 min/max, 1 scale, 1 compare
+# each) and a 5-exchange sorting network (1 compare, 4 selects each).
 OPS_NODE = 41
+OPS_NODE4 = 81
 OPS_TRI = 38
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
@@ -525,7 +529,8 @@ def run_sbr(args, case, ws, rank, local, pg):
     e2e_value = ws * bounces * args.steps / t_e2e
 
     # --- roofline of the transport passes (FP32 issue bound)
-    ops = OPS_NODE * cnt["node_visits"] + OPS_TRI * cnt["tri_tests"]
+    wide = ctx.tuning()["bvh_width"] == 4
+    ops = (OPS_NODE4 if wide else OPS_NODE) * cnt["node_visits"] + OPS_TRI * cnt["tri_tests"]
     pass_s = float(np.mean([s["pass_ms"] for s in stats])) / 1e3
     pk, src = peaks()
     peak_ops = SM_COUNT * FP32_LANES_PER_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
@@ -538,7 +543,8 @@ def run_sbr(args, case, ws, rank, local, pg):
             "angles_per_s": ws * na * args.steps / t_dev,
             "rays_launched_per_step": stats[0]["rays_launched"], "ray_bounces_per_step": bounces,
             "valid_rays_per_step": stats[0]["valid_rays"],
-            "roofline": {"bound": "alu", "kernel": "k_primary+k_bounce (transport passes)",
+            "roofline": {"bound": "alu", "kernel": "k_primary+k_bounce (transport passes, "
+                                                   f"{'4-wide' if wide else 'binary'} tree)",
                          "achieved": achieved, "peak": peak_ops, "unit": "T FP32-op/s",
                          "frac": achieved / peak_ops, "traffic": None,
                          "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "

@@ -150,7 +150,8 @@ int sbr_get_bbox(sbr_ctx* ctx, float* bbox6);
  * builder, this is a GPU LBVH): 63-bit Morton codes of the triangle centroids,
  * device radix sort, Karras hierarchy, bottom-up AABB refit and SAH leaf
  * collapse with C_T, C_I and leaf_max from `opt` (NULL = defaults), triangles
- * reordered so each leaf is a contiguous range. Runs on the context stream. */
+ * reordered so each leaf is a contiguous range; then the 4-wide collapse of
+ * that tree (sbr_tuning.bvh_width picks the one traversed). Synchronises. */
 int sbr_build_bvh(sbr_ctx* ctx, const sbr_bvh_opts* opt);
 
 /* Ray grid of one aspect for the loaded mesh (Eq. L1-L3), computed on the host.
@@ -258,6 +259,11 @@ typedef struct {
                             reported as a stack overflow (SBR_ERR_STACK_OVERFLOW) */
     int chunk_rays_log2; /* rays per chunk when opt->chunk_rays is 0: 2^20 .. 2^27 (default 27) */
     int po_item;         /* records per PO block: 512, 1024 or 2048 (default 1024) */
+    int bvh_width;       /* 2: binary LBVH; 4: its 4-wide collapse (same boxes, fewer dependent fetches);
+                            default 2 */
+    int packet;          /* 1: the 32 rays of a warp walk the binary tree together (one broadcast fetch
+                            per node, no divergence; each ray still tests only the boxes it enters);
+                            needs bvh_width 2 and stack_depth <= 64; default 0 */
 } sbr_tuning;
 int sbr_get_tuning(const sbr_ctx* ctx, sbr_tuning* out);
 /* SBR_ERR_ARG for a value outside the ranges above. */
@@ -277,13 +283,14 @@ typedef struct {
 
 /* Autotuner: times sbr_run_batch on the given sample batch (arguments as for
  * sbr_run_batch) under the current setting and then, one parameter at a
- * time (blocks per SM, ray tile, stack depth, PO item, chunk size), under
+ * time (traversal: binary / 4-wide / warp-cooperative, blocks per SM, ray
+ * tile, stack depth, PO item, chunk size), under
  * each alternative value, keeping a change when it is faster and its results
  * agree (see sbr_tune_trial). Each timing is the mean of `reps` runs after one
  * warm-up run. Leaves the fastest accepted setting on the ctx and returns it
  * in *best (and its time in *best_ms). trials: host array of capacity
  * trial_cap (may be NULL); *n_trials receives the number of runs tried.
- * Synchronises; takes about (2 + reps) x 16 runs of the sample. */
+ * Synchronises; takes about (2 + reps) x 18 runs of the sample. */
 int sbr_autotune(sbr_ctx* ctx, const sbr_request* req, int64_t n_req, const double* freq_hz, int64_t n_freq_total,
                  double margin_eta, int max_bounces, int pol_mask, int po_mode, const sbr_trace_opts* opt, int reps,
                  sbr_tune_trial* trials, int trial_cap, int* n_trials, sbr_tuning* best, double* best_ms);

@@ -85,6 +85,8 @@ struct sbr_ctx {
     bool has_mesh = false, has_bvh = false;
     // BVH
     DevBuf nodes, tris, bvh_scratch, bbox_dev, err_dev;
+    DevBuf nodes4;  // 4-wide collapse of the binary tree
+    int n_nodes4 = 0;
     // trace
     DevBuf angles, rayoff, mask, tilebase, scan_scr, recoff, q0, q1, ctr64, ctr32, stats, rec;
     DevBuf hit_tri, hit_t, hit_nb;
@@ -254,7 +256,8 @@ int log2i(int v)
 bool tuning_ok(const sbr_tuning& t)
 {
     const bool tile = t.tile_w >= 1 && t.tile_w <= 32 && (t.tile_w & (t.tile_w - 1)) == 0;
-    return tile && t.blocks_per_sm >= 1 && t.blocks_per_sm <= 4 &&
+    const bool trav = t.packet == 0 || (t.packet == 1 && t.bvh_width == 2 && t.stack_depth <= 64);
+    return tile && trav && (t.bvh_width == 2 || t.bvh_width == 4) && t.blocks_per_sm >= 1 && t.blocks_per_sm <= 4 &&
            (t.stack_depth == 32 || t.stack_depth == 64 || t.stack_depth == 128) && t.chunk_rays_log2 >= 20 &&
            t.chunk_rays_log2 <= 27 && (t.po_item == 512 || t.po_item == 1024 || t.po_item == 2048);
 }
@@ -322,6 +325,8 @@ int sbr_create(sbr_ctx** out, int device, void* cuda_stream)
     c->tune.stack_depth = 64;
     c->tune.chunk_rays_log2 = 27;
     c->tune.po_item = kPoItemRecords;
+    c->tune.bvh_width = 2;
+    c->tune.packet = 0;
     *out = c;
     return SBR_OK;
 }
@@ -331,7 +336,7 @@ void sbr_destroy(sbr_ctx* c)
     if (!c) return;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
-    DevBuf* all[] = {&c->xyz, &c->tri, &c->nodes, &c->tris, &c->bvh_scratch, &c->bbox_dev, &c->err_dev,
+    DevBuf* all[] = {&c->xyz, &c->tri, &c->nodes, &c->tris, &c->bvh_scratch, &c->bbox_dev, &c->err_dev, &c->nodes4,
                      &c->angles, &c->rayoff, &c->mask, &c->tilebase, &c->scan_scr, &c->recoff, &c->q0, &c->q1,
                      &c->ctr64, &c->ctr32, &c->stats, &c->rec, &c->hit_tri, &c->hit_t, &c->hit_nb, &c->items,
                      &c->itemoff, &c->freq, &c->kfreq, &c->partial, &c->E, &c->rcs};
@@ -420,6 +425,16 @@ int sbr_build_bvh(sbr_ctx* c, const sbr_bvh_opts* opt)
         return fail(c, SBR_ERR_ARG, "sbr_build_bvh: triangle index out of range");
     }
     memcpy(c->bbox, hb, sizeof(c->bbox));
+    // 4-wide tree over the same boxes; its work queues reuse the (now free) build scratch
+    CK(c->nodes4.ensure(sizeof(float4) * kNode4Float4 * (size_t)n_nodes), "alloc 4-wide nodes");
+    {
+        char* scr = (char*)c->bvh_scratch.p;
+        const size_t qb = ((sizeof(int2) * (size_t)n_nodes + 255) / 256) * 256;
+        if (2 * qb + 256 > c->bvh_scratch.cap) return fail(c, SBR_ERR_ARG, "sbr_build_bvh: scratch too small");
+        CK(bvh4_collapse(c->nodes.as<float4>(), c->nodes4.as<float4>(), (int2*)scr, (int2*)(scr + qb),
+                         (int*)(scr + 2 * qb), &c->n_nodes4, c->stream),
+           "4-wide collapse");
+    }
     c->has_bvh = true;
     c->has_trace = false;
     return SBR_OK;
@@ -574,7 +589,9 @@ int trace_chunk(sbr_ctx* c, TraceRun& R, int64_t a0, int64_t a1, long long rec_b
     CK(cudaMemsetAsync(c->ctr32.p, 0, c->ctr32.cap, c->stream), "memset counters");
     TraceArgs ta;
     memset(&ta, 0, sizeof(ta));
-    ta.nodes = c->nodes.as<float4>();
+    ta.wide = c->tune.bvh_width == 4;
+    ta.packet = c->tune.packet;
+    ta.nodes = ta.wide ? c->nodes4.as<float4>() : c->nodes.as<float4>();
     ta.tris = c->tris.as<float4>();
     ta.angles = c->angles.as<AngleDev>();
     ta.ray_off = c->rayoff.as<long long>();
@@ -846,7 +863,9 @@ cudaError_t enqueue_plan(const sbr_ctx* c, BatchPlan& P, cudaStream_t st)
         if (e != cudaSuccess) break;
         TraceArgs ta;
         memset(&ta, 0, sizeof(ta));
-        ta.nodes = c->nodes.as<float4>();
+        ta.wide = P.tune.bvh_width == 4;
+        ta.packet = P.tune.packet;
+        ta.nodes = ta.wide ? c->nodes4.as<float4>() : c->nodes.as<float4>();
         ta.tris = c->tris.as<float4>();
         ta.angles = P.angles.as<AngleDev>() + a0;
         ta.ray_off = P.rayoff.as<long long>() + a0 + (int64_t)k;  // chunk k's table has na + 1 entries
@@ -1385,20 +1404,30 @@ int sbr_autotune(sbr_ctx* c, const sbr_request* req, int64_t n_req, const double
     }
     sbr_tuning bestt = start;
     const int occ = std::min(4, std::max(1, trace_blocks_per_sm()));
-    for (int p = 0; p < 5; ++p) {
+    // parameter 0 is the traversal: binary per lane, 4-wide per lane, binary per warp
+    for (int p = 0; p < 6; ++p) {
         std::vector<int> vals;
-        if (p == 0)
+        if (p == 0) vals = {0, 1, 2};
+        if (p == 1)
             for (int v = 1; v <= occ; ++v) vals.push_back(v);
-        if (p == 1) vals = {32, 16, 8, 4};
-        if (p == 2) vals = {32, 64, 128};
-        if (p == 3) vals = {512, 1024, 2048};
-        if (p == 4) vals = {22, 24, 25, 26, 27};
+        if (p == 2) vals = {32, 16, 8, 4};
+        if (p == 3) vals = {32, 64, 128};
+        if (p == 4) vals = {512, 1024, 2048};
+        if (p == 5) vals = {22, 24, 25, 26, 27};
         for (int v : vals) {
             sbr_tuning t = bestt;
-            int* field = p == 0 ? &t.blocks_per_sm
-                                : p == 1 ? &t.tile_w : p == 2 ? &t.stack_depth : p == 3 ? &t.po_item : &t.chunk_rays_log2;
-            if (*field == v) continue;
-            *field = v;
+            if (p == 0) {
+                const int w = v == 1 ? 4 : 2, pk = v == 2 ? 1 : 0;
+                if (t.bvh_width == w && t.packet == pk) continue;
+                t.bvh_width = w;
+                t.packet = pk;
+                if (pk && t.stack_depth > 64) t.stack_depth = 64;
+            } else {
+                int* fields[6] = {nullptr, &t.blocks_per_sm, &t.tile_w, &t.stack_depth, &t.po_item, &t.chunk_rays_log2};
+                if (*fields[p] == v) continue;
+                *fields[p] = v;
+            }
+            if (!tuning_ok(t)) continue;
             double ms = 0.0;
             int st = run(t, cur, &ms);
             if (st == SBR_OK) {

@@ -376,6 +376,99 @@ __global__ void __launch_bounds__(kThreads) k_reorder(const float* xyz, const in
     tris[3 * p + 2] = make_float4(cx - ax, cy - ay, cz - az, 0.f);
 }
 
+// ---------------------------------------------------------------- 4-wide collapse
+__device__ __forceinline__ float half_area(float4 lo, float4 hi)
+{
+    const float dx = hi.x - lo.x, dy = hi.y - lo.y, dz = hi.z - lo.z;
+    return dx * dy + dy * dz + dz * dx;
+}
+
+// children (box, ref) of binary node b; a missing child has ref kEmptyRef
+__device__ __forceinline__ void binary_children(const float4* nodes2, int b, float4* lo, float4* hi, int* ref)
+{
+    const float4 n0 = nodes2[4 * (size_t)b], n1 = nodes2[4 * (size_t)b + 1], n2 = nodes2[4 * (size_t)b + 2],
+                 n3 = nodes2[4 * (size_t)b + 3];
+    lo[0] = make_float4(n0.x, n0.z, n2.x, 0.f);
+    hi[0] = make_float4(n0.y, n0.w, n2.y, 0.f);
+    lo[1] = make_float4(n1.x, n1.z, n2.z, 0.f);
+    hi[1] = make_float4(n1.y, n1.w, n2.w, 0.f);
+    ref[0] = __float_as_int(n3.x);
+    ref[1] = __float_as_int(n3.y);
+}
+
+// One level: every queued (binary node, 4-wide slot) pair opens binary
+// children, largest surface area first, until it has 4 children or only
+// leaves; its internal children get new slots and go to the next level's queue.
+__global__ void __launch_bounds__(kThreads) k_collapse4(const float4* nodes2, const int2* qin, int nin, int2* qout,
+                                                        int* nout, int* count4, float4* nodes4)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nin) return;
+    const int2 job = qin[w];
+    float4 lo[4], hi[4];
+    int ref[4];
+    int cnt = 0;
+    {
+        float4 l2[2], h2[2];
+        int r2[2];
+        binary_children(nodes2, job.x, l2, h2, r2);
+        for (int c = 0; c < 2; ++c)
+            if (r2[c] != kEmptyRef) {
+                lo[cnt] = l2[c];
+                hi[cnt] = h2[c];
+                ref[cnt] = r2[c];
+                ++cnt;
+            }
+    }
+    while (cnt < 4) {
+        int best = -1;
+        float ba = -1.f;
+        for (int c = 0; c < cnt; ++c)
+            if (ref[c] >= 0) {
+                const float a = half_area(lo[c], hi[c]);
+                if (a > ba) {
+                    ba = a;
+                    best = c;
+                }
+            }
+        if (best < 0) break;
+        float4 l2[2], h2[2];
+        int r2[2];
+        binary_children(nodes2, ref[best], l2, h2, r2);
+        lo[best] = l2[0];
+        hi[best] = h2[0];
+        ref[best] = r2[0];
+        if (r2[1] != kEmptyRef) {
+            lo[cnt] = l2[1];
+            hi[cnt] = h2[1];
+            ref[cnt] = r2[1];
+            ++cnt;
+        }
+    }
+    for (int c = 0; c < cnt; ++c)
+        if (ref[c] >= 0) {
+            const int t = atomicAdd(count4, 1);
+            qout[atomicAdd(nout, 1)] = make_int2(ref[c], t);
+            ref[c] = t;
+        }
+    float v[6][4];
+    int r[4];
+    for (int c = 0; c < 4; ++c) {
+        const bool on = c < cnt;
+        v[0][c] = on ? lo[c].x : FLT_MAX;
+        v[1][c] = on ? hi[c].x : -FLT_MAX;
+        v[2][c] = on ? lo[c].y : FLT_MAX;
+        v[3][c] = on ? hi[c].y : -FLT_MAX;
+        v[4][c] = on ? lo[c].z : FLT_MAX;
+        v[5][c] = on ? hi[c].z : -FLT_MAX;
+        r[c] = on ? ref[c] : kEmptyRef;
+    }
+    float4* o = nodes4 + (size_t)kNode4Float4 * job.y;
+    for (int k = 0; k < 6; ++k) o[k] = make_float4(v[k][0], v[k][1], v[k][2], v[k][3]);
+    o[6] = make_float4(__int_as_float(r[0]), __int_as_float(r[1]), __int_as_float(r[2]), __int_as_float(r[3]));
+    o[7] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 struct Carve {
     char* p;
     size_t off, cap;
@@ -469,6 +562,34 @@ cudaError_t bvh_build(const BvhBuild& b, cudaStream_t st)
     k_emit<<<ge, kThreads, 0, st>>>(n, left, right, first, lbox, nbox, ncnt, ncol, b.nodes);
     k_reorder<<<g, kThreads, 0, st>>>(b.xyz, b.tri, b.n_vert, vi, n, b.tris);
     return cudaGetLastError();
+}
+
+cudaError_t bvh4_collapse(const float4* nodes2, float4* nodes4, int2* queue_a, int2* queue_b, int* counters,
+                          int* n_nodes4, cudaStream_t st)
+{
+    // counters[0]: 4-wide nodes allocated; counters[1]: next-level queue length
+    const int2 root = make_int2(0, 0);
+    const int one = 1;
+    cudaError_t e = cudaMemcpyAsync(queue_a, &root, sizeof(int2), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(counters, &one, sizeof(int), cudaMemcpyHostToDevice, st);
+    int nin = 1;
+    int2 *qi = queue_a, *qo = queue_b;
+    for (int level = 0; e == cudaSuccess && nin > 0; ++level) {
+        if (level > 4096) return cudaErrorInvalidValue;  // deeper than any binary tree of < 2^27 leaves
+        e = cudaMemsetAsync(counters + 1, 0, sizeof(int), st);
+        if (e != cudaSuccess) break;
+        k_collapse4<<<(nin + kThreads - 1) / kThreads, kThreads, 0, st>>>(nodes2, qi, nin, qo, counters + 1,
+                                                                          counters, nodes4);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&nin, counters + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        int2* t = qi;
+        qi = qo;
+        qo = t;
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(n_nodes4, counters, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e;
 }
 
 }  // namespace sbr

@@ -70,6 +70,20 @@ enum { kStatQueries = 0, kStatNodes = 1, kStatTris = 2, kStatOverflow = 3, kStat
 // ---------------------------------------------------------------- launchers
 // All launchers enqueue on `st` and return the launch error (cudaSuccess if none).
 
+// 4-wide BVH (collapsed from the binary one): node k is 8 float4 (128 bytes)
+//   f0 = lo.x, f1 = hi.x, f2 = lo.y, f3 = hi.y, f4 = lo.z, f5 = hi.z  (children 0..3 in x, y, z, w)
+//   f6 = (ref 0, ref 1, ref 2, ref 3)  (int bits, same encoding as above; kEmptyRef for a missing child,
+//         whose box is empty: lo = +FLT_MAX, hi = -FLT_MAX)
+//   f7 = 0
+// Node 0 is the root. Each child box is the box of a binary node or leaf, so
+// the 4-wide tree tests exactly the boxes the binary tree would.
+constexpr int kNode4Float4 = 8;
+// Collapse the binary node array (root 0) into nodes4 (room for max(n_tri - 1, 1) nodes).
+// queue_a / queue_b: int2 [max(n_tri - 1, 1)]; counters: int [4]. Synchronises once per level;
+// *n_nodes4 receives the node count.
+cudaError_t bvh4_collapse(const float4* nodes2, float4* nodes4, int2* queue_a, int2* queue_b, int* counters,
+                          int* n_nodes4, cudaStream_t st);
+
 struct BvhBuild {
     // inputs
     const float* xyz;
@@ -90,7 +104,9 @@ size_t bvh_scratch_bytes(long long n_tri);
 cudaError_t bvh_build(const BvhBuild& b, cudaStream_t st);
 
 struct TraceArgs {
-    const float4* nodes;
+    const float4* nodes;          // binary nodes, or 4-wide nodes when wide = 1
+    int wide;
+    int packet;                   // 1: warp-cooperative traversal of the binary tree
     const float4* tris;
     const AngleDev* angles;
     const long long* ray_off;     // [n_angles + 1] chunk-relative, multiples of 32
@@ -114,7 +130,8 @@ struct TraceArgs {
     int* hit_nb;                  // optional [total_rays]
 };
 int trace_blocks_per_sm();
-// stack_depth: 32, 64 or 128 entries of the traversal stack (other values: 64)
+// stack_depth: 32, 64 or 128 entries of the traversal stack (other values: 64;
+// the warp-cooperative traversal uses at most 64)
 cudaError_t launch_trace(const TraceArgs& a, int n_blocks, bool count_visits, int stack_depth, cudaStream_t st);
 cudaError_t launch_emit_all(const TraceArgs& a, int n_blocks, cudaStream_t st);
 

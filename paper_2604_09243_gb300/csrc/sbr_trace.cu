@@ -104,6 +104,43 @@ __device__ __forceinline__ float dot_s(float3 a, float3 b)
 }
 
 // ---------------------------------------------------------------- closest hit
+// Watertight-by-slack FP32 Moller-Trumbore over the triangles of leaf `ref`,
+// keeping the closest hit (ties: smaller original triangle index).
+template <bool kCount>
+__device__ __forceinline__ void leaf_test(const float4* __restrict__ tris, int ref, float3 o, float3 d, int skip,
+                                          Hit& h, unsigned& ntri)
+{
+    const int first = leaf_first(ref), cnt = leaf_count(ref);
+    for (int q = 0; q < cnt; ++q) {
+        const int k = first + q;
+        if (kCount) ++ntri;
+        if (k == skip) continue;
+        const float4* tp = tris + 3 * (size_t)k;
+        const float4 A = __ldg(tp), B = __ldg(tp + 1), C = __ldg(tp + 2);
+        // Moller-Trumbore in the written FP32 operation order (division
+        // only for a candidate inside the triangle)
+        const float3 e1 = make_float3(B.x, B.y, B.z), e2 = make_float3(C.x, C.y, C.z);
+        const float3 p = cross_s(d, e2);
+        const float det = dot_s(e1, p);
+        const float3 s = make_float3(__fsub_rn(o.x, A.x), __fsub_rn(o.y, A.y), __fsub_rn(o.z, A.z));
+        const float3 qv = cross_s(s, e1);
+        const float U0 = dot_s(s, p), V0 = dot_s(d, qv), T0 = dot_s(e2, qv);
+        const bool neg = det < 0.f;
+        const float U = neg ? -U0 : U0, V = neg ? -V0 : V0, T = neg ? -T0 : T0;
+        const float ad = fabsf(det);
+        const float mg = __fmul_rn(ad, kSlack);
+        if (det != 0.f && U >= -mg && V >= -mg && __fadd_rn(U, V) <= __fadd_rn(ad, mg) && T > 0.f) {
+            const float t = __fdiv_rn(T0, det);
+            const int orig = __float_as_int(A.w);
+            if (t < h.t || (t == h.t && orig < h.orig)) {
+                h.t = t;
+                h.k = k;
+                h.orig = orig;
+            }
+        }
+    }
+}
+
 template <bool kCount, int kStack>
 __device__ __forceinline__ void closest_hit(const float4* __restrict__ nodes, const float4* __restrict__ tris, float3 o,
                                             float3 d, int skip, int limit, Hit& h, unsigned& nvis, unsigned& ntri,
@@ -152,39 +189,211 @@ __device__ __forceinline__ void closest_hit(const float4* __restrict__ nodes, co
             if (hl) { ref = lref; continue; }
             if (hr) { ref = rref; continue; }
         } else {
-            const int first = leaf_first(ref), cnt = leaf_count(ref);
-            for (int q = 0; q < cnt; ++q) {
-                const int k = first + q;
-                if (kCount) ++ntri;
-                if (k == skip) continue;
-                const float4* tp = tris + 3 * (size_t)k;
-                const float4 A = __ldg(tp), B = __ldg(tp + 1), C = __ldg(tp + 2);
-                // Moller-Trumbore in the written FP32 operation order (division
-                // only for a candidate inside the triangle)
-                const float3 e1 = make_float3(B.x, B.y, B.z), e2 = make_float3(C.x, C.y, C.z);
-                const float3 p = cross_s(d, e2);
-                const float det = dot_s(e1, p);
-                const float3 s = make_float3(__fsub_rn(o.x, A.x), __fsub_rn(o.y, A.y), __fsub_rn(o.z, A.z));
-                const float3 qv = cross_s(s, e1);
-                const float U0 = dot_s(s, p), V0 = dot_s(d, qv), T0 = dot_s(e2, qv);
-                const bool neg = det < 0.f;
-                const float U = neg ? -U0 : U0, V = neg ? -V0 : V0, T = neg ? -T0 : T0;
-                const float ad = fabsf(det);
-                const float mg = __fmul_rn(ad, kSlack);
-                if (det != 0.f && U >= -mg && V >= -mg && __fadd_rn(U, V) <= __fadd_rn(ad, mg) && T > 0.f) {
-                    const float t = __fdiv_rn(T0, det);
-                    const int orig = __float_as_int(A.w);
-                    if (t < h.t || (t == h.t && orig < h.orig)) {
-                        h.t = t;
-                        h.k = k;
-                        h.orig = orig;
-                    }
-                }
-            }
+            leaf_test<kCount>(tris, ref, o, d, skip, h, ntri);
         }
         if (sp == 0) break;
         ref = stack[--sp];
     }
+}
+
+// 4-wide variant: the near and far slab of each axis are chosen once per ray
+// from the sign of its direction, which gives the same FP32 values as the
+// per-axis min / max of the binary test (the fused product is monotone in the
+// box coordinate), so both trees accept exactly the same child boxes. Hit
+// children are ordered near to far by a 5-exchange sorting network; the far
+// ones go on the stack with their entry distance and are skipped when popped
+// behind the closest hit so far.
+__device__ __forceinline__ void cswap(float& ka, int& ra, float& kb, int& rb)
+{
+    const bool sw = kb < ka;
+    const float k = sw ? kb : ka, k2 = sw ? ka : kb;
+    const int r = sw ? rb : ra, r2 = sw ? ra : rb;
+    ka = k;
+    kb = k2;
+    ra = r;
+    rb = r2;
+}
+
+template <bool kCount, int kStack>
+__device__ __forceinline__ void closest_hit4(const float4* __restrict__ nodes, const float4* __restrict__ tris,
+                                             float3 o, float3 d, int skip, int limit, Hit& h, unsigned& nvis,
+                                             unsigned& ntri, bool& overflow)
+{
+    int stack[kStack];
+    float stack_t[kStack];
+    const float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+    const float3 oi = make_float3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
+    // float4 index of the near slab of each axis inside a node (lo: even, hi: odd)
+    const int sx = inv.x >= 0.f ? 0 : 1, sy = inv.y >= 0.f ? 2 : 3, sz = inv.z >= 0.f ? 4 : 5;
+    h.t = FLT_MAX;
+    h.k = -1;
+    h.orig = INT_MAX;
+    int sp = 0;
+    int ref = 0;
+    for (int it = 0;; ++it) {
+        if (it >= limit) {
+            overflow = true;
+            break;
+        }
+        if (ref >= 0) {
+            const float4* nd = nodes + (size_t)kNode4Float4 * ref;
+            const float4 nx = __ldg(nd + sx), fx = __ldg(nd + (sx ^ 1)), ny = __ldg(nd + sy), fy = __ldg(nd + (sy ^ 1));
+            const float4 nz = __ldg(nd + sz), fz = __ldg(nd + (sz ^ 1));
+            const float4 rr = __ldg(nd + 6);
+            if (kCount) ++nvis;
+            const float tmax = h.t;
+#define SBR_SLAB(c, tn, tf)                                                                                  \
+    const float tn = fmaxf(fmaxf(fmaf(nx.c, inv.x, -oi.x), fmaf(ny.c, inv.y, -oi.y)),                       \
+                           fmaxf(fmaf(nz.c, inv.z, -oi.z), 0.f));                                           \
+    const float tf = fminf(fminf(fmaf(fx.c, inv.x, -oi.x), fmaf(fy.c, inv.y, -oi.y)),                       \
+                           fminf(fmaf(fz.c, inv.z, -oi.z), tmax));
+            SBR_SLAB(x, tn0, tf0)
+            SBR_SLAB(y, tn1, tf1)
+            SBR_SLAB(z, tn2, tf2)
+            SBR_SLAB(w, tn3, tf3)
+#undef SBR_SLAB
+            int r0 = __float_as_int(rr.x), r1 = __float_as_int(rr.y), r2 = __float_as_int(rr.z),
+                r3 = __float_as_int(rr.w);
+            float k0 = (tn0 <= tf0 * kBoxGrow && r0 != kEmptyRef) ? tn0 : FLT_MAX;
+            float k1 = (tn1 <= tf1 * kBoxGrow && r1 != kEmptyRef) ? tn1 : FLT_MAX;
+            float k2 = (tn2 <= tf2 * kBoxGrow && r2 != kEmptyRef) ? tn2 : FLT_MAX;
+            float k3 = (tn3 <= tf3 * kBoxGrow && r3 != kEmptyRef) ? tn3 : FLT_MAX;
+            cswap(k0, r0, k1, r1);
+            cswap(k2, r2, k3, r3);
+            cswap(k0, r0, k2, r2);
+            cswap(k1, r1, k3, r3);
+            cswap(k1, r1, k2, r2);
+            if (k0 == FLT_MAX) {
+                ref = kEmptyRef;  // no child hit: pop
+            } else {
+                // push hits far to near (the nearest is visited now)
+                if (k3 != FLT_MAX) {
+                    if (sp < kStack) {
+                        stack[sp] = r3;
+                        stack_t[sp++] = k3;
+                    } else {
+                        overflow = true;
+                    }
+                }
+                if (k2 != FLT_MAX) {
+                    if (sp < kStack) {
+                        stack[sp] = r2;
+                        stack_t[sp++] = k2;
+                    } else {
+                        overflow = true;
+                    }
+                }
+                if (k1 != FLT_MAX) {
+                    if (sp < kStack) {
+                        stack[sp] = r1;
+                        stack_t[sp++] = k1;
+                    } else {
+                        overflow = true;
+                    }
+                }
+                ref = r0;
+                continue;
+            }
+        } else {
+            leaf_test<kCount>(tris, ref, o, d, skip, h, ntri);
+        }
+        // pop, skipping entries that start behind the closest hit so far
+        ref = kEmptyRef;
+        while (sp > 0) {
+            --sp;
+            if (stack_t[sp] <= h.t * kBoxGrow) {
+                ref = stack[sp];
+                break;
+            }
+        }
+        if (ref == kEmptyRef) break;
+    }
+}
+
+// Warp-cooperative (packet) traversal of the binary tree: the 32 lanes walk
+// one path together, so every node and leaf fetch is a single broadcast and
+// the loop never diverges. Each lane carries a "wants" flag per node (and one
+// bit per stack entry): it wants a node when its own ray enters the node's box,
+// and it tests boxes and leaf triangles only for nodes it wants, so its
+// result and its visit counts are those of its own ray. The warp descends into
+// a child when any lane wants it; when both children are wanted, the one that
+// most lanes reach first goes first. Must be called by all 32 lanes together.
+template <bool kCount, int kStack>
+__device__ __forceinline__ void closest_hit_packet(const float4* __restrict__ nodes, const float4* __restrict__ tris,
+                                                   bool active, float3 o, float3 d, int skip, int limit, Hit& h,
+                                                   unsigned& nvis, unsigned& ntri, bool& overflow)
+{
+    static_assert(kStack <= 64, "packet stack flags are one 64-bit word");
+    int stack[kStack];
+    unsigned long long wb = 0;  // lane wants stack entry k: bit k
+    const float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+    const float3 oi = make_float3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
+    h.t = FLT_MAX;
+    h.k = -1;
+    h.orig = INT_MAX;
+    int sp = 0;
+    int ref = 0;
+    bool want = active;
+    bool ovf = false;
+    for (int it = 0;; ++it) {
+        if (it >= limit) {
+            ovf = true;
+            break;
+        }
+        if (ref >= 0) {
+            const float4* nd = nodes + 4 * (size_t)ref;
+            const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
+            if (kCount && want) ++nvis;
+            const float tmax = h.t;
+            float ax0 = fmaf(n0.x, inv.x, -oi.x), ax1 = fmaf(n0.y, inv.x, -oi.x);
+            float ay0 = fmaf(n0.z, inv.y, -oi.y), ay1 = fmaf(n0.w, inv.y, -oi.y);
+            float az0 = fmaf(n2.x, inv.z, -oi.z), az1 = fmaf(n2.y, inv.z, -oi.z);
+            float bx0 = fmaf(n1.x, inv.x, -oi.x), bx1 = fmaf(n1.y, inv.x, -oi.x);
+            float by0 = fmaf(n1.z, inv.y, -oi.y), by1 = fmaf(n1.w, inv.y, -oi.y);
+            float bz0 = fmaf(n2.z, inv.z, -oi.z), bz1 = fmaf(n2.w, inv.z, -oi.z);
+            float an = fmaxf(fmaxf(fminf(ax0, ax1), fminf(ay0, ay1)), fmaxf(fminf(az0, az1), 0.f));
+            float af = fminf(fminf(fmaxf(ax0, ax1), fmaxf(ay0, ay1)), fminf(fmaxf(az0, az1), tmax));
+            float bn = fmaxf(fmaxf(fminf(bx0, bx1), fminf(by0, by1)), fmaxf(fminf(bz0, bz1), 0.f));
+            float bf = fminf(fminf(fmaxf(bx0, bx1), fmaxf(by0, by1)), fminf(fmaxf(bz0, bz1), tmax));
+            const int lref = __float_as_int(n3.x), rref = __float_as_int(n3.y);
+            const bool hl = want && an <= af * kBoxGrow;
+            const bool hr = want && (bn <= bf * kBoxGrow) && (rref != kEmptyRef);
+            const unsigned ml = __ballot_sync(kFull, hl), mr = __ballot_sync(kFull, hr);
+            if (ml && mr) {
+                const unsigned both = ml & mr, lfirst = __ballot_sync(kFull, hl && hr && an <= bn);
+                const bool goleft = both ? 2 * __popc(lfirst) >= __popc(both) : __popc(ml) >= __popc(mr);
+                const int fref = goleft ? rref : lref;
+                const bool wfar = goleft ? hr : hl;
+                if (sp < kStack) {
+                    stack[sp] = fref;
+                    wb = wfar ? (wb | (1ull << sp)) : (wb & ~(1ull << sp));
+                    ++sp;
+                } else {
+                    ovf = true;
+                }
+                ref = goleft ? lref : rref;
+                want = goleft ? hl : hr;
+                continue;
+            }
+            if (ml) {
+                ref = lref;
+                want = hl;
+                continue;
+            }
+            if (mr) {
+                ref = rref;
+                want = hr;
+                continue;
+            }
+        } else if (want) {
+            leaf_test<kCount>(tris, ref, o, d, skip, h, ntri);
+        }
+        if (sp == 0) break;
+        --sp;
+        ref = stack[sp];
+        want = (wb >> sp) & 1ull;
+    }
+    if (active && ovf) overflow = true;
 }
 
 // ---------------------------------------------------------------- per-ray state in registers
@@ -386,8 +595,23 @@ __device__ __forceinline__ void flush_stats(const TraceArgs& a, unsigned q, unsi
     }
 }
 
+// One closest-hit query per lane. kMode 0: per-lane binary traversal; 1: per-lane
+// 4-wide traversal; 2: warp-cooperative binary traversal (all 32 lanes call it).
+template <bool kCount, int kStack, int kMode>
+__device__ __forceinline__ void query(const TraceArgs& a, bool active, float3 o, float3 d, int skip, Hit& h,
+                                      unsigned& nvis, unsigned& ntri, bool& ovf)
+{
+    if (kMode == 2) {
+        closest_hit_packet<kCount, (kStack < 64 ? kStack : 64)>(a.nodes, a.tris, active, o, d, skip, a.visit_limit, h,
+                                                                nvis, ntri, ovf);
+    } else if (active) {
+        if (kMode == 1) closest_hit4<kCount, kStack>(a.nodes, a.tris, o, d, skip, a.visit_limit, h, nvis, ntri, ovf);
+        else closest_hit<kCount, kStack>(a.nodes, a.tris, o, d, skip, a.visit_limit, h, nvis, ntri, ovf);
+    }
+}
+
 // ---------------------------------------------------------------- pass 0: primary rays
-template <bool kCount, int kStack>
+template <bool kCount, int kStack, int kMode>
 __global__ void __launch_bounds__(kTraceThreads, 4) k_primary(const TraceArgs a)
 {
     const int lane = threadIdx.x & 31;
@@ -410,6 +634,8 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_primary(const TraceArgs a)
         Ray r;
         r.angle = ang;
         r.local = local;
+        r.o = make_float3(0.f, 0.f, 0.f);
+        r.d = make_float3(0.f, 0.f, 1.f);
         if (active) {
             const float fi = (float)i, fj = (float)j;
             r.o = make_float3(__fadd_rn(__fadd_rn(A.p0[0], __fmul_rn(fi, A.du[0])), __fmul_rn(fj, A.dv[0])),
@@ -421,8 +647,10 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_primary(const TraceArgs a)
             r.cos0 = 0.f;
             r.nb = 0;
             r.last = -1;
-            Hit h;
-            closest_hit<kCount, kStack>(a.nodes, a.tris, r.o, r.d, -1, a.visit_limit, h, nvis, ntri, ovf);
+        }
+        Hit h;
+        query<kCount, kStack, kMode>(a, active, r.o, r.d, -1, h, nvis, ntri, ovf);
+        if (active) {
             ++nq;
             if (h.k >= 0) {
                 hit = true;
@@ -438,7 +666,7 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_primary(const TraceArgs a)
 }
 
 // ---------------------------------------------------------------- pass b >= 1: live rays
-template <bool kCount, int kStack>
+template <bool kCount, int kStack, int kMode>
 __global__ void __launch_bounds__(kTraceThreads, 4) k_bounce(const TraceArgs a)
 {
     const int lane = threadIdx.x & 31;
@@ -454,11 +682,15 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_bounce(const TraceArgs a)
         const unsigned idx = (unsigned)base + lane;
         bool again = false;
         Ray r;
-        if (idx < n_in) {
-            load_state(a.q_in, idx, r);
+        const bool active = idx < n_in;
+        r.o = make_float3(0.f, 0.f, 0.f);
+        r.d = make_float3(0.f, 0.f, 1.f);
+        r.last = -1;
+        if (active) load_state(a.q_in, idx, r);
+        Hit h;
+        query<kCount, kStack, kMode>(a, active, r.o, r.d, r.last, h, nvis, ntri, ovf);
+        if (active) {
             const AngleDev& A = a.angles[r.angle];
-            Hit h;
-            closest_hit<kCount, kStack>(a.nodes, a.tris, r.o, r.d, r.last, a.visit_limit, h, nvis, ntri, ovf);
             ++nq;
             if (h.k < 0) {
                 emit(a, r, false);                     // escaped: its last hit radiates
@@ -500,27 +732,43 @@ __global__ void k_angle_offsets(const long long* ray_off, const unsigned* tile_b
 int trace_blocks_per_sm()
 {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bounce<false, 64>, kTraceThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bounce<false, 64, 0>, kTraceThreads, 0);
     return nb > 0 ? nb : 1;
 }
 
-template <int kStack>
+template <int kStack, int kMode>
 void launch_trace_s(const TraceArgs& a, int n_blocks, bool count_visits, cudaStream_t st)
 {
     if (a.bounce == 0) {
-        if (count_visits) k_primary<true, kStack><<<n_blocks, kTraceThreads, 0, st>>>(a);
-        else k_primary<false, kStack><<<n_blocks, kTraceThreads, 0, st>>>(a);
+        if (count_visits) k_primary<true, kStack, kMode><<<n_blocks, kTraceThreads, 0, st>>>(a);
+        else k_primary<false, kStack, kMode><<<n_blocks, kTraceThreads, 0, st>>>(a);
     } else {
-        if (count_visits) k_bounce<true, kStack><<<n_blocks, kTraceThreads, 0, st>>>(a);
-        else k_bounce<false, kStack><<<n_blocks, kTraceThreads, 0, st>>>(a);
+        if (count_visits) k_bounce<true, kStack, kMode><<<n_blocks, kTraceThreads, 0, st>>>(a);
+        else k_bounce<false, kStack, kMode><<<n_blocks, kTraceThreads, 0, st>>>(a);
     }
+}
+
+template <int kMode>
+void launch_trace_m(const TraceArgs& a, int n_blocks, bool count_visits, int stack_depth, cudaStream_t st)
+{
+    if (stack_depth == 32) {
+        launch_trace_s<32, kMode>(a, n_blocks, count_visits, st);
+        return;
+    }
+    if constexpr (kMode != 2) {
+        if (stack_depth == 128) {
+            launch_trace_s<128, kMode>(a, n_blocks, count_visits, st);
+            return;
+        }
+    }
+    launch_trace_s<64, kMode>(a, n_blocks, count_visits, st);
 }
 
 cudaError_t launch_trace(const TraceArgs& a, int n_blocks, bool count_visits, int stack_depth, cudaStream_t st)
 {
-    if (stack_depth == 32) launch_trace_s<32>(a, n_blocks, count_visits, st);
-    else if (stack_depth == 128) launch_trace_s<128>(a, n_blocks, count_visits, st);
-    else launch_trace_s<64>(a, n_blocks, count_visits, st);
+    if (a.wide) launch_trace_m<1>(a, n_blocks, count_visits, stack_depth, st);
+    else if (a.packet) launch_trace_m<2>(a, n_blocks, count_visits, stack_depth, st);
+    else launch_trace_m<0>(a, n_blocks, count_visits, stack_depth, st);
     return cudaGetLastError();
 }
 

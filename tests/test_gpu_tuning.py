@@ -31,7 +31,9 @@ def _trace(c, case, angles, **kw):
 
 @pytest.mark.parametrize("setting", [dict(tile_w=1), dict(tile_w=4), dict(tile_w=32), dict(stack_depth=32),
                                      dict(stack_depth=128), dict(blocks_per_sm=1), dict(po_item=512),
-                                     dict(po_item=2048), dict(chunk_rays_log2=20)])
+                                     dict(po_item=2048), dict(chunk_rays_log2=20), dict(bvh_width=4),
+                                     dict(bvh_width=4, stack_depth=32, tile_w=4), dict(packet=1),
+                                     dict(packet=1, stack_depth=32, tile_w=32)])
 def test_setting_keeps_hits_and_fields(G, tri_case, setting):
     case = tri_case
     angles = case["angles"][[0, 45, 90, 135, 180]]
@@ -59,7 +61,8 @@ def test_bad_settings_refused(G):
     with G.Context(0) as c:
         before = c.tuning()
         for bad in (dict(tile_w=3), dict(tile_w=64), dict(blocks_per_sm=0), dict(blocks_per_sm=5),
-                    dict(stack_depth=48), dict(po_item=300), dict(chunk_rays_log2=19), dict(chunk_rays_log2=28)):
+                    dict(stack_depth=48), dict(po_item=300), dict(chunk_rays_log2=19), dict(chunk_rays_log2=28),
+                    dict(bvh_width=3), dict(packet=2), dict(packet=1, bvh_width=4), dict(packet=1, stack_depth=128)):
             with pytest.raises(G.SbrError):
                 c.set_tuning(**bad)
         assert c.tuning() == before
@@ -96,3 +99,29 @@ def test_autotune_keeps_an_accepted_setting(G, tri_case):
         assert ok[0]["ms"] >= ms  # the starting setting is never faster than the kept one
         assert any(all(t[k] == best[k] for k in best) for t in ok)
         assert ms == min(t["ms"] for t in ok if all(t[k] == best[k] for k in best))
+
+
+def test_wide_tree_same_hits_aircraft(G):
+    """The 4-wide tree and the warp-cooperative traversal of the ~1M-triangle
+    aircraft give every ray the same hits (bit for bit) as the per-ray binary
+    traversal, over 10 bounces."""
+    case = S.aircraft_case(1e9, n_az=360)
+    angles = case["angles"][[0, 90, 180, 270]]
+    out = []
+    for w, pk in ((2, 0), (4, 0), (2, 1)):
+        with G.Context(0) as c:
+            c.load_mesh(case["xyz"], case["tri"])
+            c.set_tuning(bvh_width=w, packet=pk)
+            st = c.trace(angles, case["spacing"], eta=case["eta"], max_bounces=case["max_bounces"],
+                         offset=case["offset"], flags=G.TRACE_RECORD_HITS | G.TRACE_COUNT_VISITS)
+            out.append((st, [c.get_hits(a) for a in range(len(angles))], c.po_integrate([1e9])[1]))
+    (s2, h2, R2) = out[0]
+    for k, (s4, h4, R4) in enumerate(out[1:]):
+        assert s2["ray_bounces"] == s4["ray_bounces"] and s2["valid_rays"] == s4["valid_rays"]
+        assert s4["stack_overflows"] == 0
+        if k == 0:
+            assert s4["node_visits"] < s2["node_visits"]
+        for a, b in zip(h2, h4):
+            for x, y in zip(a, b):
+                assert np.array_equal(x, y)
+        assert np.array_equal(R2, R4)
