@@ -51,6 +51,14 @@ import sbr_inputs as S  # noqa: E402
 OPS_NODE = 41
 OPS_NODE4 = 81
 OPS_TRI = 38
+# DRAM bytes of the three transport passes per launched ray of the trihedral
+# sweep (ncu dram__bytes_read.sum + dram__bytes_write.sum over k_primary and
+# both k_bounce passes, 9 of its aspects = 2,114,692 rays: 190.03 MB, captured
+# with 4 x 8 tiles and a 32-entry stack), for the ray tile and traversal below
+# (stack depth and chunk size leave the DRAM bytes per ray unchanged: the
+# queues and records are the traffic); it grows with the rays, so it is scaled
+# by the rays of a step.
+TRAFFIC_PER_RAY = {"trihedral": (190.03e6 / 2114692, dict(tile_w=4, bvh_width=2, packet=0))}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -201,6 +209,45 @@ def run_reference(args, case, ws, rank, pg):
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def precision_report(G, torch, dev, n_az=4, freq=(8e9, 12e9, 17)):
+    """Precision form: the same traced records of the aircraft at 10 GHz
+    (lambda/10, B = 10, n_az azimuths at el 0) integrated with the three phase
+    modes. Paths reach ~60 m, so k L ~ 1.3e4 rad. Errors are against the FP64
+    phase (same records, same FP64 cross-item sums), in dB where that result
+    is above -40 dBsm; times are the PO kernels alone (CUDA events)."""
+    case = S.aircraft_case(10e9, n_az=360)
+    ang = case["angles"][np.linspace(0, 359, n_az).round().astype(int)]
+    freqs = np.linspace(*freq)
+    stream = torch.cuda.Stream(dev)
+    ctx = G.Context(dev, stream=stream)
+    ctx.load_mesh(case["xyz"], case["tri"])
+    st = ctx.trace(ang, case["spacing"], eta=case["eta"], max_bounces=case["max_bounces"], offset=case["offset"])
+    out, ms = {}, {}
+    for ph in ("fp64", "compensated", "fp32"):
+        E = torch.empty((len(ang), len(freqs), 2, 2), dtype=torch.float64, device=f"cuda:{dev}")
+        R = torch.empty((len(ang), len(freqs), 2), dtype=torch.float64, device=f"cuda:{dev}")
+        ctx.po_integrate(freqs, "HH,VV", phase=ph, E_out=E, rcs_out=R)  # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(5):
+            ctx.po_integrate(freqs, "HH,VV", phase=ph, E_out=E, rcs_out=R)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms[ph] = e0.elapsed_time(e1) / 5
+        out[ph] = R.cpu().numpy()
+    ctx.close()
+    ref = out["fp64"]
+    big = ref > -40.0
+    return {"case": f"aircraft 10 GHz, lambda/10, B = 10, {n_az} azimuths at el 0, {len(freqs)} frequencies "
+                    f"{freq[0] / 1e9:g}-{freq[1] / 1e9:g} GHz, HH and VV",
+            "valid_rays": st["valid_rays"],
+            "max_db_error_vs_fp64_phase": {k: float(np.max(np.abs(out[k][big] - ref[big])))
+                                           for k in ("compensated", "fp32")},
+            "median_db_error_vs_fp64_phase": {k: float(np.median(np.abs(out[k][big] - ref[big])))
+                                              for k in ("compensated", "fp32")},
+            "po_ms": ms}
+
+
 def batched_vs_plain(G, torch, dev, n_req):
     """Batched form against plain per-request SBR on the first ``n_req`` requests
     of the mixed-request workload (4096 requests, seed 2, over the sphere,
@@ -465,7 +512,11 @@ def run_sbr(args, case, ws, rank, local, pg):
         return st
 
     tune = None
-    if not args.no_autotune:
+    if args.tune:
+        # a fixed setting (e.g. the one the autotuner picked), no tuning runs
+        ctx.set_tuning(**{k: int(v) for k, v in (kv.split("=") for kv in args.tune.split(","))})
+        tune = {"best": ctx.tuning(), "fixed": True}
+    elif not args.no_autotune:
         # untimed: the autotuner picks blocks per SM, ray tile, stack depth, PO item and chunk size on an
         # evenly spaced sample of the workload's aspects
         pick = np.linspace(0, na - 1, min(na, args.tune_aspects)).round().astype(int)
@@ -473,6 +524,8 @@ def run_sbr(args, case, ws, rank, local, pg):
         best, best_ms, trials = ctx.autotune(sample, reps=3, **kw)
         tune = {"best": best, "start": {k: trials[0][k] for k in best}, "start_ms": trials[0]["ms"],
                 "best_ms": best_ms, "trials": len(trials),
+                "tried": [[{k: t[k] for k in best if t[k] != best[k]}, round(t["ms"], 4), t["status"]]
+                          for t in trials],
                 "refused": sum(1 for t in trials if t["status"] != 0),
                 "sample": f"{len(pick)} of {na} aspects, mean of 3 runs per setting"}
 
@@ -530,6 +583,11 @@ def run_sbr(args, case, ws, rank, local, pg):
 
     # --- roofline of the transport passes (FP32 issue bound)
     wide = ctx.tuning()["bvh_width"] == 4
+    traffic = None
+    if args.workload in TRAFFIC_PER_RAY:
+        per_ray, setting = TRAFFIC_PER_RAY[args.workload]
+        if all(ctx.tuning()[k] == v for k, v in setting.items()):
+            traffic = per_ray * stats[0]["rays_launched"]
     ops = (OPS_NODE4 if wide else OPS_NODE) * cnt["node_visits"] + OPS_TRI * cnt["tri_tests"]
     pass_s = float(np.mean([s["pass_ms"] for s in stats])) / 1e3
     pk, src = peaks()
@@ -546,7 +604,7 @@ def run_sbr(args, case, ws, rank, local, pg):
             "roofline": {"bound": "alu", "kernel": "k_primary+k_bounce (transport passes, "
                                                    f"{'4-wide' if wide else 'binary'} tree)",
                          "achieved": achieved, "peak": peak_ops, "unit": "T FP32-op/s",
-                         "frac": achieved / peak_ops, "traffic": None,
+                         "frac": achieved / peak_ops, "traffic": traffic,
                          "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                         f"{pk.get('sm_max_mhz', 2070.0):g} MHz ({src} SM clock)",
                          "ops_per_step": ops, "node_visits": cnt["node_visits"], "tri_tests": cnt["tri_tests"],
@@ -558,6 +616,8 @@ def run_sbr(args, case, ws, rank, local, pg):
             "clocks": clocks}
     if args.batch_requests > 0:
         line["batched_vs_plain"] = batched_vs_plain(G, torch, local, args.batch_requests)
+    if not args.no_precision:
+        line["precision"] = precision_report(G, torch, local)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
         b, t, idx = oracle_sample(case, args.ref_angles, threads)
@@ -584,7 +644,9 @@ def main():
                     help="use this many evenly spaced aspects of the sweep (small profiling cases); 0 = all")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tuning")
+    ap.add_argument("--no-precision", action="store_true", help="skip the phase-precision report")
     ap.add_argument("--tune-aspects", type=int, default=24, help="aspects in the autotuner's sample")
+    ap.add_argument("--tune", default="", help="fixed tuning instead of the autotuner, e.g. tile_w=4,stack_depth=32")
     ap.add_argument("--sur-domains", default="full,patch", help="surrogate: domains to evaluate")
     ap.add_argument("--sur-scale", type=float, default=1.0, help="surrogate: fraction of the sample counts")
     ap.add_argument("--sur-epochs", type=int, default=60)
