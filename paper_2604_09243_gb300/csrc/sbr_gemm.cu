@@ -2,15 +2,21 @@
 // (tcgen05) for the learned surrogate: C = A B^T with A [M x K] and B [N x K]
 // both K-contiguous BF16, FP32 accumulation in tensor memory (TMEM).
 //
-// One CTA of 128 threads computes a 128 x 128 tile:
-//   - thread 0 streams 128 x 64 tiles of A and B into shared memory with TMA
-//     (cp.async.bulk.tensor, 128-byte swizzle) through a 4-stage ring of
-//     mbarriers, and issues tcgen05.mma (M = 128, N = 128, K = 16 per
-//     instruction, 4 per stage); tcgen05.commit frees a stage when its MMAs
-//     have read it;
+// One CTA of 128 threads computes a 128 x BN tile (BN = 128, or 64 when the
+// 128-wide grid would leave SMs idle):
+//   - warp 0 (one lane) streams 128 x 64 tiles of A and BN x 64 tiles of B
+//     into shared memory with TMA (cp.async.bulk.tensor, 128-byte swizzle)
+//     through a 4-stage ring of mbarriers, refilling a stage once the MMAs
+//     that read it have completed;
+//   - warp 1 (one lane) issues tcgen05.mma (M = 128, N = BN, K = 16 per
+//     instruction, 4 per stage) as soon as a stage lands and commits each
+//     stage back to the producer, so MMA issue never waits for a refill;
 //   - after the last K step all four warps read the accumulator out of TMEM
-//     with tcgen05.ld (warp w owns rows 32w .. 32w + 31) and apply the fused
-//     epilogue (bias, GELU, GELU derivative, FP32 or BF16 store).
+//     with tcgen05.ld (warp w owns rows 32w .. 32w + 31), apply the fused
+//     epilogue (bias, GELU, GELU derivative) into the now idle pipeline
+//     buffers, and write the tile out row by row with coalesced 16-byte stores
+//     (the pre-activation read of the GELU-derivative epilogue is staged the
+//     same way).
 // Every wait is bounded: on a timeout the CTA records an error flag, skips the
 // remaining work, frees its TMEM and returns.
 #include <cuda.h>
@@ -26,12 +32,22 @@ namespace sbr {
 
 namespace {
 
-constexpr int kBM = 128, kBN = 128, kBK = 64, kStages = 4;
+constexpr int kBM = 128, kBK = 64, kStages = 4;
 constexpr int kTileA = kBM * kBK * 2;  // bytes
-constexpr int kTileB = kBN * kBK * 2;
-constexpr int kStageBytes = kTileA + kTileB;
 constexpr unsigned kSpin = 1u << 24;  // try_wait rounds before a wait gives up
-constexpr int kGemmSmem = kStages * kStageBytes + 1024;
+template <int BN>
+struct Cfg {
+    static constexpr int kTileB = BN * kBK * 2;
+    static constexpr int kStageBytes = kTileA + kTileB;
+    static constexpr int kPipe = kStages * kStageBytes;
+    // epilogue staging (reuses the pipeline buffers): FP32 [128][BN + 4] and BF16 [128][BN + 8]
+    static constexpr int kLdF = BN + 4, kLdH = BN + 8;
+    static constexpr int kStageF = kBM * kLdF * 4, kStageH = kBM * kLdH * 2;
+    static constexpr int kSmem = (kPipe > kStageF + kStageH ? kPipe : kStageF + kStageH) + 1024;
+    // instruction descriptor: D FP32, A and B BF16, both K-major, M = 128, N = BN
+    static constexpr uint32_t kIdesc =
+        (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -70,15 +86,12 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr)
 {
     return (uint64_t)((saddr >> 4) & 0x3FFF) | (1ull << 16) | (64ull << 32) | (1ull << 46) | (2ull << 61);
 }
-// instruction descriptor: D FP32, A and B BF16, both K-major, M = 128, N = 128
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t acc)
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc)
 {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
             tmem),
-        "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc)
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
         : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar)
@@ -111,29 +124,35 @@ __device__ __forceinline__ float gelu_grad(float z)
     return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * 0.3989422804014327f * expf(-0.5f * z * z);
 }
 
+template <int BN>
 __global__ void __launch_bounds__(128, 1) k_gemm_tn(const __grid_constant__ CUtensorMap tmA,
                                                     const __grid_constant__ CUtensorMap tmB, const GemmEpi ep, int K,
                                                     int* err)
 {
+    using C = Cfg<BN>;
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
     __shared__ uint32_t tmem_base;
+    __shared__ int s_fail, s_issued, s_consumed;
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
+    const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
     const int KT = K / kBK;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                     "r"(kBN)
+                     "r"(BN)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+        for (int st = 0; st < kStages; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], 1);
         }
         mbar_init(&done, 1);
+        s_fail = 0;
+        s_issued = 0;
+        s_consumed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc_fence_before();
@@ -142,86 +161,116 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tn(const __grid_constant__ CUte
     const uint32_t tmem = tmem_base;
 
     if (tid == 0) {
-        bool ok = true;
-        const int pre = KT < kStages ? KT : kStages;
-        for (int s = 0; s < pre; ++s) {
-            unsigned char* sa = smem + s * kStageBytes;
-            mbar_expect_tx(&full[s], kStageBytes);
-            tma_load_2d(sa, &tmA, s * kBK, m0, &full[s]);
-            tma_load_2d(sa + kTileA, &tmB, s * kBK, n0, &full[s]);
+        // producer: stage kt % kStages is refilled once the MMAs of step kt - kStages have completed
+        for (int kt = 0; kt < KT; ++kt) {
+            const int st = kt % kStages;
+            if (kt >= kStages && !mbar_wait(&empty[st], (unsigned)(kt / kStages - 1) & 1u)) {
+                s_fail = 1;
+                break;
+            }
+            if (*(volatile int*)&s_fail) break;
+            unsigned char* sa = smem + st * C::kStageBytes;
+            mbar_expect_tx(&full[st], C::kStageBytes);
+            tma_load_2d(sa, &tmA, kt * kBK, m0, &full[st]);
+            tma_load_2d(sa + kTileA, &tmB, kt * kBK, n0, &full[st]);
+            *(volatile int*)&s_issued = kt + 1;
         }
-        for (int kt = 0; kt < KT && ok; ++kt) {
-            const int s = kt % kStages;
-            const unsigned ph = (unsigned)(kt / kStages) & 1u;
-            if (!mbar_wait(&full[s], ph)) {
+    } else if (tid == 32) {
+        // MMA issuer
+        bool ok = true;
+        for (int kt = 0; kt < KT; ++kt) {
+            const int st = kt % kStages;
+            if (!mbar_wait(&full[st], (unsigned)(kt / kStages) & 1u)) {
                 ok = false;
                 break;
             }
             tc_fence_after();
-            const uint32_t sa = smem_u32(smem + s * kStageBytes);
+            const uint32_t sa = smem_u32(smem + st * C::kStageBytes);
             const uint32_t sb = sa + kTileA;
 #pragma unroll
             for (int kk = 0; kk < kBK / 16; ++kk)
-                mma_bf16(tmem, desc_sw128(sa + 32 * kk), desc_sw128(sb + 32 * kk), (kt | kk) != 0);
-            mma_commit(&empty[s]);
-            if (kt + kStages < KT) {
-                if (!mbar_wait(&empty[s], ph)) {  // the MMAs above have read stage s
-                    ok = false;
-                    break;
-                }
-                unsigned char* sp = smem + s * kStageBytes;
-                mbar_expect_tx(&full[s], kStageBytes);
-                tma_load_2d(sp, &tmA, (kt + kStages) * kBK, m0, &full[s]);
-                tma_load_2d(sp + kTileA, &tmB, (kt + kStages) * kBK, n0, &full[s]);
-            }
+                mma_bf16(tmem, desc_sw128(sa + 32 * kk), desc_sw128(sb + 32 * kk), C::kIdesc, (kt | kk) != 0);
+            mma_commit(&empty[st]);
+            *(volatile int*)&s_consumed = kt + 1;
         }
-        if (ok) {
-            mma_commit(&done);
-        } else {
-            atomicExch(err, 1);
-        }
+        if (ok) mma_commit(&done);
+        else *(volatile int*)&s_fail = 1;
     }
-    // epilogue: wait for the accumulator, then warp w reads TMEM lanes 32w .. 32w + 31
-    const bool ready = mbar_wait(&done, 0);
+    // wait for the accumulator (or for the issuer to give up)
+    bool ready = false;
+    for (int r = 0; r < 4 && !ready; ++r) {
+        ready = mbar_wait(&done, 0);
+        if (*(volatile int*)&s_fail) break;
+    }
     tc_fence_after();
-    if (!ready) {
-        if (lane == 0) atomicExch(err, 1);
+    __syncthreads();  // all TMA writes and MMA reads of the pipeline buffers are over: reuse them
+    if (!ready || s_fail) {
+        if (tid == 0) {
+            atomicExch(err, 1);
+            // let the loads still in flight land before the CTA's shared memory goes away
+            for (int kt = s_consumed; kt < s_issued; ++kt) mbar_wait(&full[kt % kStages], (unsigned)(kt / kStages) & 1u);
+        }
     } else {
-        const int row = m0 + warp * 32 + lane;
-        for (int c0 = 0; c0 < kBN; c0 += 32) {
+        float* sf = reinterpret_cast<float*>(smem);                          // FP32 [128][kLdF]
+        __nv_bfloat16* sh = reinterpret_cast<__nv_bfloat16*>(smem + C::kStageF);  // BF16 [128][kLdH]
+        const int r = warp * 32 + lane;  // tile row of this thread
+        if (ep.mode == kEpiGeluGrad) {
+            // stage the pre-activation tile with coalesced loads
+            for (int q = tid; q < kBM * (BN / 4); q += 128) {
+                const int rr = q / (BN / 4), cc = (q % (BN / 4)) * 4;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (m0 + rr < ep.M) v = *reinterpret_cast<const float4*>(ep.z + (size_t)(m0 + rr) * ep.ldz + n0 + cc);
+                *reinterpret_cast<float4*>(sf + rr * C::kLdF + cc) = v;
+            }
+            __syncthreads();
+        }
+        for (int c0 = 0; c0 < BN; c0 += 32) {
             float v[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            if (row >= ep.M) continue;
-            const int col = n0 + c0;
             if (ep.mode == kEpiF32) {
-                float* dst = ep.c_f32 + (size_t)row * ep.ldc + col;
 #pragma unroll
                 for (int i = 0; i < 32; i += 4)
-                    *reinterpret_cast<float4*>(dst + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                    *reinterpret_cast<float4*>(sf + r * C::kLdF + c0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
             } else if (ep.mode == kEpiBiasGelu) {
-                float* zd = ep.c_f32 + (size_t)row * ep.ldc + col;
-                __nv_bfloat16* hd = ep.out_bf16 + (size_t)row * ep.ldo + col;
 #pragma unroll
                 for (int i = 0; i < 32; i += 2) {
-                    const float z0 = v[i] + ep.bias[col + i], z1 = v[i + 1] + ep.bias[col + i + 1];
-                    zd[i] = z0;
-                    zd[i + 1] = z1;
-                    *reinterpret_cast<__nv_bfloat162*>(hd + i) = __floats2bfloat162_rn(gelu(z0), gelu(z1));
+                    const float z0 = v[i] + ep.bias[n0 + c0 + i], z1 = v[i + 1] + ep.bias[n0 + c0 + i + 1];
+                    *reinterpret_cast<float2*>(sf + r * C::kLdF + c0 + i) = make_float2(z0, z1);
+                    *reinterpret_cast<__nv_bfloat162*>(sh + r * C::kLdH + c0 + i) =
+                        __floats2bfloat162_rn(gelu(z0), gelu(z1));
                 }
             } else {  // kEpiGeluGrad: dz = acc * gelu'(z)
-                const float* zs = ep.z + (size_t)row * ep.ldz + col;
-                __nv_bfloat16* hd = ep.out_bf16 + (size_t)row * ep.ldo + col;
 #pragma unroll
-                for (int i = 0; i < 32; i += 2)
-                    *reinterpret_cast<__nv_bfloat162*>(hd + i) =
-                        __floats2bfloat162_rn(v[i] * gelu_grad(zs[i]), v[i + 1] * gelu_grad(zs[i + 1]));
+                for (int i = 0; i < 32; i += 2) {
+                    const float2 z = *reinterpret_cast<const float2*>(sf + r * C::kLdF + c0 + i);
+                    *reinterpret_cast<__nv_bfloat162*>(sh + r * C::kLdH + c0 + i) =
+                        __floats2bfloat162_rn(v[i] * gelu_grad(z.x), v[i + 1] * gelu_grad(z.y));
+                }
+            }
+        }
+        __syncthreads();
+        // coalesced write-out: consecutive threads take consecutive 16-byte pieces of a row
+        if (ep.mode != kEpiGeluGrad) {
+            for (int q = tid; q < kBM * (BN / 4); q += 128) {
+                const int rr = q / (BN / 4), cc = (q % (BN / 4)) * 4;
+                if (m0 + rr < ep.M)
+                    *reinterpret_cast<float4*>(ep.c_f32 + (size_t)(m0 + rr) * ep.ldc + n0 + cc) =
+                        *reinterpret_cast<const float4*>(sf + rr * C::kLdF + cc);
+            }
+        }
+        if (ep.mode != kEpiF32) {
+            for (int q = tid; q < kBM * (BN / 8); q += 128) {
+                const int rr = q / (BN / 8), cc = (q % (BN / 8)) * 8;
+                if (m0 + rr < ep.M)
+                    *reinterpret_cast<uint4*>(ep.out_bf16 + (size_t)(m0 + rr) * ep.ldo + n0 + cc) =
+                        *reinterpret_cast<const uint4*>(sh + rr * C::kLdH + cc);
             }
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kBN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -238,14 +287,14 @@ cudaError_t get_encode()
 }
 
 // 2-D BF16 tensor map over a row-major [rows x cols] matrix (row stride ld
-// elements), box of 64 columns x 128 rows, 128-byte swizzle
-cudaError_t make_map(CUtensorMap* m, const void* base, int rows, int cols, int ld)
+// elements), box of 64 columns x box_rows rows, 128-byte swizzle
+cudaError_t make_map(CUtensorMap* m, const void* base, int rows, int cols, int ld, int box_rows)
 {
     cudaError_t e = get_encode();
     if (e != cudaSuccess) return e;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-    cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
+    cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -257,28 +306,52 @@ cudaError_t make_map(CUtensorMap* m, const void* base, int rows, int cols, int l
 
 bool gemm_shape_ok(int M, int N, int K)
 {
-    return M > 0 && N > 0 && K > 0 && M % kBM == 0 && N % kBN == 0 && K % kBK == 0;
+    return M > 0 && N > 0 && K > 0 && M % kBM == 0 && N % 128 == 0 && K % kBK == 0;
 }
 
+namespace {
+
+template <int BN>
+cudaError_t launch_gemm(const void* A, int lda, const void* B, int ldb, int M, int N, int K, const GemmEpi& ep,
+                        int* err, cudaStream_t st)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_tn<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<BN>::kSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    CUtensorMap ta, tb;
+    cudaError_t e = make_map(&ta, A, M, K, lda, kBM);
+    if (e == cudaSuccess) e = make_map(&tb, B, N, K, ldb, BN);
+    if (e != cudaSuccess) return e;
+    dim3 grid(N / BN, M / kBM);
+    k_gemm_tn<BN><<<grid, 128, Cfg<BN>::kSmem, st>>>(ta, tb, ep, K, err);
+    return cudaGetLastError();
+}
+
+int g_sms = 0;
+
+}  // namespace
+
 // C = A B^T; A [M x K] (row stride lda), B [N x K] (row stride ldb), BF16, K-contiguous.
+// 128 x 64 tiles when 128 x 128 tiles would cover fewer CTAs than SMs.
 cudaError_t gemm_bf16_tn(const void* A, int lda, const void* B, int ldb, int M, int N, int K, const GemmEpi& ep,
                          int* err, cudaStream_t st)
 {
     if (!gemm_shape_ok(M, N, K) || lda % 8 || ldb % 8 || ((uintptr_t)A & 15) || ((uintptr_t)B & 15))
         return cudaErrorInvalidValue;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm_tn, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
-        if (e != cudaSuccess) return e;
-        attr = true;
+    if (ep.mode != kEpiGeluGrad && (ep.ldc % 4 || ((uintptr_t)ep.c_f32 & 15))) return cudaErrorInvalidValue;
+    if (ep.mode != kEpiF32 && (ep.ldo % 8 || ((uintptr_t)ep.out_bf16 & 15))) return cudaErrorInvalidValue;
+    if (ep.mode == kEpiGeluGrad && (ep.ldz % 4 || ((uintptr_t)ep.z & 15))) return cudaErrorInvalidValue;
+    if (!g_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_sms <= 0) g_sms = 1;
     }
-    CUtensorMap ta, tb;
-    cudaError_t e = make_map(&ta, A, M, K, lda);
-    if (e == cudaSuccess) e = make_map(&tb, B, N, K, ldb);
-    if (e != cudaSuccess) return e;
-    dim3 grid(N / kBN, M / kBM);
-    k_gemm_tn<<<grid, 128, kGemmSmem, st>>>(ta, tb, ep, K, err);
-    return cudaGetLastError();
+    if ((long long)(M / kBM) * (N / 128) < g_sms) return launch_gemm<64>(A, lda, B, ldb, M, N, K, ep, err, st);
+    return launch_gemm<128>(A, lda, B, ldb, M, N, K, ep, err, st);
 }
 
 }  // namespace sbr
