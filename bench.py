@@ -150,6 +150,11 @@ def workload(name: str) -> dict:
         return S.trihedral_case()
     if name == "sphere":
         return S.sphere_case(n_random=64)
+    if name == "aircraft3deep":
+        # deep cavities: up to 100 bounces, a ray still hitting after them is invalid (escape required)
+        c = S.aircraft_case(3e9, n_az=360)
+        c.update(name="aircraft_3GHz_B100_escape", max_bounces=100, escape=True)
+        return c
     if name.startswith("aircraft"):
         f = {"aircraft1": 1e9, "aircraft3": 3e9, "aircraft10": 10e9}[name]
         return S.aircraft_case(f, n_az=360)
@@ -159,7 +164,8 @@ def workload(name: str) -> dict:
 def wl_config(case: dict, name: str) -> dict:
     return {"workload": case["name"], "mesh_triangles": int(len(case["tri"])), "aspects": int(len(case["angles"])),
             "freq_ghz": [float(f) / 1e9 for f in case["freqs"]], "ray_spacing_m": float(case["spacing"]),
-            "max_bounces": int(case["max_bounces"]), "grid_offset": list(case.get("offset", (0.0, 0.0))),
+            "max_bounces": int(case["max_bounces"]), "require_escape": bool(case.get("escape", False)),
+            "grid_offset": list(case.get("offset", (0.0, 0.0))),
             "po": "vector", "pols": "HH,VV",
             "l2": "flushed between timed steps (512 MB write)"}
 
@@ -176,7 +182,7 @@ def oracle_sample(case, n_angles: int, threads: int):
         az, el = case["angles"][a]
         fr = oracle.make_frame(om.bbox, az, el, case["spacing"], eta=case["eta"], window=case.get("window", 0.0),
                                offset=case.get("offset", (0.0, 0.0)))
-        tr = oracle.trace(om, fr, case["max_bounces"], threads=threads)
+        tr = oracle.trace(om, fr, case["max_bounces"], threads=threads, require_escape=case.get("escape", False))
         oracle.po(tr["coef"], tr["L"], tr["valid"], case["freqs"])
         nb = tr["nb"]
         bounces += int(np.sum(nb + (nb < case["max_bounces"])))
@@ -506,8 +512,10 @@ def run_sbr(args, case, ws, rank, local, pg):
     R_dev = torch.empty((na, nf, npol), dtype=torch.float64, device=f"cuda:{local}")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=f"cuda:{local}")
 
+    xf = G.TRACE_REQUIRE_ESCAPE if case.get("escape") else 0
+
     def step(flags=G.TRACE_TIME_PASSES):
-        st = ctx.trace(ang, case["spacing"], flags=flags, **kw)
+        st = ctx.trace(ang, case["spacing"], flags=flags | xf, **kw)
         ctx.po_integrate(freqs, "HH,VV", E_out=E_dev, rcs_out=R_dev)
         return st
 
@@ -521,7 +529,7 @@ def run_sbr(args, case, ws, rank, local, pg):
         # evenly spaced sample of the workload's aspects
         pick = np.linspace(0, na - 1, min(na, args.tune_aspects)).round().astype(int)
         sample = [dict(az=float(ang[i, 0]), el=float(ang[i, 1]), freqs=freqs, spacing=case["spacing"]) for i in pick]
-        best, best_ms, trials = ctx.autotune(sample, reps=3, **kw)
+        best, best_ms, trials = ctx.autotune(sample, reps=3, flags=xf, **kw)
         tune = {"best": best, "start": {k: trials[0][k] for k in best}, "start_ms": trials[0]["ms"],
                 "best_ms": best_ms, "trials": len(trials),
                 "tried": [[{k: t[k] for k in best if t[k] != best[k]}, round(t["ms"], 4), t["status"]]
@@ -531,7 +539,7 @@ def run_sbr(args, case, ws, rank, local, pg):
 
     for _ in range(args.warmup):
         step()
-    cnt = ctx.trace(ang, case["spacing"], flags=G.TRACE_COUNT_VISITS, **kw)  # counting run, untimed
+    cnt = ctx.trace(ang, case["spacing"], flags=G.TRACE_COUNT_VISITS | xf, **kw)  # counting run, untimed
     stream.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     sampler = ClockSampler(local)
@@ -565,7 +573,7 @@ def run_sbr(args, case, ws, rank, local, pg):
 
     def e2e_step():
         ctx.load_mesh(xyz_p.numpy(), tri_p.numpy())
-        ctx.trace(ang_p.numpy(), case["spacing"], **kw)
+        ctx.trace(ang_p.numpy(), case["spacing"], flags=xf, **kw)
         E, R = ctx.po_integrate(freqs, "HH,VV")
         E_h[...] = np.stack([E.real, E.imag], -1)
         R_h[...] = R
@@ -636,7 +644,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sbr", choices=["sbr", "reference"])
     ap.add_argument("--workload", default="trihedral",
-                    choices=["trihedral", "sphere", "aircraft1", "aircraft3", "aircraft10", "surrogate"])
+                    choices=["trihedral", "sphere", "aircraft1", "aircraft3", "aircraft10", "aircraft3deep",
+                             "surrogate"])
     ap.add_argument("--ref-angles", type=int, default=24)
     ap.add_argument("--batch-requests", type=int, default=256,
                     help="mixed requests for the batched-vs-plain comparison (0 = skip)")

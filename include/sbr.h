@@ -175,7 +175,7 @@ int sbr_ray_grid_box(const float* bbox6, double az_deg, double el_deg, double ra
  * trace-integrate decomposition). The records stay in the context until the
  * next sbr_trace or sbr_load_mesh; sbr_po_integrate reads them for any list of
  * frequencies. `opt` may be NULL; `stats` may be NULL (it is filled on return
- * and then the stream is synchronised). max_bounces in 1..64. */
+ * and then the stream is synchronised). max_bounces in 1..128. */
 int sbr_trace(sbr_ctx* ctx, const double* az_el_deg, int64_t n_angles, double ray_spacing_m, double margin_eta,
               int max_bounces, const sbr_trace_opts* opt, sbr_trace_stats* stats);
 
@@ -264,6 +264,9 @@ typedef struct {
     int packet;          /* 1: the 32 rays of a warp walk the binary tree together (one broadcast fetch
                             per node, no divergence; each ray still tests only the boxes it enters);
                             needs bvh_width 2 and stack_depth <= 64; default 0 */
+    int silhouette;      /* 1: before the primary pass, rasterise every triangle's widened projection onto
+                            the ray grid and skip the query of rays outside all of them (sure misses: no
+                            hit, not counted as ray-bounces); default 0 */
 } sbr_tuning;
 int sbr_get_tuning(const sbr_ctx* ctx, sbr_tuning* out);
 /* SBR_ERR_ARG for a value outside the ranges above. */
@@ -284,8 +287,8 @@ typedef struct {
 /* Autotuner: times sbr_run_batch on the given sample batch (arguments as for
  * sbr_run_batch) under the current setting and then, one parameter at a
  * time (traversal: binary / 4-wide / warp-cooperative, blocks per SM, ray
- * tile, stack depth, PO item, chunk size), under
- * each alternative value, keeping a change when it is faster and its results
+ * tile, stack depth, PO item, chunk size, silhouette mask), under
+ * each alternative value, keeping a change when it is more than 1 % faster and its results
  * agree (see sbr_tune_trial). Each timing is the mean of `reps` runs after one
  * warm-up run. Leaves the fastest accepted setting on the ctx and returns it
  * in *best (and its time in *best_ms). trials: host array of capacity

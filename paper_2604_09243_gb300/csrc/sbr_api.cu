@@ -22,7 +22,7 @@ namespace {
 
 constexpr double kC0 = 299792458.0;
 constexpr double kPi = 3.14159265358979323846;
-constexpr int kMaxBounces = 64;
+constexpr int kMaxBounces = 128;
 
 std::string g_create_error;
 
@@ -88,7 +88,7 @@ struct sbr_ctx {
     DevBuf nodes4;  // 4-wide collapse of the binary tree
     int n_nodes4 = 0;
     // trace
-    DevBuf angles, rayoff, mask, tilebase, scan_scr, recoff, q0, q1, ctr64, ctr32, stats, rec;
+    DevBuf angles, rayoff, mask, tilebase, scan_scr, recoff, q0, q1, ctr64, ctr32, stats, rec, cover;
     DevBuf hit_tri, hit_t, hit_nb;
     long long rec_total = 0;
     int max_bounces = 0, trace_flags = 0;
@@ -256,7 +256,8 @@ int log2i(int v)
 bool tuning_ok(const sbr_tuning& t)
 {
     const bool tile = t.tile_w >= 1 && t.tile_w <= 32 && (t.tile_w & (t.tile_w - 1)) == 0;
-    const bool trav = t.packet == 0 || (t.packet == 1 && t.bvh_width == 2 && t.stack_depth <= 64);
+    const bool trav = (t.packet == 0 || (t.packet == 1 && t.bvh_width == 2 && t.stack_depth <= 64)) &&
+                      (t.silhouette == 0 || t.silhouette == 1);
     return tile && trav && (t.bvh_width == 2 || t.bvh_width == 4) && t.blocks_per_sm >= 1 && t.blocks_per_sm <= 4 &&
            (t.stack_depth == 32 || t.stack_depth == 64 || t.stack_depth == 128) && t.chunk_rays_log2 >= 20 &&
            t.chunk_rays_log2 <= 27 && (t.po_item == 512 || t.po_item == 1024 || t.po_item == 2048);
@@ -327,6 +328,7 @@ int sbr_create(sbr_ctx** out, int device, void* cuda_stream)
     c->tune.po_item = kPoItemRecords;
     c->tune.bvh_width = 2;
     c->tune.packet = 0;
+    c->tune.silhouette = 0;
     *out = c;
     return SBR_OK;
 }
@@ -337,7 +339,7 @@ void sbr_destroy(sbr_ctx* c)
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     DevBuf* all[] = {&c->xyz, &c->tri, &c->nodes, &c->tris, &c->bvh_scratch, &c->bbox_dev, &c->err_dev, &c->nodes4,
-                     &c->angles, &c->rayoff, &c->mask, &c->tilebase, &c->scan_scr, &c->recoff, &c->q0, &c->q1,
+                     &c->angles, &c->rayoff, &c->mask, &c->tilebase, &c->scan_scr, &c->recoff, &c->q0, &c->q1, &c->cover,
                      &c->ctr64, &c->ctr32, &c->stats, &c->rec, &c->hit_tri, &c->hit_t, &c->hit_nb, &c->items,
                      &c->itemoff, &c->freq, &c->kfreq, &c->partial, &c->E, &c->rcs};
     for (DevBuf* b : all) b->release();
@@ -512,6 +514,7 @@ int plan_chunks(sbr_ctx* c, TraceRun& R, std::vector<int64_t>& cut, long long* t
     CK(c->rayoff.ensure(sizeof(long long) * (size_t)(max_angles + 1)), "alloc ray offsets");
     CK(c->recoff.ensure(sizeof(unsigned) * (size_t)(max_angles + 1)), "alloc record offsets");
     CK(c->mask.ensure(sizeof(unsigned) * (size_t)max_tiles), "alloc mask");
+    if (c->tune.silhouette) CK(c->cover.ensure(sizeof(unsigned) * (size_t)(max_tiles + max_angles)), "alloc cover");
     CK(c->tilebase.ensure(sizeof(unsigned) * (size_t)max_tiles), "alloc tile base");
     CK(c->scan_scr.ensure(scan_scratch_bytes(max_tiles)), "alloc scan scratch");
     CK(c->q0.ensure(sizeof(RayState) * (size_t)max_chunk), "alloc ray queue");
@@ -609,6 +612,12 @@ int trace_chunk(sbr_ctx* c, TraceRun& R, int64_t a0, int64_t a1, long long rec_b
         ta.hit_nb = c->hit_nb.as<int>() + base;
     }
     RayState* qs[2] = {c->q0.as<RayState>(), c->q1.as<RayState>()};
+    if (c->tune.silhouette) {
+        CK(cudaMemsetAsync(c->cover.p, 0, sizeof(unsigned) * (size_t)(chunk_rays / 32 + na), c->stream), "memset cover");
+        CK(launch_silhouette(ta, (int)c->n_tri, c->cover.as<unsigned>(), c->stream), "silhouette");
+        ++R.n_launch;
+        ta.cover = c->cover.as<unsigned>();
+    }
     ta.bounce = 0;  // pass 0: primary rays -> queue 0
     ta.work = c->ctr64.as<unsigned long long>();
     ta.q_out = qs[0];
@@ -813,7 +822,7 @@ struct BatchPlan {
     PoArgs pa;
     // device buffers
     DevBuf angles, rayoff, pang, recoff, mask, tilebase, scan_scr, q0, q1, ctr64, ctr32, stats, rec, items, nitems,
-        valid, freq_t, kfreq, partial;
+        valid, freq_t, kfreq, partial, cover;
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -827,7 +836,7 @@ void free_plan(BatchPlan* p)
     if (p->cap) cudaStreamDestroy(p->cap);
     DevBuf* all[] = {&p->angles, &p->rayoff, &p->pang,   &p->recoff, &p->mask,   &p->tilebase, &p->scan_scr,
                      &p->q0,     &p->q1,     &p->ctr64,  &p->ctr32,  &p->stats,  &p->rec,      &p->items,
-                     &p->nitems, &p->valid,  &p->freq_t, &p->kfreq,  &p->partial};
+                     &p->nitems, &p->valid,  &p->freq_t, &p->kfreq,  &p->partial, &p->cover};
     for (DevBuf* b : all) b->release();
     delete p;
 }
@@ -877,6 +886,12 @@ cudaError_t enqueue_plan(const sbr_ctx* c, BatchPlan& P, cudaStream_t st)
         ta.mask = P.mask.as<unsigned>();
         ta.tile_base = P.tilebase.as<unsigned>();
         ta.stats = P.stats.as<unsigned long long>();
+        if (P.tune.silhouette) {
+            e = cudaMemsetAsync(P.cover.p, 0, sizeof(unsigned) * (size_t)(rays / 32 + na), st);
+            if (e == cudaSuccess) e = launch_silhouette(ta, (int)c->n_tri, P.cover.as<unsigned>(), st);
+            if (e != cudaSuccess) break;
+            ta.cover = P.cover.as<unsigned>();
+        }
         ta.bounce = 0;
         ta.work = P.ctr64.as<unsigned long long>();
         ta.q_out = qs[0];
@@ -987,6 +1002,7 @@ int build_plan(sbr_ctx* c, BatchPlan& P)
     CK(P.pang.ensure(sizeof(PoAngle) * (size_t)n), "alloc aspect table");
     CK(P.recoff.ensure(sizeof(unsigned) * (size_t)(max_angles + 1)), "alloc record offsets");
     CK(P.mask.ensure(sizeof(unsigned) * (size_t)max_tiles), "alloc mask");
+    if (P.tune.silhouette) CK(P.cover.ensure(sizeof(unsigned) * (size_t)(max_tiles + max_angles)), "alloc cover");
     CK(P.tilebase.ensure(sizeof(unsigned) * (size_t)max_tiles), "alloc tile base");
     CK(P.scan_scr.ensure(scan_scratch_bytes(max_tiles)), "alloc scan scratch");
     CK(P.q0.ensure(sizeof(RayState) * (size_t)max_rays), "alloc ray queue");
@@ -1048,7 +1064,8 @@ int build_plan(sbr_ctx* c, BatchPlan& P)
     P.n_pass = (int64_t)nc * passes;
     P.n_launch = 0;
     for (size_t k = 0; k < nc; ++k)
-        P.n_launch += passes + ((P.max_bounces == 1 && !escape) ? 1 : 0) + 3 + 1 + 2 + (P.items_bound[k] > 0 ? 1 : 0) + 1;
+        P.n_launch += passes + ((P.max_bounces == 1 && !escape) ? 1 : 0) + 3 + 1 + 2 + (P.items_bound[k] > 0 ? 1 : 0) + 1 +
+                      (P.tune.silhouette ? 1 : 0);
     return SBR_OK;
 }
 
@@ -1064,7 +1081,7 @@ int sbr_trace(sbr_ctx* c, const double* az_el, int64_t n_angles, double ds, doub
     if (!az_el || n_angles < 1) return fail(c, SBR_ERR_ARG, "sbr_trace: no angles");
     if (n_angles > (1ll << 30)) return fail(c, SBR_ERR_ARG, "sbr_trace: too many angles");
     if (!(ds > 0.0) || !(eta >= 0.0)) return fail(c, SBR_ERR_ARG, "sbr_trace: spacing must be > 0, eta >= 0");
-    if (max_bounces < 1 || max_bounces > kMaxBounces) return fail(c, SBR_ERR_ARG, "sbr_trace: max_bounces in 1..64");
+    if (max_bounces < 1 || max_bounces > kMaxBounces) return fail(c, SBR_ERR_ARG, "sbr_trace: max_bounces in 1..128");
     CK(cudaSetDevice(c->device), "cudaSetDevice");
     TraceRun R;
     R.flags = opt ? opt->flags : 0;
@@ -1147,7 +1164,7 @@ int sbr_run_batch(sbr_ctx* c, const sbr_request* req, int64_t n_req, const doubl
     if (!freq_hz || n_freq_total < 1 || n_freq_total > (1ll << 30))
         return fail(c, SBR_ERR_ARG, "sbr_run_batch: bad frequency array");
     if (!(eta >= 0.0)) return fail(c, SBR_ERR_ARG, "sbr_run_batch: eta >= 0");
-    if (max_bounces < 1 || max_bounces > kMaxBounces) return fail(c, SBR_ERR_ARG, "sbr_run_batch: max_bounces in 1..64");
+    if (max_bounces < 1 || max_bounces > kMaxBounces) return fail(c, SBR_ERR_ARG, "sbr_run_batch: max_bounces in 1..128");
     if (opt && (opt->flags & SBR_TRACE_RECORD_HITS))
         return fail(c, SBR_ERR_ARG, "sbr_run_batch: SBR_TRACE_RECORD_HITS is for sbr_trace");
     PoArgs pa;
@@ -1228,7 +1245,7 @@ int sbr_submit_batch(sbr_ctx* c, const sbr_request* req, int64_t n_req, const do
         return fail(c, SBR_ERR_ARG, "sbr_submit_batch: bad frequency array");
     if (!(eta >= 0.0)) return fail(c, SBR_ERR_ARG, "sbr_submit_batch: eta >= 0");
     if (max_bounces < 1 || max_bounces > kMaxBounces)
-        return fail(c, SBR_ERR_ARG, "sbr_submit_batch: max_bounces in 1..64");
+        return fail(c, SBR_ERR_ARG, "sbr_submit_batch: max_bounces in 1..128");
     sbr_trace_opts o;
     memset(&o, 0, sizeof(o));
     if (opt) o = *opt;
@@ -1405,9 +1422,10 @@ int sbr_autotune(sbr_ctx* c, const sbr_request* req, int64_t n_req, const double
     sbr_tuning bestt = start;
     const int occ = std::min(4, std::max(1, trace_blocks_per_sm()));
     // parameter 0 is the traversal: binary per lane, 4-wide per lane, binary per warp
-    for (int p = 0; p < 6; ++p) {
+    for (int p = 0; p < 7; ++p) {
         std::vector<int> vals;
         if (p == 0) vals = {0, 1, 2};
+        if (p == 6) vals = {0, 1};
         if (p == 1)
             for (int v = 1; v <= occ; ++v) vals.push_back(v);
         if (p == 2) vals = {32, 16, 8, 4};
@@ -1423,7 +1441,8 @@ int sbr_autotune(sbr_ctx* c, const sbr_request* req, int64_t n_req, const double
                 t.packet = pk;
                 if (pk && t.stack_depth > 64) t.stack_depth = 64;
             } else {
-                int* fields[6] = {nullptr, &t.blocks_per_sm, &t.tile_w, &t.stack_depth, &t.po_item, &t.chunk_rays_log2};
+                int* fields[7] = {nullptr,    &t.blocks_per_sm,   &t.tile_w,    &t.stack_depth,
+                                  &t.po_item, &t.chunk_rays_log2, &t.silhouette};
                 if (*fields[p] == v) continue;
                 *fields[p] = v;
             }
@@ -1438,7 +1457,7 @@ int sbr_autotune(sbr_ctx* c, const sbr_request* req, int64_t n_req, const double
                     }
             }
             note(t, ms, st);
-            if (st == SBR_OK && ms < cur_ms) {
+            if (st == SBR_OK && ms < 0.99 * cur_ms) {  // keep a change only when it is clearly faster
                 cur_ms = ms;
                 bestt = t;
             }

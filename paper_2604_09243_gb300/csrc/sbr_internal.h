@@ -121,6 +121,8 @@ struct TraceArgs {
     RayState* q_out;
     unsigned* q_out_count;
     unsigned* mask;               // [total_rays / 32] valid bits of primary rays
+    const unsigned* cover;        // optional [total_rays / 32 + n_angles] silhouette bits (0 = the ray surely
+                                  // misses) and per-aspect all-rays flags
     const unsigned* tile_base;    // [total_rays / 32] exclusive prefix of popcount(mask)
     Record* rec;                  // dense records of this chunk (already offset to the chunk)
     unsigned long long* work;     // work counter (zeroed before each pass)
@@ -134,6 +136,12 @@ int trace_blocks_per_sm();
 // the warp-cooperative traversal uses at most 64)
 cudaError_t launch_trace(const TraceArgs& a, int n_blocks, bool count_visits, int stack_depth, cudaStream_t st);
 cudaError_t launch_emit_all(const TraceArgs& a, int n_blocks, cudaStream_t st);
+// Silhouette mask of the aspects of a chunk (a.angles, a.ray_off, a.n_angles):
+// sets cover bit (processing layout) of every grid ray whose (u, v) lies in
+// the conservatively widened projected box of some triangle, or the aspect's
+// all-rays flag (word a.total_rays / 32 + aspect) for a triangle too large to
+// rasterise. cover must be zeroed first ([a.total_rays / 32 + a.n_angles] words).
+cudaError_t launch_silhouette(const TraceArgs& a, int n_tri, unsigned* cover, cudaStream_t st);
 
 // exclusive scan of in[i] (or popcount(in[i])) -> out[i]; total written to *total
 size_t scan_scratch_bytes(long long n);

@@ -17,6 +17,8 @@
 #include <float.h>
 #include <limits.h>
 
+#include <algorithm>
+
 #include "sbr_internal.h"
 
 namespace sbr {
@@ -610,6 +612,68 @@ __device__ __forceinline__ void query(const TraceArgs& a, bool active, float3 o,
     }
 }
 
+// ---------------------------------------------------------------- silhouette mask
+// Ray (i, j) of an aspect travels along k through the aperture point
+// u = u0 + i ds, v = v0 + j ds (u, v along H and V; u0, v0 those of P0). It can
+// only hit a triangle whose projection contains (u, v); the FP32 ray origin,
+// the intersection slack (2^-12 of the determinant) and the FP32 projection
+// below all stay within the margin of 0.01 cell + 2^-10 of the triangle's
+// projected extent + 2^-18 of its distance from P0 (in cells). One thread
+// projects one triangle for one aspect and ORs its cells into the tile words.
+// A triangle whose widened box spans more than 2^16 cells sets the aspect's
+// "all rays" flag (word total_tiles + aspect) instead.
+__global__ void __launch_bounds__(256) k_silhouette(const float4* __restrict__ tris, int n_tri,
+                                                    const AngleDev* __restrict__ angles,
+                                                    const long long* __restrict__ ray_off, int n_angles,
+                                                    long long total_tiles, unsigned* cover)
+{
+    for (int ang = blockIdx.y; ang < n_angles; ang += gridDim.y) {
+        const AngleDev& A = angles[ang];
+        const float ds = sqrtf(A.dA), ids = 1.f / ds;
+        const int tw = A.tw_log2, W = 1 << tw, H = 32 >> tw;
+        for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tri; t += gridDim.x * blockDim.x) {
+            const float4 a = __ldg(tris + 3 * (size_t)t), b = __ldg(tris + 3 * (size_t)t + 1),
+                         c = __ldg(tris + 3 * (size_t)t + 2);
+            const float px[3] = {a.x, a.x + b.x, a.x + c.x}, py[3] = {a.y, a.y + b.y, a.y + c.y},
+                        pz[3] = {a.z, a.z + b.z, a.z + c.z};
+            float umin = FLT_MAX, umax = -FLT_MAX, vmin = FLT_MAX, vmax = -FLT_MAX, mag = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float dx = px[k] - A.p0[0], dy = py[k] - A.p0[1], dz = pz[k] - A.p0[2];
+                const float u = (dx * A.hhat[0] + dy * A.hhat[1] + dz * A.hhat[2]) * ids;
+                const float v = (dx * A.vhat[0] + dy * A.vhat[1] + dz * A.vhat[2]) * ids;
+                umin = fminf(umin, u);
+                umax = fmaxf(umax, u);
+                vmin = fminf(vmin, v);
+                vmax = fmaxf(vmax, v);
+                mag = fmaxf(mag, (fabsf(dx) + fabsf(dy) + fabsf(dz)) * ids);
+            }
+            if (!(umin <= umax) || !(vmin <= vmax)) continue;  // NaN vertices: no ray can hit it
+            const float m = 0.01f + (umax - umin + vmax - vmin) * (1.f / 1024.f) + mag * (1.f / 262144.f);
+            const float fi0 = ceilf(umin - m), fi1 = floorf(umax + m), fj0 = ceilf(vmin - m), fj1 = floorf(vmax + m);
+            if (fi1 < 0.f || fj1 < 0.f || fi0 > (float)(A.nu - 1) || fj0 > (float)(A.nv - 1)) continue;
+            const int i0 = max(0, (int)fi0), i1 = min(A.nu - 1, (int)fi1);
+            const int j0 = max(0, (int)fj0), j1 = min(A.nv - 1, (int)fj1);
+            if ((long long)(i1 - i0 + 1) * (j1 - j0 + 1) > 65536) {
+                atomicOr(cover + total_tiles + ang, 1u);
+                continue;
+            }
+            const long long base = ray_off[ang];
+            for (int j = j0; j <= j1; ++j) {
+                const int bv = j / H, jl = j - bv * H;
+                for (int i = i0; i <= i1;) {
+                    const int bu = i >> tw, ie = min(i1, (bu << tw) + W - 1);
+                    // bits (jl W + i % W) .. (jl W + ie % W) of tile (bv nbu + bu)
+                    const int lo = jl * W + (i & (W - 1)), hi = jl * W + (ie & (W - 1));
+                    const unsigned bits = (hi - lo == 31) ? 0xFFFFFFFFu : (((1u << (hi - lo + 1)) - 1u) << lo);
+                    atomicOr(cover + ((base >> 5) + (long long)bv * A.nbu + bu), bits);
+                    i = ie + 1;
+                }
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------- pass 0: primary rays
 template <bool kCount, int kStack, int kMode>
 __global__ void __launch_bounds__(kTraceThreads, 4) k_primary(const TraceArgs a)
@@ -629,7 +693,9 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_primary(const TraceArgs a)
         const int local = (int)((long long)base + lane - a.ray_off[ang]);
         int i, j;
         tile_ij(A, local, i, j);
-        const bool active = i < A.nu && j < A.nv;
+        bool active = i < A.nu && j < A.nv;
+        if (a.cover)
+            active = active && (((a.cover[base >> 5] >> lane) & 1u) || a.cover[(a.total_rays >> 5) + ang]);
         bool hit = false;
         Ray r;
         r.angle = ang;
@@ -775,6 +841,16 @@ cudaError_t launch_trace(const TraceArgs& a, int n_blocks, bool count_visits, in
 cudaError_t launch_emit_all(const TraceArgs& a, int n_blocks, cudaStream_t st)
 {
     k_emit_all<<<n_blocks, kTraceThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_silhouette(const TraceArgs& a, int n_tri, unsigned* cover, cudaStream_t st)
+{
+    if (a.n_angles <= 0 || n_tri <= 0) return cudaSuccess;
+    const int bx = (int)std::min<long long>((n_tri + 255) / 256, 64);
+    const int by = std::min(a.n_angles, 4096);
+    k_silhouette<<<dim3(bx, by), 256, 0, st>>>(a.tris, n_tri, a.angles, a.ray_off, a.n_angles, a.total_rays >> 5,
+                                               cover);
     return cudaGetLastError();
 }
 

@@ -303,3 +303,21 @@ def test_aircraft_sampled_parity(G, ctx, orc):
         assert_hit_parity(s)
         Eo, Ro = orc.po(o["coef"], o["L"], o["valid"], case["freqs"])
         assert_rcs_close(R[a, 0], Ro[0, :2])
+
+
+def test_deep_cavity_escape_parity(G, ctx, orc):
+    """Nose-on view into the two 3 m engine inlets of the aircraft at 1 GHz: up
+    to 100 bounces, a ray still hitting after them is invalid. Every ray's hits,
+    bounce count and the RCS match the oracle."""
+    case = S.aircraft_case(1e9, n_az=360)
+    ctx.load_mesh(case["xyz"], case["tri"])
+    om = orc.Mesh(case["xyz"], case["tri"])
+    ang = case["angles"][[180]]
+    st, res = _trace_both(G, ctx, orc, om, ang, case["spacing"], 100, eta=case["eta"], offset=case["offset"],
+                          flags=G.TRACE_REQUIRE_ESCAPE)
+    E, R = ctx.po_integrate(case["freqs"], "HH,VV")
+    g, o, fr = res[0]
+    assert_hit_parity(compare_hits(*g, o))
+    assert int(o["nb"].max()) > 10  # rays do bounce deep inside the inlets
+    Eo, Ro = orc.po(o["coef"], o["L"], o["valid"], case["freqs"])
+    assert_rcs_close(R[0, 0], Ro[0, :2])

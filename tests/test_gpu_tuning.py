@@ -33,7 +33,8 @@ def _trace(c, case, angles, **kw):
                                      dict(stack_depth=128), dict(blocks_per_sm=1), dict(po_item=512),
                                      dict(po_item=2048), dict(chunk_rays_log2=20), dict(bvh_width=4),
                                      dict(bvh_width=4, stack_depth=32, tile_w=4), dict(packet=1),
-                                     dict(packet=1, stack_depth=32, tile_w=32)])
+                                     dict(packet=1, stack_depth=32, tile_w=32), dict(silhouette=1),
+                                     dict(silhouette=1, bvh_width=4, tile_w=16)])
 def test_setting_keeps_hits_and_fields(G, tri_case, setting):
     case = tri_case
     angles = case["angles"][[0, 45, 90, 135, 180]]
@@ -62,7 +63,8 @@ def test_bad_settings_refused(G):
         before = c.tuning()
         for bad in (dict(tile_w=3), dict(tile_w=64), dict(blocks_per_sm=0), dict(blocks_per_sm=5),
                     dict(stack_depth=48), dict(po_item=300), dict(chunk_rays_log2=19), dict(chunk_rays_log2=28),
-                    dict(bvh_width=3), dict(packet=2), dict(packet=1, bvh_width=4), dict(packet=1, stack_depth=128)):
+                    dict(bvh_width=3), dict(packet=2), dict(packet=1, bvh_width=4), dict(packet=1, stack_depth=128),
+                    dict(silhouette=2)):
             with pytest.raises(G.SbrError):
                 c.set_tuning(**bad)
         assert c.tuning() == before
@@ -125,3 +127,35 @@ def test_wide_tree_same_hits_aircraft(G):
             for x, y in zip(a, b):
                 assert np.array_equal(x, y)
         assert np.array_equal(R2, R4)
+
+
+def test_silhouette_mask_skips_only_misses(G):
+    """With the silhouette mask the aircraft's rays keep their hits (bit for
+    bit) and valid count while fewer queries run; a two-triangle plate much
+    larger than the grid cells takes the all-rays path and keeps its RCS."""
+    case = S.aircraft_case(1e9, n_az=360)
+    angles = case["angles"][[0, 45, 180, 300]]
+    out = []
+    for sil in (0, 1):
+        with G.Context(0) as c:
+            c.load_mesh(case["xyz"], case["tri"])
+            c.set_tuning(silhouette=sil)
+            st = c.trace(angles, case["spacing"], eta=case["eta"], max_bounces=case["max_bounces"],
+                         offset=case["offset"], flags=G.TRACE_RECORD_HITS)
+            out.append((st, [c.get_hits(a) for a in range(len(angles))], c.po_integrate([1e9])[1]))
+    (s0, h0, R0), (s1, h1, R1) = out
+    assert s1["valid_rays"] == s0["valid_rays"] and s1["rays_launched"] == s0["rays_launched"]
+    assert s1["ray_bounces"] < s0["ray_bounces"]
+    for a, b in zip(h0, h1):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+    assert np.array_equal(R0, R1)
+    xyz, tri = S.square_plate(1.0, m=1)  # two 1 m triangles: 500 x 500 cells each at 2 mm
+    res = []
+    for sil in (0, 1):
+        with G.Context(0) as c:
+            c.load_mesh(xyz, tri)
+            c.set_tuning(silhouette=sil)
+            c.trace([[0.0, 90.0], [10.0, 80.0]], 0.002, max_bounces=1)
+            res.append(c.po_integrate([10e9])[1])
+    assert np.array_equal(res[0], res[1])
