@@ -206,7 +206,7 @@ def run_reference(args, case, ws, rank, pg):
     line = {"impl": "reference", "metric": "ray-bounces/s", "value": v, "unit": "ray-bounces/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": wl_config(case, args.workload),
+            "config": dict(wl_config(case, args.workload), bvh_builder=args.builder),
             "angles_per_s": n * args.steps / tot_t,
             "cpu_baseline": {"value": v, "unit": "ray-bounces/s", "cores": threads, "kind": "oracle",
                              "sample": f"{n} of {len(case['angles'])} aspects per step (evenly spaced), full ray grids"},
@@ -503,6 +503,8 @@ def run_sbr(args, case, ws, rank, local, pg):
     stream = torch.cuda.Stream()
     ctx = G.Context(local, stream=stream)
     ctx.load_mesh(case["xyz"], case["tri"])
+    if args.builder != "lbvh":
+        ctx.build_bvh(builder=args.builder)
     ang = np.ascontiguousarray(case["angles"], np.float64)
     freqs = np.ascontiguousarray(case["freqs"], np.float64)
     B = case["max_bounces"]
@@ -573,6 +575,8 @@ def run_sbr(args, case, ws, rank, local, pg):
 
     def e2e_step():
         ctx.load_mesh(xyz_p.numpy(), tri_p.numpy())
+        if args.builder != "lbvh":
+            ctx.build_bvh(builder=args.builder)
         ctx.trace(ang_p.numpy(), case["spacing"], flags=xf, **kw)
         E, R = ctx.po_integrate(freqs, "HH,VV")
         E_h[...] = np.stack([E.real, E.imag], -1)
@@ -605,7 +609,7 @@ def run_sbr(args, case, ws, rank, local, pg):
     line = {"metric": "ray-bounces/s", "value": value, "unit": "ray-bounces/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": wl_config(case, args.workload),
+            "config": dict(wl_config(case, args.workload), bvh_builder=args.builder),
             "angles_per_s": ws * na * args.steps / t_dev,
             "rays_launched_per_step": stats[0]["rays_launched"], "ray_bounces_per_step": bounces,
             "valid_rays_per_step": stats[0]["valid_rays"],
@@ -654,6 +658,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tuning")
     ap.add_argument("--no-precision", action="store_true", help="skip the phase-precision report")
+    ap.add_argument("--builder", default="lbvh", choices=["lbvh", "ploc"], help="BVH builder of the timed workload")
     ap.add_argument("--tune-aspects", type=int, default=24, help="aspects in the autotuner's sample")
     ap.add_argument("--tune", default="", help="fixed tuning instead of the autotuner, e.g. tile_w=4,stack_depth=32")
     ap.add_argument("--sur-domains", default="full,patch", help="surrogate: domains to evaluate")

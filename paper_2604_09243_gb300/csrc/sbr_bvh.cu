@@ -376,6 +376,172 @@ __global__ void __launch_bounds__(kThreads) k_reorder(const float* xyz, const in
     tris[3 * p + 2] = make_float4(cx - ax, cy - ay, cz - az, 0.f);
 }
 
+// ---------------------------------------------------------------- PLOC builder
+// Agglomerative clustering over the Morton-ordered triangles: every round,
+// each cluster looks for the cluster within `radius` positions whose union
+// box has the smallest surface area (ties: the lower position); mutual nearest
+// neighbours merge into a new node, the survivors are compacted, until one
+// cluster is left. Node ids count down from n - 2, so the root is node 0 and
+// a node's id is below its children's. The SAH leaf-collapse decision of each
+// node is taken when it is made, from its children's costs (same rule as the
+// LBVH refit). A top-down pass then gives every node the first position of
+// its triangles, so each collapsed subtree is a contiguous range.
+struct Clusters {
+    float4* lo;
+    float4* hi;
+    int* ref;    // >= 0 node id, < 0 ~triangle id
+    int* cnt;
+    float* cost;
+};
+
+__global__ void __launch_bounds__(kThreads) k_ploc_init(const unsigned* vals, const float4* tbox, int n, float c_i,
+                                                        Clusters c)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const unsigned t = vals[i];
+    const float4 lo = tbox[2 * (size_t)t], hi = tbox[2 * (size_t)t + 1];
+    c.lo[i] = lo;
+    c.hi[i] = hi;
+    c.ref[i] = ~(int)t;
+    c.cnt[i] = 1;
+    c.cost[i] = c_i * area(lo, hi);
+}
+
+__device__ __forceinline__ float union_area(float4 al, float4 ah, float4 bl, float4 bh)
+{
+    return area(make_float4(fminf(al.x, bl.x), fminf(al.y, bl.y), fminf(al.z, bl.z), 0.f),
+                make_float4(fmaxf(ah.x, bh.x), fmaxf(ah.y, bh.y), fmaxf(ah.z, bh.z), 0.f));
+}
+
+__global__ void __launch_bounds__(kThreads) k_ploc_nn(int m, int radius, Clusters c, int* nn)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const float4 lo = c.lo[i], hi = c.hi[i];
+    float best = FLT_MAX;
+    int bj = -1;
+    const int j0 = max(0, i - radius), j1 = min(m - 1, i + radius);
+    for (int j = j0; j <= j1; ++j) {
+        if (j == i) continue;
+        const float a = union_area(lo, hi, c.lo[j], c.hi[j]);
+        if (a < best) {  // strict: the lowest position wins ties
+            best = a;
+            bj = j;
+        }
+    }
+    nn[i] = bj;
+}
+
+__global__ void __launch_bounds__(kThreads) k_ploc_merge(int m, Clusters c, const int* nn, int* next_id, int* left,
+                                                         int* right, float4* nbox, int* ncnt, float* ncost, int* ncol,
+                                                         unsigned* keep, int leaf_max, float c_t, float c_i)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int j = nn[i];
+    if (j < 0 || nn[j] != i) {
+        keep[i] = 1;  // no mutual partner this round
+        return;
+    }
+    if (i > j) {
+        keep[i] = 0;  // merged into j
+        return;
+    }
+    const float4 al = c.lo[i], ah = c.hi[i], bl = c.lo[j], bh = c.hi[j];
+    const float4 lo = make_float4(fminf(al.x, bl.x), fminf(al.y, bl.y), fminf(al.z, bl.z), 0.f);
+    const float4 hi = make_float4(fmaxf(ah.x, bh.x), fmaxf(ah.y, bh.y), fmaxf(ah.z, bh.z), 0.f);
+    const int cnt = c.cnt[i] + c.cnt[j];
+    const float sa = area(lo, hi);
+    const float split = c_t * sa + c.cost[i] + c.cost[j];
+    const float as_leaf = c_i * (float)cnt * sa;
+    const int col = (cnt <= leaf_max) && (as_leaf <= split);
+    const int id = atomicSub(next_id, 1);
+    left[id] = c.ref[i];
+    right[id] = c.ref[j];
+    nbox[2 * id] = lo;
+    nbox[2 * id + 1] = hi;
+    ncnt[id] = cnt;
+    ncost[id] = col ? as_leaf : split;
+    ncol[id] = col;
+    c.lo[i] = lo;
+    c.hi[i] = hi;
+    c.ref[i] = id;
+    c.cnt[i] = cnt;
+    c.cost[i] = col ? as_leaf : split;
+    keep[i] = 1;
+}
+
+__global__ void __launch_bounds__(kThreads) k_ploc_compact(int m, Clusters in, const unsigned* keep,
+                                                           const unsigned* pos, Clusters out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m || !keep[i]) return;
+    const unsigned k = pos[i];
+    out.lo[k] = in.lo[i];
+    out.hi[k] = in.hi[i];
+    out.ref[k] = in.ref[i];
+    out.cnt[k] = in.cnt[i];
+    out.cost[k] = in.cost[i];
+}
+
+// one level of the top-down pass: node q of the frontier starts at noff[q];
+// its left subtree goes first; triangles get their positions (perm)
+__global__ void __launch_bounds__(kThreads) k_ploc_offsets(const int* qin, int nin, const int* left, const int* right,
+                                                           const int* ncnt, int* noff, unsigned* perm, int* qout,
+                                                           int* nout)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nin) return;
+    const int q = qin[w];
+    const int o = noff[q];
+    const int ch[2] = {left[q], right[q]};
+    int off = o;
+    for (int s = 0; s < 2; ++s) {
+        const int c = ch[s];
+        if (c < 0) {
+            perm[off] = (unsigned)(~c);
+            off += 1;
+        } else {
+            noff[c] = off;
+            qout[atomicAdd(nout, 1)] = c;
+            off += ncnt[c];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_ploc_emit(int n, const int* left, const int* right, const float4* nbox,
+                                                        const int* ncnt, const int* ncol, const int* noff,
+                                                        const float4* tbox, float4* nodes)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    const float4 elo = make_float4(FLT_MAX, FLT_MAX, FLT_MAX, 0.f), ehi = make_float4(-FLT_MAX, -FLT_MAX, -FLT_MAX, 0.f);
+    if (i == 0 && ncol[0]) {
+        put_node(nodes, 0, nbox[0], nbox[1], elo, ehi, leaf_ref(0, ncnt[0]), kEmptyRef);
+        return;
+    }
+    float4 bl[2], bh[2];
+    int ref[2];
+    const int ch[2] = {left[i], right[i]};
+    int off = noff[i];
+    for (int s = 0; s < 2; ++s) {
+        const int c = ch[s];
+        if (c < 0) {
+            bl[s] = tbox[2 * (size_t)(~c)];
+            bh[s] = tbox[2 * (size_t)(~c) + 1];
+            ref[s] = leaf_ref(off, 1);
+            off += 1;
+        } else {
+            bl[s] = nbox[2 * c];
+            bh[s] = nbox[2 * c + 1];
+            ref[s] = ncol[c] ? leaf_ref(off, ncnt[c]) : c;
+            off += ncnt[c];
+        }
+    }
+    put_node(nodes, i, bl[0], bh[0], bl[1], bh[1], ref[0], ref[1]);
+}
+
 // ---------------------------------------------------------------- 4-wide collapse
 __device__ __forceinline__ float half_area(float4 lo, float4 hi)
 {
@@ -500,6 +666,14 @@ size_t bvh_scratch_bytes(long long n_tri)
     add(n * 4);                             // flags
     add(n * 32); add(n * 32);               // lbox nbox
     add(n * 4); add(n * 4); add(n * 4);     // ncnt ncost ncol
+    for (int k = 0; k < 2; ++k) {           // PLOC clusters, two buffers
+        add(n * 16); add(n * 16); add(n * 4); add(n * 4); add(n * 4);
+    }
+    add(n * 4); add(n * 4); add(n * 4);     // nn keep pos
+    add(scan_scratch_bytes((long long)n));
+    add(n * 4); add(n * 4);                 // noff perm
+    add(n * 4); add(n * 4);                 // level queues
+    add(64);                                // counters
     return b + 256;
 }
 
@@ -531,6 +705,23 @@ cudaError_t bvh_build(const BvhBuild& b, cudaStream_t st)
     int* ncnt = cv.take<int>(nn);
     float* ncost = cv.take<float>(nn);
     int* ncol = cv.take<int>(nn);
+    Clusters cl[2];
+    for (int k = 0; k < 2; ++k) {
+        cl[k].lo = cv.take<float4>(nn);
+        cl[k].hi = cv.take<float4>(nn);
+        cl[k].ref = cv.take<int>(nn);
+        cl[k].cnt = cv.take<int>(nn);
+        cl[k].cost = cv.take<float>(nn);
+    }
+    int* pnn = cv.take<int>(nn);
+    unsigned* keep = cv.take<unsigned>(nn);
+    unsigned* pos = cv.take<unsigned>(nn);
+    void* pscan = cv.take<char>(scan_scratch_bytes((long long)nn));
+    int* noff = cv.take<int>(nn);
+    unsigned* perm = cv.take<unsigned>(nn);
+    int* qa = cv.take<int>(nn);
+    int* qb = cv.take<int>(nn);
+    int* ctr = cv.take<int>(16);
     if (cv.off > cv.cap) return cudaErrorInvalidValue;
 
     const int g = (n + kThreads - 1) / kThreads;
@@ -551,6 +742,54 @@ cudaError_t bvh_build(const BvhBuild& b, cudaStream_t st)
         unsigned* tv = vi; vi = vo; vo = tv;
     }
     // after an even number of passes the sorted data is back in (k0, v0)
+    if (b.builder == 1 && n > 1) {
+        // PLOC over the Morton order (synchronises once per round and per level)
+        const float c_t = b.c_t, c_i = b.c_i;
+        const int radius = b.radius > 0 ? b.radius : 16;
+        k_ploc_init<<<g, kThreads, 0, st>>>(vi, tbox, n, c_i, cl[0]);
+        int h[2] = {n - 2, 0};
+        cudaError_t e = cudaMemcpyAsync(ctr, h, sizeof(h), cudaMemcpyHostToDevice, st);
+        int m = n, cur = 0;
+        for (int round = 0; e == cudaSuccess && m > 1; ++round) {
+            if (round >= 1 << 16) return cudaErrorInvalidValue;  // every round merges at least one pair
+            const int gm = (m + kThreads - 1) / kThreads;
+            k_ploc_nn<<<gm, kThreads, 0, st>>>(m, radius, cl[cur], pnn);
+            k_ploc_merge<<<gm, kThreads, 0, st>>>(m, cl[cur], pnn, ctr, left, right, nbox, ncnt, ncost, ncol, keep,
+                                                  b.leaf_max, c_t, c_i);
+            e = scan_exclusive_u32(keep, pos, m, false, (unsigned*)(ctr + 1), pscan, st);
+            if (e != cudaSuccess) break;
+            k_ploc_compact<<<gm, kThreads, 0, st>>>(m, cl[cur], keep, pos, cl[cur ^ 1]);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&m, ctr + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            cur ^= 1;
+        }
+        if (e != cudaSuccess) return e;
+        // positions: top-down, one level at a time from the root (node 0)
+        const int zero = 0;
+        e = cudaMemcpyAsync(noff, &zero, sizeof(int), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(qa, &zero, sizeof(int), cudaMemcpyHostToDevice, st);
+        int nin = 1;
+        int *qi = qa, *qo = qb;
+        for (int level = 0; e == cudaSuccess && nin > 0; ++level) {
+            if (level > n) return cudaErrorInvalidValue;
+            e = cudaMemsetAsync(ctr + 2, 0, sizeof(int), st);
+            if (e != cudaSuccess) break;
+            k_ploc_offsets<<<(nin + kThreads - 1) / kThreads, kThreads, 0, st>>>(qi, nin, left, right, ncnt, noff,
+                                                                                perm, qo, ctr + 2);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&nin, ctr + 2, sizeof(int), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            int* t = qi;
+            qi = qo;
+            qo = t;
+        }
+        if (e != cudaSuccess) return e;
+        k_ploc_emit<<<(n - 1 + kThreads - 1) / kThreads, kThreads, 0, st>>>(n, left, right, nbox, ncnt, ncol, noff,
+                                                                            tbox, b.nodes);
+        k_reorder<<<g, kThreads, 0, st>>>(b.xyz, b.tri, b.n_vert, perm, n, b.tris);
+        return cudaGetLastError();
+    }
     if (n > 1) {
         k_karras<<<(n - 1 + kThreads - 1) / kThreads, kThreads, 0, st>>>(ki, n, left, right, first, last, par_int,
                                                                          par_leaf);

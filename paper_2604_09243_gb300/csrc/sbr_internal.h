@@ -91,6 +91,8 @@ struct BvhBuild {
     long long n_vert, n_tri;
     int leaf_max;
     float c_t, c_i;
+    int builder;  // 0: Karras LBVH with SAH refit; 1: PLOC clustering (synchronises per round)
+    int radius;   // PLOC search radius (0: 16)
     // outputs (allocated by the caller: nodes [max(n_tri-1,1)*4] float4, tris [n_tri*3] float4)
     float4* nodes;
     float4* tris;

@@ -43,7 +43,8 @@ class SbrError(RuntimeError):
 
 
 class BvhOpts(C.Structure):
-    _fields_ = [("leaf_max", C.c_int), ("cost_traverse", C.c_float), ("cost_intersect", C.c_float)]
+    _fields_ = [("leaf_max", C.c_int), ("cost_traverse", C.c_float), ("cost_intersect", C.c_float),
+                ("builder", C.c_int), ("ploc_radius", C.c_int)]
 
 
 class TraceOpts(C.Structure):
@@ -263,8 +264,11 @@ class Context:
         self._check(lib().sbr_load_mesh(self._h, xyz.ctypes.data, len(xyz), tri.ctypes.data, len(tri), 0))
         self.n_tri = len(tri)
 
-    def build_bvh(self, leaf_max: int = 4, cost_traverse: float = 1.0, cost_intersect: float = 1.0):
-        o = BvhOpts(int(leaf_max), float(cost_traverse), float(cost_intersect))
+    def build_bvh(self, leaf_max: int = 4, cost_traverse: float = 1.0, cost_intersect: float = 1.0,
+                  builder: str = "lbvh", ploc_radius: int = 0):
+        """sbr_build_bvh; builder "lbvh" (Karras) or "ploc" (nearest-neighbour clustering)."""
+        o = BvhOpts(int(leaf_max), float(cost_traverse), float(cost_intersect), {"lbvh": 0, "ploc": 1}[builder],
+                    int(ploc_radius))
         self._check(lib().sbr_build_bvh(self._h, C.byref(o)))
 
     def get_bbox(self) -> np.ndarray:

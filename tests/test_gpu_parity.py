@@ -194,6 +194,47 @@ def test_leaf_sizes_same_hits(G, ctx, orc, leaf):
     assert_hit_parity(compare_hits(*res[0][0], res[0][1]))
 
 
+@pytest.mark.parametrize("leaf,radius", [(1, 0), (4, 0), (4, 1), (16, 64)])
+def test_ploc_tree_same_hits(G, ctx, orc, leaf, radius):
+    """The clustering-built tree gives every ray the oracle's hits (sphere and
+    trihedral, 3 bounces) and, on the trihedral, fewer node visits than the
+    Karras LBVH."""
+    for xyz, tri, ang, sp, B, win in ((*S.icosphere(4), [[12.0, 34.0]], 0.01, 1, 2.2),
+                                      (*S.trihedral(1.0, 32), [[30.0, 35.26], [72.5, 35.26]], 0.006, 3, 0.0)):
+        ctx.load_mesh(xyz, tri)
+        om = orc.Mesh(xyz, tri)
+        ctx.build_bvh(leaf_max=leaf)
+        lb = ctx.trace(ang, sp, max_bounces=B, window=win, flags=G.TRACE_COUNT_VISITS)
+        ctx.build_bvh(leaf_max=leaf, builder="ploc", ploc_radius=radius)
+        st, res = _trace_both(G, ctx, orc, om, np.array(ang), sp, B, window=win)
+        for g, o, _ in res:
+            assert_hit_parity(compare_hits(*g, o))
+        pl = ctx.trace(ang, sp, max_bounces=B, window=win, flags=G.TRACE_COUNT_VISITS)
+        assert pl["ray_bounces"] == lb["ray_bounces"] and pl["stack_overflows"] == 0
+        if B == 3 and radius != 1 and leaf == 4:
+            assert pl["node_visits"] < lb["node_visits"], (pl["node_visits"], lb["node_visits"])
+
+
+def test_ploc_tree_aircraft(G, ctx, orc):
+    """~1M triangles: the clustering tree traces the same hits as the Karras
+    tree on both tree widths."""
+    case = S.aircraft_case(1e9, n_az=360)
+    ctx.load_mesh(case["xyz"], case["tri"])
+    ang = case["angles"][[0, 120]]
+    kw = dict(eta=case["eta"], max_bounces=case["max_bounces"], offset=case["offset"])
+    ctx.trace(ang, case["spacing"], flags=G.TRACE_RECORD_HITS, **kw)
+    ref = [ctx.get_hits(a) for a in range(len(ang))]
+    ctx.build_bvh(builder="ploc")
+    for w in (2, 4):
+        ctx.set_tuning(bvh_width=w)
+        st = ctx.trace(ang, case["spacing"], flags=G.TRACE_RECORD_HITS, **kw)
+        assert st["stack_overflows"] == 0
+        for a in range(len(ang)):
+            for x, y in zip(ref[a], ctx.get_hits(a)):
+                assert np.array_equal(x, y)
+    ctx.set_tuning(bvh_width=2)
+
+
 def test_chunked_trace_matches_single_chunk(G, ctx):
     case = S.trihedral_case(az_step=10.0)
     ctx.load_mesh(case["xyz"], case["tri"])
