@@ -53,12 +53,12 @@ OPS_NODE4 = 81
 OPS_TRI = 38
 # DRAM bytes of the three transport passes per launched ray of the trihedral
 # sweep (ncu dram__bytes_read.sum + dram__bytes_write.sum over k_primary and
-# both k_bounce passes, 9 of its aspects = 2,114,692 rays: 190.03 MB, captured
-# with 4 x 8 tiles and a 32-entry stack), for the ray tile and traversal below
+# both k_bounce passes, 9 of its aspects = 2,114,692 rays: 188.39 MB, captured
+# with 4 x 8 tiles on the PLOC tree), for the ray tile, traversal and builder below
 # (stack depth and chunk size leave the DRAM bytes per ray unchanged: the
 # queues and records are the traffic); it grows with the rays, so it is scaled
 # by the rays of a step.
-TRAFFIC_PER_RAY = {"trihedral": (190.03e6 / 2114692, dict(tile_w=4, bvh_width=2, packet=0))}
+TRAFFIC_PER_RAY = {"trihedral": (188.39e6 / 2114692, dict(tile_w=4, bvh_width=2, packet=0), "ploc")}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -503,7 +503,7 @@ def run_sbr(args, case, ws, rank, local, pg):
     stream = torch.cuda.Stream()
     ctx = G.Context(local, stream=stream)
     ctx.load_mesh(case["xyz"], case["tri"])
-    if args.builder != "lbvh":
+    if args.builder != "ploc":
         ctx.build_bvh(builder=args.builder)
     ang = np.ascontiguousarray(case["angles"], np.float64)
     freqs = np.ascontiguousarray(case["freqs"], np.float64)
@@ -575,7 +575,7 @@ def run_sbr(args, case, ws, rank, local, pg):
 
     def e2e_step():
         ctx.load_mesh(xyz_p.numpy(), tri_p.numpy())
-        if args.builder != "lbvh":
+        if args.builder != "ploc":
             ctx.build_bvh(builder=args.builder)
         ctx.trace(ang_p.numpy(), case["spacing"], flags=xf, **kw)
         E, R = ctx.po_integrate(freqs, "HH,VV")
@@ -597,8 +597,8 @@ def run_sbr(args, case, ws, rank, local, pg):
     wide = ctx.tuning()["bvh_width"] == 4
     traffic = None
     if args.workload in TRAFFIC_PER_RAY:
-        per_ray, setting = TRAFFIC_PER_RAY[args.workload]
-        if all(ctx.tuning()[k] == v for k, v in setting.items()):
+        per_ray, setting, builder = TRAFFIC_PER_RAY[args.workload]
+        if builder == args.builder and all(ctx.tuning()[k] == v for k, v in setting.items()):
             traffic = per_ray * stats[0]["rays_launched"]
     ops = (OPS_NODE4 if wide else OPS_NODE) * cnt["node_visits"] + OPS_TRI * cnt["tri_tests"]
     pass_s = float(np.mean([s["pass_ms"] for s in stats])) / 1e3
@@ -658,7 +658,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tuning")
     ap.add_argument("--no-precision", action="store_true", help="skip the phase-precision report")
-    ap.add_argument("--builder", default="lbvh", choices=["lbvh", "ploc"], help="BVH builder of the timed workload")
+    ap.add_argument("--builder", default="ploc", choices=["ploc", "lbvh"], help="BVH builder of the timed workload")
     ap.add_argument("--tune-aspects", type=int, default=24, help="aspects in the autotuner's sample")
     ap.add_argument("--tune", default="", help="fixed tuning instead of the autotuner, e.g. tile_w=4,stack_depth=32")
     ap.add_argument("--sur-domains", default="full,patch", help="surrogate: domains to evaluate")

@@ -75,12 +75,12 @@ typedef struct {
     int leaf_max;         /* largest leaf after the SAH collapse, 1..16 (default 4) */
     float cost_traverse;  /* C_T (default 1) */
     float cost_intersect; /* C_I (default 1) */
-    int builder;          /* SBR_BVH_LBVH (default) or SBR_BVH_PLOC */
+    int builder;          /* SBR_BVH_PLOC (0, default) or SBR_BVH_LBVH */
     int ploc_radius;      /* PLOC search radius in Morton order, 1..64 (0 = 16) */
 } sbr_bvh_opts;
-#define SBR_BVH_LBVH 0 /* Karras hierarchy over the Morton order, bottom-up refit */
-#define SBR_BVH_PLOC 1 /* agglomerative clustering of nearest neighbours in the Morton order (closer to a
-                          full SAH tree; one host synchronisation per clustering round) */
+#define SBR_BVH_PLOC 0 /* agglomerative clustering of mutual nearest neighbours in the Morton order, close
+                          to a full SAH tree (one host synchronisation per four clustering rounds) */
+#define SBR_BVH_LBVH 1 /* Karras hierarchy over the Morton order, bottom-up refit */
 
 /* Ray-grid and transport options of sbr_trace. A zeroed struct gives the defaults. */
 typedef struct {
@@ -156,9 +156,10 @@ int sbr_get_bbox(sbr_ctx* ctx, float* bbox6);
  * device radix sort, Karras hierarchy, bottom-up AABB refit and SAH leaf
  * collapse with C_T, C_I and leaf_max from `opt` (NULL = defaults), triangles
  * reordered so each leaf is a contiguous range; then the 4-wide collapse of
- * that tree (sbr_tuning.bvh_width picks the one traversed). With
- * builder = SBR_BVH_PLOC the hierarchy is built by nearest-neighbour
- * clustering instead of the Karras split, same leaf collapse and layout.
+ * that tree (sbr_tuning.bvh_width picks the one traversed). By default
+ * (SBR_BVH_PLOC; also what sbr_load_mesh builds) the hierarchy comes from
+ * nearest-neighbour clustering of the Morton-ordered triangles instead of the
+ * Karras split (SBR_BVH_LBVH); leaf collapse and layout are the same.
  * Synchronises. */
 int sbr_build_bvh(sbr_ctx* ctx, const sbr_bvh_opts* opt);
 

@@ -392,7 +392,7 @@ int sbr_build_bvh(sbr_ctx* c, const sbr_bvh_opts* opt)
     float ct = opt ? opt->cost_traverse : 1.f, ci = opt ? opt->cost_intersect : 1.f;
     if (leaf_max < 1 || leaf_max > kLeafMax) return fail(c, SBR_ERR_ARG, "sbr_build_bvh: leaf_max must be 1..16");
     if (!(ct >= 0.f) || !(ci > 0.f)) return fail(c, SBR_ERR_ARG, "sbr_build_bvh: costs must be C_T >= 0, C_I > 0");
-    const int builder = opt ? opt->builder : SBR_BVH_LBVH, radius = opt ? opt->ploc_radius : 0;
+    const int builder = opt ? opt->builder : SBR_BVH_PLOC, radius = opt ? opt->ploc_radius : 0;
     if (builder != SBR_BVH_LBVH && builder != SBR_BVH_PLOC) return fail(c, SBR_ERR_ARG, "sbr_build_bvh: unknown builder");
     if (radius < 0 || radius > 64) return fail(c, SBR_ERR_ARG, "sbr_build_bvh: ploc_radius must be 0..64");
     CK(cudaSetDevice(c->device), "cudaSetDevice");
@@ -413,7 +413,7 @@ int sbr_build_bvh(sbr_ctx* c, const sbr_bvh_opts* opt)
     b.leaf_max = leaf_max;
     b.c_t = ct;
     b.c_i = ci;
-    b.builder = builder;
+    b.builder = builder == SBR_BVH_PLOC ? 1 : 0;
     b.radius = radius;
     b.nodes = c->nodes.as<float4>();
     b.tris = c->tris.as<float4>();

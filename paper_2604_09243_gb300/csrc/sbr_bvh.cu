@@ -414,9 +414,10 @@ __device__ __forceinline__ float union_area(float4 al, float4 ah, float4 bl, flo
                 make_float4(fmaxf(ah.x, bh.x), fmaxf(ah.y, bh.y), fmaxf(ah.z, bh.z), 0.f));
 }
 
-__global__ void __launch_bounds__(kThreads) k_ploc_nn(int m, int radius, Clusters c, int* nn)
+__global__ void __launch_bounds__(kThreads) k_ploc_nn(const int* m_dev, int radius, Clusters c, int* nn)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int m = *m_dev;
     if (i >= m) return;
     const float4 lo = c.lo[i], hi = c.hi[i];
     float best = FLT_MAX;
@@ -433,12 +434,19 @@ __global__ void __launch_bounds__(kThreads) k_ploc_nn(int m, int radius, Cluster
     nn[i] = bj;
 }
 
-__global__ void __launch_bounds__(kThreads) k_ploc_merge(int m, Clusters c, const int* nn, int* next_id, int* left,
-                                                         int* right, float4* nbox, int* ncnt, float* ncost, int* ncol,
-                                                         unsigned* keep, int leaf_max, float c_t, float c_i)
+// par / rel: parent and offset within the parent of node x (x < n - 1) or of
+// triangle t (x = n - 1 + t), for the pointer-jumping position pass
+__global__ void __launch_bounds__(kThreads) k_ploc_merge(const int* m_dev, int m_ub, int n, Clusters c, const int* nn,
+                                                         int* next_id, int* left, int* right, float4* nbox, int* ncnt,
+                                                         float* ncost, int* ncol, int* par, int* rel, unsigned* keep,
+                                                         int leaf_max, float c_t, float c_i)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
+    if (i >= m_ub) return;
+    if (i >= *m_dev) {
+        keep[i] = 0;  // beyond the live clusters of this round
+        return;
+    }
     const int j = nn[i];
     if (j < 0 || nn[j] != i) {
         keep[i] = 1;  // no mutual partner this round
@@ -457,8 +465,14 @@ __global__ void __launch_bounds__(kThreads) k_ploc_merge(int m, Clusters c, cons
     const float as_leaf = c_i * (float)cnt * sa;
     const int col = (cnt <= leaf_max) && (as_leaf <= split);
     const int id = atomicSub(next_id, 1);
-    left[id] = c.ref[i];
-    right[id] = c.ref[j];
+    const int ri = c.ref[i], rj = c.ref[j];
+    left[id] = ri;
+    right[id] = rj;
+    const int xi = ri >= 0 ? ri : n - 1 + ~ri, xj = rj >= 0 ? rj : n - 1 + ~rj;
+    par[xi] = id;
+    rel[xi] = 0;
+    par[xj] = id;
+    rel[xj] = c.cnt[i];
     nbox[2 * id] = lo;
     nbox[2 * id + 1] = hi;
     ncnt[id] = cnt;
@@ -472,11 +486,11 @@ __global__ void __launch_bounds__(kThreads) k_ploc_merge(int m, Clusters c, cons
     keep[i] = 1;
 }
 
-__global__ void __launch_bounds__(kThreads) k_ploc_compact(int m, Clusters in, const unsigned* keep,
+__global__ void __launch_bounds__(kThreads) k_ploc_compact(int m_ub, Clusters in, const unsigned* keep,
                                                            const unsigned* pos, Clusters out)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m || !keep[i]) return;
+    if (i >= m_ub || !keep[i]) return;
     const unsigned k = pos[i];
     out.lo[k] = in.lo[i];
     out.hi[k] = in.hi[i];
@@ -485,29 +499,29 @@ __global__ void __launch_bounds__(kThreads) k_ploc_compact(int m, Clusters in, c
     out.cost[k] = in.cost[i];
 }
 
-// one level of the top-down pass: node q of the frontier starts at noff[q];
-// its left subtree goes first; triangles get their positions (perm)
-__global__ void __launch_bounds__(kThreads) k_ploc_offsets(const int* qin, int nin, const int* left, const int* right,
-                                                           const int* ncnt, int* noff, unsigned* perm, int* qout,
-                                                           int* nout)
+// position pass by pointer jumping: after round r every entry holds the sum of
+// rel over its nearest 2^r ancestors and points 2^r levels up; once every
+// pointer has left the root, rel is the first position of the node's triangles
+__global__ void __launch_bounds__(kThreads) k_ploc_jump(int count, const int* par_in, const int* rel_in, int* par_out,
+                                                        int* rel_out)
 {
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= nin) return;
-    const int q = qin[w];
-    const int o = noff[q];
-    const int ch[2] = {left[q], right[q]};
-    int off = o;
-    for (int s = 0; s < 2; ++s) {
-        const int c = ch[s];
-        if (c < 0) {
-            perm[off] = (unsigned)(~c);
-            off += 1;
-        } else {
-            noff[c] = off;
-            qout[atomicAdd(nout, 1)] = c;
-            off += ncnt[c];
-        }
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= count) return;
+    const int p = par_in[x];
+    if (p < 0) {
+        par_out[x] = p;
+        rel_out[x] = rel_in[x];
+    } else {
+        par_out[x] = par_in[p];
+        rel_out[x] = rel_in[x] + rel_in[p];
     }
+}
+
+__global__ void __launch_bounds__(kThreads) k_ploc_positions(int n, const int* rel, int* noff, unsigned* perm)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x < n - 1) noff[x] = rel[x];
+    else if (x < 2 * n - 1) perm[rel[x]] = (unsigned)(x - (n - 1));
 }
 
 __global__ void __launch_bounds__(kThreads) k_ploc_emit(int n, const int* left, const int* right, const float4* nbox,
@@ -672,7 +686,7 @@ size_t bvh_scratch_bytes(long long n_tri)
     add(n * 4); add(n * 4); add(n * 4);     // nn keep pos
     add(scan_scratch_bytes((long long)n));
     add(n * 4); add(n * 4);                 // noff perm
-    add(n * 4); add(n * 4);                 // level queues
+    for (int k = 0; k < 4; ++k) add(2 * n * 4);  // parent links and offsets, two buffers each
     add(64);                                // counters
     return b + 256;
 }
@@ -719,8 +733,12 @@ cudaError_t bvh_build(const BvhBuild& b, cudaStream_t st)
     void* pscan = cv.take<char>(scan_scratch_bytes((long long)nn));
     int* noff = cv.take<int>(nn);
     unsigned* perm = cv.take<unsigned>(nn);
-    int* qa = cv.take<int>(nn);
-    int* qb = cv.take<int>(nn);
+    int* par[2];
+    int* rel[2];
+    for (int k = 0; k < 2; ++k) {
+        par[k] = cv.take<int>(2 * (size_t)nn);
+        rel[k] = cv.take<int>(2 * (size_t)nn);
+    }
     int* ctr = cv.take<int>(16);
     if (cv.off > cv.cap) return cudaErrorInvalidValue;
 
@@ -743,48 +761,43 @@ cudaError_t bvh_build(const BvhBuild& b, cudaStream_t st)
     }
     // after an even number of passes the sorted data is back in (k0, v0)
     if (b.builder == 1 && n > 1) {
-        // PLOC over the Morton order (synchronises once per round and per level)
+        // PLOC over the Morton order; the live-cluster count stays on the device and the host reads it every
+        // kRoundsPerSync rounds (extra rounds after the last merge change nothing)
+        constexpr int kRoundsPerSync = 4;
         const float c_t = b.c_t, c_i = b.c_i;
         const int radius = b.radius > 0 ? b.radius : 16;
+        const int nx = 2 * n - 1;
         k_ploc_init<<<g, kThreads, 0, st>>>(vi, tbox, n, c_i, cl[0]);
-        int h[2] = {n - 2, 0};
+        int h[2] = {n - 2, n};  // next node id, live clusters
         cudaError_t e = cudaMemcpyAsync(ctr, h, sizeof(h), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(par[0], 0xFF, sizeof(int) * (size_t)nx, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(rel[0], 0, sizeof(int) * (size_t)nx, st);
         int m = n, cur = 0;
-        for (int round = 0; e == cudaSuccess && m > 1; ++round) {
+        for (int round = 0; e == cudaSuccess && m > 1; round += kRoundsPerSync) {
             if (round >= 1 << 16) return cudaErrorInvalidValue;  // every round merges at least one pair
             const int gm = (m + kThreads - 1) / kThreads;
-            k_ploc_nn<<<gm, kThreads, 0, st>>>(m, radius, cl[cur], pnn);
-            k_ploc_merge<<<gm, kThreads, 0, st>>>(m, cl[cur], pnn, ctr, left, right, nbox, ncnt, ncost, ncol, keep,
-                                                  b.leaf_max, c_t, c_i);
-            e = scan_exclusive_u32(keep, pos, m, false, (unsigned*)(ctr + 1), pscan, st);
-            if (e != cudaSuccess) break;
-            k_ploc_compact<<<gm, kThreads, 0, st>>>(m, cl[cur], keep, pos, cl[cur ^ 1]);
-            e = cudaGetLastError();
+            for (int r = 0; r < kRoundsPerSync && e == cudaSuccess; ++r) {
+                k_ploc_nn<<<gm, kThreads, 0, st>>>(ctr + 1, radius, cl[cur], pnn);
+                k_ploc_merge<<<gm, kThreads, 0, st>>>(ctr + 1, m, n, cl[cur], pnn, ctr, left, right, nbox, ncnt, ncost,
+                                                      ncol, par[0], rel[0], keep, b.leaf_max, c_t, c_i);
+                e = scan_exclusive_u32(keep, pos, m, false, (unsigned*)(ctr + 1), pscan, st);
+                if (e != cudaSuccess) break;
+                k_ploc_compact<<<gm, kThreads, 0, st>>>(m, cl[cur], keep, pos, cl[cur ^ 1]);
+                e = cudaGetLastError();
+                cur ^= 1;
+            }
             if (e == cudaSuccess) e = cudaMemcpyAsync(&m, ctr + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            cur ^= 1;
         }
         if (e != cudaSuccess) return e;
-        // positions: top-down, one level at a time from the root (node 0)
-        const int zero = 0;
-        e = cudaMemcpyAsync(noff, &zero, sizeof(int), cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(qa, &zero, sizeof(int), cudaMemcpyHostToDevice, st);
-        int nin = 1;
-        int *qi = qa, *qo = qb;
-        for (int level = 0; e == cudaSuccess && nin > 0; ++level) {
-            if (level > n) return cudaErrorInvalidValue;
-            e = cudaMemsetAsync(ctr + 2, 0, sizeof(int), st);
-            if (e != cudaSuccess) break;
-            k_ploc_offsets<<<(nin + kThreads - 1) / kThreads, kThreads, 0, st>>>(qi, nin, left, right, ncnt, noff,
-                                                                                perm, qo, ctr + 2);
-            e = cudaGetLastError();
-            if (e == cudaSuccess) e = cudaMemcpyAsync(&nin, ctr + 2, sizeof(int), cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            int* t = qi;
-            qi = qo;
-            qo = t;
-        }
-        if (e != cudaSuccess) return e;
+        // first positions: pointer jumping over parent links (depth <= n - 1 < 2^rounds)
+        int jr = 1;
+        while ((1ll << jr) < (long long)n) ++jr;
+        const int gx = (nx + kThreads - 1) / kThreads;
+        int pj = 0;
+        for (int r = 0; r <= jr; ++r, pj ^= 1)
+            k_ploc_jump<<<gx, kThreads, 0, st>>>(nx, par[pj], rel[pj], par[pj ^ 1], rel[pj ^ 1]);
+        k_ploc_positions<<<gx, kThreads, 0, st>>>(n, rel[pj], noff, perm);
         k_ploc_emit<<<(n - 1 + kThreads - 1) / kThreads, kThreads, 0, st>>>(n, left, right, nbox, ncnt, ncol, noff,
                                                                             tbox, b.nodes);
         k_reorder<<<g, kThreads, 0, st>>>(b.xyz, b.tri, b.n_vert, perm, n, b.tris);

@@ -265,9 +265,9 @@ class Context:
         self.n_tri = len(tri)
 
     def build_bvh(self, leaf_max: int = 4, cost_traverse: float = 1.0, cost_intersect: float = 1.0,
-                  builder: str = "lbvh", ploc_radius: int = 0):
-        """sbr_build_bvh; builder "lbvh" (Karras) or "ploc" (nearest-neighbour clustering)."""
-        o = BvhOpts(int(leaf_max), float(cost_traverse), float(cost_intersect), {"lbvh": 0, "ploc": 1}[builder],
+                  builder: str = "ploc", ploc_radius: int = 0):
+        """sbr_build_bvh; builder "ploc" (nearest-neighbour clustering, default) or "lbvh" (Karras)."""
+        o = BvhOpts(int(leaf_max), float(cost_traverse), float(cost_intersect), {"ploc": 0, "lbvh": 1}[builder],
                     int(ploc_radius))
         self._check(lib().sbr_build_bvh(self._h, C.byref(o)))
 

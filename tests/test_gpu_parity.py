@@ -188,7 +188,7 @@ def test_all_rays_miss_gives_empty_sum(G, ctx):
 def test_leaf_sizes_same_hits(G, ctx, orc, leaf):
     xyz, tri = S.icosphere(4)
     ctx.load_mesh(xyz, tri)
-    ctx.build_bvh(leaf_max=leaf)
+    ctx.build_bvh(leaf_max=leaf, builder="lbvh")
     om = orc.Mesh(xyz, tri)
     st, res = _trace_both(G, ctx, orc, om, np.array([[12.0, 34.0]]), 0.01, 1, window=2.2)
     assert_hit_parity(compare_hits(*res[0][0], res[0][1]))
@@ -203,7 +203,7 @@ def test_ploc_tree_same_hits(G, ctx, orc, leaf, radius):
                                       (*S.trihedral(1.0, 32), [[30.0, 35.26], [72.5, 35.26]], 0.006, 3, 0.0)):
         ctx.load_mesh(xyz, tri)
         om = orc.Mesh(xyz, tri)
-        ctx.build_bvh(leaf_max=leaf)
+        ctx.build_bvh(leaf_max=leaf, builder="lbvh")
         lb = ctx.trace(ang, sp, max_bounces=B, window=win, flags=G.TRACE_COUNT_VISITS)
         ctx.build_bvh(leaf_max=leaf, builder="ploc", ploc_radius=radius)
         st, res = _trace_both(G, ctx, orc, om, np.array(ang), sp, B, window=win)
@@ -222,6 +222,7 @@ def test_ploc_tree_aircraft(G, ctx, orc):
     ctx.load_mesh(case["xyz"], case["tri"])
     ang = case["angles"][[0, 120]]
     kw = dict(eta=case["eta"], max_bounces=case["max_bounces"], offset=case["offset"])
+    ctx.build_bvh(builder="lbvh")
     ctx.trace(ang, case["spacing"], flags=G.TRACE_RECORD_HITS, **kw)
     ref = [ctx.get_hits(a) for a in range(len(ang))]
     ctx.build_bvh(builder="ploc")
