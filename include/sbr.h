@@ -188,6 +188,23 @@ int sbr_ray_grid_box(const float* bbox6, double az_deg, double el_deg, double ra
 int sbr_trace(sbr_ctx* ctx, const double* az_el_deg, int64_t n_angles, double ray_spacing_m, double margin_eta,
               int max_bounces, const sbr_trace_opts* opt, sbr_trace_stats* stats);
 
+/* Bistatic variant of sbr_trace (the paper notes that monostatic SBR needs no
+ * visibility function, Sec. 3 footnote; a bistatic one does): aspect a is lit
+ * from az_el_tx[a] (the ray grid, as in sbr_trace) and observed from the
+ * receiver direction az_el_rx[a] (host double [n][2], degrees, same axis
+ * convention). The PO terms of the records radiate toward the receiver and are
+ * projected on its H, V basis (pq = receive p, transmit q), the path becomes
+ * L = k.o0 + sum t - r_rx.x_last, and a ray's last hit counts only if it sees
+ * the receiver: the receiver lies on the side of the hit's oriented normal and
+ * a query from the offset hit point toward the receiver meets no triangle
+ * (its records are zero otherwise). Each visibility query counts as a
+ * ray-bounce. sbr_po_integrate then gives the bistatic field (vector form; the
+ * paper scalar form stays monostatic). With az_el_rx = az_el_tx the fields
+ * equal the monostatic ones for rays whose last hit sees the radar. */
+int sbr_trace_bistatic(sbr_ctx* ctx, const double* az_el_tx, const double* az_el_rx, int64_t n_angles,
+                       double ray_spacing_m, double margin_eta, int max_bounces, const sbr_trace_opts* opt,
+                       sbr_trace_stats* stats);
+
 /* Physical-optics ray-tube sum over the valid hits of the last sbr_trace, for
  * every traced aspect and every frequency of freq_hz (host, n_freq values):
  *   E_pq = (-j k / 4 pi) sum_i c_pq,i e^{-j k L_i},  k = 2 pi f / c0,

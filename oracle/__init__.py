@@ -41,7 +41,9 @@ class Frame(C.Structure):
                 ("Lu", C.c_double), ("Lv", C.c_double),
                 ("spacing", C.c_double), ("dA", C.c_double), ("eps", C.c_double),
                 ("nu", C.c_int64), ("nv", C.c_int64),
-                ("P0", C.c_float * 3), ("U", C.c_float * 3), ("V", C.c_float * 3), ("d", C.c_float * 3)]
+                ("P0", C.c_float * 3), ("U", C.c_float * 3), ("V", C.c_float * 3), ("d", C.c_float * 3),
+                ("bistatic", C.c_int), ("rx_rhat", C.c_double * 3), ("rx_hhat", C.c_double * 3),
+                ("rx_vhat", C.c_double * 3), ("rx_r32", C.c_float * 3)]
 
     @property
     def n_rays(self) -> int:
@@ -66,6 +68,8 @@ def lib():
                                      C.c_double, C.c_double, C.c_double, P(Frame)]
         L.orc_make_frame.restype = C.c_int
         L.orc_ray.argtypes = [P(Frame), C.c_int64, C.c_int64, P(C.c_float), P(C.c_float)]
+        L.orc_frame_set_receiver.argtypes = [P(Frame), C.c_double, C.c_double]
+        L.orc_frame_set_receiver.restype = C.c_int
         L.orc_ray.restype = None
         L.orc_mesh_create.argtypes = [P(C.c_float), C.c_int64, P(C.c_int32), C.c_int64]
         L.orc_mesh_create.restype = C.c_void_p
@@ -103,14 +107,17 @@ def default_threads() -> int:
     return max(1, os.cpu_count() or 1)
 
 
-def make_frame(bbox, az_deg, el_deg, spacing, eta=0.05, window=0.0, offset=(0.0, 0.0)) -> Frame:
-    """Aperture frame and ray grid of one aspect (Eq. L1-L3)."""
+def make_frame(bbox, az_deg, el_deg, spacing, eta=0.05, window=0.0, offset=(0.0, 0.0), rx=None) -> Frame:
+    """Aperture frame and ray grid of one aspect (Eq. L1-L3). ``rx`` = (az, el) of a
+    bistatic receiver (None: monostatic)."""
     b = np.ascontiguousarray(bbox, dtype=np.float32)
     f = Frame()
     rc = lib().orc_make_frame(_ptr(b, C.c_float), float(az_deg), float(el_deg), float(spacing), float(eta),
                               float(window), float(offset[0]), float(offset[1]), C.byref(f))
     if rc != 0:
         raise ValueError("orc_make_frame failed")
+    if rx is not None:
+        lib().orc_frame_set_receiver(C.byref(f), float(rx[0]), float(rx[1]))
     return f
 
 
@@ -241,9 +248,10 @@ def mie_pec_backscatter(x: float) -> float:
 
 def rcs_angle(mesh: Mesh, bbox, az, el, spacing, freqs, max_bounces, eta=0.05, window=0.0, offset=(0.0, 0.0),
               po_mode="vector", phase_literal=False, require_escape=False, threads=None, ids=None,
-              transport="fp32"):
-    """Convenience: one aspect, trace + PO. Returns (E [nf,4], rcs_dbsm [nf,4], trace dict, frame)."""
-    fr = make_frame(bbox, az, el, spacing, eta=eta, window=window, offset=offset)
+              transport="fp32", rx=None):
+    """Convenience: one aspect, trace + PO. Returns (E [nf,4], rcs_dbsm [nf,4], trace dict, frame).
+    ``rx`` = (az, el) of a bistatic receiver (None: monostatic)."""
+    fr = make_frame(bbox, az, el, spacing, eta=eta, window=window, offset=offset, rx=rx)
     tr = trace(mesh, fr, max_bounces, po_mode=po_mode, phase_literal=phase_literal,
                require_escape=require_escape, ids=ids, threads=threads, transport=transport)
     E, rcs = po(tr["coef"], tr["L"], tr["valid"], freqs)

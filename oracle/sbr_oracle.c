@@ -84,6 +84,11 @@ typedef struct {
     double spacing, dA, eps;
     int64_t nu, nv;
     float P0[3], U[3], V[3], d[3];
+    /* receiver (bistatic): direction to the receiver and its H, V basis; equal to
+     * the transmitter's unless orc_frame_set_receiver was called */
+    int bistatic;
+    double rx_rhat[3], rx_hhat[3], rx_vhat[3];
+    float rx_r32[3];
 } orc_frame;
 
 int orc_make_frame(const float* bbox, double az_deg, double el_deg, double spacing, double eta,
@@ -143,6 +148,29 @@ int orc_make_frame(const float* bbox, double az_deg, double el_deg, double spaci
         f->V[c] = (float)(spacing * f->vhat[c]);
         f->d[c] = (float)f->khat[c];
     }
+    for (int c = 0; c < 3; ++c) {
+        f->rx_rhat[c] = f->rhat[c];
+        f->rx_hhat[c] = f->hhat[c];
+        f->rx_vhat[c] = f->vhat[c];
+        f->rx_r32[c] = (float)f->rhat[c];
+    }
+    f->bistatic = 0;
+    return 0;
+}
+
+/* Bistatic receiver at (az, el): same axis convention as the transmitter. The
+ * PO terms radiate toward it and are projected on its H, V basis; the last hit
+ * of a ray contributes only if it sees the receiver (visibility test). */
+int orc_frame_set_receiver(orc_frame* f, double az_deg, double el_deg)
+{
+    if (!f) return -1;
+    double a = az_deg * (ORC_PI / 180.0), e = el_deg * (ORC_PI / 180.0);
+    double ca = cos(a), sa = sin(a), ce = cos(e), se = sin(e);
+    f->rx_rhat[0] = ce * ca; f->rx_rhat[1] = ce * sa; f->rx_rhat[2] = se;
+    f->rx_vhat[0] = se * ca; f->rx_vhat[1] = se * sa; f->rx_vhat[2] = -ce;
+    f->rx_hhat[0] = -sa; f->rx_hhat[1] = ca; f->rx_hhat[2] = 0.0;
+    for (int c = 0; c < 3; ++c) f->rx_r32[c] = (float)f->rx_rhat[c];
+    f->bistatic = 1;
     return 0;
 }
 
@@ -550,6 +578,7 @@ static void trace_one(trace_job* J, int64_t r)
     double ref = dot3(f->khat, o); /* k.o0 */
     double R = 0.0, L = 0.0, cos0 = 0.0;
     double cv[4] = {0, 0, 0, 0};
+    double nf_last[3] = {0, 0, 0};
     int N = 0;
     uint8_t band = 0;
     double bmin_path = 1.0;
@@ -611,8 +640,10 @@ static void trace_one(trace_job* J, int64_t r)
         double nf[3];
         for (int c = 0; c < 3; ++c) nf[c] = front ? n[c] : -n[c];
         if (N == 1) cos0 = dot3(nf, f->rhat);
-        /* candidate contribution if this hit is the last one */
-        L = ref + R + dot3(f->khat, x);
+        for (int c = 0; c < 3; ++c) nf_last[c] = nf[c];
+        /* candidate contribution if this hit is the last one; the far-field
+         * phase reference is the origin, toward the receiver: L = k.o0 + R - r_rx.x */
+        L = ref + R - dot3(f->rx_rhat, x);
         {
             double adn = fabs(dn);
             double dS = adn > 0.0 ? f->dA / adn : 0.0;
@@ -623,13 +654,13 @@ static void trace_one(trace_job* J, int64_t r)
                 cross3(din, Eq[q], Hf);
                 cross3(nf, Hf, Jc);
                 for (int c = 0; c < 3; ++c) Jc[c] *= 2.0;
-                double jr = dot3(Jc, f->rhat);
-                for (int c = 0; c < 3; ++c) W[q][c] = dS * (Jc[c] - jr * f->rhat[c]);
+                double jr = dot3(Jc, f->rx_rhat);
+                for (int c = 0; c < 3; ++c) W[q][c] = dS * (Jc[c] - jr * f->rx_rhat[c]);
             }
-            cv[0] = dot3(W[0], f->hhat); /* HH: receive H, transmit H */
-            cv[1] = dot3(W[1], f->vhat); /* VV */
-            cv[2] = dot3(W[1], f->hhat); /* HV: receive H, transmit V */
-            cv[3] = dot3(W[0], f->vhat); /* VH: receive V, transmit H */
+            cv[0] = dot3(W[0], f->rx_hhat); /* HH: receive H, transmit H */
+            cv[1] = dot3(W[1], f->rx_vhat); /* VV */
+            cv[2] = dot3(W[1], f->rx_hhat); /* HV: receive H, transmit V */
+            cv[3] = dot3(W[0], f->rx_vhat); /* VH: receive V, transmit H */
         }
         if (fp32) {
             double dd[3] = {din[0], din[1], din[2]};
@@ -647,6 +678,31 @@ static void trace_one(trace_job* J, int64_t r)
         J->tests += h.tests;
         J->nodes += h.nodes;
         if (h.k >= 0) valid = 0;
+    }
+    if (valid && f->bistatic) {
+        /* visibility of the last hit from the receiver: the receiver lies on the
+         * side of the oriented normal, and a ray from the offset origin toward it
+         * meets no triangle (the one just hit is skipped). FP32 transport: the
+         * side test is the written FP32 dot and the ray is the FP32 one. */
+        int sees;
+        double rxd[3] = {f->rx_r32[0], f->rx_r32[1], f->rx_r32[2]};
+        if (fp32) {
+            float nf32[3] = {(float)nf_last[0], (float)nf_last[1], (float)nf_last[2]};
+            float rx32[3] = {f->rx_r32[0], f->rx_r32[1], f->rx_r32[2]};
+            sees = dot32(nf32, rx32) > 0.0f;
+        } else {
+            sees = dot3(nf_last, f->rx_rhat) > 0.0;
+            for (int c = 0; c < 3; ++c) rxd[c] = f->rx_rhat[c];
+        }
+        if (sees) {
+            orc_hit h;
+            float rx32[3] = {f->rx_r32[0], f->rx_r32[1], f->rx_r32[2]};
+            closest(J->m, opt->use_bvh, o, rxd, o32, rx32, fp32, skip, &h);
+            J->tests += h.tests;
+            J->nodes += h.nodes;
+            sees = h.k < 0;
+        }
+        if (!sees) valid = 0;
     }
     if (opt->po_mode == 1) {
         double s = (N & 1) ? -1.0 : 1.0; /* Gamma^N, Gamma = -1 */

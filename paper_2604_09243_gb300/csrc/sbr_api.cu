@@ -62,6 +62,8 @@ struct DevBuf {
 struct AngleHost {
     sbr_ray_grid grid;
     int tw;               // ray tile width log2 used for this trace
+    bool bistatic = false;
+    double rx_az = 0.0, rx_el = 0.0;  // receiver of a bistatic aspect (degrees)
     long long ray_begin;  // first ray (padded layout) over the whole trace
     long long rec_begin, rec_count;
 };
@@ -216,7 +218,8 @@ void make_grid(const float* bbox, double az_deg, double el_deg, double ds, doubl
     }
 }
 
-AngleDev to_dev(const sbr_ray_grid& g, long long ray_off, int tw)
+// rx: (az, el) of a bistatic receiver in degrees, or null (receiver = transmitter)
+AngleDev to_dev(const sbr_ray_grid& g, long long ray_off, int tw, const double* rx = nullptr)
 {
     AngleDev d;
     memset(&d, 0, sizeof(d));
@@ -235,6 +238,27 @@ AngleDev to_dev(const sbr_ray_grid& g, long long ray_off, int tw)
     d.nv = (int)g.nv;
     d.nbu = (int)((g.nu + (1 << tw) - 1) >> tw);
     d.tw_log2 = tw;
+    if (rx) {
+        // same axis convention as the transmitter (make_grid)
+        const double a = rx[0] * (kPi / 180.0), e = rx[1] * (kPi / 180.0);
+        const double ca = cos(a), sa = sin(a), ce = cos(e), se = sin(e);
+        const double rr[3] = {ce * ca, ce * sa, se}, vv[3] = {se * ca, se * sa, -ce}, hh[3] = {-sa, ca, 0.0};
+        for (int k = 0; k < 3; ++k) {
+            d.rxr[k] = (float)rr[k];
+            d.rxv[k] = (float)vv[k];
+            d.rxh[k] = (float)hh[k];
+            d.rxdir[k] = (float)(-rr[k]);
+        }
+        d.bistatic = 1;
+    } else {
+        for (int k = 0; k < 3; ++k) {
+            d.rxr[k] = d.rhat[k];
+            d.rxv[k] = d.vhat[k];
+            d.rxh[k] = d.hhat[k];
+            d.rxdir[k] = d.dir[k];
+        }
+        d.bistatic = 0;
+    }
     d.ray_off = ray_off;
     return d;
 }
@@ -588,7 +612,8 @@ int trace_chunk(sbr_ctx* c, TraceRun& R, int64_t a0, int64_t a1, long long rec_b
     for (int i = 0; i < na; ++i) {
         const AngleHost& h = c->ang[(size_t)(a0 + i)];
         ho[i] = h.ray_begin - base;
-        ha[i] = to_dev(h.grid, ho[i], h.tw);
+        double rx[2] = {h.rx_az, h.rx_el};
+        ha[i] = to_dev(h.grid, ho[i], h.tw, h.bistatic ? rx : nullptr);
     }
     ho[na] = chunk_rays;
     CK(cudaMemcpyAsync(c->angles.p, ha, bytes_a, cudaMemcpyHostToDevice, c->stream), "copy angles");
@@ -599,6 +624,7 @@ int trace_chunk(sbr_ctx* c, TraceRun& R, int64_t a0, int64_t a1, long long rec_b
     memset(&ta, 0, sizeof(ta));
     ta.wide = c->tune.bvh_width == 4;
     ta.packet = c->tune.packet;
+    for (int i = 0; i < na; ++i) ta.bistatic |= c->ang[(size_t)(a0 + i)].bistatic ? 1 : 0;
     ta.nodes = ta.wide ? c->nodes4.as<float4>() : c->nodes.as<float4>();
     ta.tris = c->tris.as<float4>();
     ta.angles = c->angles.as<AngleDev>();
@@ -1074,12 +1100,9 @@ int build_plan(sbr_ctx* c, BatchPlan& P)
     return SBR_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-int sbr_trace(sbr_ctx* c, const double* az_el, int64_t n_angles, double ds, double eta, int max_bounces,
-              const sbr_trace_opts* opt, sbr_trace_stats* stats)
+// sbr_trace and sbr_trace_bistatic (az_el_rx: [n][2] receivers, or null for monostatic)
+int trace_impl(sbr_ctx* c, const double* az_el, const double* az_el_rx, int64_t n_angles, double ds, double eta,
+               int max_bounces, const sbr_trace_opts* opt, sbr_trace_stats* stats)
 {
     if (!c) return SBR_ERR_ARG;
     if (!c->has_bvh) return fail(c, SBR_ERR_STATE, "sbr_trace: no BVH (load a mesh first)");
@@ -1100,8 +1123,12 @@ int sbr_trace(sbr_ctx* c, const double* az_el, int64_t n_angles, double ds, doub
     c->has_trace = false;
     c->ang.resize((size_t)n_angles);
     for (int64_t a = 0; a < n_angles; ++a) {
-        make_grid(c->bbox, az_el[2 * a], az_el[2 * a + 1], ds, eta, opt, &c->ang[(size_t)a].grid);
-        c->ang[(size_t)a].tw = log2i(c->tune.tile_w);
+        AngleHost& h = c->ang[(size_t)a];
+        make_grid(c->bbox, az_el[2 * a], az_el[2 * a + 1], ds, eta, opt, &h.grid);
+        h.tw = log2i(c->tune.tile_w);
+        h.bistatic = az_el_rx != nullptr;
+        h.rx_az = az_el_rx ? az_el_rx[2 * a] : 0.0;
+        h.rx_el = az_el_rx ? az_el_rx[2 * a + 1] : 0.0;
     }
     std::vector<int64_t> cut;
     long long total = 0, launched = 0;
@@ -1119,6 +1146,23 @@ int sbr_trace(sbr_ctx* c, const double* az_el, int64_t n_angles, double ds, doub
     c->trace_flags = R.flags;
     c->has_trace = rc == SBR_OK;
     return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sbr_trace(sbr_ctx* c, const double* az_el, int64_t n_angles, double ds, double eta, int max_bounces,
+              const sbr_trace_opts* opt, sbr_trace_stats* stats)
+{
+    return trace_impl(c, az_el, nullptr, n_angles, ds, eta, max_bounces, opt, stats);
+}
+
+int sbr_trace_bistatic(sbr_ctx* c, const double* az_el_tx, const double* az_el_rx, int64_t n_angles, double ds,
+                       double eta, int max_bounces, const sbr_trace_opts* opt, sbr_trace_stats* stats)
+{
+    if (c && !az_el_rx) return fail(c, SBR_ERR_ARG, "sbr_trace_bistatic: no receiver angles");
+    return trace_impl(c, az_el_tx, az_el_rx, n_angles, ds, eta, max_bounces, opt, stats);
 }
 
 int sbr_po_integrate(sbr_ctx* c, const double* freq_hz, int64_t n_freq, int pol_mask, int po_mode, double* E_out,
@@ -1202,6 +1246,7 @@ int sbr_run_batch(sbr_ctx* c, const sbr_request* req, int64_t n_req, const doubl
     for (int64_t r = 0; r < n_req; ++r) {
         make_grid(c->bbox, req[r].az_deg, req[r].el_deg, req[r].ray_spacing_m, eta, opt, &c->ang[(size_t)r].grid);
         c->ang[(size_t)r].tw = log2i(c->tune.tile_w);
+        c->ang[(size_t)r].bistatic = false;
     }
     std::vector<int64_t> cut;
     long long total = 0, launched = 0;

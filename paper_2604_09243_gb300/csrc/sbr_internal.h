@@ -33,7 +33,7 @@ __host__ __device__ inline int leaf_count(int ref) { return (int)((unsigned)ref 
 // (e2, 0) with e1 = v1 - v0, e2 = v2 - v0 rounded to FP32.
 
 // ---------------------------------------------------------------- per-aspect data
-struct AngleDev {            // 128 bytes
+struct AngleDev {            // 192 bytes
     float p0[3], du[3], dv[3], dir[3];  // FP32 ray grid: o(i, j) = (p0 + i du) + j dv
     float rhat[3], vhat[3], hhat[3];    // radar direction, V (theta_hat), H (phi_hat)
     float dA, eps;                      // tube area ds^2, origin offset after a hit
@@ -41,9 +41,13 @@ struct AngleDev {            // 128 bytes
     long long ray_off;                  // first ray of this aspect in the chunk, multiple of 32
     int nbu;                            // ray tiles per aperture row: ceil(nu / tile width)
     int tw_log2;                        // tile width 2^tw_log2 (height 32 / width): one warp per tile
-    int pad[2];
+    int bistatic;                       // 1: receiver below differs from the transmitter (visibility test)
+    int pad;
+    float rxr[3], rxv[3], rxh[3];       // receiver direction and its V, H basis (= rhat, vhat, hhat monostatic)
+    float rxdir[3];                     // -rxr in FP32 (= dir monostatic): the path term of the receiver
+    float pad2[4];
 };
-static_assert(sizeof(AngleDev) == 128, "AngleDev layout");
+static_assert(sizeof(AngleDev) == 192, "AngleDev layout");
 
 // live ray between bounces (96 bytes, three 32-byte sectors)
 struct __align__(16) RayState {
@@ -51,7 +55,8 @@ struct __align__(16) RayState {
     float dy, dz, evx, evy;
     float evz, lacc_hi, lacc_lo, cos0;  // E of the V transmit case; path so far (two-float)
     float c0, c1, c2, c3;               // candidate tube coefficients HH, VV, HV, VH at the last hit
-    float cs, lc_hi, lc_lo, pad;        // candidate scalar coefficient, candidate path L (two-float)
+    float cs, lc_hi, lc_lo, nfs;        // candidate scalar coefficient, candidate path L (two-float), side of the
+                                        // last hit's normal facing the incoming ray (+1 / -1)
     int angle, local, last, nb;         // aspect (chunk-local), processing index (8x4 tiles), last sorted triangle, bounces
 };
 static_assert(sizeof(RayState) == 96, "RayState layout");
@@ -109,6 +114,7 @@ struct TraceArgs {
     const float4* nodes;          // binary nodes, or 4-wide nodes when wide = 1
     int wide;
     int packet;                   // 1: warp-cooperative traversal of the binary tree
+    int bistatic;                 // 1: some aspect of the chunk has a bistatic receiver (visibility tests)
     const float4* tris;
     const AngleDev* angles;
     const long long* ray_off;     // [n_angles + 1] chunk-relative, multiples of 32

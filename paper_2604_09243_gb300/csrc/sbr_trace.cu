@@ -403,7 +403,7 @@ struct Ray {
     float3 o, d, ev;
     float lacc_hi, lacc_lo, cos0;
     float c[5];
-    float lc_hi, lc_lo;
+    float lc_hi, lc_lo, nfs;
     int angle, local, last, nb;
 };
 
@@ -422,6 +422,7 @@ __device__ __forceinline__ void load_state(const RayState* __restrict__ q, unsig
     r.c[4] = f.x;
     r.lc_hi = f.y;
     r.lc_lo = f.z;
+    r.nfs = f.w;
     r.angle = g.x; r.local = g.y; r.last = g.z; r.nb = g.w;
 }
 
@@ -432,7 +433,7 @@ __device__ __forceinline__ void store_state(RayState* __restrict__ q, unsigned i
     p[1] = make_float4(r.d.y, r.d.z, r.ev.x, r.ev.y);
     p[2] = make_float4(r.ev.z, r.lacc_hi, r.lacc_lo, r.cos0);
     p[3] = make_float4(r.c[0], r.c[1], r.c[2], r.c[3]);
-    p[4] = make_float4(r.c[4], r.lc_hi, r.lc_lo, 0.f);
+    p[4] = make_float4(r.c[4], r.lc_hi, r.lc_lo, r.nfs);
     reinterpret_cast<int4*>(p)[5] = make_int4(r.angle, r.local, r.last, r.nb);
 }
 
@@ -457,12 +458,13 @@ __device__ __forceinline__ void apply_hit(const AngleDev& A, const float4* __res
     n = make_float3(__fmul_rn(n.x, rl), __fmul_rn(n.y, rl), __fmul_rn(n.z, rl));
     const float dn = dot_s(r.d, n);
     const float3 nf = dn < 0.f ? n : make_float3(-n.x, -n.y, -n.z);
+    r.nfs = dn < 0.f ? 1.f : -1.f;
     const float adn = fabsf(dn);
     const float3 rh = make_float3(A.rhat[0], A.rhat[1], A.rhat[2]);
     if (r.nb == 1) r.cos0 = dot3(nf, rh);
-    // candidate path L = k.o0 + sum t + k.x
+    // candidate path L = k.o0 + sum t - r_rx.x (monostatic: r_rx = -k)
     float kh, kl;
-    tf_dot(A.dir, x, kh, kl);
+    tf_dot(A.rxdir, x, kh, kl);
     r.lc_hi = r.lacc_hi;
     r.lc_lo = r.lacc_lo;
     tf_add_tf(r.lc_hi, r.lc_lo, kh, kl);
@@ -472,8 +474,10 @@ __device__ __forceinline__ void apply_hit(const AngleDev& A, const float4* __res
                                   sH * (r.d.x * r.ev.y - r.d.y * r.ev.x));
     const float dS = adn > 0.f ? __fdiv_rn(A.dA, adn) : 0.f;
     const float nfd = dot3(nf, r.d);
-    const float3 vh = make_float3(A.vhat[0], A.vhat[1], A.vhat[2]);
-    const float3 hh = make_float3(A.hhat[0], A.hhat[1], A.hhat[2]);
+    // radiation toward the receiver, projected on its basis
+    const float3 rr = make_float3(A.rxr[0], A.rxr[1], A.rxr[2]);
+    const float3 vh = make_float3(A.rxv[0], A.rxv[1], A.rxv[2]);
+    const float3 hh = make_float3(A.rxh[0], A.rxh[1], A.rxh[2]);
     float3 W[2];
     const float3 Eq[2] = {eh, r.ev};
 #pragma unroll
@@ -482,8 +486,8 @@ __device__ __forceinline__ void apply_hit(const AngleDev& A, const float4* __res
         // J = 2 nf x (d x E) = 2 (d (nf.E) - E (nf.d))
         const float3 J = make_float3(2.f * (r.d.x * ne - Eq[q].x * nfd), 2.f * (r.d.y * ne - Eq[q].y * nfd),
                                      2.f * (r.d.z * ne - Eq[q].z * nfd));
-        const float jr = dot3(J, rh);
-        W[q] = make_float3(dS * (J.x - jr * rh.x), dS * (J.y - jr * rh.y), dS * (J.z - jr * rh.z));
+        const float jr = dot3(J, rr);
+        W[q] = make_float3(dS * (J.x - jr * rr.x), dS * (J.y - jr * rr.y), dS * (J.z - jr * rr.z));
     }
     r.c[0] = dot3(W[0], hh);  // HH
     r.c[1] = dot3(W[1], vh);  // VV
@@ -521,6 +525,27 @@ __device__ __forceinline__ void tile_ij(const AngleDev& A, int p, int& i, int& j
     const int bv = blk / A.nbu, bu = blk - bv * A.nbu;
     i = (bu << tw) + (l & ((1 << tw) - 1));
     j = bv * (32 >> tw) + (l >> tw);
+}
+
+// Bistatic: the last hit contributes only if the receiver lies on the side of
+// its oriented normal (written FP32 dot) and a query from the offset origin
+// toward the receiver meets no triangle (the one just hit is skipped); the
+// same decision order as the transport, so the oracle takes it identically.
+__device__ __forceinline__ bool rx_visible(const TraceArgs& a, const AngleDev& A, const Ray& r, unsigned& nq,
+                                           bool& ovf)
+{
+    const float4 B = __ldg(a.tris + 3 * (size_t)r.last + 1), C = __ldg(a.tris + 3 * (size_t)r.last + 2);
+    float3 n = cross_s(make_float3(B.x, B.y, B.z), make_float3(C.x, C.y, C.z));
+    const float rl = __fdiv_rn(1.f, __fsqrt_rn(dot_s(n, n)));
+    n = make_float3(__fmul_rn(n.x, rl) * r.nfs, __fmul_rn(n.y, rl) * r.nfs, __fmul_rn(n.z, rl) * r.nfs);
+    const float3 rx = make_float3(A.rxr[0], A.rxr[1], A.rxr[2]);
+    if (!(dot_s(n, rx) > 0.f)) return false;
+    Hit h;
+    unsigned nv = 0, nt = 0;
+    if (a.wide) closest_hit4<false, 64>(a.nodes, a.tris, r.o, rx, r.last, a.visit_limit, h, nv, nt, ovf);
+    else closest_hit<false, 64>(a.nodes, a.tris, r.o, rx, r.last, a.visit_limit, h, nv, nt, ovf);
+    ++nq;
+    return h.k < 0;
 }
 
 __device__ __forceinline__ void emit(const TraceArgs& a, const Ray& r, bool zero)
@@ -732,7 +757,7 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_primary(const TraceArgs a)
 }
 
 // ---------------------------------------------------------------- pass b >= 1: live rays
-template <bool kCount, int kStack, int kMode>
+template <bool kCount, int kStack, int kMode, bool kBi = false>
 __global__ void __launch_bounds__(kTraceThreads, 4) k_bounce(const TraceArgs a)
 {
     const int lane = threadIdx.x & 31;
@@ -759,14 +784,15 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_bounce(const TraceArgs a)
             const AngleDev& A = a.angles[r.angle];
             ++nq;
             if (h.k < 0) {
-                emit(a, r, false);                     // escaped: its last hit radiates
+                // escaped: its last hit radiates
+                emit(a, r, kBi && A.bistatic && !rx_visible(a, A, r, nq, ovf));
             } else if (escape_pass) {
                 emit(a, r, true);                      // still trapped after B_max: invalid
             } else {
                 apply_hit(A, a.tris, h, a.flags, r);
                 record_hit(a, r, h);
                 if (r.nb < a.max_bounces || (a.flags & kFlagEscape)) again = true;
-                else emit(a, r, false);
+                else emit(a, r, kBi && A.bistatic && !rx_visible(a, A, r, nq, ovf));
             }
         }
         push(a, again, r);
@@ -775,14 +801,20 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_bounce(const TraceArgs a)
 }
 
 // every ray of the queue writes its record (B_max = 1 without the escape check)
+template <bool kBi>
 __global__ void __launch_bounds__(kTraceThreads) k_emit_all(const TraceArgs a)
 {
     const unsigned n_in = *a.q_in_count;
+    unsigned nq = 0;
+    bool ovf = false;
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n_in; i += gridDim.x * blockDim.x) {
         Ray r;
         load_state(a.q_in, i, r);
-        emit(a, r, false);
+        const AngleDev& A = a.angles[r.angle];
+        emit(a, r, kBi && A.bistatic && !rx_visible(a, A, r, nq, ovf));
     }
+    if (nq) atomicAdd(a.stats + kStatQueries, (unsigned long long)nq);
+    if (ovf) atomicAdd(a.stats + kStatOverflow, 1ull);
 }
 
 __global__ void k_angle_offsets(const long long* ray_off, const unsigned* tile_base, const unsigned* total,
@@ -832,6 +864,17 @@ void launch_trace_m(const TraceArgs& a, int n_blocks, bool count_visits, int sta
 
 cudaError_t launch_trace(const TraceArgs& a, int n_blocks, bool count_visits, int stack_depth, cudaStream_t st)
 {
+    if (a.bistatic && a.bounce > 0) {
+        // bounce passes of chunks with a bistatic aspect: per-lane traversal, 64-entry stack, visibility tests
+        if (a.wide) {
+            if (count_visits) k_bounce<true, 64, 1, true><<<n_blocks, kTraceThreads, 0, st>>>(a);
+            else k_bounce<false, 64, 1, true><<<n_blocks, kTraceThreads, 0, st>>>(a);
+        } else {
+            if (count_visits) k_bounce<true, 64, 0, true><<<n_blocks, kTraceThreads, 0, st>>>(a);
+            else k_bounce<false, 64, 0, true><<<n_blocks, kTraceThreads, 0, st>>>(a);
+        }
+        return cudaGetLastError();
+    }
     if (a.wide) launch_trace_m<1>(a, n_blocks, count_visits, stack_depth, st);
     else if (a.packet) launch_trace_m<2>(a, n_blocks, count_visits, stack_depth, st);
     else launch_trace_m<0>(a, n_blocks, count_visits, stack_depth, st);
@@ -840,7 +883,8 @@ cudaError_t launch_trace(const TraceArgs& a, int n_blocks, bool count_visits, in
 
 cudaError_t launch_emit_all(const TraceArgs& a, int n_blocks, cudaStream_t st)
 {
-    k_emit_all<<<n_blocks, kTraceThreads, 0, st>>>(a);
+    if (a.bistatic) k_emit_all<true><<<n_blocks, kTraceThreads, 0, st>>>(a);
+    else k_emit_all<false><<<n_blocks, kTraceThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -30,7 +30,7 @@ TRACE_NO_GRAPH = 32
 EXPORTS = ("sbr_version", "sbr_create", "sbr_destroy", "sbr_last_error", "sbr_load_mesh", "sbr_get_bbox",
            "sbr_build_bvh", "sbr_ray_grid_for", "sbr_ray_grid_box", "sbr_trace", "sbr_po_integrate", "sbr_get_hits",
            "sbr_get_records", "sbr_spacing_for", "sbr_po_integrate_noalloc", "sbr_run_batch", "sbr_submit_batch",
-           "sbr_sync", "sbr_get_tuning", "sbr_set_tuning", "sbr_autotune",
+           "sbr_sync", "sbr_get_tuning", "sbr_set_tuning", "sbr_autotune", "sbr_trace_bistatic",
            "sbr_surrogate_create", "sbr_surrogate_destroy", "sbr_surrogate_last_error", "sbr_surrogate_num_params",
            "sbr_surrogate_params", "sbr_surrogate_fourier", "sbr_surrogate_train", "sbr_surrogate_grads",
            "sbr_surrogate_predict", "sbr_gemm_bf16_tn")
@@ -112,6 +112,7 @@ def lib() -> C.CDLL:
         "sbr_ray_grid_for": ([vp, d, d, d, d, P(TraceOpts), P(RayGrid)], C.c_int),
         "sbr_ray_grid_box": ([P(C.c_float), d, d, d, d, P(TraceOpts), P(RayGrid)], C.c_int),
         "sbr_trace": ([vp, P(d), i64, d, d, C.c_int, P(TraceOpts), P(TraceStats)], C.c_int),
+        "sbr_trace_bistatic": ([vp, P(d), P(d), i64, d, d, C.c_int, P(TraceOpts), P(TraceStats)], C.c_int),
         "sbr_po_integrate": ([vp, P(d), i64, C.c_int, C.c_int, vp, vp, C.c_int], C.c_int),
         "sbr_get_hits": ([vp, i64, vp, vp, vp], C.c_int),
         "sbr_get_records": ([vp, i64, i64, vp, vp, vp, P(i64)], C.c_int),
@@ -284,15 +285,25 @@ class Context:
         return _grid_dict(g)
 
     def trace(self, angles, spacing, eta=0.05, max_bounces=1, window=0.0, offset=(0.0, 0.0), flags=0,
-              stats=True, chunk_rays=0) -> dict | None:
-        """Trace aspects ``angles`` ([n, 2] az, el degrees); returns the trace stats."""
+              stats=True, chunk_rays=0, rx=None) -> dict | None:
+        """Trace aspects ``angles`` ([n, 2] az, el degrees); returns the trace stats. ``rx``: [n, 2]
+        bistatic receiver directions (sbr_trace_bistatic), None for monostatic."""
         a = np.ascontiguousarray(np.atleast_2d(angles), dtype=np.float64)
         if a.shape[1] != 2:
             raise ValueError("angles must be [n, 2] (az, el)")
         o = _opts(window, offset, flags, chunk_rays)
         st = TraceStats()
-        self._check(lib().sbr_trace(self._h, a.ctypes.data_as(C.POINTER(C.c_double)), len(a), float(spacing),
-                                    float(eta), int(max_bounces), C.byref(o), C.byref(st) if stats else None))
+        sp = C.byref(st) if stats else None
+        dp = C.POINTER(C.c_double)
+        if rx is None:
+            self._check(lib().sbr_trace(self._h, a.ctypes.data_as(dp), len(a), float(spacing), float(eta),
+                                        int(max_bounces), C.byref(o), sp))
+        else:
+            r = np.ascontiguousarray(np.atleast_2d(rx), dtype=np.float64)
+            if r.shape != a.shape:
+                raise ValueError("rx must be [n, 2] like angles")
+            self._check(lib().sbr_trace_bistatic(self._h, a.ctypes.data_as(dp), r.ctypes.data_as(dp), len(a),
+                                                 float(spacing), float(eta), int(max_bounces), C.byref(o), sp))
         self.max_bounces = int(max_bounces)
         self.n_angles = len(a)
         self._last_angles = a.copy()

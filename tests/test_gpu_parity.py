@@ -363,3 +363,64 @@ def test_deep_cavity_escape_parity(G, ctx, orc):
     assert int(o["nb"].max()) > 10  # rays do bounce deep inside the inlets
     Eo, Ro = orc.po(o["coef"], o["L"], o["valid"], case["freqs"])
     assert_rcs_close(R[0, 0], Ro[0, :2])
+
+
+# ----------------------------------------------------------------------------- bistatic variant
+def _blocked_plate():
+    plate_xyz, plate_tri = S.square_plate(1.0, 8)
+    xb, z0, z1 = 0.30131, 0.05, 0.35
+    bl = np.array([[xb, -0.6, z0], [xb, 0.6, z0], [xb, 0.6, z1], [xb, -0.6, z1]], np.float32)
+    nv = len(plate_xyz)
+    xyz = np.concatenate([plate_xyz, bl]).astype(np.float32)
+    tri = np.concatenate([plate_tri, np.array([[nv, nv + 1, nv + 2], [nv, nv + 2, nv + 3]])]).astype(np.int32)
+    return xyz, tri
+
+
+def _bistatic_compare(G, ctx, orc, xyz, tri, tx, rx, sp, B, freqs, window=0.0, offset=(0.0, 0.0)):
+    ctx.load_mesh(xyz, tri)
+    om = orc.Mesh(xyz, tri)
+    ctx.trace(tx, sp, max_bounces=B, window=window, offset=offset, rx=rx, flags=HITS)
+    E, R = ctx.po_integrate(freqs, "HH,VV,HV,VH")
+    for a in range(len(tx)):
+        fr = orc.make_frame(om.bbox, tx[a][0], tx[a][1], sp, window=window, offset=offset, rx=rx[a])
+        o = orc.trace(om, fr, B)
+        assert_hit_parity(compare_hits(*ctx.get_hits(a), o))
+        rec = ctx.get_records(a)
+        vis = np.zeros(fr.n_rays, bool)
+        vis[rec["ray"]] = np.any(rec["coef"][:, :4] != 0, axis=1)
+        assert np.array_equal(vis, o["valid"].astype(bool))  # every visibility decision
+        Eo, Ro = orc.po(o["coef"], o["L"], o["valid"], freqs)
+        assert_rcs_close(R[a, :, :2], Ro[:, :2])
+    return R
+
+
+def test_bistatic_blocker_and_plate(G, ctx, orc):
+    xyz, tri = _blocked_plate()
+    _bistatic_compare(G, ctx, orc, xyz, tri, [[0.0, 90.0], [0.0, 90.0], [0.0, 60.0]],
+                      [[0.0, 30.0], [180.0, 40.0], [180.0, 60.0]], 0.004, 1, [10e9, 9e9], window=1.3)
+    # without the blocker, the specular receiver of a 30 deg incidence sees the whole plate:
+    # sigma = 4 pi (A cos 30)^2 / lambda^2 (PO closed form)
+    pxyz, ptri = S.square_plate(1.0, 8)
+    R = _bistatic_compare(G, ctx, orc, pxyz, ptri, [[0.0, 60.0]], [[180.0, 60.0]], 0.003, 1, [10e9], window=1.3)
+    lam = C0 / 10e9
+    want = 10 * math.log10(4 * math.pi * math.cos(math.radians(30.0)) ** 2 / lam**2)
+    assert abs(R[0, 0, 0] - want) < 0.15 and abs(R[0, 0, 1] - want) < 0.15
+
+
+def test_bistatic_trihedral_multibounce(G, ctx, orc):
+    case = S.trihedral_case()
+    tx = case["angles"][[60, 90]]
+    rx = np.array([[40.0, 30.0], [60.0, 40.0]])
+    _bistatic_compare(G, ctx, orc, case["xyz"], case["tri"], tx, rx, 2 * case["spacing"], 3, [10e9],
+                      offset=case["offset"])
+
+
+def test_bistatic_at_transmitter_matches_monostatic_single_bounce(G, ctx):
+    xyz, tri = S.square_plate(1.0, 8)
+    ctx.load_mesh(xyz, tri)
+    ang = np.array([[0.0, 90.0], [20.0, 75.0]])
+    ctx.trace(ang, 0.004, max_bounces=1, window=1.3)
+    E0, R0 = ctx.po_integrate([10e9], "HH,VV")
+    ctx.trace(ang, 0.004, max_bounces=1, window=1.3, rx=ang)
+    E1, R1 = ctx.po_integrate([10e9], "HH,VV")
+    assert np.array_equal(E0, E1)

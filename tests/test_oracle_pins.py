@@ -372,3 +372,75 @@ def test_fp32_transport_tracks_exact_transport(orc, which):
         dt = np.abs(t32["hit_t"][both] - t64["hit_t"][both])
         assert np.all(dt < 1e-5 * t64["hit_t"][both] + 1e-6)
     assert mism / n < 2e-3, (mism, n)
+
+
+# ----------------------------------------------------------------------------- bistatic variant
+def test_bistatic_monostatic_limit(orc):
+    # a receiver at the transmitter reproduces the monostatic fields bit for bit (plate, one bounce)
+    xyz, tri = S.square_plate(1.0, 4)
+    m = orc.Mesh(xyz, tri)
+    for az, el in ((0.0, 90.0), (30.0, 70.0)):
+        E0, _, _, _ = orc.rcs_angle(m, m.bbox, az, el, 0.01, [10e9, 3e9], 1, window=1.5)
+        E1, _, t1, _ = orc.rcs_angle(m, m.bbox, az, el, 0.01, [10e9, 3e9], 1, window=1.5, rx=(az, el))
+        assert np.array_equal(E0, E1)
+
+
+def _plate_bistatic(orc, th_deg, phi_deg, f=10e9, ds=0.003):
+    # 1 m x 1 m plate in z = 0; transmitter theta from the normal on the +x side, receiver phi on the -x side
+    xyz, tri = S.square_plate(1.0, 8)
+    m = orc.Mesh(xyz, tri)
+    E, R, tr, fr = orc.rcs_angle(m, m.bbox, 0.0, 90.0 - th_deg, ds, [f], 1, window=1.3,
+                                 rx=(180.0, 90.0 - phi_deg))
+    return R[0], tr
+
+
+@pytest.mark.parametrize("th", [0.0, 30.0, 50.0])
+def test_bistatic_plate_specular_closed_form(orc, th):
+    # PO in the specular direction of a flat PEC plate: sigma = 4 pi (A cos theta)^2 / lambda^2, both polarisations
+    lam = C0 / 10e9
+    want = db(4 * math.pi * (1.0 * math.cos(math.radians(th))) ** 2 / lam**2)
+    R, _ = _plate_bistatic(orc, th, th)
+    assert abs(R[0] - want) < 0.15 and abs(R[1] - want) < 0.15, (R[:2], want)
+
+
+def test_bistatic_plate_null_and_sidelobe(orc):
+    # along x the plate is a uniform aperture of length a: |sum| ~ sinc(k a q / 2), q = sin(th) - sin(phi);
+    # first null at q = lambda / a, first sidelobe (-13.26 dB) near q = 1.4303 lambda / a. A wrong sign of the
+    # receiver path term would move the peak away from the specular direction.
+    lam, a, th = C0 / 10e9, 1.0, 30.0
+    spec, _ = _plate_bistatic(orc, th, th)
+    s_th = math.sin(math.radians(th))
+    null, _ = _plate_bistatic(orc, th, math.degrees(math.asin(s_th - lam / a)))
+    side, _ = _plate_bistatic(orc, th, math.degrees(math.asin(s_th - 1.4303 * lam / a)))
+    # the obliquity factor changes by < 0.1 dB over these few degrees
+    assert null[0] < spec[0] - 25.0 and null[1] < spec[1] - 25.0
+    assert abs((side[0] - spec[0]) + 13.26) < 0.6 and abs((side[1] - spec[1]) + 13.26) < 0.6
+    mono, _ = _plate_bistatic(orc, th, -th)  # receiver back at the transmitter: far off specular
+    assert mono[0] < spec[0] - 25.0
+
+
+def test_bistatic_visibility_by_brute_force(orc):
+    # plate in z = 0 lit from the normal; a vertical blocker (normal along x, parallel to the incident rays,
+    # so no incident ray hits it) hides part of the plate from a receiver 60 deg toward +x. A hit point at x
+    # is hidden exactly when x lies in [xb - z1 tan60, xb - z0 tan60].
+    plate_xyz, plate_tri = S.square_plate(1.0, 8)
+    xb, z0, z1 = 0.30131, 0.05, 0.35
+    bl = np.array([[xb, -0.6, z0], [xb, 0.6, z0], [xb, 0.6, z1], [xb, -0.6, z1]], np.float32)
+    xyz = np.concatenate([plate_xyz, bl]).astype(np.float32)
+    nv = len(plate_xyz)
+    tri = np.concatenate([plate_tri, np.array([[nv, nv + 1, nv + 2], [nv, nv + 2, nv + 3]])]).astype(np.int32)
+    m = orc.Mesh(xyz, tri)
+    fr = orc.make_frame(m.bbox, 0.0, 90.0, 0.004, window=1.3, rx=(0.0, 30.0))
+    tr = orc.trace(m, fr, 1)
+    n_blk = len(plate_tri)
+    hit_plate = (tr["hit_tri"][:, 0] >= 0) & (tr["hit_tri"][:, 0] < n_blk)
+    assert not np.any(tr["hit_tri"][:, 0] >= n_blk)  # the blocker is edge-on to the incident rays
+    ids = np.arange(fr.n_rays)
+    xs = np.array([orc.ray(fr, int(i % fr.nu), int(i // fr.nu))[0][0] for i in ids[hit_plate]])
+    t60 = math.tan(math.radians(60.0))
+    lo, hi = xb - z1 * t60, xb - z0 * t60
+    hidden = (xs > lo) & (xs < hi)
+    near = (np.abs(xs - lo) < 1e-4) | (np.abs(xs - hi) < 1e-4)
+    vis = tr["valid"][hit_plate].astype(bool)
+    assert np.array_equal(vis[~near], ~hidden[~near])
+    assert hidden.sum() > 1000 and (~hidden).sum() > 1000
