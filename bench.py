@@ -332,8 +332,9 @@ SURROGATE_DOMAINS = {
     "full": dict(az=(0.0, 360.0), el=(-30.0, 30.0), f=(1e9, 12e9), n_aspects=2000, f_per=100, n_heldout=10000,
                  lattice=(500, 40, 50), sigmas=(1.0, 4.0, 16.0, 64.0)),
     # a dense sweep patch around nose-on: 4 deg x 2 deg x 1.0-1.2 GHz, 200k samples
+    # held-out points traced on the training data's ray grid (10 rays per wavelength of 1.2 GHz)
     "patch": dict(az=(178.0, 182.0), el=(-1.0, 1.0), f=(1e9, 1.2e9), n_aspects=2000, f_per=100, n_heldout=10000,
-                  lattice=(100, 20, 500), sigmas=(16.0, 32.0, 64.0, 128.0, 256.0)),
+                  lattice=(100, 20, 500), sigmas=(16.0, 32.0, 64.0, 128.0, 256.0), heldout_grid="domain"),
 }
 
 
@@ -391,12 +392,23 @@ def surrogate_eval(G, torch, ctx, dom, epochs=60, batch=2048, spread_db=1.0, sca
     rng = np.random.default_rng(4)
     hx = np.stack([rng.uniform(a0, a1, n_heldout), rng.uniform(e0, e1, n_heldout),
                    np.exp(rng.uniform(np.log(f0), np.log(f1), n_heldout))], 1)
-    hreq = [dict(az=a, el=e, freqs=np.array([f]), spacing=S.spacing_for(f, 10.0)) for a, e, f in hx]
+    # plain SBR of each held-out point: 10 rays per wavelength of its own frequency, or of the domain's
+    # highest frequency (the training data's grid) when the domain says so
+    domain_grid = dom.get("heldout_grid") == "domain"
+    hreq = [dict(az=a, el=e, freqs=np.array([f]), spacing=S.spacing_for(f1 if domain_grid else f, 10.0))
+            for a, e, f in hx]
     torch.cuda.synchronize()
     t0 = _t.perf_counter()
     _, Rh, _ = ctx.run_batch(hreq, eta=0.05, max_bounces=10, offset=off)
     t_sbr = _t.perf_counter() - t0
     Rh = np.concatenate(Rh)  # [n, 2] dBsm HH, VV
+    grid_sens = None
+    if domain_grid:
+        # how much plain SBR itself moves between the two ray grids (its own discretisation)
+        _, Rg, _ = ctx.run_batch([dict(r, spacing=S.spacing_for(float(r["freqs"][0]), 10.0)) for r in hreq],
+                                 eta=0.05, max_bounces=10, offset=off)
+        dg = np.max(np.abs(np.concatenate(Rg) - Rh), axis=1)
+        grid_sens = {"median_db": float(np.median(dg)), "within_0.5dB": float(np.mean(dg <= 0.5))}
     t0 = _t.perf_counter()
     ym, spread = sur.predict(hx)
     t_pred = _t.perf_counter() - t0
@@ -444,6 +456,9 @@ def surrogate_eval(G, torch, ctx, dom, epochs=60, batch=2048, spread_db=1.0, sca
             "all_median_db_error": float(np.median(err[m])) if m.any() else None}
     sur.close()
     return {"domain": {k: dom[k] for k in ("az", "el", "f")}, "training_samples": int(len(x)),
+            "heldout_grid": "10 rays per wavelength of " + ("the domain's highest frequency" if domain_grid
+                                                             else "each point's frequency"),
+            "sbr_grid_sensitivity": grid_sens,
             "training_aspects": n_aspects, "data_gen_s": t_data, "data_ray_bounces": st["ray_bounces"],
             "sigma_validation_rel_rms": {str(k): v for k, v in tune.items()}, "fourier_sigma": sigma,
             "tune_s": t_tune, "train_s": t_train, "epochs": epochs, "batch": batch,

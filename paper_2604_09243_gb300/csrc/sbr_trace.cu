@@ -37,7 +37,6 @@ constexpr unsigned kFull = 0xffffffffu;
 // trace flag bits (mirror of SBR_TRACE_* in sbr.h)
 constexpr int kFlagLiteral = 1;
 constexpr int kFlagEscape = 2;
-constexpr int kFlagHits = 4;
 
 struct Hit {
     float t;
@@ -426,6 +425,35 @@ __device__ __forceinline__ void load_state(const RayState* __restrict__ q, unsig
     r.angle = g.x; r.local = g.y; r.last = g.z; r.nb = g.w;
 }
 
+// The traversal needs only the origin, the direction and the triangle to
+// skip: load those first and the rest of the state after the query, so the
+// payload does not occupy registers during the traversal.
+__device__ __forceinline__ void load_geom(const RayState* __restrict__ q, unsigned i, Ray& r)
+{
+    const float4* p = reinterpret_cast<const float4*>(q + i);
+    const float4 a = p[0], b = p[1];
+    r.o = make_float3(a.x, a.y, a.z);
+    r.d = make_float3(a.w, b.x, b.y);
+    r.last = reinterpret_cast<const int4*>(p)[5].z;
+}
+
+__device__ __forceinline__ void load_payload(const RayState* __restrict__ q, unsigned i, Ray& r)
+{
+    const float4* p = reinterpret_cast<const float4*>(q + i);
+    const float4 b = p[1], c = p[2], e = p[3], f = p[4];
+    const int4 g = reinterpret_cast<const int4*>(p)[5];
+    r.ev = make_float3(b.z, b.w, c.x);
+    r.lacc_hi = c.y;
+    r.lacc_lo = c.z;
+    r.cos0 = c.w;
+    r.c[0] = e.x; r.c[1] = e.y; r.c[2] = e.z; r.c[3] = e.w;
+    r.c[4] = f.x;
+    r.lc_hi = f.y;
+    r.lc_lo = f.z;
+    r.nfs = f.w;
+    r.angle = g.x; r.local = g.y; r.nb = g.w;
+}
+
 __device__ __forceinline__ void store_state(RayState* __restrict__ q, unsigned i, const Ray& r)
 {
     float4* p = reinterpret_cast<float4*>(q + i);
@@ -438,7 +466,6 @@ __device__ __forceinline__ void store_state(RayState* __restrict__ q, unsigned i
 }
 
 __device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-__device__ __forceinline__ float dot3(const float* a, float3 b) { return a[0] * b.x + a[1] * b.y + a[2] * b.z; }
 
 // Update the ray at its closest hit: path, bounce count, candidate PO
 // coefficients of this hit (used if it turns out to be the last), reflection,
@@ -733,17 +760,18 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_primary(const TraceArgs a)
                               __fadd_rn(__fadd_rn(A.p0[1], __fmul_rn(fi, A.du[1])), __fmul_rn(fj, A.dv[1])),
                               __fadd_rn(__fadd_rn(A.p0[2], __fmul_rn(fi, A.du[2])), __fmul_rn(fj, A.dv[2])));
             r.d = make_float3(A.dir[0], A.dir[1], A.dir[2]);
-            r.ev = make_float3(A.vhat[0], A.vhat[1], A.vhat[2]);
-            tf_dot(A.dir, r.o, r.lacc_hi, r.lacc_lo);
-            r.cos0 = 0.f;
-            r.nb = 0;
-            r.last = -1;
         }
         Hit h;
         query<kCount, kStack, kMode>(a, active, r.o, r.d, -1, h, nvis, ntri, ovf);
         if (active) {
             ++nq;
             if (h.k >= 0) {
+                const AngleDev& A2 = a.angles[ang];
+                r.ev = make_float3(A2.vhat[0], A2.vhat[1], A2.vhat[2]);
+                tf_dot(A2.dir, r.o, r.lacc_hi, r.lacc_lo);
+                r.cos0 = 0.f;
+                r.nb = 0;
+                r.last = -1;
                 hit = true;
                 apply_hit(A, a.tris, h, a.flags, r);
                 record_hit(a, r, h);
@@ -777,10 +805,11 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_bounce(const TraceArgs a)
         r.o = make_float3(0.f, 0.f, 0.f);
         r.d = make_float3(0.f, 0.f, 1.f);
         r.last = -1;
-        if (active) load_state(a.q_in, idx, r);
+        if (active) load_geom(a.q_in, idx, r);
         Hit h;
         query<kCount, kStack, kMode>(a, active, r.o, r.d, r.last, h, nvis, ntri, ovf);
         if (active) {
+            load_payload(a.q_in, idx, r);
             const AngleDev& A = a.angles[r.angle];
             ++nq;
             if (h.k < 0) {
