@@ -194,9 +194,11 @@ def run_reference(args, case, ws, rank, pg):
     if rank != 0:
         return
     threads = os.cpu_count() or 1
-    n = args.ref_angles
-    for _ in range(args.warmup):
-        oracle_sample(case, 1, threads)
+    t1 = 0.0
+    for _ in range(max(1, args.warmup)):
+        t1 = oracle_sample(case, 1, threads)[1]
+    # aspects per step: at most --ref-angles, fewer when the steps would take more than about two minutes
+    n = max(1, min(args.ref_angles, int(120.0 / (max(1, args.steps) * max(t1, 1e-3)))))
     tot_b, tot_t = 0, 0.0
     for _ in range(args.steps):
         b, t, idx = oracle_sample(case, n, threads)
@@ -659,7 +661,7 @@ def run_sbr(args, case, ws, rank, local, pg):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sbr", choices=["sbr", "reference"])
     ap.add_argument("--workload", default="trihedral",
