@@ -49,6 +49,7 @@ import sbr_inputs as S  # noqa: E402
 # the near/far slabs picked per ray (6 FMA, 6 min/max, 1 scale, 1 compare
 # each) and a 5-exchange sorting network (1 compare, 4 selects each).
 OPS_NODE = 41
+OPS_NODE_OCT = 29  # binary node over the octant copies: 2 x (6 FMA + 6 min/max + 1 scale + 1 compare) + ordering
 OPS_NODE4 = 81
 OPS_TRI = 38
 # DRAM bytes of the three transport passes per launched ray of the trihedral
@@ -58,7 +59,7 @@ OPS_TRI = 38
 # (stack depth and chunk size leave the DRAM bytes per ray unchanged: the
 # queues and records are the traffic); it grows with the rays, so it is scaled
 # by the rays of a step.
-TRAFFIC_PER_RAY = {"trihedral": (188.39e6 / 2114692, dict(tile_w=4, bvh_width=2, packet=0), "ploc")}
+TRAFFIC_PER_RAY = {"trihedral": (188.39e6 / 2114692, dict(tile_w=4, bvh_width=2, packet=0, octant=0), "ploc")}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -340,6 +341,19 @@ SURROGATE_DOMAINS = {
 }
 
 
+def _tensor_roofline(points, members, seconds, width=512, depth=6, n_fourier=256):
+    """Ensemble prediction as a tensor-core contraction: 2 (n_fourier W + (D - 1) W^2 + 4 W) FLOP per point
+    and member (BF16 GEMMs with FP32 accumulation), over the whole prediction call (host wall clock, so
+    the Fourier features, head, ensemble statistics and transfers count against it)."""
+    flops = 2.0 * (n_fourier * width + (depth - 1) * width * width + 4 * width) * points * members
+    pk, src = peaks()
+    peak = pk.get("bf16_tflops", 1900.0)
+    ach = flops / seconds / 1e12
+    return {"bound": "tensor", "kernel": "k_gemm_tn (tcgen05, BF16 in, FP32 accumulate) in sbr_surrogate_predict",
+            "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+            "peak_source": f"bf16 dense GEMM burst, {src}", "flop": flops}
+
+
 def surrogate_eval(G, torch, ctx, dom, epochs=60, batch=2048, spread_db=1.0, scale=1.0):
     """Learned surrogate on the aircraft mesh against plain SBR over one domain.
 
@@ -475,6 +489,7 @@ def surrogate_eval(G, torch, ctx, dom, epochs=60, batch=2048, spread_db=1.0, sca
             "all_median_db_error": float(np.median(err)),
             "hybrid_points_per_s": n_heldout / (t_pred + t_fb), "hybrid_vs_plain": t_sbr / (t_pred + t_fb),
             "lattice_points": int(len(q)), "lattice_surrogate_s": t_q,
+            "lattice_roofline": _tensor_roofline(len(q), 4, t_q),
             "lattice_served_fraction": float(np.mean(qs <= spread_db)),
             "lattice_sbr_s": t_lat, "lattice_sbr_sample": f"{n_lat_sbr} of {lat_aspects} lattice aspects, scaled",
             "bands": bands}
@@ -506,7 +521,7 @@ def run_surrogate(args, ws, rank, local, pg):
                           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
                           "data": "synthetic", "config": {"workload": "aircraft_surrogate", "mesh": "aircraft seed 1",
                                                           "parallelism": f"replicas{ws}"},
-                          "surrogate": res}))
+                          "roofline": head["lattice_roofline"], "surrogate": res}))
 
 
 def run_sbr(args, case, ws, rank, local, pg):
@@ -612,12 +627,14 @@ def run_sbr(args, case, ws, rank, local, pg):
 
     # --- roofline of the transport passes (FP32 issue bound)
     wide = ctx.tuning()["bvh_width"] == 4
+    octant = ctx.tuning()["octant"] == 1
     traffic = None
     if args.workload in TRAFFIC_PER_RAY:
         per_ray, setting, builder = TRAFFIC_PER_RAY[args.workload]
         if builder == args.builder and all(ctx.tuning()[k] == v for k, v in setting.items()):
             traffic = per_ray * stats[0]["rays_launched"]
-    ops = (OPS_NODE4 if wide else OPS_NODE) * cnt["node_visits"] + OPS_TRI * cnt["tri_tests"]
+    ops = (OPS_NODE4 if wide else (OPS_NODE_OCT if octant else OPS_NODE)) * cnt["node_visits"] + \
+        OPS_TRI * cnt["tri_tests"]
     pass_s = float(np.mean([s["pass_ms"] for s in stats])) / 1e3
     pk, src = peaks()
     peak_ops = SM_COUNT * FP32_LANES_PER_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
@@ -631,7 +648,7 @@ def run_sbr(args, case, ws, rank, local, pg):
             "rays_launched_per_step": stats[0]["rays_launched"], "ray_bounces_per_step": bounces,
             "valid_rays_per_step": stats[0]["valid_rays"],
             "roofline": {"bound": "alu", "kernel": "k_primary+k_bounce (transport passes, "
-                                                   f"{'4-wide' if wide else 'binary'} tree)",
+                                                   f"{'4-wide' if wide else ('binary, octant copies' if octant else 'binary')} tree)",
                          "achieved": achieved, "peak": peak_ops, "unit": "T FP32-op/s",
                          "frac": achieved / peak_ops, "traffic": traffic,
                          "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "

@@ -290,6 +290,9 @@ typedef struct {
     int packet;          /* 1: the 32 rays of a warp walk the binary tree together (one broadcast fetch
                             per node, no divergence; each ray still tests only the boxes it enters);
                             needs bvh_width 2 and stack_depth <= 64; default 0 */
+    int octant;          /* 1: traverse copies of the binary nodes stored per direction octant with the near
+                            and far slab of each axis chosen in advance (no per-axis min/max; 8 x the node
+                            memory, built on first use); needs bvh_width 2 and packet 0; default 0 */
     int silhouette;      /* 1: before the primary pass, rasterise every triangle's widened projection onto
                             the ray grid and skip the query of rays outside all of them (sure misses: no
                             hit, not counted as ray-bounces); default 0 */
@@ -312,7 +315,7 @@ typedef struct {
 
 /* Autotuner: times sbr_run_batch on the given sample batch (arguments as for
  * sbr_run_batch) under the current setting and then, one parameter at a
- * time (traversal: binary / 4-wide / warp-cooperative, blocks per SM, ray
+ * time (traversal: binary / 4-wide / warp-cooperative / octant copies, blocks per SM, ray
  * tile, stack depth, PO item, chunk size, silhouette mask), under
  * each alternative value, keeping a change when it is more than 1 % faster and its results
  * agree (see sbr_tune_trial). Each timing is the mean of `reps` runs after one

@@ -89,6 +89,8 @@ struct sbr_ctx {
     DevBuf nodes, tris, bvh_scratch, bbox_dev, err_dev;
     DevBuf nodes4;  // 4-wide collapse of the binary tree
     int n_nodes4 = 0;
+    DevBuf nodes_oct;  // octant copies of the binary nodes (built on first use)
+    long long n_nodes = 0, oct_gen = -1;
     // trace
     DevBuf angles, rayoff, mask, tilebase, scan_scr, recoff, q0, q1, ctr64, ctr32, stats, rec, cover;
     DevBuf hit_tri, hit_t, hit_nb;
@@ -281,7 +283,8 @@ bool tuning_ok(const sbr_tuning& t)
 {
     const bool tile = t.tile_w >= 1 && t.tile_w <= 32 && (t.tile_w & (t.tile_w - 1)) == 0;
     const bool trav = (t.packet == 0 || (t.packet == 1 && t.bvh_width == 2 && t.stack_depth <= 64)) &&
-                      (t.silhouette == 0 || t.silhouette == 1);
+                      (t.silhouette == 0 || t.silhouette == 1) &&
+                      (t.octant == 0 || (t.octant == 1 && t.bvh_width == 2 && t.packet == 0));
     return tile && trav && (t.bvh_width == 2 || t.bvh_width == 4) && t.blocks_per_sm >= 1 && t.blocks_per_sm <= 4 &&
            (t.stack_depth == 32 || t.stack_depth == 64 || t.stack_depth == 128) && t.chunk_rays_log2 >= 20 &&
            t.chunk_rays_log2 <= 27 && (t.po_item == 512 || t.po_item == 1024 || t.po_item == 2048);
@@ -353,6 +356,7 @@ int sbr_create(sbr_ctx** out, int device, void* cuda_stream)
     c->tune.bvh_width = 2;
     c->tune.packet = 0;
     c->tune.silhouette = 0;
+    c->tune.octant = 0;
     *out = c;
     return SBR_OK;
 }
@@ -364,6 +368,7 @@ void sbr_destroy(sbr_ctx* c)
     cudaStreamSynchronize(c->stream);
     DevBuf* all[] = {&c->xyz, &c->tri, &c->nodes, &c->tris, &c->bvh_scratch, &c->bbox_dev, &c->err_dev, &c->nodes4,
                      &c->angles, &c->rayoff, &c->mask, &c->tilebase, &c->scan_scr, &c->recoff, &c->q0, &c->q1, &c->cover,
+                     &c->nodes_oct,
                      &c->ctr64, &c->ctr32, &c->stats, &c->rec, &c->hit_tri, &c->hit_t, &c->hit_nb, &c->items,
                      &c->itemoff, &c->freq, &c->kfreq, &c->partial, &c->E, &c->rcs};
     for (DevBuf* b : all) b->release();
@@ -423,6 +428,7 @@ int sbr_build_bvh(sbr_ctx* c, const sbr_bvh_opts* opt)
     ++c->mesh_gen;  // captured batch graphs hold the node and triangle pointers
     const long long n = c->n_tri;
     const long long n_nodes = n > 1 ? n - 1 : 1;
+    c->n_nodes = n_nodes;
     CK(c->nodes.ensure(sizeof(float4) * 4 * (size_t)n_nodes), "alloc nodes");
     CK(c->tris.ensure(sizeof(float4) * 3 * (size_t)n), "alloc tris");
     size_t sb = bvh_scratch_bytes(n);
@@ -577,6 +583,16 @@ cudaEvent_t pool_event(sbr_ctx* c, size_t i)
     return c->evpool[i];
 }
 
+// the octant copies of the current binary nodes (built once per tree)
+cudaError_t ensure_octant_nodes(sbr_ctx* c, cudaStream_t st)
+{
+    if (c->oct_gen == c->mesh_gen) return cudaSuccess;
+    cudaError_t e = c->nodes_oct.ensure(sizeof(float4) * 4 * 8 * (size_t)c->n_nodes);
+    if (e == cudaSuccess) e = build_octant_nodes(c->nodes.as<float4>(), c->n_nodes, c->nodes_oct.as<float4>(), st);
+    if (e == cudaSuccess) c->oct_gen = c->mesh_gen;
+    return e;
+}
+
 // Trace the aspects [a0, a1) (one chunk): primary pass, popcount scan of the
 // hit masks (one synchronisation to learn the record counts), bounce passes.
 // Records go to c->rec from index rec_base on; earlier records are kept.
@@ -624,8 +640,11 @@ int trace_chunk(sbr_ctx* c, TraceRun& R, int64_t a0, int64_t a1, long long rec_b
     memset(&ta, 0, sizeof(ta));
     ta.wide = c->tune.bvh_width == 4;
     ta.packet = c->tune.packet;
+    ta.octant = c->tune.octant;
+    ta.n_nodes = c->n_nodes;
     for (int i = 0; i < na; ++i) ta.bistatic |= c->ang[(size_t)(a0 + i)].bistatic ? 1 : 0;
-    ta.nodes = ta.wide ? c->nodes4.as<float4>() : c->nodes.as<float4>();
+    if (ta.octant) CK(ensure_octant_nodes(c, c->stream), "octant nodes");
+    ta.nodes = ta.wide ? c->nodes4.as<float4>() : (ta.octant ? c->nodes_oct.as<float4>() : c->nodes.as<float4>());
     ta.tris = c->tris.as<float4>();
     ta.angles = c->angles.as<AngleDev>();
     ta.ray_off = c->rayoff.as<long long>();
@@ -905,7 +924,9 @@ cudaError_t enqueue_plan(const sbr_ctx* c, BatchPlan& P, cudaStream_t st)
         memset(&ta, 0, sizeof(ta));
         ta.wide = P.tune.bvh_width == 4;
         ta.packet = P.tune.packet;
-        ta.nodes = ta.wide ? c->nodes4.as<float4>() : c->nodes.as<float4>();
+        ta.octant = P.tune.octant;
+        ta.n_nodes = c->n_nodes;
+        ta.nodes = ta.wide ? c->nodes4.as<float4>() : (ta.octant ? c->nodes_oct.as<float4>() : c->nodes.as<float4>());
         ta.tris = c->tris.as<float4>();
         ta.angles = P.angles.as<AngleDev>() + a0;
         ta.ray_off = P.rayoff.as<long long>() + a0 + (int64_t)k;  // chunk k's table has na + 1 entries
@@ -1346,6 +1367,7 @@ int sbr_submit_batch(sbr_ctx* c, const sbr_request* req, int64_t n_req, const do
         c->plan = P;
     }
     BatchPlan& P = *c->plan;
+    if (P.tune.octant) CK(ensure_octant_nodes(c, c->stream), "octant nodes");
     if (!graph) {
         CK(enqueue_plan(c, P, c->stream), "enqueue batch");
     } else {
@@ -1471,10 +1493,10 @@ int sbr_autotune(sbr_ctx* c, const sbr_request* req, int64_t n_req, const double
     }
     sbr_tuning bestt = start;
     const int occ = std::min(4, std::max(1, trace_blocks_per_sm()));
-    // parameter 0 is the traversal: binary per lane, 4-wide per lane, binary per warp
+    // parameter 0 is the traversal: binary per lane, 4-wide per lane, binary per warp, binary over octant copies
     for (int p = 0; p < 7; ++p) {
         std::vector<int> vals;
-        if (p == 0) vals = {0, 1, 2};
+        if (p == 0) vals = {0, 1, 2, 3};
         if (p == 6) vals = {0, 1};
         if (p == 1)
             for (int v = 1; v <= occ; ++v) vals.push_back(v);
@@ -1485,10 +1507,11 @@ int sbr_autotune(sbr_ctx* c, const sbr_request* req, int64_t n_req, const double
         for (int v : vals) {
             sbr_tuning t = bestt;
             if (p == 0) {
-                const int w = v == 1 ? 4 : 2, pk = v == 2 ? 1 : 0;
-                if (t.bvh_width == w && t.packet == pk) continue;
+                const int w = v == 1 ? 4 : 2, pk = v == 2 ? 1 : 0, oc = v == 3 ? 1 : 0;
+                if (t.bvh_width == w && t.packet == pk && t.octant == oc) continue;
                 t.bvh_width = w;
                 t.packet = pk;
+                t.octant = oc;
                 if (pk && t.stack_depth > 64) t.stack_depth = 64;
             } else {
                 int* fields[7] = {nullptr,    &t.blocks_per_sm,   &t.tile_w,    &t.stack_depth,

@@ -649,6 +649,32 @@ __global__ void __launch_bounds__(kThreads) k_collapse4(const float4* nodes2, co
     o[7] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+// ---------------------------------------------------------------- octant copies
+__global__ void __launch_bounds__(kThreads) k_octant_nodes(const float4* nodes, long long n_nodes, float4* out)
+{
+    const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= n_nodes) return;
+    const float4 n0 = nodes[4 * k], n1 = nodes[4 * k + 1], n2 = nodes[4 * k + 2], n3 = nodes[4 * k + 3];
+    // (lo, hi) per axis: L x = n0.xy, L y = n0.zw, L z = n2.xy; R x = n1.xy, R y = n1.zw, R z = n2.zw
+    const float Llo[3] = {n0.x, n0.z, n2.x}, Lhi[3] = {n0.y, n0.w, n2.y};
+    const float Rlo[3] = {n1.x, n1.z, n2.z}, Rhi[3] = {n1.y, n1.w, n2.w};
+    for (int o = 0; o < 8; ++o) {
+        float Ln[3], Lf[3], Rn[3], Rf[3];
+        for (int a = 0; a < 3; ++a) {
+            const bool neg = (o >> a) & 1;
+            Ln[a] = neg ? Lhi[a] : Llo[a];
+            Lf[a] = neg ? Llo[a] : Lhi[a];
+            Rn[a] = neg ? Rhi[a] : Rlo[a];
+            Rf[a] = neg ? Rlo[a] : Rhi[a];
+        }
+        float4* d = out + 4 * ((long long)o * n_nodes + k);
+        d[0] = make_float4(Ln[0], Ln[1], Ln[2], Rn[0]);
+        d[1] = make_float4(Rn[1], Rn[2], Lf[0], Lf[1]);
+        d[2] = make_float4(Lf[2], Rf[0], Rf[1], Rf[2]);
+        d[3] = n3;
+    }
+}
+
 struct Carve {
     char* p;
     size_t off, cap;
@@ -813,6 +839,13 @@ cudaError_t bvh_build(const BvhBuild& b, cudaStream_t st)
     int ge = n > 1 ? (n - 1 + kThreads - 1) / kThreads : 1;
     k_emit<<<ge, kThreads, 0, st>>>(n, left, right, first, lbox, nbox, ncnt, ncol, b.nodes);
     k_reorder<<<g, kThreads, 0, st>>>(b.xyz, b.tri, b.n_vert, vi, n, b.tris);
+    return cudaGetLastError();
+}
+
+cudaError_t build_octant_nodes(const float4* nodes, long long n_nodes, float4* out, cudaStream_t st)
+{
+    if (n_nodes <= 0) return cudaErrorInvalidValue;
+    k_octant_nodes<<<(unsigned)((n_nodes + kThreads - 1) / kThreads), kThreads, 0, st>>>(nodes, n_nodes, out);
     return cudaGetLastError();
 }
 

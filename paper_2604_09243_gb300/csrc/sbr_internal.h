@@ -83,6 +83,17 @@ enum { kStatQueries = 0, kStatNodes = 1, kStatTris = 2, kStatOverflow = 3, kStat
 // Node 0 is the root. Each child box is the box of a binary node or leaf, so
 // the 4-wide tree tests exactly the boxes the binary tree would.
 constexpr int kNode4Float4 = 8;
+// Octant copies of the binary nodes: copy o (bit 0: x, bit 1: y, bit 2: z set
+// when the ray's direction is negative on that axis) stores for both children
+// the near and far slab of each axis already chosen (near = lo on a positive
+// axis, hi on a negative one):
+//   f0 = (L.near.x, L.near.y, L.near.z, R.near.x)
+//   f1 = (R.near.y, R.near.z, L.far.x, L.far.y)
+//   f2 = (L.far.z, R.far.x, R.far.y, R.far.z)
+//   f3 = (ref L, ref R, 0, 0)
+// at octant_nodes[(o * n_nodes + k) * 4 ..]. An empty child box (lo = +FLT_MAX,
+// hi = -FLT_MAX) has near > far on every axis, so it is never entered.
+cudaError_t build_octant_nodes(const float4* nodes, long long n_nodes, float4* out, cudaStream_t st);
 // Collapse the binary node array (root 0) into nodes4 (room for max(n_tri - 1, 1) nodes).
 // queue_a / queue_b: int2 [max(n_tri - 1, 1)]; counters: int [4]. Synchronises once per level;
 // *n_nodes4 receives the node count.
@@ -115,6 +126,8 @@ struct TraceArgs {
     int wide;
     int packet;                   // 1: warp-cooperative traversal of the binary tree
     int bistatic;                 // 1: some aspect of the chunk has a bistatic receiver (visibility tests)
+    int octant;                   // 1: nodes are the octant copies of the binary nodes (n_nodes per copy)
+    long long n_nodes;
     const float4* tris;
     const AngleDev* angles;
     const long long* ray_off;     // [n_angles + 1] chunk-relative, multiples of 32

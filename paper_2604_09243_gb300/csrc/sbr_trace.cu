@@ -197,6 +197,64 @@ __device__ __forceinline__ void closest_hit(const float4* __restrict__ nodes, co
     }
 }
 
+// Binary traversal over the octant copies of the nodes: the ray's direction
+// signs pick the copy whose near and far slabs are already chosen, so a child
+// test is 6 FMA and 6 min/max instead of 6 FMA and 12 min/max. The FMA is
+// monotone in the box coordinate, so every slab value, accepted box and visit
+// order equals the min/max form of closest_hit.
+template <bool kCount, int kStack>
+__device__ __forceinline__ void closest_hit_oct(const float4* __restrict__ octant_nodes, long long n_nodes,
+                                                const float4* __restrict__ tris, float3 o, float3 d, int skip,
+                                                int limit, Hit& h, unsigned& nvis, unsigned& ntri, bool& overflow)
+{
+    int stack[kStack];
+    const float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
+    const float3 oi = make_float3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
+    const int oct = (inv.x < 0.f ? 1 : 0) | (inv.y < 0.f ? 2 : 0) | (inv.z < 0.f ? 4 : 0);
+    const float4* nodes = octant_nodes + 4 * (size_t)oct * (size_t)n_nodes;
+    h.t = FLT_MAX;
+    h.k = -1;
+    h.orig = INT_MAX;
+    int sp = 0;
+    int ref = 0;
+    for (int it = 0;; ++it) {
+        if (it >= limit) {
+            overflow = true;
+            break;
+        }
+        if (ref >= 0) {
+            const float4* nd = nodes + 4 * (size_t)ref;
+            const float4 f0 = __ldg(nd), f1 = __ldg(nd + 1), f2 = __ldg(nd + 2), f3 = __ldg(nd + 3);
+            if (kCount) ++nvis;
+            const float tmax = h.t;
+            const float an = fmaxf(fmaxf(fmaf(f0.x, inv.x, -oi.x), fmaf(f0.y, inv.y, -oi.y)),
+                                   fmaxf(fmaf(f0.z, inv.z, -oi.z), 0.f));
+            const float af = fminf(fminf(fmaf(f1.z, inv.x, -oi.x), fmaf(f1.w, inv.y, -oi.y)),
+                                   fminf(fmaf(f2.x, inv.z, -oi.z), tmax));
+            const float bn = fmaxf(fmaxf(fmaf(f0.w, inv.x, -oi.x), fmaf(f1.x, inv.y, -oi.y)),
+                                   fmaxf(fmaf(f1.y, inv.z, -oi.z), 0.f));
+            const float bf = fminf(fminf(fmaf(f2.y, inv.x, -oi.x), fmaf(f2.z, inv.y, -oi.y)),
+                                   fminf(fmaf(f2.w, inv.z, -oi.z), tmax));
+            const int lref = __float_as_int(f3.x), rref = __float_as_int(f3.y);
+            const bool hl = an <= af * kBoxGrow;
+            const bool hr = bn <= bf * kBoxGrow;
+            if (hl && hr) {
+                const bool lnear = an <= bn;
+                if (sp < kStack) stack[sp++] = lnear ? rref : lref;
+                else overflow = true;
+                ref = lnear ? lref : rref;
+                continue;
+            }
+            if (hl) { ref = lref; continue; }
+            if (hr) { ref = rref; continue; }
+        } else {
+            leaf_test<kCount>(tris, ref, o, d, skip, h, ntri);
+        }
+        if (sp == 0) break;
+        ref = stack[--sp];
+    }
+}
+
 // 4-wide variant: the near and far slab of each axis are chosen once per ray
 // from the sign of its direction, which gives the same FP32 values as the
 // per-axis min / max of the binary test (the fused product is monotone in the
@@ -570,6 +628,8 @@ __device__ __forceinline__ bool rx_visible(const TraceArgs& a, const AngleDev& A
     Hit h;
     unsigned nv = 0, nt = 0;
     if (a.wide) closest_hit4<false, 64>(a.nodes, a.tris, r.o, rx, r.last, a.visit_limit, h, nv, nt, ovf);
+    else if (a.octant)
+        closest_hit_oct<false, 64>(a.nodes, a.n_nodes, a.tris, r.o, rx, r.last, a.visit_limit, h, nv, nt, ovf);
     else closest_hit<false, 64>(a.nodes, a.tris, r.o, rx, r.last, a.visit_limit, h, nv, nt, ovf);
     ++nq;
     return h.k < 0;
@@ -650,7 +710,8 @@ __device__ __forceinline__ void flush_stats(const TraceArgs& a, unsigned q, unsi
 }
 
 // One closest-hit query per lane. kMode 0: per-lane binary traversal; 1: per-lane
-// 4-wide traversal; 2: warp-cooperative binary traversal (all 32 lanes call it).
+// 4-wide traversal; 2: warp-cooperative binary traversal (all 32 lanes call it);
+// 3: per-lane binary traversal over the octant node copies.
 template <bool kCount, int kStack, int kMode>
 __device__ __forceinline__ void query(const TraceArgs& a, bool active, float3 o, float3 d, int skip, Hit& h,
                                       unsigned& nvis, unsigned& ntri, bool& ovf)
@@ -660,6 +721,8 @@ __device__ __forceinline__ void query(const TraceArgs& a, bool active, float3 o,
                                                                 nvis, ntri, ovf);
     } else if (active) {
         if (kMode == 1) closest_hit4<kCount, kStack>(a.nodes, a.tris, o, d, skip, a.visit_limit, h, nvis, ntri, ovf);
+        else if (kMode == 3)
+            closest_hit_oct<kCount, kStack>(a.nodes, a.n_nodes, a.tris, o, d, skip, a.visit_limit, h, nvis, ntri, ovf);
         else closest_hit<kCount, kStack>(a.nodes, a.tris, o, d, skip, a.visit_limit, h, nvis, ntri, ovf);
     }
 }
@@ -898,6 +961,9 @@ cudaError_t launch_trace(const TraceArgs& a, int n_blocks, bool count_visits, in
         if (a.wide) {
             if (count_visits) k_bounce<true, 64, 1, true><<<n_blocks, kTraceThreads, 0, st>>>(a);
             else k_bounce<false, 64, 1, true><<<n_blocks, kTraceThreads, 0, st>>>(a);
+        } else if (a.octant) {
+            if (count_visits) k_bounce<true, 64, 3, true><<<n_blocks, kTraceThreads, 0, st>>>(a);
+            else k_bounce<false, 64, 3, true><<<n_blocks, kTraceThreads, 0, st>>>(a);
         } else {
             if (count_visits) k_bounce<true, 64, 0, true><<<n_blocks, kTraceThreads, 0, st>>>(a);
             else k_bounce<false, 64, 0, true><<<n_blocks, kTraceThreads, 0, st>>>(a);
@@ -906,6 +972,7 @@ cudaError_t launch_trace(const TraceArgs& a, int n_blocks, bool count_visits, in
     }
     if (a.wide) launch_trace_m<1>(a, n_blocks, count_visits, stack_depth, st);
     else if (a.packet) launch_trace_m<2>(a, n_blocks, count_visits, stack_depth, st);
+    else if (a.octant) launch_trace_m<3>(a, n_blocks, count_visits, stack_depth, st);
     else launch_trace_m<0>(a, n_blocks, count_visits, stack_depth, st);
     return cudaGetLastError();
 }

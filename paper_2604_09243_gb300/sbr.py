@@ -55,7 +55,7 @@ class TraceOpts(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("tile_w", C.c_int), ("blocks_per_sm", C.c_int), ("stack_depth", C.c_int),
                 ("chunk_rays_log2", C.c_int), ("po_item", C.c_int), ("bvh_width", C.c_int), ("packet", C.c_int),
-                ("silhouette", C.c_int)]
+                ("octant", C.c_int), ("silhouette", C.c_int)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

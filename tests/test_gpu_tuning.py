@@ -33,7 +33,8 @@ def _trace(c, case, angles, **kw):
                                      dict(stack_depth=128), dict(blocks_per_sm=1), dict(po_item=512),
                                      dict(po_item=2048), dict(chunk_rays_log2=20), dict(bvh_width=4),
                                      dict(bvh_width=4, stack_depth=32, tile_w=4), dict(packet=1),
-                                     dict(packet=1, stack_depth=32, tile_w=32), dict(silhouette=1),
+                                     dict(packet=1, stack_depth=32, tile_w=32), dict(silhouette=1), dict(octant=1),
+                                     dict(octant=1, stack_depth=32, tile_w=16),
                                      dict(silhouette=1, bvh_width=4, tile_w=16)])
 def test_setting_keeps_hits_and_fields(G, tri_case, setting):
     case = tri_case
@@ -64,7 +65,7 @@ def test_bad_settings_refused(G):
         for bad in (dict(tile_w=3), dict(tile_w=64), dict(blocks_per_sm=0), dict(blocks_per_sm=5),
                     dict(stack_depth=48), dict(po_item=300), dict(chunk_rays_log2=19), dict(chunk_rays_log2=28),
                     dict(bvh_width=3), dict(packet=2), dict(packet=1, bvh_width=4), dict(packet=1, stack_depth=128),
-                    dict(silhouette=2)):
+                    dict(silhouette=2), dict(octant=1, bvh_width=4), dict(octant=1, packet=1), dict(octant=2)):
             with pytest.raises(G.SbrError):
                 c.set_tuning(**bad)
         assert c.tuning() == before
@@ -110,10 +111,10 @@ def test_wide_tree_same_hits_aircraft(G):
     case = S.aircraft_case(1e9, n_az=360)
     angles = case["angles"][[0, 90, 180, 270]]
     out = []
-    for w, pk in ((2, 0), (4, 0), (2, 1)):
+    for w, pk, oc in ((2, 0, 0), (4, 0, 0), (2, 1, 0), (2, 0, 1)):
         with G.Context(0) as c:
             c.load_mesh(case["xyz"], case["tri"])
-            c.set_tuning(bvh_width=w, packet=pk)
+            c.set_tuning(bvh_width=w, packet=pk, octant=oc)
             st = c.trace(angles, case["spacing"], eta=case["eta"], max_bounces=case["max_bounces"],
                          offset=case["offset"], flags=G.TRACE_RECORD_HITS | G.TRACE_COUNT_VISITS)
             out.append((st, [c.get_hits(a) for a in range(len(angles))], c.po_integrate([1e9])[1]))
