@@ -48,15 +48,20 @@ __device__ __forceinline__ void phase_cs(const PoArgs& a, float4 fq, double kd, 
 }
 
 // kPoPer records per thread: items of kPoPer * kPoThreads records
-template <int kPoPer>
+// kPoPer records per thread (items of kPoPer * kPoThreads records) and room for
+// kPol polarisations (2 or 4). Every block reduction carries 8 sums: two
+// frequencies at a time when kPol = 2, one when kPol = 4. Each sum is formed
+// in the same order whatever kPol, so the results do not depend on it.
+template <int kPoPer, int kPol>
 __global__ void __launch_bounds__(kPoThreads) k_po(const PoArgs a)
 {
+    constexpr int kF = 4 / kPol;  // frequencies per block reduction
     __shared__ float s_red[kWarps][8];
     const int n_items = a.n_items_dev ? *a.n_items_dev : a.n_items;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         const PoItem I = a.items[item];
-        float cf[kPoPer][4];
+        float cf[kPoPer][kPol];
         float lh[kPoPer], ll[kPoPer];
 #pragma unroll
         for (int k = 0; k < kPoPer; ++k) {
@@ -66,7 +71,7 @@ __global__ void __launch_bounds__(kPoThreads) k_po(const PoArgs a)
                 const float4 x = __ldg(p), y = __ldg(p + 1);
                 const float cv[5] = {x.x, x.y, x.z, x.w, y.x};
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
+                for (int q = 0; q < kPol; ++q) {
                     const int sel = a.pol_sel[q];
                     float v = 0.f;
                     if (q < a.n_pol) v = a.scalar ? (sel < 2 ? cv[4] : 0.f) : cv[sel];
@@ -76,45 +81,48 @@ __global__ void __launch_bounds__(kPoThreads) k_po(const PoArgs a)
                 ll[k] = y.z;
             } else {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) cf[k][q] = 0.f;
+                for (int q = 0; q < kPol; ++q) cf[k][q] = 0.f;
                 lh[k] = 0.f;
                 ll[k] = 0.f;
             }
         }
-        for (int fi = 0; fi < I.nf; ++fi) {
-            const float4 fq = a.freq[I.f0 + fi];
-            const double kd = a.kfreq[I.f0 + fi];
-            float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int f0 = 0; f0 < I.nf; f0 += kF) {
+            float acc[8];
 #pragma unroll
-            for (int k = 0; k < kPoPer; ++k) {
-                if (k * kPoThreads + tid >= I.count) break;
-                float c, s;
-                phase_cs(a, fq, kd, lh[k], ll[k], c, s);
+            for (int v = 0; v < 8; ++v) acc[v] = 0.f;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    re[q] = fmaf(cf[k][q], c, re[q]);
-                    im[q] = fmaf(-cf[k][q], s, im[q]);
+            for (int fj = 0; fj < kF; ++fj) {
+                if (f0 + fj >= I.nf) break;
+                const float4 fq = a.freq[I.f0 + f0 + fj];
+                const double kd = a.kfreq[I.f0 + f0 + fj];
+#pragma unroll
+                for (int k = 0; k < kPoPer; ++k) {
+                    if (k * kPoThreads + tid >= I.count) break;
+                    float c, s;
+                    phase_cs(a, fq, kd, lh[k], ll[k], c, s);
+#pragma unroll
+                    for (int q = 0; q < kPol; ++q) {
+                        acc[(fj * kPol + q) * 2] = fmaf(cf[k][q], c, acc[(fj * kPol + q) * 2]);
+                        acc[(fj * kPol + q) * 2 + 1] = fmaf(-cf[k][q], s, acc[(fj * kPol + q) * 2 + 1]);
+                    }
                 }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    re[q] += __shfl_xor_sync(0xffffffffu, re[q], o);
-                    im[q] += __shfl_xor_sync(0xffffffffu, im[q], o);
-                }
+                for (int v = 0; v < 8; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
             if (lane == 0)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    s_red[w][2 * q] = re[q];
-                    s_red[w][2 * q + 1] = im[q];
-                }
+                for (int v = 0; v < 8; ++v) s_red[w][v] = acc[v];
             __syncthreads();
-            if (tid < 2 * a.n_pol) {
-                float v = 0.f;
+            if (tid < 8) {
+                const int fj = tid / (2 * kPol), r = tid - fj * (2 * kPol);  // r = 2 q + (0 re, 1 im)
+                if (f0 + fj < I.nf && r < 2 * a.n_pol) {
+                    float v = 0.f;
 #pragma unroll
-                for (int k = 0; k < kWarps; ++k) v += s_red[k][tid];
-                a.partial[I.part + (size_t)fi * (2 * a.n_pol) + tid] = (double)v;
+                    for (int k = 0; k < kWarps; ++k) v += s_red[k][tid];
+                    a.partial[I.part + (size_t)(f0 + fj) * (2 * a.n_pol) + r] = (double)v;
+                }
             }
             __syncthreads();
         }
@@ -233,10 +241,19 @@ cudaError_t launch_po(const PoArgs& a, cudaStream_t st, int n_blocks)
     const int grid = n_blocks > 0 ? n_blocks : a.n_items;
     if (grid <= 0) return cudaSuccess;
     const int per = (a.item_records > 0 ? a.item_records : kPoItemRecords) / kPoThreads;
-    if (per == 2) k_po<2><<<grid, kPoThreads, 0, st>>>(a);
-    else if (per == 8) k_po<8><<<grid, kPoThreads, 0, st>>>(a);
-    else if (per == 4) k_po<4><<<grid, kPoThreads, 0, st>>>(a);
-    else return cudaErrorInvalidValue;
+    const bool two = a.n_pol <= 2;
+    if (per == 2) {
+        if (two) k_po<2, 2><<<grid, kPoThreads, 0, st>>>(a);
+        else k_po<2, 4><<<grid, kPoThreads, 0, st>>>(a);
+    } else if (per == 8) {
+        if (two) k_po<8, 2><<<grid, kPoThreads, 0, st>>>(a);
+        else k_po<8, 4><<<grid, kPoThreads, 0, st>>>(a);
+    } else if (per == 4) {
+        if (two) k_po<4, 2><<<grid, kPoThreads, 0, st>>>(a);
+        else k_po<4, 4><<<grid, kPoThreads, 0, st>>>(a);
+    } else {
+        return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
