@@ -524,6 +524,53 @@ def run_surrogate(args, ws, rank, local, pg):
                           "roofline": head["lattice_roofline"], "surrogate": res}))
 
 
+def run_gemm(args, ws, rank, local, pg):
+    """The surrogate's tensor-core GEMM alone (C = A B^T, BF16 in, FP32 out) on its layer shapes:
+    K = 512 hidden layers and K = 256 first layer, M = batch rows. Device time per GEMM from CUDA events
+    over args.steps launches after args.warmup, inputs resident (they fit in L2, as in training)."""
+    import torch
+    import paper_2604_09243_gb300 as G
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "no CPU counterpart of the tensor-core GEMM"}))
+        return
+    torch.cuda.set_device(local)
+    pk, src = peaks()
+    peak = pk.get("bf16_tflops", 1900.0)
+    res = []
+    # sbr_gemm_bf16_tn synchronises after each launch, so the per-call time includes that round trip (a few
+    # microseconds); the large shapes amortise it
+    for M, N, K in ((2048, 512, 512), (8192, 512, 512), (8192, 512, 256), (32768, 512, 512), (65536, 512, 512),
+                    (131072, 512, 512)):
+        g = torch.Generator(device="cpu").manual_seed(M + K)
+        A = torch.randn(M, K, generator=g).to(torch.bfloat16).cuda()
+        B = torch.randn(N, K, generator=g).to(torch.bfloat16).cuda()
+        C = torch.empty(M, N, dtype=torch.float32, device="cuda")
+        for _ in range(args.warmup):
+            G.gemm_bf16_tn(A.data_ptr(), K, B.data_ptr(), K, M, N, K, C.data_ptr(), N)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            G.gemm_bf16_tn(A.data_ptr(), K, B.data_ptr(), K, M, N, K, C.data_ptr(), N)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        tf = 2.0 * M * N * K / (ms * 1e-3) / 1e12
+        res.append({"M": M, "N": N, "K": K, "us": ms * 1e3, "tflops": tf, "frac": tf / peak})
+    top = res[-1]
+    if rank == 0:
+        print(json.dumps({"metric": "BF16 GEMM TFLOP/s (surrogate layer shapes)", "value": top["tflops"] * ws,
+                          "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+                          "data": "synthetic", "config": {"workload": "surrogate_gemm", "shapes": "M x 512 x K"},
+                          "roofline": {"bound": "tensor", "kernel": "k_gemm_tn (tcgen05)", "achieved": top["tflops"],
+                                       "peak": peak, "unit": "TFLOP/s", "frac": top["frac"], "traffic": None,
+                                       "peak_source": f"bf16 dense GEMM burst, {src}"},
+                          "shapes": res}))
+
+
 def run_sbr(args, case, ws, rank, local, pg):
     import torch
 
@@ -683,7 +730,7 @@ def main():
     ap.add_argument("--impl", default="sbr", choices=["sbr", "reference"])
     ap.add_argument("--workload", default="trihedral",
                     choices=["trihedral", "sphere", "aircraft1", "aircraft3", "aircraft10", "aircraft3deep",
-                             "surrogate"])
+                             "surrogate", "gemm"])
     ap.add_argument("--ref-angles", type=int, default=24)
     ap.add_argument("--batch-requests", type=int, default=256,
                     help="mixed requests for the batched-vs-plain comparison (0 = skip)")
@@ -700,6 +747,11 @@ def main():
     ap.add_argument("--sur-epochs", type=int, default=60)
     args = ap.parse_args()
     ws, rank, local, pg = dist_setup()
+    if args.workload == "gemm":
+        run_gemm(args, ws, rank, local, pg)
+        if pg is not None:
+            pg.destroy_process_group()
+        return
     if args.workload == "surrogate":
         run_surrogate(args, ws, rank, local, pg)
         if pg is not None:

@@ -6,7 +6,7 @@
 // 128-wide grid would leave SMs idle):
 //   - warp 0 (one lane) streams 128 x 64 tiles of A and BN x 64 tiles of B
 //     into shared memory with TMA (cp.async.bulk.tensor, 128-byte swizzle)
-//     through a 4-stage ring of mbarriers, refilling a stage once the MMAs
+//     through a 3-stage ring of mbarriers, refilling a stage once the MMAs
 //     that read it have completed;
 //   - warp 1 (one lane) issues tcgen05.mma (M = 128, N = BN, K = 16 per
 //     instruction, 4 per stage) as soon as a stage lands and commits each
@@ -32,7 +32,7 @@ namespace sbr {
 
 namespace {
 
-constexpr int kBM = 128, kBK = 64, kStages = 4;
+constexpr int kBM = 128, kBK = 64, kStages = 3;  // 3 stages keep a CTA at ~103 KB: two per SM
 constexpr int kTileA = kBM * kBK * 2;  // bytes
 constexpr unsigned kSpin = 1u << 24;  // try_wait rounds before a wait gives up
 template <int BN>
@@ -125,7 +125,7 @@ __device__ __forceinline__ float gelu_grad(float z)
 }
 
 template <int BN>
-__global__ void __launch_bounds__(128, 1) k_gemm_tn(const __grid_constant__ CUtensorMap tmA,
+__global__ void __launch_bounds__(128, 2) k_gemm_tn(const __grid_constant__ CUtensorMap tmA,
                                                     const __grid_constant__ CUtensorMap tmB, const GemmEpi ep, int K,
                                                     int* err)
 {
