@@ -130,6 +130,27 @@ def test_full_size_sampled_rays(G, ctx, orc):
         assert_hit_parity(s)
 
 
+def test_aircraft_10ghz_full_grid_sampled_rays(G, ctx, orc):
+    """The aircraft at 10 GHz: full lambda/10 ray grids (about 12 M primary rays per aspect, up to 10 bounces) traced in the
+    configuration the autotuner picks for the aircraft (4-wide tree, 32 x 1 ray tiles); sampled rays checked one
+    by one against the oracle."""
+    case = S.aircraft_case(10e9, n_az=360)
+    ctx.load_mesh(case["xyz"], case["tri"])
+    om = orc.Mesh(case["xyz"], case["tri"])
+    ctx.set_tuning(bvh_width=4, tile_w=32)
+    ang = case["angles"][[0, 200]]
+    st = ctx.trace(ang, case["spacing"], eta=case["eta"], max_bounces=case["max_bounces"], flags=HITS,
+                   offset=case["offset"])
+    assert st["stack_overflows"] == 0 and st["rays_launched"] > 20_000_000
+    rng = np.random.default_rng(10)
+    for a, (az, el) in enumerate(ang):
+        fr = orc.make_frame(om.bbox, az, el, case["spacing"], eta=case["eta"], offset=case["offset"])
+        ids = rng.choice(fr.n_rays, 3000, replace=False)
+        o = orc.trace(om, fr, case["max_bounces"], ids=ids)
+        assert_hit_parity(compare_hits(*ctx.get_hits(a), o, ids=ids))
+    ctx.set_tuning(bvh_width=2, tile_w=8)
+
+
 # ----------------------------------------------------------------------------- closed forms
 def test_flat_plate_and_dihedral_closed_forms(G, ctx, orc):
     xyz, tri = S.square_plate(1.0, 4)
