@@ -141,7 +141,10 @@ const char* sbr_last_error(const sbr_ctx* ctx);
  * caller, no file I/O). xyz: float32 [n_vert][3] metres; tri: int32 [n_tri][3]
  * vertex indices. on_device = 0: host pointers; 1: device pointers on the
  * context's device. The data are copied; the caller keeps ownership. Indices
- * outside [0, n_vert) give SBR_ERR_ARG. Replaces any previous mesh and drops
+ * outside [0, n_vert) and non-finite vertex coordinates give SBR_ERR_ARG. A
+ * degenerate triangle, |e1 x e2|^2 <= 2^-40 |e1|^2 |e2|^2 in FP32 (repeated or
+ * collinear vertices, slivers whose edge angle has a sine of at most 2^-20),
+ * stays in the mesh but takes no hits. Replaces any previous mesh and drops
  * the trace results; it also computes the scene box and builds a BVH with the
  * default options (sbr_build_bvh rebuilds it with others). Synchronises. */
 int sbr_load_mesh(sbr_ctx* ctx, const float* xyz, int64_t n_vert, const int32_t* tri, int64_t n_tri,

@@ -77,6 +77,8 @@ def lib():
         L.orc_mesh_free.restype = None
         L.orc_mesh_bbox.argtypes = [C.c_void_p, P(C.c_float)]
         L.orc_mesh_bbox.restype = None
+        L.orc_mesh_n_degenerate.argtypes = [C.c_void_p]
+        L.orc_mesh_n_degenerate.restype = C.c_int64
         L.orc_mesh_build_bvh.argtypes = [C.c_void_p, C.c_int]
         L.orc_mesh_build_bvh.restype = C.c_int
         L.orc_mesh_bvh_nodes.argtypes = [C.c_void_p]
@@ -137,7 +139,7 @@ class Mesh:
         h = lib().orc_mesh_create(_ptr(self.xyz, C.c_float), len(self.xyz), _ptr(self.tri, C.c_int32),
                                   len(self.tri))
         if not h:
-            raise ValueError("orc_mesh_create failed (bad indices?)")
+            raise ValueError("orc_mesh_create failed (bad indices or non-finite coordinates)")
         self._h = h
         self.has_bvh = False
         if bvh_leaf:
@@ -157,6 +159,11 @@ class Mesh:
         if lib().orc_mesh_build_bvh(self._h, int(leaf)) != 0:
             raise ValueError("bvh build failed")
         self.has_bvh = True
+
+    @property
+    def n_degenerate(self) -> int:
+        """Triangles that take no hits: sine of the FP32 edge angle at most 2^-20."""
+        return int(lib().orc_mesh_n_degenerate(self._h))
 
     @property
     def bvh_nodes(self) -> int:

@@ -206,6 +206,7 @@ typedef struct {
     float* v0f;  /* [nt][3] FP32 vertex 0 */
     float* e1f;  /* [nt][3] FP32 edge v1 - v0 (rounded) */
     float* e2f;  /* [nt][3] FP32 edge v2 - v0 (rounded) */
+    unsigned char* deg; /* [nt] 1: the FP32 normal e1f x e2f has zero squared length, no hits */
     float bbox[6];
     orc_node* nodes;
     int64_t n_nodes, cap_nodes;
@@ -217,14 +218,26 @@ void orc_mesh_free(orc_mesh* m)
 {
     if (!m) return;
     free(m->v0); free(m->e1); free(m->e2); free(m->nrm); free(m->cen); free(m->tlo); free(m->thi);
-    free(m->v0f); free(m->e1f); free(m->e2f);
+    free(m->v0f); free(m->e1f); free(m->e2f); free(m->deg);
     free(m->nodes); free(m->order);
     free(m);
 }
 
+static void cross32(const float* a, const float* b, float* c);
+static float dot32(const float* a, const float* b);
+
+/* Refuses bad indices and non-finite coordinates (NULL). A degenerate
+ * triangle is kept but takes no hits: in the written FP32 order,
+ * |e1 x e2|^2 <= (2^-20 |e1|^2)(2^-20 |e2|^2), so the sine of the angle between
+ * its edges is at most 2^-20 and the rounding of the cross product (about
+ * 2^-24 |e1||e2|) is over 6 % of its length; repeated or collinear vertices
+ * give zero. The paper assumes a valid surface mesh; such a triangle has no
+ * usable normal to reflect about. */
 orc_mesh* orc_mesh_create(const float* xyz, int64_t nv, const int32_t* tri, int64_t nt)
 {
     if (!xyz || !tri || nt < 1 || nv < 3) return NULL;
+    for (int64_t i = 0; i < 3 * nv; ++i)
+        if (!isfinite(xyz[i])) return NULL;
     orc_mesh* m = (orc_mesh*)calloc(1, sizeof(orc_mesh));
     m->nt = nt;
     size_t b = sizeof(double) * 3 * (size_t)nt;
@@ -232,6 +245,7 @@ orc_mesh* orc_mesh_create(const float* xyz, int64_t nv, const int32_t* tri, int6
     m->cen = malloc(b); m->tlo = malloc(b); m->thi = malloc(b);
     size_t bf = sizeof(float) * 3 * (size_t)nt;
     m->v0f = malloc(bf); m->e1f = malloc(bf); m->e2f = malloc(bf);
+    m->deg = malloc((size_t)nt);
     for (int c = 0; c < 3; ++c) { m->bbox[c] = INFINITY; m->bbox[3 + c] = -INFINITY; }
     for (int64_t v = 0; v < nv; ++v)
         for (int c = 0; c < 3; ++c) {
@@ -267,12 +281,25 @@ orc_mesh* orc_mesh_create(const float* xyz, int64_t nv, const int32_t* tri, int6
             m->tlo[3 * k + c] -= grow;
             m->thi[3 * k + c] += grow;
         }
+        float n32[3];
+        cross32(m->e1f + 3 * k, m->e2f + 3 * k, n32);
+        {
+            const float l1 = dot32(m->e1f + 3 * k, m->e1f + 3 * k), l2 = dot32(m->e2f + 3 * k, m->e2f + 3 * k);
+            m->deg[k] = dot32(n32, n32) <= (l1 * 0x1p-20f) * (l2 * 0x1p-20f);
+        }
         double n[3];
         cross3(m->e1 + 3 * k, m->e2 + 3 * k, n);
         double ln = sqrt(dot3(n, n));
         for (int c = 0; c < 3; ++c) m->nrm[3 * k + c] = ln > 0.0 ? n[c] / ln : 0.0;
     }
     return m;
+}
+
+int64_t orc_mesh_n_degenerate(const orc_mesh* m)
+{
+    int64_t c = 0;
+    for (int64_t k = 0; m && k < m->nt; ++k) c += m->deg[k];
+    return c;
 }
 
 void orc_mesh_bbox(const orc_mesh* m, float* out)
@@ -355,6 +382,7 @@ static int tri_hit(const orc_mesh* m, int64_t k, const double* o, const double* 
 {
     const double *v0 = m->v0 + 3 * k, *e1 = m->e1 + 3 * k, *e2 = m->e2 + 3 * k;
     double p[3], q[3], s[3];
+    if (m->deg[k]) return 0;
     cross3(d, e2, p);
     double det = dot3(e1, p);
     if (det == 0.0) return 0;
@@ -391,6 +419,7 @@ static int tri_hit32(const orc_mesh* m, int64_t k, const float* o, const float* 
 {
     const float *v0 = m->v0f + 3 * k, *e1 = m->e1f + 3 * k, *e2 = m->e2f + 3 * k;
     float p[3], q[3], s[3];
+    if (m->deg[k]) return 0;
     cross32(d, e2, p);
     float det = dot32(e1, p);
     if (det == 0.0f) return 0;

@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <string>
 #include <vector>
@@ -391,6 +392,9 @@ int sbr_load_mesh(sbr_ctx* c, const float* xyz, int64_t n_vert, const int32_t* t
     if (!on_device) {
         for (int64_t i = 0; i < 3 * n_tri; ++i)
             if (tri[i] < 0 || tri[i] >= n_vert) return fail(c, SBR_ERR_ARG, "sbr_load_mesh: index %lld out of range", (long long)i);
+        for (int64_t i = 0; i < 3 * n_vert; ++i)
+            if (!std::isfinite(xyz[i]))
+                return fail(c, SBR_ERR_ARG, "sbr_load_mesh: vertex coordinate %lld is not finite", (long long)i);
     }
     CK(c->xyz.ensure(sizeof(float) * 3 * (size_t)n_vert), "alloc xyz");
     CK(c->tri.ensure(sizeof(int32_t) * 3 * (size_t)n_tri), "alloc tri");
@@ -459,7 +463,8 @@ int sbr_build_bvh(sbr_ctx* c, const sbr_bvh_opts* opt)
     CK(cudaStreamSynchronize(c->stream), "bvh build sync");
     if (herr) {
         c->has_mesh = false;
-        return fail(c, SBR_ERR_ARG, "sbr_build_bvh: triangle index out of range");
+        return fail(c, SBR_ERR_ARG, (herr & 1) ? "sbr_build_bvh: triangle index out of range"
+                                               : "sbr_build_bvh: a vertex coordinate is not finite");
     }
     memcpy(c->bbox, hb, sizeof(c->bbox));
     // 4-wide tree over the same boxes; its work queues reuse the (now free) build scratch

@@ -71,11 +71,13 @@ __device__ __forceinline__ void warp_minmax_atomic(float3 lo, float3 hi, unsigne
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_vertex_box(const float* xyz, long long nv, unsigned* acc)
+// err bit 1: a triangle index out of range; bit 2: a non-finite vertex coordinate
+__global__ void __launch_bounds__(kThreads) k_vertex_box(const float* xyz, long long nv, unsigned* acc, int* err)
 {
     float3 lo = make_float3(FLT_MAX, FLT_MAX, FLT_MAX), hi = make_float3(-FLT_MAX, -FLT_MAX, -FLT_MAX);
     for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv; v += (long long)gridDim.x * blockDim.x) {
         float x = xyz[3 * v], y = xyz[3 * v + 1], z = xyz[3 * v + 2];
+        if (!isfinite(x) || !isfinite(y) || !isfinite(z)) atomicOr(err, 2);
         lo = make_float3(fminf(lo.x, x), fminf(lo.y, y), fminf(lo.z, z));
         hi = make_float3(fmaxf(hi.x, x), fmaxf(hi.y, y), fmaxf(hi.z, z));
     }
@@ -88,13 +90,18 @@ __global__ void __launch_bounds__(kThreads) k_prep(const float* xyz, const int* 
     float3 lo = make_float3(FLT_MAX, FLT_MAX, FLT_MAX), hi = make_float3(-FLT_MAX, -FLT_MAX, -FLT_MAX);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int ia = tri[3 * (long long)i], ib = tri[3 * (long long)i + 1], ic = tri[3 * (long long)i + 2];
-        if (ia < 0 || ib < 0 || ic < 0 || ia >= nv || ib >= nv || ic >= nv) {
-            *err = 1;
+        const bool bad = ia < 0 || ib < 0 || ic < 0 || ia >= nv || ib >= nv || ic >= nv;
+        if (bad) {
+            atomicOr(err, 1);
             ia = ib = ic = 0;
         }
         float3 a = make_float3(xyz[3 * (long long)ia], xyz[3 * (long long)ia + 1], xyz[3 * (long long)ia + 2]);
         float3 b = make_float3(xyz[3 * (long long)ib], xyz[3 * (long long)ib + 1], xyz[3 * (long long)ib + 2]);
         float3 c = make_float3(xyz[3 * (long long)ic], xyz[3 * (long long)ic + 1], xyz[3 * (long long)ic + 2]);
+        // a refused mesh (bad index, non-finite vertex: flagged above and in
+        // k_vertex_box) still completes its build with finite boxes
+        if (bad || !isfinite(a.x + a.y + a.z + b.x + b.y + b.z + c.x + c.y + c.z))
+            a = b = c = make_float3(0.f, 0.f, 0.f);
         float3 bl = make_float3(fminf(a.x, fminf(b.x, c.x)), fminf(a.y, fminf(b.y, c.y)), fminf(a.z, fminf(b.z, c.z)));
         float3 bh = make_float3(fmaxf(a.x, fmaxf(b.x, c.x)), fmaxf(a.y, fmaxf(b.y, c.y)), fmaxf(a.z, fmaxf(b.z, c.z)));
         // the FP32 triangle test accepts hits up to its slack (2^-12 of the
@@ -371,9 +378,25 @@ __global__ void __launch_bounds__(kThreads) k_reorder(const float* xyz, const in
     float ax = xyz[3 * (long long)ia], ay = xyz[3 * (long long)ia + 1], az = xyz[3 * (long long)ia + 2];
     float bx = xyz[3 * (long long)ib], by = xyz[3 * (long long)ib + 1], bz = xyz[3 * (long long)ib + 2];
     float cx = xyz[3 * (long long)ic], cy = xyz[3 * (long long)ic + 1], cz = xyz[3 * (long long)ic + 2];
+    float4 e1 = make_float4(__fsub_rn(bx, ax), __fsub_rn(by, ay), __fsub_rn(bz, az), 0.f);
+    float4 e2 = make_float4(__fsub_rn(cx, ax), __fsub_rn(cy, ay), __fsub_rn(cz, az), 0.f);
+    // Degenerate triangle: |e1 x e2|^2 <= (2^-20 |e1|^2)(2^-20 |e2|^2), i.e. the
+    // sine of the angle between its edges is at most 2^-20, where the FP32
+    // rounding of e1 x e2 (about 2^-24 |e1||e2|) exceeds 6 % of its length and
+    // the normal is mostly noise (repeated or collinear vertices give 0). It
+    // takes no hits: zero edges make the determinant of every test exactly 0.
+    // Written FP32 order of the hit normal: cross = fma(a.y, b.z, -(a.z b.y))
+    // and cyclic, dot = fma(a.x, b.x, fma(a.y, b.y, a.z b.z)).
+    const float nx = __fmaf_rn(e1.y, e2.z, -__fmul_rn(e1.z, e2.y));
+    const float ny = __fmaf_rn(e1.z, e2.x, -__fmul_rn(e1.x, e2.z));
+    const float nz = __fmaf_rn(e1.x, e2.y, -__fmul_rn(e1.y, e2.x));
+    const float nn = __fmaf_rn(nx, nx, __fmaf_rn(ny, ny, __fmul_rn(nz, nz)));
+    const float l1 = __fmaf_rn(e1.x, e1.x, __fmaf_rn(e1.y, e1.y, __fmul_rn(e1.z, e1.z)));
+    const float l2 = __fmaf_rn(e2.x, e2.x, __fmaf_rn(e2.y, e2.y, __fmul_rn(e2.z, e2.z)));
+    if (nn <= __fmul_rn(__fmul_rn(l1, 0x1p-20f), __fmul_rn(l2, 0x1p-20f))) e1 = e2 = make_float4(0.f, 0.f, 0.f, 0.f);
     tris[3 * p + 0] = make_float4(ax, ay, az, __int_as_float((int)t));
-    tris[3 * p + 1] = make_float4(bx - ax, by - ay, bz - az, 0.f);
-    tris[3 * p + 2] = make_float4(cx - ax, cy - ay, cz - az, 0.f);
+    tris[3 * p + 1] = e1;
+    tris[3 * p + 2] = e2;
 }
 
 // ---------------------------------------------------------------- PLOC builder
@@ -772,7 +795,7 @@ cudaError_t bvh_build(const BvhBuild& b, cudaStream_t st)
     k_acc_init<<<1, 32, 0, st>>>(acc, b.err_flag);
     int gv = (int)((b.n_vert + kThreads - 1) / kThreads);
     if (gv > 4096) gv = 4096;
-    k_vertex_box<<<gv, kThreads, 0, st>>>(b.xyz, b.n_vert, acc);
+    k_vertex_box<<<gv, kThreads, 0, st>>>(b.xyz, b.n_vert, acc, b.err_flag);
     k_prep<<<g, kThreads, 0, st>>>(b.xyz, b.tri, b.n_vert, n, tbox, cen, acc, b.err_flag);
     k_morton<<<g, kThreads, 0, st>>>(cen, n, acc, k0, v0, b.bbox_out);
     unsigned long long *ki = k0, *ko = k1;

@@ -196,6 +196,51 @@ def test_single_and_two_triangles(G, ctx, orc):
             assert_hit_parity(compare_hits(*g, o))
 
 
+def test_degenerate_duplicate_and_non_finite_meshes(G, ctx, orc):
+    """Degenerate triangles (parallel edges within a sine of 2^-20: repeated
+    vertices, a collinear midpoint, a 5e-7 sliver), exact copies and
+    reversed-winding copies of every triangle on the trihedral (3 bounces): the
+    GPU takes every hit decision of the oracle; the degenerate ones are never
+    hit. Non-finite vertices are refused from host and device memory, and the
+    context stays usable."""
+    torch = pytest.importorskip("torch")
+    xyz0, tri0 = S.trihedral(1.0, 16)
+    a0, b0 = np.array([0.21, 0.33, 0.27], np.float32), np.array([0.62, 0.18, 0.44], np.float32)
+    mid = ((a0.astype(np.float64) + b0) / 2).astype(np.float32)
+    v = np.stack([a0, b0, mid, np.array([0.1, 0.1, 0.6], np.float32), np.array([0.9, 0.1, 0.6], np.float32),
+                  np.array([0.9, 0.1 + 4e-7, 0.6], np.float32)])
+    n = len(xyz0)
+    deg = np.array([[n, n + 1, n + 1], [n, n, n + 1], [n, n + 1, n + 2], [n + 3, n + 4, n + 5]], np.int32)
+    xyz = np.concatenate([xyz0, v])
+    nt = len(tri0)
+    tri = np.concatenate([tri0, deg, tri0, tri0[:, [0, 2, 1]]])
+    ctx.load_mesh(xyz, tri)
+    om = orc.Mesh(xyz, tri)
+    assert om.n_degenerate == len(deg)
+    ang = np.array([[45.0, 35.26], [20.0, 50.0], [71.0, 30.0]])
+    st, res = _trace_both(G, ctx, orc, om, ang, 0.006, 3)
+    E, R = ctx.po_integrate([10e9], "HH,VV")
+    for a, (g, o, fr) in enumerate(res):
+        assert_hit_parity(compare_hits(*g, o))
+        ht = g[0]
+        assert not np.any((ht >= nt) & (ht < nt + len(deg)))
+        assert np.any(ht >= 0)
+        Eo, Ro = orc.po(o["coef"], o["L"], o["valid"], [10e9])
+        assert_rcs_close(R[a, 0], Ro[0][:2])  # oracle order HH, VV, HV, VH
+    # refused meshes: host arrays, then device tensors; a valid mesh loads and traces afterwards
+    for bad in (np.nan, np.inf):
+        x = xyz0.copy()
+        x[5, 2] = bad
+        with pytest.raises(G.SbrError):
+            ctx.load_mesh(x, tri0)
+        with pytest.raises(G.SbrError):
+            ctx.load_mesh(torch.from_numpy(x).cuda(), torch.from_numpy(tri0).cuda())
+    ctx.load_mesh(xyz0, tri0)
+    om0 = orc.Mesh(xyz0, tri0)
+    st, res = _trace_both(G, ctx, orc, om0, ang[:1], 0.006, 3)
+    assert_hit_parity(compare_hits(*res[0][0], res[0][1]))
+
+
 def test_all_rays_miss_gives_empty_sum(G, ctx):
     xyz, tri = S.square_plate(1.0, 2)
     ctx.load_mesh(xyz, tri)

@@ -154,6 +154,87 @@ def test_single_triangle_hit_distance(orc):
     assert m.closest_hit([0.1, 0.0, 2.0], [0, 0, -1.0], skip=0)[0] == -1
 
 
+def _degenerate_extras(n_vert):
+    """Vertices inside the unit trihedral's box and triangles on them whose
+    edges are parallel or nearly so: repeated vertices, an exactly collinear
+    midpoint, a sliver with edge-angle sine ~5e-7 (all degenerate), plus one
+    thin but valid sliver (sine ~1e-3)."""
+    a = np.array([0.21, 0.33, 0.27], np.float32)
+    b = np.array([0.62, 0.18, 0.44], np.float32)
+    mid = ((a.astype(np.float64) + b) / 2).astype(np.float32)
+    v = np.stack([a, b, mid,
+                  np.array([0.1, 0.1, 0.6], np.float32), np.array([0.9, 0.1, 0.6], np.float32),
+                  np.array([0.9, 0.1 + 4e-7, 0.6], np.float32), np.array([0.9, 0.1008, 0.6], np.float32)])
+    n = n_vert
+    deg = np.array([[n, n + 1, n + 1], [n, n, n + 1], [n + 1, n + 1, n + 1], [n, n + 1, n + 2],
+                    [n + 3, n + 4, n + 5]], np.int32)
+    thin = np.array([[n + 3, n + 4, n + 6]], np.int32)
+    return v, deg, thin
+
+
+def test_degenerate_triangles_take_no_hits(orc):
+    """A triangle whose edges are parallel to within a sine of 2^-20 has no
+    usable FP32 normal and is never hit: a ray aimed through the inside of such
+    a sliver misses it while the same ray hits a thin but valid sliver (sine
+    ~1e-3); the ordinary meshes have no such triangle; adding degenerate
+    triangles to a mesh leaves every ray's hits, fields and path bit for bit."""
+    xyz0, tri0 = S.trihedral(1.0, 8)
+    v, deg, thin = _degenerate_extras(len(xyz0))
+    xyz = np.concatenate([xyz0, v])
+    # the sliver spans x in [0.1, 0.9] at y = 0.1 .. 0.1 + 4e-7 x' / 0.8 in the plane z = 0.6
+    for use_bvh in (True, False):
+        m = orc.Mesh(xyz, deg[4:5], bvh_leaf=4 if use_bvh else None)
+        assert m.n_degenerate == 1
+        assert m.closest_hit([0.8, 0.1 + 1e-7, 1.5], [0, 0, -1.0], use_bvh=use_bvh)[0] == -1
+        m = orc.Mesh(xyz, thin, bvh_leaf=4 if use_bvh else None)
+        assert m.n_degenerate == 0
+        k, t, _, _ = m.closest_hit([0.8, 0.1 + 1e-4, 1.5], [0, 0, -1.0], use_bvh=use_bvh)
+        assert k == 0 and t == pytest.approx(1.5 - 0.6, rel=1e-6)
+    for xyz_m, tri_m in (S.trihedral(1.0, 32), S.icosphere(4), S.square_plate(1.0, 8, tilt_deg=30.0)):
+        assert orc.Mesh(xyz_m, tri_m, bvh_leaf=None).n_degenerate == 0
+    base = orc.Mesh(xyz0, tri0)
+    more = orc.Mesh(xyz, np.concatenate([tri0, deg, thin]))
+    assert more.n_degenerate == len(deg)
+    assert np.array_equal(base.bbox, more.bbox)
+    for az, el in ((45.0, 35.26), (20.0, 50.0)):
+        fa = orc.make_frame(base.bbox, az, el, 0.01)
+        ta, tb = orc.trace(base, fa, 3), orc.trace(more, fa, 3)
+        hit_thin = np.any(tb["hit_tri"] == len(tri0) + len(deg), axis=1)
+        assert not np.any((tb["hit_tri"] >= len(tri0)) & (tb["hit_tri"] < len(tri0) + len(deg)))
+        keep = ~hit_thin
+        assert keep.sum() > 0.99 * len(keep)
+        for key in ("hit_tri", "hit_t", "nb", "valid", "coef", "L"):
+            assert np.array_equal(ta[key][keep], tb[key][keep]), key
+
+
+def test_duplicate_triangles_resolve_to_the_lower_index(orc):
+    """A copy of every triangle appended to the mesh ties with its original at
+    every hit (same FP32 edges, same t); the lower index wins, so every ray's
+    hits, fields and path equal those of the mesh without copies."""
+    xyz, tri = S.trihedral(1.0, 8)
+    base = orc.Mesh(xyz, tri)
+    dup = orc.Mesh(xyz, np.concatenate([tri, tri]))
+    for az, el in ((45.0, 35.26), (10.0, 20.0)):
+        f = orc.make_frame(base.bbox, az, el, 0.01)
+        ta, tb = orc.trace(base, f, 3), orc.trace(dup, f, 3)
+        assert ta["valid"].sum() > 1000
+        for key in ("hit_tri", "hit_t", "nb", "valid", "coef", "L"):
+            assert np.array_equal(ta[key], tb[key]), key
+
+
+def test_non_finite_vertices_refused(orc):
+    xyz, tri = S.square_plate(1.0, 2)
+    for bad in (np.nan, np.inf, -np.inf):
+        x = xyz.copy()
+        x[3, 1] = bad
+        with pytest.raises(ValueError):
+            orc.Mesh(x, tri)
+    # an unreferenced vertex counts too: it would set the scene box
+    x = np.concatenate([xyz, np.array([[0.0, np.nan, 0.0]], np.float32)])
+    with pytest.raises(ValueError):
+        orc.Mesh(x, tri)
+
+
 def test_watertight_closed_icosphere(orc):
     # every ray aimed inside the silhouette of a closed mesh must hit it
     xyz, tri = S.icosphere(4)
