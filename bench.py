@@ -52,14 +52,14 @@ OPS_NODE = 41
 OPS_NODE_OCT = 29  # binary node over the octant copies: 2 x (6 FMA + 6 min/max + 1 scale + 1 compare) + ordering
 OPS_NODE4 = 81
 OPS_TRI = 38
-# DRAM bytes of the three transport passes per launched ray of the trihedral
-# sweep (ncu dram__bytes_read.sum + dram__bytes_write.sum over k_primary and
-# both k_bounce passes, 9 of its aspects = 2,114,692 rays: 188.39 MB, captured
-# with 4 x 8 tiles on the PLOC tree), for the ray tile, traversal and builder below
-# (stack depth and chunk size leave the DRAM bytes per ray unchanged: the
-# queues and records are the traffic); it grows with the rays, so it is scaled
-# by the rays of a step.
-TRAFFIC_PER_RAY = {"trihedral": (188.39e6 / 2114692, dict(tile_w=4, bvh_width=2, packet=0, octant=0), "ploc")}
+# DRAM bytes per launched ray of the kernel the roofline describes, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum) of the trihedral sweep's
+# 9-aspect sample (2,114,692 rays) on the PLOC tree, for the setting listed:
+# with traversed primary rays, k_primary and both k_bounce passes (188.39 MB);
+# with rasterised primary hits, both k_bounce passes. Stack depth and chunk
+# size leave the bytes per ray unchanged (the queues and records are the
+# traffic); it grows with the rays, so it is scaled by the rays of a step.
+TRAFFIC_PER_RAY = {"trihedral": [(188.39e6 / 2114692, dict(tile_w=4, bvh_width=2, packet=0, octant=0, raster=0), "ploc")]}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -675,14 +675,22 @@ def run_sbr(args, case, ws, rank, local, pg):
     # --- roofline of the transport passes (FP32 issue bound)
     wide = ctx.tuning()["bvh_width"] == 4
     octant = ctx.tuning()["octant"] == 1
+    raster = ctx.tuning()["raster"] == 1
     traffic = None
-    if args.workload in TRAFFIC_PER_RAY:
-        per_ray, setting, builder = TRAFFIC_PER_RAY[args.workload]
+    for per_ray, setting, builder in TRAFFIC_PER_RAY.get(args.workload, []):
         if builder == args.builder and all(ctx.tuning()[k] == v for k, v in setting.items()):
             traffic = per_ray * stats[0]["rays_launched"]
-    ops = (OPS_NODE4 if wide else (OPS_NODE_OCT if octant else OPS_NODE)) * cnt["node_visits"] + \
-        OPS_TRI * cnt["tri_tests"]
-    pass_s = float(np.mean([s["pass_ms"] for s in stats])) / 1e3
+    pass_all_s = float(np.mean([s["pass_ms"] for s in stats])) / 1e3
+    primary_s = float(np.mean([s["primary_ms"] for s in stats])) / 1e3
+    if raster:
+        # the traversal of the bounce passes: node visits and their triangle tests over their time
+        ops = (OPS_NODE4 if wide else (OPS_NODE_OCT if octant else OPS_NODE)) * cnt["node_visits"] + \
+            OPS_TRI * (cnt["tri_tests"] - cnt["raster_tests"])
+        pass_s = pass_all_s - primary_s
+    else:
+        ops = (OPS_NODE4 if wide else (OPS_NODE_OCT if octant else OPS_NODE)) * cnt["node_visits"] + \
+            OPS_TRI * cnt["tri_tests"]
+        pass_s = pass_all_s
     pk, src = peaks()
     peak_ops = SM_COUNT * FP32_LANES_PER_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     achieved = ops / pass_s / 1e12
@@ -694,14 +702,20 @@ def run_sbr(args, case, ws, rank, local, pg):
             "angles_per_s": ws * na * args.steps / t_dev,
             "rays_launched_per_step": stats[0]["rays_launched"], "ray_bounces_per_step": bounces,
             "valid_rays_per_step": stats[0]["valid_rays"],
-            "roofline": {"bound": "alu", "kernel": "k_primary+k_bounce (transport passes, "
-                                                   f"{'4-wide' if wide else ('binary, octant copies' if octant else 'binary')} tree)",
+            "roofline": {"bound": "alu", "kernel": ("k_bounce (bounce passes" if raster else
+                                                    "k_primary+k_bounce (transport passes") +
+                         f", {'4-wide' if wide else ('binary, octant copies' if octant else 'binary')} tree)",
                          "achieved": achieved, "peak": peak_ops, "unit": "T FP32-op/s",
                          "frac": achieved / peak_ops, "traffic": traffic,
                          "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                         f"{pk.get('sm_max_mhz', 2070.0):g} MHz ({src} SM clock)",
-                         "ops_per_step": ops, "node_visits": cnt["node_visits"], "tri_tests": cnt["tri_tests"],
+                         "ops_per_step": ops, "node_visits": cnt["node_visits"],
+                         "tri_tests": cnt["tri_tests"] - (cnt["raster_tests"] if raster else 0),
                          "pass_ms_per_step": pass_s * 1e3},
+            "primary": {"kernel": "k_raster+k_vis_mask+k_primary_vis (rasterised primary hits)" if raster else
+                        "k_primary (traversed)", "ms_per_step": primary_s * 1e3,
+                        "transport_ms_per_step": pass_all_s * 1e3, "raster_tests": cnt["raster_tests"],
+                        "raster_tests_per_s": cnt["raster_tests"] / primary_s if raster and primary_s > 0 else None},
             "e2e": {"value": e2e_value, "unit": "ray-bounces/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * t_e2e / args.steps},
             "gpu_launches": int(launches * args.steps),

@@ -104,6 +104,10 @@ typedef struct {
     int64_t kernel_launches; /* CUDA kernels this call enqueued */
     int64_t pass_launches;   /* transport-pass kernels among them (primary and bounce passes) */
     double pass_ms;          /* with SBR_TRACE_TIME_PASSES: summed device time of those passes */
+    int64_t raster_tests;    /* only with SBR_TRACE_COUNT_VISITS: triangle tests of the rasterised primary hits
+                                (included in tri_tests) */
+    double primary_ms;       /* with SBR_TRACE_TIME_PASSES: the part of pass_ms spent in primary passes
+                                (rasterisation included) */
 } sbr_trace_stats;
 
 /* Per-aspect ray grid (Eq. L1-L3) exactly as sbr_trace generates it. */
@@ -299,6 +303,11 @@ typedef struct {
     int silhouette;      /* 1: before the primary pass, rasterise every triangle's widened projection onto
                             the ray grid and skip the query of rays outside all of them (sure misses: no
                             hit, not counted as ray-bounces); default 0 */
+    int raster;          /* 1: find the primary hits by rasterisation instead of traversal: every triangle
+                            runs the FP32 test for each grid ray of its widened projected box and a 64-bit
+                            atomic minimum of (t, original index) keeps the closest hit, so the hits are
+                            those of the traversal; an aspect with a triangle spanning more than 2^14 grid
+                            cells traverses instead. The silhouette mask is then not used. Default 1 */
 } sbr_tuning;
 int sbr_get_tuning(const sbr_ctx* ctx, sbr_tuning* out);
 /* SBR_ERR_ARG for a value outside the ranges above. */

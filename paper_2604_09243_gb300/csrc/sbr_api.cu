@@ -95,6 +95,7 @@ struct sbr_ctx {
     // trace
     DevBuf angles, rayoff, mask, tilebase, scan_scr, recoff, q0, q1, ctr64, ctr32, stats, rec, cover;
     DevBuf hit_tri, hit_t, hit_nb;
+    DevBuf tripos, vis, visfull;  // position of each original triangle; raster keys and per-aspect flags
     long long rec_total = 0;
     int max_bounces = 0, trace_flags = 0;
     bool has_trace = false;
@@ -236,6 +237,7 @@ AngleDev to_dev(const sbr_ray_grid& g, long long ray_off, int tw, const double* 
         d.hhat[k] = (float)g.hhat[k];
     }
     d.dA = (float)(g.spacing * g.spacing);
+    d.ids = 1.f / sqrtf(d.dA);
     d.eps = (float)g.eps;
     d.nu = (int)g.nu;
     d.nv = (int)g.nv;
@@ -285,7 +287,8 @@ bool tuning_ok(const sbr_tuning& t)
     const bool tile = t.tile_w >= 1 && t.tile_w <= 32 && (t.tile_w & (t.tile_w - 1)) == 0;
     const bool trav = (t.packet == 0 || (t.packet == 1 && t.bvh_width == 2 && t.stack_depth <= 64)) &&
                       (t.silhouette == 0 || t.silhouette == 1) &&
-                      (t.octant == 0 || (t.octant == 1 && t.bvh_width == 2 && t.packet == 0));
+                      (t.octant == 0 || (t.octant == 1 && t.bvh_width == 2 && t.packet == 0)) &&
+                      (t.raster == 0 || t.raster == 1);
     return tile && trav && (t.bvh_width == 2 || t.bvh_width == 4) && t.blocks_per_sm >= 1 && t.blocks_per_sm <= 4 &&
            (t.stack_depth == 32 || t.stack_depth == 64 || t.stack_depth == 128) && t.chunk_rays_log2 >= 20 &&
            t.chunk_rays_log2 <= 27 && (t.po_item == 512 || t.po_item == 1024 || t.po_item == 2048);
@@ -358,6 +361,7 @@ int sbr_create(sbr_ctx** out, int device, void* cuda_stream)
     c->tune.packet = 0;
     c->tune.silhouette = 0;
     c->tune.octant = 0;
+    c->tune.raster = 1;
     *out = c;
     return SBR_OK;
 }
@@ -435,6 +439,7 @@ int sbr_build_bvh(sbr_ctx* c, const sbr_bvh_opts* opt)
     c->n_nodes = n_nodes;
     CK(c->nodes.ensure(sizeof(float4) * 4 * (size_t)n_nodes), "alloc nodes");
     CK(c->tris.ensure(sizeof(float4) * 3 * (size_t)n), "alloc tris");
+    CK(c->tripos.ensure(sizeof(int) * (size_t)n), "alloc triangle positions");
     size_t sb = bvh_scratch_bytes(n);
     CK(c->bvh_scratch.ensure(sb), "alloc bvh scratch");
     CK(c->bbox_dev.ensure(sizeof(float) * 8), "alloc bbox");
@@ -451,6 +456,7 @@ int sbr_build_bvh(sbr_ctx* c, const sbr_bvh_opts* opt)
     b.radius = radius;
     b.nodes = c->nodes.as<float4>();
     b.tris = c->tris.as<float4>();
+    b.tri_pos = c->tripos.as<int>();
     b.bbox_out = c->bbox_dev.as<float>();
     b.err_flag = c->err_dev.as<int>();
     b.scratch = c->bvh_scratch.p;
@@ -513,6 +519,7 @@ struct TraceRun {
     int n_blocks = 0;
     int64_t n_launch = 0, n_pass = 0;
     size_t n_ev = 0;
+    std::vector<char> ev_primary;  // per timed pass: 1 for a primary pass
 };
 
 // Lay out the aspects c->ang[0..n) (grids filled) in processing order, cut them
@@ -555,6 +562,10 @@ int plan_chunks(sbr_ctx* c, TraceRun& R, std::vector<int64_t>& cut, long long* t
     CK(c->recoff.ensure(sizeof(unsigned) * (size_t)(max_angles + 1)), "alloc record offsets");
     CK(c->mask.ensure(sizeof(unsigned) * (size_t)max_tiles), "alloc mask");
     if (c->tune.silhouette) CK(c->cover.ensure(sizeof(unsigned) * (size_t)(max_tiles + max_angles)), "alloc cover");
+    if (c->tune.raster) {
+        CK(c->vis.ensure(sizeof(unsigned long long) * (size_t)max_chunk), "alloc raster keys");
+        CK(c->visfull.ensure(sizeof(unsigned) * (size_t)(max_angles + 1)), "alloc raster flags");
+    }
     CK(c->tilebase.ensure(sizeof(unsigned) * (size_t)max_tiles), "alloc tile base");
     CK(c->scan_scr.ensure(scan_scratch_bytes(max_tiles)), "alloc scan scratch");
     CK(c->q0.ensure(sizeof(RayState) * (size_t)max_chunk), "alloc ray queue");
@@ -609,6 +620,7 @@ int trace_chunk(sbr_ctx* c, TraceRun& R, int64_t a0, int64_t a1, long long rec_b
                                  tiled_rays(c->ang[(size_t)a1 - 1].grid, c->ang[(size_t)a1 - 1].tw) - base;
     unsigned* q_count = c->ctr32.as<unsigned>();
     unsigned* total_dev = q_count + 2 * (kMaxBounces + 2);
+    // a transport pass; the primary pass includes the rasterisation of its hits
     auto pass = [&](const TraceArgs& t) -> cudaError_t {
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (R.timed) {
@@ -616,9 +628,16 @@ int trace_chunk(sbr_ctx* c, TraceRun& R, int64_t a0, int64_t a1, long long rec_b
             e1 = pool_event(c, R.n_ev + 1);
             if (!e0 || !e1) return cudaErrorMemoryAllocation;
             R.n_ev += 2;
+            R.ev_primary.push_back(t.bounce == 0 ? 1 : 0);
             cudaEventRecord(e0, c->stream);
         }
-        cudaError_t e = launch_trace(t, R.n_blocks, R.count, c->tune.stack_depth, c->stream);
+        cudaError_t e = cudaSuccess;
+        if (t.vis) {
+            e = launch_raster(t, (int)c->n_tri, c->vis.as<unsigned long long>(), c->visfull.as<unsigned>(), R.count,
+                              c->n_sms * 16, c->scan_scr.p, c->stream);
+            R.n_launch += 6;  // rasterisation, masks, 3-kernel scan, primary pass of the rasterised rays
+        }
+        if (e == cudaSuccess) e = launch_trace(t, R.n_blocks, R.count, c->tune.stack_depth, c->stream);
         if (R.timed) cudaEventRecord(e1, c->stream);
         ++R.n_launch;
         ++R.n_pass;
@@ -667,7 +686,11 @@ int trace_chunk(sbr_ctx* c, TraceRun& R, int64_t a0, int64_t a1, long long rec_b
         ta.hit_nb = c->hit_nb.as<int>() + base;
     }
     RayState* qs[2] = {c->q0.as<RayState>(), c->q1.as<RayState>()};
-    if (c->tune.silhouette) {
+    if (c->tune.raster) {  // primary hits by rasterisation (the silhouette mask is then not needed)
+        ta.vis = c->vis.as<unsigned long long>();
+        ta.vis_full = c->visfull.as<unsigned>();
+        ta.tri_pos = c->tripos.as<int>();
+    } else if (c->tune.silhouette) {
         CK(cudaMemsetAsync(c->cover.p, 0, sizeof(unsigned) * (size_t)(chunk_rays / 32 + na), c->stream), "memset cover");
         CK(launch_silhouette(ta, (int)c->n_tri, c->cover.as<unsigned>(), c->stream), "silhouette");
         ++R.n_launch;
@@ -678,6 +701,7 @@ int trace_chunk(sbr_ctx* c, TraceRun& R, int64_t a0, int64_t a1, long long rec_b
     ta.q_out = qs[0];
     ta.q_out_count = q_count + 1;
     CK(pass(ta), "trace primary");
+    ta.vis = nullptr;
     CK(scan_popc(ta.mask, c->tilebase.as<unsigned>(), chunk_rays / 32, total_dev, c->scan_scr.p, c->stream), "scan");
     R.n_launch += 3;
     CK(launch_angle_offsets(ta.ray_off, c->tilebase.as<unsigned>(), total_dev, na, c->recoff.as<unsigned>(), c->stream),
@@ -744,10 +768,15 @@ int finish_stats(sbr_ctx* c, const TraceRun& R, int64_t n_angles, long long laun
         stats->stack_overflows = (int64_t)hs_stats[kStatOverflow];
         stats->kernel_launches = R.n_launch;
         stats->pass_launches = R.n_pass;
+        stats->raster_tests = (int64_t)hs_stats[kStatRaster];
         stats->pass_ms = 0.0;
+        stats->primary_ms = 0.0;
         for (size_t i = 0; R.timed && i + 1 < R.n_ev; i += 2) {
             float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, c->evpool[i], c->evpool[i + 1]) == cudaSuccess) stats->pass_ms += ms;
+            if (cudaEventElapsedTime(&ms, c->evpool[i], c->evpool[i + 1]) == cudaSuccess) {
+                stats->pass_ms += ms;
+                if (R.ev_primary[i / 2]) stats->primary_ms += ms;
+            }
         }
     }
     if (hs_stats[kStatOverflow])
@@ -877,7 +906,7 @@ struct BatchPlan {
     PoArgs pa;
     // device buffers
     DevBuf angles, rayoff, pang, recoff, mask, tilebase, scan_scr, q0, q1, ctr64, ctr32, stats, rec, items, nitems,
-        valid, freq_t, kfreq, partial, cover;
+        valid, freq_t, kfreq, partial, cover, vis, visfull;
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -891,7 +920,8 @@ void free_plan(BatchPlan* p)
     if (p->cap) cudaStreamDestroy(p->cap);
     DevBuf* all[] = {&p->angles, &p->rayoff, &p->pang,   &p->recoff, &p->mask,   &p->tilebase, &p->scan_scr,
                      &p->q0,     &p->q1,     &p->ctr64,  &p->ctr32,  &p->stats,  &p->rec,      &p->items,
-                     &p->nitems, &p->valid,  &p->freq_t, &p->kfreq,  &p->partial, &p->cover};
+                     &p->nitems, &p->valid,  &p->freq_t, &p->kfreq,  &p->partial, &p->cover,
+                     &p->vis,    &p->visfull};
     for (DevBuf* b : all) b->release();
     delete p;
 }
@@ -943,17 +973,25 @@ cudaError_t enqueue_plan(const sbr_ctx* c, BatchPlan& P, cudaStream_t st)
         ta.mask = P.mask.as<unsigned>();
         ta.tile_base = P.tilebase.as<unsigned>();
         ta.stats = P.stats.as<unsigned long long>();
-        if (P.tune.silhouette) {
+        ta.bounce = 0;
+        ta.work = P.ctr64.as<unsigned long long>();
+        ta.q_out = qs[0];
+        ta.q_out_count = q_count + 1;
+        if (P.tune.raster) {
+            ta.vis = P.vis.as<unsigned long long>();
+            ta.vis_full = P.visfull.as<unsigned>();
+            ta.tri_pos = c->tripos.as<int>();
+            e = launch_raster(ta, (int)c->n_tri, P.vis.as<unsigned long long>(), P.visfull.as<unsigned>(), P.count,
+                              c->n_sms * 16, P.scan_scr.p, st);
+            if (e != cudaSuccess) break;
+        } else if (P.tune.silhouette) {
             e = cudaMemsetAsync(P.cover.p, 0, sizeof(unsigned) * (size_t)(rays / 32 + na), st);
             if (e == cudaSuccess) e = launch_silhouette(ta, (int)c->n_tri, P.cover.as<unsigned>(), st);
             if (e != cudaSuccess) break;
             ta.cover = P.cover.as<unsigned>();
         }
-        ta.bounce = 0;
-        ta.work = P.ctr64.as<unsigned long long>();
-        ta.q_out = qs[0];
-        ta.q_out_count = q_count + 1;
         e = launch_trace(ta, n_blocks, P.count, P.tune.stack_depth, st);
+        ta.vis = nullptr;
         if (e == cudaSuccess) e = scan_popc(ta.mask, P.tilebase.as<unsigned>(), rays / 32, total_dev, P.scan_scr.p, st);
         if (e == cudaSuccess)
             e = launch_angle_offsets(ta.ray_off, ta.tile_base, total_dev, na, P.recoff.as<unsigned>(), st);
@@ -1060,6 +1098,10 @@ int build_plan(sbr_ctx* c, BatchPlan& P)
     CK(P.recoff.ensure(sizeof(unsigned) * (size_t)(max_angles + 1)), "alloc record offsets");
     CK(P.mask.ensure(sizeof(unsigned) * (size_t)max_tiles), "alloc mask");
     if (P.tune.silhouette) CK(P.cover.ensure(sizeof(unsigned) * (size_t)(max_tiles + max_angles)), "alloc cover");
+    if (P.tune.raster) {
+        CK(P.vis.ensure(sizeof(unsigned long long) * (size_t)max_rays), "alloc raster keys");
+        CK(P.visfull.ensure(sizeof(unsigned) * (size_t)(max_angles + 1)), "alloc raster flags");
+    }
     CK(P.tilebase.ensure(sizeof(unsigned) * (size_t)max_tiles), "alloc tile base");
     CK(P.scan_scr.ensure(scan_scratch_bytes(max_tiles)), "alloc scan scratch");
     CK(P.q0.ensure(sizeof(RayState) * (size_t)max_rays), "alloc ray queue");
@@ -1122,7 +1164,7 @@ int build_plan(sbr_ctx* c, BatchPlan& P)
     P.n_launch = 0;
     for (size_t k = 0; k < nc; ++k)
         P.n_launch += passes + ((P.max_bounces == 1 && !escape) ? 1 : 0) + 3 + 1 + 2 + (P.items_bound[k] > 0 ? 1 : 0) + 1 +
-                      (P.tune.silhouette ? 1 : 0);
+                      (P.tune.raster ? 6 : (P.tune.silhouette ? 1 : 0));
     return SBR_OK;
 }
 
@@ -1420,6 +1462,7 @@ int sbr_sync(sbr_ctx* c, sbr_trace_stats* stats)
         stats->valid_rays = valid;
         stats->node_visits = (int64_t)hs[kStatNodes];
         stats->tri_tests = (int64_t)hs[kStatTris];
+        stats->raster_tests = (int64_t)hs[kStatRaster];
         stats->stack_overflows = (int64_t)hs[kStatOverflow];
         stats->kernel_launches = P.n_launch;
         stats->pass_launches = P.n_pass;
@@ -1499,10 +1542,10 @@ int sbr_autotune(sbr_ctx* c, const sbr_request* req, int64_t n_req, const double
     sbr_tuning bestt = start;
     const int occ = std::min(4, std::max(1, trace_blocks_per_sm()));
     // parameter 0 is the traversal: binary per lane, 4-wide per lane, binary per warp, binary over octant copies
-    for (int p = 0; p < 7; ++p) {
+    for (int p = 0; p < 8; ++p) {
         std::vector<int> vals;
         if (p == 0) vals = {0, 1, 2, 3};
-        if (p == 6) vals = {0, 1};
+        if (p == 6 || p == 7) vals = {0, 1};
         if (p == 1)
             for (int v = 1; v <= occ; ++v) vals.push_back(v);
         if (p == 2) vals = {32, 16, 8, 4};
@@ -1519,8 +1562,8 @@ int sbr_autotune(sbr_ctx* c, const sbr_request* req, int64_t n_req, const double
                 t.octant = oc;
                 if (pk && t.stack_depth > 64) t.stack_depth = 64;
             } else {
-                int* fields[7] = {nullptr,    &t.blocks_per_sm,   &t.tile_w,    &t.stack_depth,
-                                  &t.po_item, &t.chunk_rays_log2, &t.silhouette};
+                int* fields[8] = {nullptr,    &t.blocks_per_sm,   &t.tile_w,     &t.stack_depth,
+                                  &t.po_item, &t.chunk_rays_log2, &t.silhouette, &t.raster};
                 if (*fields[p] == v) continue;
                 *fields[p] = v;
             }

@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(kThreads) k_emit(int n, const int* left, const
 }
 
 __global__ void __launch_bounds__(kThreads) k_reorder(const float* xyz, const int* tri, long long nv,
-                                                      const unsigned* vals, int n, float4* tris)
+                                                      const unsigned* vals, int n, float4* tris, int* pos)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
@@ -397,6 +397,7 @@ __global__ void __launch_bounds__(kThreads) k_reorder(const float* xyz, const in
     tris[3 * p + 0] = make_float4(ax, ay, az, __int_as_float((int)t));
     tris[3 * p + 1] = e1;
     tris[3 * p + 2] = e2;
+    if (pos) pos[t] = p;
 }
 
 // ---------------------------------------------------------------- PLOC builder
@@ -849,7 +850,7 @@ cudaError_t bvh_build(const BvhBuild& b, cudaStream_t st)
         k_ploc_positions<<<gx, kThreads, 0, st>>>(n, rel[pj], noff, perm);
         k_ploc_emit<<<(n - 1 + kThreads - 1) / kThreads, kThreads, 0, st>>>(n, left, right, nbox, ncnt, ncol, noff,
                                                                             tbox, b.nodes);
-        k_reorder<<<g, kThreads, 0, st>>>(b.xyz, b.tri, b.n_vert, perm, n, b.tris);
+        k_reorder<<<g, kThreads, 0, st>>>(b.xyz, b.tri, b.n_vert, perm, n, b.tris, b.tri_pos);
         return cudaGetLastError();
     }
     if (n > 1) {
@@ -861,7 +862,7 @@ cudaError_t bvh_build(const BvhBuild& b, cudaStream_t st)
                                     b.leaf_max, b.c_t, b.c_i);
     int ge = n > 1 ? (n - 1 + kThreads - 1) / kThreads : 1;
     k_emit<<<ge, kThreads, 0, st>>>(n, left, right, first, lbox, nbox, ncnt, ncol, b.nodes);
-    k_reorder<<<g, kThreads, 0, st>>>(b.xyz, b.tri, b.n_vert, vi, n, b.tris);
+    k_reorder<<<g, kThreads, 0, st>>>(b.xyz, b.tri, b.n_vert, vi, n, b.tris, b.tri_pos);
     return cudaGetLastError();
 }
 

@@ -45,7 +45,8 @@ struct AngleDev {            // 192 bytes
     int pad;
     float rxr[3], rxv[3], rxh[3];       // receiver direction and its V, H basis (= rhat, vhat, hhat monostatic)
     float rxdir[3];                     // -rxr in FP32 (= dir monostatic): the path term of the receiver
-    float pad2[4];
+    float ids;                          // 1 / sqrt(dA) in FP32: grid cells per metre (rasterisation)
+    float pad2[3];
 };
 static_assert(sizeof(AngleDev) == 192, "AngleDev layout");
 
@@ -70,7 +71,7 @@ struct __align__(16) Record {
 static_assert(sizeof(Record) == 32, "Record layout");
 
 // stats counters on the device (unsigned long long each)
-enum { kStatQueries = 0, kStatNodes = 1, kStatTris = 2, kStatOverflow = 3, kStatCount = 4 };
+enum { kStatQueries = 0, kStatNodes = 1, kStatTris = 2, kStatOverflow = 3, kStatRaster = 4, kStatCount = 5 };
 
 // ---------------------------------------------------------------- launchers
 // All launchers enqueue on `st` and return the launch error (cudaSuccess if none).
@@ -112,8 +113,9 @@ struct BvhBuild {
     // outputs (allocated by the caller: nodes [max(n_tri-1,1)*4] float4, tris [n_tri*3] float4)
     float4* nodes;
     float4* tris;
+    int* tri_pos;     // [n_tri]: position in tris of each original triangle index
     float* bbox_out;  // device float[6] scene box of the vertices
-    int* err_flag;    // device int: set to 1 if a triangle index is out of range
+    int* err_flag;    // device int: bit 1 a triangle index out of range, bit 2 a non-finite coordinate
     // scratch (caller-owned)
     void* scratch;
     size_t scratch_bytes;
@@ -151,6 +153,10 @@ struct TraceArgs {
     int* hit_tri;                 // optional [total_rays][max_bounces] (RECORD_HITS)
     float* hit_t;                 // optional [total_rays][max_bounces]
     int* hit_nb;                  // optional [total_rays]
+    const unsigned long long* vis; // optional (primary pass) [total_rays] closest-hit keys from k_raster
+    const unsigned* vis_full;     // with vis: [n_angles + 1] 1 = the aspect's primary rays traverse the tree;
+                                  // [n_angles]: 1 if any aspect does
+    const int* tri_pos;           // with vis: [n_tri] position in tris of each original triangle index
 };
 int trace_blocks_per_sm();
 // stack_depth: 32, 64 or 128 entries of the traversal stack (other values: 64;
@@ -163,6 +169,19 @@ cudaError_t launch_emit_all(const TraceArgs& a, int n_blocks, cudaStream_t st);
 // all-rays flag (word a.total_rays / 32 + aspect) for a triangle too large to
 // rasterise. cover must be zeroed first ([a.total_rays / 32 + a.n_angles] words).
 cudaError_t launch_silhouette(const TraceArgs& a, int n_tri, unsigned* cover, cudaStream_t st);
+// Primary closest hits by rasterisation (aspects a.angles, a.ray_off, a.n_angles
+// of a chunk of a.total_rays rays): vis[g] becomes the smallest key
+// (FP32 t bits << 32 | original triangle index) over the triangles whose FP32
+// test accepts primary ray g, or ~0 for none; full[aspect] = 1 and
+// full[n_angles] = 1 when a triangle covers more than kRasterMaxCells cells of
+// that aspect (its rays then traverse the tree). Clears vis and full itself.
+// Then sets a.mask to the valid bits of the rasterised rays, a.tile_base to
+// their exclusive scan and *a.q_out_count to their number: the primary pass
+// stores those rays at fixed queue slots and appends the traversing ones after
+// them.
+constexpr long long kRasterMaxCells = 1 << 14;
+cudaError_t launch_raster(const TraceArgs& a, int n_tri, unsigned long long* vis, unsigned* full, bool count,
+                          int n_blocks, void* scan_scratch, cudaStream_t st);
 
 // exclusive scan of in[i] (or popcount(in[i])) -> out[i]; total written to *total
 size_t scan_scratch_bytes(long long n);

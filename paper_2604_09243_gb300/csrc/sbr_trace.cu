@@ -105,8 +105,30 @@ __device__ __forceinline__ float dot_s(float3 a, float3 b)
 }
 
 // ---------------------------------------------------------------- closest hit
-// Watertight-by-slack FP32 Moller-Trumbore over the triangles of leaf `ref`,
-// keeping the closest hit (ties: smaller original triangle index).
+// Watertight-by-slack FP32 Moller-Trumbore of one triangle (A: v0 and the
+// original index, B: e1, C: e2) in the written FP32 operation order (division
+// only for a candidate inside the triangle); t of an accepted hit.
+__device__ __forceinline__ bool tri_test(float4 A, float4 B, float4 C, float3 o, float3 d, float& t)
+{
+    const float3 e1 = make_float3(B.x, B.y, B.z), e2 = make_float3(C.x, C.y, C.z);
+    const float3 p = cross_s(d, e2);
+    const float det = dot_s(e1, p);
+    const float3 s = make_float3(__fsub_rn(o.x, A.x), __fsub_rn(o.y, A.y), __fsub_rn(o.z, A.z));
+    const float3 qv = cross_s(s, e1);
+    const float U0 = dot_s(s, p), V0 = dot_s(d, qv), T0 = dot_s(e2, qv);
+    const bool neg = det < 0.f;
+    const float U = neg ? -U0 : U0, V = neg ? -V0 : V0, T = neg ? -T0 : T0;
+    const float ad = fabsf(det);
+    const float mg = __fmul_rn(ad, kSlack);
+    if (det != 0.f && U >= -mg && V >= -mg && __fadd_rn(U, V) <= __fadd_rn(ad, mg) && T > 0.f) {
+        t = __fdiv_rn(T0, det);
+        return true;
+    }
+    return false;
+}
+
+// The triangles of leaf `ref`, keeping the closest hit (ties: smaller
+// original triangle index).
 template <bool kCount>
 __device__ __forceinline__ void leaf_test(const float4* __restrict__ tris, int ref, float3 o, float3 d, int skip,
                                           Hit& h, unsigned& ntri)
@@ -118,20 +140,8 @@ __device__ __forceinline__ void leaf_test(const float4* __restrict__ tris, int r
         if (k == skip) continue;
         const float4* tp = tris + 3 * (size_t)k;
         const float4 A = __ldg(tp), B = __ldg(tp + 1), C = __ldg(tp + 2);
-        // Moller-Trumbore in the written FP32 operation order (division
-        // only for a candidate inside the triangle)
-        const float3 e1 = make_float3(B.x, B.y, B.z), e2 = make_float3(C.x, C.y, C.z);
-        const float3 p = cross_s(d, e2);
-        const float det = dot_s(e1, p);
-        const float3 s = make_float3(__fsub_rn(o.x, A.x), __fsub_rn(o.y, A.y), __fsub_rn(o.z, A.z));
-        const float3 qv = cross_s(s, e1);
-        const float U0 = dot_s(s, p), V0 = dot_s(d, qv), T0 = dot_s(e2, qv);
-        const bool neg = det < 0.f;
-        const float U = neg ? -U0 : U0, V = neg ? -V0 : V0, T = neg ? -T0 : T0;
-        const float ad = fabsf(det);
-        const float mg = __fmul_rn(ad, kSlack);
-        if (det != 0.f && U >= -mg && V >= -mg && __fadd_rn(U, V) <= __fadd_rn(ad, mg) && T > 0.f) {
-            const float t = __fdiv_rn(T0, det);
+        float t;
+        if (tri_test(A, B, C, o, d, t)) {
             const int orig = __float_as_int(A.w);
             if (t < h.t || (t == h.t && orig < h.orig)) {
                 h.t = t;
@@ -737,6 +747,38 @@ __device__ __forceinline__ void query(const TraceArgs& a, bool active, float3 o,
 // projects one triangle for one aspect and ORs its cells into the tile words.
 // A triangle whose widened box spans more than 2^16 cells sets the aspect's
 // "all rays" flag (word total_tiles + aspect) instead.
+// The grid cells (i0..i1, j0..j1) of aspect A whose rays the FP32 test could
+// accept on triangle (a: v0, b: e1, c: e2); false if none.
+// ids = 1 / sqrt(A.dA), the inverse grid spacing (FP32, set with the aspect table)
+__device__ __forceinline__ float cell_scale(const AngleDev& A) { return A.ids; }
+__device__ __forceinline__ bool tri_cells(const AngleDev& A, float ids, float4 a, float4 b, float4 c, int& i0, int& i1,
+                                          int& j0, int& j1)
+{
+    const float px[3] = {a.x, a.x + b.x, a.x + c.x}, py[3] = {a.y, a.y + b.y, a.y + c.y},
+                pz[3] = {a.z, a.z + b.z, a.z + c.z};
+    float umin = FLT_MAX, umax = -FLT_MAX, vmin = FLT_MAX, vmax = -FLT_MAX, mag = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float dx = px[k] - A.p0[0], dy = py[k] - A.p0[1], dz = pz[k] - A.p0[2];
+        const float u = (dx * A.hhat[0] + dy * A.hhat[1] + dz * A.hhat[2]) * ids;
+        const float v = (dx * A.vhat[0] + dy * A.vhat[1] + dz * A.vhat[2]) * ids;
+        umin = fminf(umin, u);
+        umax = fmaxf(umax, u);
+        vmin = fminf(vmin, v);
+        vmax = fmaxf(vmax, v);
+        mag = fmaxf(mag, (fabsf(dx) + fabsf(dy) + fabsf(dz)) * ids);
+    }
+    if (!(umin <= umax) || !(vmin <= vmax)) return false;  // NaN vertices: no ray can hit it
+    const float m = 0.01f + (umax - umin + vmax - vmin) * (1.f / 1024.f) + mag * (1.f / 262144.f);
+    const float fi0 = ceilf(umin - m), fi1 = floorf(umax + m), fj0 = ceilf(vmin - m), fj1 = floorf(vmax + m);
+    if (fi1 < 0.f || fj1 < 0.f || fi0 > (float)(A.nu - 1) || fj0 > (float)(A.nv - 1)) return false;
+    i0 = max(0, (int)fi0);
+    i1 = min(A.nu - 1, (int)fi1);
+    j0 = max(0, (int)fj0);
+    j1 = min(A.nv - 1, (int)fj1);
+    return true;
+}
+
 __global__ void __launch_bounds__(256) k_silhouette(const float4* __restrict__ tris, int n_tri,
                                                     const AngleDev* __restrict__ angles,
                                                     const long long* __restrict__ ray_off, int n_angles,
@@ -744,31 +786,13 @@ __global__ void __launch_bounds__(256) k_silhouette(const float4* __restrict__ t
 {
     for (int ang = blockIdx.y; ang < n_angles; ang += gridDim.y) {
         const AngleDev& A = angles[ang];
-        const float ds = sqrtf(A.dA), ids = 1.f / ds;
         const int tw = A.tw_log2, W = 1 << tw, H = 32 >> tw;
+        const float ids = cell_scale(A);
         for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tri; t += gridDim.x * blockDim.x) {
             const float4 a = __ldg(tris + 3 * (size_t)t), b = __ldg(tris + 3 * (size_t)t + 1),
                          c = __ldg(tris + 3 * (size_t)t + 2);
-            const float px[3] = {a.x, a.x + b.x, a.x + c.x}, py[3] = {a.y, a.y + b.y, a.y + c.y},
-                        pz[3] = {a.z, a.z + b.z, a.z + c.z};
-            float umin = FLT_MAX, umax = -FLT_MAX, vmin = FLT_MAX, vmax = -FLT_MAX, mag = 0.f;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const float dx = px[k] - A.p0[0], dy = py[k] - A.p0[1], dz = pz[k] - A.p0[2];
-                const float u = (dx * A.hhat[0] + dy * A.hhat[1] + dz * A.hhat[2]) * ids;
-                const float v = (dx * A.vhat[0] + dy * A.vhat[1] + dz * A.vhat[2]) * ids;
-                umin = fminf(umin, u);
-                umax = fmaxf(umax, u);
-                vmin = fminf(vmin, v);
-                vmax = fmaxf(vmax, v);
-                mag = fmaxf(mag, (fabsf(dx) + fabsf(dy) + fabsf(dz)) * ids);
-            }
-            if (!(umin <= umax) || !(vmin <= vmax)) continue;  // NaN vertices: no ray can hit it
-            const float m = 0.01f + (umax - umin + vmax - vmin) * (1.f / 1024.f) + mag * (1.f / 262144.f);
-            const float fi0 = ceilf(umin - m), fi1 = floorf(umax + m), fj0 = ceilf(vmin - m), fj1 = floorf(vmax + m);
-            if (fi1 < 0.f || fj1 < 0.f || fi0 > (float)(A.nu - 1) || fj0 > (float)(A.nv - 1)) continue;
-            const int i0 = max(0, (int)fi0), i1 = min(A.nu - 1, (int)fi1);
-            const int j0 = max(0, (int)fj0), j1 = min(A.nv - 1, (int)fj1);
+            int i0, i1, j0, j1;
+            if (!tri_cells(A, ids, a, b, c, i0, i1, j0, j1)) continue;
             if ((long long)(i1 - i0 + 1) * (j1 - j0 + 1) > 65536) {
                 atomicOr(cover + total_tiles + ang, 1u);
                 continue;
@@ -789,10 +813,184 @@ __global__ void __launch_bounds__(256) k_silhouette(const float4* __restrict__ t
     }
 }
 
+// origin of primary ray (i, j) of aspect A (Eq. L1-L3 grid), in FP32
+__device__ __forceinline__ float3 primary_origin(const AngleDev& A, int i, int j)
+{
+    const float fi = (float)i, fj = (float)j;
+    return make_float3(__fadd_rn(__fadd_rn(A.p0[0], __fmul_rn(fi, A.du[0])), __fmul_rn(fj, A.dv[0])),
+                       __fadd_rn(__fadd_rn(A.p0[1], __fmul_rn(fi, A.du[1])), __fmul_rn(fj, A.dv[1])),
+                       __fadd_rn(__fadd_rn(A.p0[2], __fmul_rn(fi, A.du[2])), __fmul_rn(fj, A.dv[2])));
+}
+
+// ---------------------------------------------------------------- primary hits by rasterisation
+// All primary rays of an aspect are parallel, so the closest hit of every ray
+// can be found triangle by triangle: the FP32 test of a triangle runs for every
+// grid ray in its conservative cell range (the silhouette range, which
+// contains every ray the test accepts), and each ray keeps the smallest key
+// (t bits << 32 | original index) by a 64-bit atomic minimum. t > 0, so the
+// key order is (t, index): the closest hit and the tie rule of the traversal,
+// whose t is <= FLT_MAX. A triangle spanning more than kRasterMaxCells cells
+// flags its aspect instead, whose primary rays then traverse the tree.
+constexpr int kRasterSmall = 32;    // cells a thread tests by itself
+constexpr int kRasterQueue = 256;   // larger triangles a block defers to its warps per round
+
+__device__ __forceinline__ void raster_cell(const AngleDev& A, float4 P, float4 B, float4 C, float3 d, unsigned orig,
+                                            int i, int j, unsigned long long* vrow)
+{
+    float th;
+    if (tri_test(P, B, C, primary_origin(A, i, j), d, th) && th <= FLT_MAX) {
+        const int tw = A.tw_log2, sh = 5 - tw;  // tile of W = 2^tw by H = 2^sh rays
+        const int bu = i >> tw, bv = j >> sh;
+        const long long pidx = ((long long)(bv * A.nbu + bu) << 5) + ((j & ((1 << sh) - 1)) << tw) + (i & ((1 << tw) - 1));
+        atomicMin(vrow + pidx, ((unsigned long long)__float_as_uint(th) << 32) | orig);
+    }
+}
+
+// Items q = aspect * n_tri + triangle in grid-stride rounds of 256 per block
+// (aspect-major: a block's threads take neighbouring triangles of one aspect,
+// whose cells are neighbours too). A triangle with at most kRasterSmall cells
+// is tested by its thread; larger ones are queued with their cell range and
+// tested by the block's warps, 32 cells at a time.
+__global__ void __launch_bounds__(256, 4) k_raster(const TraceArgs a, int n_tri, unsigned long long* vis,
+                                                   unsigned* full, int count)
+{
+    __shared__ int4 s_rng[kRasterQueue];  // i0, i1, j0, j1
+    __shared__ int s_item[kRasterQueue];  // triangle
+    __shared__ int s_ang[kRasterQueue];
+    __shared__ int s_n;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+    const unsigned long long n_items = (unsigned long long)a.n_angles * (unsigned long long)n_tri;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    // (aspect, triangle) of this thread's item, advanced by the stride without a division per round
+    const unsigned long long q0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int ang = (int)(q0 / (unsigned long long)n_tri), t = (int)(q0 % (unsigned long long)n_tri);
+    const int step_a = (int)(stride / (unsigned long long)n_tri), step_t = (int)(stride % (unsigned long long)n_tri);
+    unsigned long long ntri = 0;
+    // the rounds depend on the block only: every thread reaches the barriers
+    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < n_items; base += stride) {
+        if (threadIdx.x == 0) s_n = 0;
+        __syncthreads();
+        if (base + threadIdx.x < n_items) {
+            const AngleDev& A = a.angles[ang];
+            const float4* tp = a.tris + 3 * (size_t)t;
+            const float4 P = __ldg(tp), B = __ldg(tp + 1), C = __ldg(tp + 2);
+            int i0, i1, j0, j1;
+            if (tri_cells(A, cell_scale(A), P, B, C, i0, i1, j0, j1)) {
+                const long long ncell = (long long)(i1 - i0 + 1) * (j1 - j0 + 1);
+                int slot = kRasterQueue;
+                if (ncell > kRasterMaxCells) {
+                    atomicOr(full + ang, 1u);
+                    atomicOr(full + a.n_angles, 1u);  // some aspect of the chunk traverses
+                } else if (ncell > kRasterSmall && (slot = atomicAdd(&s_n, 1)) < kRasterQueue) {
+                    s_rng[slot] = make_int4(i0, i1, j0, j1);
+                    s_item[slot] = t;
+                    s_ang[slot] = ang;
+                } else {
+                    const float3 d = make_float3(A.dir[0], A.dir[1], A.dir[2]);
+                    unsigned long long* vrow = vis + a.ray_off[ang];
+                    const unsigned orig = (unsigned)__float_as_int(P.w);
+                    for (int j = j0; j <= j1; ++j)
+                        for (int i = i0; i <= i1; ++i) raster_cell(A, P, B, C, d, orig, i, j, vrow);
+                    ntri += (unsigned long long)ncell;
+                }
+            }
+        }
+        t += step_t;
+        ang += step_a;
+        if (t >= n_tri) {
+            t -= n_tri;
+            ++ang;
+        }
+        __syncthreads();
+        const int n_def = min(s_n, kRasterQueue);
+        for (int k = warp; k < n_def; k += n_warps) {
+            const int td = s_item[k], ad = s_ang[k];
+            const int4 r = s_rng[k];
+            const AngleDev& A = a.angles[ad];
+            const float4* tp = a.tris + 3 * (size_t)td;
+            const float4 P = __ldg(tp), B = __ldg(tp + 1), C = __ldg(tp + 2);
+            const unsigned orig = (unsigned)__float_as_int(P.w);
+            const float3 d = make_float3(A.dir[0], A.dir[1], A.dir[2]);
+            unsigned long long* vrow = vis + a.ray_off[ad];
+            const int w = r.y - r.x + 1, ncell = w * (r.w - r.z + 1);
+            // cell c = (c / w, c % w) from (j0, i0); steps of 32 cells: sj rows and si columns
+            const int sj = 32 / w, si = 32 - sj * w, l0 = lane / w;
+            int i = r.x + (lane - l0 * w), j = r.z + l0;
+            for (int cidx = lane; cidx < ncell; cidx += 32) {
+                raster_cell(A, P, B, C, d, orig, i, j, vrow);
+                i += si;
+                j += sj;
+                if (i > r.y) {
+                    i -= w;
+                    ++j;
+                }
+            }
+            if (lane == 0) ntri += (unsigned long long)ncell;
+        }
+        __syncthreads();
+    }
+    if (count) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ntri += __shfl_xor_sync(kFull, ntri, o);
+        if (lane == 0 && ntri) {
+            atomicAdd(a.stats + kStatTris, ntri);
+            atomicAdd(a.stats + kStatRaster, ntri);
+        }
+    }
+}
+
+// contiguous tile range [t0, t1) of warp gw of nw over n_tiles tiles
+__device__ __forceinline__ void warp_tiles(long long n_tiles, long long gw, long long nw, long long& t0, long long& t1)
+{
+    const long long per = (n_tiles + nw - 1) / nw;
+    t0 = gw * per;
+    t1 = t0 + per < n_tiles ? t0 + per : n_tiles;
+}
+
+// valid bits of the rasterised primary rays (0 for the tiles of flagged
+// aspects, which traverse); each warp a contiguous range of tiles
+__global__ void __launch_bounds__(256) k_vis_mask(const TraceArgs a, const unsigned long long* __restrict__ vis,
+                                                  const unsigned* __restrict__ full, unsigned* mask)
+{
+    const int lane = threadIdx.x & 31;
+    long long t0, t1;
+    warp_tiles(a.total_rays >> 5, ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+               ((long long)gridDim.x * blockDim.x) >> 5, t0, t1);
+    if (t0 >= t1) return;  // warp-uniform
+    const bool any_full = full[a.n_angles] != 0;
+    int ang = 0;
+    if (any_full) {
+        if (lane == 0) ang = find_angle(a.ray_off, a.n_angles, t0 << 5);
+        ang = __shfl_sync(kFull, ang, 0);
+    }
+#pragma unroll 4
+    for (long long tile = t0; tile < t1; ++tile) {
+        unsigned m = __ballot_sync(kFull, vis[(tile << 5) + lane] != ~0ull);
+        if (any_full) {
+            while (a.ray_off[ang + 1] <= (tile << 5)) ++ang;
+            if (full[ang]) m = 0;
+        }
+        if (lane == 0) mask[tile] = m;
+    }
+}
+
 // ---------------------------------------------------------------- pass 0: primary rays
+// state of a primary ray before its first hit: receive basis field, path
+// term k.o0 (two-float), no bounce yet
+__device__ __forceinline__ void start_ray(const AngleDev& A, Ray& r)
+{
+    r.ev = make_float3(A.vhat[0], A.vhat[1], A.vhat[2]);
+    tf_dot(A.dir, r.o, r.lacc_hi, r.lacc_lo);
+    r.cos0 = 0.f;
+    r.nb = 0;
+    r.last = -1;
+}
+
 template <bool kCount, int kStack, int kMode>
 __global__ void __launch_bounds__(kTraceThreads, 4) k_primary(const TraceArgs a)
 {
+    // with rasterised hits this kernel only traverses for flagged aspects
+    if (a.vis && !a.vis_full[a.n_angles]) return;
     const int lane = threadIdx.x & 31;
     unsigned nq = 0, nvis = 0, ntri = 0;
     bool ovf = false;
@@ -804,6 +1002,7 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_primary(const TraceArgs a)
         int ang = 0;
         if (lane == 0) ang = find_angle(a.ray_off, a.n_angles, (long long)base);
         ang = __shfl_sync(kFull, ang, 0);
+        if (a.vis && !a.vis_full[ang]) continue;  // warp-uniform; k_primary_vis takes this tile
         const AngleDev& A = a.angles[ang];
         const int local = (int)((long long)base + lane - a.ray_off[ang]);
         int i, j;
@@ -818,10 +1017,7 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_primary(const TraceArgs a)
         r.o = make_float3(0.f, 0.f, 0.f);
         r.d = make_float3(0.f, 0.f, 1.f);
         if (active) {
-            const float fi = (float)i, fj = (float)j;
-            r.o = make_float3(__fadd_rn(__fadd_rn(A.p0[0], __fmul_rn(fi, A.du[0])), __fmul_rn(fj, A.dv[0])),
-                              __fadd_rn(__fadd_rn(A.p0[1], __fmul_rn(fi, A.du[1])), __fmul_rn(fj, A.dv[1])),
-                              __fadd_rn(__fadd_rn(A.p0[2], __fmul_rn(fi, A.du[2])), __fmul_rn(fj, A.dv[2])));
+            r.o = primary_origin(A, i, j);
             r.d = make_float3(A.dir[0], A.dir[1], A.dir[2]);
         }
         Hit h;
@@ -829,12 +1025,7 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_primary(const TraceArgs a)
         if (active) {
             ++nq;
             if (h.k >= 0) {
-                const AngleDev& A2 = a.angles[ang];
-                r.ev = make_float3(A2.vhat[0], A2.vhat[1], A2.vhat[2]);
-                tf_dot(A2.dir, r.o, r.lacc_hi, r.lacc_lo);
-                r.cos0 = 0.f;
-                r.nb = 0;
-                r.last = -1;
+                start_ray(a.angles[ang], r);
                 hit = true;
                 apply_hit(A, a.tris, h, a.flags, r);
                 record_hit(a, r, h);
@@ -845,6 +1036,55 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_primary(const TraceArgs a)
         push(a, hit, r);
     }
     flush_stats<kCount>(a, nq, nvis, ntri, ovf);
+}
+
+// Primary pass of the rasterised aspects: each ray reads its key; the hit rays
+// go to the queue slots given by the scan of the raster masks (no atomics),
+// so the tiles are assigned statically (every tile costs about the same).
+template <bool kCount>
+__global__ void __launch_bounds__(kTraceThreads) k_primary_vis(const TraceArgs a)
+{
+    constexpr int kChunk = 4;  // tiles of a chunk; chunks interleaved over the warps (hits cluster in the grid)
+    const int lane = threadIdx.x & 31;
+    unsigned nq = 0;
+    const long long n_tiles = a.total_rays >> 5, n_chunks = (n_tiles + kChunk - 1) / kChunk;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    int ang = 0;
+    if (gw < n_chunks) {
+        if (lane == 0) ang = find_angle(a.ray_off, a.n_angles, (gw * kChunk) << 5);
+        ang = __shfl_sync(kFull, ang, 0);
+    }
+    for (long long chunk = gw; chunk < n_chunks; chunk += nw) {
+        for (long long tile = chunk * kChunk; tile < (chunk + 1) * kChunk && tile < n_tiles; ++tile) {
+            const long long base = tile << 5;
+            while (a.ray_off[ang + 1] <= base) ++ang;  // the tiles of a warp only move forward
+            if (a.vis_full[ang]) continue;  // warp-uniform; k_primary traverses this tile
+            const AngleDev& A = a.angles[ang];
+            const int local = (int)(base + lane - a.ray_off[ang]);
+            int i, j;
+            tile_ij(A, local, i, j);
+            if (i < A.nu && j < A.nv) ++nq;
+            const unsigned vmask = a.mask[tile];  // k_vis_mask
+            if ((vmask >> lane) & 1u) {
+                const unsigned long long key = a.vis[base + lane];
+                Hit h;
+                h.t = __uint_as_float((unsigned)(key >> 32));
+                h.orig = (int)(unsigned)key;
+                h.k = __ldg(a.tri_pos + h.orig);
+                Ray r;
+                r.angle = ang;
+                r.local = local;
+                r.o = primary_origin(A, i, j);
+                r.d = make_float3(A.dir[0], A.dir[1], A.dir[2]);
+                start_ray(A, r);
+                apply_hit(A, a.tris, h, a.flags, r);
+                record_hit(a, r, h);
+                store_state(a.q_out, a.tile_base[tile] + __popc(vmask & ((1u << lane) - 1u)), r);
+            }
+        }
+    }
+    flush_stats<kCount>(a, nq, 0u, 0u, false);
 }
 
 // ---------------------------------------------------------------- pass b >= 1: live rays
@@ -930,6 +1170,10 @@ template <int kStack, int kMode>
 void launch_trace_s(const TraceArgs& a, int n_blocks, bool count_visits, cudaStream_t st)
 {
     if (a.bounce == 0) {
+        if (a.vis) {
+            if (count_visits) k_primary_vis<true><<<n_blocks, kTraceThreads, 0, st>>>(a);
+            else k_primary_vis<false><<<n_blocks, kTraceThreads, 0, st>>>(a);
+        }
         if (count_visits) k_primary<true, kStack, kMode><<<n_blocks, kTraceThreads, 0, st>>>(a);
         else k_primary<false, kStack, kMode><<<n_blocks, kTraceThreads, 0, st>>>(a);
     } else {
@@ -992,6 +1236,26 @@ cudaError_t launch_silhouette(const TraceArgs& a, int n_tri, unsigned* cover, cu
     k_silhouette<<<dim3(bx, by), 256, 0, st>>>(a.tris, n_tri, a.angles, a.ray_off, a.n_angles, a.total_rays >> 5,
                                                cover);
     return cudaGetLastError();
+}
+
+cudaError_t launch_raster(const TraceArgs& a, int n_tri, unsigned long long* vis, unsigned* full, bool count,
+                          int n_blocks, void* scan_scratch, cudaStream_t st)
+{
+    if (a.n_angles <= 0 || n_tri <= 0) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(vis, 0xFF, sizeof(unsigned long long) * (size_t)a.total_rays, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(full, 0, sizeof(unsigned) * (size_t)(a.n_angles + 1), st);
+    if (e != cudaSuccess) return e;
+    const long long need = ((long long)a.n_angles * n_tri + 255) / 256;
+    k_raster<<<(int)std::max(1ll, std::min<long long>(need, n_blocks)), 256, 0, st>>>(a, n_tri, vis, full,
+                                                                                   count ? 1 : 0);
+    const long long n_tiles = a.total_rays >> 5;
+    k_vis_mask<<<(int)std::max(1ll, std::min<long long>((n_tiles + 7) / 8, n_blocks)), 256, 0, st>>>(a, vis, full,
+                                                                                                     a.mask);
+    e = cudaGetLastError();
+    // queue slots of the rasterised hits; the traversing rays append after them
+    if (e == cudaSuccess)
+        e = scan_popc(a.mask, const_cast<unsigned*>(a.tile_base), n_tiles, a.q_out_count, scan_scratch, st);
+    return e;
 }
 
 cudaError_t launch_angle_offsets(const long long* ray_off, const unsigned* tile_base, const unsigned* total,

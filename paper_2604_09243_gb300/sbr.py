@@ -55,7 +55,7 @@ class TraceOpts(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("tile_w", C.c_int), ("blocks_per_sm", C.c_int), ("stack_depth", C.c_int),
                 ("chunk_rays_log2", C.c_int), ("po_item", C.c_int), ("bvh_width", C.c_int), ("packet", C.c_int),
-                ("octant", C.c_int), ("silhouette", C.c_int)]
+                ("octant", C.c_int), ("silhouette", C.c_int), ("raster", C.c_int)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -69,10 +69,10 @@ class TraceStats(C.Structure):
     _fields_ = [("n_angles", C.c_int64), ("rays_launched", C.c_int64), ("ray_bounces", C.c_int64),
                 ("valid_rays", C.c_int64), ("node_visits", C.c_int64), ("tri_tests", C.c_int64),
                 ("stack_overflows", C.c_int64), ("kernel_launches", C.c_int64), ("pass_launches", C.c_int64),
-                ("pass_ms", C.c_double)]
+                ("pass_ms", C.c_double), ("raster_tests", C.c_int64), ("primary_ms", C.c_double)]
 
     def as_dict(self):
-        return {k: (float if k == "pass_ms" else int)(getattr(self, k)) for k, _ in self._fields_}
+        return {k: (float if k.endswith("_ms") else int)(getattr(self, k)) for k, _ in self._fields_}
 
 
 class Request(C.Structure):
@@ -357,7 +357,8 @@ class Context:
         return t.as_dict()
 
     def set_tuning(self, **kw):
-        """Change some tuning fields (tile_w, blocks_per_sm, stack_depth, chunk_rays_log2, po_item)."""
+        """Change some tuning fields (tile_w, blocks_per_sm, stack_depth, chunk_rays_log2, po_item, bvh_width,
+        packet, octant, silhouette, raster)."""
         t = Tuning(**{**self.tuning(), **kw})
         self._check(lib().sbr_set_tuning(self._h, C.byref(t)))
 

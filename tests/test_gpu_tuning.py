@@ -33,9 +33,10 @@ def _trace(c, case, angles, **kw):
                                      dict(stack_depth=128), dict(blocks_per_sm=1), dict(po_item=512),
                                      dict(po_item=2048), dict(chunk_rays_log2=20), dict(bvh_width=4),
                                      dict(bvh_width=4, stack_depth=32, tile_w=4), dict(packet=1),
-                                     dict(packet=1, stack_depth=32, tile_w=32), dict(silhouette=1), dict(octant=1),
-                                     dict(octant=1, stack_depth=32, tile_w=16),
-                                     dict(silhouette=1, bvh_width=4, tile_w=16)])
+                                     dict(packet=1, stack_depth=32, tile_w=32), dict(raster=0),
+                                     dict(raster=0, silhouette=1), dict(octant=1),
+                                     dict(octant=1, stack_depth=32, tile_w=16, raster=0),
+                                     dict(raster=0, silhouette=1, bvh_width=4, tile_w=16)])
 def test_setting_keeps_hits_and_fields(G, tri_case, setting):
     case = tri_case
     angles = case["angles"][[0, 45, 90, 135, 180]]
@@ -65,7 +66,8 @@ def test_bad_settings_refused(G):
         for bad in (dict(tile_w=3), dict(tile_w=64), dict(blocks_per_sm=0), dict(blocks_per_sm=5),
                     dict(stack_depth=48), dict(po_item=300), dict(chunk_rays_log2=19), dict(chunk_rays_log2=28),
                     dict(bvh_width=3), dict(packet=2), dict(packet=1, bvh_width=4), dict(packet=1, stack_depth=128),
-                    dict(silhouette=2), dict(octant=1, bvh_width=4), dict(octant=1, packet=1), dict(octant=2)):
+                    dict(silhouette=2), dict(octant=1, bvh_width=4), dict(octant=1, packet=1), dict(octant=2),
+                    dict(raster=2), dict(raster=-1)):
             with pytest.raises(G.SbrError):
                 c.set_tuning(**bad)
         assert c.tuning() == before
@@ -131,32 +133,95 @@ def test_wide_tree_same_hits_aircraft(G):
 
 
 def test_silhouette_mask_skips_only_misses(G):
-    """With the silhouette mask the aircraft's rays keep their hits (bit for
-    bit) and valid count while fewer queries run; a two-triangle plate much
-    larger than the grid cells takes the all-rays path and keeps its RCS."""
+    """With the silhouette mask (primary rays traversing the tree) the
+    aircraft's rays keep their hits (bit for bit) and valid count while fewer
+    queries run; with the rasterised primary hits they keep them too and every
+    grid ray is answered. A two-triangle plate much larger than the grid cells
+    takes the all-rays path of the mask and the traversal fallback of the
+    rasterisation, and keeps its RCS."""
     case = S.aircraft_case(1e9, n_az=360)
     angles = case["angles"][[0, 45, 180, 300]]
     out = []
-    for sil in (0, 1):
+    for sil, ras in ((0, 0), (1, 0), (0, 1)):
         with G.Context(0) as c:
             c.load_mesh(case["xyz"], case["tri"])
-            c.set_tuning(silhouette=sil)
+            c.set_tuning(silhouette=sil, raster=ras)
             st = c.trace(angles, case["spacing"], eta=case["eta"], max_bounces=case["max_bounces"],
                          offset=case["offset"], flags=G.TRACE_RECORD_HITS)
             out.append((st, [c.get_hits(a) for a in range(len(angles))], c.po_integrate([1e9])[1]))
-    (s0, h0, R0), (s1, h1, R1) = out
+    (s0, h0, R0), (s1, h1, R1), (s2, h2, R2) = out
     assert s1["valid_rays"] == s0["valid_rays"] and s1["rays_launched"] == s0["rays_launched"]
     assert s1["ray_bounces"] < s0["ray_bounces"]
-    for a, b in zip(h0, h1):
-        for x, y in zip(a, b):
-            assert np.array_equal(x, y)
-    assert np.array_equal(R0, R1)
+    assert s2["ray_bounces"] == s0["ray_bounces"] and s2["valid_rays"] == s0["valid_rays"]
+    for hh in (h1, h2):
+        for a, b in zip(h0, hh):
+            for x, y in zip(a, b):
+                assert np.array_equal(x, y)
+    assert np.array_equal(R0, R1) and np.array_equal(R0, R2)
     xyz, tri = S.square_plate(1.0, m=1)  # two 1 m triangles: 500 x 500 cells each at 2 mm
     res = []
-    for sil in (0, 1):
+    for sil, ras in ((0, 0), (1, 0), (0, 1)):
         with G.Context(0) as c:
             c.load_mesh(xyz, tri)
-            c.set_tuning(silhouette=sil)
+            c.set_tuning(silhouette=sil, raster=ras)
             c.trace([[0.0, 90.0], [10.0, 80.0]], 0.002, max_bounces=1)
             res.append(c.po_integrate([10e9])[1])
+    assert np.array_equal(res[0], res[1]) and np.array_equal(res[0], res[2])
+
+
+def test_raster_primary_hits_equal_traversal(G, tri_case):
+    """Primary hits found by rasterisation (one FP32 test per triangle and
+    covered grid ray, 64-bit atomic minimum of (t, index)) equal those of the
+    tree traversal bit for bit: sphere with its window, aircraft at 3 GHz over
+    10 bounces, a bistatic trihedral, and the submitted batch path; the
+    rasterisation counts its triangle tests and the primary pass visits no
+    nodes."""
+    torch = pytest.importorskip("torch")
+    sph = S.sphere_case(n_random=3)
+    air = S.aircraft_case(3e9, n_az=360)
+    cases = [(sph["xyz"], sph["tri"], sph["angles"], sph["spacing"], 1, dict(window=sph["window"])),
+             (air["xyz"], air["tri"], air["angles"][[10, 100, 250]], air["spacing"], air["max_bounces"],
+              dict(eta=air["eta"], offset=air["offset"])),
+             (tri_case["xyz"], tri_case["tri"], tri_case["angles"][[20, 90, 150]], tri_case["spacing"], 3,
+              dict(eta=tri_case["eta"], offset=tri_case["offset"], rx=tri_case["angles"][[30, 60, 100]] + [0, 5]))]
+    for xyz, tri, ang, sp, B, kw in cases:
+        out = []
+        for ras in (0, 1):
+            with G.Context(0) as c:
+                c.load_mesh(xyz, tri)
+                c.set_tuning(raster=ras)
+                st = c.trace(ang, sp, max_bounces=B, flags=G.TRACE_RECORD_HITS | G.TRACE_COUNT_VISITS, **kw)
+                p1 = c.trace(ang, sp, max_bounces=1, flags=G.TRACE_COUNT_VISITS,
+                             **{k: v for k, v in kw.items() if k != "rx"})
+                out.append((st, p1, c.po_integrate([3e9, 10e9])[1]))
+        (s0, p0, R0), (s1, q1, R1) = out
+        assert s0["ray_bounces"] == s1["ray_bounces"] and s0["valid_rays"] == s1["valid_rays"]
+        assert s1["stack_overflows"] == 0
+        assert q1["node_visits"] == 0 and q1["tri_tests"] > 0 and p0["node_visits"] > 0
+        assert np.array_equal(R0, R1)
+    # hits ray by ray (aircraft) and the submitted batch path (trihedral)
+    hits = []
+    for ras in (0, 1):
+        with G.Context(0) as c:
+            c.load_mesh(air["xyz"], air["tri"])
+            c.set_tuning(raster=ras)
+            c.trace(air["angles"][[10, 100]], air["spacing"], eta=air["eta"], max_bounces=air["max_bounces"],
+                    offset=air["offset"], flags=G.TRACE_RECORD_HITS)
+            hits.append([c.get_hits(a) for a in range(2)])
+    for a, b in zip(*hits):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+    rng = np.random.default_rng(5)
+    reqs = [dict(az=float(rng.uniform(0, 90)), el=35.26, freqs=np.array([6e9, 10e9]),
+                 spacing=S.spacing_for(10e9, 6.0)) for _ in range(5)]
+    res = []
+    for ras in (0, 1):
+        with G.Context(0) as c:
+            c.load_mesh(tri_case["xyz"], tri_case["tri"])
+            c.set_tuning(raster=ras)
+            R = torch.zeros((10, 2), dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            c.submit_batch(reqs, None, R, max_bounces=3, offset=tri_case["offset"])
+            c.sync()
+            res.append(R.cpu().numpy())
     assert np.array_equal(res[0], res[1])
