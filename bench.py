@@ -684,11 +684,19 @@ def run_sbr(args, case, ws, rank, local, pg):
             traffic = per_ray * stats[0]["rays_launched"]
     pass_all_s = float(np.mean([s["pass_ms"] for s in stats])) / 1e3
     primary_s = float(np.mean([s["primary_ms"] for s in stats])) / 1e3
-    if raster:
+    bounce_s = pass_all_s - primary_s
+    dominant = "all"
+    if raster and bounce_s >= primary_s:
         # the traversal of the bounce passes: node visits and their triangle tests over their time
+        dominant = "bounce"
         ops = (OPS_NODE4 if wide else (OPS_NODE_OCT if octant else OPS_NODE)) * cnt["node_visits"] + \
             OPS_TRI * (cnt["tri_tests"] - cnt["raster_tests"])
-        pass_s = pass_all_s - primary_s
+        pass_s = bounce_s
+    elif raster:
+        # one bounce or short bounce passes: the rasterised primary pass, its triangle tests over its time
+        dominant = "primary"
+        ops = OPS_TRI * cnt["raster_tests"]
+        pass_s = primary_s
     else:
         ops = (OPS_NODE4 if wide else (OPS_NODE_OCT if octant else OPS_NODE)) * cnt["node_visits"] + \
             OPS_TRI * cnt["tri_tests"]
@@ -704,15 +712,18 @@ def run_sbr(args, case, ws, rank, local, pg):
             "angles_per_s": ws * na * args.steps / t_dev,
             "rays_launched_per_step": stats[0]["rays_launched"], "ray_bounces_per_step": bounces,
             "valid_rays_per_step": stats[0]["valid_rays"],
-            "roofline": {"bound": "alu", "kernel": ("k_bounce (bounce passes" if raster else
-                                                    "k_primary+k_bounce (transport passes") +
-                         f", {'4-wide' if wide else ('binary, octant copies' if octant else 'binary')} tree)",
+            "roofline": {"bound": "alu", "kernel": ("k_raster+k_vis_mask+k_primary_vis (rasterised primary pass)"
+                                                    if dominant == "primary" else
+                                                    ("k_bounce (bounce passes" if dominant == "bounce" else
+                                                     "k_primary+k_bounce (transport passes") +
+                                                    f", {'4-wide' if wide else ('binary, octant copies' if octant else 'binary')} tree)"),
                          "achieved": achieved, "peak": peak_ops, "unit": "T FP32-op/s",
                          "frac": achieved / peak_ops, "traffic": traffic,
                          "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                         f"{pk.get('sm_max_mhz', 2070.0):g} MHz ({src} SM clock)",
-                         "ops_per_step": ops, "node_visits": cnt["node_visits"],
-                         "tri_tests": cnt["tri_tests"] - (cnt["raster_tests"] if raster else 0),
+                         "ops_per_step": ops, "node_visits": 0 if dominant == "primary" else cnt["node_visits"],
+                         "tri_tests": (cnt["raster_tests"] if dominant == "primary" else
+                                       cnt["tri_tests"] - (cnt["raster_tests"] if raster else 0)),
                          "pass_ms_per_step": pass_s * 1e3},
             "primary": {"kernel": "k_raster+k_vis_mask+k_primary_vis (rasterised primary hits)" if raster else
                         "k_primary (traversed)", "ms_per_step": primary_s * 1e3,
