@@ -225,3 +225,56 @@ def test_raster_primary_hits_equal_traversal(G, tri_case):
             c.sync()
             res.append(R.cpu().numpy())
     assert np.array_equal(res[0], res[1])
+
+
+def test_raster_with_flagged_and_rasterised_aspects_in_one_chunk(G, orc):
+    """A chunk whose aspects split between rasterised primary hits and the
+    traversal fallback: a 1 m plate triangle spans ~20,000 grid cells seen
+    face-on (flagged: its aspect traverses) and ~1,700 at grazing incidence
+    (rasterised), beside a small-triangle sphere. The traversing rays are
+    appended after the rasterised ones; every hit equals the traversal's and
+    the oracle's, in the plain and the submitted batch paths."""
+    torch = pytest.importorskip("torch")
+    from parity import assert_hit_parity, compare_hits
+
+    xs, ts = S.icosphere(3, radius=0.3)
+    xs = xs + np.array([0.0, 0.0, 0.8], np.float32)
+    xp = np.array([[-0.5, -0.5, 0.0], [0.5, -0.5, 0.0], [-0.5, 0.5, 0.0]], np.float32)
+    xyz = np.concatenate([xs, xp])
+    tri = np.concatenate([ts, np.array([[0, 1, 2]], np.int32) + len(xs)])
+    ang = np.array([[0.0, 90.0], [30.0, 5.0], [200.0, 60.0], [45.0, 5.0]])
+    sp = 0.005
+    om = orc.Mesh(xyz, tri)
+    out = []
+    for ras in (0, 1):
+        with G.Context(0) as c:
+            c.load_mesh(xyz, tri)
+            c.set_tuning(raster=ras)
+            st = c.trace(ang, sp, max_bounces=3, flags=G.TRACE_RECORD_HITS | G.TRACE_COUNT_VISITS)
+            hits = [c.get_hits(a) for a in range(len(ang))]
+            out.append((st, hits, c.po_integrate([10e9])[1]))
+            if ras:
+                for a, (az, el) in enumerate(ang):
+                    fr = orc.make_frame(om.bbox, az, el, sp)
+                    assert_hit_parity(compare_hits(*hits[a], orc.trace(om, fr, 3)))
+    (s0, h0, R0), (s1, h1, R1) = out
+    assert s1["raster_tests"] > 0 and 0 < s1["node_visits"]
+    assert s0["ray_bounces"] == s1["ray_bounces"] and s0["valid_rays"] == s1["valid_rays"]
+    for a, b in zip(h0, h1):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
+    assert np.array_equal(R0, R1)
+    reqs = [dict(az=float(az), el=float(el), freqs=np.array([10e9]), spacing=sp) for az, el in ang]
+    res = []
+    for ras in (0, 1):
+        with G.Context(0) as c:
+            c.load_mesh(xyz, tri)
+            c.set_tuning(raster=ras)
+            R = torch.zeros((len(reqs), 2), dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            c.submit_batch(reqs, None, R, max_bounces=3)
+            c.sync()
+            res.append(R.cpu().numpy())
+    assert np.array_equal(res[0], res[1])
+    assert np.array_equal(res[1], R1[:, 0, :])
+
