@@ -469,6 +469,7 @@ int sbr_build_bvh(sbr_ctx* c, const sbr_bvh_opts* opt)
     CK(cudaStreamSynchronize(c->stream), "bvh build sync");
     if (herr) {
         c->has_mesh = false;
+        if (herr & 4) return fail(c, SBR_ERR_CUDA, "sbr_build_bvh: the clustering did not converge");
         return fail(c, SBR_ERR_ARG, (herr & 1) ? "sbr_build_bvh: triangle index out of range"
                                                : "sbr_build_bvh: a vertex coordinate is not finite");
     }
@@ -479,7 +480,7 @@ int sbr_build_bvh(sbr_ctx* c, const sbr_bvh_opts* opt)
         char* scr = (char*)c->bvh_scratch.p;
         const size_t qb = ((sizeof(int2) * (size_t)n_nodes + 255) / 256) * 256;
         if (2 * qb + 256 > c->bvh_scratch.cap) return fail(c, SBR_ERR_ARG, "sbr_build_bvh: scratch too small");
-        CK(bvh4_collapse(c->nodes.as<float4>(), c->nodes4.as<float4>(), (int2*)scr, (int2*)(scr + qb),
+        CK(bvh4_collapse(c->nodes.as<float4>(), n_nodes, c->nodes4.as<float4>(), (int2*)scr, (int2*)(scr + qb),
                          (int*)(scr + 2 * qb), &c->n_nodes4, c->stream),
            "4-wide collapse");
     }

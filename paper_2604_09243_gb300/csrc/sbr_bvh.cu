@@ -418,11 +418,8 @@ struct Clusters {
     float* cost;
 };
 
-__global__ void __launch_bounds__(kThreads) k_ploc_init(const unsigned* vals, const float4* tbox, int n, float c_i,
-                                                        Clusters c)
+__device__ __forceinline__ void ploc_init_one(int i, const unsigned* vals, const float4* tbox, float c_i, Clusters c)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
     const unsigned t = vals[i];
     const float4 lo = tbox[2 * (size_t)t], hi = tbox[2 * (size_t)t + 1];
     c.lo[i] = lo;
@@ -432,17 +429,21 @@ __global__ void __launch_bounds__(kThreads) k_ploc_init(const unsigned* vals, co
     c.cost[i] = c_i * area(lo, hi);
 }
 
+__global__ void __launch_bounds__(kThreads) k_ploc_init(const unsigned* vals, const float4* tbox, int n, float c_i,
+                                                        Clusters c)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) ploc_init_one(i, vals, tbox, c_i, c);
+}
+
 __device__ __forceinline__ float union_area(float4 al, float4 ah, float4 bl, float4 bh)
 {
     return area(make_float4(fminf(al.x, bl.x), fminf(al.y, bl.y), fminf(al.z, bl.z), 0.f),
                 make_float4(fmaxf(ah.x, bh.x), fmaxf(ah.y, bh.y), fmaxf(ah.z, bh.z), 0.f));
 }
 
-__global__ void __launch_bounds__(kThreads) k_ploc_nn(const int* m_dev, int radius, Clusters c, int* nn)
+__device__ __forceinline__ void ploc_nn_one(int i, int m, int radius, Clusters c, int* nn)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int m = *m_dev;
-    if (i >= m) return;
     const float4 lo = c.lo[i], hi = c.hi[i];
     float best = FLT_MAX;
     int bj = -1;
@@ -458,19 +459,39 @@ __global__ void __launch_bounds__(kThreads) k_ploc_nn(const int* m_dev, int radi
     nn[i] = bj;
 }
 
-// par / rel: parent and offset within the parent of node x (x < n - 1) or of
-// triangle t (x = n - 1 + t), for the pointer-jumping position pass
-__global__ void __launch_bounds__(kThreads) k_ploc_merge(const int* m_dev, int m_ub, int n, Clusters c, const int* nn,
-                                                         int* next_id, int* left, int* right, float4* nbox, int* ncnt,
-                                                         float* ncost, int* ncol, int* par, int* rel, unsigned* keep,
-                                                         int leaf_max, float c_t, float c_i)
+__global__ void __launch_bounds__(kThreads) k_ploc_nn(const int* m_dev, int radius, Clusters c, int* nn)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m_ub) return;
-    if (i >= *m_dev) {
-        keep[i] = 0;  // beyond the live clusters of this round
-        return;
-    }
+    const int m = *m_dev;
+    if (i < m) ploc_nn_one(i, m, radius, c, nn);
+}
+
+// par / rel: parent and offset within the parent of node x (x < n - 1) or of
+// triangle t (x = n - 1 + t), for the pointer-jumping position pass
+// node arrays written by the merges
+struct PlocNodes {
+    int* left;
+    int* right;
+    float4* nbox;
+    int* ncnt;
+    float* ncost;
+    int* ncol;
+    int* par;  // parent and offset within the parent of node x or triangle n - 1 + t
+    int* rel;
+};
+
+// cluster i < m of this round: merge with its mutual nearest neighbour
+__device__ __forceinline__ void ploc_merge_one(int i, int n, Clusters c, const int* nn, int* next_id, PlocNodes g,
+                                               unsigned* keep, int leaf_max, float c_t, float c_i)
+{
+    int* left = g.left;
+    int* right = g.right;
+    float4* nbox = g.nbox;
+    int* ncnt = g.ncnt;
+    float* ncost = g.ncost;
+    int* ncol = g.ncol;
+    int* par = g.par;
+    int* rel = g.rel;
     const int j = nn[i];
     if (j < 0 || nn[j] != i) {
         keep[i] = 1;  // no mutual partner this round
@@ -510,11 +531,23 @@ __global__ void __launch_bounds__(kThreads) k_ploc_merge(const int* m_dev, int m
     keep[i] = 1;
 }
 
-__global__ void __launch_bounds__(kThreads) k_ploc_compact(int m_ub, Clusters in, const unsigned* keep,
-                                                           const unsigned* pos, Clusters out)
+__global__ void __launch_bounds__(kThreads) k_ploc_merge(const int* m_dev, int m_ub, int n, Clusters c, const int* nn,
+                                                         int* next_id, PlocNodes g, unsigned* keep, int leaf_max,
+                                                         float c_t, float c_i)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m_ub || !keep[i]) return;
+    if (i >= m_ub) return;
+    if (i >= *m_dev) {
+        keep[i] = 0;  // beyond the live clusters of this round
+        return;
+    }
+    ploc_merge_one(i, n, c, nn, next_id, g, keep, leaf_max, c_t, c_i);
+}
+
+__device__ __forceinline__ void ploc_compact_one(int i, Clusters in, const unsigned* keep, const unsigned* pos,
+                                                 Clusters out)
+{
+    if (!keep[i]) return;
     const unsigned k = pos[i];
     out.lo[k] = in.lo[i];
     out.hi[k] = in.hi[i];
@@ -523,14 +556,18 @@ __global__ void __launch_bounds__(kThreads) k_ploc_compact(int m_ub, Clusters in
     out.cost[k] = in.cost[i];
 }
 
+__global__ void __launch_bounds__(kThreads) k_ploc_compact(int m_ub, Clusters in, const unsigned* keep,
+                                                           const unsigned* pos, Clusters out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m_ub) ploc_compact_one(i, in, keep, pos, out);
+}
+
 // position pass by pointer jumping: after round r every entry holds the sum of
 // rel over its nearest 2^r ancestors and points 2^r levels up; once every
 // pointer has left the root, rel is the first position of the node's triangles
-__global__ void __launch_bounds__(kThreads) k_ploc_jump(int count, const int* par_in, const int* rel_in, int* par_out,
-                                                        int* rel_out)
+__device__ __forceinline__ void ploc_jump_one(int x, const int* par_in, const int* rel_in, int* par_out, int* rel_out)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= count) return;
     const int p = par_in[x];
     if (p < 0) {
         par_out[x] = p;
@@ -541,11 +578,22 @@ __global__ void __launch_bounds__(kThreads) k_ploc_jump(int count, const int* pa
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_ploc_positions(int n, const int* rel, int* noff, unsigned* perm)
+__global__ void __launch_bounds__(kThreads) k_ploc_jump(int count, const int* par_in, const int* rel_in, int* par_out,
+                                                        int* rel_out)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x < count) ploc_jump_one(x, par_in, rel_in, par_out, rel_out);
+}
+
+__device__ __forceinline__ void ploc_positions_one(int x, int n, const int* rel, int* noff, unsigned* perm)
+{
     if (x < n - 1) noff[x] = rel[x];
     else if (x < 2 * n - 1) perm[rel[x]] = (unsigned)(x - (n - 1));
+}
+
+__global__ void __launch_bounds__(kThreads) k_ploc_positions(int n, const int* rel, int* noff, unsigned* perm)
+{
+    ploc_positions_one(blockIdx.x * blockDim.x + threadIdx.x, n, rel, noff, perm);
 }
 
 __global__ void __launch_bounds__(kThreads) k_ploc_emit(int n, const int* left, const int* right, const float4* nbox,
@@ -603,12 +651,9 @@ __device__ __forceinline__ void binary_children(const float4* nodes2, int b, flo
 // One level: every queued (binary node, 4-wide slot) pair opens binary
 // children, largest surface area first, until it has 4 children or only
 // leaves; its internal children get new slots and go to the next level's queue.
-__global__ void __launch_bounds__(kThreads) k_collapse4(const float4* nodes2, const int2* qin, int nin, int2* qout,
-                                                        int* nout, int* count4, float4* nodes4)
+__device__ __forceinline__ void collapse4_one(const float4* nodes2, int2 job, int2* qout, int* nout, int* count4,
+                                              float4* nodes4)
 {
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= nin) return;
-    const int2 job = qin[w];
     float4 lo[4], hi[4];
     int ref[4];
     int cnt = 0;
@@ -671,6 +716,185 @@ __global__ void __launch_bounds__(kThreads) k_collapse4(const float4* nodes2, co
     for (int k = 0; k < 6; ++k) o[k] = make_float4(v[k][0], v[k][1], v[k][2], v[k][3]);
     o[6] = make_float4(__int_as_float(r[0]), __int_as_float(r[1]), __int_as_float(r[2]), __int_as_float(r[3]));
     o[7] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__global__ void __launch_bounds__(kThreads) k_collapse4(const float4* nodes2, const int2* qin, int nin, int2* qout,
+                                                        int* nout, int* count4, float4* nodes4)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w < nin) collapse4_one(nodes2, qin[w], qout, nout, count4, nodes4);
+}
+
+// ---------------------------------------------------------------- single-block build of small meshes
+// A mesh of at most kSmallBuild triangles is too small to fill the GPU, and
+// the per-round launches and host reads of the clustering would dominate its
+// build. One block of kSmallThreads threads runs the same steps with barriers
+// between them: the Morton sort (bitonic network on (key, index) pairs in
+// shared memory, which gives the order of the stable radix sort), the PLOC
+// rounds (same nearest-neighbour, merge and compaction functions) and the
+// pointer-jumping positions; the 4-wide collapse runs its levels the same way.
+constexpr int kSmallThreads = 1024;
+constexpr int kSmallBuild = 16384;  // 12 bytes per triangle of shared memory for the sort
+
+struct SmallBuild {
+    const unsigned long long* keys;  // Morton keys of the triangles (unsorted)
+    const unsigned* vals;            // their triangle ids
+    const float4* tbox;
+    int n, leaf_max, radius;
+    float c_t, c_i;
+    Clusters cl[2];
+    int* nn;
+    unsigned* keep;
+    unsigned* pos;
+    PlocNodes g;
+    int* par[2];
+    int* rel[2];
+    int* noff;
+    unsigned* perm;
+    int* err;  // bit 4: the clustering did not converge
+};
+
+// exclusive scan of in[0..m) into out over the whole block; returns the total
+__device__ unsigned block_exclusive_scan(const unsigned* in, unsigned* out, int m, unsigned* s_part)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, n_warps = blockDim.x >> 5;
+    const int per = (m + blockDim.x - 1) / blockDim.x;
+    const int b0 = min(m, tid * per), b1 = min(m, b0 + per);
+    unsigned sum = 0;
+    for (int k = b0; k < b1; ++k) sum += in[k];
+    unsigned x = sum;  // inclusive scan over the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_part[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned w = lane < n_warps ? s_part[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        s_part[lane] = w;  // inclusive over the warps
+    }
+    __syncthreads();
+    unsigned pre = x - sum + (warp > 0 ? s_part[warp - 1] : 0u);
+    for (int k = b0; k < b1; ++k) {
+        out[k] = pre;
+        pre += in[k];
+    }
+    const unsigned total = s_part[n_warps - 1];
+    __syncthreads();  // s_part is reused by the next call
+    return total;
+}
+
+__global__ void __launch_bounds__(kSmallThreads) k_build_small(const SmallBuild b)
+{
+    extern __shared__ unsigned long long s_key[];  // [n] keys, then [n] triangle ids
+    __shared__ unsigned s_part[32];
+    __shared__ int s_m, s_next;
+    const int tid = threadIdx.x, nt = blockDim.x, n = b.n;
+    unsigned* s_val = reinterpret_cast<unsigned*>(s_key + n);
+    for (int i = tid; i < n; i += nt) {
+        s_key[i] = b.keys[i];
+        s_val[i] = b.vals[i];
+    }
+    __syncthreads();
+    // ascending by (key, id): bitonic merges over the next power of two; the
+    // first step of each merge compares mirrored positions, so pairs reaching
+    // past n (virtual +infinity) are already in order and are skipped
+    int P = 1;
+    while (P < n) P <<= 1;
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < (P >> 1); i += nt) {
+                const int blk = i / j, off = i - blk * j;
+                const int a = (j == (k >> 1)) ? blk * k + off : blk * 2 * j + off;
+                const int c = (j == (k >> 1)) ? blk * k + k - 1 - off : a + j;
+                if (c < n) {
+                    const unsigned long long ka = s_key[a], kc = s_key[c];
+                    const unsigned va = s_val[a], vc = s_val[c];
+                    if (ka > kc || (ka == kc && va > vc)) {
+                        s_key[a] = kc;
+                        s_key[c] = ka;
+                        s_val[a] = vc;
+                        s_val[c] = va;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = tid; i < n; i += nt) ploc_init_one(i, s_val, b.tbox, b.c_i, b.cl[0]);
+    if (tid == 0) {
+        s_m = n;
+        s_next = n - 2;
+    }
+    __syncthreads();
+    int cur = 0;
+    for (int round = 0;; ++round) {
+        const int m = s_m;  // the same in every thread: read after a barrier
+        if (m <= 1) break;
+        if (round >= (1 << 16)) {  // every round merges at least one pair
+            if (tid == 0) atomicOr(b.err, 4);
+            break;
+        }
+        for (int i = tid; i < m; i += nt) ploc_nn_one(i, m, b.radius, b.cl[cur], b.nn);
+        __syncthreads();
+        for (int i = tid; i < m; i += nt)
+            ploc_merge_one(i, n, b.cl[cur], b.nn, &s_next, b.g, b.keep, b.leaf_max, b.c_t, b.c_i);
+        __syncthreads();
+        const unsigned total = block_exclusive_scan(b.keep, b.pos, m, s_part);
+        for (int i = tid; i < m; i += nt) ploc_compact_one(i, b.cl[cur], b.keep, b.pos, b.cl[cur ^ 1]);
+        __syncthreads();
+        if (tid == 0) s_m = (int)total;
+        cur ^= 1;
+        __syncthreads();
+    }
+    int jr = 1;
+    while ((1 << jr) < n) ++jr;
+    int pj = 0;
+    for (int r = 0; r <= jr; ++r, pj ^= 1) {
+        for (int x = tid; x < 2 * n - 1; x += nt) ploc_jump_one(x, b.par[pj], b.rel[pj], b.par[pj ^ 1], b.rel[pj ^ 1]);
+        __syncthreads();
+    }
+    for (int x = tid; x < 2 * n - 1; x += nt) ploc_positions_one(x, n, b.rel[pj], b.noff, b.perm);
+}
+
+// counters[0]: 4-wide nodes allocated; [1]: next-level queue length; [2]: 1 if too deep
+__global__ void __launch_bounds__(kSmallThreads) k_collapse4_small(const float4* nodes2, int2* qa, int2* qb,
+                                                                   int* counters, float4* nodes4)
+{
+    __shared__ int s_nin;
+    if (threadIdx.x == 0) {
+        qa[0] = make_int2(0, 0);
+        counters[0] = 1;
+        counters[1] = 0;
+        counters[2] = 0;
+        s_nin = 1;
+    }
+    __syncthreads();
+    int2 *qi = qa, *qo = qb;
+    for (int level = 0;; ++level) {
+        const int nin = s_nin;
+        if (nin <= 0) break;
+        if (level > 4096) {  // deeper than any binary tree of < 2^27 leaves
+            if (threadIdx.x == 0) counters[2] = 1;
+            break;
+        }
+        for (int w = threadIdx.x; w < nin; w += blockDim.x) collapse4_one(nodes2, qi[w], qo, counters + 1, counters, nodes4);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_nin = counters[1];
+            counters[1] = 0;
+        }
+        __syncthreads();
+        int2* t = qi;
+        qi = qo;
+        qo = t;
+    }
 }
 
 // ---------------------------------------------------------------- octant copies
@@ -799,6 +1023,42 @@ cudaError_t bvh_build(const BvhBuild& b, cudaStream_t st)
     k_vertex_box<<<gv, kThreads, 0, st>>>(b.xyz, b.n_vert, acc, b.err_flag);
     k_prep<<<g, kThreads, 0, st>>>(b.xyz, b.tri, b.n_vert, n, tbox, cen, acc, b.err_flag);
     k_morton<<<g, kThreads, 0, st>>>(cen, n, acc, k0, v0, b.bbox_out);
+    if (b.builder == 1 && n > 1 && n <= kSmallBuild) {
+        const int nx = 2 * n - 1;
+        cudaError_t e = cudaMemsetAsync(par[0], 0xFF, sizeof(int) * (size_t)nx, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(rel[0], 0, sizeof(int) * (size_t)nx, st);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_build_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(12 * (size_t)kSmallBuild));
+        if (e != cudaSuccess) return e;
+        SmallBuild sb;
+        sb.keys = k0;
+        sb.vals = v0;
+        sb.tbox = tbox;
+        sb.n = n;
+        sb.leaf_max = b.leaf_max;
+        sb.radius = b.radius > 0 ? b.radius : 16;
+        sb.c_t = b.c_t;
+        sb.c_i = b.c_i;
+        sb.cl[0] = cl[0];
+        sb.cl[1] = cl[1];
+        sb.nn = pnn;
+        sb.keep = keep;
+        sb.pos = pos;
+        sb.g = {left, right, nbox, ncnt, ncost, ncol, par[0], rel[0]};
+        sb.par[0] = par[0];
+        sb.par[1] = par[1];
+        sb.rel[0] = rel[0];
+        sb.rel[1] = rel[1];
+        sb.noff = noff;
+        sb.perm = perm;
+        sb.err = b.err_flag;
+        k_build_small<<<1, kSmallThreads, 12 * (size_t)n, st>>>(sb);
+        k_ploc_emit<<<(n - 1 + kThreads - 1) / kThreads, kThreads, 0, st>>>(n, left, right, nbox, ncnt, ncol, noff,
+                                                                            tbox, b.nodes);
+        k_reorder<<<g, kThreads, 0, st>>>(b.xyz, b.tri, b.n_vert, perm, n, b.tris, b.tri_pos);
+        return cudaGetLastError();
+    }
     unsigned long long *ki = k0, *ko = k1;
     unsigned *vi = v0, *vo = v1;
     for (int pass = 0; pass < 8; ++pass) {
@@ -822,14 +1082,14 @@ cudaError_t bvh_build(const BvhBuild& b, cudaStream_t st)
         cudaError_t e = cudaMemcpyAsync(ctr, h, sizeof(h), cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(par[0], 0xFF, sizeof(int) * (size_t)nx, st);
         if (e == cudaSuccess) e = cudaMemsetAsync(rel[0], 0, sizeof(int) * (size_t)nx, st);
+        const PlocNodes pg = {left, right, nbox, ncnt, ncost, ncol, par[0], rel[0]};
         int m = n, cur = 0;
         for (int round = 0; e == cudaSuccess && m > 1; round += kRoundsPerSync) {
             if (round >= 1 << 16) return cudaErrorInvalidValue;  // every round merges at least one pair
             const int gm = (m + kThreads - 1) / kThreads;
             for (int r = 0; r < kRoundsPerSync && e == cudaSuccess; ++r) {
                 k_ploc_nn<<<gm, kThreads, 0, st>>>(ctr + 1, radius, cl[cur], pnn);
-                k_ploc_merge<<<gm, kThreads, 0, st>>>(ctr + 1, m, n, cl[cur], pnn, ctr, left, right, nbox, ncnt, ncost,
-                                                      ncol, par[0], rel[0], keep, b.leaf_max, c_t, c_i);
+                k_ploc_merge<<<gm, kThreads, 0, st>>>(ctr + 1, m, n, cl[cur], pnn, ctr, pg, keep, b.leaf_max, c_t, c_i);
                 e = scan_exclusive_u32(keep, pos, m, false, (unsigned*)(ctr + 1), pscan, st);
                 if (e != cudaSuccess) break;
                 k_ploc_compact<<<gm, kThreads, 0, st>>>(m, cl[cur], keep, pos, cl[cur ^ 1]);
@@ -873,9 +1133,19 @@ cudaError_t build_octant_nodes(const float4* nodes, long long n_nodes, float4* o
     return cudaGetLastError();
 }
 
-cudaError_t bvh4_collapse(const float4* nodes2, float4* nodes4, int2* queue_a, int2* queue_b, int* counters,
-                          int* n_nodes4, cudaStream_t st)
+cudaError_t bvh4_collapse(const float4* nodes2, long long n_nodes2, float4* nodes4, int2* queue_a, int2* queue_b,
+                          int* counters, int* n_nodes4, cudaStream_t st)
 {
+    if (n_nodes2 <= kSmallBuild) {
+        k_collapse4_small<<<1, kSmallThreads, 0, st>>>(nodes2, queue_a, queue_b, counters, nodes4);
+        int h[3] = {0, 0, 0};
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h, counters, sizeof(h), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess && h[2]) e = cudaErrorInvalidValue;
+        if (e == cudaSuccess) *n_nodes4 = h[0];
+        return e;
+    }
     // counters[0]: 4-wide nodes allocated; counters[1]: next-level queue length
     const int2 root = make_int2(0, 0);
     const int one = 1;

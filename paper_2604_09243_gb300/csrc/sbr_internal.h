@@ -96,10 +96,11 @@ constexpr int kNode4Float4 = 8;
 // hi = -FLT_MAX) has near > far on every axis, so it is never entered.
 cudaError_t build_octant_nodes(const float4* nodes, long long n_nodes, float4* out, cudaStream_t st);
 // Collapse the binary node array (root 0) into nodes4 (room for max(n_tri - 1, 1) nodes).
-// queue_a / queue_b: int2 [max(n_tri - 1, 1)]; counters: int [4]. Synchronises once per level;
+// queue_a / queue_b: int2 [max(n_tri - 1, 1)]; counters: int [4]. A tree of at most 16384 binary
+// nodes is collapsed by one block in one launch; a larger one synchronises once per level.
 // *n_nodes4 receives the node count.
-cudaError_t bvh4_collapse(const float4* nodes2, float4* nodes4, int2* queue_a, int2* queue_b, int* counters,
-                          int* n_nodes4, cudaStream_t st);
+cudaError_t bvh4_collapse(const float4* nodes2, long long n_nodes2, float4* nodes4, int2* queue_a, int2* queue_b,
+                          int* counters, int* n_nodes4, cudaStream_t st);
 
 struct BvhBuild {
     // inputs
@@ -115,7 +116,8 @@ struct BvhBuild {
     float4* tris;
     int* tri_pos;     // [n_tri]: position in tris of each original triangle index
     float* bbox_out;  // device float[6] scene box of the vertices
-    int* err_flag;    // device int: bit 1 a triangle index out of range, bit 2 a non-finite coordinate
+    int* err_flag;    // device int: bit 1 a triangle index out of range, bit 2 a non-finite coordinate,
+                      // bit 4 the clustering did not converge
     // scratch (caller-owned)
     void* scratch;
     size_t scratch_bytes;
