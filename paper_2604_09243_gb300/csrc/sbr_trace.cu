@@ -474,11 +474,14 @@ struct Ray {
     int angle, local, last, nb;
 };
 
+// The live-ray queues, the records and the raster keys are each written once
+// and read once: their loads and stores are marked evict-first (__ldcs /
+// __stcs) so that they do not push the tree and the triangles out of L1 and L2.
 __device__ __forceinline__ void load_state(const RayState* __restrict__ q, unsigned i, Ray& r)
 {
     const float4* p = reinterpret_cast<const float4*>(q + i);
-    float4 a = p[0], b = p[1], c = p[2], e = p[3], f = p[4];
-    int4 g = reinterpret_cast<const int4*>(p)[5];
+    float4 a = __ldcs(p), b = __ldcs(p + 1), c = __ldcs(p + 2), e = __ldcs(p + 3), f = __ldcs(p + 4);
+    int4 g = __ldcs(reinterpret_cast<const int4*>(p) + 5);
     r.o = make_float3(a.x, a.y, a.z);
     r.d = make_float3(a.w, b.x, b.y);
     r.ev = make_float3(b.z, b.w, c.x);
@@ -499,17 +502,17 @@ __device__ __forceinline__ void load_state(const RayState* __restrict__ q, unsig
 __device__ __forceinline__ void load_geom(const RayState* __restrict__ q, unsigned i, Ray& r)
 {
     const float4* p = reinterpret_cast<const float4*>(q + i);
-    const float4 a = p[0], b = p[1];
+    const float4 a = __ldcs(p), b = __ldcs(p + 1);
     r.o = make_float3(a.x, a.y, a.z);
     r.d = make_float3(a.w, b.x, b.y);
-    r.last = reinterpret_cast<const int4*>(p)[5].z;
+    r.last = __ldcs(reinterpret_cast<const int4*>(p) + 5).z;
 }
 
 __device__ __forceinline__ void load_payload(const RayState* __restrict__ q, unsigned i, Ray& r)
 {
     const float4* p = reinterpret_cast<const float4*>(q + i);
-    const float4 b = p[1], c = p[2], e = p[3], f = p[4];
-    const int4 g = reinterpret_cast<const int4*>(p)[5];
+    const float4 b = __ldcs(p + 1), c = __ldcs(p + 2), e = __ldcs(p + 3), f = __ldcs(p + 4);
+    const int4 g = __ldcs(reinterpret_cast<const int4*>(p) + 5);
     r.ev = make_float3(b.z, b.w, c.x);
     r.lacc_hi = c.y;
     r.lacc_lo = c.z;
@@ -525,12 +528,12 @@ __device__ __forceinline__ void load_payload(const RayState* __restrict__ q, uns
 __device__ __forceinline__ void store_state(RayState* __restrict__ q, unsigned i, const Ray& r)
 {
     float4* p = reinterpret_cast<float4*>(q + i);
-    p[0] = make_float4(r.o.x, r.o.y, r.o.z, r.d.x);
-    p[1] = make_float4(r.d.y, r.d.z, r.ev.x, r.ev.y);
-    p[2] = make_float4(r.ev.z, r.lacc_hi, r.lacc_lo, r.cos0);
-    p[3] = make_float4(r.c[0], r.c[1], r.c[2], r.c[3]);
-    p[4] = make_float4(r.c[4], r.lc_hi, r.lc_lo, r.nfs);
-    reinterpret_cast<int4*>(p)[5] = make_int4(r.angle, r.local, r.last, r.nb);
+    __stcs(p + 0, make_float4(r.o.x, r.o.y, r.o.z, r.d.x));
+    __stcs(p + 1, make_float4(r.d.y, r.d.z, r.ev.x, r.ev.y));
+    __stcs(p + 2, make_float4(r.ev.z, r.lacc_hi, r.lacc_lo, r.cos0));
+    __stcs(p + 3, make_float4(r.c[0], r.c[1], r.c[2], r.c[3]));
+    __stcs(p + 4, make_float4(r.c[4], r.lc_hi, r.lc_lo, r.nfs));
+    __stcs(reinterpret_cast<int4*>(p) + 5, make_int4(r.angle, r.local, r.last, r.nb));
 }
 
 __device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
@@ -657,11 +660,11 @@ __device__ __forceinline__ void emit(const TraceArgs& a, const Ray& r, bool zero
     const unsigned slot = a.tile_base[tile] + __popc(a.mask[tile] & ((1u << bit) - 1u));
     float4* p = reinterpret_cast<float4*>(a.rec + slot);
     if (zero) {
-        p[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-        p[1] = make_float4(0.f, 0.f, 0.f, __int_as_float(ray_id));
+        __stcs(p + 0, make_float4(0.f, 0.f, 0.f, 0.f));
+        __stcs(p + 1, make_float4(0.f, 0.f, 0.f, __int_as_float(ray_id)));
     } else {
-        p[0] = make_float4(r.c[0], r.c[1], r.c[2], r.c[3]);
-        p[1] = make_float4(r.c[4], r.lc_hi, r.lc_lo, __int_as_float(ray_id));
+        __stcs(p + 0, make_float4(r.c[0], r.c[1], r.c[2], r.c[3]));
+        __stcs(p + 1, make_float4(r.c[4], r.lc_hi, r.lc_lo, __int_as_float(ray_id)));
     }
     if (a.hit_nb) a.hit_nb[g] = r.nb;
 }
@@ -1067,7 +1070,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_primary_vis(const TraceArgs a
             if (i < A.nu && j < A.nv) ++nq;
             const unsigned vmask = a.mask[tile];  // k_vis_mask
             if ((vmask >> lane) & 1u) {
-                const unsigned long long key = a.vis[base + lane];
+                const unsigned long long key = __ldcs(a.vis + base + lane);
                 Hit h;
                 h.t = __uint_as_float((unsigned)(key >> 32));
                 h.orig = (int)(unsigned)key;
