@@ -60,8 +60,8 @@ OPS_TRI = 38
 # size leave the bytes per ray unchanged (the queues and records are the
 # traffic); it grows with the rays, so it is scaled by the rays of a step.
 TRAFFIC_PER_RAY = {"trihedral": [(188.39e6 / 2114692, dict(tile_w=4, bvh_width=2, packet=0, octant=0, raster=0), "ploc"),
-                                  (179.67e6 / 2114692, dict(tile_w=4, bvh_width=2, packet=0, octant=0, raster=1), "ploc"),
-                                  (179.46e6 / 2114692, dict(tile_w=4, bvh_width=2, packet=0, octant=1, raster=1), "ploc")]}
+                                  (176.22e6 / 2114692, dict(tile_w=4, bvh_width=2, packet=0, octant=0, raster=1), "ploc"),
+                                  (175.73e6 / 2114692, dict(tile_w=4, bvh_width=2, packet=0, octant=1, raster=1), "ploc")]}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
