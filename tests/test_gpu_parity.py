@@ -241,6 +241,21 @@ def test_degenerate_duplicate_and_non_finite_meshes(G, ctx, orc):
     assert_hit_parity(compare_hits(*res[0][0], res[0][1]))
 
 
+@pytest.mark.parametrize("n_tri", [16383, 16384, 16385])
+def test_tree_build_size_limits(G, ctx, orc, n_tri):
+    """Meshes at the size where the tree build changes from one block (sort,
+    clustering and collapse in one launch, up to 16384 triangles) to a launch
+    per clustering round: both trees give every ray the oracle's hits."""
+    xyz, tri = S.icosphere(5)
+    tri = tri[:n_tri]
+    ctx.load_mesh(xyz, tri)
+    om = orc.Mesh(xyz, tri)
+    st, res = _trace_both(G, ctx, orc, om, np.array([[10.0, 20.0], [200.0, -35.0]]), 0.01, 2, window=2.2)
+    assert st["stack_overflows"] == 0
+    for g, o, fr in res:
+        assert_hit_parity(compare_hits(*g, o))
+
+
 def test_all_rays_miss_gives_empty_sum(G, ctx):
     xyz, tri = S.square_plate(1.0, 2)
     ctx.load_mesh(xyz, tri)
