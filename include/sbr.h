@@ -407,6 +407,12 @@ int sbr_surrogate_predict(sbr_surrogate* s, const double* x, int64_t n, double* 
  * the stream; SBR_ERR_TIMEOUT if a bounded wait inside the kernel gave up. */
 int sbr_gemm_bf16_tn(const void* A, int lda, const void* B, int ldb, int M, int N, int K, float* C, int ldc,
                      void* cuda_stream);
+/* The same GEMM, only enqueued on the stream (no synchronisation): for callers that launch many and time them
+ * on the device. err_dev: a device int the caller zeroes beforehand; a kernel whose bounded wait gave up sets
+ * it to 1 (the caller reads it after synchronising). Returns SBR_ERR_ARG for a bad shape or pointer and
+ * SBR_ERR_CUDA if the launch failed. */
+int sbr_gemm_bf16_tn_async(const void* A, int lda, const void* B, int ldb, int M, int N, int K, float* C, int ldc,
+                           int* err_dev, void* cuda_stream);
 
 /* ---- allocation-free PO sum ------------------------------------------------
  * The paper has no counterpart of this call; it exists for callers that cannot

@@ -4,8 +4,8 @@ The compute path lives in ``lib/libsbr.so`` (CUDA, C ABI in ``include/sbr.h``);
 ``sbr`` is its ctypes binding. Build with ``paper_2604_09243_gb300.build.build()``.
 """
 from .sbr import (  # noqa: F401
-    Context, SbrError, Surrogate, gemm_bf16_tn, lib, ray_grid, spacing_for, version, POL_ORDER, EXPORTS,
-    po_integrate_noalloc,
+    Context, SbrError, Surrogate, gemm_bf16_tn, gemm_bf16_tn_async, lib, ray_grid, spacing_for, version, POL_ORDER,
+    EXPORTS, po_integrate_noalloc,
     TRACE_PHASE_LITERAL_2R, TRACE_REQUIRE_ESCAPE, TRACE_RECORD_HITS, TRACE_COUNT_VISITS, TRACE_TIME_PASSES,
     TRACE_NO_GRAPH,
 )

@@ -515,6 +515,22 @@ int sbr_gemm_bf16_tn(const void* A, int lda, const void* B, int ldb, int M, int 
     return herr ? SBR_ERR_TIMEOUT : SBR_OK;
 }
 
+int sbr_gemm_bf16_tn_async(const void* A, int lda, const void* B, int ldb, int M, int N, int K, float* C, int ldc,
+                           int* err_dev, void* cuda_stream)
+{
+    if (!A || !B || !C || !err_dev) return SBR_ERR_ARG;
+    if (!gemm_shape_ok(M, N, K) || lda < K || ldb < K || ldc < N || lda % 8 || ldb % 8 || ldc % 4)
+        return SBR_ERR_ARG;
+    GemmEpi ep;
+    memset(&ep, 0, sizeof(ep));
+    ep.mode = kEpiF32;
+    ep.M = M;
+    ep.c_f32 = C;
+    ep.ldc = ldc;
+    return gemm_bf16_tn(A, lda, B, ldb, M, N, K, ep, err_dev, (cudaStream_t)cuda_stream) == cudaSuccess ? SBR_OK
+                                                                                                      : SBR_ERR_CUDA;
+}
+
 const char* sbr_surrogate_last_error(const sbr_surrogate* s) { return s ? s->err.c_str() : ""; }
 
 int sbr_surrogate_create(sbr_surrogate** out, int device, void* cuda_stream, const sbr_surrogate_opts* opt)

@@ -33,7 +33,7 @@ EXPORTS = ("sbr_version", "sbr_create", "sbr_destroy", "sbr_last_error", "sbr_lo
            "sbr_sync", "sbr_get_tuning", "sbr_set_tuning", "sbr_autotune", "sbr_trace_bistatic",
            "sbr_surrogate_create", "sbr_surrogate_destroy", "sbr_surrogate_last_error", "sbr_surrogate_num_params",
            "sbr_surrogate_params", "sbr_surrogate_fourier", "sbr_surrogate_train", "sbr_surrogate_grads",
-           "sbr_surrogate_predict", "sbr_gemm_bf16_tn")
+           "sbr_surrogate_predict", "sbr_gemm_bf16_tn", "sbr_gemm_bf16_tn_async")
 
 
 class SbrError(RuntimeError):
@@ -464,6 +464,8 @@ def _surrogate_sigs(L):
         "sbr_surrogate_grads": ([vp, C.c_int, vp, vp, i64, P(d), vp], C.c_int),
         "sbr_surrogate_predict": ([vp, vp, i64, vp, vp], C.c_int),
         "sbr_gemm_bf16_tn": ([vp, C.c_int, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_int, vp], C.c_int),
+        "sbr_gemm_bf16_tn_async": ([vp, C.c_int, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_int, vp, vp],
+                                   C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -480,6 +482,17 @@ def gemm_bf16_tn(A_ptr: int, lda: int, B_ptr: int, ldb: int, M: int, N: int, K: 
     rc = L.sbr_gemm_bf16_tn(A_ptr, lda, B_ptr, ldb, M, N, K, C_ptr, ldc, C.c_void_p(s) if s else None)
     if rc != SBR_OK:
         raise SbrError(rc, "sbr_gemm_bf16_tn failed")
+
+
+def gemm_bf16_tn_async(A_ptr: int, lda: int, B_ptr: int, ldb: int, M: int, N: int, K: int, C_ptr: int, ldc: int,
+                       err_ptr: int, stream=None) -> None:
+    """As gemm_bf16_tn, only enqueued (sbr_gemm_bf16_tn_async); err_ptr: a zeroed device int32 set to 1 if a
+    bounded wait in the kernel gave up."""
+    L = _surrogate_sigs(lib())
+    s = int(getattr(stream, "cuda_stream", stream)) if stream is not None else None
+    rc = L.sbr_gemm_bf16_tn_async(A_ptr, lda, B_ptr, ldb, M, N, K, C_ptr, ldc, err_ptr, C.c_void_p(s) if s else None)
+    if rc != SBR_OK:
+        raise SbrError(rc, "sbr_gemm_bf16_tn_async failed")
 
 
 class Surrogate:

@@ -31,6 +31,15 @@ def test_tensor_core_gemm(G, M, N, K, pad):
     assert not np.isnan(got).any()
     # exact BF16 products, FP32 accumulation
     assert np.max(np.abs(got - ref)) <= 2e-6 * np.sqrt(K) * np.abs(ref).max()
+    # the enqueue-only entry point: the same result bit for bit, no bounded wait gave up
+    C2 = torch.full((M, N), float("nan"), device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    G.gemm_bf16_tn_async(A.data_ptr(), K + pad, B.data_ptr(), K + pad, M, N, K, C2.data_ptr(), N, err.data_ptr(),
+                         torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    assert np.array_equal(C2.cpu().numpy(), got)
 
 
 def _samples(n, seed):
