@@ -340,6 +340,11 @@ SURROGATE_DOMAINS = {
     # held-out points traced on the training data's ray grid (10 rays per wavelength of 1.2 GHz)
     "patch": dict(az=(178.0, 182.0), el=(-1.0, 1.0), f=(1e9, 1.2e9), n_aspects=2000, f_per=100, n_heldout=10000,
                   lattice=(100, 20, 500), sigmas=(16.0, 32.0, 64.0, 128.0, 256.0), heldout_grid="domain"),
+    # the same patch with SBR (training data and judge) at 50 rays per wavelength, where SBR's own
+    # dependence on the ray grid (0.28 dB median) is below the 0.5 dB target
+    "patch_dense": dict(az=(178.0, 182.0), el=(-1.0, 1.0), f=(1e9, 1.2e9), n_aspects=2000, f_per=100,
+                        n_heldout=10000, lattice=(100, 20, 500), sigmas=(16.0, 32.0, 64.0, 128.0, 256.0),
+                        heldout_grid="domain", rpl=50.0),
 }
 
 
@@ -370,6 +375,7 @@ def surrogate_eval(G, torch, ctx, dom, epochs=60, batch=2048, spread_db=1.0, sca
     import time as _t
 
     off = S.grid_offset(6)
+    rpl = dom.get("rpl", 10.0)  # rays per wavelength of the SBR runs
     n_aspects = max(8, int(dom["n_aspects"] * scale))
     n_heldout = max(64, int(dom["n_heldout"] * scale))
     f_per = dom["f_per"]
@@ -379,7 +385,7 @@ def surrogate_eval(G, torch, ctx, dom, epochs=60, batch=2048, spread_db=1.0, sca
     for _ in range(n_aspects):
         f = np.sort(np.exp(rng.uniform(np.log(f0), np.log(f1), f_per)))
         reqs.append(dict(az=float(rng.uniform(a0, a1)), el=float(rng.uniform(e0, e1)), freqs=f,
-                         spacing=S.spacing_for(float(f[-1]), 10.0)))
+                         spacing=S.spacing_for(float(f[-1]), rpl)))
     torch.cuda.synchronize()
     t0 = _t.perf_counter()
     E, _, st = ctx.run_batch(reqs, eta=0.05, max_bounces=10, offset=off)
@@ -413,7 +419,7 @@ def surrogate_eval(G, torch, ctx, dom, epochs=60, batch=2048, spread_db=1.0, sca
     # plain SBR of each held-out point: 10 rays per wavelength of its own frequency, or of the domain's
     # highest frequency (the training data's grid) when the domain says so
     domain_grid = dom.get("heldout_grid") == "domain"
-    hreq = [dict(az=a, el=e, freqs=np.array([f]), spacing=S.spacing_for(f1 if domain_grid else f, 10.0))
+    hreq = [dict(az=a, el=e, freqs=np.array([f]), spacing=S.spacing_for(f1 if domain_grid else f, rpl))
             for a, e, f in hx]
     torch.cuda.synchronize()
     t0 = _t.perf_counter()
@@ -423,7 +429,7 @@ def surrogate_eval(G, torch, ctx, dom, epochs=60, batch=2048, spread_db=1.0, sca
     grid_sens = None
     if domain_grid:
         # how much plain SBR itself moves between the two ray grids (its own discretisation)
-        _, Rg, _ = ctx.run_batch([dict(r, spacing=S.spacing_for(float(r["freqs"][0]), 10.0)) for r in hreq],
+        _, Rg, _ = ctx.run_batch([dict(r, spacing=S.spacing_for(float(r["freqs"][0]), rpl)) for r in hreq],
                                  eta=0.05, max_bounces=10, offset=off)
         dg = np.max(np.abs(np.concatenate(Rg) - Rh), axis=1)
         grid_sens = {"median_db": float(np.median(dg)), "within_0.5dB": float(np.mean(dg <= 0.5))}
@@ -455,7 +461,7 @@ def surrogate_eval(G, torch, ctx, dom, epochs=60, batch=2048, spread_db=1.0, sca
     lat_aspects = naz * nel
     n_lat_sbr = min(lat_aspects, 256)
     pick = np.linspace(0, lat_aspects - 1, n_lat_sbr).round().astype(int)
-    lreq = [dict(az=float(la[k // nel]), el=float(le[k % nel]), freqs=lf, spacing=S.spacing_for(f1, 10.0))
+    lreq = [dict(az=float(la[k // nel]), el=float(le[k % nel]), freqs=lf, spacing=S.spacing_for(f1, rpl))
             for k in pick]
     torch.cuda.synchronize()
     t0 = _t.perf_counter()
@@ -474,8 +480,9 @@ def surrogate_eval(G, torch, ctx, dom, epochs=60, batch=2048, spread_db=1.0, sca
             "all_median_db_error": float(np.median(err[m])) if m.any() else None}
     sur.close()
     return {"domain": {k: dom[k] for k in ("az", "el", "f")}, "training_samples": int(len(x)),
-            "heldout_grid": "10 rays per wavelength of " + ("the domain's highest frequency" if domain_grid
-                                                             else "each point's frequency"),
+            "heldout_grid": f"{rpl:g} rays per wavelength of " + ("the domain's highest frequency" if domain_grid
+                                                                   else "each point's frequency"),
+            "rays_per_wavelength": rpl,
             "sbr_grid_sensitivity": grid_sens,
             "training_aspects": n_aspects, "data_gen_s": t_data, "data_ray_bounces": st["ray_bounces"],
             "sigma_validation_rel_rms": {str(k): v for k, v in tune.items()}, "fourier_sigma": sigma,
@@ -513,8 +520,10 @@ def run_surrogate(args, ws, rank, local, pg):
     ctx.load_mesh(xyz, tri)
     res = {}
     for name in args.sur_domains.split(","):
-        res[name] = surrogate_eval(G, torch, ctx, SURROGATE_DOMAINS[name], epochs=args.sur_epochs,
-                                   scale=args.sur_scale)
+        dom = dict(SURROGATE_DOMAINS[name])
+        if args.sur_rpl > 0:
+            dom["rpl"] = args.sur_rpl
+        res[name] = surrogate_eval(G, torch, ctx, dom, epochs=args.sur_epochs, scale=args.sur_scale)
     ctx.close()
     head = res[args.sur_domains.split(",")[0]]
     if rank == 0:
@@ -785,9 +794,11 @@ def main():
     ap.add_argument("--builder", default="ploc", choices=["ploc", "lbvh"], help="BVH builder of the timed workload")
     ap.add_argument("--tune-aspects", type=int, default=24, help="aspects in the autotuner's sample")
     ap.add_argument("--tune", default="", help="fixed tuning instead of the autotuner, e.g. tile_w=4,stack_depth=32")
-    ap.add_argument("--sur-domains", default="full,patch", help="surrogate: domains to evaluate")
+    ap.add_argument("--sur-domains", default="full,patch,patch_dense", help="surrogate: domains to evaluate")
     ap.add_argument("--sur-scale", type=float, default=1.0, help="surrogate: fraction of the sample counts")
     ap.add_argument("--sur-epochs", type=int, default=60)
+    ap.add_argument("--sur-rpl", type=float, default=0.0,
+                    help="surrogate: rays per wavelength of its SBR runs (0: the domain's own, 10 unless set)")
     args = ap.parse_args()
     ws, rank, local, pg = dist_setup()
     if args.workload == "gemm":
