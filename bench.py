@@ -52,16 +52,27 @@ OPS_NODE = 41
 OPS_NODE_OCT = 29  # binary node over the octant copies: 2 x (6 FMA + 6 min/max + 1 scale + 1 compare) + ordering
 OPS_NODE4 = 81
 OPS_TRI = 38
+# FP32 operations of the per-hit arithmetic (apply_hit in sbr_trace.cu, each add, multiply, fma, divide,
+# square root and select one): hit point 3, path accumulation 9, unit normal 14, orientation 8, receiver path
+# term 25 + 11, H field 10, tube area 2, the two vector PO terms 3 + 42, four coefficients 12, scalar
+# coefficient 4, PEC field update 7, reflection 4, new origin 3 = 157 per hit of a bounce pass; a primary hit
+# adds the two-float k.o0 of its start (25) and the first-hit cosine (3). A rasterised cell test is the ray's
+# FP32 origin (12) and the triangle test.
+OPS_HIT = 157
+OPS_PRIMARY_HIT = 185
+OPS_RASTER_CELL = 12 + OPS_TRI
 # DRAM bytes per launched ray of the kernel the roofline describes, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the trihedral sweep's
 # 9-aspect sample (2,114,692 rays) on the PLOC tree, for the setting listed:
 # with traversed primary rays, k_primary and both k_bounce passes (188.39 MB);
 # with rasterised primary hits, both k_bounce passes. Stack depth and chunk
 # size leave the bytes per ray unchanged (the queues and records are the
-# traffic); it grows with the rays, so it is scaled by the rays of a step.
+# traffic), and so does the ray tile once the primary hits are rasterised (the
+# bounce passes stream the same queues; the tree stays in L1/L2); it grows with
+# the rays, so it is scaled by the rays of a step.
 TRAFFIC_PER_RAY = {"trihedral": [(188.39e6 / 2114692, dict(tile_w=4, bvh_width=2, packet=0, octant=0, raster=0), "ploc"),
-                                  (176.22e6 / 2114692, dict(tile_w=4, bvh_width=2, packet=0, octant=0, raster=1), "ploc"),
-                                  (175.73e6 / 2114692, dict(tile_w=4, bvh_width=2, packet=0, octant=1, raster=1), "ploc")]}
+                                  (176.22e6 / 2114692, dict(bvh_width=2, packet=0, octant=0, raster=1), "ploc"),
+                                  (175.73e6 / 2114692, dict(bvh_width=2, packet=0, octant=1, raster=1), "ploc")]}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -715,16 +726,16 @@ def run_sbr(args, case, ws, rank, local, pg):
         # the traversal of the bounce passes: node visits and their triangle tests over their time
         dominant = "bounce"
         ops = (OPS_NODE4 if wide else (OPS_NODE_OCT if octant else OPS_NODE)) * cnt["node_visits"] + \
-            OPS_TRI * (cnt["tri_tests"] - cnt["raster_tests"])
+            OPS_TRI * (cnt["tri_tests"] - cnt["raster_tests"]) + OPS_HIT * cnt["bounce_hits"]
         pass_s = bounce_s
     elif raster:
-        # one bounce or short bounce passes: the rasterised primary pass, its triangle tests over its time
+        # one bounce or short bounce passes: the rasterised primary pass, its cell tests and hits over its time
         dominant = "primary"
-        ops = OPS_TRI * cnt["raster_tests"]
+        ops = OPS_RASTER_CELL * cnt["raster_tests"] + OPS_PRIMARY_HIT * cnt["valid_rays"]
         pass_s = primary_s
     else:
         ops = (OPS_NODE4 if wide else (OPS_NODE_OCT if octant else OPS_NODE)) * cnt["node_visits"] + \
-            OPS_TRI * cnt["tri_tests"]
+            OPS_TRI * cnt["tri_tests"] + OPS_HIT * cnt["bounce_hits"] + OPS_PRIMARY_HIT * cnt["valid_rays"]
         pass_s = pass_all_s
     pk, src = peaks()
     peak_ops = SM_COUNT * FP32_LANES_PER_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
@@ -749,6 +760,11 @@ def run_sbr(args, case, ws, rank, local, pg):
                          "ops_per_step": ops, "node_visits": 0 if dominant == "primary" else cnt["node_visits"],
                          "tri_tests": (cnt["raster_tests"] if dominant == "primary" else
                                        cnt["tri_tests"] - (cnt["raster_tests"] if raster else 0)),
+                         "hits": (cnt["valid_rays"] if dominant == "primary" else
+                                  cnt["bounce_hits"] + (0 if raster else cnt["valid_rays"])),
+                         "ops_per_unit": {"node_visit": OPS_NODE4 if wide else (OPS_NODE_OCT if octant else OPS_NODE),
+                                          "tri_test": OPS_TRI, "bounce_hit": OPS_HIT,
+                                          "primary_hit": OPS_PRIMARY_HIT, "raster_cell": OPS_RASTER_CELL},
                          "pass_ms_per_step": pass_s * 1e3},
             "primary": {"kernel": "k_raster+k_vis_mask+k_primary_vis (rasterised primary hits)" if raster else
                         "k_primary (traversed)", "ms_per_step": primary_s * 1e3,

@@ -108,6 +108,8 @@ typedef struct {
                                 (included in tri_tests) */
     double primary_ms;       /* with SBR_TRACE_TIME_PASSES: the part of pass_ms spent in primary passes
                                 (rasterisation included) */
+    int64_t bounce_hits;     /* only with SBR_TRACE_COUNT_VISITS: hits processed by the bounce passes (reflection,
+                                field update and candidate coefficients each) */
 } sbr_trace_stats;
 
 /* Per-aspect ray grid (Eq. L1-L3) exactly as sbr_trace generates it. */

@@ -71,7 +71,7 @@ struct __align__(16) Record {
 static_assert(sizeof(Record) == 32, "Record layout");
 
 // stats counters on the device (unsigned long long each)
-enum { kStatQueries = 0, kStatNodes = 1, kStatTris = 2, kStatOverflow = 3, kStatRaster = 4, kStatCount = 5 };
+enum { kStatQueries = 0, kStatNodes = 1, kStatTris = 2, kStatOverflow = 3, kStatRaster = 4, kStatHits = 5, kStatCount = 6 };
 
 // ---------------------------------------------------------------- launchers
 // All launchers enqueue on `st` and return the launch error (cudaSuccess if none).

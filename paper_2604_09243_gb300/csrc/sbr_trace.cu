@@ -701,7 +701,8 @@ __device__ __forceinline__ void push(const TraceArgs& a, bool want, const Ray& r
 }
 
 template <bool kCount>
-__device__ __forceinline__ void flush_stats(const TraceArgs& a, unsigned q, unsigned nvis, unsigned ntri, bool ovf)
+__device__ __forceinline__ void flush_stats(const TraceArgs& a, unsigned q, unsigned nvis, unsigned ntri, bool ovf,
+                                            unsigned nhit = 0)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -709,6 +710,7 @@ __device__ __forceinline__ void flush_stats(const TraceArgs& a, unsigned q, unsi
         if (kCount) {
             nvis += __shfl_xor_sync(kFull, nvis, o);
             ntri += __shfl_xor_sync(kFull, ntri, o);
+            nhit += __shfl_xor_sync(kFull, nhit, o);
         }
     }
     const unsigned ov = __ballot_sync(kFull, ovf);
@@ -717,6 +719,7 @@ __device__ __forceinline__ void flush_stats(const TraceArgs& a, unsigned q, unsi
         if (kCount) {
             atomicAdd(a.stats + kStatNodes, (unsigned long long)nvis);
             atomicAdd(a.stats + kStatTris, (unsigned long long)ntri);
+            if (nhit) atomicAdd(a.stats + kStatHits, (unsigned long long)nhit);
         }
         if (ov) atomicAdd(a.stats + kStatOverflow, (unsigned long long)__popc(ov));
     }
@@ -1097,7 +1100,7 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_bounce(const TraceArgs a)
     const int lane = threadIdx.x & 31;
     const unsigned n_in = *a.q_in_count;
     const bool escape_pass = a.bounce >= a.max_bounces;
-    unsigned nq = 0, nvis = 0, ntri = 0;
+    unsigned nq = 0, nvis = 0, ntri = 0, nhit = 0;  // nhit: hits processed (counting runs only)
     bool ovf = false;
     while (true) {
         unsigned long long base = 0;
@@ -1124,6 +1127,7 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_bounce(const TraceArgs a)
             } else if (escape_pass) {
                 emit(a, r, true);                      // still trapped after B_max: invalid
             } else {
+                if (kCount) ++nhit;
                 apply_hit(A, a.tris, h, a.flags, r);
                 record_hit(a, r, h);
                 if (r.nb < a.max_bounces || (a.flags & kFlagEscape)) again = true;
@@ -1132,7 +1136,7 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_bounce(const TraceArgs a)
         }
         push(a, again, r);
     }
-    flush_stats<kCount>(a, nq, nvis, ntri, ovf);
+    flush_stats<kCount>(a, nq, nvis, ntri, ovf, nhit);
 }
 
 // every ray of the queue writes its record (B_max = 1 without the escape check)

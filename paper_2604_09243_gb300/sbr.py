@@ -69,7 +69,8 @@ class TraceStats(C.Structure):
     _fields_ = [("n_angles", C.c_int64), ("rays_launched", C.c_int64), ("ray_bounces", C.c_int64),
                 ("valid_rays", C.c_int64), ("node_visits", C.c_int64), ("tri_tests", C.c_int64),
                 ("stack_overflows", C.c_int64), ("kernel_launches", C.c_int64), ("pass_launches", C.c_int64),
-                ("pass_ms", C.c_double), ("raster_tests", C.c_int64), ("primary_ms", C.c_double)]
+                ("pass_ms", C.c_double), ("raster_tests", C.c_int64), ("primary_ms", C.c_double),
+                ("bounce_hits", C.c_int64)]
 
     def as_dict(self):
         return {k: (float if k.endswith("_ms") else int)(getattr(self, k)) for k, _ in self._fields_}

@@ -256,6 +256,25 @@ def test_tree_build_size_limits(G, ctx, orc, n_tri):
         assert_hit_parity(compare_hits(*g, o))
 
 
+def test_bounce_hit_count(G, ctx, orc):
+    """The counting run's bounce_hits is the number of hits the bounce passes processed: every hit after a
+    ray's first, i.e. the sum of (bounces - 1) over the rays, on the GPU's own records and on the oracle's."""
+    case = S.trihedral_case()
+    ctx.load_mesh(case["xyz"], case["tri"])
+    om = orc.Mesh(case["xyz"], case["tri"])
+    ang = case["angles"][[10, 77, 150]]
+    for raster in (1, 0):
+        ctx.set_tuning(raster=raster)
+        st, res = _trace_both(G, ctx, orc, om, ang, case["spacing"], 3, eta=case["eta"], offset=case["offset"],
+                              flags=G.TRACE_COUNT_VISITS)
+        own = sum(int(np.maximum(g[2] - 1, 0).sum()) for g, o, fr in res)
+        ref = sum(int(np.maximum(o["nb"].astype(np.int64) - 1, 0).sum()) for g, o, fr in res)
+        assert st["bounce_hits"] == own
+        assert abs(own - ref) <= 1e-5 * max(ref, 1) + 2  # hit decisions equal outside the edge band
+        assert st["bounce_hits"] > 0
+    ctx.set_tuning(raster=1)
+
+
 def test_all_rays_miss_gives_empty_sum(G, ctx):
     xyz, tri = S.square_plate(1.0, 2)
     ctx.load_mesh(xyz, tri)
