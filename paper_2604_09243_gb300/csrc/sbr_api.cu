@@ -96,6 +96,7 @@ struct sbr_ctx {
     DevBuf angles, rayoff, mask, tilebase, scan_scr, recoff, q0, q1, ctr64, ctr32, stats, rec, cover;
     DevBuf hit_tri, hit_t, hit_nb;
     DevBuf tripos, vis, visfull;  // position of each original triangle; raster keys and per-aspect flags
+    DevBuf hitlist;               // (ray, aspect) of the rasterised primary hits, read by bounce pass 1
     long long rec_total = 0;
     int max_bounces = 0, trace_flags = 0;
     bool has_trace = false;
@@ -566,6 +567,7 @@ int plan_chunks(sbr_ctx* c, TraceRun& R, std::vector<int64_t>& cut, long long* t
     if (c->tune.raster) {
         CK(c->vis.ensure(sizeof(unsigned long long) * (size_t)max_chunk), "alloc raster keys");
         CK(c->visfull.ensure(sizeof(unsigned) * (size_t)(max_angles + 1)), "alloc raster flags");
+        CK(c->hitlist.ensure(sizeof(uint2) * (size_t)max_chunk), "alloc raster hit list");
     }
     CK(c->tilebase.ensure(sizeof(unsigned) * (size_t)max_tiles), "alloc tile base");
     CK(c->scan_scr.ensure(scan_scratch_bytes(max_tiles)), "alloc scan scratch");
@@ -633,7 +635,7 @@ int trace_chunk(sbr_ctx* c, TraceRun& R, int64_t a0, int64_t a1, long long rec_b
             cudaEventRecord(e0, c->stream);
         }
         cudaError_t e = cudaSuccess;
-        if (t.vis) {
+        if (t.vis && t.bounce == 0) {
             e = launch_raster(t, (int)c->n_tri, c->vis.as<unsigned long long>(), c->visfull.as<unsigned>(), R.count,
                               c->n_sms * 16, c->scan_scr.p, c->stream);
             R.n_launch += 6;  // rasterisation, masks, 3-kernel scan, primary pass of the rasterised rays
@@ -691,6 +693,12 @@ int trace_chunk(sbr_ctx* c, TraceRun& R, int64_t a0, int64_t a1, long long rec_b
         ta.vis = c->vis.as<unsigned long long>();
         ta.vis_full = c->visfull.as<unsigned>();
         ta.tri_pos = c->tripos.as<int>();
+        ta.list_count = total_dev + 4;
+        // a bounce pass follows: list the hits and let it rebuild their states (not for B = 1, whose
+        // records are written from the stored states, nor for bistatic chunks; binary traversals only,
+        // where the rebuilding fits the bounce kernel's registers)
+        if (!ta.bistatic && !ta.wide && !ta.packet && (R.max_bounces >= 2 || R.escape))
+            ta.hit_list = c->hitlist.as<uint2>();
     } else if (c->tune.silhouette) {
         CK(cudaMemsetAsync(c->cover.p, 0, sizeof(unsigned) * (size_t)(chunk_rays / 32 + na), c->stream), "memset cover");
         CK(launch_silhouette(ta, (int)c->n_tri, c->cover.as<unsigned>(), c->stream), "silhouette");
@@ -702,7 +710,6 @@ int trace_chunk(sbr_ctx* c, TraceRun& R, int64_t a0, int64_t a1, long long rec_b
     ta.q_out = qs[0];
     ta.q_out_count = q_count + 1;
     CK(pass(ta), "trace primary");
-    ta.vis = nullptr;
     CK(scan_popc(ta.mask, c->tilebase.as<unsigned>(), chunk_rays / 32, total_dev, c->scan_scr.p, c->stream), "scan");
     R.n_launch += 3;
     CK(launch_angle_offsets(ta.ray_off, c->tilebase.as<unsigned>(), total_dev, na, c->recoff.as<unsigned>(), c->stream),
@@ -746,6 +753,7 @@ int trace_chunk(sbr_ctx* c, TraceRun& R, int64_t a0, int64_t a1, long long rec_b
             ta.q_out = qs[b & 1];
             ta.q_out_count = q_count + b + 1;
             CK(pass(ta), "trace bounce");
+            ta.hit_list = nullptr;  // only bounce pass 1 reads the list
         }
     }
     *n_valid_out = n_valid;
@@ -908,7 +916,7 @@ struct BatchPlan {
     PoArgs pa;
     // device buffers
     DevBuf angles, rayoff, pang, recoff, mask, tilebase, scan_scr, q0, q1, ctr64, ctr32, stats, rec, items, nitems,
-        valid, freq_t, kfreq, partial, cover, vis, visfull;
+        valid, freq_t, kfreq, partial, cover, vis, visfull, hitlist;
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -923,7 +931,7 @@ void free_plan(BatchPlan* p)
     DevBuf* all[] = {&p->angles, &p->rayoff, &p->pang,   &p->recoff, &p->mask,   &p->tilebase, &p->scan_scr,
                      &p->q0,     &p->q1,     &p->ctr64,  &p->ctr32,  &p->stats,  &p->rec,      &p->items,
                      &p->nitems, &p->valid,  &p->freq_t, &p->kfreq,  &p->partial, &p->cover,
-                     &p->vis,    &p->visfull};
+                     &p->vis,    &p->visfull, &p->hitlist};
     for (DevBuf* b : all) b->release();
     delete p;
 }
@@ -983,6 +991,9 @@ cudaError_t enqueue_plan(const sbr_ctx* c, BatchPlan& P, cudaStream_t st)
             ta.vis = P.vis.as<unsigned long long>();
             ta.vis_full = P.visfull.as<unsigned>();
             ta.tri_pos = c->tripos.as<int>();
+            ta.list_count = total_dev + 4;
+            if (!ta.bistatic && !ta.wide && !ta.packet && (P.max_bounces >= 2 || escape))
+                ta.hit_list = P.hitlist.as<uint2>();
             e = launch_raster(ta, (int)c->n_tri, P.vis.as<unsigned long long>(), P.visfull.as<unsigned>(), P.count,
                               c->n_sms * 16, P.scan_scr.p, st);
             if (e != cudaSuccess) break;
@@ -993,7 +1004,6 @@ cudaError_t enqueue_plan(const sbr_ctx* c, BatchPlan& P, cudaStream_t st)
             ta.cover = P.cover.as<unsigned>();
         }
         e = launch_trace(ta, n_blocks, P.count, P.tune.stack_depth, st);
-        ta.vis = nullptr;
         if (e == cudaSuccess) e = scan_popc(ta.mask, P.tilebase.as<unsigned>(), rays / 32, total_dev, P.scan_scr.p, st);
         if (e == cudaSuccess)
             e = launch_angle_offsets(ta.ray_off, ta.tile_base, total_dev, na, P.recoff.as<unsigned>(), st);
@@ -1013,6 +1023,7 @@ cudaError_t enqueue_plan(const sbr_ctx* c, BatchPlan& P, cudaStream_t st)
                 ta.q_out = qs[b & 1];
                 ta.q_out_count = q_count + b + 1;
                 e = launch_trace(ta, n_blocks, P.count, P.tune.stack_depth, st);
+                ta.hit_list = nullptr;  // only bounce pass 1 reads the list
             }
         }
         PoAngle* pang = P.pang.as<PoAngle>() + a0;
@@ -1103,6 +1114,7 @@ int build_plan(sbr_ctx* c, BatchPlan& P)
     if (P.tune.raster) {
         CK(P.vis.ensure(sizeof(unsigned long long) * (size_t)max_rays), "alloc raster keys");
         CK(P.visfull.ensure(sizeof(unsigned) * (size_t)(max_angles + 1)), "alloc raster flags");
+        CK(P.hitlist.ensure(sizeof(uint2) * (size_t)max_rays), "alloc raster hit list");
     }
     CK(P.tilebase.ensure(sizeof(unsigned) * (size_t)max_tiles), "alloc tile base");
     CK(P.scan_scr.ensure(scan_scratch_bytes(max_tiles)), "alloc scan scratch");

@@ -159,6 +159,10 @@ struct TraceArgs {
     const unsigned* vis_full;     // with vis: [n_angles + 1] 1 = the aspect's primary rays traverse the tree;
                                   // [n_angles]: 1 if any aspect does
     const int* tri_pos;           // with vis: [n_tri] position in tris of each original triangle index
+    unsigned* list_count;         // with vis: device count of the rasterised primary hits
+    uint2* hit_list;              // optional (rasterised hits, a bounce pass follows): the primary pass
+                                  // lists (ray, aspect) of each rasterised hit here instead of storing
+                                  // its state, and bounce pass 1 rebuilds the state from the list
 };
 int trace_blocks_per_sm();
 // stack_depth: 32, 64 or 128 entries of the traversal stack (other values: 64;

@@ -1072,7 +1072,10 @@ __global__ void __launch_bounds__(kTraceThreads) k_primary_vis(const TraceArgs a
             tile_ij(A, local, i, j);
             if (i < A.nu && j < A.nv) ++nq;
             const unsigned vmask = a.mask[tile];  // k_vis_mask
-            if ((vmask >> lane) & 1u) {
+            if (((vmask >> lane) & 1u) && a.hit_list) {
+                a.hit_list[a.tile_base[tile] + __popc(vmask & ((1u << lane) - 1u))] =
+                    make_uint2((unsigned)(base + lane), (unsigned)ang);
+            } else if ((vmask >> lane) & 1u) {
                 const unsigned long long key = __ldcs(a.vis + base + lane);
                 Hit h;
                 h.t = __uint_as_float((unsigned)(key >> 32));
@@ -1094,11 +1097,34 @@ __global__ void __launch_bounds__(kTraceThreads) k_primary_vis(const TraceArgs a
 }
 
 // ---------------------------------------------------------------- pass b >= 1: live rays
-template <bool kCount, int kStack, int kMode, bool kBi = false>
+// State of rasterised primary hit (ray g of the chunk, aspect ang) after its
+// first hit: the same steps as k_primary_vis.
+__device__ __forceinline__ void primary_state(const TraceArgs& a, unsigned g, int ang, Ray& r)
+{
+    const AngleDev& A = a.angles[ang];
+    const int local = (int)((long long)g - a.ray_off[ang]);
+    int i, j;
+    tile_ij(A, local, i, j);
+    const unsigned long long key = __ldcs(a.vis + g);
+    Hit h;
+    h.t = __uint_as_float((unsigned)(key >> 32));
+    h.orig = (int)(unsigned)key;
+    h.k = __ldg(a.tri_pos + h.orig);
+    r.angle = ang;
+    r.local = local;
+    r.o = primary_origin(A, i, j);
+    r.d = make_float3(A.dir[0], A.dir[1], A.dir[2]);
+    start_ray(A, r);
+    apply_hit(A, a.tris, h, a.flags, r);
+    record_hit(a, r, h);
+}
+
+template <bool kCount, int kStack, int kMode, bool kBi = false, bool kList = false>
 __global__ void __launch_bounds__(kTraceThreads, 4) k_bounce(const TraceArgs a)
 {
     const int lane = threadIdx.x & 31;
     const unsigned n_in = *a.q_in_count;
+    const unsigned n_list = kList ? *a.list_count : 0u;  // entries below n_list come from the hit list
     const bool escape_pass = a.bounce >= a.max_bounces;
     unsigned nq = 0, nvis = 0, ntri = 0, nhit = 0;  // nhit: hits processed (counting runs only)
     bool ovf = false;
@@ -1114,11 +1140,16 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_bounce(const TraceArgs a)
         r.o = make_float3(0.f, 0.f, 0.f);
         r.d = make_float3(0.f, 0.f, 1.f);
         r.last = -1;
-        if (active) load_geom(a.q_in, idx, r);
+        const bool listed = kList && idx < n_list;
+        if (listed) {
+            const uint2 e = a.hit_list[idx];
+            primary_state(a, e.x, (int)e.y, r);
+        }
+        else if (active) load_geom(a.q_in, idx, r);
         Hit h;
         query<kCount, kStack, kMode>(a, active, r.o, r.d, r.last, h, nvis, ntri, ovf);
         if (active) {
-            load_payload(a.q_in, idx, r);
+            if (!listed) load_payload(a.q_in, idx, r);
             const AngleDev& A = a.angles[r.angle];
             ++nq;
             if (h.k < 0) {
@@ -1183,6 +1214,9 @@ void launch_trace_s(const TraceArgs& a, int n_blocks, bool count_visits, cudaStr
         }
         if (count_visits) k_primary<true, kStack, kMode><<<n_blocks, kTraceThreads, 0, st>>>(a);
         else k_primary<false, kStack, kMode><<<n_blocks, kTraceThreads, 0, st>>>(a);
+    } else if (a.bounce == 1 && a.hit_list) {
+        if (count_visits) k_bounce<true, kStack, kMode, false, true><<<n_blocks, kTraceThreads, 0, st>>>(a);
+        else k_bounce<false, kStack, kMode, false, true><<<n_blocks, kTraceThreads, 0, st>>>(a);
     } else {
         if (count_visits) k_bounce<true, kStack, kMode><<<n_blocks, kTraceThreads, 0, st>>>(a);
         else k_bounce<false, kStack, kMode><<<n_blocks, kTraceThreads, 0, st>>>(a);
@@ -1261,7 +1295,9 @@ cudaError_t launch_raster(const TraceArgs& a, int n_tri, unsigned long long* vis
     e = cudaGetLastError();
     // queue slots of the rasterised hits; the traversing rays append after them
     if (e == cudaSuccess)
-        e = scan_popc(a.mask, const_cast<unsigned*>(a.tile_base), n_tiles, a.q_out_count, scan_scratch, st);
+        e = scan_popc(a.mask, const_cast<unsigned*>(a.tile_base), n_tiles, a.list_count, scan_scratch, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(a.q_out_count, a.list_count, sizeof(unsigned), cudaMemcpyDeviceToDevice, st);
     return e;
 }
 
