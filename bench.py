@@ -65,14 +65,15 @@ OPS_RASTER_CELL = 12 + OPS_TRI
 # capture (dram__bytes_read.sum + dram__bytes_write.sum) of the trihedral sweep's
 # 9-aspect sample (2,114,692 rays) on the PLOC tree, for the setting listed:
 # with traversed primary rays, k_primary and both k_bounce passes (188.39 MB);
-# with rasterised primary hits, both k_bounce passes. Stack depth and chunk
+# with rasterised primary hits (bounce pass 1 rebuilding them from the hit
+# list), both k_bounce passes. Stack depth and chunk
 # size leave the bytes per ray unchanged (the queues and records are the
 # traffic), and so does the ray tile once the primary hits are rasterised (the
 # bounce passes stream the same queues; the tree stays in L1/L2); it grows with
 # the rays, so it is scaled by the rays of a step.
 TRAFFIC_PER_RAY = {"trihedral": [(188.39e6 / 2114692, dict(tile_w=4, bvh_width=2, packet=0, octant=0, raster=0), "ploc"),
-                                  (176.22e6 / 2114692, dict(bvh_width=2, packet=0, octant=0, raster=1), "ploc"),
-                                  (175.73e6 / 2114692, dict(bvh_width=2, packet=0, octant=1, raster=1), "ploc")]}
+                                  (103.70e6 / 2114692, dict(bvh_width=2, packet=0, octant=0, raster=1), "ploc"),
+                                  (104.17e6 / 2114692, dict(bvh_width=2, packet=0, octant=1, raster=1), "ploc")]}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -725,13 +726,15 @@ def run_sbr(args, case, ws, rank, local, pg):
     if raster and bounce_s >= primary_s:
         # the traversal of the bounce passes: node visits and their triangle tests over their time
         dominant = "bounce"
+        # (with the hit list, bounce pass 1 also rebuilds the rasterised primary hits: listed_hits)
         ops = (OPS_NODE4 if wide else (OPS_NODE_OCT if octant else OPS_NODE)) * cnt["node_visits"] + \
-            OPS_TRI * (cnt["tri_tests"] - cnt["raster_tests"]) + OPS_HIT * cnt["bounce_hits"]
+            OPS_TRI * (cnt["tri_tests"] - cnt["raster_tests"]) + OPS_HIT * cnt["bounce_hits"] + \
+            OPS_PRIMARY_HIT * cnt["listed_hits"]
         pass_s = bounce_s
     elif raster:
         # one bounce or short bounce passes: the rasterised primary pass, its cell tests and hits over its time
         dominant = "primary"
-        ops = OPS_RASTER_CELL * cnt["raster_tests"] + OPS_PRIMARY_HIT * cnt["valid_rays"]
+        ops = OPS_RASTER_CELL * cnt["raster_tests"] + OPS_PRIMARY_HIT * (cnt["valid_rays"] - cnt["listed_hits"])
         pass_s = primary_s
     else:
         ops = (OPS_NODE4 if wide else (OPS_NODE_OCT if octant else OPS_NODE)) * cnt["node_visits"] + \
@@ -760,8 +763,8 @@ def run_sbr(args, case, ws, rank, local, pg):
                          "ops_per_step": ops, "node_visits": 0 if dominant == "primary" else cnt["node_visits"],
                          "tri_tests": (cnt["raster_tests"] if dominant == "primary" else
                                        cnt["tri_tests"] - (cnt["raster_tests"] if raster else 0)),
-                         "hits": (cnt["valid_rays"] if dominant == "primary" else
-                                  cnt["bounce_hits"] + (0 if raster else cnt["valid_rays"])),
+                         "hits": (cnt["valid_rays"] - cnt["listed_hits"] if dominant == "primary" else
+                                  cnt["bounce_hits"] + (cnt["listed_hits"] if raster else cnt["valid_rays"])),
                          "ops_per_unit": {"node_visit": OPS_NODE4 if wide else (OPS_NODE_OCT if octant else OPS_NODE),
                                           "tri_test": OPS_TRI, "bounce_hit": OPS_HIT,
                                           "primary_hit": OPS_PRIMARY_HIT, "raster_cell": OPS_RASTER_CELL},

@@ -110,6 +110,8 @@ typedef struct {
                                 (rasterisation included) */
     int64_t bounce_hits;     /* only with SBR_TRACE_COUNT_VISITS: hits processed by the bounce passes (reflection,
                                 field update and candidate coefficients each) */
+    int64_t listed_hits;     /* only with SBR_TRACE_COUNT_VISITS: rasterised primary hits whose state bounce pass 1
+                                rebuilt from the hit list (their per-hit arithmetic runs there) */
 } sbr_trace_stats;
 
 /* Per-aspect ray grid (Eq. L1-L3) exactly as sbr_trace generates it. */

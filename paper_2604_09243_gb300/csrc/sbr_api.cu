@@ -779,6 +779,7 @@ int finish_stats(sbr_ctx* c, const TraceRun& R, int64_t n_angles, long long laun
         stats->pass_launches = R.n_pass;
         stats->raster_tests = (int64_t)hs_stats[kStatRaster];
         stats->bounce_hits = (int64_t)hs_stats[kStatHits];
+        stats->listed_hits = (int64_t)hs_stats[kStatListed];
         stats->pass_ms = 0.0;
         stats->primary_ms = 0.0;
         for (size_t i = 0; R.timed && i + 1 < R.n_ev; i += 2) {
@@ -1478,6 +1479,7 @@ int sbr_sync(sbr_ctx* c, sbr_trace_stats* stats)
         stats->tri_tests = (int64_t)hs[kStatTris];
         stats->raster_tests = (int64_t)hs[kStatRaster];
         stats->bounce_hits = (int64_t)hs[kStatHits];
+        stats->listed_hits = (int64_t)hs[kStatListed];
         stats->stack_overflows = (int64_t)hs[kStatOverflow];
         stats->kernel_launches = P.n_launch;
         stats->pass_launches = P.n_pass;

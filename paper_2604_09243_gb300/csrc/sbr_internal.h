@@ -71,7 +71,8 @@ struct __align__(16) Record {
 static_assert(sizeof(Record) == 32, "Record layout");
 
 // stats counters on the device (unsigned long long each)
-enum { kStatQueries = 0, kStatNodes = 1, kStatTris = 2, kStatOverflow = 3, kStatRaster = 4, kStatHits = 5, kStatCount = 6 };
+enum { kStatQueries = 0, kStatNodes = 1, kStatTris = 2, kStatOverflow = 3, kStatRaster = 4, kStatHits = 5, kStatListed = 6,
+       kStatCount = 7 };
 
 // ---------------------------------------------------------------- launchers
 // All launchers enqueue on `st` and return the launch error (cudaSuccess if none).

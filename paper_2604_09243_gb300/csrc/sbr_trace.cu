@@ -702,7 +702,7 @@ __device__ __forceinline__ void push(const TraceArgs& a, bool want, const Ray& r
 
 template <bool kCount>
 __device__ __forceinline__ void flush_stats(const TraceArgs& a, unsigned q, unsigned nvis, unsigned ntri, bool ovf,
-                                            unsigned nhit = 0)
+                                            unsigned nhit = 0, unsigned nlist = 0)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -711,6 +711,7 @@ __device__ __forceinline__ void flush_stats(const TraceArgs& a, unsigned q, unsi
             nvis += __shfl_xor_sync(kFull, nvis, o);
             ntri += __shfl_xor_sync(kFull, ntri, o);
             nhit += __shfl_xor_sync(kFull, nhit, o);
+            nlist += __shfl_xor_sync(kFull, nlist, o);
         }
     }
     const unsigned ov = __ballot_sync(kFull, ovf);
@@ -720,6 +721,7 @@ __device__ __forceinline__ void flush_stats(const TraceArgs& a, unsigned q, unsi
             atomicAdd(a.stats + kStatNodes, (unsigned long long)nvis);
             atomicAdd(a.stats + kStatTris, (unsigned long long)ntri);
             if (nhit) atomicAdd(a.stats + kStatHits, (unsigned long long)nhit);
+            if (nlist) atomicAdd(a.stats + kStatListed, (unsigned long long)nlist);
         }
         if (ov) atomicAdd(a.stats + kStatOverflow, (unsigned long long)__popc(ov));
     }
@@ -1126,7 +1128,7 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_bounce(const TraceArgs a)
     const unsigned n_in = *a.q_in_count;
     const unsigned n_list = kList ? *a.list_count : 0u;  // entries below n_list come from the hit list
     const bool escape_pass = a.bounce >= a.max_bounces;
-    unsigned nq = 0, nvis = 0, ntri = 0, nhit = 0;  // nhit: hits processed (counting runs only)
+    unsigned nq = 0, nvis = 0, ntri = 0, nhit = 0, nlist = 0;  // hits processed, hits rebuilt (counting runs)
     bool ovf = false;
     while (true) {
         unsigned long long base = 0;
@@ -1144,6 +1146,7 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_bounce(const TraceArgs a)
         if (listed) {
             const uint2 e = a.hit_list[idx];
             primary_state(a, e.x, (int)e.y, r);
+            if (kCount) ++nlist;
         }
         else if (active) load_geom(a.q_in, idx, r);
         Hit h;
@@ -1167,7 +1170,7 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_bounce(const TraceArgs a)
         }
         push(a, again, r);
     }
-    flush_stats<kCount>(a, nq, nvis, ntri, ovf, nhit);
+    flush_stats<kCount>(a, nq, nvis, ntri, ovf, nhit, nlist);
 }
 
 // every ray of the queue writes its record (B_max = 1 without the escape check)

@@ -272,6 +272,8 @@ def test_bounce_hit_count(G, ctx, orc):
         assert st["bounce_hits"] == own
         assert abs(own - ref) <= 1e-5 * max(ref, 1) + 2  # hit decisions equal outside the edge band
         assert st["bounce_hits"] > 0
+        # rasterised primary hits are rebuilt by bounce pass 1 from the hit list (no aspect falls back here)
+        assert st["listed_hits"] == (st["valid_rays"] if raster else 0)
     ctx.set_tuning(raster=1)
 
 
