@@ -75,6 +75,20 @@ def test_no_device_reports_nodev(G):
     assert e.value.code == -7
 
 
+def test_gemm_entry_points_refuse_bad_arguments(G):
+    """Both GEMM entry points check pointers and shapes on the host, before any device work."""
+    for fn in (lambda *a: G.gemm_bf16_tn(*a), lambda *a: G.gemm_bf16_tn_async(*a, 8)):
+        for args in ((0, 512, 8, 512, 128, 128, 512, 8, 128),      # null A
+                     (8, 512, 8, 512, 100, 128, 512, 8, 128),      # M not a multiple of 128
+                     (8, 512, 8, 512, 128, 128, 96, 8, 128),       # K not a multiple of 64
+                     (8, 500, 8, 512, 128, 128, 512, 8, 128)):     # lda not a multiple of 8
+            with pytest.raises(G.SbrError) as e:
+                fn(*args)
+            assert e.value.code == -1
+    with pytest.raises(G.SbrError):  # no error flag for the enqueue-only call
+        G.gemm_bf16_tn_async(8, 512, 8, 512, 128, 128, 512, 8, 128, 0)
+
+
 def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     import paper_2604_09243_gb300.sbr as mod
 
