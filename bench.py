@@ -649,13 +649,13 @@ def run_sbr(args, case, ws, rank, local, pg):
         # evenly spaced sample of the workload's aspects
         pick = np.linspace(0, na - 1, min(na, args.tune_aspects)).round().astype(int)
         sample = [dict(az=float(ang[i, 0]), el=float(ang[i, 1]), freqs=freqs, spacing=case["spacing"]) for i in pick]
-        best, best_ms, trials = ctx.autotune(sample, reps=3, flags=xf, **kw)
+        best, best_ms, trials = ctx.autotune(sample, reps=5, flags=xf, **kw)
         tune = {"best": best, "start": {k: trials[0][k] for k in best}, "start_ms": trials[0]["ms"],
                 "best_ms": best_ms, "trials": len(trials),
                 "tried": [[{k: t[k] for k in best if t[k] != best[k]}, round(t["ms"], 4), t["status"]]
                           for t in trials],
                 "refused": sum(1 for t in trials if t["status"] != 0),
-                "sample": f"{len(pick)} of {na} aspects, mean of 3 runs per setting"}
+                "sample": f"{len(pick)} of {na} aspects, fastest of 5 runs per setting"}
 
     for _ in range(args.warmup):
         step()

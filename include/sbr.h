@@ -317,7 +317,7 @@ int sbr_get_tuning(const sbr_ctx* ctx, sbr_tuning* out);
 /* SBR_ERR_ARG for a value outside the ranges above. */
 int sbr_set_tuning(sbr_ctx* ctx, const sbr_tuning* t);
 
-/* One configuration tried by sbr_autotune: its mean time per run of the
+/* One configuration tried by sbr_autotune: its fastest time per run of the
  * sample batch (host wall clock of sbr_run_batch) and status: 0 accepted,
  * 1 refused because its dBsm differ from the starting configuration's by more
  * than 0.01 dB where those are above -40 dBsm, < 0 the error code of the run
@@ -332,13 +332,13 @@ typedef struct {
 /* Autotuner: times sbr_run_batch on the given sample batch (arguments as for
  * sbr_run_batch) under the current setting and then, one parameter at a
  * time (traversal: binary / 4-wide / warp-cooperative / octant copies, blocks per SM, ray
- * tile, stack depth, PO item, chunk size, silhouette mask), under
+ * tile, stack depth, PO item, chunk size, silhouette mask, rasterised primary hits), under
  * each alternative value, keeping a change when it is more than 1 % faster and its results
- * agree (see sbr_tune_trial). Each timing is the mean of `reps` runs after one
+ * agree (see sbr_tune_trial). Each timing is the fastest of `reps` runs after one
  * warm-up run. Leaves the fastest accepted setting on the ctx and returns it
  * in *best (and its time in *best_ms). trials: host array of capacity
- * trial_cap (may be NULL); *n_trials receives the number of runs tried.
- * Synchronises; takes about (2 + reps) x 18 runs of the sample. */
+ * trial_cap (may be NULL); *n_trials receives the number of settings tried.
+ * Synchronises; takes 1 + reps runs of the sample per setting tried. */
 int sbr_autotune(sbr_ctx* ctx, const sbr_request* req, int64_t n_req, const double* freq_hz, int64_t n_freq_total,
                  double margin_eta, int max_bounces, int pol_mask, int po_mode, const sbr_trace_opts* opt, int reps,
                  sbr_tune_trial* trials, int trial_cap, int* n_trials, sbr_tuning* best, double* best_ms);

@@ -239,6 +239,10 @@ cudaError_t launch_po(const PoArgs& a, cudaStream_t st, int n_blocks = 0);
 constexpr int kPoItemRecords = 1024;
 cudaError_t launch_po_items(const unsigned* recoff, PoAngle* angles, int n_angles, int n_pol, int item_records,
                             PoItem* items, int* n_items, long long* valid, cudaStream_t st);
+// the work list from host-built aspect tables: 64-bit record offsets (n_angles + 1) and PoAngle rows
+// whose item ranges and partial offsets are set
+cudaError_t launch_po_items_fill(const long long* recoff, const PoAngle* angles, int n_angles, int n_pol,
+                                 int item_records, PoItem* items, cudaStream_t st);
 // E[row][n_pol][2] and rcs[row][n_pol] for every aspect's rows (fixed-order FP64 sums of the partials)
 cudaError_t launch_po_final(const double* partial, const PoItem* items, const PoAngle* angles, int n_angles,
                             const double* kfreq, int n_pol, double* E, double* rcs, cudaStream_t st);

@@ -187,20 +187,22 @@ __global__ void k_po_items_scan(const unsigned* recoff, PoAngle* angles, int na,
     }
 }
 
-// Work list, stage 2: one warp per aspect writes its items.
-__global__ void k_po_items_fill(const unsigned* recoff, const PoAngle* angles, int na, int n_pol, int item_records,
+// Work list, stage 2: one warp per aspect writes its items. recoff: the record
+// offsets of the aspects (32-bit within a chunk, or 64-bit over a whole trace).
+template <typename Off>
+__global__ void k_po_items_fill(const Off* recoff, const PoAngle* angles, int na, int n_pol, int item_records,
                                 PoItem* items)
 {
     const int lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; a < na; a += nwarps) {
         const PoAngle A = angles[a];
-        const unsigned r0 = recoff[a], rc = recoff[a + 1] - r0;
+        const long long r0 = (long long)recoff[a], rc = (long long)recoff[a + 1] - r0;
         for (int r = lane; r < A.item_end - A.item_begin; r += 32) {
             PoItem it;
             it.angle = a;
-            it.count = (int)min((unsigned)item_records, rc - (unsigned)r * item_records);
-            it.first = (long long)r0 + (long long)r * item_records;
+            it.count = (int)min((long long)item_records, rc - (long long)r * item_records);
+            it.first = r0 + (long long)r * item_records;
             it.f0 = A.f0;
             it.nf = A.nf;
             it.part = A.part + (long long)r * A.nf * 2 * n_pol;
@@ -263,7 +265,16 @@ cudaError_t launch_po_items(const unsigned* recoff, PoAngle* angles, int n_angle
     if (n_angles <= 0 || item_records <= 0) return cudaErrorInvalidValue;
     k_po_items_scan<<<1, 1024, 0, st>>>(recoff, angles, n_angles, n_pol, item_records, n_items, valid);
     const int blocks = (int)std::min<long long>(((long long)n_angles * 32 + 255) / 256, 4096);
-    k_po_items_fill<<<blocks, 256, 0, st>>>(recoff, angles, n_angles, n_pol, item_records, items);
+    k_po_items_fill<unsigned><<<blocks, 256, 0, st>>>(recoff, angles, n_angles, n_pol, item_records, items);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_po_items_fill(const long long* recoff, const PoAngle* angles, int n_angles, int n_pol,
+                                 int item_records, PoItem* items, cudaStream_t st)
+{
+    if (n_angles <= 0 || item_records <= 0) return cudaErrorInvalidValue;
+    const int blocks = (int)std::min<long long>(((long long)n_angles * 32 + 255) / 256, 4096);
+    k_po_items_fill<long long><<<blocks, 256, 0, st>>>(recoff, angles, n_angles, n_pol, item_records, items);
     return cudaGetLastError();
 }
 
