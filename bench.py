@@ -743,7 +743,7 @@ def run_sbr(args, case, ws, rank, local, pg):
     pk, src = peaks()
     peak_ops = SM_COUNT * FP32_LANES_PER_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     achieved = ops / pass_s / 1e12
-    launches = stats[0]["kernel_launches"] + 2  # + PO reduce and PO final
+    launches = stats[0]["kernel_launches"] + 3  # + PO work list, PO reduce and PO final
     line = {"metric": "ray-bounces/s", "value": value, "unit": "ray-bounces/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
