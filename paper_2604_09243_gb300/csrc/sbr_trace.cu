@@ -1046,38 +1046,70 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_primary(const TraceArgs a)
     flush_stats<kCount>(a, nq, nvis, ntri, ovf);
 }
 
-// Primary pass of the rasterised aspects: each ray reads its key; the hit rays
-// go to the queue slots given by the scan of the raster masks (no atomics),
-// so the tiles are assigned statically (every tile costs about the same).
-template <bool kCount>
+// Primary pass of the rasterised aspects. The hit rays go to the queue slots
+// given by the scan of the raster masks (no atomics). Without a hit list each
+// ray reads its key and its state is written to its slot, the tiles assigned
+// statically (every tile costs about the same). With a hit list only (ray,
+// aspect) of each hit is written, from the mask words and slots alone.
+template <bool kCount, bool kList>
 __global__ void __launch_bounds__(kTraceThreads) k_primary_vis(const TraceArgs a)
 {
-    constexpr int kChunk = 4;  // tiles of a chunk; chunks interleaved over the warps (hits cluster in the grid)
     const int lane = threadIdx.x & 31;
+    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gw = gtid >> 5, nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long n_tiles = a.total_rays >> 5;
+    // one primary query per grid ray of every rasterised aspect
     unsigned nq = 0;
-    const long long n_tiles = a.total_rays >> 5, n_chunks = (n_tiles + kChunk - 1) / kChunk;
-    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    int ang = 0;
-    if (gw < n_chunks) {
-        if (lane == 0) ang = find_angle(a.ray_off, a.n_angles, (gw * kChunk) << 5);
-        ang = __shfl_sync(kFull, ang, 0);
-    }
-    for (long long chunk = gw; chunk < n_chunks; chunk += nw) {
-        for (long long tile = chunk * kChunk; tile < (chunk + 1) * kChunk && tile < n_tiles; ++tile) {
-            const long long base = tile << 5;
-            while (a.ray_off[ang + 1] <= base) ++ang;  // the tiles of a warp only move forward
-            if (a.vis_full[ang]) continue;  // warp-uniform; k_primary traverses this tile
-            const AngleDev& A = a.angles[ang];
-            const int local = (int)(base + lane - a.ray_off[ang]);
-            int i, j;
-            tile_ij(A, local, i, j);
-            if (i < A.nu && j < A.nv) ++nq;
-            const unsigned vmask = a.mask[tile];  // k_vis_mask
-            if (((vmask >> lane) & 1u) && a.hit_list) {
-                a.hit_list[a.tile_base[tile] + __popc(vmask & ((1u << lane) - 1u))] =
-                    make_uint2((unsigned)(base + lane), (unsigned)ang);
-            } else if ((vmask >> lane) & 1u) {
+    for (long long ang = gtid; ang < a.n_angles; ang += (long long)gridDim.x * blockDim.x)
+        if (!a.vis_full[ang]) nq += (unsigned)a.angles[ang].nu * (unsigned)a.angles[ang].nv;
+    if (kList) {
+        // 32 tiles per warp step: lane l loads the mask word and slot of tile t0 + l, then the warp
+        // writes the list entries tile by tile (a set bit implies a rasterised aspect: k_vis_mask
+        // clears the masks of flagged ones)
+        long long t0 = gw << 5;
+        int ang = 0;
+        long long next = 0;
+        if (t0 < n_tiles) {
+            if (lane == 0) ang = find_angle(a.ray_off, a.n_angles, t0 << 5);
+            ang = __shfl_sync(kFull, ang, 0);
+            next = a.ray_off[ang + 1];
+        }
+        for (; t0 < n_tiles; t0 += nw << 5) {
+            const long long t = t0 + lane;
+            unsigned m = 0, slot = 0;
+            if (t < n_tiles) {
+                m = a.mask[t];
+                if (m) slot = a.tile_base[t];
+            }
+            unsigned todo = __ballot_sync(kFull, m != 0u);
+            while (todo) {
+                const int k = __ffs(todo) - 1;
+                todo &= todo - 1u;
+                const unsigned mk = __shfl_sync(kFull, m, k), sk = __shfl_sync(kFull, slot, k);
+                const long long base = (t0 + k) << 5;
+                while (next <= base) next = a.ray_off[++ang + 1];  // the tiles of a warp only move forward
+                if ((mk >> lane) & 1u)
+                    a.hit_list[sk + __popc(mk & ((1u << lane) - 1u))] = make_uint2((unsigned)(base + lane), (unsigned)ang);
+            }
+        }
+    } else {
+        constexpr int kChunk = 4;  // tiles of a chunk; chunks interleaved over the warps (hits cluster in the grid)
+        const long long n_chunks = (n_tiles + kChunk - 1) / kChunk;
+        int ang = 0;
+        if (gw < n_chunks) {
+            if (lane == 0) ang = find_angle(a.ray_off, a.n_angles, (gw * kChunk) << 5);
+            ang = __shfl_sync(kFull, ang, 0);
+        }
+        for (long long chunk = gw; chunk < n_chunks; chunk += nw) {
+            for (long long tile = chunk * kChunk; tile < (chunk + 1) * kChunk && tile < n_tiles; ++tile) {
+                const long long base = tile << 5;
+                while (a.ray_off[ang + 1] <= base) ++ang;  // the tiles of a warp only move forward
+                const unsigned vmask = a.mask[tile];        // k_vis_mask; 0 for a flagged aspect
+                if (!((vmask >> lane) & 1u)) continue;
+                const AngleDev& A = a.angles[ang];
+                const int local = (int)(base + lane - a.ray_off[ang]);
+                int i, j;
+                tile_ij(A, local, i, j);
                 const unsigned long long key = __ldcs(a.vis + base + lane);
                 Hit h;
                 h.t = __uint_as_float((unsigned)(key >> 32));
@@ -1212,8 +1244,13 @@ void launch_trace_s(const TraceArgs& a, int n_blocks, bool count_visits, cudaStr
 {
     if (a.bounce == 0) {
         if (a.vis) {
-            if (count_visits) k_primary_vis<true><<<n_blocks, kTraceThreads, 0, st>>>(a);
-            else k_primary_vis<false><<<n_blocks, kTraceThreads, 0, st>>>(a);
+            if (a.hit_list) {
+                if (count_visits) k_primary_vis<true, true><<<n_blocks, kTraceThreads, 0, st>>>(a);
+                else k_primary_vis<false, true><<<n_blocks, kTraceThreads, 0, st>>>(a);
+            } else {
+                if (count_visits) k_primary_vis<true, false><<<n_blocks, kTraceThreads, 0, st>>>(a);
+                else k_primary_vis<false, false><<<n_blocks, kTraceThreads, 0, st>>>(a);
+            }
         }
         if (count_visits) k_primary<true, kStack, kMode><<<n_blocks, kTraceThreads, 0, st>>>(a);
         else k_primary<false, kStack, kMode><<<n_blocks, kTraceThreads, 0, st>>>(a);
