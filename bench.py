@@ -647,7 +647,12 @@ def run_sbr(args, case, ws, rank, local, pg):
     elif not args.no_autotune:
         # untimed: the autotuner picks blocks per SM, ray tile, stack depth, PO item and chunk size on an
         # evenly spaced sample of the workload's aspects
-        pick = np.linspace(0, na - 1, min(na, args.tune_aspects)).round().astype(int)
+        # enough aspects for at least 16 M rays, so the sample's passes fill the GPU as the full sweep does
+        per = np.mean([(lambda g: g["nu"] * g["nv"])(ctx.ray_grid_for(
+            ang[i, 0], ang[i, 1], case["spacing"], eta=case["eta"], window=case.get("window", 0.0),
+            offset=case.get("offset", (0.0, 0.0)))) for i in np.linspace(0, na - 1, min(na, 8)).round().astype(int)])
+        n_tune = max(args.tune_aspects, int(np.ceil(16e6 / max(1.0, per))))
+        pick = np.linspace(0, na - 1, min(na, n_tune)).round().astype(int)
         sample = [dict(az=float(ang[i, 0]), el=float(ang[i, 1]), freqs=freqs, spacing=case["spacing"]) for i in pick]
         best, best_ms, trials = ctx.autotune(sample, reps=5, flags=xf, **kw)
         tune = {"best": best, "start": {k: trials[0][k] for k in best}, "start_ms": trials[0]["ms"],
@@ -811,7 +816,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tuning")
     ap.add_argument("--no-precision", action="store_true", help="skip the phase-precision report")
     ap.add_argument("--builder", default="ploc", choices=["ploc", "lbvh"], help="BVH builder of the timed workload")
-    ap.add_argument("--tune-aspects", type=int, default=24, help="aspects in the autotuner's sample")
+    ap.add_argument("--tune-aspects", type=int, default=24,
+                    help="fewest aspects in the autotuner's sample (more where needed for 16 M rays)")
     ap.add_argument("--tune", default="", help="fixed tuning instead of the autotuner, e.g. tile_w=4,stack_depth=32")
     ap.add_argument("--sur-domains", default="full,patch,patch_dense", help="surrogate: domains to evaluate")
     ap.add_argument("--sur-scale", type=float, default=1.0, help="surrogate: fraction of the sample counts")
