@@ -842,14 +842,43 @@ __device__ __forceinline__ float3 primary_origin(const AngleDev& A, int i, int j
 constexpr int kRasterSmall = 32;    // cells a thread tests by itself
 constexpr int kRasterQueue = 256;   // larger triangles a block defers to its warps per round
 
-__device__ __forceinline__ void raster_cell(const AngleDev& A, float4 P, float4 B, float4 C, float3 d, unsigned orig,
-                                            int i, int j, unsigned long long* vrow)
+// An aspect's ray grid held in registers for the cell loops: the loops' atomics
+// could alias the aspect table as far as the compiler knows, so fields read
+// through it would be loaded again after every atomic.
+struct RasterGrid {
+    float3 p0, du, dv, d;
+    int nbu, tw;
+};
+
+__device__ __forceinline__ RasterGrid raster_grid(const AngleDev& A)
+{
+    RasterGrid G;
+    G.p0 = make_float3(A.p0[0], A.p0[1], A.p0[2]);
+    G.du = make_float3(A.du[0], A.du[1], A.du[2]);
+    G.dv = make_float3(A.dv[0], A.dv[1], A.dv[2]);
+    G.d = make_float3(A.dir[0], A.dir[1], A.dir[2]);
+    G.nbu = A.nbu;
+    G.tw = A.tw_log2;
+    return G;
+}
+
+// the origin of grid ray (i, j): primary_origin's operations in its order
+__device__ __forceinline__ float3 grid_origin(const RasterGrid& G, int i, int j)
+{
+    const float fi = (float)i, fj = (float)j;
+    return make_float3(__fadd_rn(__fadd_rn(G.p0.x, __fmul_rn(fi, G.du.x)), __fmul_rn(fj, G.dv.x)),
+                       __fadd_rn(__fadd_rn(G.p0.y, __fmul_rn(fi, G.du.y)), __fmul_rn(fj, G.dv.y)),
+                       __fadd_rn(__fadd_rn(G.p0.z, __fmul_rn(fi, G.du.z)), __fmul_rn(fj, G.dv.z)));
+}
+
+__device__ __forceinline__ void raster_cell(const RasterGrid& G, float4 P, float4 B, float4 C, unsigned orig, int i,
+                                            int j, unsigned long long* vrow)
 {
     float th;
-    if (tri_test(P, B, C, primary_origin(A, i, j), d, th) && th <= FLT_MAX) {
-        const int tw = A.tw_log2, sh = 5 - tw;  // tile of W = 2^tw by H = 2^sh rays
+    if (tri_test(P, B, C, grid_origin(G, i, j), G.d, th) && th <= FLT_MAX) {
+        const int tw = G.tw, sh = 5 - tw;  // tile of W = 2^tw by H = 2^sh rays
         const int bu = i >> tw, bv = j >> sh;
-        const long long pidx = ((long long)(bv * A.nbu + bu) << 5) + ((j & ((1 << sh) - 1)) << tw) + (i & ((1 << tw) - 1));
+        const long long pidx = ((long long)(bv * G.nbu + bu) << 5) + ((j & ((1 << sh) - 1)) << tw) + (i & ((1 << tw) - 1));
         atomicMin(vrow + pidx, ((unsigned long long)__float_as_uint(th) << 32) | orig);
     }
 }
@@ -894,11 +923,11 @@ __global__ void __launch_bounds__(256, 4) k_raster(const TraceArgs a, int n_tri,
                     s_item[slot] = t;
                     s_ang[slot] = ang;
                 } else {
-                    const float3 d = make_float3(A.dir[0], A.dir[1], A.dir[2]);
+                    const RasterGrid G = raster_grid(A);
                     unsigned long long* vrow = vis + a.ray_off[ang];
                     const unsigned orig = (unsigned)__float_as_int(P.w);
                     for (int j = j0; j <= j1; ++j)
-                        for (int i = i0; i <= i1; ++i) raster_cell(A, P, B, C, d, orig, i, j, vrow);
+                        for (int i = i0; i <= i1; ++i) raster_cell(G, P, B, C, orig, i, j, vrow);
                     ntri += (unsigned long long)ncell;
                 }
             }
@@ -914,18 +943,17 @@ __global__ void __launch_bounds__(256, 4) k_raster(const TraceArgs a, int n_tri,
         for (int k = warp; k < n_def; k += n_warps) {
             const int td = s_item[k], ad = s_ang[k];
             const int4 r = s_rng[k];
-            const AngleDev& A = a.angles[ad];
+            const RasterGrid G = raster_grid(a.angles[ad]);
             const float4* tp = a.tris + 3 * (size_t)td;
             const float4 P = __ldg(tp), B = __ldg(tp + 1), C = __ldg(tp + 2);
             const unsigned orig = (unsigned)__float_as_int(P.w);
-            const float3 d = make_float3(A.dir[0], A.dir[1], A.dir[2]);
             unsigned long long* vrow = vis + a.ray_off[ad];
             const int w = r.y - r.x + 1, ncell = w * (r.w - r.z + 1);
             // cell c = (c / w, c % w) from (j0, i0); steps of 32 cells: sj rows and si columns
             const int sj = 32 / w, si = 32 - sj * w, l0 = lane / w;
             int i = r.x + (lane - l0 * w), j = r.z + l0;
             for (int cidx = lane; cidx < ncell; cidx += 32) {
-                raster_cell(A, P, B, C, d, orig, i, j, vrow);
+                raster_cell(G, P, B, C, orig, i, j, vrow);
                 i += si;
                 j += sj;
                 if (i > r.y) {
