@@ -335,10 +335,11 @@ typedef struct {
  * tile, stack depth, PO item, chunk size, silhouette mask, rasterised primary hits), under
  * each alternative value, keeping a change when it is more than 1 % faster and its results
  * agree (see sbr_tune_trial). Each timing is the fastest of `reps` runs after one
- * warm-up run. Leaves the fastest accepted setting on the ctx and returns it
- * in *best (and its time in *best_ms). trials: host array of capacity
- * trial_cap (may be NULL); *n_trials receives the number of settings tried.
- * Synchronises; takes 1 + reps runs of the sample per setting tried. */
+ * warm-up run; a candidate's runs alternate with runs of the current setting,
+ * and the two are compared on those. Leaves the fastest accepted setting on the
+ * ctx and returns it in *best (and its time in *best_ms). trials: host array of
+ * capacity trial_cap (may be NULL); *n_trials receives the number of settings
+ * tried. Synchronises; takes 1 + 2 reps runs of the sample per setting tried. */
 int sbr_autotune(sbr_ctx* ctx, const sbr_request* req, int64_t n_req, const double* freq_hz, int64_t n_freq_total,
                  double margin_eta, int max_bounces, int pol_mask, int po_mode, const sbr_trace_opts* opt, int reps,
                  sbr_tune_trial* trials, int trial_cap, int* n_trials, sbr_tuning* best, double* best_ms);

@@ -1572,23 +1572,38 @@ int sbr_autotune(sbr_ctx* c, const sbr_request* req, int64_t n_req, const double
     const sbr_tuning start = c->tune;
     std::vector<double> ref((size_t)(rows * n_pol)), cur(ref.size());
     int nt = 0;
-    auto run = [&](const sbr_tuning& t, std::vector<double>& rcs, double* ms) -> int {
+    // one run of the sample under setting t (results left in dR), its wall time in *ms
+    auto once = [&](const sbr_tuning& t, double* ms) -> int {
         c->tune = t;
+        const auto t0 = std::chrono::steady_clock::now();
         int rc = sbr_run_batch(c, req, n_req, freq_hz, n_freq_total, eta, max_bounces, pol_mask, po_mode, opt,
                                nullptr, dR.as<double>(), 1, nullptr);
+        if (cudaDeviceSynchronize() != cudaSuccess) return fail(c, SBR_ERR_CUDA, "sbr_autotune: sync");
+        *ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        return rc;
+    };
+    // a warm-up run of t (its dBsm into rcs), then `reps` timed runs of t, each followed by a run of the
+    // setting `base` when given, so that both see the same drift of clocks and host; the fastest run of
+    // each (host jitter only ever adds time)
+    auto run = [&](const sbr_tuning& t, std::vector<double>& rcs, double* ms, const sbr_tuning* base,
+                   double* base_ms) -> int {
+        double w = 0.0;
+        int rc = once(t, &w);
         if (rc != SBR_OK) return rc;
         if (cudaMemcpy(rcs.data(), dR.p, sizeof(double) * rcs.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
             return fail(c, SBR_ERR_CUDA, "sbr_autotune: copy results");
-        // the fastest of the timed runs: host jitter only ever adds time
-        double fastest = 1e300;
+        double fastest = 1e300, fastest_b = 1e300;
         for (int k = 0; k < reps && rc == SBR_OK; ++k) {
-            const auto t0 = std::chrono::steady_clock::now();
-            rc = sbr_run_batch(c, req, n_req, freq_hz, n_freq_total, eta, max_bounces, pol_mask, po_mode, opt,
-                               nullptr, dR.as<double>(), 1, nullptr);
-            if (cudaDeviceSynchronize() != cudaSuccess) return fail(c, SBR_ERR_CUDA, "sbr_autotune: sync");
-            fastest = std::min(fastest, std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
+            rc = once(t, &w);
+            fastest = std::min(fastest, w);
+            if (base && rc == SBR_OK) {
+                const int rb = once(*base, &w);
+                if (rb != SBR_OK) return rb;
+                fastest_b = std::min(fastest_b, w);
+            }
         }
         *ms = fastest;
+        if (base_ms) *base_ms = fastest_b;
         return rc;
     };
     auto note = [&](const sbr_tuning& t, double ms, int status) {
@@ -1601,7 +1616,7 @@ int sbr_autotune(sbr_ctx* c, const sbr_request* req, int64_t n_req, const double
         ++nt;
     };
     double cur_ms = 0.0;
-    int rc = run(start, ref, &cur_ms);
+    int rc = run(start, ref, &cur_ms, nullptr, nullptr);
     note(start, cur_ms, rc);
     if (rc != SBR_OK) {
         c->tune = start;
@@ -1637,8 +1652,8 @@ int sbr_autotune(sbr_ctx* c, const sbr_request* req, int64_t n_req, const double
                 *fields[p] = v;
             }
             if (!tuning_ok(t)) continue;
-            double ms = 0.0;
-            int st = run(t, cur, &ms);
+            double ms = 0.0, base_ms = 0.0;
+            int st = run(t, cur, &ms, &bestt, &base_ms);
             if (st == SBR_OK) {
                 for (size_t i = 0; i < ref.size(); ++i)
                     if (ref[i] > -40.0 && !(fabs(cur[i] - ref[i]) <= 0.01)) {
@@ -1647,9 +1662,12 @@ int sbr_autotune(sbr_ctx* c, const sbr_request* req, int64_t n_req, const double
                     }
             }
             note(t, ms, st);
-            if (st == SBR_OK && ms < 0.99 * cur_ms) {  // keep a change only when it is clearly faster
+            // keep a change only when it is clearly faster than the current setting timed beside it
+            if (st == SBR_OK && ms < 0.99 * base_ms) {
                 cur_ms = ms;
                 bestt = t;
+            } else if (st == SBR_OK) {
+                cur_ms = std::min(cur_ms, base_ms);
             }
         }
     }
