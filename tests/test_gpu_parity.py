@@ -352,6 +352,27 @@ def test_chunked_trace_matches_single_chunk(G, ctx):
     assert np.array_equal(E1, E2)
 
 
+def test_many_aspects_match_split_calls(G, ctx):
+    """20,000 aspects in one call (a staging upload above the first pinned
+    buffer, a PO work list of 20,000 aspect rows expanded on the device) give
+    the same fields, bit for bit, as the same aspects in four calls."""
+    xyz, tri = S.dihedral(1.0, 4)
+    ctx.load_mesh(xyz, tri)
+    rng = np.random.default_rng(21)
+    ang = np.stack([rng.uniform(0.0, 360.0, 20_000), rng.uniform(-30.0, 60.0, 20_000)], 1)
+    st = ctx.trace(ang, 0.1, max_bounces=2)
+    E1, R1 = ctx.po_integrate([3e9, 5e9], "HH,VV")
+    assert st["n_angles"] == 20_000 and st["valid_rays"] > 0
+    valid = 0
+    for k in range(4):
+        part = ctx.trace(ang[k * 5000:(k + 1) * 5000], 0.1, max_bounces=2)
+        valid += part["valid_rays"]
+        E2, R2 = ctx.po_integrate([3e9, 5e9], "HH,VV")
+        assert np.array_equal(E1[k * 5000:(k + 1) * 5000], E2)
+        assert np.array_equal(R1[k * 5000:(k + 1) * 5000], R2)
+    assert valid == st["valid_rays"]
+
+
 def test_deterministic_results(G, ctx):
     case = S.trihedral_case(az_step=15.0)
     ctx.load_mesh(case["xyz"], case["tri"])
