@@ -337,7 +337,8 @@ typedef struct {
  * agree (see sbr_tune_trial). Each timing is the fastest of `reps` runs after one
  * warm-up run; a candidate's runs alternate with runs of the current setting,
  * and the two are compared on those. Leaves the fastest accepted setting on the
- * ctx and returns it in *best (and its time in *best_ms). trials: host array of
+ * ctx and returns it in *best, and in *best_ms the fastest time measured for it
+ * (its own trial or a run beside a later candidate). trials: host array of
  * capacity trial_cap (may be NULL); *n_trials receives the number of settings
  * tried. Synchronises; takes 1 + 2 reps runs of the sample per setting tried. */
 int sbr_autotune(sbr_ctx* ctx, const sbr_request* req, int64_t n_req, const double* freq_hz, int64_t n_freq_total,

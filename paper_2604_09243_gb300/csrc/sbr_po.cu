@@ -69,12 +69,13 @@ __global__ void __launch_bounds__(kPoThreads) k_po(const PoArgs a)
             if (idx < I.count) {
                 const float4* p = reinterpret_cast<const float4*>(a.rec + I.first + idx);
                 const float4 x = __ldg(p), y = __ldg(p + 1);
-                const float cv[5] = {x.x, x.y, x.z, x.w, y.x};
 #pragma unroll
                 for (int q = 0; q < kPol; ++q) {
+                    // coefficient of polarisation pol_sel[q] (a selection, not an indexed local array)
                     const int sel = a.pol_sel[q];
+                    const float vec = sel == 0 ? x.x : (sel == 1 ? x.y : (sel == 2 ? x.z : x.w));
                     float v = 0.f;
-                    if (q < a.n_pol) v = a.scalar ? (sel < 2 ? cv[4] : 0.f) : cv[sel];
+                    if (q < a.n_pol) v = a.scalar ? (sel < 2 ? y.x : 0.f) : vec;
                     cf[k][q] = v;
                 }
                 lh[k] = y.y;
@@ -218,11 +219,26 @@ __global__ void k_po_final(const double* partial, const PoItem* items, const PoA
     const PoAngle A = angles[blockIdx.x];
     for (int o = threadIdx.x; o < A.nf * n_pol; o += blockDim.x) {
         const int q = o / n_pol, p = o - q * n_pol;
+        // item order, as written; the loads of 8 items are issued before their additions
         double sr = 0.0, si = 0.0;
-        for (int it = A.item_begin; it < A.item_end; ++it) {
-            const double* v = partial + items[it].part + (size_t)q * (2 * n_pol) + 2 * p;
-            sr += v[0];
-            si += v[1];
+        for (int it0 = A.item_begin; it0 < A.item_end; it0 += 8) {
+            double vr[8], vi[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                vr[u] = 0.0;
+                vi[u] = 0.0;
+                if (it0 + u < A.item_end) {
+                    const double* v = partial + items[it0 + u].part + (size_t)q * (2 * n_pol) + 2 * p;
+                    vr[u] = v[0];
+                    vi[u] = v[1];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (it0 + u < A.item_end) {
+                    sr += vr[u];
+                    si += vi[u];
+                }
         }
         // E = (-j k / 4 pi) (sr + j si)
         const double pre = kfreq[A.f0 + q] / (4.0 * 3.14159265358979323846);

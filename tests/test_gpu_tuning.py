@@ -101,9 +101,12 @@ def test_autotune_keeps_an_accepted_setting(G, tri_case):
         assert c.tuning() == best
         assert len(trials) >= 10 and ms > 0
         ok = [t for t in trials if t["status"] == 0]
-        assert ok[0]["ms"] >= ms  # the starting setting is never faster than the kept one
+        # every kept change beat the setting before it, timed beside it, by 1 %; separate timings of the
+        # starting setting and the kept one can still differ by noise
+        assert ms <= 1.05 * ok[0]["ms"]
         assert any(all(t[k] == best[k] for k in best) for t in ok)
-        assert ms == min(t["ms"] for t in ok if all(t[k] == best[k] for k in best))
+        # best_ms is the fastest of all the kept setting's timings, its own trial's among them
+        assert ms <= min(t["ms"] for t in ok if all(t[k] == best[k] for k in best))
 
 
 def test_wide_tree_same_hits_aircraft(G):
