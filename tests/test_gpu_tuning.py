@@ -260,6 +260,13 @@ def test_raster_with_flagged_and_rasterised_aspects_in_one_chunk(G, orc):
                 for a, (az, el) in enumerate(ang):
                     fr = orc.make_frame(om.bbox, az, el, sp)
                     assert_hit_parity(compare_hits(*hits[a], orc.trace(om, fr, 3)))
+                # the same aspects again in reverse order, in the same context: the raster keys left by
+                # the first trace (a flagged aspect's included) must all read "no hit" again
+                c.trace(ang[::-1], sp, max_bounces=3, flags=G.TRACE_RECORD_HITS)
+                again = [c.get_hits(a) for a in range(len(ang))][::-1]
+                for x0, y0 in zip(hits, again):
+                    for x, y in zip(x0, y0):
+                        assert np.array_equal(x, y)
     (s0, h0, R0), (s1, h1, R1) = out
     assert s1["raster_tests"] > 0 and 0 < s1["node_visits"]
     assert s0["ray_bounces"] == s1["ray_bounces"] and s0["valid_rays"] == s1["valid_rays"]
