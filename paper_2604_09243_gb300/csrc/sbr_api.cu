@@ -673,10 +673,14 @@ int trace_chunk(sbr_ctx* c, TraceRun& R, int64_t a0, int64_t a1, long long rec_b
     if (need > c->rec.cap) {
         DevBuf nb;
         CK(nb.ensure(need + need / 4), "alloc records");
+        cudaError_t e = cudaSuccess;
         if (rec_base > 0)
-            CK(cudaMemcpyAsync(nb.p, c->rec.p, sizeof(Record) * (size_t)rec_base, cudaMemcpyDeviceToDevice, c->stream),
-               "copy records");
-        CK(cudaStreamSynchronize(c->stream), "records sync");
+            e = cudaMemcpyAsync(nb.p, c->rec.p, sizeof(Record) * (size_t)rec_base, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            nb.release();
+            return cuda_fail(c, e, "copy records");
+        }
         c->rec.release();
         c->rec = nb;
     }
