@@ -52,8 +52,7 @@ class Frame(C.Structure):
 
 class TraceOpts(C.Structure):
     _fields_ = [("max_bounces", C.c_int), ("po_mode", C.c_int), ("phase_literal", C.c_int),
-                ("require_escape", C.c_int), ("use_bvh", C.c_int), ("n_threads", C.c_int),
-                ("transport", C.c_int)]
+                ("require_escape", C.c_int), ("use_bvh", C.c_int), ("n_threads", C.c_int)]
 
 
 _lib = None
@@ -77,6 +76,8 @@ def lib():
         L.orc_mesh_free.restype = None
         L.orc_mesh_bbox.argtypes = [C.c_void_p, P(C.c_float)]
         L.orc_mesh_bbox.restype = None
+        L.orc_mesh_normals.argtypes = [C.c_void_p, P(C.c_float)]
+        L.orc_mesh_normals.restype = None
         L.orc_mesh_n_degenerate.argtypes = [C.c_void_p]
         L.orc_mesh_n_degenerate.restype = C.c_int64
         L.orc_mesh_build_bvh.argtypes = [C.c_void_p, C.c_int]
@@ -162,8 +163,15 @@ class Mesh:
 
     @property
     def n_degenerate(self) -> int:
-        """Triangles that take no hits: sine of the FP32 edge angle at most 2^-20."""
+        """Triangles that take no hits: sine of the edge angle at most 2^-20."""
         return int(lib().orc_mesh_n_degenerate(self._h))
+
+    @property
+    def normals(self) -> np.ndarray:
+        """FP32 unit normals [n_tri, 3] (the rounded FP64 normal; 0 for a degenerate triangle)."""
+        n = np.zeros((self.n_tri, 3), np.float32)
+        lib().orc_mesh_normals(self._h, _ptr(n, C.c_float))
+        return n
 
     @property
     def bvh_nodes(self) -> int:
@@ -185,16 +193,17 @@ class Mesh:
 
 
 def trace(mesh: Mesh, frame: Frame, max_bounces: int, po_mode: str = "vector", phase_literal: bool = False,
-          require_escape: bool = False, use_bvh: bool = True, ids=None, threads: int | None = None,
-          transport: str = "fp32") -> dict:
+          require_escape: bool = False, use_bvh: bool = True, ids=None, threads: int | None = None) -> dict:
     """Trace rays of ``frame`` (all, or the ray ids ``ids`` = j*nu + i) through
     ``mesh`` (Algorithm 2) and return per-ray arrays: hit_tri/hit_t [n, B],
-    nb, valid, band, coef [n, 4] (HH, VV, HV, VH) and L.
+    nb, valid, band (bit 0: a hit within 1e-6 barycentric of an edge, bit 1: a
+    runner-up within 1e-6 relative in t), bmin, coef [n, 4] (HH, VV, HV, VH)
+    and L.
 
-    transport="fp32": hit decisions, hit points, normals, reflections and
-    offsets in the written FP32 operation order (the precision the traversal
-    runs in); transport="exact": the same steps in FP64 with exact inclusive
-    edges. Path length, fields and coefficients are FP64 in both."""
+    Hit decisions are exact (FP64 on the FP32 ray and vertices); the ray state
+    between bounces is FP32, each value the rounding of its defining formula
+    (hit_t is the stored FP32 distance t32). Path length, fields and
+    coefficients are FP64."""
     B = int(max_bounces)
     if ids is None:
         n = frame.n_rays
@@ -208,8 +217,7 @@ def trace(mesh: Mesh, frame: Frame, max_bounces: int, po_mode: str = "vector", p
                coef=np.empty((n, 4), np.float64), L=np.empty(n, np.float64), bmin=np.empty(n, np.float64),
                counters=np.zeros(2, np.int64))
     o = TraceOpts(B, 1 if po_mode == "scalar" else 0, int(bool(phase_literal)), int(bool(require_escape)),
-                  int(bool(use_bvh) and mesh.has_bvh), int(threads or default_threads()),
-                  {"fp32": 0, "exact": 1}[transport])
+                  int(bool(use_bvh) and mesh.has_bvh), int(threads or default_threads()))
     rc = lib().orc_trace(mesh._h, C.byref(frame), C.byref(o), _ptr(idp, C.c_int64), n,
                          _ptr(out["hit_tri"], C.c_int32), _ptr(out["hit_t"], C.c_double),
                          _ptr(out["nb"], C.c_int32), _ptr(out["valid"], C.c_uint8), _ptr(out["band"], C.c_uint8),
@@ -254,12 +262,11 @@ def mie_pec_backscatter(x: float) -> float:
 
 
 def rcs_angle(mesh: Mesh, bbox, az, el, spacing, freqs, max_bounces, eta=0.05, window=0.0, offset=(0.0, 0.0),
-              po_mode="vector", phase_literal=False, require_escape=False, threads=None, ids=None,
-              transport="fp32", rx=None):
+              po_mode="vector", phase_literal=False, require_escape=False, threads=None, ids=None, rx=None):
     """Convenience: one aspect, trace + PO. Returns (E [nf,4], rcs_dbsm [nf,4], trace dict, frame).
     ``rx`` = (az, el) of a bistatic receiver (None: monostatic)."""
     fr = make_frame(bbox, az, el, spacing, eta=eta, window=window, offset=offset, rx=rx)
     tr = trace(mesh, fr, max_bounces, po_mode=po_mode, phase_literal=phase_literal,
-               require_escape=require_escape, ids=ids, threads=threads, transport=transport)
+               require_escape=require_escape, ids=ids, threads=threads)
     E, rcs = po(tr["coef"], tr["L"], tr["valid"], freqs)
     return E, rcs, tr, fr

@@ -31,20 +31,25 @@
  *     P0, ds*u, ds*v and k are rounded once to FP32 and ray (i, j) starts at
  *     o = (P0 + i*U) + j*V evaluated in FP32 without fused multiply-add, so both
  *     sides trace bit-identical rays; the oracle then continues in FP64.
- *   - Intersection: Moller-Trumbore form, t > 0, the triangle just left is
- *     skipped, and the closest hit is the smallest (t, original triangle index)
- *     pair.
- *   - Transport precision. Which triangle a ray hits is an integer decided by
- *     floating point; the oracle takes that decision in FP32, the precision the
- *     paper runs its traversal in and the kernel's, following a written
- *     operation order (ORC_FP32 transport below: explicit fused multiply-adds,
- *     IEEE division and square root, a barycentric slack of 2^-12 that closes
- *     FP32 cracks along shared edges). Everything downstream of the hits (path
- *     length, field transport, PO sums) is FP64. An exact FP64 transport
- *     (inclusive edges, no slack) is kept beside it for the physics checks and
- *     for measuring the edge band.
- *   - eps = 1e-5 * bbox diagonal, applied along the normal turned toward the
- *     incoming side.
+ *   - Intersection: the exact test of the ray o + t d against the closed
+ *     triangle (inclusive edges, t > 0) in Moller-Trumbore form, evaluated in
+ *     FP64 on the FP32 ray and the FP32 vertices (edge differences, products
+ *     and the decision carry rounding errors near 1e-16 relative, far inside the
+ *     1e-6 edge band). The triangle just left is skipped, and the closest hit is
+ *     the smallest (t, original triangle index) pair.
+ *   - Ray state. The paper traces in FP32, so each bounce's ray is stored in
+ *     FP32: every stored value is the FP32 rounding of its defining formula,
+ *     evaluated on the previous FP32 state (the primary rays follow the grid
+ *     rule above):
+ *       n32 = fl32(N / |N|), N = (v1 - v0) x (v2 - v0)     (FP64, per triangle)
+ *       t32 = fl32(((v0 - o) . n32) / (d . n32))   (hit distance to the plane of
+ *             n32 through v0; the hit triangle itself is decided exactly)
+ *       x   = fl32(o + t32 d),  c = fl32(d . n32)
+ *       d'  = fl32(d - 2 c n32),  o' = fl32(x + eps32 nf),
+ *     with nf = n32 turned toward the incoming side (sign of d . n32) and
+ *     eps32 = fl32(1e-5 * bbox diagonal). Paths, fields and PO sums stay FP64.
+ *   - Degenerate triangle (no hits): |N|^2 <= (2^-20 |e1|^2)(2^-20 |e2|^2) in
+ *     FP64 (sine of the edge angle at most 2^-20).
  *   - Path L = k.o0 + sum t_b + k.x_last (monostatic round trip to a reference
  *     plane through the world origin); for one bounce this is 2 k.x1, i.e. the
  *     paper's e^{-j2kR} up to a constant phase. PHASE_LITERAL uses 2 (k.o0 + R).
@@ -197,16 +202,13 @@ typedef struct {
 typedef struct {
     int64_t nt;
     double* v0;  /* [nt][3] */
-    double* e1;  /* [nt][3] */
-    double* e2;  /* [nt][3] */
-    double* nrm; /* [nt][3] unit normal e1 x e2 / |e1 x e2| */
+    double* e1;  /* [nt][3] v1 - v0 (exact: a difference of FP32 values) */
+    double* e2;  /* [nt][3] v2 - v0 */
+    float* n32;  /* [nt][3] FP32 rounding of the unit normal e1 x e2 / |e1 x e2| (0 when degenerate) */
     double* cen; /* [nt][3] centroid */
-    double* tlo; /* [nt][3] triangle AABB, enlarged to cover the FP32 test's slack */
+    double* tlo; /* [nt][3] triangle AABB, widened by a few FP64 rounding units */
     double* thi;
-    float* v0f;  /* [nt][3] FP32 vertex 0 */
-    float* e1f;  /* [nt][3] FP32 edge v1 - v0 (rounded) */
-    float* e2f;  /* [nt][3] FP32 edge v2 - v0 (rounded) */
-    unsigned char* deg; /* [nt] 1: the FP32 normal e1f x e2f has zero squared length, no hits */
+    unsigned char* deg; /* [nt] 1: degenerate, takes no hits */
     float bbox[6];
     orc_node* nodes;
     int64_t n_nodes, cap_nodes;
@@ -217,22 +219,18 @@ typedef struct {
 void orc_mesh_free(orc_mesh* m)
 {
     if (!m) return;
-    free(m->v0); free(m->e1); free(m->e2); free(m->nrm); free(m->cen); free(m->tlo); free(m->thi);
-    free(m->v0f); free(m->e1f); free(m->e2f); free(m->deg);
+    free(m->v0); free(m->e1); free(m->e2); free(m->n32); free(m->cen); free(m->tlo); free(m->thi);
+    free(m->deg);
     free(m->nodes); free(m->order);
     free(m);
 }
 
-static void cross32(const float* a, const float* b, float* c);
-static float dot32(const float* a, const float* b);
-
 /* Refuses bad indices and non-finite coordinates (NULL). A degenerate
- * triangle is kept but takes no hits: in the written FP32 order,
- * |e1 x e2|^2 <= (2^-20 |e1|^2)(2^-20 |e2|^2), so the sine of the angle between
- * its edges is at most 2^-20 and the rounding of the cross product (about
- * 2^-24 |e1||e2|) is over 6 % of its length; repeated or collinear vertices
- * give zero. The paper assumes a valid surface mesh; such a triangle has no
- * usable normal to reflect about. */
+ * triangle is kept but takes no hits: |e1 x e2|^2 <= (2^-20 |e1|^2)(2^-20 |e2|^2)
+ * in FP64 (cross product, squared lengths and products in that order), so the
+ * sine of the angle between its edges is at most 2^-20; repeated or collinear
+ * vertices give zero. The paper assumes a valid surface mesh; such a triangle
+ * has no usable normal to reflect about. */
 orc_mesh* orc_mesh_create(const float* xyz, int64_t nv, const int32_t* tri, int64_t nt)
 {
     if (!xyz || !tri || nt < 1 || nv < 3) return NULL;
@@ -241,10 +239,9 @@ orc_mesh* orc_mesh_create(const float* xyz, int64_t nv, const int32_t* tri, int6
     orc_mesh* m = (orc_mesh*)calloc(1, sizeof(orc_mesh));
     m->nt = nt;
     size_t b = sizeof(double) * 3 * (size_t)nt;
-    m->v0 = malloc(b); m->e1 = malloc(b); m->e2 = malloc(b); m->nrm = malloc(b);
+    m->v0 = malloc(b); m->e1 = malloc(b); m->e2 = malloc(b);
     m->cen = malloc(b); m->tlo = malloc(b); m->thi = malloc(b);
-    size_t bf = sizeof(float) * 3 * (size_t)nt;
-    m->v0f = malloc(bf); m->e1f = malloc(bf); m->e2f = malloc(bf);
+    m->n32 = malloc(sizeof(float) * 3 * (size_t)nt);
     m->deg = malloc((size_t)nt);
     for (int c = 0; c < 3; ++c) { m->bbox[c] = INFINITY; m->bbox[3 + c] = -INFINITY; }
     for (int64_t v = 0; v < nv; ++v)
@@ -265,34 +262,34 @@ orc_mesh* orc_mesh_create(const float* xyz, int64_t nv, const int32_t* tri, int6
             m->cen[3 * k + c] = (A[c] + B[c] + C[c]) / 3.0;
             m->tlo[3 * k + c] = fmin(A[c], fmin(B[c], C[c]));
             m->thi[3 * k + c] = fmax(A[c], fmax(B[c], C[c]));
-            m->v0f[3 * k + c] = xyz[3 * ia + c];
-            m->e1f[3 * k + c] = xyz[3 * ib + c] - xyz[3 * ia + c];
-            m->e2f[3 * k + c] = xyz[3 * ic + c] - xyz[3 * ia + c];
         }
-        /* FP32 hits may lie up to the slack (2^-12 of the triangle) plus a few
-         * FP32 rounding units outside the exact triangle: widen its box */
+        /* the exact hit lies in the triangle's box; widen it by a few FP64
+         * rounding units so the FP64 slab test cannot cull a flat (axis-aligned)
+         * triangle's box on rounding */
         double ext = 0.0, mag = 0.0;
         for (int c = 0; c < 3; ++c) {
             ext = fmax(ext, m->thi[3 * k + c] - m->tlo[3 * k + c]);
             mag = fmax(mag, fmax(fabs(m->tlo[3 * k + c]), fabs(m->thi[3 * k + c])));
         }
-        double grow = ext * 0x1p-11 + mag * 0x1p-19 + 1e-30;
+        double grow = (ext + mag) * 0x1p-36 + 1e-30;
         for (int c = 0; c < 3; ++c) {
             m->tlo[3 * k + c] -= grow;
             m->thi[3 * k + c] += grow;
         }
-        float n32[3];
-        cross32(m->e1f + 3 * k, m->e2f + 3 * k, n32);
-        {
-            const float l1 = dot32(m->e1f + 3 * k, m->e1f + 3 * k), l2 = dot32(m->e2f + 3 * k, m->e2f + 3 * k);
-            m->deg[k] = dot32(n32, n32) <= (l1 * 0x1p-20f) * (l2 * 0x1p-20f);
-        }
         double n[3];
         cross3(m->e1 + 3 * k, m->e2 + 3 * k, n);
-        double ln = sqrt(dot3(n, n));
-        for (int c = 0; c < 3; ++c) m->nrm[3 * k + c] = ln > 0.0 ? n[c] / ln : 0.0;
+        const double nn = dot3(n, n), l1 = dot3(m->e1 + 3 * k, m->e1 + 3 * k), l2 = dot3(m->e2 + 3 * k, m->e2 + 3 * k);
+        m->deg[k] = nn <= (l1 * 0x1p-20) * (l2 * 0x1p-20);
+        const double ln = sqrt(nn);
+        for (int c = 0; c < 3; ++c) m->n32[3 * k + c] = m->deg[k] ? 0.0f : (float)(n[c] / ln);
     }
     return m;
+}
+
+/* FP32 unit normals of the triangles [nt][3] (0 for a degenerate one) */
+void orc_mesh_normals(const orc_mesh* m, float* out)
+{
+    memcpy(out, m->n32, sizeof(float) * 3 * (size_t)m->nt);
 }
 
 int64_t orc_mesh_n_degenerate(const orc_mesh* m)
@@ -400,63 +397,18 @@ static int tri_hit(const orc_mesh* m, int64_t k, const double* o, const double* 
     return 1;
 }
 
-/* ORC_FP32 transport: the FP32 operation order both implementations follow.
- * fmaf is one rounding; every other operation is one FP32 round-to-nearest
- * operation (this file is compiled without contraction). */
-static void cross32(const float* a, const float* b, float* c)
-{
-    c[0] = fmaf(a[1], b[2], -(a[2] * b[1]));
-    c[1] = fmaf(a[2], b[0], -(a[0] * b[2]));
-    c[2] = fmaf(a[0], b[1], -(a[1] * b[0]));
-}
-static float dot32(const float* a, const float* b) { return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2])); }
-
-/* Moller-Trumbore in FP32: e1 = v1 - v0 and e2 = v2 - v0 rounded to FP32,
- * p = d x e2, det = e1.p, s = o - v0, U = s.p, q = s x e1, V = d.q, T = e2.q;
- * with U, V, T negated when det < 0 and a = |det|, m = a 2^-12 (the slack),
- * a hit needs det != 0, U >= -m, V >= -m, U + V <= a + m, T > 0; t = T / det. */
-static int tri_hit32(const orc_mesh* m, int64_t k, const float* o, const float* d, float* t, double* bmin)
-{
-    const float *v0 = m->v0f + 3 * k, *e1 = m->e1f + 3 * k, *e2 = m->e2f + 3 * k;
-    float p[3], q[3], s[3];
-    if (m->deg[k]) return 0;
-    cross32(d, e2, p);
-    float det = dot32(e1, p);
-    if (det == 0.0f) return 0;
-    for (int c = 0; c < 3; ++c) s[c] = o[c] - v0[c];
-    float U = dot32(s, p);
-    cross32(s, e1, q);
-    float V = dot32(d, q);
-    float T = dot32(e2, q);
-    float a = det, Us = U, Vs = V, Ts = T;
-    if (det < 0.0f) { a = -det; Us = -U; Vs = -V; Ts = -T; }
-    float mg = a * 0x1p-12f;
-    if (!(Us >= -mg && Vs >= -mg && Us + Vs <= a + mg && Ts > 0.0f)) return 0;
-    *t = T / det;
-    double ad = (double)a;
-    *bmin = fmin((double)Us, fmin((double)Vs, ad - (double)Us - (double)Vs)) / ad;
-    return 1;
-}
-
 typedef struct {
     double t, t2, bmin;
     int64_t k;
     int64_t tests, nodes;
 } orc_hit;
 
-/* candidate triangle k; fp32 selects the FP32 test (ray o32, d32), else FP64 (o, d) */
-static void consider(const orc_mesh* m, int64_t k, const double* o, const double* d, const float* o32,
-                     const float* d32, int fp32, orc_hit* h)
+/* candidate triangle k of the FP64 ray (o, d) */
+static void consider(const orc_mesh* m, int64_t k, const double* o, const double* d, orc_hit* h)
 {
     double t, b;
     h->tests++;
-    if (fp32) {
-        float tf;
-        if (!tri_hit32(m, k, o32, d32, &tf, &b)) return;
-        t = (double)tf;
-    } else if (!tri_hit(m, k, o, d, &t, &b)) {
-        return;
-    }
+    if (!tri_hit(m, k, o, d, &t, &b)) return;
     if (t < h->t || (t == h->t && k < h->k)) {
         if (h->k >= 0 && h->t < h->t2) h->t2 = h->t;
         h->t = t;
@@ -485,11 +437,9 @@ static int slab(const orc_node* nd, const double* o, const double* d, double tma
     return 1;
 }
 
-/* closest hit skipping triangle `skip`; use_bvh = 0 brute force, 1 median BVH.
- * With fp32 set the FP32 ray (o32, d32) is tested; (o, d) is then the same ray
- * in FP64 and only drives the (conservative) box culling. */
-static void closest(const orc_mesh* m, int use_bvh, const double* o, const double* d, const float* o32,
-                    const float* d32, int fp32, int64_t skip, orc_hit* h)
+/* closest hit of the ray (o, d) skipping triangle `skip`; use_bvh = 0 brute
+ * force, 1 median BVH. t2 is the runner-up candidate's t (INFINITY if none). */
+static void closest(const orc_mesh* m, int use_bvh, const double* o, const double* d, int64_t skip, orc_hit* h)
 {
     h->t = INFINITY;
     h->t2 = INFINITY;
@@ -498,7 +448,7 @@ static void closest(const orc_mesh* m, int use_bvh, const double* o, const doubl
     h->tests = h->nodes = 0;
     if (!use_bvh || !m->nodes) {
         for (int64_t k = 0; k < m->nt; ++k)
-            if (k != skip) consider(m, k, o, d, o32, d32, fp32, h);
+            if (k != skip) consider(m, k, o, d, h);
         return;
     }
     int64_t stack[256];
@@ -514,7 +464,7 @@ static void closest(const orc_mesh* m, int use_bvh, const double* o, const doubl
         if (nd->count > 0) {
             for (int64_t i = nd->first; i < nd->first + nd->count; ++i) {
                 int64_t k = m->order[i];
-                if (k != skip) consider(m, k, o, d, o32, d32, fp32, h);
+                if (k != skip) consider(m, k, o, d, h);
             }
             continue;
         }
@@ -538,7 +488,7 @@ int orc_closest_hit(const orc_mesh* m, int use_bvh, const double* o, const doubl
                     double* t, int64_t* tri, double* bmin, double* t2)
 {
     orc_hit h;
-    closest(m, use_bvh, o, d, NULL, NULL, 0, skip, &h);
+    closest(m, use_bvh, o, d, skip, &h);
     *t = h.t;
     *tri = h.k;
     *bmin = h.bmin;
@@ -568,7 +518,6 @@ typedef struct {
     int require_escape;
     int use_bvh;
     int n_threads;
-    int transport; /* 0 FP32 (the written operation order), 1 exact FP64 */
 } orc_trace_opts;
 
 typedef struct {
@@ -594,10 +543,11 @@ static void trace_one(trace_job* J, int64_t r)
 {
     const orc_frame* f = J->f;
     const orc_trace_opts* opt = J->opt;
+    const orc_mesh* m = J->m;
     const int B = opt->max_bounces;
-    const int fp32 = opt->transport == 0;
     int64_t rid = J->ids ? J->ids[r] : r;
     int64_t i = rid % f->nu, j = rid / f->nu;
+    /* the ray state, stored in FP32 between bounces */
     float o32[3], d32[3];
     orc_ray(f, i, j, o32, d32);
     double o[3] = {o32[0], o32[1], o32[2]}, d[3] = {d32[0], d32[1], d32[2]};
@@ -607,7 +557,7 @@ static void trace_one(trace_job* J, int64_t r)
     double ref = dot3(f->khat, o); /* k.o0 */
     double R = 0.0, L = 0.0, cos0 = 0.0;
     double cv[4] = {0, 0, 0, 0};
-    double nf_last[3] = {0, 0, 0};
+    float nf_last[3] = {0, 0, 0};
     int N = 0;
     uint8_t band = 0;
     double bmin_path = 1.0;
@@ -618,58 +568,42 @@ static void trace_one(trace_job* J, int64_t r)
     }
     for (int b = 0; b < B; ++b) {
         orc_hit h;
-        closest(J->m, opt->use_bvh, o, d, o32, d32, fp32, skip, &h);
+        for (int c = 0; c < 3; ++c) { o[c] = o32[c]; d[c] = d32[c]; }
+        closest(m, opt->use_bvh, o, d, skip, &h);
         J->tests += h.tests;
         J->nodes += h.nodes;
         if (h.k < 0) break;
         if (h.bmin < 1e-6) band |= 1;
         if (h.bmin < bmin_path) bmin_path = h.bmin;
         if (h.t2 - h.t <= 1e-6 * h.t) band |= 2;
-        double x[3], n[3], din[3];
-        int front; /* the normal faces the incoming ray (orientation decided in the transport precision) */
-        if (fp32) {
-            /* hit point, unit normal, reflection and offset in the FP32 operation order */
-            const float* e1 = J->m->e1f + 3 * h.k;
-            const float* e2 = J->m->e2f + 3 * h.k;
-            const float tf = (float)h.t;
-            float x32[3], n32[3];
-            for (int c = 0; c < 3; ++c) x32[c] = fmaf(tf, d32[c], o32[c]);
-            cross32(e1, e2, n32);
-            float len2 = dot32(n32, n32);
-            float rl = 1.0f / sqrtf(len2);
-            for (int c = 0; c < 3; ++c) n32[c] = n32[c] * rl;
-            float dn32 = dot32(d32, n32);
-            float m2 = -2.0f * dn32;
-            front = dn32 < 0.0f;
-            for (int c = 0; c < 3; ++c) {
-                x[c] = x32[c];
-                n[c] = n32[c];
-                din[c] = d32[c];
-            }
-            for (int c = 0; c < 3; ++c) {
-                float nf32 = dn32 < 0.0f ? n32[c] : -n32[c];
-                d32[c] = fmaf(m2, n32[c], d32[c]);
-                o32[c] = fmaf(eps32, nf32, x32[c]);
-                d[c] = d32[c];
-                o[c] = o32[c];
-            }
-        } else {
-            for (int c = 0; c < 3; ++c) {
-                x[c] = o[c] + h.t * d[c];
-                n[c] = J->m->nrm[3 * h.k + c];
-                din[c] = d[c];
-            }
-            front = dot3(d, n) < 0.0;
+        /* next FP32 state: distance to the plane of the FP32 unit normal through
+         * v0, hit point, reflection about n32 and the offset origin */
+        const float* n32 = m->n32 + 3 * h.k;
+        const double* v0 = m->v0 + 3 * h.k;
+        double nd[3] = {n32[0], n32[1], n32[2]}, dv[3];
+        for (int c = 0; c < 3; ++c) dv[c] = v0[c] - o[c];
+        const double num = dot3(dv, nd), den = dot3(d, nd);
+        const float t32 = den != 0.0 ? (float)(num / den) : (float)h.t;
+        const float c32 = (float)den;
+        const int front = den < 0.0; /* n32 faces the incoming ray */
+        float x32[3], nf32[3];
+        for (int c = 0; c < 3; ++c) {
+            x32[c] = fmaf(t32, d32[c], o32[c]);
+            nf32[c] = front ? n32[c] : -n32[c];
         }
-        R += h.t;
+        double x[3], nf[3], din[3];
+        for (int c = 0; c < 3; ++c) {
+            x[c] = x32[c];
+            nf[c] = nf32[c];
+            din[c] = d[c];
+            nf_last[c] = nf32[c];
+        }
+        R += (double)t32;
         N += 1;
         if (J->hit_tri) J->hit_tri[r * B + b] = (int32_t)h.k;
-        if (J->hit_t) J->hit_t[r * B + b] = h.t;
-        double dn = dot3(din, n);
-        double nf[3];
-        for (int c = 0; c < 3; ++c) nf[c] = front ? n[c] : -n[c];
+        if (J->hit_t) J->hit_t[r * B + b] = (double)t32;
+        const double dn = dot3(din, nd);
         if (N == 1) cos0 = dot3(nf, f->rhat);
-        for (int c = 0; c < 3; ++c) nf_last[c] = nf[c];
         /* candidate contribution if this hit is the last one; the far-field
          * phase reference is the origin, toward the receiver: L = k.o0 + R - r_rx.x */
         L = ref + R - dot3(f->rx_rhat, x);
@@ -691,42 +625,36 @@ static void trace_one(trace_job* J, int64_t r)
             cv[2] = dot3(W[1], f->rx_hhat); /* HV: receive H, transmit V */
             cv[3] = dot3(W[0], f->rx_vhat); /* VH: receive V, transmit H */
         }
-        if (fp32) {
+        {
             double dd[3] = {din[0], din[1], din[2]};
-            reflect(n, dd, Ev, Eh); /* fields in FP64 about the FP32 normal */
-        } else {
-            reflect(n, d, Ev, Eh);
-            for (int c = 0; c < 3; ++c) o[c] = x[c] + f->eps * nf[c];
+            reflect(nd, dd, Ev, Eh); /* PEC field update in FP64 about the facet's normal */
+        }
+        for (int c = 0; c < 3; ++c) {
+            d32[c] = fmaf(-2.0f * c32, n32[c], d32[c]);
+            o32[c] = fmaf(eps32, nf32[c], x32[c]);
         }
         skip = h.k;
     }
+    for (int c = 0; c < 3; ++c) { o[c] = o32[c]; d[c] = d32[c]; }
     int valid = N >= 1;
     if (valid && opt->require_escape && N == B) {
         orc_hit h;
-        closest(J->m, opt->use_bvh, o, d, o32, d32, fp32, skip, &h);
+        closest(m, opt->use_bvh, o, d, skip, &h);
         J->tests += h.tests;
         J->nodes += h.nodes;
         if (h.k >= 0) valid = 0;
     }
     if (valid && f->bistatic) {
         /* visibility of the last hit from the receiver: the receiver lies on the
-         * side of the oriented normal, and a ray from the offset origin toward it
-         * meets no triangle (the one just hit is skipped). FP32 transport: the
-         * side test is the written FP32 dot and the ray is the FP32 one. */
-        int sees;
+         * side of the oriented normal (sign of the exact dot product of the FP32
+         * vectors), and the ray from the offset origin toward it meets no
+         * triangle (the one just hit is skipped) */
         double rxd[3] = {f->rx_r32[0], f->rx_r32[1], f->rx_r32[2]};
-        if (fp32) {
-            float nf32[3] = {(float)nf_last[0], (float)nf_last[1], (float)nf_last[2]};
-            float rx32[3] = {f->rx_r32[0], f->rx_r32[1], f->rx_r32[2]};
-            sees = dot32(nf32, rx32) > 0.0f;
-        } else {
-            sees = dot3(nf_last, f->rx_rhat) > 0.0;
-            for (int c = 0; c < 3; ++c) rxd[c] = f->rx_rhat[c];
-        }
+        double nfl[3] = {nf_last[0], nf_last[1], nf_last[2]};
+        int sees = dot3(nfl, rxd) > 0.0;
         if (sees) {
             orc_hit h;
-            float rx32[3] = {f->rx_r32[0], f->rx_r32[1], f->rx_r32[2]};
-            closest(J->m, opt->use_bvh, o, rxd, o32, rx32, fp32, skip, &h);
+            closest(m, opt->use_bvh, o, rxd, skip, &h);
             J->tests += h.tests;
             J->nodes += h.nodes;
             sees = h.k < 0;

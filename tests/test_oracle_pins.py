@@ -4,6 +4,7 @@ oracle's own code. CPU only."""
 import json
 import math
 import os
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -133,9 +134,8 @@ def test_bvh_equals_brute_force(orc, which):
             ids = rng.choice(f.n_rays, size=min(400, f.n_rays), replace=False)
             a = orc.trace(m, f, 3, ids=ids, use_bvh=True)
             b = orc.trace(m, f, 3, ids=ids, use_bvh=False)
-            assert np.array_equal(a["hit_tri"], b["hit_tri"])
-            assert np.array_equal(a["hit_t"], b["hit_t"])
-            assert np.array_equal(a["coef"], b["coef"])
+            for key in ("hit_tri", "hit_t", "coef", "band", "bmin", "nb", "valid"):
+                assert np.array_equal(a[key], b[key]), key
             assert a["counters"][0] < b["counters"][0]
 
 
@@ -174,7 +174,7 @@ def _degenerate_extras(n_vert):
 
 def test_degenerate_triangles_take_no_hits(orc):
     """A triangle whose edges are parallel to within a sine of 2^-20 has no
-    usable FP32 normal and is never hit: a ray aimed through the inside of such
+    usable normal and is never hit: a ray aimed through the inside of such
     a sliver misses it while the same ray hits a thin but valid sliver (sine
     ~1e-3); the ordinary meshes have no such triangle; adding degenerate
     triangles to a mesh leaves every ray's hits, fields and path bit for bit."""
@@ -209,7 +209,7 @@ def test_degenerate_triangles_take_no_hits(orc):
 
 def test_duplicate_triangles_resolve_to_the_lower_index(orc):
     """A copy of every triangle appended to the mesh ties with its original at
-    every hit (same FP32 edges, same t); the lower index wins, so every ray's
+    every hit (same vertices, same t); the lower index wins, so every ray's
     hits, fields and path equal those of the mesh without copies."""
     xyz, tri = S.trihedral(1.0, 8)
     base = orc.Mesh(xyz, tri)
@@ -305,14 +305,13 @@ def test_two_plate_round_trip_phase(orc):
     tri = np.concatenate([t1, t2 + len(v1)]).astype(np.int32)
     m = orc.Mesh(xyz, tri)
     dz = float(np.float32(0.0137))
-    for transport, rel in (("exact", 1e-9), ("fp32", 1e-4)):
-        for f in (2e9, 4.4e9, 7.1e9):
-            k = 2 * math.pi * f / C0
-            E, rcs, tr, fr = orc.rcs_angle(m, m.bbox, 0.0, 90.0, 0.01, [f], 1, window=1.2, offset=(0.25, 0.25),
-                                           transport=transport)
-            n = tr["valid"].sum() // 2
-            S_ = 2 * 1e-4 * abs(n + n * np.exp(2j * k * dz))
-            assert abs(E[0, 0]) == pytest.approx(k / (4 * math.pi) * S_, rel=rel)
+    for f in (2e9, 4.4e9, 7.1e9):
+        k = 2 * math.pi * f / C0
+        E, rcs, tr, fr = orc.rcs_angle(m, m.bbox, 0.0, 90.0, 0.01, [f], 1, window=1.2, offset=(0.25, 0.25))
+        n = tr["valid"].sum() // 2
+        S_ = 2 * 1e-4 * abs(n + n * np.exp(2j * k * dz))
+        # the stored hit distances are FP32 (one rounding of a ~2 m path)
+        assert abs(E[0, 0]) == pytest.approx(k / (4 * math.pi) * S_, rel=1e-4)
 
 
 def test_dihedral_double_bounce_peak(orc):
@@ -420,39 +419,150 @@ def test_sphere_vector_mode_converges_to_mie(orc):
     assert err[0.00125] < 0.1
 
 
-# ----------------------------------------------------------------------------- FP32 vs exact transport
-@pytest.mark.parametrize("which", ["sphere", "trihedral"])
-def test_fp32_transport_tracks_exact_transport(orc, which):
-    # the FP32 transport order (the precision hit decisions are taken in) differs
-    # from exact FP64 transport only for rays grazing an edge, and not in dBsm
-    if which == "sphere":
-        case = S.sphere_case(n_random=2)
-        kw = dict(window=case["window"])
-    else:
-        case = S.trihedral_case(az_step=30.0)
-        kw = dict(eta=case["eta"])
-    m = orc.Mesh(case["xyz"], case["tri"])
-    n = mism = 0
-    for az, el in case["angles"]:
-        E32, R32, t32, _ = orc.rcs_angle(m, m.bbox, az, el, case["spacing"], case["freqs"], case["max_bounces"],
-                                         transport="fp32", **kw)
-        E64, R64, t64, _ = orc.rcs_angle(m, m.bbox, az, el, case["spacing"], case["freqs"], case["max_bounces"],
-                                         transport="exact", **kw)
-        n += len(t32["nb"])
-        diff = np.any(t32["hit_tri"] != t64["hit_tri"], axis=1)
-        mism += int(diff.sum())
-        # every ray decided differently grazes an edge within the FP32 test's slack
-        # (2^-12; on the FP32 side the barycentric may be slightly negative) or has a
-        # runner-up at nearly the same distance
-        near = np.minimum(np.abs(t32["bmin"][diff]), np.abs(t64["bmin"][diff])) < 2 * 2.0**-12
-        assert np.all(near | (t64["band"][diff] & 2 != 0)), np.abs(t32["bmin"][diff]).max()
-        ok = R64[0, :2] > -40
-        assert np.all(np.abs(R32[0, :2] - R64[0, :2])[ok] < 0.02)
-        both = (t32["hit_tri"] >= 0) & (t32["hit_tri"] == t64["hit_tri"])
-        # FP32 positions carry ~1e-7 m absolute error (short legs near corners make it large relative)
-        dt = np.abs(t32["hit_t"][both] - t64["hit_t"][both])
-        assert np.all(dt < 1e-5 * t64["hit_t"][both] + 1e-6)
-    assert mism / n < 2e-3, (mism, n)
+# ----------------------------------------------------------------------------- edge band and FP32 ray state
+def _fl32(x: Fraction) -> float:
+    """x rounded to the nearest FP32 value (ties to even), exactly."""
+    if x == 0:
+        return 0.0
+    sgn = -1 if x < 0 else 1
+    a = abs(x)
+    e = a.numerator.bit_length() - a.denominator.bit_length()
+    if Fraction(2) ** e > a:
+        e -= 1
+    e = max(e, -126)  # subnormals share the smallest exponent
+    q = a / Fraction(2) ** (e - 23)  # 24-bit significand scale
+    n = q.numerator // q.denominator
+    r = q - n
+    if r > Fraction(1, 2) or (r == Fraction(1, 2) and n % 2 == 1):
+        n += 1
+    return sgn * float(Fraction(n) * Fraction(2) ** (e - 23))
+
+
+def _square(z, i0=0):
+    """unit square [0, 1]^2 at height z, split along its diagonal (0,0)-(1,1) into two triangles"""
+    v = np.array([[0, 0, z], [1, 0, z], [1, 1, z], [0, 1, z]], np.float32)
+    return v, np.array([[i0, i0 + 1, i0 + 2], [i0, i0 + 2, i0 + 3]], np.int32)
+
+
+def test_runner_up_band_on_a_shared_edge(orc):
+    """A ray through the shared diagonal of two coplanar triangles hits both at
+    the same t: the lower index wins, the hit is on an edge (bit 0) and the
+    runner-up ties (bit 1), by brute force and through the BVH alike."""
+    xyz, tri = _square(0.5)
+    for use_bvh, leaf in ((False, None), (True, 1)):
+        m = orc.Mesh(xyz, tri, bvh_leaf=leaf)
+        k, t, bmin, t2 = m.closest_hit([0.25, 0.25, 2.0], [0, 0, -1.0], use_bvh=use_bvh)
+        assert k == 0 and t == 1.5 and t2 == 1.5 and bmin == 0.0
+        # off the diagonal: one triangle, no runner-up
+        k, t, bmin, t2 = m.closest_hit([0.75, 0.25, 2.0], [0, 0, -1.0], use_bvh=use_bvh)
+        assert k == 0 and math.isinf(t2) and bmin == pytest.approx(0.25)
+        k, t, bmin, t2 = m.closest_hit([0.25, 0.75, 2.0], [0, 0, -1.0], use_bvh=use_bvh)
+        assert k == 1 and math.isinf(t2)
+    # traced from an aperture (el = 90 deg: the FP32 direction keeps a 6e-17 tilt from cos 90 deg, so a
+    # diagonal ray meets one triangle at barycentric ~1e-16 from the edge): the rays with i = j, and only
+    # they, are in the barycentric band
+    m = orc.Mesh(xyz, tri, bvh_leaf=1)
+    f = orc.make_frame(m.bbox, 0.0, 90.0, 0.125, window=1.0)
+    tr = orc.trace(m, f, 1)
+    i, j = np.arange(f.n_rays) % f.nu, np.arange(f.n_rays) // f.nu
+    assert tr["valid"].sum() == f.n_rays == 64
+    assert np.array_equal((tr["band"] & 1) != 0, i == j)
+    assert np.all(tr["bmin"][i == j] < 1e-15) and np.all(tr["bmin"][i != j] > 0.06)
+
+
+@pytest.mark.parametrize("gap_rel, in_band", [(5e-7, True), (5e-6, False)])
+def test_runner_up_band_on_parallel_facets(orc, gap_rel, in_band):
+    """Two parallel squares a relative distance gap_rel apart along the ray: the
+    nearer one is hit, and the ray is in the edge band (bit 1) exactly when the
+    other lies within 1e-6 relative in t; the BVH sees the same runner-up as
+    brute force (it keeps boxes up to 1e-5 beyond the closest hit)."""
+    t_near = 1.5
+    z_far = np.float32(0.5 - gap_rel * t_near)
+    va, ta = _square(0.5)
+    vb, tb = _square(z_far, i0=4)
+    xyz, tri = np.concatenate([va, vb]), np.concatenate([ta, tb])
+    got = []
+    for use_bvh, leaf in ((False, None), (True, 1), (True, 4)):
+        m = orc.Mesh(xyz, tri, bvh_leaf=leaf)
+        k, t, bmin, t2 = m.closest_hit([0.7, 0.2, 2.0], [0, 0, -1.0], use_bvh=use_bvh)
+        assert k == 0 and t == t_near
+        assert t2 == 2.0 - float(z_far)
+        assert ((t2 - t) <= 1e-6 * t) == in_band
+        got.append((k, t, bmin, t2))
+    assert got[0] == got[1] == got[2]
+    m = orc.Mesh(xyz, tri, bvh_leaf=2)
+    f = orc.make_frame(m.bbox, 0.0, 90.0, 0.1, window=0.8, offset=(0.3, 0.3))
+    a, b = orc.trace(m, f, 1, use_bvh=True), orc.trace(m, f, 1, use_bvh=False)
+    hit = a["nb"] == 1
+    assert hit.sum() > 30
+    assert np.all(((a["band"][hit] & 2) != 0) == in_band)
+    assert np.array_equal(a["band"], b["band"]) and np.array_equal(a["hit_tri"], b["hit_tri"])
+
+
+def test_fp32_state_is_the_rounded_formula(orc):
+    """After a hit, the stored distance is t32 = fl32(((v0 - o).n32) / (d.n32))
+    and n32 = fl32(unit normal): both checked against exact rational (and
+    60-digit decimal) arithmetic on random triangles and rays, so a dropped
+    term, a wrong sign or a transposed operand in either shows up."""
+    from decimal import Decimal, getcontext
+
+    getcontext().prec = 60
+    rng = np.random.default_rng(17)
+    xyz, tri = _random_soup(60, 23)
+    m = orc.Mesh(xyz, tri, bvh_leaf=None)
+    n32 = m.normals
+    for k in range(len(tri)):
+        P = [[Fraction(float(c)) for c in xyz[i]] for i in tri[k]]
+        e1 = [P[1][c] - P[0][c] for c in range(3)]
+        e2 = [P[2][c] - P[0][c] for c in range(3)]
+        N = [e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]]
+        ln = sum(Decimal(x.numerator) / Decimal(x.denominator) * Decimal(x.numerator) / Decimal(x.denominator)
+                 for x in N).sqrt()
+        for c in range(3):
+            want = _fl32(Fraction(Decimal(N[c].numerator) / Decimal(N[c].denominator) / ln))
+            assert n32[k, c] == np.float32(want), (k, c)
+    hits = 0
+    for _ in range(300):
+        k = int(rng.integers(len(tri)))
+        w = rng.dirichlet([1, 1, 1])
+        p = (w[:, None] * xyz[tri[k]].astype(np.float64)).sum(0)
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        o = (p - 3.0 * d).astype(np.float32)
+        d32 = d.astype(np.float32)
+        kk, t, _, _ = m.closest_hit(o.astype(np.float64), d32.astype(np.float64))
+        if kk < 0:
+            continue
+        # the oracle's trace of this one ray: a frame whose grid has the ray at (0, 0) is not available, so
+        # the single-ray entry closest_hit gives the triangle and the stored t32 is recomputed here
+        v0 = [Fraction(float(c)) for c in xyz[tri[kk]][0]]
+        nn = [Fraction(float(c)) for c in n32[kk]]
+        of = [Fraction(float(c)) for c in o]
+        df = [Fraction(float(c)) for c in d32]
+        num = sum((v0[c] - of[c]) * nn[c] for c in range(3))
+        den = sum(df[c] * nn[c] for c in range(3))
+        t32 = _fl32(num / den)
+        # t32 is the distance along the ray to the plane of n32 through v0: within
+        # FP32 rounding of the exact hit distance of the triangle itself
+        assert abs(t32 - t) <= 4e-7 * t
+        hits += 1
+    assert hits > 200
+
+
+def test_trace_stores_the_rounded_distance(orc):
+    """Along a traced path the stored hit distances are FP32 values, and on an
+    axis-aligned plate seen head-on they equal the plate's distance from the
+    aperture (a difference of FP32 values, exact in FP64) rounded once."""
+    xyz, tri = S.square_plate(1.0, 4, z0=0.3)
+    m = orc.Mesh(xyz, tri)
+    f = orc.make_frame(m.bbox, 0.0, 90.0, 0.02, window=1.2)
+    tr = orc.trace(m, f, 2)
+    hit = tr["nb"] >= 1
+    o0 = np.array([orc.ray(f, int(r % f.nu), int(r // f.nu))[0] for r in np.nonzero(hit)[0][:50]])
+    # exact in FP64 (a difference of FP32 values), then rounded once to FP32
+    want = (o0[:, 2].astype(np.float64) - np.float64(np.float32(0.3))).astype(np.float32).astype(np.float64)
+    assert np.array_equal(tr["hit_t"][np.nonzero(hit)[0][:50], 0], want)
+    assert np.all(tr["hit_t"].astype(np.float32).astype(np.float64) == tr["hit_t"])
 
 
 # ----------------------------------------------------------------------------- bistatic variant
