@@ -112,6 +112,9 @@ typedef struct {
                                 field update and candidate coefficients each) */
     int64_t listed_hits;     /* only with SBR_TRACE_COUNT_VISITS: rasterised primary hits whose state bounce pass 1
                                 rebuilt from the hit list (their per-hit arithmetic runs there) */
+    int64_t open_tests;      /* only with SBR_TRACE_COUNT_VISITS: triangle tests whose FP32 filter left the decision
+                                open (taken again near the triangle, then in FP64 if still open) */
+    int64_t fp64_tests;      /* only with SBR_TRACE_COUNT_VISITS: of those, the tests decided in FP64 */
 } sbr_trace_stats;
 
 /* Per-aspect ray grid (Eq. L1-L3) exactly as sbr_trace generates it. */

@@ -454,7 +454,8 @@ int sbr_build_bvh(sbr_ctx* c, const sbr_bvh_opts* opt)
     const long long n_nodes = n > 1 ? n - 1 : 1;
     c->n_nodes = n_nodes;
     CK(c->nodes.ensure(sizeof(float4) * 4 * (size_t)n_nodes), "alloc nodes");
-    CK(c->tris.ensure(sizeof(float4) * 3 * (size_t)n), "alloc tris");
+    // records (3 float4), normals (1) and exact v1, v2 (2) per triangle
+    CK(c->tris.ensure(sizeof(float4) * 6 * (size_t)n), "alloc tris");
     CK(c->tripos.ensure(sizeof(int) * (size_t)n), "alloc triangle positions");
     size_t sb = bvh_scratch_bytes(n);
     CK(c->bvh_scratch.ensure(sb), "alloc bvh scratch");
@@ -472,6 +473,8 @@ int sbr_build_bvh(sbr_ctx* c, const sbr_bvh_opts* opt)
     b.radius = radius;
     b.nodes = c->nodes.as<float4>();
     b.tris = c->tris.as<float4>();
+    b.tri_nrm = c->tris.as<float4>() + 3 * (size_t)n;
+    b.tri_v12 = c->tris.as<float4>() + 4 * (size_t)n;
     b.tri_pos = c->tripos.as<int>();
     b.bbox_out = c->bbox_dev.as<float>();
     b.err_flag = c->err_dev.as<int>();
@@ -707,6 +710,8 @@ int trace_chunk(sbr_ctx* c, TraceRun& R, int64_t a0, int64_t a1, long long rec_b
     if (ta.octant) CK(ensure_octant_nodes(c, c->stream), "octant nodes");
     ta.nodes = ta.wide ? c->nodes4.as<float4>() : (ta.octant ? c->nodes_oct.as<float4>() : c->nodes.as<float4>());
     ta.tris = c->tris.as<float4>();
+    ta.tri_nrm = ta.tris + 3 * (size_t)c->n_tri;
+    ta.tri_v12 = ta.tris + 4 * (size_t)c->n_tri;
     ta.angles = c->angles.as<AngleDev>();
     ta.ray_off = c->rayoff.as<long long>();
     ta.n_angles = na;
@@ -817,6 +822,8 @@ int finish_stats(sbr_ctx* c, const TraceRun& R, const unsigned long long* hs_sta
         stats->raster_tests = (int64_t)hs_stats[kStatRaster];
         stats->bounce_hits = (int64_t)hs_stats[kStatHits];
         stats->listed_hits = (int64_t)hs_stats[kStatListed];
+        stats->open_tests = (int64_t)hs_stats[kStatOpen];
+        stats->fp64_tests = (int64_t)hs_stats[kStatFp64];
         stats->pass_ms = 0.0;
         stats->primary_ms = 0.0;
         for (size_t i = 0; R.timed && i + 1 < R.n_ev; i += 2) {
@@ -1013,6 +1020,8 @@ cudaError_t enqueue_plan(const sbr_ctx* c, BatchPlan& P, cudaStream_t st)
         ta.n_nodes = c->n_nodes;
         ta.nodes = ta.wide ? c->nodes4.as<float4>() : (ta.octant ? c->nodes_oct.as<float4>() : c->nodes.as<float4>());
         ta.tris = c->tris.as<float4>();
+        ta.tri_nrm = ta.tris + 3 * (size_t)c->n_tri;
+        ta.tri_v12 = ta.tris + 4 * (size_t)c->n_tri;
         ta.angles = P.angles.as<AngleDev>() + a0;
         ta.ray_off = P.rayoff.as<long long>() + a0 + (int64_t)k;  // chunk k's table has na + 1 entries
         ta.n_angles = na;
@@ -1532,6 +1541,8 @@ int sbr_sync(sbr_ctx* c, sbr_trace_stats* stats)
         stats->raster_tests = (int64_t)hs[kStatRaster];
         stats->bounce_hits = (int64_t)hs[kStatHits];
         stats->listed_hits = (int64_t)hs[kStatListed];
+        stats->open_tests = (int64_t)hs[kStatOpen];
+        stats->fp64_tests = (int64_t)hs[kStatFp64];
         stats->stack_overflows = (int64_t)hs[kStatOverflow];
         stats->kernel_launches = P.n_launch;
         stats->pass_launches = P.n_pass;

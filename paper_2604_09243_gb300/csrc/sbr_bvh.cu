@@ -104,9 +104,9 @@ __global__ void __launch_bounds__(kThreads) k_prep(const float* xyz, const int* 
             a = b = c = make_float3(0.f, 0.f, 0.f);
         float3 bl = make_float3(fminf(a.x, fminf(b.x, c.x)), fminf(a.y, fminf(b.y, c.y)), fminf(a.z, fminf(b.z, c.z)));
         float3 bh = make_float3(fmaxf(a.x, fmaxf(b.x, c.x)), fmaxf(a.y, fmaxf(b.y, c.y)), fmaxf(a.z, fmaxf(b.z, c.z)));
-        // the FP32 triangle test accepts hits up to its slack (2^-12 of the
-        // triangle) plus a few rounding units outside the exact triangle: widen
-        // the leaf box so the culling stays conservative
+        // widen the leaf box well beyond the FP32 slab test's rounding (a few
+        // units of the coordinates' magnitude) so that no box of a triangle the
+        // exact test accepts is culled
         const float ext = fmaxf(bh.x - bl.x, fmaxf(bh.y - bl.y, bh.z - bl.z));
         const float mag = fmaxf(fmaxf(fmaxf(fabsf(bl.x), fabsf(bh.x)), fmaxf(fabsf(bl.y), fabsf(bh.y))),
                                 fmaxf(fabsf(bl.z), fabsf(bh.z)));
@@ -367,8 +367,25 @@ __global__ void __launch_bounds__(kThreads) k_emit(int n, const int* left, const
     put_node(nodes, i, bl[0], bh[0], bl[1], bh[1], ref[0], ref[1]);
 }
 
+// FP64 vectors of the per-triangle preprocessing, each operation one IEEE
+// rounding (no contraction): the unit normal and the degeneracy test below are
+// the same FP64 evaluations as the oracle's, so both keep the same FP32 normal.
+struct D3 {
+    double x, y, z;
+};
+__device__ __forceinline__ D3 dcross(D3 a, D3 b)
+{
+    return {__dsub_rn(__dmul_rn(a.y, b.z), __dmul_rn(a.z, b.y)), __dsub_rn(__dmul_rn(a.z, b.x), __dmul_rn(a.x, b.z)),
+            __dsub_rn(__dmul_rn(a.x, b.y), __dmul_rn(a.y, b.x))};
+}
+__device__ __forceinline__ double ddot(D3 a, D3 b)
+{
+    return __dadd_rn(__dadd_rn(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y)), __dmul_rn(a.z, b.z));
+}
+
 __global__ void __launch_bounds__(kThreads) k_reorder(const float* xyz, const int* tri, long long nv,
-                                                      const unsigned* vals, int n, float4* tris, int* pos)
+                                                      const unsigned* vals, int n, float4* tris, float4* nrm,
+                                                      float4* v12, int* pos)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
@@ -380,23 +397,34 @@ __global__ void __launch_bounds__(kThreads) k_reorder(const float* xyz, const in
     float cx = xyz[3 * (long long)ic], cy = xyz[3 * (long long)ic + 1], cz = xyz[3 * (long long)ic + 2];
     float4 e1 = make_float4(__fsub_rn(bx, ax), __fsub_rn(by, ay), __fsub_rn(bz, az), 0.f);
     float4 e2 = make_float4(__fsub_rn(cx, ax), __fsub_rn(cy, ay), __fsub_rn(cz, az), 0.f);
-    // Degenerate triangle: |e1 x e2|^2 <= (2^-20 |e1|^2)(2^-20 |e2|^2), i.e. the
-    // sine of the angle between its edges is at most 2^-20, where the FP32
-    // rounding of e1 x e2 (about 2^-24 |e1||e2|) exceeds 6 % of its length and
-    // the normal is mostly noise (repeated or collinear vertices give 0). It
-    // takes no hits: zero edges make the determinant of every test exactly 0.
-    // Written FP32 order of the hit normal: cross = fma(a.y, b.z, -(a.z b.y))
-    // and cyclic, dot = fma(a.x, b.x, fma(a.y, b.y, a.z b.z)).
-    const float nx = __fmaf_rn(e1.y, e2.z, -__fmul_rn(e1.z, e2.y));
-    const float ny = __fmaf_rn(e1.z, e2.x, -__fmul_rn(e1.x, e2.z));
-    const float nz = __fmaf_rn(e1.x, e2.y, -__fmul_rn(e1.y, e2.x));
-    const float nn = __fmaf_rn(nx, nx, __fmaf_rn(ny, ny, __fmul_rn(nz, nz)));
-    const float l1 = __fmaf_rn(e1.x, e1.x, __fmaf_rn(e1.y, e1.y, __fmul_rn(e1.z, e1.z)));
-    const float l2 = __fmaf_rn(e2.x, e2.x, __fmaf_rn(e2.y, e2.y, __fmul_rn(e2.z, e2.z)));
-    if (nn <= __fmul_rn(__fmul_rn(l1, 0x1p-20f), __fmul_rn(l2, 0x1p-20f))) e1 = e2 = make_float4(0.f, 0.f, 0.f, 0.f);
+    // Exact edges (differences of FP32 values) and the normal N = E1 x E2 in FP64.
+    // Degenerate triangle: |N|^2 <= (2^-20 |E1|^2)(2^-20 |E2|^2), i.e. the sine of
+    // the angle between its edges is at most 2^-20 (repeated or collinear vertices
+    // give 0): it has no usable normal and takes no hits. Its edges and filter
+    // constants are zeroed, which makes the test reject every ray.
+    const D3 E1 = {__dsub_rn(bx, ax), __dsub_rn(by, ay), __dsub_rn(bz, az)};
+    const D3 E2 = {__dsub_rn(cx, ax), __dsub_rn(cy, ay), __dsub_rn(cz, az)};
+    const D3 N = dcross(E1, E2);
+    const double nn = ddot(N, N), l1 = ddot(E1, E1), l2 = ddot(E2, E2);
+    const bool deg = nn <= __dmul_rn(__dmul_rn(l1, 0x1p-20), __dmul_rn(l2, 0x1p-20));
+    float4 n32 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (deg) {
+        e1 = e2 = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+        const double ln = __dsqrt_rn(nn);
+        n32 = make_float4(__double2float_rn(__ddiv_rn(N.x, ln)), __double2float_rn(__ddiv_rn(N.y, ln)),
+                          __double2float_rn(__ddiv_rn(N.z, ln)), 0.f);
+        // filter constants of the FP32 test's forward error bounds (u = 2^-24)
+        const float L = fmaxf(fabsf(e1.x) + fabsf(e1.y) + fabsf(e1.z), fabsf(e2.x) + fabsf(e2.y) + fabsf(e2.z));
+        e1.w = (24.f * 0x1p-24f * 1.0009765625f) * L;
+        e2.w = (14.f * 0x1p-24f * 1.0009765625f) * L * L;
+    }
     tris[3 * p + 0] = make_float4(ax, ay, az, __int_as_float((int)t));
     tris[3 * p + 1] = e1;
     tris[3 * p + 2] = e2;
+    nrm[p] = n32;
+    v12[2 * p] = make_float4(bx, by, bz, 0.f);
+    v12[2 * p + 1] = make_float4(cx, cy, cz, 0.f);
     if (pos) pos[t] = p;
 }
 
@@ -1056,7 +1084,7 @@ cudaError_t bvh_build(const BvhBuild& b, cudaStream_t st)
         k_build_small<<<1, kSmallThreads, 12 * (size_t)n, st>>>(sb);
         k_ploc_emit<<<(n - 1 + kThreads - 1) / kThreads, kThreads, 0, st>>>(n, left, right, nbox, ncnt, ncol, noff,
                                                                             tbox, b.nodes);
-        k_reorder<<<g, kThreads, 0, st>>>(b.xyz, b.tri, b.n_vert, perm, n, b.tris, b.tri_pos);
+        k_reorder<<<g, kThreads, 0, st>>>(b.xyz, b.tri, b.n_vert, perm, n, b.tris, b.tri_nrm, b.tri_v12, b.tri_pos);
         return cudaGetLastError();
     }
     unsigned long long *ki = k0, *ko = k1;
@@ -1110,7 +1138,7 @@ cudaError_t bvh_build(const BvhBuild& b, cudaStream_t st)
         k_ploc_positions<<<gx, kThreads, 0, st>>>(n, rel[pj], noff, perm);
         k_ploc_emit<<<(n - 1 + kThreads - 1) / kThreads, kThreads, 0, st>>>(n, left, right, nbox, ncnt, ncol, noff,
                                                                             tbox, b.nodes);
-        k_reorder<<<g, kThreads, 0, st>>>(b.xyz, b.tri, b.n_vert, perm, n, b.tris, b.tri_pos);
+        k_reorder<<<g, kThreads, 0, st>>>(b.xyz, b.tri, b.n_vert, perm, n, b.tris, b.tri_nrm, b.tri_v12, b.tri_pos);
         return cudaGetLastError();
     }
     if (n > 1) {
@@ -1122,7 +1150,7 @@ cudaError_t bvh_build(const BvhBuild& b, cudaStream_t st)
                                     b.leaf_max, b.c_t, b.c_i);
     int ge = n > 1 ? (n - 1 + kThreads - 1) / kThreads : 1;
     k_emit<<<ge, kThreads, 0, st>>>(n, left, right, first, lbox, nbox, ncnt, ncol, b.nodes);
-    k_reorder<<<g, kThreads, 0, st>>>(b.xyz, b.tri, b.n_vert, vi, n, b.tris, b.tri_pos);
+    k_reorder<<<g, kThreads, 0, st>>>(b.xyz, b.tri, b.n_vert, vi, n, b.tris, b.tri_nrm, b.tri_v12, b.tri_pos);
     return cudaGetLastError();
 }
 

@@ -29,8 +29,15 @@ __host__ __device__ inline int leaf_ref(int first, int count)
 __host__ __device__ inline int leaf_first(int ref) { return (int)(((unsigned)ref & 0x7FFFFFFFu) >> 4); }
 __host__ __device__ inline int leaf_count(int ref) { return (int)((unsigned)ref & 15u) + 1; }
 
-// A triangle is 3 float4 (48 bytes): (v0, original index as int bits), (e1, 0),
-// (e2, 0) with e1 = v1 - v0, e2 = v2 - v0 rounded to FP32.
+// A triangle is 3 float4 (48 bytes): (v0, original index as int bits), (e1, bUV),
+// (e2, bD) with e1 = v1 - v0, e2 = v2 - v0 rounded to FP32 and the constants of
+// the FP32 filter's error bounds, u = 2^-24 and L = max(|e1|_1, |e2|_1):
+//   bUV = 24 u L (1 + 2^-10),  bD = 14 u L^2 (1 + 2^-10)
+// (all zero for a degenerate triangle: it takes no hits). Beside the records,
+// at the same position: tri_nrm = (n32, 0), the FP32 rounding of the FP64 unit
+// normal, read for the hit point, the reflection and the hit distance; and
+// tri_v12 = (v1, 0), (v2, 0), the exact vertices, read only when the filter
+// leaves a decision open and it is taken again in FP64.
 
 // ---------------------------------------------------------------- per-aspect data
 struct AngleDev {            // 192 bytes
@@ -72,7 +79,7 @@ static_assert(sizeof(Record) == 32, "Record layout");
 
 // stats counters on the device (unsigned long long each)
 enum { kStatQueries = 0, kStatNodes = 1, kStatTris = 2, kStatOverflow = 3, kStatRaster = 4, kStatHits = 5, kStatListed = 6,
-       kStatCount = 7 };
+       kStatOpen = 7, kStatFp64 = 8, kStatCount = 9 };
 
 // ---------------------------------------------------------------- launchers
 // All launchers enqueue on `st` and return the launch error (cudaSuccess if none).
@@ -115,6 +122,8 @@ struct BvhBuild {
     // outputs (allocated by the caller: nodes [max(n_tri-1,1)*4] float4, tris [n_tri*3] float4)
     float4* nodes;
     float4* tris;
+    float4* tri_nrm;  // [n_tri] (n32, 0) per reordered triangle
+    float4* tri_v12;  // [2 n_tri] (v1, 0), (v2, 0) per reordered triangle
     int* tri_pos;     // [n_tri]: position in tris of each original triangle index
     float* bbox_out;  // device float[6] scene box of the vertices
     int* err_flag;    // device int: bit 1 a triangle index out of range, bit 2 a non-finite coordinate,
@@ -134,6 +143,8 @@ struct TraceArgs {
     int octant;                   // 1: nodes are the octant copies of the binary nodes (n_nodes per copy)
     long long n_nodes;
     const float4* tris;
+    const float4* tri_nrm;        // [n_tri] FP32 unit normals (reordered like tris)
+    const float4* tri_v12;        // [2 n_tri] exact v1, v2 (reordered like tris)
     const AngleDev* angles;
     const long long* ray_off;     // [n_angles + 1] chunk-relative, multiples of 32
     int n_angles;

