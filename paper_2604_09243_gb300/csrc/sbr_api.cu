@@ -96,6 +96,8 @@ struct sbr_ctx {
     DevBuf angles, rayoff, mask, tilebase, scan_scr, recoff, q0, q1, ctr64, ctr32, stats, rec, cover;
     DevBuf hit_tri, hit_t, hit_nb;
     DevBuf tripos, vis, visfull;  // position of each original triangle; raster keys and per-aspect flags
+    DevBuf rbig, rbigctr;         // large triangles of a rasterised chunk and their two counters
+    long long rbig_cap = 0;
     DevBuf hitlist;               // (ray, aspect) of the rasterised primary hits, read by bounce pass 1
     long long rec_total = 0;
     int max_bounces = 0, trace_flags = 0;
@@ -285,6 +287,13 @@ AngleDev to_dev(const sbr_ray_grid& g, long long ray_off, int tw, const double* 
 }
 
 // rays an aspect occupies in the processing layout: whole tiles of 2^tw x 32 / 2^tw
+// entries of the rasterisation's list of large triangles for a chunk of `rays` primary rays (an aspect whose
+// large triangles do not fit traverses instead)
+long long raster_big_cap(long long rays)
+{
+    return std::min<long long>(std::max<long long>(1ll << 16, rays / 4), 1ll << 30);
+}
+
 long long tiled_rays(const sbr_ray_grid& g, int tw)
 {
     const long long th = 32 >> tw;
@@ -389,7 +398,7 @@ void sbr_destroy(sbr_ctx* c)
     cudaStreamSynchronize(c->stream);
     DevBuf* all[] = {&c->xyz, &c->tri, &c->nodes, &c->tris, &c->bvh_scratch, &c->bbox_dev, &c->err_dev, &c->nodes4,
                      &c->angles, &c->rayoff, &c->mask, &c->tilebase, &c->scan_scr, &c->recoff, &c->q0, &c->q1, &c->cover,
-                     &c->nodes_oct, &c->tripos, &c->vis, &c->visfull, &c->hitlist,
+                     &c->nodes_oct, &c->tripos, &c->vis, &c->visfull, &c->hitlist, &c->rbig, &c->rbigctr,
                      &c->ctr64, &c->ctr32, &c->stats, &c->rec, &c->hit_tri, &c->hit_t, &c->hit_nb, &c->items,
                      &c->itemoff, &c->recbeg, &c->freq, &c->kfreq, &c->partial, &c->E, &c->rcs};
     for (DevBuf* b : all) b->release();
@@ -586,6 +595,9 @@ int plan_chunks(sbr_ctx* c, TraceRun& R, std::vector<int64_t>& cut, long long* t
         CK(c->vis.ensure(sizeof(unsigned long long) * (size_t)max_chunk), "alloc raster keys");
         CK(c->visfull.ensure(sizeof(unsigned) * (size_t)(max_angles + 1)), "alloc raster flags");
         CK(c->hitlist.ensure(sizeof(uint2) * (size_t)max_chunk), "alloc raster hit list");
+        c->rbig_cap = raster_big_cap(max_chunk);
+        CK(c->rbig.ensure(sizeof(int4) * (size_t)c->rbig_cap), "alloc raster triangle list");
+        CK(c->rbigctr.ensure(sizeof(unsigned) * 2), "alloc raster triangle counters");
     }
     CK(c->tilebase.ensure(sizeof(unsigned) * (size_t)max_tiles), "alloc tile base");
     CK(c->scan_scr.ensure(scan_scratch_bytes(max_tiles)), "alloc scan scratch");
@@ -731,6 +743,9 @@ int trace_chunk(sbr_ctx* c, TraceRun& R, int64_t a0, int64_t a1, long long rec_b
     if (c->tune.raster) {  // primary hits by rasterisation (the silhouette mask is then not needed)
         ta.vis = c->vis.as<unsigned long long>();
         ta.vis_full = c->visfull.as<unsigned>();
+        ta.big = c->rbig.as<int4>();
+        ta.big_ctr = c->rbigctr.as<unsigned>();
+        ta.big_cap = (unsigned)c->rbig_cap;
         ta.tri_pos = c->tripos.as<int>();
         ta.list_count = total_dev + 4;
         // a bounce pass follows: list the hits and let it rebuild their states (not for B = 1, whose
@@ -960,10 +975,11 @@ struct BatchPlan {
     long long launched = 0;
     int64_t n_launch = 0, n_pass = 0;
     bool count = false;
+    unsigned big_cap = 0;  // entries of rbig
     PoArgs pa;
     // device buffers
     DevBuf angles, rayoff, pang, recoff, mask, tilebase, scan_scr, q0, q1, ctr64, ctr32, stats, rec, items, nitems,
-        valid, freq_t, kfreq, partial, cover, vis, visfull, hitlist;
+        valid, freq_t, kfreq, partial, cover, vis, visfull, hitlist, rbig, rbigctr;
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -978,7 +994,7 @@ void free_plan(BatchPlan* p)
     DevBuf* all[] = {&p->angles, &p->rayoff, &p->pang,   &p->recoff, &p->mask,   &p->tilebase, &p->scan_scr,
                      &p->q0,     &p->q1,     &p->ctr64,  &p->ctr32,  &p->stats,  &p->rec,      &p->items,
                      &p->nitems, &p->valid,  &p->freq_t, &p->kfreq,  &p->partial, &p->cover,
-                     &p->vis,    &p->visfull, &p->hitlist};
+                     &p->vis,    &p->visfull, &p->hitlist, &p->rbig, &p->rbigctr};
     for (DevBuf* b : all) b->release();
     delete p;
 }
@@ -1039,6 +1055,9 @@ cudaError_t enqueue_plan(const sbr_ctx* c, BatchPlan& P, cudaStream_t st)
         if (P.tune.raster) {
             ta.vis = P.vis.as<unsigned long long>();
             ta.vis_full = P.visfull.as<unsigned>();
+            ta.big = P.rbig.as<int4>();
+            ta.big_ctr = P.rbigctr.as<unsigned>();
+            ta.big_cap = P.big_cap;
             ta.tri_pos = c->tripos.as<int>();
             ta.list_count = total_dev + 4;
             if (!ta.bistatic && !ta.wide && !ta.packet && (P.max_bounces >= 2 || escape))
@@ -1164,6 +1183,9 @@ int build_plan(sbr_ctx* c, BatchPlan& P)
         CK(P.vis.ensure(sizeof(unsigned long long) * (size_t)max_rays), "alloc raster keys");
         CK(P.visfull.ensure(sizeof(unsigned) * (size_t)(max_angles + 1)), "alloc raster flags");
         CK(P.hitlist.ensure(sizeof(uint2) * (size_t)max_rays), "alloc raster hit list");
+        P.big_cap = (unsigned)raster_big_cap(max_rays);
+        CK(P.rbig.ensure(sizeof(int4) * (size_t)P.big_cap), "alloc raster triangle list");
+        CK(P.rbigctr.ensure(sizeof(unsigned) * 2), "alloc raster triangle counters");
     }
     CK(P.tilebase.ensure(sizeof(unsigned) * (size_t)max_tiles), "alloc tile base");
     CK(P.scan_scr.ensure(scan_scratch_bytes(max_tiles)), "alloc scan scratch");

@@ -172,6 +172,10 @@ struct TraceArgs {
                                   // [n_angles]: 1 if any aspect does
     const int* tri_pos;           // with vis: [n_tri] position in tris of each original triangle index
     unsigned* list_count;         // with vis: device count of the rasterised primary hits
+    int4* big;                    // with vis: triangles of more than 32 cells, (triangle, aspect, i0 | j0 << 16,
+                                  // (i1 - i0) | (j1 - j0) << 16), tested by warps after the per-thread pass
+    unsigned* big_ctr;            // with vis: [2] entries appended, (unused)
+    unsigned big_cap;             // with vis: capacity of big (an aspect whose entry does not fit traverses)
     uint2* hit_list;              // optional (rasterised hits, a bounce pass follows): the primary pass
                                   // lists (ray, aspect) of each rasterised hit here instead of storing
                                   // its state, and bounce pass 1 rebuilds the state from the list

@@ -165,9 +165,19 @@ __device__ __forceinline__ int tri_filter(float4 A, float4 B, float4 C, float3 o
     const float U0 = dot_s(s, p), V0 = dot_s(d, qv), T0 = dot_s(e2, qv);
     const float smax = fmaxf(fmaxf(fabsf(s.x), fabsf(s.y)), fabsf(s.z));
     const float bUV = __fmul_rn(smax, B.w);
-    if (!(B.w > 0.f)) return 0;  // degenerate: edges and constants zeroed, no hits
-    const int f = filter_core(U0, V0, T0, det, bUV, bUV, C.w, __fmul_rn(2.f * smax, C.w), tc, et);
-    if (f < 2) return f;
+    if (!(B.w > 0.f)) return 0;
+    return filter_core(U0, V0, T0, det, bUV, bUV, C.w, __fmul_rn(2.f * smax, C.w), tc, et);
+}
+
+// the per-component bounds of a test the norm bounds left open
+__device__ __forceinline__ int tri_filter_tight(float4 A, float4 B, float4 C, float3 o, float3 d, float& tc, float& et)
+{
+    const float3 e1 = make_float3(B.x, B.y, B.z), e2 = make_float3(C.x, C.y, C.z);
+    const float3 p = cross_s(d, e2);
+    const float det = dot_s(e1, p);
+    const float3 s = make_float3(__fsub_rn(o.x, A.x), __fsub_rn(o.y, A.y), __fsub_rn(o.z, A.z));
+    const float3 qv = cross_s(s, e1);
+    const float U0 = dot_s(s, p), V0 = dot_s(d, qv), T0 = dot_s(e2, qv);
     const float3 pa = cross_abs(d, e2), qa = cross_abs(s, e1);
     const float3 as = abs3(s), ad3 = abs3(d), a1 = abs3(e1), a2 = abs3(e2);
     return filter_core(U0, V0, T0, det, 0x1.03p-21f * dot_s(as, pa), 0x1.03p-21f * dot_s(ad3, qa),
@@ -192,6 +202,11 @@ __device__ __noinline__ int tri_refine(const float4* __restrict__ rec, const flo
                                         float3 d, int code, float& tc)
 {
     const float4 A = __ldg(rec + 3 * (size_t)k), B = __ldg(rec + 3 * (size_t)k + 1), C = __ldg(rec + 3 * (size_t)k + 2);
+    if (code >= 4) {  // from the norm bounds: try the per-component ones first
+        float et;
+        code = tri_filter_tight(A, B, C, o, d, tc, et);
+        if (code < 2) return code;
+    }
     const float3 e1 = make_float3(B.x, B.y, B.z), e2 = make_float3(C.x, C.y, C.z);
     const float3 p = cross_s(d, e2);
     const float det = dot_s(e1, p);
@@ -382,7 +397,7 @@ __device__ __forceinline__ void leaf_test(const TriRefs& tr, int ref, float3 o, 
         const int f = tri_filter(A, B, C, o, d, tc, et);
         if (f == 0) continue;
         if (f >= 2) {
-            const int r = tri_refine(tr.rec, tr.v12, k, o, d, f, tc);
+            const int r = tri_refine(tr.rec, tr.v12, k, o, d, f + 2, tc);
             if (kCount) count_open(tr.stats, r);
             if (!(r & 1)) continue;
             et = FLT_MAX;
@@ -1035,6 +1050,62 @@ __device__ __forceinline__ bool tri_cells(const AngleDev& A, float ids, float4 a
     return true;
 }
 
+// The projected triangle as three edge half-planes in the cell coordinates of
+// an item's range (origin at its first cell i0, j0): cell (i, j) passes when
+// nx (i - i0) + ny (j - j0) + c <= 0 for every edge. Each half-plane is moved
+// outward by the margin m of tri_cells (the vertices' and ray origins' FP32
+// errors) plus 0.002 cells (the local shift) and 1e-5 of the range per unit of
+// |n| (the evaluation), so every cell of the conservative range whose ray the
+// exact test can accept passes: the moved half-planes contain the projection
+// widened by m in u and v. A projection of (nearly) zero area keeps every
+// cell of the range.
+struct CellEdges {
+    float nx[3], ny[3], c[3];
+};
+
+__device__ __forceinline__ void tri_cell_edges(const AngleDev& A, float ids, float4 a, float4 b, float4 c, int i0,
+                                               int i1, int j0, int j1, CellEdges& E)
+{
+    const float px[3] = {a.x, a.x + b.x, a.x + c.x}, py[3] = {a.y, a.y + b.y, a.y + c.y},
+                pz[3] = {a.z, a.z + b.z, a.z + c.z};
+    float u[3], v[3], umin = FLT_MAX, umax = -FLT_MAX, vmin = FLT_MAX, vmax = -FLT_MAX, mag = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float dx = px[k] - A.p0[0], dy = py[k] - A.p0[1], dz = pz[k] - A.p0[2];
+        const float uu = (dx * A.hhat[0] + dy * A.hhat[1] + dz * A.hhat[2]) * ids;
+        const float vv = (dx * A.vhat[0] + dy * A.vhat[1] + dz * A.vhat[2]) * ids;
+        umin = fminf(umin, uu);
+        umax = fmaxf(umax, uu);
+        vmin = fminf(vmin, vv);
+        vmax = fmaxf(vmax, vv);
+        mag = fmaxf(mag, (fabsf(dx) + fabsf(dy) + fabsf(dz)) * ids);
+        u[k] = uu - (float)i0;
+        v[k] = vv - (float)j0;
+    }
+    const float m = 0.01f + (umax - umin + vmax - vmin) * (1.f / 1024.f) + mag * (1.f / 262144.f) + 0.002f;
+    const float a2 = (u[1] - u[0]) * (v[2] - v[0]) - (v[1] - v[0]) * (u[2] - u[0]);
+    const float sg = a2 > 0.f ? 1.f : -1.f;
+    const bool flat = !(fabsf(a2) > 1e-2f);
+    const float ext = 1e-5f * (float)(i1 - i0 + j1 - j0 + 2);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int k1 = k == 2 ? 0 : k + 1;
+        // outward normal of edge k -> k1 (counter-clockwise after the sign sg)
+        const float nx = sg * (v[k1] - v[k]), ny = -sg * (u[k1] - u[k]);
+        const float w = (fabsf(nx) + fabsf(ny)) * (m + ext);
+        E.nx[k] = flat ? 0.f : nx;
+        E.ny[k] = flat ? 0.f : ny;
+        E.c[k] = flat ? -1.f : -(nx * u[k] + ny * v[k]) - w;
+    }
+}
+
+__device__ __forceinline__ bool cell_inside(const CellEdges& E, int di, int dj)
+{
+    const float x = (float)di, y = (float)dj;
+    return fmaf(E.nx[0], x, fmaf(E.ny[0], y, E.c[0])) <= 0.f && fmaf(E.nx[1], x, fmaf(E.ny[1], y, E.c[1])) <= 0.f &&
+           fmaf(E.nx[2], x, fmaf(E.ny[2], y, E.c[2])) <= 0.f;
+}
+
 __global__ void __launch_bounds__(256) k_silhouette(const float4* __restrict__ tris, int n_tri,
                                                     const AngleDev* __restrict__ angles,
                                                     const long long* __restrict__ ray_off, int n_angles,
@@ -1087,8 +1158,6 @@ __device__ __forceinline__ float3 primary_origin(const AngleDev& A, int i, int j
 // key order is (t, index): the closest hit and the tie rule of the traversal,
 // whose t is <= FLT_MAX. A triangle spanning more than kRasterMaxCells cells
 // flags its aspect instead, whose primary rays then traverse the tree.
-constexpr int kRasterSmall = 32;    // cells a thread tests by itself
-constexpr int kRasterQueue = 256;   // larger triangles a block defers to its warps per round
 
 // An aspect's ray grid held in registers for the cell loops: the loops' atomics
 // could alias the aspect table as far as the compiler knows, so fields read
@@ -1126,24 +1195,41 @@ __device__ __forceinline__ float3 grid_origin(const RasterGrid& G, int i, int j)
 // tri_filter (each below 8 u sum|S_i| of the absolute cross products).
 struct RasterTri {
     float3 v0, p, p2, nn;  // vertex 0, d x e2, e1 x d, e1 x e2
-    float3 pa, pa2, na;    // the same cross products of the absolute values
-    float det, bd;         // e1 . (d x e2) and its error bound
+    float det, bd;         // e1 . (d x e2) and its error bound (-1: degenerate, no hits)
+    float bU, bV, bT;      // error bounds of U, V and T for every cell of the range
 };
 
-__device__ __forceinline__ RasterTri raster_tri(float4 P, float4 B, float4 C, float3 d)
+// The per-cell bounds 8.1 u |S|.(|d| x |e2|), 8.1 u |S|.(|e1| x |d|) and
+// 9.1 u |S|.(|e1| x |e2|) taken once for the cell range i0..i1, j0..j1: each
+// |S_c| is at most its largest value at the range's corner rays (|o - v0| is
+// convex in (i, j) for the exact grid points) plus 8 u of the largest |o_c|
+// (the FP32 rounding of the ray origins and of S).
+__device__ __forceinline__ RasterTri raster_tri(const RasterGrid& G, float4 P, float4 B, float4 C, int i0, int i1,
+                                                int j0, int j1)
 {
     RasterTri R;
-    const float3 e1 = make_float3(B.x, B.y, B.z), e2 = make_float3(C.x, C.y, C.z);
+    const float3 e1 = make_float3(B.x, B.y, B.z), e2 = make_float3(C.x, C.y, C.z), d = G.d;
     R.v0 = make_float3(P.x, P.y, P.z);
     R.p = cross_s(d, e2);
     R.p2 = cross_s(e1, d);
     R.nn = cross_s(e1, e2);
-    R.pa = cross_abs(d, e2);
-    R.pa2 = cross_abs(e1, d);
-    R.na = cross_abs(e1, e2);
     R.det = dot_s(e1, R.p);
-    // a degenerate triangle (zeroed edges) keeps det = 0 and bd = -1: every test is a miss
-    R.bd = B.w > 0.f ? 0x1.03p-21f * dot_s(abs3(e1), R.pa) : -1.f;
+    const float3 pa = cross_abs(d, e2);
+    R.bd = B.w > 0.f ? 0x1.03p-21f * dot_s(abs3(e1), pa) : -1.f;
+    float3 sm = make_float3(0.f, 0.f, 0.f), om = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const float3 o = grid_origin(G, (c & 1) ? i1 : i0, (c & 2) ? j1 : j0);
+        sm = make_float3(fmaxf(sm.x, fabsf(o.x - R.v0.x)), fmaxf(sm.y, fabsf(o.y - R.v0.y)),
+                         fmaxf(sm.z, fabsf(o.z - R.v0.z)));
+        om = make_float3(fmaxf(om.x, fabsf(o.x)), fmaxf(om.y, fabsf(o.y)), fmaxf(om.z, fabsf(o.z)));
+    }
+    const float g = 8.f * kU;
+    sm = make_float3(__fmaf_rn(g, om.x + fabsf(R.v0.x), sm.x), __fmaf_rn(g, om.y + fabsf(R.v0.y), sm.y),
+                     __fmaf_rn(g, om.z + fabsf(R.v0.z), sm.z));
+    R.bU = 0x1.03p-21f * dot_s(sm, pa);
+    R.bV = 0x1.03p-21f * dot_s(sm, cross_abs(e1, d));
+    R.bT = 0x1.23p-21f * dot_s(sm, cross_abs(e1, e2));
     return R;
 }
 
@@ -1153,12 +1239,9 @@ __device__ __forceinline__ void raster_cell(const RasterGrid& G, const TraceArgs
 {
     const float3 o = grid_origin(G, i, j);
     const float3 s = make_float3(__fsub_rn(o.x, R.v0.x), __fsub_rn(o.y, R.v0.y), __fsub_rn(o.z, R.v0.z));
-    const float3 as = abs3(s);
     float tc, et;
-    if (!(R.bd >= 0.f)) return;
     // V = S.(e1 x d) and T = S.(e1 x e2) are the triple products of tri_filter, with the same bounds
-    const int f = filter_core(dot_s(s, R.p), dot_s(s, R.p2), dot_s(s, R.nn), R.det, 0x1.03p-21f * dot_s(as, R.pa),
-                              0x1.03p-21f * dot_s(as, R.pa2), R.bd, 0x1.23p-21f * dot_s(as, R.na), tc, et);
+    const int f = filter_core(dot_s(s, R.p), dot_s(s, R.p2), dot_s(s, R.nn), R.det, R.bU, R.bV, R.bd, R.bT, tc, et);
     if (f == 0) return;
     if (f >= 2) {
         const int r = tri_refine(a.tris, a.tri_v12, k, o, G.d, f, tc);
@@ -1174,91 +1257,209 @@ __device__ __forceinline__ void raster_cell(const RasterGrid& G, const TraceArgs
     }
 }
 
-// Items q = aspect * n_tri + triangle in grid-stride rounds of 256 per block
-// (aspect-major: a block's threads take neighbouring triangles of one aspect,
-// whose cells are neighbours too). A triangle with at most kRasterSmall cells
-// is tested by its thread; larger ones are queued with their cell range and
-// tested by the block's warps, 32 cells at a time.
-__global__ void __launch_bounds__(256, 2) k_raster(const TraceArgs a, int n_tri, unsigned long long* vis,
-                                                   unsigned* full, int count)
+// A triangle of the flattened rasterisation and everything its cells need,
+// one per lane in shared memory (53 words, an odd stride: the lanes' writes hit
+// distinct banks, and lanes reading one triangle's fields share a broadcast).
+struct RasterItem {
+    float3 p0, du, dv;  // the aspect's ray grid
+    int nbu, tw;
+    RasterTri R;
+    PlaneKey K;
+    CellEdges E;
+    int i0, j0, w, ncell;  // cell range: w columns from (i0, j0), ncell cells
+    float rw;              // 1 / w
+    unsigned orig;         // original triangle index
+    int t, ang;            // reordered triangle and aspect
+};
+static_assert(sizeof(RasterItem) == 53 * 4, "RasterItem layout");
+constexpr int kRasterWarps = 8;    // warps of a k_raster block
+constexpr int kRasterFlat = 512;   // cells of a triangle the warps flatten; larger ones go to k_raster_big
+constexpr size_t kRasterSmem = sizeof(RasterItem) * 32 * kRasterWarps;
+
+// Items q = aspect * n_tri + triangle, one per lane in grid-stride order
+// (aspect-major: neighbouring lanes take neighbouring triangles of one
+// aspect). Each lane projects its triangle and, for a range of at most
+// kRasterFlat cells, writes the triangle's constants to shared memory; the
+// warp then walks the (triangle, cell) pairs of its 32 triangles, lane l taking
+// pairs l, l + 32, ..., so every lane works until the warp's cells run out. A
+// triangle with a larger range is appended to the list `big` (warp-aggregated)
+// for k_raster_big. Each cell passes the edge pretest before the triangle test.
+__global__ void __launch_bounds__(256, 4) k_raster(const TraceArgs a, int n_tri, unsigned long long* vis, unsigned* full,
+                                                   int count)
 {
-    __shared__ int4 s_rng[kRasterQueue];  // i0, i1, j0, j1
-    __shared__ int s_item[kRasterQueue];  // triangle
-    __shared__ int s_ang[kRasterQueue];
-    __shared__ int s_n;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+    extern __shared__ RasterItem s_items[];
+    __shared__ int s_off[kRasterWarps][33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    RasterItem* my = s_items + warp * 32;
+    int* off = s_off[warp];
     const unsigned long long n_items = (unsigned long long)a.n_angles * (unsigned long long)n_tri;
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    // (aspect, triangle) of this thread's item, advanced by the stride without a division per round
     const unsigned long long q0 = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     int ang = (int)(q0 / (unsigned long long)n_tri), t = (int)(q0 % (unsigned long long)n_tri);
     const int step_a = (int)(stride / (unsigned long long)n_tri), step_t = (int)(stride % (unsigned long long)n_tri);
     unsigned long long ntri = 0;
-    // the rounds depend on the block only: every thread reaches the barriers
-    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < n_items; base += stride) {
-        if (threadIdx.x == 0) s_n = 0;
-        __syncthreads();
-        if (base + threadIdx.x < n_items) {
+    // the rounds depend on the warp only: every lane reaches the ballots and shuffles
+    for (unsigned long long base = q0 - lane; base < n_items; base += stride) {
+        bool want_big = false;
+        int4 rng = make_int4(0, 0, 0, 0);
+        int nc = 0;
+        if (base + lane < n_items) {
             const AngleDev& A = a.angles[ang];
             const float4* tp = a.tris + 3 * (size_t)t;
             const float4 P = __ldg(tp), B = __ldg(tp + 1), C = __ldg(tp + 2);
             int i0, i1, j0, j1;
             if (tri_cells(A, cell_scale(A), P, B, C, i0, i1, j0, j1)) {
                 const long long ncell = (long long)(i1 - i0 + 1) * (j1 - j0 + 1);
-                int slot = kRasterQueue;
-                if (ncell > kRasterMaxCells) {
+                if (ncell > kRasterMaxCells || A.nu > 65535 || A.nv > 65535) {
                     atomicOr(full + ang, 1u);
                     atomicOr(full + a.n_angles, 1u);  // some aspect of the chunk traverses
-                } else if (ncell > kRasterSmall && (slot = atomicAdd(&s_n, 1)) < kRasterQueue) {
-                    s_rng[slot] = make_int4(i0, i1, j0, j1);
-                    s_item[slot] = t;
-                    s_ang[slot] = ang;
+                } else if (ncell > kRasterFlat) {
+                    want_big = true;
+                    rng = make_int4(t, ang, i0 | (j0 << 16), (i1 - i0) | ((j1 - j0) << 16));
                 } else {
                     const RasterGrid G = raster_grid(A);
-                    unsigned long long* vrow = vis + a.ray_off[ang];
-                    const unsigned orig = (unsigned)__float_as_int(P.w);
-                    const PlaneKey K = plane_key(a.tri_nrm, t, P, G.d);
-                    const RasterTri R = raster_tri(P, B, C, G.d);
-                    for (int j = j0; j <= j1; ++j)
-                        for (int i = i0; i <= i1; ++i) raster_cell(G, a, R, K, t, orig, i, j, vrow, count);
-                    ntri += (unsigned long long)ncell;
+                    const RasterTri R = raster_tri(G, P, B, C, i0, i1, j0, j1);
+                    if (R.bd >= 0.f) {
+                        RasterItem& it = my[lane];
+                        it.p0 = G.p0;
+                        it.du = G.du;
+                        it.dv = G.dv;
+                        it.nbu = G.nbu;
+                        it.tw = G.tw;
+                        it.R = R;
+                        it.K = plane_key(a.tri_nrm, t, P, G.d);
+                        tri_cell_edges(A, cell_scale(A), P, B, C, i0, i1, j0, j1, it.E);
+                        it.i0 = i0;
+                        it.j0 = j0;
+                        it.w = i1 - i0 + 1;
+                        it.ncell = (int)ncell;
+                        it.rw = 1.f / (float)(i1 - i0 + 1);
+                        it.orig = (unsigned)__float_as_int(P.w);
+                        it.t = t;
+                        it.ang = ang;
+                        nc = (int)ncell;
+                    }
                 }
             }
         }
+        const unsigned m = __ballot_sync(kFull, want_big);
+        if (m) {
+            unsigned slot = 0;
+            if (lane == __ffs(m) - 1) slot = atomicAdd(a.big_ctr, (unsigned)__popc(m));
+            slot = __shfl_sync(kFull, slot, __ffs(m) - 1) + __popc(m & ((1u << lane) - 1u));
+            if (want_big) {
+                if (slot < a.big_cap) {
+                    a.big[slot] = rng;
+                } else {  // no room: this aspect's primary rays traverse
+                    atomicOr(full + rng.y, 1u);
+                    atomicOr(full + a.n_angles, 1u);
+                }
+            }
+        }
+        // inclusive scan of the cell counts: off[k] = first pair of lane k's triangle
+        int incl = nc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        off[lane + 1] = incl;
+        if (lane == 0) off[0] = 0;
+        __syncwarp();
+        const int total = __shfl_sync(kFull, incl, 31);
+        int k = 0;
+        for (int c = lane; c < total; c += 32) {
+            while (off[k + 1] <= c) ++k;
+            const RasterItem& it = my[k];
+            const int loc = c - off[k];
+            // (loc + 0.5) / w is at least 0.5 / w from an integer and loc, w <= 512: the FP32 product floors exactly
+            const int dj = __float2int_rz(((float)loc + 0.5f) * it.rw), di = loc - dj * it.w;
+            if (!cell_inside(it.E, di, dj)) continue;
+            ++ntri;
+            const int i = it.i0 + di, j = it.j0 + dj;
+            const float fi = (float)i, fj = (float)j;
+            const float3 o = make_float3(__fadd_rn(__fadd_rn(it.p0.x, __fmul_rn(fi, it.du.x)), __fmul_rn(fj, it.dv.x)),
+                                         __fadd_rn(__fadd_rn(it.p0.y, __fmul_rn(fi, it.du.y)), __fmul_rn(fj, it.dv.y)),
+                                         __fadd_rn(__fadd_rn(it.p0.z, __fmul_rn(fi, it.du.z)), __fmul_rn(fj, it.dv.z)));
+            const float3 sv = make_float3(__fsub_rn(o.x, it.R.v0.x), __fsub_rn(o.y, it.R.v0.y), __fsub_rn(o.z, it.R.v0.z));
+            float tc, et;
+            const int f = filter_core(dot_s(sv, it.R.p), dot_s(sv, it.R.p2), dot_s(sv, it.R.nn), it.R.det, it.R.bU,
+                                      it.R.bV, it.R.bd, it.R.bT, tc, et);
+            if (f == 0) continue;
+            if (f >= 2) {
+                const AngleDev& A = a.angles[it.ang];
+                const int r = tri_refine(a.tris, a.tri_v12, it.t, o, make_float3(A.dir[0], A.dir[1], A.dir[2]), f, tc);
+                if (count) count_open(a.stats, r);
+                if (!(r & 1)) continue;
+            }
+            const float th = plane_key_t(it.K, o, tc);
+            if (th >= 0.f && th <= FLT_MAX) {
+                const int tw = it.tw, sh = 5 - tw;  // tile of W = 2^tw by H = 2^sh rays
+                const int bu = i >> tw, bv = j >> sh;
+                const long long pidx =
+                    ((long long)(bv * it.nbu + bu) << 5) + ((j & ((1 << sh) - 1)) << tw) + (i & ((1 << tw) - 1));
+                atomicMin(vis + a.ray_off[it.ang] + pidx, ((unsigned long long)__float_as_uint(th) << 32) | it.orig);
+            }
+        }
+        __syncwarp();  // the next round rewrites my[] and off[]
         t += step_t;
         ang += step_a;
         if (t >= n_tri) {
             t -= n_tri;
             ++ang;
         }
-        __syncthreads();
-        const int n_def = min(s_n, kRasterQueue);
-        for (int k = warp; k < n_def; k += n_warps) {
-            const int td = s_item[k], ad = s_ang[k];
-            const int4 r = s_rng[k];
-            const RasterGrid G = raster_grid(a.angles[ad]);
-            const float4* tp = a.tris + 3 * (size_t)td;
-            const float4 P = __ldg(tp), B = __ldg(tp + 1), C = __ldg(tp + 2);
-            const unsigned orig = (unsigned)__float_as_int(P.w);
-            unsigned long long* vrow = vis + a.ray_off[ad];
-            const PlaneKey K = plane_key(a.tri_nrm, td, P, G.d);
-            const RasterTri R = raster_tri(P, B, C, G.d);
-            const int w = r.y - r.x + 1, ncell = w * (r.w - r.z + 1);
-            // cell c = (c / w, c % w) from (j0, i0); steps of 32 cells: sj rows and si columns
-            const int sj = 32 / w, si = 32 - sj * w, l0 = lane / w;
-            int i = r.x + (lane - l0 * w), j = r.z + l0;
-            for (int cidx = lane; cidx < ncell; cidx += 32) {
-                raster_cell(G, a, R, K, td, orig, i, j, vrow, count);
-                i += si;
-                j += sj;
-                if (i > r.y) {
-                    i -= w;
-                    ++j;
-                }
-            }
-            if (lane == 0) ntri += (unsigned long long)ncell;
+    }
+    if (count) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ntri += __shfl_xor_sync(kFull, ntri, o);
+        if (lane == 0 && ntri) {
+            atomicAdd(a.stats + kStatTris, ntri);
+            atomicAdd(a.stats + kStatRaster, ntri);
         }
-        __syncthreads();
+    }
+}
+
+// The listed large triangles, warp w taking entries w, w + warps, ... (every
+// warp has hundreds of entries, so the few very large triangles average out),
+// their cells 32 at a time.
+__global__ void __launch_bounds__(256, 3) k_raster_big(const TraceArgs a, unsigned long long* vis, int count)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned n_big = min(a.big_ctr[0], a.big_cap);
+    const unsigned nw = (gridDim.x * blockDim.x) >> 5;
+    unsigned long long ntri = 0;
+    for (unsigned it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < n_big; it += nw) {
+        const int4 b = a.big[it];
+        const int td = b.x, ad = b.y;
+        const int i0 = b.z & 0xFFFF, j0 = (unsigned)b.z >> 16, w = (b.w & 0xFFFF) + 1, h = ((unsigned)b.w >> 16) + 1;
+        const int i1 = i0 + w - 1, j1 = j0 + h - 1;
+        const AngleDev& A = a.angles[ad];
+        const RasterGrid G = raster_grid(A);
+        const float4* tp = a.tris + 3 * (size_t)td;
+        const float4 P = __ldg(tp), B = __ldg(tp + 1), C = __ldg(tp + 2);
+        const RasterTri R = raster_tri(G, P, B, C, i0, i1, j0, j1);
+        if (!(R.bd >= 0.f)) continue;  // warp-uniform
+        const unsigned orig = (unsigned)__float_as_int(P.w);
+        unsigned long long* vrow = vis + a.ray_off[ad];
+        const PlaneKey K = plane_key(a.tri_nrm, td, P, G.d);
+        CellEdges E;
+        tri_cell_edges(A, cell_scale(A), P, B, C, i0, i1, j0, j1, E);
+        const int ncell = w * h;
+        // cell c = (c / w, c % w) from (j0, i0); steps of 32 cells: sj rows and si columns
+        const int sj = 32 / w, si = 32 - sj * w, l0 = lane / w;
+        int i = i0 + (lane - l0 * w), j = j0 + l0;
+        for (int cidx = lane; cidx < ncell; cidx += 32) {
+            if (cell_inside(E, i - i0, j - j0)) {
+                raster_cell(G, a, R, K, td, orig, i, j, vrow, count);
+                ++ntri;
+            }
+            i += si;
+            j += sj;
+            if (i > i1) {
+                i -= w;
+                ++j;
+            }
+        }
     }
     if (count) {
 #pragma unroll
@@ -1648,10 +1849,21 @@ cudaError_t launch_raster(const TraceArgs& a, int n_tri, unsigned long long* vis
     if (a.n_angles <= 0 || n_tri <= 0) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(vis, 0xFF, sizeof(unsigned long long) * (size_t)a.total_rays, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(full, 0, sizeof(unsigned) * (size_t)(a.n_angles + 1), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.big_ctr, 0, sizeof(unsigned) * 2, st);
     if (e != cudaSuccess) return e;
+    static int smem_set[64] = {0};  // per device: k_raster's dynamic shared memory above 48 KB allowed
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!smem_set[dev]) {
+        e = cudaFuncSetAttribute(k_raster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRasterSmem);
+        if (e != cudaSuccess) return e;
+        smem_set[dev] = 1;
+    }
     const long long need = ((long long)a.n_angles * n_tri + 255) / 256;
-    k_raster<<<(int)std::max(1ll, std::min<long long>(need, n_blocks)), 256, 0, st>>>(a, n_tri, vis, full,
-                                                                                   count ? 1 : 0);
+    k_raster<<<(int)std::max(1ll, std::min<long long>(need, n_blocks)), 32 * kRasterWarps, kRasterSmem, st>>>(
+        a, n_tri, vis, full, count ? 1 : 0);
+    k_raster_big<<<n_blocks, 256, 0, st>>>(a, vis, count ? 1 : 0);
     const long long n_tiles = a.total_rays >> 5;
     k_vis_mask<<<(int)std::max(1ll, std::min<long long>((n_tiles + 7) / 8, n_blocks)), 256, 0, st>>>(a, vis, full,
                                                                                                      a.mask);
