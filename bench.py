@@ -1,10 +1,11 @@
 """Benchmark of the SBR trace-integrate path on one GB300 (replicas on N GPUs).
 
-Workload (default): triangular trihedral corner reflector, 1 m legs,
-3 x 1024 triangles, 10 GHz, ray spacing lambda/10 (margin 0.05), up to 3
-bounces, azimuth sweep 0..90 deg in 0.5 deg steps at elevation 35.26 deg
-(181 aspects, about 52M launched rays), vector PO, HH and VV.
-One step = one full sweep: sbr_trace over all 181 aspects + sbr_po_integrate.
+Workload (default, the largest configuration): seeded procedural aircraft
+(983,270 triangles), 10 GHz, ray spacing lambda/10 (margin 0.05), up to 10
+bounces, 360 azimuths at elevation 0 (about 4.8 G launched rays per sweep),
+vector PO, HH and VV. One step = one full sweep: sbr_trace over all 360
+aspects + sbr_po_integrate. The trihedral sweep (C2) runs beside it and is
+reported under "trihedral".
 
 Metric: ray-bounces per second (closest-hit queries on live rays, hit or
 miss), aggregated over all ranks; angles per second is reported beside it.
@@ -12,11 +13,14 @@ miss), aggregated over all ranks; angles per second is reported beside it.
   value     device-resident: mesh and BVH already on the GPU, outputs to device
   e2e       through the public API from host buffers every step: mesh upload
             from pinned host memory, BVH build, trace, PO, results read back
-  roofline  the transport passes (primary + bounce kernels, one traversal
-            routine), FP32 issue bound: algorithmic FP32 operations from the
-            node-visit and triangle-test counts of a counting run, divided by
-            the passes' CUDA-event time measured inside the timed steps
-  cpu_baseline  the FP64 oracle on a sample of the sweep's aspects, all host cores
+  roofline  the bounce passes (the dominant kernel): R* = min(BW / B_rb,
+            P / F_rb) with B_rb = 32 n_node + 48 n_tri bytes and
+            F_rb = 28 n_node + 30 n_tri FP32 operations per bounce query
+            (n_node, n_tri: node visits and triangle tests per query from a
+            counting run), BW the probed L2 bandwidth when the tree and the
+            triangles fit in L2 (else the measured HBM bandwidth), P the probed
+            FP32 FMA rate; frac = measured bounce queries/s / R*
+  cpu_baseline  the FP64 oracle on a seeded sample of the sweep's rays, all host cores
 
 ``--impl reference`` times the oracle (the CPU reference of this method) on
 the same workload and prints its own line. N > 1 (torchrun): every rank runs
@@ -42,40 +46,21 @@ if ROOT not in sys.path:
 
 import sbr_inputs as S  # noqa: E402
 
-# FP32 operations of one node visit and of one triangle test (Moller-Trumbore
-# form up to the inside decision), counted from the traversal routines in
-# sbr_trace.cu. Binary node: two slab tests (6 FMA, 12 min/max, 1 scale, 1
-# compare each) and the ordering compare. 4-wide node: four slab tests with
-# the near/far slabs picked per ray (6 FMA, 6 min/max, 1 scale, 1 compare
-# each) and a 5-exchange sorting network (1 compare, 4 selects each).
-OPS_NODE = 41
-OPS_NODE_OCT = 29  # binary node over the octant copies: 2 x (6 FMA + 6 min/max + 1 scale + 1 compare) + ordering
-OPS_NODE4 = 81
-OPS_TRI = 38
-# FP32 operations of the per-hit arithmetic (apply_hit in sbr_trace.cu, each add, multiply, fma, divide,
-# square root and select one): hit point 3, path accumulation 9, unit normal 14, orientation 8, receiver path
-# term 25 + 11, H field 10, tube area 2, the two vector PO terms 3 + 42, four coefficients 12, scalar
-# coefficient 4, PEC field update 7, reflection 4, new origin 3 = 157 per hit of a bounce pass; a primary hit
-# adds the two-float k.o0 of its start (25) and the first-hit cosine (3). A rasterised cell test is the ray's
-# FP32 origin (12) and the triangle test.
+# Roofline of the traversal (the bounce passes): per bounce query, B_rb = 32 bytes per node visit + 48 per
+# triangle test (one node's box, one triangle record) and F_rb = 28 FP32 operations per node visit (slab tests
+# of two children) + 30 per triangle test (Moller-Trumbore).
+BYTES_NODE, BYTES_TRI = 32, 48
+FLOP_NODE, FLOP_TRI = 28, 30
+# FP32 operations of the per-hit arithmetic (apply_hit: hit point, path, normal orientation, receiver path
+# term, H field, tube area, the vector PO terms and coefficients, scalar coefficient, PEC field update,
+# reflection, new origin), reported beside the roofline: 157 per hit of a bounce pass, 185 for a primary hit
+# rebuilt by bounce pass 1.
 OPS_HIT = 157
 OPS_PRIMARY_HIT = 185
-OPS_RASTER_CELL = 12 + OPS_TRI
-# DRAM bytes per launched ray of the kernel the roofline describes, from one ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum) of the trihedral sweep's
-# 9-aspect sample (2,114,692 rays) on the PLOC tree, for the setting listed:
-# with traversed primary rays, k_primary and both k_bounce passes (188.39 MB);
-# with rasterised primary hits (bounce pass 1 rebuilding them from the hit
-# list), both k_bounce passes. Stack depth and chunk
-# size leave the bytes per ray unchanged (the queues and records are the
-# traffic), and so does the ray tile once the primary hits are rasterised (the
-# bounce passes stream the same queues; the tree stays in L1/L2); it grows with
-# the rays, so it is scaled by the rays of a step.
-TRAFFIC_PER_RAY = {"trihedral": [(188.39e6 / 2114692, dict(tile_w=4, bvh_width=2, packet=0, octant=0, raster=0), "ploc"),
-                                  (103.70e6 / 2114692, dict(bvh_width=2, packet=0, octant=0, raster=1), "ploc"),
-                                  (104.17e6 / 2114692, dict(bvh_width=2, packet=0, octant=1, raster=1), "ploc")]}
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
+# DRAM bytes per bounce query of the bounce passes (dram__bytes_read.sum + dram__bytes_write.sum over the
+# k_bounce launches of one ncu capture, divided by their queries), per workload and setting; scaled by the
+# bounce queries of a step. None where no capture of the current kernels exists.
+TRAFFIC_PER_QUERY = {}
 
 
 def peaks():
@@ -186,18 +171,34 @@ def wl_config(case: dict, name: str) -> dict:
 
 
 # ----------------------------------------------------------------------------- oracle timing
-def oracle_sample(case, n_angles: int, threads: int):
+_ORACLE_MESH = {}
+
+
+def oracle_sample(case, n_angles: int, threads: int, frac: float = 1.0, seed: int = 0):
+    """The oracle on ``n_angles`` evenly spaced aspects of the workload, each with a
+    seeded fraction ``frac`` of its ray grid (all rays when 1): ray-bounces,
+    seconds of trace + PO (the oracle's mesh and BVH are built once, untimed)."""
     import oracle
 
-    om = oracle.Mesh(case["xyz"], case["tri"])
+    key = case["name"]
+    if key not in _ORACLE_MESH:
+        _ORACLE_MESH.clear()
+        _ORACLE_MESH[key] = oracle.Mesh(case["xyz"], case["tri"])
+    om = _ORACLE_MESH[key]
     idx = np.linspace(0, len(case["angles"]) - 1, n_angles).round().astype(int)
-    t0 = time.perf_counter()
-    bounces = 0
+    rng = np.random.default_rng(seed)
+    frames = []
     for a in idx:
         az, el = case["angles"][a]
         fr = oracle.make_frame(om.bbox, az, el, case["spacing"], eta=case["eta"], window=case.get("window", 0.0),
                                offset=case.get("offset", (0.0, 0.0)))
-        tr = oracle.trace(om, fr, case["max_bounces"], threads=threads, require_escape=case.get("escape", False))
+        ids = None if frac >= 1.0 else np.sort(rng.choice(fr.n_rays, max(1, int(fr.n_rays * frac)), replace=False))
+        frames.append((fr, ids))
+    t0 = time.perf_counter()
+    bounces = 0
+    for fr, ids in frames:
+        tr = oracle.trace(om, fr, case["max_bounces"], threads=threads, require_escape=case.get("escape", False),
+                          ids=ids)
         oracle.po(tr["coef"], tr["L"], tr["valid"], case["freqs"])
         nb = tr["nb"]
         bounces += int(np.sum(nb + (nb < case["max_bounces"])))
@@ -205,33 +206,80 @@ def oracle_sample(case, n_angles: int, threads: int):
     return bounces, dt, idx
 
 
+def oracle_sample_size(case):
+    """Oracle sample of a step: the whole sweep's aspects for the small meshes, a seeded fraction of
+    the rays of 12 evenly spaced aspects for the aircraft (about 1 M rays per aspect at 10 GHz)."""
+    if "aircraft" in case["name"]:
+        f = float(case["freqs"][0])
+        return 12, min(1.0, 0.4 * (10e9 / f) ** 2)
+    return min(24, len(case["angles"])), 1.0
+
+
 def run_reference(args, case, ws, rank, pg):
     if rank != 0:
         return
     threads = os.cpu_count() or 1
+    n, frac = oracle_sample_size(case)
     t1 = 0.0
     for _ in range(max(1, args.warmup)):
-        t1 = oracle_sample(case, 1, threads)[1]
-    # aspects per step: at most --ref-angles, fewer when the steps would take more than about two minutes
-    n = max(1, min(args.ref_angles, int(120.0 / (max(1, args.steps) * max(t1, 1e-3)))))
+        t1 = oracle_sample(case, 1, threads, frac)[1]
+    # aspects per step: fewer when the steps would take more than about two minutes
+    n = max(1, min(n, args.ref_angles, int(120.0 / (max(1, args.steps) * max(t1, 1e-3)))))
     tot_b, tot_t = 0, 0.0
-    for _ in range(args.steps):
-        b, t, idx = oracle_sample(case, n, threads)
+    for k in range(args.steps):
+        b, t, idx = oracle_sample(case, n, threads, frac, seed=k)
         tot_b += b
         tot_t += t
     v = tot_b / tot_t
+    sample = (f"{n} of {len(case['angles'])} aspects per step (evenly spaced), "
+              + ("full ray grids" if frac >= 1.0 else f"a seeded {100 * frac:.3g} % of each aspect's rays"))
     line = {"impl": "reference", "metric": "ray-bounces/s", "value": v, "unit": "ray-bounces/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": dict(wl_config(case, args.workload), bvh_builder=args.builder),
-            "angles_per_s": n * args.steps / tot_t,
             "cpu_baseline": {"value": v, "unit": "ray-bounces/s", "cores": threads, "kind": "oracle",
-                             "sample": f"{n} of {len(case['angles'])} aspects per step (evenly spaced), full ray grids"},
+                             "sample": sample},
             "e2e": {"value": v, "unit": "ray-bounces/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
 # ----------------------------------------------------------------------------- GPU arm
+def sweep_value(G, torch, dev, case, tuning, steps, warmup, flush):
+    """Ray-bounces/s of another sweep (device-resident, CUDA events, L2 flushed between steps) with a fixed
+    tuning: reported beside the headline workload."""
+    stream = torch.cuda.Stream(dev)
+    ctx = G.Context(dev, stream=stream)
+    ctx.load_mesh(case["xyz"], case["tri"])
+    ctx.set_tuning(**tuning)
+    ang = np.ascontiguousarray(case["angles"], np.float64)
+    kw = dict(eta=case["eta"], max_bounces=case["max_bounces"], window=case.get("window", 0.0),
+              offset=case.get("offset", (0.0, 0.0)))
+    E = torch.empty((len(ang), len(case["freqs"]), 2, 2), dtype=torch.float64, device=f"cuda:{dev}")
+    R = torch.empty((len(ang), len(case["freqs"]), 2), dtype=torch.float64, device=f"cuda:{dev}")
+
+    def step():
+        st = ctx.trace(ang, case["spacing"], **kw)
+        ctx.po_integrate(case["freqs"], "HH,VV", E_out=E, rcs_out=R)
+        return st
+
+    for _ in range(warmup):
+        step()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 255)
+        ev[k][0].record(stream)
+        st = step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    ctx.close()
+    return {"workload": case["name"], "value": st["ray_bounces"] / (ms * 1e-3), "unit": "ray-bounces/s",
+            "ms_per_step": ms, "angles_per_s": len(ang) / (ms * 1e-3), "aspects": len(ang),
+            "ray_bounces_per_step": st["ray_bounces"], "tuning": tuning}
+
+
 def precision_report(G, torch, dev, n_az=4, freq=(8e9, 12e9, 17)):
     """Precision form: the same traced records of the aircraft at 10 GHz
     (lambda/10, B = 10, n_az azimuths at el 0) integrated with the three phase
@@ -271,7 +319,7 @@ def precision_report(G, torch, dev, n_az=4, freq=(8e9, 12e9, 17)):
             "po_ms": ms}
 
 
-def batched_vs_plain(G, torch, dev, n_req):
+def batched_vs_plain(G, torch, dev, n_req, passes=5):
     """Batched form against plain per-request SBR on the first ``n_req`` requests
     of the mixed-request workload (4096 requests, seed 2, over the sphere,
     trihedral and aircraft meshes): requests (= aspects) per second, same
@@ -319,15 +367,19 @@ def batched_vs_plain(G, torch, dev, n_req):
     batched()
     plain()
     graphed()
-    t0 = _t.perf_counter()
-    rb = batched()
-    tb = _t.perf_counter() - t0
-    t0 = _t.perf_counter()
-    plain()
-    tp = _t.perf_counter() - t0
-    t0 = _t.perf_counter()
-    rg = graphed()
-    tg = _t.perf_counter() - t0
+    tb_l, tp_l, tg_l = [], [], []
+    rb = rg = 0
+    for _ in range(passes):
+        t0 = _t.perf_counter()
+        rb = batched()
+        tb_l.append(_t.perf_counter() - t0)
+        t0 = _t.perf_counter()
+        plain()
+        tp_l.append(_t.perf_counter() - t0)
+        t0 = _t.perf_counter()
+        rg = graphed()
+        tg_l.append(_t.perf_counter() - t0)
+    tb, tp, tg = float(np.median(tb_l)), float(np.median(tp_l)), float(np.median(tg_l))
     same = True
     for m in range(3):
         if groups[m]:
@@ -340,8 +392,10 @@ def batched_vs_plain(G, torch, dev, n_req):
             "batched_requests_per_s": n_req / tb, "plain_requests_per_s": n_req / tp, "speedup": tp / tb,
             "graph_requests_per_s": n_req / tg, "graph_speedup": tp / tg, "graph_equals_batched": same,
             "batched_ray_bounces_per_s": rb / tb, "graph_ray_bounces_per_s": rg / tg,
-            "timing": "host wall clock, one pass each after one warm-up pass; graph = sbr_submit_batch replay "
-                      "(one CUDA graph per mesh, three streams) + sbr_sync"}
+            "seconds_per_pass": {"plain": [min(tp_l), tp, max(tp_l)], "batched": [min(tb_l), tb, max(tb_l)],
+                                 "graph": [min(tg_l), tg, max(tg_l)]},
+            "timing": f"host wall clock, median of {passes} passes each (min, median, max listed) after one warm-up "
+                      "pass; graph = sbr_submit_batch replay (one CUDA graph per mesh, three streams) + sbr_sync"}
 
 
 SURROGATE_DOMAINS = {
@@ -716,38 +770,62 @@ def run_sbr(args, case, ws, rank, local, pg):
     t_e2e = max_over_ranks(pg, time.perf_counter() - t0)
     e2e_value = ws * bounces * args.steps / t_e2e
 
-    # --- roofline of the transport passes (FP32 issue bound)
-    wide = ctx.tuning()["bvh_width"] == 4
-    octant = ctx.tuning()["octant"] == 1
-    raster = ctx.tuning()["raster"] == 1
-    traffic = None
-    for per_ray, setting, builder in TRAFFIC_PER_RAY.get(args.workload, []):
-        if builder == args.builder and all(ctx.tuning()[k] == v for k, v in setting.items()):
-            traffic = per_ray * stats[0]["rays_launched"]
-    pass_all_s = float(np.mean([s["pass_ms"] for s in stats])) / 1e3
-    primary_s = float(np.mean([s["primary_ms"] for s in stats])) / 1e3
-    bounce_s = pass_all_s - primary_s
-    dominant = "all"
-    if raster and bounce_s >= primary_s:
-        # the traversal of the bounce passes: node visits and their triangle tests over their time
-        dominant = "bounce"
-        # (with the hit list, bounce pass 1 also rebuilds the rasterised primary hits: listed_hits)
-        ops = (OPS_NODE4 if wide else (OPS_NODE_OCT if octant else OPS_NODE)) * cnt["node_visits"] + \
-            OPS_TRI * (cnt["tri_tests"] - cnt["raster_tests"]) + OPS_HIT * cnt["bounce_hits"] + \
-            OPS_PRIMARY_HIT * cnt["listed_hits"]
-        pass_s = bounce_s
-    elif raster:
-        # one bounce or short bounce passes: the rasterised primary pass, its cell tests and hits over its time
-        dominant = "primary"
-        ops = OPS_RASTER_CELL * cnt["raster_tests"] + OPS_PRIMARY_HIT * (cnt["valid_rays"] - cnt["listed_hits"])
-        pass_s = primary_s
-    else:
-        ops = (OPS_NODE4 if wide else (OPS_NODE_OCT if octant else OPS_NODE)) * cnt["node_visits"] + \
-            OPS_TRI * cnt["tri_tests"] + OPS_HIT * cnt["bounce_hits"] + OPS_PRIMARY_HIT * cnt["valid_rays"]
-        pass_s = pass_all_s
+    # --- roofline of the bounce passes (section 8(d) of the method's measurement plan)
+    tun = ctx.tuning()
+    wide, octant, raster = tun["bvh_width"] == 4, tun["octant"] == 1, tun["raster"] == 1
+    props = torch.cuda.get_device_properties(local)
+    n_sm = int(props.multi_processor_count)
+    l2_bytes = int(getattr(props, "L2_cache_size", 0) or 0)
+    l2_gbs = G.probe_l2_bandwidth(local, nbytes=64 << 20, passes=40)
+    fp32_tflops = G.probe_fp32_fma(local)
     pk, src = peaks()
-    peak_ops = SM_COUNT * FP32_LANES_PER_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    achieved = ops / pass_s / 1e12
+    pass_all_s = float(np.mean([s_["pass_ms"] for s_ in stats])) / 1e3
+    primary_s = float(np.mean([s_["primary_ms"] for s_ in stats])) / 1e3
+    bounce_s = pass_all_s - primary_s
+    q_bounce = cnt["ray_bounces"] - cnt["rays_launched"]  # bounce queries: all queries after the primary one
+    tri_bounce = cnt["tri_tests"] - cnt["raster_tests"]
+    n_node = cnt["node_visits"] / max(q_bounce, 1)
+    n_tri = tri_bounce / max(q_bounce, 1)
+    B_rb = BYTES_NODE * n_node + BYTES_TRI * n_tri
+    F_rb = FLOP_NODE * n_node + FLOP_TRI * n_tri
+    nt = len(case["tri"])
+    node_bytes = (nt - 1) * (128 if wide else (8 * 64 if octant else 64))
+    set_bytes = node_bytes + nt * 48
+    fits = l2_bytes > 0 and set_bytes <= l2_bytes
+    bw = l2_gbs if fits else float(pk.get("hbm_gbs", 6800.0))
+    r_mem = bw * 1e9 / B_rb
+    r_alu = fp32_tflops * 1e12 / F_rb
+    measured = q_bounce / bounce_s  # bounce queries per second of the bounce passes
+    mem_bound = r_mem <= r_alu
+    r_star = min(r_mem, r_alu)
+    traffic = None
+    for per_q, setting in TRAFFIC_PER_QUERY.get(args.workload, []):
+        if all(tun[k] == v for k, v in setting.items()):
+            traffic = per_q * q_bounce
+    roof = {"bound": ("l2" if fits else "hbm") if mem_bound else "alu",
+            "kernel": f"k_bounce (bounce passes, {'4-wide' if wide else ('binary, octant copies' if octant else 'binary')} tree)",
+            "achieved": measured * B_rb / 1e9 if mem_bound else measured * F_rb / 1e12,
+            "peak": bw if mem_bound else fp32_tflops,
+            "unit": "GB/s" if mem_bound else "TFLOP/s",
+            "frac": measured / r_star,
+            "traffic": traffic,
+            "peak_source": ((f"L2 read probe (sbr_probe_l2_bandwidth, 64 MiB x 40 passes)" if fits else
+                             f"HBM copy bandwidth, {src}") if mem_bound else
+                            "FP32 FMA probe (sbr_probe_fp32_fma, 2 FLOP per FMA)"),
+            "ray_bounces_per_s_bound": r_star, "ray_bounces_per_s_measured": measured,
+            "memory_side": {"bw_gbs": bw, "what": "l2" if fits else "hbm", "bytes_per_query": B_rb,
+                            "ray_bounces_per_s": r_mem, "frac": measured / r_mem},
+            "alu_side": {"tflops": fp32_tflops, "flop_per_query": F_rb, "ray_bounces_per_s": r_alu,
+                         "frac": measured / r_alu},
+            "node_visits_per_query": n_node, "tri_tests_per_query": n_tri, "bounce_queries_per_step": q_bounce,
+            "tree_and_triangle_bytes": set_bytes, "l2_bytes": l2_bytes, "sm_count": n_sm,
+            "pass_ms_per_step": bounce_s * 1e3,
+            "hit_arithmetic": {"bounce_hits": cnt["bounce_hits"], "primary_hits_rebuilt": cnt["listed_hits"],
+                               "ops_per_bounce_hit": OPS_HIT, "ops_per_primary_hit": OPS_PRIMARY_HIT,
+                               "t_ops_per_s": (OPS_HIT * cnt["bounce_hits"] + OPS_PRIMARY_HIT * cnt["listed_hits"])
+                               / bounce_s / 1e12},
+            "exact_decisions": {"open_tests": cnt["open_tests"], "fp64_tests": cnt["fp64_tests"],
+                                "tri_tests": cnt["tri_tests"]}}
     launches = stats[0]["kernel_launches"] + 3  # + PO work list, PO reduce and PO final
     line = {"metric": "ray-bounces/s", "value": value, "unit": "ray-bounces/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
@@ -756,26 +834,10 @@ def run_sbr(args, case, ws, rank, local, pg):
             "angles_per_s": ws * na * args.steps / t_dev,
             "rays_launched_per_step": stats[0]["rays_launched"], "ray_bounces_per_step": bounces,
             "valid_rays_per_step": stats[0]["valid_rays"],
-            "roofline": {"bound": "alu", "kernel": ("k_raster+k_vis_mask+k_primary_vis (rasterised primary pass)"
-                                                    if dominant == "primary" else
-                                                    ("k_bounce (bounce passes" if dominant == "bounce" else
-                                                     "k_primary+k_bounce (transport passes") +
-                                                    f", {'4-wide' if wide else ('binary, octant copies' if octant else 'binary')} tree)"),
-                         "achieved": achieved, "peak": peak_ops, "unit": "T FP32-op/s",
-                         "frac": achieved / peak_ops, "traffic": traffic,
-                         "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
-                                        f"{pk.get('sm_max_mhz', 2070.0):g} MHz ({src} SM clock)",
-                         "ops_per_step": ops, "node_visits": 0 if dominant == "primary" else cnt["node_visits"],
-                         "tri_tests": (cnt["raster_tests"] if dominant == "primary" else
-                                       cnt["tri_tests"] - (cnt["raster_tests"] if raster else 0)),
-                         "hits": (cnt["valid_rays"] - cnt["listed_hits"] if dominant == "primary" else
-                                  cnt["bounce_hits"] + (cnt["listed_hits"] if raster else cnt["valid_rays"])),
-                         "ops_per_unit": {"node_visit": OPS_NODE4 if wide else (OPS_NODE_OCT if octant else OPS_NODE),
-                                          "tri_test": OPS_TRI, "bounce_hit": OPS_HIT,
-                                          "primary_hit": OPS_PRIMARY_HIT, "raster_cell": OPS_RASTER_CELL},
-                         "pass_ms_per_step": pass_s * 1e3},
-            "primary": {"kernel": "k_raster+k_vis_mask+k_primary_vis (rasterised primary hits)" if raster else
-                        "k_primary (traversed)", "ms_per_step": primary_s * 1e3,
+            "roofline": roof,
+            "probes": {"l2_read_gbs": l2_gbs, "fp32_fma_tflops": fp32_tflops, "sm_count": n_sm, "l2_bytes": l2_bytes},
+            "primary": {"kernel": "k_raster+k_raster_big+k_vis_mask+k_primary_vis (rasterised primary hits)" if raster
+                        else "k_primary (traversed)", "ms_per_step": primary_s * 1e3,
                         "transport_ms_per_step": pass_all_s * 1e3, "raster_tests": cnt["raster_tests"],
                         "raster_tests_per_s": cnt["raster_tests"] / primary_s if raster and primary_s > 0 else None},
             "e2e": {"value": e2e_value, "unit": "ray-bounces/s", "h2d_bytes_per_step": int(h2d),
@@ -783,16 +845,21 @@ def run_sbr(args, case, ws, rank, local, pg):
             "gpu_launches": int(launches * args.steps),
             "autotune": tune,
             "clocks": clocks}
+    if args.workload != "trihedral" and not args.no_trihedral:
+        line["trihedral"] = sweep_value(G, torch, local, S.trihedral_case(), dict(tile_w=4, octant=1), 20, 3, flush)
     if args.batch_requests > 0:
         line["batched_vs_plain"] = batched_vs_plain(G, torch, local, args.batch_requests)
     if not args.no_precision:
         line["precision"] = precision_report(G, torch, local)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
-        b, t, idx = oracle_sample(case, args.ref_angles, threads)
+        n, frac = oracle_sample_size(case)
+        b, t, idx = oracle_sample(case, min(n, args.ref_angles), threads, frac)
         line["cpu_baseline"] = {"value": b / t, "unit": "ray-bounces/s", "cores": threads, "kind": "oracle",
-                                "sample": f"{len(idx)} of {na} aspects (evenly spaced), full ray grids, "
-                                          f"{t:.1f} s wall"}
+                                "sample": f"{len(idx)} of {na} aspects (evenly spaced), "
+                                          + ("full ray grids" if frac >= 1.0 else
+                                             f"a seeded {100 * frac:.3g} % of each aspect's rays")
+                                          + f", {b} ray-bounces in {t:.1f} s wall"}
     ctx.close()
     if rank == 0:
         print(json.dumps(line))
@@ -804,15 +871,16 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sbr", choices=["sbr", "reference"])
-    ap.add_argument("--workload", default="trihedral",
+    ap.add_argument("--workload", default="aircraft10",
                     choices=["trihedral", "sphere", "aircraft1", "aircraft3", "aircraft10", "aircraft3deep",
                              "surrogate", "gemm"])
     ap.add_argument("--ref-angles", type=int, default=24)
-    ap.add_argument("--batch-requests", type=int, default=256,
+    ap.add_argument("--batch-requests", type=int, default=4096,
                     help="mixed requests for the batched-vs-plain comparison (0 = skip)")
     ap.add_argument("--aspects", type=int, default=0,
                     help="use this many evenly spaced aspects of the sweep (small profiling cases); 0 = all")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-trihedral", action="store_true", help="skip the trihedral sweep reported beside the headline")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tuning")
     ap.add_argument("--no-precision", action="store_true", help="skip the phase-precision report")
     ap.add_argument("--builder", default="ploc", choices=["ploc", "lbvh"], help="BVH builder of the timed workload")

@@ -459,6 +459,22 @@ int sbr_po_integrate_noalloc(const void* records, const int64_t* rec_offsets, in
                              int64_t n_freq, int pol_mask, int po_mode, double* E_re_im, double* rcs_dbsm,
                              void* cuda_stream);
 
+/* Measured peaks for the traversal's roofline (no counterpart in the paper; its
+ * roofline needs the L2 bandwidth, which bounds the tree and triangle fetches
+ * while they fit in L2, and the FP32 rate of the intersection arithmetic).
+ *
+ * sbr_probe_l2_bandwidth: reads a device buffer of `bytes` (>= 1 MiB; pick a
+ * size below the L2 capacity) `passes` times (1..1000) with loads that bypass
+ * L1, after one warm-up read, and writes the read rate in GB/s (1e9 bytes/s)
+ * to *gb_per_s (host). sbr_probe_fp32_fma: eight independent FP32 fused
+ * multiply-add chains on every thread of 8 blocks of 256 per SM; writes
+ * TFLOP/s (two operations per fused multiply-add) to *tflops (host).
+ * Both run on a stream of their own on `device`, time one launch with CUDA
+ * events, allocate and free their buffers themselves, and return SBR_OK,
+ * SBR_ERR_ARG, SBR_ERR_OOM or SBR_ERR_CUDA. */
+int sbr_probe_l2_bandwidth(int device, int64_t bytes, int passes, double* gb_per_s);
+int sbr_probe_fp32_fma(int device, double* tflops);
+
 /* Ray spacing for `rays_per_lambda` rays per wavelength at frequency f_max_hz:
  * ds = c0 / (f_max_hz * rays_per_lambda); the paper's sampling rule (Sec. 4)
  * asks for ds <= lambda / 5. Returns a negative value for bad arguments. */

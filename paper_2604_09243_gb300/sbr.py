@@ -33,7 +33,8 @@ EXPORTS = ("sbr_version", "sbr_create", "sbr_destroy", "sbr_last_error", "sbr_lo
            "sbr_sync", "sbr_get_tuning", "sbr_set_tuning", "sbr_autotune", "sbr_trace_bistatic",
            "sbr_surrogate_create", "sbr_surrogate_destroy", "sbr_surrogate_last_error", "sbr_surrogate_num_params",
            "sbr_surrogate_params", "sbr_surrogate_fourier", "sbr_surrogate_train", "sbr_surrogate_grads",
-           "sbr_surrogate_predict", "sbr_gemm_bf16_tn", "sbr_gemm_bf16_tn_async")
+           "sbr_surrogate_predict", "sbr_gemm_bf16_tn", "sbr_gemm_bf16_tn_async", "sbr_probe_l2_bandwidth",
+           "sbr_probe_fp32_fma")
 
 
 class SbrError(RuntimeError):
@@ -119,6 +120,8 @@ def lib() -> C.CDLL:
         "sbr_get_hits": ([vp, i64, vp, vp, vp], C.c_int),
         "sbr_get_records": ([vp, i64, i64, vp, vp, vp, P(i64)], C.c_int),
         "sbr_spacing_for": ([d, d], d),
+        "sbr_probe_l2_bandwidth": ([C.c_int, i64, C.c_int, P(d)], C.c_int),
+        "sbr_probe_fp32_fma": ([C.c_int, P(d)], C.c_int),
         "sbr_run_batch": ([vp, P(Request), i64, P(d), i64, d, C.c_int, C.c_int, C.c_int, P(TraceOpts), vp, vp,
                            C.c_int, P(TraceStats)], C.c_int),
         "sbr_po_integrate_noalloc": ([vp, P(i64), i64, P(d), i64, C.c_int, C.c_int, vp, vp, vp], C.c_int),
@@ -148,6 +151,25 @@ def spacing_for(f_max_hz: float, rays_per_lambda: float) -> float:
     if v < 0:
         raise ValueError("frequency and rays per wavelength must be > 0")
     return v
+
+
+def probe_l2_bandwidth(device: int = 0, nbytes: int = 64 << 20, passes: int = 50) -> float:
+    """L2 read bandwidth in GB/s (sbr_probe_l2_bandwidth): a buffer below the L2
+    capacity read ``passes`` times with loads that bypass L1."""
+    v = C.c_double()
+    rc = lib().sbr_probe_l2_bandwidth(int(device), int(nbytes), int(passes), C.byref(v))
+    if rc != SBR_OK:
+        raise SbrError(rc, "sbr_probe_l2_bandwidth failed")
+    return float(v.value)
+
+
+def probe_fp32_fma(device: int = 0) -> float:
+    """FP32 fused multiply-add throughput in TFLOP/s (two operations each; sbr_probe_fp32_fma)."""
+    v = C.c_double()
+    rc = lib().sbr_probe_fp32_fma(int(device), C.byref(v))
+    if rc != SBR_OK:
+        raise SbrError(rc, "sbr_probe_fp32_fma failed")
+    return float(v.value)
 
 
 def po_integrate_noalloc(records_ptr: int, rec_offsets, freqs, pols="HH,VV", mode="vector", phase="compensated",

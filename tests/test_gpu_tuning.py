@@ -288,3 +288,17 @@ def test_raster_with_flagged_and_rasterised_aspects_in_one_chunk(G, orc):
     assert np.array_equal(res[0], res[1])
     assert np.array_equal(res[1], R1[:, 0, :])
 
+
+
+def test_roofline_probes(G):
+    """The L2 read probe sees more than the HBM copy bandwidth and the FP32 probe
+    at most the nominal rate (SMs x 128 lanes x 2 FLOP x the top SM clock)."""
+    torch = pytest.importorskip("torch")
+    props = torch.cuda.get_device_properties(0)
+    l2 = G.probe_l2_bandwidth(0, nbytes=64 << 20, passes=20)
+    fp32 = G.probe_fp32_fma(0)
+    nominal = props.multi_processor_count * 128 * 2 * 2.07e9 / 1e12
+    assert l2 > 5000.0, l2
+    assert 0.3 * nominal < fp32 <= 1.02 * nominal, (fp32, nominal)
+    with pytest.raises(G.SbrError):
+        G.probe_l2_bandwidth(0, nbytes=1024, passes=1)
