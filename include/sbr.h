@@ -425,10 +425,10 @@ int sbr_gemm_bf16_tn_async(const void* A, int lda, const void* B, int ldb, int M
 
 /* ---- allocation-free PO sum ------------------------------------------------
  * The paper has no counterpart of this call; it exists for callers that cannot
- * allocate device memory where they need the sum: work recorded into a CUDA
- * graph (no cudaMalloc while a stream is captured), plug-ins running inside an
- * application that owns all device memory, loops that must not enter the
- * allocator. It computes what sbr_po_integrate computes, with the same kernels,
+ * allocate device memory where they need the sum: plug-ins running inside an
+ * application that owns and budgets all device memory, loops that must not
+ * enter the allocator (whose calls can synchronise the device). It computes
+ * what sbr_po_integrate computes, with the same kernels,
  * from caller-provided device records, and keeps all scratch in one fixed
  * file-scope device array (about 9 MB, held by every GPU that loads the
  * library until the process exits). It calls no cudaMalloc/cudaFree.
@@ -448,9 +448,12 @@ int sbr_gemm_bf16_tn_async(const void* A, int lda, const void* B, int ldb, int M
  * blocks x n_freq x n_pol x 16 bytes <= SBR_NOALLOC_PARTIAL_BYTES; larger
  * requests return SBR_ERR_ARG with the reason in sbr_last_error(NULL).
  * The first call on a device looks up the array's device address (make that
- * first call outside any stream capture). Every call reuses the same array and
+ * first call before any stream capture). Every call reuses the same array and
  * overwrites what it reads, so calls that overlap on the GPU (other streams,
- * other host threads) race: order them. Returns once the work is enqueued. */
+ * other host threads) race: order them. The small tables are copied from
+ * pageable host memory under one lock: the call returns once the work is
+ * enqueued and its tables are read, which can mean waiting for work already
+ * queued on cuda_stream, and calls from several host threads take turns. */
 #define SBR_NOALLOC_MAX_ANGLES 4096
 #define SBR_NOALLOC_MAX_FREQ 256
 #define SBR_NOALLOC_MAX_ITEMS 16384

@@ -2,19 +2,22 @@
 //
 // sbr_po_integrate keeps its scratch (tube blocks, frequency table, FP64
 // partial sums) in buffers the context allocates. Some callers cannot allocate
-// device memory at the point where they need the sum: code recorded into a
-// CUDA graph (cudaMalloc is not allowed while a stream is being captured),
-// plug-ins that run inside a host application which owns and budgets all
-// device memory, or latency-critical loops that must not call into the
-// allocator. This entry point runs the same reduction kernels with all scratch
-// in one file-scope device array of fixed size, so it never allocates: the
-// caller passes the records and the output buffers.
+// device memory at the point where they need the sum: plug-ins that run inside
+// a host application which owns and budgets all device memory (the host hands
+// them buffers and forbids their own allocations), or latency-critical loops
+// that must not call into the allocator, whose calls can synchronise the
+// device. This entry point runs the same reduction kernels with all scratch in
+// one file-scope device array of fixed size, so it never allocates: the caller
+// passes the records and the output buffers.
 //
 // The array lives in every device that loads the library until the process
 // exits. Its device address is looked up once per device, the first time the
-// entry point runs with that device current (do that first call outside any
+// entry point runs with that device current (make that first call before any
 // stream capture). All calls share the array: calls that overlap on the GPU
-// (different streams, different host threads) race on it, so order them.
+// (different streams, different host threads) race on it, so order them. The
+// small tables are staged in host arrays under one lock and copied from
+// pageable memory, so a call can wait for work already queued on its stream,
+// and calls from several host threads take turns.
 #include <math.h>
 #include <string.h>
 
@@ -151,8 +154,9 @@ extern "C" int sbr_po_integrate_noalloc(const void* records, const int64_t* rec_
     }
     char* base = (char*)g_addr[dev];
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    // pageable sources: each copy returns once the source has been read, so the
-    // host tables can be refilled by the next call
+    // pageable sources: each copy returns once the source has been read (it may
+    // first wait for the stream's earlier work), so the host tables can be
+    // refilled by the next call
     if (ni > 0) e = cudaMemcpyAsync(base + kOffItems, g_items, sizeof(PoItem) * (size_t)ni, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(base + kOffOff, g_angles, sizeof(PoAngle) * (size_t)n_angles, cudaMemcpyHostToDevice, st);

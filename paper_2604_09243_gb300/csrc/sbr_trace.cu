@@ -276,48 +276,49 @@ __device__ __forceinline__ void tf_dot3(float3 a, float3 b, float& hi, float& lo
 
 // Hit distance stored with a hit: t32 = fl32(((v0 - o) . n) / (d . n)), the
 // distance along the ray to the plane of the FP32 unit normal n through v0,
-// rounded once: h = v0.n and d.n as two-float sums (exact products, compensated
-// sums) and 1 / d.n are taken once per (direction, triangle) -- once per
-// (aspect, triangle) for the parallel primary rays -- then per origin o the
-// numerator h - o.n as a two-float sum, a quotient within a few units of the
-// last place, its remainder and one correction.
+// rounded once. d.n as a two-float sum (exact products, compensated sum) and
+// its reciprocal are taken once per (direction, triangle) -- once per (aspect,
+// triangle) for the parallel primary rays; per origin o, v0 - o exactly as a
+// two-float vector (TwoSum), the numerator (v0 - o).n as a two-float sum (its
+// error relative to |v0 - o|, so short hops keep their precision), a quotient
+// within a few units of the last place, its remainder and one correction.
 struct PlaneKey {
     float3 n;
-    float dh, dl, rd, hh, hl;
+    float dh, dl, rd;
 };
 
-__device__ __forceinline__ PlaneKey plane_key(const float4* __restrict__ nrm, int k, float4 P, float3 d)
+__device__ __forceinline__ PlaneKey plane_key(const float4* __restrict__ nrm, int k, float3 d)
 {
     PlaneKey K;
     const float4 N = __ldg(nrm + k);
     K.n = make_float3(N.x, N.y, N.z);
     tf_dot3(d, K.n, K.dh, K.dl);
     K.rd = __frcp_rn(K.dh);
-    tf_dot3(make_float3(P.x, P.y, P.z), K.n, K.hh, K.hl);
     return K;
 }
 
-// t32 for origin o (tfb when d.n is exactly 0)
-__device__ __forceinline__ float plane_key_t(const PlaneKey& K, float3 o, float tfb)
+// t32 for origin o and triangle vertex v0 (tfb when d.n is exactly 0)
+__device__ __forceinline__ float plane_key_t(const PlaneKey& K, float3 v0, float3 o, float tfb)
 {
     if (K.dh == 0.f) return tfb;
-    float oh, ol, nh, nl;
-    tf_dot3(o, K.n, oh, ol);
-    two_sum(K.hh, -oh, nh, nl);
-    nl = __fadd_rn(nl, __fsub_rn(K.hl, ol));
+    float3 a, b;
+    two_sum(v0.x, -o.x, a.x, b.x);
+    two_sum(v0.y, -o.y, a.y, b.y);
+    two_sum(v0.z, -o.z, a.z, b.z);
+    float nh, nl;
+    tf_dot3(a, K.n, nh, nl);
+    nl = __fmaf_rn(b.x, K.n.x, __fmaf_rn(b.y, K.n.y, __fmaf_rn(b.z, K.n.z, nl)));
     const float q = __fmul_rn(nh, K.rd);
     const float r = __fadd_rn(__fmaf_rn(-q, K.dh, nh), __fmaf_rn(-q, K.dl, nl));
     return __fmaf_rn(r, K.rd, q);
 }
 
-struct TriRefs {
-    const float4* rec;          // records (v0, id), (e1, bUV), (e2, bD)
-    const float4* nrm;          // FP32 unit normals
-    const float4* v12;          // exact v1, v2
-    unsigned long long* stats;  // counting runs: open and FP64 decisions
-};
+// The triangle data a query reads (records, normals, exact vertices, counters)
+// are those of the kernel's TraceArgs, read from its parameter space where
+// needed rather than held in registers through the traversal.
+using TriRefs = TraceArgs;
 
-__device__ __forceinline__ TriRefs tri_refs(const TraceArgs& a) { return TriRefs{a.tris, a.tri_nrm, a.tri_v12, a.stats}; }
+__device__ __forceinline__ const TraceArgs& tri_refs(const TraceArgs& a) { return a; }
 
 // counting runs: one test left open by the filter, decided in FP64 or not
 __device__ __forceinline__ void count_open(unsigned long long* stats, int r)
@@ -330,9 +331,9 @@ __device__ __forceinline__ void count_open(unsigned long long* stats, int r)
 // (rounding) + u L / |d.n| (plane of n32 against the triangle's own), u L <= bUV / 24
 __device__ __forceinline__ float key_of(const TriRefs& tr, int k, float3 o, float3 d, float tfb, float& slack)
 {
-    const float4 A = __ldg(tr.rec + 3 * (size_t)k), B = __ldg(tr.rec + 3 * (size_t)k + 1);
-    const PlaneKey K = plane_key(tr.nrm, k, A, d);
-    const float t = plane_key_t(K, o, tfb);
+    const float4 A = __ldg(tr.tris + 3 * (size_t)k), B = __ldg(tr.tris + 3 * (size_t)k + 1);
+    const PlaneKey K = plane_key(tr.tri_nrm, k, d);
+    const float t = plane_key_t(K, make_float3(A.x, A.y, A.z), o, tfb);
     slack = __fmaf_rn(2.f * kU, fabsf(t), __fdividef(0.08f * B.w, fabsf(K.dh)));
     return t;
 }
@@ -391,13 +392,13 @@ __device__ __forceinline__ void leaf_test(const TriRefs& tr, int ref, float3 o, 
         const int k = first + q;
         if (kCount) ++ntri;
         if (k == skip) continue;
-        const float4* tp = tr.rec + 3 * (size_t)k;
+        const float4* tp = tr.tris + 3 * (size_t)k;
         const float4 A = __ldg(tp), B = __ldg(tp + 1), C = __ldg(tp + 2);
         float tc = 0.f, et = FLT_MAX;
         const int f = tri_filter(A, B, C, o, d, tc, et);
         if (f == 0) continue;
         if (f >= 2) {
-            const int r = tri_refine(tr.rec, tr.v12, k, o, d, f + 2, tc);
+            const int r = tri_refine(tr.tris, tr.tri_v12, k, o, d, f + 2, tc);
             if (kCount) count_open(tr.stats, r);
             if (!(r & 1)) continue;
             et = FLT_MAX;
@@ -1248,7 +1249,7 @@ __device__ __forceinline__ void raster_cell(const RasterGrid& G, const TraceArgs
         if (count) count_open(a.stats, r);
         if (!(r & 1)) return;
     }
-    const float th = plane_key_t(K, o, tc);
+    const float th = plane_key_t(K, R.v0, o, tc);
     if (th >= 0.f && th <= FLT_MAX) {
         const int tw = G.tw, sh = 5 - tw;  // tile of W = 2^tw by H = 2^sh rays
         const int bu = i >> tw, bv = j >> sh;
@@ -1258,7 +1259,7 @@ __device__ __forceinline__ void raster_cell(const RasterGrid& G, const TraceArgs
 }
 
 // A triangle of the flattened rasterisation and everything its cells need,
-// one per lane in shared memory (53 words, an odd stride: the lanes' writes hit
+// one per lane in shared memory (51 words, an odd stride: the lanes' writes hit
 // distinct banks, and lanes reading one triangle's fields share a broadcast).
 struct RasterItem {
     float3 p0, du, dv;  // the aspect's ray grid
@@ -1271,7 +1272,7 @@ struct RasterItem {
     unsigned orig;         // original triangle index
     int t, ang;            // reordered triangle and aspect
 };
-static_assert(sizeof(RasterItem) == 53 * 4, "RasterItem layout");
+static_assert(sizeof(RasterItem) == 51 * 4, "RasterItem layout");
 constexpr int kRasterWarps = 8;    // warps of a k_raster block
 constexpr int kRasterFlat = 512;   // cells of a triangle the warps flatten; larger ones go to k_raster_big
 constexpr size_t kRasterSmem = sizeof(RasterItem) * 32 * kRasterWarps;
@@ -1327,7 +1328,7 @@ __global__ void __launch_bounds__(256, 4) k_raster(const TraceArgs a, int n_tri,
                         it.nbu = G.nbu;
                         it.tw = G.tw;
                         it.R = R;
-                        it.K = plane_key(a.tri_nrm, t, P, G.d);
+                        it.K = plane_key(a.tri_nrm, t, G.d);
                         tri_cell_edges(A, cell_scale(A), P, B, C, i0, i1, j0, j1, it.E);
                         it.i0 = i0;
                         it.j0 = j0;
@@ -1392,7 +1393,7 @@ __global__ void __launch_bounds__(256, 4) k_raster(const TraceArgs a, int n_tri,
                 if (count) count_open(a.stats, r);
                 if (!(r & 1)) continue;
             }
-            const float th = plane_key_t(it.K, o, tc);
+            const float th = plane_key_t(it.K, it.R.v0, o, tc);
             if (th >= 0.f && th <= FLT_MAX) {
                 const int tw = it.tw, sh = 5 - tw;  // tile of W = 2^tw by H = 2^sh rays
                 const int bu = i >> tw, bv = j >> sh;
@@ -1441,7 +1442,7 @@ __global__ void __launch_bounds__(256, 3) k_raster_big(const TraceArgs a, unsign
         if (!(R.bd >= 0.f)) continue;  // warp-uniform
         const unsigned orig = (unsigned)__float_as_int(P.w);
         unsigned long long* vrow = vis + a.ray_off[ad];
-        const PlaneKey K = plane_key(a.tri_nrm, td, P, G.d);
+        const PlaneKey K = plane_key(a.tri_nrm, td, G.d);
         CellEdges E;
         tri_cell_edges(A, cell_scale(A), P, B, C, i0, i1, j0, j1, E);
         const int ncell = w * h;
@@ -1677,6 +1678,30 @@ __device__ __forceinline__ void primary_state(const TraceArgs& a, unsigned g, in
     record_hit(a, r, h);
 }
 
+// Origin, direction and triangle after the first hit of a rasterised primary
+// ray (ray g of the chunk, aspect ang): the stored-state steps of apply_hit
+// alone (hit point, orientation, reflection, offset origin).
+__device__ __forceinline__ void primary_geom(const TraceArgs& a, unsigned g, int ang, float3& o, float3& d, int& last)
+{
+    const AngleDev& A = a.angles[ang];
+    int i, j;
+    tile_ij(A, (int)((long long)g - a.ray_off[ang]), i, j);
+    const unsigned long long key = __ldcs(a.vis + g);
+    const float t = __uint_as_float((unsigned)(key >> 32));
+    const int k = __ldg(a.tri_pos + (int)(unsigned)key);
+    const float3 o0 = primary_origin(A, i, j), d0 = make_float3(A.dir[0], A.dir[1], A.dir[2]);
+    const float3 x = make_float3(__fmaf_rn(t, d0.x, o0.x), __fmaf_rn(t, d0.y, o0.y), __fmaf_rn(t, d0.z, o0.z));
+    const float4 N4 = __ldg(a.tri_nrm + k);
+    const float3 n = make_float3(N4.x, N4.y, N4.z);
+    float dn, dnl;
+    tf_dot3(d0, n, dn, dnl);
+    const float3 nf = dn < 0.f ? n : make_float3(-n.x, -n.y, -n.z);
+    const float m2 = -2.f * dn;
+    d = make_float3(__fmaf_rn(m2, n.x, d0.x), __fmaf_rn(m2, n.y, d0.y), __fmaf_rn(m2, n.z, d0.z));
+    o = make_float3(__fmaf_rn(A.eps, nf.x, x.x), __fmaf_rn(A.eps, nf.y, x.y), __fmaf_rn(A.eps, nf.z, x.z));
+    last = k;
+}
+
 template <bool kCount, int kStack, int kMode, bool kBi = false, bool kList = false>
 __global__ void __launch_bounds__(kTraceThreads, 4) k_bounce(const TraceArgs a)
 {
@@ -1699,16 +1724,19 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_bounce(const TraceArgs a)
         r.d = make_float3(0.f, 0.f, 1.f);
         r.last = -1;
         const bool listed = kList && idx < n_list;
+        uint2 e = make_uint2(0u, 0u);
         if (listed) {
-            const uint2 e = a.hit_list[idx];
-            primary_state(a, e.x, (int)e.y, r);
+            // only the geometry during the query; the full state after it
+            e = a.hit_list[idx];
+            primary_geom(a, e.x, (int)e.y, r.o, r.d, r.last);
             if (kCount) ++nlist;
         }
         else if (active) load_geom(a.q_in, idx, r);
         Hit h;
         query<kCount, kStack, kMode>(a, active, r.o, r.d, r.last, h, nvis, ntri, ovf);
         if (active) {
-            if (!listed) load_payload(a.q_in, idx, r);
+            if (listed) primary_state(a, e.x, (int)e.y, r);
+            else load_payload(a.q_in, idx, r);
             const AngleDev& A = a.angles[r.angle];
             ++nq;
             if (h.k < 0) {
