@@ -329,13 +329,33 @@ __device__ __forceinline__ void count_open(unsigned long long* stats, int r)
 
 // t32 of reordered triangle k and its error bound: |t32 - exact t| <= u t32
 // (rounding) + u L / |d.n| (plane of n32 against the triangle's own), u L <= bUV / 24
-__device__ __forceinline__ float key_of(const TriRefs& tr, int k, float3 o, float3 d, float tfb, float& slack)
+__device__ __noinline__ float key_of(const TriRefs& tr, int k, float3 o, float3 d, float tfb, float& slack)
 {
     const float4 A = __ldg(tr.tris + 3 * (size_t)k), B = __ldg(tr.tris + 3 * (size_t)k + 1);
     const PlaneKey K = plane_key(tr.tri_nrm, k, d);
     const float t = plane_key_t(K, make_float3(A.x, A.y, A.z), o, tfb);
     slack = __fmaf_rn(2.f * kU, fabsf(t), __fdividef(0.08f * B.w, fabsf(K.dh)));
     return t;
+}
+
+// Two candidates whose distance intervals overlap: their stored distances are
+// computed and compared (rare; kept out of the traversal loop's registers).
+__device__ __noinline__ void resolve_overlap(const TriRefs& tr, int k, int orig, float tc, float3 o, float3 d, Hit& h)
+{
+    float sl;
+    if (h.key < 0.f) {
+        h.key = key_of(tr, h.k, o, d, h.t, sl);
+        h.t = __fadd_rn(h.key, sl);
+        h.lo = __fsub_rn(h.key, sl);
+    }
+    const float t = key_of(tr, k, o, d, tc, sl);
+    if (t < h.key || (t == h.key && orig < h.orig)) {
+        h.key = t;
+        h.t = __fadd_rn(t, sl);
+        h.lo = __fsub_rn(t, sl);
+        h.k = k;
+        h.orig = orig;
+    }
 }
 
 // The closest hit is the smallest (t32, original triangle index). A certain
@@ -355,20 +375,7 @@ __device__ __forceinline__ void consider_hit(const TriRefs& tr, int k, int orig,
         h.orig = orig;
         return;
     }
-    float sl;
-    if (h.key < 0.f) {
-        h.key = key_of(tr, h.k, o, d, h.t, sl);
-        h.t = __fadd_rn(h.key, sl);
-        h.lo = __fsub_rn(h.key, sl);
-    }
-    const float t = key_of(tr, k, o, d, tc, sl);
-    if (t < h.key || (t == h.key && orig < h.orig)) {
-        h.key = t;
-        h.t = __fadd_rn(t, sl);
-        h.lo = __fsub_rn(t, sl);
-        h.k = k;
-        h.orig = orig;
-    }
+    resolve_overlap(tr, k, orig, tc, o, d, h);
 }
 
 // after the traversal: the closest hit's t32 in h.t
