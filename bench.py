@@ -570,6 +570,28 @@ def surrogate_eval(G, torch, ctx, dom, epochs=60, batch=2048, spread_db=1.0, sca
             "bands": bands}
 
 
+def surrogate_leg(G, torch, dev, ctx=None, scale=0.25, epochs=30):
+    """Bounded surrogate run beside the headline: the configured sweep space (C5) and the dense nose-on patch
+    at a quarter of the sample counts and half the epochs (each domain a few tens of seconds). Reports the
+    served fraction, the served error against plain SBR per frequency band, and the hybrid's speed against
+    plain SBR on the held-out points."""
+    own = ctx is None
+    if own:
+        xyz, tri = S.aircraft(seed=1)
+        ctx = G.Context(dev)
+        ctx.load_mesh(xyz, tri)
+    out = {"scale": scale, "epochs": epochs}
+    for name in ("full", "patch_dense"):
+        r = surrogate_eval(G, torch, ctx, dict(SURROGATE_DOMAINS[name]), epochs=epochs, scale=scale)
+        out[name] = {k: r[k] for k in ("domain", "training_samples", "rays_per_wavelength", "fourier_sigma",
+                                       "served_fraction", "served_median_db_error", "served_within_0.5dB",
+                                       "all_median_db_error", "hybrid_vs_plain", "plain_sbr_points_per_s",
+                                       "hybrid_points_per_s", "lattice_served_fraction", "bands", "train_s")}
+    if own:
+        ctx.close()
+    return out
+
+
 def run_surrogate(args, ws, rank, local, pg):
     """Surrogate-with-fallback against plain SBR on the aircraft (one replica per rank)."""
     import torch
@@ -845,6 +867,8 @@ def run_sbr(args, case, ws, rank, local, pg):
             "gpu_launches": int(launches * args.steps),
             "autotune": tune,
             "clocks": clocks}
+    if not args.no_surrogate:
+        line["surrogate"] = surrogate_leg(G, torch, local, ctx if args.workload.startswith("aircraft") else None)
     if args.workload != "trihedral" and not args.no_trihedral:
         line["trihedral"] = sweep_value(G, torch, local, S.trihedral_case(), dict(tile_w=4, octant=1), 20, 3, flush)
     if args.batch_requests > 0:
@@ -881,6 +905,7 @@ def main():
                     help="use this many evenly spaced aspects of the sweep (small profiling cases); 0 = all")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-trihedral", action="store_true", help="skip the trihedral sweep reported beside the headline")
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the bounded surrogate leg beside the headline")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tuning")
     ap.add_argument("--no-precision", action="store_true", help="skip the phase-precision report")
     ap.add_argument("--builder", default="ploc", choices=["ploc", "lbvh"], help="BVH builder of the timed workload")

@@ -48,25 +48,85 @@ def _samples(n, seed):
     return rng, x
 
 
+def _fp32(a):
+    return np.asarray(a, np.float64).astype(np.float32).astype(np.float64)
+
+
+def _bf16(a):
+    """Round to BF16 (nearest, ties to even) from the FP32 value, as the kernels do."""
+    u = np.asarray(a, np.float64).astype(np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _bf16_network(p, B, x, t, width, depth, nf):
+    """The FP64 reference network with the surrogate kernels' roundings: FP32
+    inputs, BF16 Fourier features, BF16 weights and activations into every hidden
+    GEMM, FP32 pre-activations and head, BF16 deltas (dz) out of every backward
+    step; products and sums otherwise exact. Returns (loss, flat gradient)."""
+    Ws = mlp.unpack(p, width, depth, nf)
+    arg = _fp32(_fp32(mlp.encode(x)) @ _fp32(B).T)
+    h = [_bf16(np.concatenate([np.sin(2 * np.pi * arg), np.cos(2 * np.pi * arg)], 1))]
+    zs = []
+    for l in range(depth):
+        W, b = Ws[l]
+        z = _fp32(h[-1] @ _bf16(W).T + _fp32(b))
+        zs.append(z)
+        h.append(_bf16(mlp.gelu(z)))
+    Wh, bh = _fp32(Ws[depth][0]), _fp32(Ws[depth][1])
+    y = _fp32(h[-1] @ Wh.T + bh)
+    t = np.asarray(t, np.float64)
+    dy = _fp32(2.0 * (y - t) / y.size)
+    grads = [None] * (depth + 1)
+    grads[depth] = (dy.T @ h[depth], dy.sum(0))
+    dz = _bf16(_fp32(dy @ Wh) * mlp.gelu_grad(zs[depth - 1]))
+    for l in range(depth - 1, -1, -1):
+        grads[l] = (dz.T @ h[l], dz.sum(0))
+        if l > 0:
+            dz = _bf16(_fp32(dz @ _bf16(Ws[l][0])) * mlp.gelu_grad(zs[l - 1]))
+    loss = float(np.mean((y - t) ** 2))
+    return loss, np.concatenate([np.concatenate([gw.ravel(), gb]) for gw, gb in grads])
+
+
 @pytest.mark.parametrize("width,depth,nf", [(128, 2, 128), (512, 6, 256)])
 def test_gradients_against_fp64_reference(G, width, depth, nf):
+    """Loss and gradients of the tensor-core forward and backward against the FP64
+    reference network (oracle/mlp.py). The bound comes from BF16 itself: the same
+    network with the kernels' BF16 and FP32 roundings (in FP64 otherwise) moves
+    each layer's gradient by some amount from the exact one; the GPU must stay
+    within twice that plus 1e-3 of the layer's largest entry, and within
+    1e-3 per layer back from the output of the rounded network (FP32 sums and
+    library functions left)."""
     s = G.Surrogate(0, n_members=1, width=width, depth=depth, n_fourier=nf, fourier_sigma=2.0, seed=3)
     rng, x = _samples(512, 4)
     t = rng.normal(0, 1, (512, 4))
     p = s.params(0).astype(np.float64)
     B = s.fourier(0).astype(np.float64)
     loss_g, g = s.grads(x, t)
+    s.close()
     loss_o, go, _ = mlp.loss_and_grads(p, B, x, t, width, depth, nf)
-    assert abs(loss_g - loss_o) <= 0.02 * loss_o
+    loss_b, gb = _bf16_network(p, B, x, t, width, depth, nf)
+    assert abs(loss_g - loss_b) <= 1e-4 * loss_o
+    assert abs(loss_g - loss_o) <= 1.5 * abs(loss_b - loss_o) + 1e-4 * loss_o
     lay, n = mlp.layout(width, depth, nf)
-    assert n == s.n_params
+    assert n == len(g)
+    g = g.astype(np.float64)
+    rows = []
     for l, (o, shp, ob, nb) in enumerate(lay):
         for a, b in ((o, o + shp[0] * shp[1]), (ob, ob + nb)):
-            u, v = g[a:b].astype(np.float64), go[a:b]
-            cos = np.dot(u, v) / (np.linalg.norm(u) * np.linalg.norm(v) + 1e-300)
-            assert cos > 0.99, (l, cos)
-            assert abs(np.linalg.norm(u) / np.linalg.norm(v) - 1) < 0.05, l
-    s.close()
+            scale = np.abs(go[a:b]).max()
+            e_gpu = np.abs(g[a:b] - go[a:b]).max() / scale
+            e_bf = np.abs(gb[a:b] - go[a:b]).max() / scale
+            e_emu = np.abs(g[a:b] - gb[a:b]).max() / scale
+            rows.append((l, e_gpu, e_bf, e_emu))
+    print("per layer (W, b): max |GPU - FP64| / max|g|, BF16 bound, max |GPU - rounded network| / max|g|")
+    for r in rows:
+        print("  layer %d: %.2e  %.2e  %.2e" % r)
+    for l, e_gpu, e_bf, e_emu in rows:
+        # the GPU's FP32 sums round a few entries to the other BF16 neighbour than the FP64 sums of the
+        # rounded network do; those differences add up layer by layer on the way back from the output
+        assert e_emu <= 1e-3 * (depth - l + 1), (l, e_emu)
+        assert e_gpu <= 2.0 * e_bf + 1e-3, (l, e_gpu, e_bf)
 
 
 def test_training_reduces_loss_and_ensemble_spread(G):
