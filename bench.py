@@ -60,7 +60,10 @@ OPS_PRIMARY_HIT = 185
 # DRAM bytes per bounce query of the bounce passes (dram__bytes_read.sum + dram__bytes_write.sum over the
 # k_bounce launches of one ncu capture, divided by their queries), per workload and setting; scaled by the
 # bounce queries of a step. None where no capture of the current kernels exists.
-TRAFFIC_PER_QUERY = {}
+TRAFFIC_PER_QUERY = {
+    # k_bounce, warm L2 (ncu --cache-control none), 36 of the 360 aspects, five identical sweeps
+    "aircraft10": [(96.3, {"bvh_width": 2, "octant": 0, "packet": 0})],
+}
 
 
 def peaks():
@@ -840,6 +843,7 @@ def run_sbr(args, case, ws, rank, local, pg):
             "alu_side": {"tflops": fp32_tflops, "flop_per_query": F_rb, "ray_bounces_per_s": r_alu,
                          "frac": measured / r_alu},
             "node_visits_per_query": n_node, "tri_tests_per_query": n_tri, "bounce_queries_per_step": q_bounce,
+            "lane_occupancy_bound": cnt["node_visits"] / max(cnt["warp_node_visits"], 1),
             "tree_and_triangle_bytes": set_bytes, "l2_bytes": l2_bytes, "sm_count": n_sm,
             "pass_ms_per_step": bounce_s * 1e3,
             "hit_arithmetic": {"bounce_hits": cnt["bounce_hits"], "primary_hits_rebuilt": cnt["listed_hits"],

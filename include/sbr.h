@@ -115,6 +115,9 @@ typedef struct {
     int64_t open_tests;      /* only with SBR_TRACE_COUNT_VISITS: triangle tests whose FP32 filter left the decision
                                 open (taken again near the triangle, then in FP64 if still open) */
     int64_t fp64_tests;      /* only with SBR_TRACE_COUNT_VISITS: of those, the tests decided in FP64 */
+    int64_t warp_node_visits; /* only with SBR_TRACE_COUNT_VISITS: over the bounce passes' warp-wide queries, 32 x the
+                                 largest node visit count among the warp's lanes (node_visits of the bounce passes
+                                 divided by it is the lane occupancy their traversal lengths allow) */
 } sbr_trace_stats;
 
 /* Per-aspect ray grid (Eq. L1-L3) exactly as sbr_trace generates it. */

@@ -839,6 +839,7 @@ int finish_stats(sbr_ctx* c, const TraceRun& R, const unsigned long long* hs_sta
         stats->listed_hits = (int64_t)hs_stats[kStatListed];
         stats->open_tests = (int64_t)hs_stats[kStatOpen];
         stats->fp64_tests = (int64_t)hs_stats[kStatFp64];
+        stats->warp_node_visits = (int64_t)hs_stats[kStatWarpNodes];
         stats->pass_ms = 0.0;
         stats->primary_ms = 0.0;
         for (size_t i = 0; R.timed && i + 1 < R.n_ev; i += 2) {
@@ -1565,6 +1566,7 @@ int sbr_sync(sbr_ctx* c, sbr_trace_stats* stats)
         stats->listed_hits = (int64_t)hs[kStatListed];
         stats->open_tests = (int64_t)hs[kStatOpen];
         stats->fp64_tests = (int64_t)hs[kStatFp64];
+        stats->warp_node_visits = (int64_t)hs[kStatWarpNodes];
         stats->stack_overflows = (int64_t)hs[kStatOverflow];
         stats->kernel_launches = P.n_launch;
         stats->pass_launches = P.n_pass;

@@ -79,7 +79,7 @@ static_assert(sizeof(Record) == 32, "Record layout");
 
 // stats counters on the device (unsigned long long each)
 enum { kStatQueries = 0, kStatNodes = 1, kStatTris = 2, kStatOverflow = 3, kStatRaster = 4, kStatHits = 5, kStatListed = 6,
-       kStatOpen = 7, kStatFp64 = 8, kStatCount = 9 };
+       kStatOpen = 7, kStatFp64 = 8, kStatWarpNodes = 9, kStatCount = 10 };
 
 // ---------------------------------------------------------------- launchers
 // All launchers enqueue on `st` and return the launch error (cudaSuccess if none).

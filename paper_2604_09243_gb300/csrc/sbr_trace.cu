@@ -972,7 +972,7 @@ __device__ __forceinline__ void push(const TraceArgs& a, bool want, const Ray& r
 
 template <bool kCount>
 __device__ __forceinline__ void flush_stats(const TraceArgs& a, unsigned q, unsigned nvis, unsigned ntri, bool ovf,
-                                            unsigned nhit = 0, unsigned nlist = 0)
+                                            unsigned nhit = 0, unsigned nlist = 0, unsigned long long wvis = 0)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -992,6 +992,7 @@ __device__ __forceinline__ void flush_stats(const TraceArgs& a, unsigned q, unsi
             atomicAdd(a.stats + kStatTris, (unsigned long long)ntri);
             if (nhit) atomicAdd(a.stats + kStatHits, (unsigned long long)nhit);
             if (nlist) atomicAdd(a.stats + kStatListed, (unsigned long long)nlist);
+            if (wvis) atomicAdd(a.stats + kStatWarpNodes, wvis);
         }
         if (ov) atomicAdd(a.stats + kStatOverflow, (unsigned long long)__popc(ov));
     }
@@ -1717,6 +1718,7 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_bounce(const TraceArgs a)
     const unsigned n_list = kList ? *a.list_count : 0u;  // entries below n_list come from the hit list
     const bool escape_pass = a.bounce >= a.max_bounces;
     unsigned nq = 0, nvis = 0, ntri = 0, nhit = 0, nlist = 0;  // hits processed, hits rebuilt (counting runs)
+    unsigned long long wvis = 0;  // counting runs: 32 x the warp's largest node visit count, per query
     bool ovf = false;
     while (true) {
         unsigned long long base = 0;
@@ -1740,7 +1742,9 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_bounce(const TraceArgs a)
         }
         else if (active) load_geom(a.q_in, idx, r);
         Hit h;
+        const unsigned nvis0 = nvis;
         query<kCount, kStack, kMode>(a, active, r.o, r.d, r.last, h, nvis, ntri, ovf);
+        if (kCount) wvis += 32ull * __reduce_max_sync(kFull, nvis - nvis0);
         if (active) {
             if (listed) primary_state(a, e.x, (int)e.y, r);
             else load_payload(a.q_in, idx, r);
@@ -1761,7 +1765,7 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_bounce(const TraceArgs a)
         }
         push(a, again, r);
     }
-    flush_stats<kCount>(a, nq, nvis, ntri, ovf, nhit, nlist);
+    flush_stats<kCount>(a, nq, nvis, ntri, ovf, nhit, nlist, (threadIdx.x & 31) == 0 ? wvis : 0ull);
 }
 
 // every ray of the queue writes its record (B_max = 1 without the escape check)

@@ -72,7 +72,7 @@ class TraceStats(C.Structure):
                 ("stack_overflows", C.c_int64), ("kernel_launches", C.c_int64), ("pass_launches", C.c_int64),
                 ("pass_ms", C.c_double), ("raster_tests", C.c_int64), ("primary_ms", C.c_double),
                 ("bounce_hits", C.c_int64), ("listed_hits", C.c_int64), ("open_tests", C.c_int64),
-                ("fp64_tests", C.c_int64)]
+                ("fp64_tests", C.c_int64), ("warp_node_visits", C.c_int64)]
 
     def as_dict(self):
         return {k: (float if k.endswith("_ms") else int)(getattr(self, k)) for k, _ in self._fields_}
