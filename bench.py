@@ -51,6 +51,9 @@ import sbr_inputs as S  # noqa: E402
 # of two children) + 30 per triangle test (Moller-Trumbore).
 BYTES_NODE, BYTES_TRI = 32, 48
 FLOP_NODE, FLOP_TRI = 28, 30
+# one rasterised cell test: the ray's FP32 origin (12) and the triangle test with the per-(aspect, triangle)
+# constants (38), FMA counted as 2; the roofline of workloads without bounce passes (B = 1)
+FLOP_CELL = 50
 # FP32 operations of the per-hit arithmetic (apply_hit: hit point, path, normal orientation, receiver path
 # term, H field, tube area, the vector PO terms and coefficients, scalar coefficient, PEC field update,
 # reflection, new origin), reported beside the roofline: 157 per hit of a bounce pass, 185 for a primary hit
@@ -809,18 +812,21 @@ def run_sbr(args, case, ws, rank, local, pg):
     bounce_s = pass_all_s - primary_s
     q_bounce = cnt["ray_bounces"] - cnt["rays_launched"]  # bounce queries: all queries after the primary one
     tri_bounce = cnt["tri_tests"] - cnt["raster_tests"]
+    if q_bounce <= 0 and not raster:  # B = 1 with traversed primary rays: the primary pass is the traversal
+        q_bounce, tri_bounce, bounce_s = cnt["rays_launched"], cnt["tri_tests"], primary_s
     n_node = cnt["node_visits"] / max(q_bounce, 1)
     n_tri = tri_bounce / max(q_bounce, 1)
     B_rb = BYTES_NODE * n_node + BYTES_TRI * n_tri
     F_rb = FLOP_NODE * n_node + FLOP_TRI * n_tri
     nt = len(case["tri"])
-    node_bytes = (nt - 1) * (128 if wide else (8 * 64 if octant else 64))
+    tree = ctx.bvh_info()  # nodes reachable from the root (the node array holds no others)
+    node_bytes = tree["n_nodes4"] * 128 if wide else tree["n_nodes"] * (8 * 64 if octant else 64)
     set_bytes = node_bytes + nt * 48
     fits = l2_bytes > 0 and set_bytes <= l2_bytes
     bw = l2_gbs if fits else float(pk.get("hbm_gbs", 6800.0))
-    r_mem = bw * 1e9 / B_rb
-    r_alu = fp32_tflops * 1e12 / F_rb
-    measured = q_bounce / bounce_s  # bounce queries per second of the bounce passes
+    r_mem = bw * 1e9 / max(B_rb, 1e-9)
+    r_alu = fp32_tflops * 1e12 / max(F_rb, 1e-9)
+    measured = q_bounce / bounce_s if bounce_s > 0 else 0.0  # bounce queries per second of the bounce passes
     mem_bound = r_mem <= r_alu
     r_star = min(r_mem, r_alu)
     traffic = None
@@ -844,14 +850,26 @@ def run_sbr(args, case, ws, rank, local, pg):
                          "frac": measured / r_alu},
             "node_visits_per_query": n_node, "tri_tests_per_query": n_tri, "bounce_queries_per_step": q_bounce,
             "lane_occupancy_bound": cnt["node_visits"] / max(cnt["warp_node_visits"], 1),
-            "tree_and_triangle_bytes": set_bytes, "l2_bytes": l2_bytes, "sm_count": n_sm,
+            "tree_and_triangle_bytes": set_bytes, "tree_nodes": tree["n_nodes4"] if wide else tree["n_nodes"],
+            "l2_bytes": l2_bytes, "sm_count": n_sm,
             "pass_ms_per_step": bounce_s * 1e3,
             "hit_arithmetic": {"bounce_hits": cnt["bounce_hits"], "primary_hits_rebuilt": cnt["listed_hits"],
                                "ops_per_bounce_hit": OPS_HIT, "ops_per_primary_hit": OPS_PRIMARY_HIT,
                                "t_ops_per_s": (OPS_HIT * cnt["bounce_hits"] + OPS_PRIMARY_HIT * cnt["listed_hits"])
-                               / bounce_s / 1e12},
+                               / max(bounce_s, 1e-12) / 1e12},
             "exact_decisions": {"open_tests": cnt["open_tests"], "fp64_tests": cnt["fp64_tests"],
                                 "tri_tests": cnt["tri_tests"]}}
+    if q_bounce <= 0:
+        # B = 1 with rasterised primary hits: no traversal runs, and the rasterisation is the dominant kernel
+        # (ALU: FLOP_CELL per cell test against the FP32 FMA probe)
+        ach = cnt["raster_tests"] * FLOP_CELL / primary_s / 1e12
+        roof = {"bound": "alu", "kernel": "k_raster+k_raster_big (rasterised primary hits; no bounce pass at B = 1)",
+                "achieved": ach, "peak": fp32_tflops, "unit": "TFLOP/s", "frac": ach / fp32_tflops, "traffic": None,
+                "peak_source": "FP32 FMA probe (sbr_probe_fp32_fma, 2 FLOP per FMA)",
+                "flop_per_cell_test": FLOP_CELL, "cell_tests_per_step": cnt["raster_tests"],
+                "primary_ms_per_step": primary_s * 1e3, "sm_count": n_sm,
+                "exact_decisions": {"open_tests": cnt["open_tests"], "fp64_tests": cnt["fp64_tests"],
+                                    "tri_tests": cnt["tri_tests"]}}
     launches = stats[0]["kernel_launches"] + 3  # + PO work list, PO reduce and PO final
     line = {"metric": "ray-bounces/s", "value": value, "unit": "ray-bounces/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,

@@ -177,8 +177,20 @@ int sbr_get_bbox(sbr_ctx* ctx, float* bbox6);
  * (SBR_BVH_PLOC; also what sbr_load_mesh builds) the hierarchy comes from
  * nearest-neighbour clustering of the Morton-ordered triangles instead of the
  * Karras split (SBR_BVH_LBVH); leaf collapse and layout are the same.
- * Synchronises. */
+ * Synchronises. The nodes reachable from the root are then renumbered in
+ * depth-first order (the larger child first), so that each subtree is one
+ * contiguous range of the node array; boxes, leaves and hits do not change. */
 int sbr_build_bvh(sbr_ctx* ctx, const sbr_bvh_opts* opt);
+
+/* Size of the current tree: triangles, binary nodes reachable from the root
+ * (64 bytes each; the node array holds no others once built), nodes of its
+ * 4-wide collapse (128 bytes each). SBR_ERR_STATE without a mesh. */
+typedef struct {
+    int64_t n_tri;
+    int64_t n_nodes;
+    int64_t n_nodes4;
+} sbr_bvh_info;
+int sbr_get_bvh_info(sbr_ctx* ctx, sbr_bvh_info* out);
 
 /* Ray grid of one aspect for the loaded mesh (Eq. L1-L3), computed on the host.
  * ray_spacing_m = ds, margin_eta = eta of Eq. L2 (ignored when opt->window_m > 0).

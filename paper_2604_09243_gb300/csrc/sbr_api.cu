@@ -487,33 +487,51 @@ int sbr_build_bvh(sbr_ctx* c, const sbr_bvh_opts* opt)
     b.tri_pos = c->tripos.as<int>();
     b.bbox_out = c->bbox_dev.as<float>();
     b.err_flag = c->err_dev.as<int>();
+    b.n_nodes_out = c->err_dev.as<int>() + 2;
     b.scratch = c->bvh_scratch.p;
     b.scratch_bytes = c->bvh_scratch.cap;
     CK(bvh_build(b, c->stream), "bvh build");
     float hb[8];
-    int herr = 0;
+    int herr[3] = {0, 0, 0};
     CK(cudaMemcpyAsync(hb, c->bbox_dev.p, sizeof(float) * 6, cudaMemcpyDeviceToHost, c->stream), "copy bbox");
-    CK(cudaMemcpyAsync(&herr, c->err_dev.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "copy err");
+    CK(cudaMemcpyAsync(herr, c->err_dev.p, sizeof(int) * 3, cudaMemcpyDeviceToHost, c->stream), "copy err");
     CK(cudaStreamSynchronize(c->stream), "bvh build sync");
-    if (herr) {
+    if (herr[0]) {
         c->has_mesh = false;
-        if (herr & 4) return fail(c, SBR_ERR_CUDA, "sbr_build_bvh: the clustering did not converge");
-        return fail(c, SBR_ERR_ARG, (herr & 1) ? "sbr_build_bvh: triangle index out of range"
-                                               : "sbr_build_bvh: a vertex coordinate is not finite");
+        if (herr[0] & 4) return fail(c, SBR_ERR_CUDA, "sbr_build_bvh: the clustering did not converge");
+        return fail(c, SBR_ERR_ARG, (herr[0] & 1) ? "sbr_build_bvh: triangle index out of range"
+                                                  : "sbr_build_bvh: a vertex coordinate is not finite");
     }
+    // the nodes reachable from the root, renumbered 0.. in depth-first order
+    if (herr[2] < 1 || herr[2] > n_nodes) {
+        c->has_mesh = false;
+        return fail(c, SBR_ERR_CUDA, "sbr_build_bvh: malformed hierarchy (%d reachable nodes of %lld)", herr[2],
+                    n_nodes);
+    }
+    c->n_nodes = herr[2];
     memcpy(c->bbox, hb, sizeof(c->bbox));
     // 4-wide tree over the same boxes; its work queues reuse the (now free) build scratch
-    CK(c->nodes4.ensure(sizeof(float4) * kNode4Float4 * (size_t)n_nodes), "alloc 4-wide nodes");
+    CK(c->nodes4.ensure(sizeof(float4) * kNode4Float4 * (size_t)c->n_nodes), "alloc 4-wide nodes");
     {
         char* scr = (char*)c->bvh_scratch.p;
-        const size_t qb = ((sizeof(int2) * (size_t)n_nodes + 255) / 256) * 256;
+        const size_t qb = ((sizeof(int2) * (size_t)c->n_nodes + 255) / 256) * 256;
         if (2 * qb + 256 > c->bvh_scratch.cap) return fail(c, SBR_ERR_ARG, "sbr_build_bvh: scratch too small");
-        CK(bvh4_collapse(c->nodes.as<float4>(), n_nodes, c->nodes4.as<float4>(), (int2*)scr, (int2*)(scr + qb),
+        CK(bvh4_collapse(c->nodes.as<float4>(), c->n_nodes, c->nodes4.as<float4>(), (int2*)scr, (int2*)(scr + qb),
                          (int*)(scr + 2 * qb), &c->n_nodes4, c->stream),
            "4-wide collapse");
     }
     c->has_bvh = true;
     c->has_trace = false;
+    return SBR_OK;
+}
+
+int sbr_get_bvh_info(sbr_ctx* c, sbr_bvh_info* out)
+{
+    if (!c || !out) return SBR_ERR_ARG;
+    if (!c->has_bvh) return fail(c, SBR_ERR_STATE, "sbr_get_bvh_info: no tree built");
+    out->n_tri = c->n_tri;
+    out->n_nodes = c->n_nodes;
+    out->n_nodes4 = c->n_nodes4;
     return SBR_OK;
 }
 

@@ -344,10 +344,12 @@ __global__ void __launch_bounds__(kThreads) k_emit(int n, const int* left, const
         return;
     }
     if (i >= n - 1) return;
-    if (ncol[i]) {
-        if (i == 0) put_node(nodes, 0, nbox[0], nbox[1], elo, ehi, leaf_ref(0, ncnt[0]), kEmptyRef);
+    if (i == 0 && ncol[0]) {
+        put_node(nodes, 0, nbox[0], nbox[1], elo, ehi, leaf_ref(0, ncnt[0]), kEmptyRef);
         return;
     }
+    // every slot is written, those of collapsed clusters too (never reached from the root; their children
+    // lie inside them), so that no slot keeps a node of an earlier build
     float4 bl[2], bh[2];
     int ref[2];
     int ch[2] = {left[i], right[i]};
@@ -963,7 +965,126 @@ struct Carve {
     }
 };
 
+// ---------------------------------------------------------------- depth-first relayout
+// The builders leave max(n - 1, 1) node slots, and the slots of clusters that
+// the SAH collapse turned into leaves are never reached. The reachable nodes are
+// renumbered in depth-first order, the child with the larger box first (the one
+// a ray enters more often): a node's subtree becomes one contiguous range that
+// starts right after it, and the tree shrinks to its reachable part. The root
+// stays node 0; leaf references and boxes are unchanged, so every traversal
+// visits the same boxes in the same order.
+
+// parent of every internal child, as 2 * parent + side
+__global__ void __launch_bounds__(kThreads) k_rl_parent(const float4* nodes, int m, int* parent)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const float4 r = nodes[4 * (size_t)i + 3];
+    const int c0 = __float_as_int(r.x), c1 = __float_as_int(r.y);
+    if (c0 >= 0 && c0 < m) parent[c0] = 2 * i;
+    if (c1 >= 0 && c1 < m) parent[c1] = 2 * i + 1;
+}
+
+// internal nodes in each subtree, bottom-up from the nodes without internal
+// children; the last child to arrive at a node finishes it
+__global__ void __launch_bounds__(kThreads) k_rl_size(const float4* nodes, int m, const int* parent, int* arrive,
+                                                      int* size)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const float4 r = nodes[4 * (size_t)i + 3];
+    if (__float_as_int(r.x) >= 0 || __float_as_int(r.y) >= 0) return;
+    size[i] = 1;
+    __threadfence();
+    int x = i;
+    // a walk to the root passes at most m nodes; the bound guards against a malformed hierarchy
+    for (int steps = 0; steps < m; ++steps) {
+        const int pp = parent[x];
+        if (pp < 0) return;
+        const int p = pp >> 1;
+        const float4 q = nodes[4 * (size_t)p + 3];
+        const int l = __float_as_int(q.x), rr = __float_as_int(q.y);
+        const int need = (l >= 0 ? 1 : 0) + (rr >= 0 ? 1 : 0);
+        if (atomicAdd(arrive + p, 1) + 1 < need) return;  // the sibling finishes the node
+        __threadfence();
+        size[p] = 1 + (l >= 0 ? __ldcg(size + l) : 0) + (rr >= 0 ? __ldcg(size + rr) : 0);
+        __threadfence();
+        x = p;
+    }
+}
+
+// side (0 left, 1 right) whose child comes first: the larger surface area
+__device__ __forceinline__ int rl_first(const float4* nodes, int p)
+{
+    const float4 n0 = nodes[4 * (size_t)p], n1 = nodes[4 * (size_t)p + 1], n2 = nodes[4 * (size_t)p + 2];
+    const float4 llo = make_float4(n0.x, n0.z, n2.x, 0.f), lhi = make_float4(n0.y, n0.w, n2.y, 0.f);
+    const float4 rlo = make_float4(n1.x, n1.z, n2.z, 0.f), rhi = make_float4(n1.y, n1.w, n2.w, 0.f);
+    return area(llo, lhi) >= area(rlo, rhi) ? 0 : 1;
+}
+
+// depth-first position of every reachable node (-1: not reachable from the root)
+__global__ void __launch_bounds__(kThreads) k_rl_pos(const float4* nodes, int m, const int* parent, const int* size,
+                                                     int* newpos)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    int pos = 0, x = i, steps = 0;
+    for (; steps < m; ++steps) {
+        const int pp = parent[x];
+        if (pp < 0) break;
+        const int p = pp >> 1, side = pp & 1, f = rl_first(nodes, p);
+        pos += 1;
+        if (side != f) {
+            const int c = __float_as_int(f == 0 ? nodes[4 * (size_t)p + 3].x : nodes[4 * (size_t)p + 3].y);
+            if (c >= 0) pos += size[c];
+        }
+        x = p;
+    }
+    newpos[i] = (x == 0 && steps < m) ? pos : -1;
+}
+
+__global__ void __launch_bounds__(kThreads) k_rl_scatter(const float4* nodes, int m, const int* newpos, float4* out,
+                                                         const int* size, int* n_out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0 && n_out) *n_out = size[0];
+    if (i >= m) return;
+    const int q = newpos[i];
+    if (q < 0) return;
+    const float4 r = nodes[4 * (size_t)i + 3];
+    int c0 = __float_as_int(r.x), c1 = __float_as_int(r.y);
+    if (c0 >= 0) c0 = newpos[c0];
+    if (c1 >= 0) c1 = newpos[c1];
+    out[4 * (size_t)q] = nodes[4 * (size_t)i];
+    out[4 * (size_t)q + 1] = nodes[4 * (size_t)i + 1];
+    out[4 * (size_t)q + 2] = nodes[4 * (size_t)i + 2];
+    out[4 * (size_t)q + 3] = make_float4(__int_as_float(c0), __int_as_float(c1), 0.f, 0.f);
+}
+
 }  // namespace
+
+// Renumber the m node slots of b.nodes in depth-first order (the kernels
+// above) through scratch taken from cv; *b.n_nodes_out gets the node count.
+cudaError_t relayout(const BvhBuild& b, int m, Carve& cv, cudaStream_t st)
+{
+    int* parent = cv.take<int>(m);
+    int* arrive = cv.take<int>(m);
+    int* size = cv.take<int>(m);
+    int* newpos = cv.take<int>(m);
+    float4* tmp = cv.take<float4>(4 * (size_t)m);
+    if (cv.off > cv.cap) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(parent, 0xFF, sizeof(int) * (size_t)m, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(arrive, 0, sizeof(int) * (size_t)m, st);
+    if (e != cudaSuccess) return e;
+    const int gm = (m + kThreads - 1) / kThreads;
+    k_rl_parent<<<gm, kThreads, 0, st>>>(b.nodes, m, parent);
+    k_rl_size<<<gm, kThreads, 0, st>>>(b.nodes, m, parent, arrive, size);
+    k_rl_pos<<<gm, kThreads, 0, st>>>(b.nodes, m, parent, size, newpos);
+    k_rl_scatter<<<gm, kThreads, 0, st>>>(b.nodes, m, newpos, tmp, size, b.n_nodes_out);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b.nodes, tmp, sizeof(float4) * 4 * (size_t)m, cudaMemcpyDeviceToDevice, st);
+    return e;
+}
 
 size_t bvh_scratch_bytes(long long n_tri)
 {
@@ -990,6 +1111,8 @@ size_t bvh_scratch_bytes(long long n_tri)
     add(n * 4); add(n * 4);                 // noff perm
     for (int k = 0; k < 4; ++k) add(2 * n * 4);  // parent links and offsets, two buffers each
     add(64);                                // counters
+    for (int k = 0; k < 4; ++k) add(n * 4); // relayout: parent, arrivals, subtree sizes, new positions
+    add(n * 64);                            // relayout: the renumbered nodes
     return b + 256;
 }
 
@@ -1084,6 +1207,8 @@ cudaError_t bvh_build(const BvhBuild& b, cudaStream_t st)
         k_build_small<<<1, kSmallThreads, 12 * (size_t)n, st>>>(sb);
         k_ploc_emit<<<(n - 1 + kThreads - 1) / kThreads, kThreads, 0, st>>>(n, left, right, nbox, ncnt, ncol, noff,
                                                                             tbox, b.nodes);
+        e = relayout(b, n - 1, cv, st);
+        if (e != cudaSuccess) return e;
         k_reorder<<<g, kThreads, 0, st>>>(b.xyz, b.tri, b.n_vert, perm, n, b.tris, b.tri_nrm, b.tri_v12, b.tri_pos);
         return cudaGetLastError();
     }
@@ -1138,6 +1263,8 @@ cudaError_t bvh_build(const BvhBuild& b, cudaStream_t st)
         k_ploc_positions<<<gx, kThreads, 0, st>>>(n, rel[pj], noff, perm);
         k_ploc_emit<<<(n - 1 + kThreads - 1) / kThreads, kThreads, 0, st>>>(n, left, right, nbox, ncnt, ncol, noff,
                                                                             tbox, b.nodes);
+        e = relayout(b, n - 1, cv, st);
+        if (e != cudaSuccess) return e;
         k_reorder<<<g, kThreads, 0, st>>>(b.xyz, b.tri, b.n_vert, perm, n, b.tris, b.tri_nrm, b.tri_v12, b.tri_pos);
         return cudaGetLastError();
     }
@@ -1150,6 +1277,8 @@ cudaError_t bvh_build(const BvhBuild& b, cudaStream_t st)
                                     b.leaf_max, b.c_t, b.c_i);
     int ge = n > 1 ? (n - 1 + kThreads - 1) / kThreads : 1;
     k_emit<<<ge, kThreads, 0, st>>>(n, left, right, first, lbox, nbox, ncnt, ncol, b.nodes);
+    cudaError_t e = relayout(b, n > 1 ? n - 1 : 1, cv, st);
+    if (e != cudaSuccess) return e;
     k_reorder<<<g, kThreads, 0, st>>>(b.xyz, b.tri, b.n_vert, vi, n, b.tris, b.tri_nrm, b.tri_v12, b.tri_pos);
     return cudaGetLastError();
 }

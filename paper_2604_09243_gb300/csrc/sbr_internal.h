@@ -128,6 +128,7 @@ struct BvhBuild {
     float* bbox_out;  // device float[6] scene box of the vertices
     int* err_flag;    // device int: bit 1 a triangle index out of range, bit 2 a non-finite coordinate,
                       // bit 4 the clustering did not converge
+    int* n_nodes_out; // device int: reachable nodes, numbered 0.. in depth-first order
     // scratch (caller-owned)
     void* scratch;
     size_t scratch_bytes;

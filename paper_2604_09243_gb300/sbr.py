@@ -34,7 +34,7 @@ EXPORTS = ("sbr_version", "sbr_create", "sbr_destroy", "sbr_last_error", "sbr_lo
            "sbr_surrogate_create", "sbr_surrogate_destroy", "sbr_surrogate_last_error", "sbr_surrogate_num_params",
            "sbr_surrogate_params", "sbr_surrogate_fourier", "sbr_surrogate_train", "sbr_surrogate_grads",
            "sbr_surrogate_predict", "sbr_gemm_bf16_tn", "sbr_gemm_bf16_tn_async", "sbr_probe_l2_bandwidth",
-           "sbr_probe_fp32_fma")
+           "sbr_probe_fp32_fma", "sbr_get_bvh_info")
 
 
 class SbrError(RuntimeError):
@@ -64,6 +64,10 @@ class Tuning(C.Structure):
 
 class TuneTrial(C.Structure):
     _fields_ = [("tuning", Tuning), ("ms", C.c_double), ("status", C.c_int), ("reserved", C.c_int)]
+
+
+class BvhInfo(C.Structure):
+    _fields_ = [("n_tri", C.c_int64), ("n_nodes", C.c_int64), ("n_nodes4", C.c_int64)]
 
 
 class TraceStats(C.Structure):
@@ -112,6 +116,7 @@ def lib() -> C.CDLL:
         "sbr_load_mesh": ([vp, vp, i64, vp, i64, C.c_int], C.c_int),
         "sbr_get_bbox": ([vp, P(C.c_float)], C.c_int),
         "sbr_build_bvh": ([vp, P(BvhOpts)], C.c_int),
+        "sbr_get_bvh_info": ([vp, P(BvhInfo)], C.c_int),
         "sbr_ray_grid_for": ([vp, d, d, d, d, P(TraceOpts), P(RayGrid)], C.c_int),
         "sbr_ray_grid_box": ([P(C.c_float), d, d, d, d, P(TraceOpts), P(RayGrid)], C.c_int),
         "sbr_trace": ([vp, P(d), i64, d, d, C.c_int, P(TraceOpts), P(TraceStats)], C.c_int),
@@ -295,6 +300,12 @@ class Context:
         o = BvhOpts(int(leaf_max), float(cost_traverse), float(cost_intersect), {"ploc": 0, "lbvh": 1}[builder],
                     int(ploc_radius))
         self._check(lib().sbr_build_bvh(self._h, C.byref(o)))
+
+    def bvh_info(self) -> dict:
+        """sbr_get_bvh_info: triangles, reachable binary nodes, 4-wide nodes."""
+        o = BvhInfo()
+        self._check(lib().sbr_get_bvh_info(self._h, C.byref(o)))
+        return {"n_tri": int(o.n_tri), "n_nodes": int(o.n_nodes), "n_nodes4": int(o.n_nodes4)}
 
     def get_bbox(self) -> np.ndarray:
         b = np.zeros(6, np.float32)

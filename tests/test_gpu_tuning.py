@@ -135,6 +135,32 @@ def test_wide_tree_same_hits_aircraft(G):
         assert np.array_equal(R2, R4)
 
 
+def test_depth_first_layout_keeps_the_reachable_nodes(G):
+    """After the build the node array holds only the nodes reachable from the
+    root, in depth-first order: the aircraft's tree shrinks below its n - 1
+    node slots while its rays keep the oracle's hits (the parity tests), a
+    single triangle keeps one node, and the Karras tree of a plate hits as the
+    clustered one does."""
+    case = S.aircraft_case(1e9, n_az=360)
+    with G.Context(0) as c:
+        c.load_mesh(case["xyz"], case["tri"])
+        info = c.bvh_info()
+        assert info["n_tri"] == len(case["tri"])
+        assert 0 < info["n_nodes"] < len(case["tri"]) - 1
+        assert 0 < info["n_nodes4"] <= info["n_nodes"]
+        c.build_bvh(builder="lbvh")
+        assert 0 < c.bvh_info()["n_nodes"] < len(case["tri"]) - 1
+    xyz = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], np.float32)
+    with G.Context(0) as c:
+        c.load_mesh(xyz, np.array([[0, 1, 2]], np.int32))
+        assert c.bvh_info()["n_nodes"] == 1
+        st = c.trace([[0.0, 90.0]], 0.05, eta=0.0, max_bounces=1)
+        assert st["valid_rays"] > 0
+        for builder in ("ploc", "lbvh"):
+            c.build_bvh(builder=builder)
+            assert c.trace([[0.0, 90.0]], 0.05, eta=0.0, max_bounces=1)["valid_rays"] == st["valid_rays"]
+
+
 def test_silhouette_mask_skips_only_misses(G):
     """With the silhouette mask (primary rays traversing the tree) the
     aircraft's rays keep their hits (bit for bit) and valid count while fewer
