@@ -245,7 +245,11 @@ int sbr_trace_bistatic(sbr_ctx* ctx, const double* az_el_tx, const double* az_el
  * polarisations (SBR_POL_*); n_pol = popcount(pol_mask) outputs in the order
  * HH, VV, HV, VH. Outputs: E_re_im [n_angles][n_freq][n_pol][2] FP64 and
  * rcs_dbsm [n_angles][n_freq][n_pol] FP64 (either may be NULL), in host memory
- * (out_on_device = 0, synchronises) or device memory (1, stream ordered). */
+ * (out_on_device = 0, synchronises) or device memory (1, stream ordered).
+ * With one frequency (two with at most two polarisations) the records stream
+ * through shared memory by bulk copies with bounded waits; a wait that gives up
+ * makes the affected sums NaN and, with host outputs, returns SBR_ERR_TIMEOUT.
+ * The sums are the same bit for bit either way. */
 int sbr_po_integrate(sbr_ctx* ctx, const double* freq_hz, int64_t n_freq, int pol_mask, int po_mode,
                      double* E_re_im, double* rcs_dbsm, int out_on_device);
 

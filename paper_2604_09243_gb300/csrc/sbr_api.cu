@@ -966,6 +966,7 @@ int po_run(sbr_ctx* c, PoArgs pa, int64_t a0, int64_t a1, const std::vector<int>
     pa.kfreq = c->kfreq.as<double>();
     pa.partial = c->partial.as<double>();
     pa.item_records = c->tune.po_item;
+    pa.err = c->err_dev.as<int>() + 3;  // bounded waits of the staged single-frequency sum (callers clear it)
     CK(launch_po(pa, c->stream), "po reduce");
     CK(launch_po_final(pa.partial, pa.items, c->itemoff.as<PoAngle>(), na, pa.kfreq, pa.n_pol, dE, dR, c->stream),
        "po final");
@@ -1372,14 +1373,19 @@ int sbr_po_integrate(sbr_ctx* c, const double* freq_hz, int64_t n_freq, int pol_
         dE = E_out ? c->E.as<double>() : nullptr;
         dR = rcs_out ? c->rcs.as<double>() : nullptr;
     }
+    CK(cudaMemsetAsync(c->err_dev.as<int>() + 3, 0, sizeof(int), c->stream), "memset po flag");
     rc = po_run(c, pa, 0, na, f0, nf, row, dE, dR, nullptr);
     if (rc != SBR_OK) return rc;
     if (!out_on_device) {
+        int flag = 0;
         if (E_out)
             CK(cudaMemcpyAsync(E_out, dE, sizeof(double) * 2 * n_out, cudaMemcpyDeviceToHost, c->stream), "copy E");
         if (rcs_out)
             CK(cudaMemcpyAsync(rcs_out, dR, sizeof(double) * n_out, cudaMemcpyDeviceToHost, c->stream), "copy rcs");
+        CK(cudaMemcpyAsync(&flag, c->err_dev.as<int>() + 3, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+           "copy po flag");
         CK(cudaStreamSynchronize(c->stream), "po sync");
+        if (flag) return fail(c, SBR_ERR_TIMEOUT, "sbr_po_integrate: a staged record load did not arrive");
     }
     return SBR_OK;
 }
@@ -1448,6 +1454,7 @@ int sbr_run_batch(sbr_ctx* c, const sbr_request* req, int64_t n_req, const doubl
     // each chunk is traced once and integrated for all its requests' frequencies
     // before the next chunk reuses the record buffer
     long long valid = 0;
+    CK(cudaMemsetAsync(c->err_dev.as<int>() + 3, 0, sizeof(int), c->stream), "memset po flag");
     for (size_t k = 0; k + 1 < cut.size(); ++k) {
         unsigned* hro = nullptr;
         rc = trace_chunk(c, R, cut[k], cut[k + 1], 0, &hro);
@@ -1463,9 +1470,13 @@ int sbr_run_batch(sbr_ctx* c, const sbr_request* req, int64_t n_req, const doubl
         if (rcs_out)
             CK(cudaMemcpyAsync(rcs_out, dR, sizeof(double) * n_out, cudaMemcpyDeviceToHost, c->stream), "copy rcs");
     }
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, c->err_dev.as<int>() + 3, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+       "copy po flag");
     unsigned long long hs_stats[kStatCount];
-    rc = read_counters(c, hs_stats);
+    rc = read_counters(c, hs_stats);  // synchronises the stream
     if (rc != SBR_OK) return rc;
+    if (flag) return fail(c, SBR_ERR_TIMEOUT, "sbr_run_batch: a staged record load did not arrive");
     return finish_stats(c, R, hs_stats, n_req, launched, valid, stats);
 }
 

@@ -245,6 +245,8 @@ struct PoArgs {
     int scalar;           // 1: paper scalar form
     int phase_mode;       // 0 compensated, 1 FP32, 2 FP64
     double* partial;      // FP64 partials, item i at items[i].part
+    int* err = nullptr;   // optional device flag: set when a bounded wait of the staged kernel gave up (the
+                          // item's partials are then NaN); with it, single-frequency sums use that kernel
 };
 // n_blocks > 0: persistent grid of that many blocks looping over the items
 cudaError_t launch_po(const PoArgs& a, cudaStream_t st, int n_blocks = 0);

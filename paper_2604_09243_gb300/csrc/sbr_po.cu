@@ -132,6 +132,151 @@ __global__ void __launch_bounds__(kPoThreads) k_po(const PoArgs a)
 
 static_assert(kPoItemRecords == 4 * kPoThreads, "PO item size");
 
+// ---------------------------------------------------------------- staged single-frequency sum
+// With one frequency per block reduction (F <= 4 / kPol) the sum reads each
+// 32-byte record once and is bound by memory. The records of the items a block
+// owns are contiguous ranges; they are streamed in stages of kPoThreads records
+// (8 KB) by cp.async.bulk into a ring of kBulkStages shared-memory buffers, one
+// mbarrier each, issued ahead across item boundaries, so the loads of the next
+// stages overlap the phases, sums and reductions of the current one. Thread t
+// takes record k * kPoThreads + t of an item in stage k, in order, so every
+// term and every addition is that of k_po: the sums are bit-identical.
+constexpr int kBulkStages = 4;
+constexpr unsigned kPoSpin = 1u << 22;  // try_wait rounds before a wait gives up
+
+__device__ __forceinline__ uint32_t po_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool po_wait(uint64_t* bar, unsigned parity)
+{
+    const uint32_t b = po_smem(bar);
+    for (unsigned i = 0; i < kPoSpin; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(b), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+template <int kPol>
+__global__ void __launch_bounds__(kPoThreads) k_po_bulk(const PoArgs a)
+{
+    constexpr int kF = 4 / kPol;
+    __shared__ __align__(128) float4 s_rec[kBulkStages][2 * kPoThreads];
+    __shared__ __align__(8) uint64_t s_full[kBulkStages];
+    __shared__ float s_red[kWarps][8];
+    const int n_items = a.n_items_dev ? *a.n_items_dev : a.n_items;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid == 0) {
+        for (int s = 0; s < kBulkStages; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(po_smem(&s_full[s])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // producer (thread 0): the next stage to load, as (item, stage of the item), and the stages issued
+    int p_item = blockIdx.x, p_k = 0;
+    unsigned issued = 0;
+    auto produce = [&]() {
+        if (p_item >= n_items) return;
+        const PoItem I = a.items[p_item];
+        const int cnt = min(kPoThreads, I.count - p_k * kPoThreads);
+        const int s = (int)(issued % kBulkStages);
+        const unsigned bytes = (unsigned)cnt * (unsigned)sizeof(Record);
+        // the block's reads of this buffer (generic proxy) come before the copy that overwrites it
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(po_smem(&s_full[s])), "r"(bytes)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                po_smem(&s_rec[s][0])),
+            "l"(a.rec + I.first + (long long)p_k * kPoThreads), "r"(bytes), "r"(po_smem(&s_full[s]))
+            : "memory");
+        ++issued;
+        if (++p_k * kPoThreads >= I.count) {
+            p_k = 0;
+            p_item += gridDim.x;
+        }
+    };
+    if (tid == 0)
+        for (int s = 0; s < kBulkStages; ++s) produce();
+    unsigned used = 0;  // stages consumed
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const PoItem I = a.items[item];
+        float acc[8];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) acc[v] = 0.f;
+        const int n_st = (I.count + kPoThreads - 1) / kPoThreads;
+        for (int k = 0; k < n_st; ++k, ++used) {
+            const int s = (int)(used % kBulkStages);
+            const bool ok = po_wait(&s_full[s], (used / kBulkStages) & 1u);
+            if (__syncthreads_or(!ok)) {
+                // a stage did not arrive: flag it, poison this item's sums, and leave only once the copies
+                // still in flight into this block's buffers have landed (each wait bounded again)
+                if (tid == 0) {
+                    atomicOr(a.err, 1);
+                    for (int r = 0; r < I.nf * 2 * a.n_pol; ++r) a.partial[I.part + r] = __longlong_as_double(-1ll);
+                    for (unsigned u = used; u < issued; ++u)
+                        po_wait(&s_full[u % kBulkStages], (u / kBulkStages) & 1u);
+                }
+                return;
+            }
+            const int idx = k * kPoThreads + tid;
+            const bool valid = idx < I.count;
+            float4 x = make_float4(0.f, 0.f, 0.f, 0.f), y = x;
+            if (valid) {
+                x = s_rec[s][2 * tid];
+                y = s_rec[s][2 * tid + 1];
+            }
+            __syncthreads();  // every thread has read stage s: it can be refilled
+            if (tid == 0) produce();
+            if (!valid) continue;
+            float cf[kPol];
+#pragma unroll
+            for (int q = 0; q < kPol; ++q) {
+                const int sel = a.pol_sel[q];
+                const float vec = sel == 0 ? x.x : (sel == 1 ? x.y : (sel == 2 ? x.z : x.w));
+                float v = 0.f;
+                if (q < a.n_pol) v = a.scalar ? (sel < 2 ? y.x : 0.f) : vec;
+                cf[q] = v;
+            }
+#pragma unroll
+            for (int fj = 0; fj < kF; ++fj) {
+                if (fj >= I.nf) break;
+                const float4 fq = a.freq[I.f0 + fj];
+                const double kd = a.kfreq[I.f0 + fj];
+                float c, sn;
+                phase_cs(a, fq, kd, y.y, y.z, c, sn);
+#pragma unroll
+                for (int q = 0; q < kPol; ++q) {
+                    acc[(fj * kPol + q) * 2] = fmaf(cf[q], c, acc[(fj * kPol + q) * 2]);
+                    acc[(fj * kPol + q) * 2 + 1] = fmaf(-cf[q], sn, acc[(fj * kPol + q) * 2 + 1]);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int v = 0; v < 8; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
+        if (lane == 0)
+#pragma unroll
+            for (int v = 0; v < 8; ++v) s_red[w][v] = acc[v];
+        __syncthreads();
+        if (tid < 8) {
+            const int fj = tid / (2 * kPol), r = tid - fj * (2 * kPol);
+            if (fj < I.nf && r < 2 * a.n_pol) {
+                float v = 0.f;
+#pragma unroll
+                for (int k = 0; k < kWarps; ++k) v += s_red[k][tid];
+                a.partial[I.part + (size_t)fj * (2 * a.n_pol) + r] = (double)v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Work list, stage 1 (one block): 64-bit exclusive scans over the aspects of
 // their item counts and partial sizes, in tiles of the block size.
 __global__ void k_po_items_scan(const unsigned* recoff, PoAngle* angles, int na, int n_pol, int item_records,
@@ -260,6 +405,20 @@ cudaError_t launch_po(const PoArgs& a, cudaStream_t st, int n_blocks)
     if (grid <= 0) return cudaSuccess;
     const int per = (a.item_records > 0 ? a.item_records : kPoItemRecords) / kPoThreads;
     const bool two = a.n_pol <= 2;
+    if (a.err && n_blocks == 0 && a.n_freq <= (two ? 2 : 1) && (per == 2 || per == 4 || per == 8)) {
+        // one block reduction per item: the staged kernel, one persistent wave
+        int dev = 0, sms = 0, occ = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = two ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_po_bulk<2>, kPoThreads, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_po_bulk<4>, kPoThreads, 0);
+        if (e != cudaSuccess) return e;
+        const int g = (int)std::min<long long>(a.n_items, (long long)sms * std::max(occ, 1));
+        if (two) k_po_bulk<2><<<g, kPoThreads, 0, st>>>(a);
+        else k_po_bulk<4><<<g, kPoThreads, 0, st>>>(a);
+        return cudaGetLastError();
+    }
     if (per == 2) {
         if (two) k_po<2, 2><<<grid, kPoThreads, 0, st>>>(a);
         else k_po<2, 4><<<grid, kPoThreads, 0, st>>>(a);
