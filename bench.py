@@ -65,7 +65,7 @@ OPS_PRIMARY_HIT = 185
 # bounce queries of a step. None where no capture of the current kernels exists.
 TRAFFIC_PER_QUERY = {
     # k_bounce, warm L2 (ncu --cache-control none), 36 of the 360 aspects, five identical sweeps
-    "aircraft10": [(96.3, {"bvh_width": 2, "octant": 0, "packet": 0})],
+    "aircraft10": [(94.9, {"bvh_width": 2, "octant": 0, "packet": 0})],
 }
 
 
@@ -692,6 +692,69 @@ def run_gemm(args, ws, rank, local, pg):
                           "roofline": roof, "shapes": res}))
 
 
+def run_po(args, ws, rank, local, pg):
+    """The PO sum alone on the aircraft's records at 10 GHz (B = 10, every 5th of the 360 aspects unless
+    --aspects): sbr_po_integrate with device outputs, timed with CUDA events on the context's stream over
+    args.steps calls after args.warmup, for 1, 2 and 16 frequencies (HH, VV). One and two frequencies run
+    the staged kernel (records streamed through shared memory), 16 the register kernel. Roofline at one
+    frequency: the 32-byte records read once, against the HBM copy bandwidth."""
+    import torch
+    import paper_2604_09243_gb300 as G
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "the PO-only timing has no oracle leg; the oracle "
+                              "sums the same records inside the default workload's reference arm"}))
+        return
+    torch.cuda.set_device(local)
+    case = workload("aircraft10")
+    n_asp = args.aspects if args.aspects > 0 else 72
+    idx = np.linspace(0, len(case["angles"]) - 1, n_asp).round().astype(int)
+    stream = torch.cuda.Stream()
+    ctx = G.Context(local, stream=stream)
+    ctx.load_mesh(case["xyz"], case["tri"])
+    ctx.set_tuning(**({k: int(v) for k, v in (kv.split("=") for kv in args.tune.split(","))} if args.tune
+                      else {"po_item": 2048}))
+    st = ctx.trace(case["angles"][idx], case["spacing"], eta=case["eta"], max_bounces=case["max_bounces"],
+                   offset=case["offset"])
+    rec_bytes = 32.0 * st["valid_rays"]
+    pk, src = peaks()
+    hbm = pk.get("hbm_gbs", 6800.0)
+    res = []
+    for nf in (1, 2, 16):
+        f = np.linspace(9e9, 11e9, nf)
+        E = torch.empty(n_asp, nf, 2, 2, dtype=torch.float64, device="cuda")
+        R = torch.empty(n_asp, nf, 2, dtype=torch.float64, device="cuda")
+        for _ in range(max(1, args.warmup)):
+            ctx.po_integrate(f, "HH,VV", E_out=E, rcs_out=R)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            ctx.po_integrate(f, "HH,VV", E_out=E, rcs_out=R)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        res.append({"frequencies": nf, "ms": ms, "tube_freqs_per_s": st["valid_rays"] * nf / (ms * 1e-3),
+                    "record_gbs": rec_bytes / (ms * 1e-3) / 1e9,
+                    "kernel": "k_po_bulk" if nf <= 2 else "k_po"})
+    ctx.close()
+    one = res[0]
+    if rank == 0:
+        print(json.dumps({"metric": "PO tube-frequencies/s (one frequency)", "value": one["tube_freqs_per_s"] * ws,
+                          "unit": "tube-frequencies/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                          "data": "synthetic",
+                          "config": {"workload": f"po_aircraft_10GHz_{n_asp}aspects", "records": st["valid_rays"],
+                                     "record_bytes": rec_bytes, "pols": "HH,VV"},
+                          "roofline": {"bound": "hbm", "kernel": "k_po_bulk (one frequency)",
+                                       "achieved": one["record_gbs"], "peak": hbm, "unit": "GB/s",
+                                       "frac": one["record_gbs"] / hbm, "traffic": None,
+                                       "peak_source": f"HBM copy bandwidth, {src}",
+                                       "note": "time of the whole call: work list, PO sum, final sums"},
+                          "frequencies": res}))
+
+
 def run_sbr(args, case, ws, rank, local, pg):
     import torch
 
@@ -919,7 +982,7 @@ def main():
     ap.add_argument("--impl", default="sbr", choices=["sbr", "reference"])
     ap.add_argument("--workload", default="aircraft10",
                     choices=["trihedral", "sphere", "aircraft1", "aircraft3", "aircraft10", "aircraft3deep",
-                             "surrogate", "gemm"])
+                             "surrogate", "gemm", "po"])
     ap.add_argument("--ref-angles", type=int, default=24)
     ap.add_argument("--batch-requests", type=int, default=4096,
                     help="mixed requests for the batched-vs-plain comparison (0 = skip)")
@@ -941,8 +1004,8 @@ def main():
                     help="surrogate: rays per wavelength of its SBR runs (0: the domain's own, 10 unless set)")
     args = ap.parse_args()
     ws, rank, local, pg = dist_setup()
-    if args.workload == "gemm":
-        run_gemm(args, ws, rank, local, pg)
+    if args.workload in ("gemm", "po"):
+        (run_gemm if args.workload == "gemm" else run_po)(args, ws, rank, local, pg)
         if pg is not None:
             pg.destroy_process_group()
         return
