@@ -1031,25 +1031,42 @@ __device__ __forceinline__ void query(const TraceArgs& a, bool active, float3 o,
 // accept on triangle (a: v0, b: e1, c: e2); false if none.
 // ids = 1 / sqrt(A.dA), the inverse grid spacing (FP32, set with the aspect table)
 __device__ __forceinline__ float cell_scale(const AngleDev& A) { return A.ids; }
-__device__ __forceinline__ bool tri_cells(const AngleDev& A, float ids, float4 a, float4 b, float4 c, int& i0, int& i1,
-                                          int& j0, int& j1)
+
+// The triangle's vertices projected onto the aspect's grid (in cells from P0),
+// their ranges and their largest distance from P0 (in cells)
+struct TriProj {
+    float u[3], v[3], umin, umax, vmin, vmax, mag;
+};
+
+__device__ __forceinline__ void tri_project(const AngleDev& A, float ids, float4 a, float4 b, float4 c, TriProj& pr)
 {
     const float px[3] = {a.x, a.x + b.x, a.x + c.x}, py[3] = {a.y, a.y + b.y, a.y + c.y},
                 pz[3] = {a.z, a.z + b.z, a.z + c.z};
-    float umin = FLT_MAX, umax = -FLT_MAX, vmin = FLT_MAX, vmax = -FLT_MAX, mag = 0.f;
+    pr.umin = FLT_MAX;
+    pr.umax = -FLT_MAX;
+    pr.vmin = FLT_MAX;
+    pr.vmax = -FLT_MAX;
+    pr.mag = 0.f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const float dx = px[k] - A.p0[0], dy = py[k] - A.p0[1], dz = pz[k] - A.p0[2];
         const float u = (dx * A.hhat[0] + dy * A.hhat[1] + dz * A.hhat[2]) * ids;
         const float v = (dx * A.vhat[0] + dy * A.vhat[1] + dz * A.vhat[2]) * ids;
-        umin = fminf(umin, u);
-        umax = fmaxf(umax, u);
-        vmin = fminf(vmin, v);
-        vmax = fmaxf(vmax, v);
-        mag = fmaxf(mag, (fabsf(dx) + fabsf(dy) + fabsf(dz)) * ids);
+        pr.u[k] = u;
+        pr.v[k] = v;
+        pr.umin = fminf(pr.umin, u);
+        pr.umax = fmaxf(pr.umax, u);
+        pr.vmin = fminf(pr.vmin, v);
+        pr.vmax = fmaxf(pr.vmax, v);
+        pr.mag = fmaxf(pr.mag, (fabsf(dx) + fabsf(dy) + fabsf(dz)) * ids);
     }
+}
+
+__device__ __forceinline__ bool tri_cells_p(const AngleDev& A, const TriProj& pr, int& i0, int& i1, int& j0, int& j1)
+{
+    const float umin = pr.umin, umax = pr.umax, vmin = pr.vmin, vmax = pr.vmax;
     if (!(umin <= umax) || !(vmin <= vmax)) return false;  // NaN vertices: no ray can hit it
-    const float m = 0.01f + (umax - umin + vmax - vmin) * (1.f / 1024.f) + mag * (1.f / 262144.f);
+    const float m = 0.01f + (umax - umin + vmax - vmin) * (1.f / 1024.f) + pr.mag * (1.f / 262144.f);
     const float fi0 = ceilf(umin - m), fi1 = floorf(umax + m), fj0 = ceilf(vmin - m), fj1 = floorf(vmax + m);
     if (fi1 < 0.f || fj1 < 0.f || fi0 > (float)(A.nu - 1) || fj0 > (float)(A.nv - 1)) return false;
     i0 = max(0, (int)fi0);
@@ -1057,6 +1074,14 @@ __device__ __forceinline__ bool tri_cells(const AngleDev& A, float ids, float4 a
     j0 = max(0, (int)fj0);
     j1 = min(A.nv - 1, (int)fj1);
     return true;
+}
+
+__device__ __forceinline__ bool tri_cells(const AngleDev& A, float ids, float4 a, float4 b, float4 c, int& i0, int& i1,
+                                          int& j0, int& j1)
+{
+    TriProj pr;
+    tri_project(A, ids, a, b, c, pr);
+    return tri_cells_p(A, pr, i0, i1, j0, j1);
 }
 
 // The projected triangle as three edge half-planes in the cell coordinates of
@@ -1072,26 +1097,16 @@ struct CellEdges {
     float nx[3], ny[3], c[3];
 };
 
-__device__ __forceinline__ void tri_cell_edges(const AngleDev& A, float ids, float4 a, float4 b, float4 c, int i0,
-                                               int i1, int j0, int j1, CellEdges& E)
+__device__ __forceinline__ void tri_cell_edges_p(const TriProj& pr, int i0, int i1, int j0, int j1, CellEdges& E)
 {
-    const float px[3] = {a.x, a.x + b.x, a.x + c.x}, py[3] = {a.y, a.y + b.y, a.y + c.y},
-                pz[3] = {a.z, a.z + b.z, a.z + c.z};
-    float u[3], v[3], umin = FLT_MAX, umax = -FLT_MAX, vmin = FLT_MAX, vmax = -FLT_MAX, mag = 0.f;
+    float u[3], v[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const float dx = px[k] - A.p0[0], dy = py[k] - A.p0[1], dz = pz[k] - A.p0[2];
-        const float uu = (dx * A.hhat[0] + dy * A.hhat[1] + dz * A.hhat[2]) * ids;
-        const float vv = (dx * A.vhat[0] + dy * A.vhat[1] + dz * A.vhat[2]) * ids;
-        umin = fminf(umin, uu);
-        umax = fmaxf(umax, uu);
-        vmin = fminf(vmin, vv);
-        vmax = fmaxf(vmax, vv);
-        mag = fmaxf(mag, (fabsf(dx) + fabsf(dy) + fabsf(dz)) * ids);
-        u[k] = uu - (float)i0;
-        v[k] = vv - (float)j0;
+        u[k] = pr.u[k] - (float)i0;
+        v[k] = pr.v[k] - (float)j0;
     }
-    const float m = 0.01f + (umax - umin + vmax - vmin) * (1.f / 1024.f) + mag * (1.f / 262144.f) + 0.002f;
+    const float m =
+        0.01f + (pr.umax - pr.umin + pr.vmax - pr.vmin) * (1.f / 1024.f) + pr.mag * (1.f / 262144.f) + 0.002f;
     const float a2 = (u[1] - u[0]) * (v[2] - v[0]) - (v[1] - v[0]) * (u[2] - u[0]);
     const float sg = a2 > 0.f ? 1.f : -1.f;
     const bool flat = !(fabsf(a2) > 1e-2f);
@@ -1106,6 +1121,14 @@ __device__ __forceinline__ void tri_cell_edges(const AngleDev& A, float ids, flo
         E.ny[k] = flat ? 0.f : ny;
         E.c[k] = flat ? -1.f : -(nx * u[k] + ny * v[k]) - w;
     }
+}
+
+__device__ __forceinline__ void tri_cell_edges(const AngleDev& A, float ids, float4 a, float4 b, float4 c, int i0,
+                                               int i1, int j0, int j1, CellEdges& E)
+{
+    TriProj pr;
+    tri_project(A, ids, a, b, c, pr);
+    tri_cell_edges_p(pr, i0, i1, j0, j1, E);
 }
 
 __device__ __forceinline__ bool cell_inside(const CellEdges& E, int di, int dj)
@@ -1267,20 +1290,21 @@ __device__ __forceinline__ void raster_cell(const RasterGrid& G, const TraceArgs
 }
 
 // A triangle of the flattened rasterisation and everything its cells need,
-// one per lane in shared memory (51 words, an odd stride: the lanes' writes hit
-// distinct banks, and lanes reading one triangle's fields share a broadcast).
-struct RasterItem {
-    float3 p0, du, dv;  // the aspect's ray grid
-    int nbu, tw;
-    RasterTri R;
-    PlaneKey K;
-    CellEdges E;
-    int i0, j0, w, ncell;  // cell range: w columns from (i0, j0), ncell cells
-    float rw;              // 1 / w
-    unsigned orig;         // original triangle index
-    int t, ang;            // reordered triangle and aspect
+// one per lane in shared memory as 13 16-byte words (a stride of 52 words: the
+// 16-byte accesses of 8 lanes to different triangles fall in distinct banks,
+// and lanes reading one triangle's fields share a broadcast):
+//   g0 = (p0.x, p0.y, p0.z, du.x)   g1 = (du.y, du.z, dv.x, dv.y)   g2 = (dv.z, v0.x, v0.y, v0.z)
+//   r0 = (p.x, p.y, p.z, p2.x)      r1 = (p2.y, p2.z, nn.x, nn.y)   r2 = (nn.z, det, bd, bU)
+//   r3 = (bV, bT, n.x, n.y)         r4 = (n.z, dh, dl, rd)           [plane key K]
+//   e0 = (nx0, ny0, c0, nx1)        e1 = (ny1, c1, nx2, ny2)         e2 = (c2, 1 / w, tnear, ray_off)
+//   m0 = (i0, j0, w, orig)          m1 = (aspect, triangle, nbu, tw)
+// tnear: below the smallest stored distance any cell of the range can give
+// this triangle (a cell whose ray already holds a closer hit is skipped).
+struct __align__(16) RasterItem {
+    float4 g0, g1, g2, r0, r1, r2, r3, r4, e0, e1, e2;
+    int4 m0, m1;
 };
-static_assert(sizeof(RasterItem) == 51 * 4, "RasterItem layout");
+static_assert(sizeof(RasterItem) == 52 * 4, "RasterItem layout");
 constexpr int kRasterWarps = 8;    // warps of a k_raster block
 constexpr int kRasterFlat = 512;   // cells of a triangle the warps flatten; larger ones go to k_raster_big
 constexpr size_t kRasterSmem = sizeof(RasterItem) * 32 * kRasterWarps;
@@ -1317,7 +1341,9 @@ __global__ void __launch_bounds__(256, 4) k_raster(const TraceArgs a, int n_tri,
             const float4* tp = a.tris + 3 * (size_t)t;
             const float4 P = __ldg(tp), B = __ldg(tp + 1), C = __ldg(tp + 2);
             int i0, i1, j0, j1;
-            if (tri_cells(A, cell_scale(A), P, B, C, i0, i1, j0, j1)) {
+            TriProj pr;
+            tri_project(A, cell_scale(A), P, B, C, pr);
+            if (tri_cells_p(A, pr, i0, i1, j0, j1)) {
                 const long long ncell = (long long)(i1 - i0 + 1) * (j1 - j0 + 1);
                 if (ncell > kRasterMaxCells || A.nu > 65535 || A.nv > 65535) {
                     atomicOr(full + ang, 1u);
@@ -1326,26 +1352,47 @@ __global__ void __launch_bounds__(256, 4) k_raster(const TraceArgs a, int n_tri,
                     want_big = true;
                     rng = make_int4(t, ang, i0 | (j0 << 16), (i1 - i0) | ((j1 - j0) << 16));
                 } else {
+                    // each group of constants goes to shared memory as soon as it is formed
+                    RasterItem& it = my[lane];
+                    float c2;
+                    {
+                        CellEdges E;
+                        tri_cell_edges_p(pr, i0, i1, j0, j1, E);
+                        it.e0 = make_float4(E.nx[0], E.ny[0], E.c[0], E.nx[1]);
+                        it.e1 = make_float4(E.ny[1], E.c[1], E.nx[2], E.ny[2]);
+                        c2 = E.c[2];
+                    }
                     const RasterGrid G = raster_grid(A);
-                    const RasterTri R = raster_tri(G, P, B, C, i0, i1, j0, j1);
-                    if (R.bd >= 0.f) {
-                        RasterItem& it = my[lane];
-                        it.p0 = G.p0;
-                        it.du = G.du;
-                        it.dv = G.dv;
-                        it.nbu = G.nbu;
-                        it.tw = G.tw;
-                        it.R = R;
-                        it.K = plane_key(a.tri_nrm, t, G.d);
-                        tri_cell_edges(A, cell_scale(A), P, B, C, i0, i1, j0, j1, it.E);
-                        it.i0 = i0;
-                        it.j0 = j0;
-                        it.w = i1 - i0 + 1;
-                        it.ncell = (int)ncell;
-                        it.rw = 1.f / (float)(i1 - i0 + 1);
-                        it.orig = (unsigned)__float_as_int(P.w);
-                        it.t = t;
-                        it.ang = ang;
+                    float bd;
+                    {
+                        const RasterTri R = raster_tri(G, P, B, C, i0, i1, j0, j1);
+                        it.g2 = make_float4(G.dv.z, R.v0.x, R.v0.y, R.v0.z);
+                        it.r0 = make_float4(R.p.x, R.p.y, R.p.z, R.p2.x);
+                        it.r1 = make_float4(R.p2.y, R.p2.z, R.nn.x, R.nn.y);
+                        it.r2 = make_float4(R.nn.z, R.det, R.bd, R.bU);
+                        it.r3 = make_float4(R.bV, R.bT, 0.f, 0.f);
+                        bd = R.bd;
+                    }
+                    if (bd >= 0.f) {
+                        const PlaneKey K = plane_key(a.tri_nrm, t, G.d);
+                        it.r3.z = K.n.x;
+                        it.r3.w = K.n.y;
+                        it.r4 = make_float4(K.n.z, K.dh, K.dl, K.rd);
+                        // distances along d of the vertices from the grid plane (the ray origins lie in it to
+                        // within micrometres); the stored distance of any hit on the triangle is at least their
+                        // minimum less the key's plane slack (0.08 bUV / |d.n|, as in key_of), 1e-4 of it and 1 mm
+                        const float3 q0 = make_float3(P.x - G.p0.x, P.y - G.p0.y, P.z - G.p0.z);
+                        const float z0 = dot_s(q0, G.d), z1 = z0 + dot_s(make_float3(B.x, B.y, B.z), G.d),
+                                    z2 = z0 + dot_s(make_float3(C.x, C.y, C.z), G.d);
+                        const float zm = fminf(z0, fminf(z1, z2));
+                        const float slack = K.dh != 0.f ? 0.32f * B.w / fabsf(K.dh) : FLT_MAX;
+                        const float tnear = zm - (1e-4f * fabsf(zm) + 1e-3f + slack);
+                        it.e2 = make_float4(c2, 1.f / (float)(i1 - i0 + 1), isfinite(tnear) ? tnear : -FLT_MAX,
+                                            __int_as_float((int)a.ray_off[ang]));
+                        it.g0 = make_float4(G.p0.x, G.p0.y, G.p0.z, G.du.x);
+                        it.g1 = make_float4(G.du.y, G.du.z, G.dv.x, G.dv.y);
+                        it.m0 = make_int4(i0, j0, i1 - i0 + 1, __float_as_int(P.w));
+                        it.m1 = make_int4(ang, t, G.nbu, G.tw);
                         nc = (int)ncell;
                     }
                 }
@@ -1381,34 +1428,52 @@ __global__ void __launch_bounds__(256, 4) k_raster(const TraceArgs a, int n_tri,
             while (off[k + 1] <= c) ++k;
             const RasterItem& it = my[k];
             const int loc = c - off[k];
+            const int4 m0 = it.m0;
+            const float4 e0 = it.e0, e1 = it.e1, e2 = it.e2;
             // (loc + 0.5) / w is at least 0.5 / w from an integer and loc, w <= 512: the FP32 product floors exactly
-            const int dj = __float2int_rz(((float)loc + 0.5f) * it.rw), di = loc - dj * it.w;
-            if (!cell_inside(it.E, di, dj)) continue;
+            const int dj = __float2int_rz(((float)loc + 0.5f) * e2.y), di = loc - dj * m0.z;
+            {
+                const float x = (float)di, y = (float)dj;
+                if (!(fmaf(e0.x, x, fmaf(e0.y, y, e0.z)) <= 0.f && fmaf(e0.w, x, fmaf(e1.x, y, e1.y)) <= 0.f &&
+                      fmaf(e1.z, x, fmaf(e1.w, y, e2.x)) <= 0.f))
+                    continue;
+            }
+            const int i = m0.x + di, j = m0.y + dj;
+            const int4 m1 = it.m1;
+            const int tw = m1.w, sh = 5 - tw;  // tile of W = 2^tw by H = 2^sh rays
+            const long long pidx = (long long)__float_as_int(e2.w) + ((long long)((j >> sh) * m1.z + (i >> tw)) << 5) +
+                                   ((j & ((1 << sh) - 1)) << tw) + (i & ((1 << tw) - 1));
+            // the ray's closest hit so far (keys only decrease; a stale value is larger): nearer than any
+            // distance this triangle can give, the cell is decided
+            if (__uint_as_float((unsigned)(__ldcg(vis + pidx) >> 32)) < e2.z) continue;
             ++ntri;
-            const int i = it.i0 + di, j = it.j0 + dj;
+            const float4 g0 = it.g0, g1 = it.g1, g2 = it.g2;
             const float fi = (float)i, fj = (float)j;
-            const float3 o = make_float3(__fadd_rn(__fadd_rn(it.p0.x, __fmul_rn(fi, it.du.x)), __fmul_rn(fj, it.dv.x)),
-                                         __fadd_rn(__fadd_rn(it.p0.y, __fmul_rn(fi, it.du.y)), __fmul_rn(fj, it.dv.y)),
-                                         __fadd_rn(__fadd_rn(it.p0.z, __fmul_rn(fi, it.du.z)), __fmul_rn(fj, it.dv.z)));
-            const float3 sv = make_float3(__fsub_rn(o.x, it.R.v0.x), __fsub_rn(o.y, it.R.v0.y), __fsub_rn(o.z, it.R.v0.z));
+            const float3 o = make_float3(__fadd_rn(__fadd_rn(g0.x, __fmul_rn(fi, g0.w)), __fmul_rn(fj, g1.z)),
+                                         __fadd_rn(__fadd_rn(g0.y, __fmul_rn(fi, g1.x)), __fmul_rn(fj, g1.w)),
+                                         __fadd_rn(__fadd_rn(g0.z, __fmul_rn(fi, g1.y)), __fmul_rn(fj, g2.x)));
+            const float3 v0 = make_float3(g2.y, g2.z, g2.w);
+            const float3 sv = make_float3(__fsub_rn(o.x, v0.x), __fsub_rn(o.y, v0.y), __fsub_rn(o.z, v0.z));
+            const float4 r0 = it.r0, r1 = it.r1, r2 = it.r2, r3 = it.r3;
             float tc, et;
-            const int f = filter_core(dot_s(sv, it.R.p), dot_s(sv, it.R.p2), dot_s(sv, it.R.nn), it.R.det, it.R.bU,
-                                      it.R.bV, it.R.bd, it.R.bT, tc, et);
+            const int f = filter_core(dot_s(sv, make_float3(r0.x, r0.y, r0.z)), dot_s(sv, make_float3(r0.w, r1.x, r1.y)),
+                                      dot_s(sv, make_float3(r1.z, r1.w, r2.x)), r2.y, r2.w, r3.x, r2.z, r3.y, tc, et);
             if (f == 0) continue;
             if (f >= 2) {
-                const AngleDev& A = a.angles[it.ang];
-                const int r = tri_refine(a.tris, a.tri_v12, it.t, o, make_float3(A.dir[0], A.dir[1], A.dir[2]), f, tc);
+                const AngleDev& A = a.angles[m1.x];
+                const int r = tri_refine(a.tris, a.tri_v12, m1.y, o, make_float3(A.dir[0], A.dir[1], A.dir[2]), f, tc);
                 if (count) count_open(a.stats, r);
                 if (!(r & 1)) continue;
             }
-            const float th = plane_key_t(it.K, it.R.v0, o, tc);
-            if (th >= 0.f && th <= FLT_MAX) {
-                const int tw = it.tw, sh = 5 - tw;  // tile of W = 2^tw by H = 2^sh rays
-                const int bu = i >> tw, bv = j >> sh;
-                const long long pidx =
-                    ((long long)(bv * it.nbu + bu) << 5) + ((j & ((1 << sh) - 1)) << tw) + (i & ((1 << tw) - 1));
-                atomicMin(vis + a.ray_off[it.ang] + pidx, ((unsigned long long)__float_as_uint(th) << 32) | it.orig);
-            }
+            const float4 r4 = it.r4;
+            PlaneKey K;
+            K.n = make_float3(r3.z, r3.w, r4.x);
+            K.dh = r4.y;
+            K.dl = r4.z;
+            K.rd = r4.w;
+            const float th = plane_key_t(K, v0, o, tc);
+            if (th >= 0.f && th <= FLT_MAX)
+                atomicMin(vis + pidx, ((unsigned long long)__float_as_uint(th) << 32) | (unsigned)m0.w);
         }
         __syncwarp();  // the next round rewrites my[] and off[]
         t += step_t;
