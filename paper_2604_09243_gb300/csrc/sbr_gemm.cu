@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(128, 2) k_gemm_tn(const __grid_constant__ CUte
         }
         __syncthreads();
         // coalesced write-out: consecutive threads take consecutive 16-byte pieces of a row
-        if (ep.mode != kEpiGeluGrad) {
+        if (ep.mode != kEpiGeluGrad && ep.c_f32) {
             for (int q = tid; q < kBM * (BN / 4); q += 128) {
                 const int rr = q / (BN / 4), cc = (q % (BN / 4)) * 4;
                 if (m0 + rr < ep.M)
@@ -271,6 +271,219 @@ __global__ void __launch_bounds__(128, 2) k_gemm_tn(const __grid_constant__ CUte
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+}
+
+// ---------------------------------------------------------------- persistent form
+// For grids of at least two 128 x 128 tiles per SM: one CTA per SM loops over
+// the tiles t = blockIdx.x, t + gridDim.x, ... (n-tile fastest) with six warps.
+// Warp 0 (one lane) streams the A and B tiles of every k-step of every tile
+// through the 3-stage ring; warp 1 (one lane) issues the MMAs of the CTA's
+// tile j into TMEM accumulator j % 2 (128 columns each) once the epilogue has
+// drained it and commits it; warps 2-5 read their 32 rows of the accumulator
+// (TMEM lanes 32 (w % 4) ..), release it, and apply the epilogue through
+// staging rows of their own, so that a tile's read-out, epilogue and stores
+// overlap the next tile's MMAs. The MMAs of a tile come in the same order and
+// the epilogue does the same arithmetic as in k_gemm_tn: the results are the
+// same bit for bit. Every wait is bounded and polls the CTA's failure flag.
+constexpr int kPpStages = 3;
+constexpr int kPpThreads = 192;
+struct PpCfg {
+    static constexpr int BN = 128;
+    static constexpr int kStageBytes = kTileA + BN * kBK * 2;  // 32 KB
+    static constexpr int kPipe = kPpStages * kStageBytes;
+    static constexpr int kLdF = BN + 4, kLdH = BN + 8;
+    static constexpr int kWarpF = 32 * kLdF * 4, kWarpH = 32 * kLdH * 2;  // staging of one epilogue warp
+    static constexpr int kSmem = kPipe + 4 * (kWarpF + kWarpH) + 1024;
+};
+static_assert(PpCfg::kSmem <= 227 * 1024, "persistent GEMM shared memory");
+
+// a bounded wait that also gives up once another role of the CTA has failed
+__device__ __forceinline__ bool pp_wait(uint64_t* b, unsigned parity, volatile int* fail)
+{
+    const uint32_t a = smem_u32(b);
+    for (unsigned i = 0; i < kSpin; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((i & 1023u) == 1023u && *fail) return false;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(kPpThreads, 1) k_gemm_pp(const __grid_constant__ CUtensorMap tmA,
+                                                           const __grid_constant__ CUtensorMap tmB, const GemmEpi ep,
+                                                           int K, int tiles_n, int n_tiles, int* err)
+{
+    using C = PpCfg;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[kPpStages], empty[kPpStages], tfull[2], tempty[2], drained;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_fail, s_issued, s_consumed;
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int KT = K / kBK;
+    const int my_tiles = (n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    volatile int* fail = &s_fail;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(&tmem_base))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int st = 0; st < kPpStages; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);  // one arrival per epilogue warp
+        }
+        mbar_init(&drained, 1);
+        s_fail = 0;
+        s_issued = 0;
+        s_consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    if (tid == 0) {
+        // producer: global k-step g of the CTA refills stage g % kPpStages once the MMAs of step g - kPpStages
+        // have completed
+        int g = 0;
+        for (int j = 0; j < my_tiles && !*fail; ++j) {
+            const int t = (int)blockIdx.x + j * (int)gridDim.x;
+            const int m0 = (t / tiles_n) * kBM, n0 = (t % tiles_n) * C::BN;
+            for (int kt = 0; kt < KT; ++kt, ++g) {
+                const int st = g % kPpStages;
+                if (g >= kPpStages && !pp_wait(&empty[st], (unsigned)(g / kPpStages - 1) & 1u, fail)) {
+                    *fail = 1;
+                    break;
+                }
+                unsigned char* sa = smem + st * C::kStageBytes;
+                mbar_expect_tx(&full[st], C::kStageBytes);
+                tma_load_2d(sa, &tmA, kt * kBK, m0, &full[st]);
+                tma_load_2d(sa + kTileA, &tmB, kt * kBK, n0, &full[st]);
+                *(volatile int*)&s_issued = g + 1;
+            }
+        }
+    } else if (tid == 32) {
+        // MMA issuer: tile j into accumulator j % 2 once the epilogue has drained tile j - 2 from it
+        int g = 0;
+        bool ok = true;
+        for (int j = 0; j < my_tiles && ok; ++j) {
+            const int b = j & 1;
+            if (j >= 2 && !pp_wait(&tempty[b], (unsigned)((j >> 1) - 1) & 1u, fail)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t acc = tmem + (uint32_t)(b * C::BN);
+            for (int kt = 0; kt < KT; ++kt, ++g) {
+                const int st = g % kPpStages;
+                if (!pp_wait(&full[st], (unsigned)(g / kPpStages) & 1u, fail)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t sa = smem_u32(smem + st * C::kStageBytes);
+                const uint32_t sb = sa + kTileA;
+#pragma unroll
+                for (int kk = 0; kk < kBK / 16; ++kk)
+                    mma_bf16(acc, desc_sw128(sa + 32 * kk), desc_sw128(sb + 32 * kk), Cfg<128>::kIdesc,
+                             (kt | kk) != 0);
+                mma_commit(&empty[st]);
+                *(volatile int*)&s_consumed = g + 1;
+            }
+            if (ok) mma_commit(&tfull[b]);
+        }
+        if (!ok) *fail = 1;
+        // every MMA issued has completed before the accumulators are freed (waited for even after a failure)
+        mma_commit(&drained);
+        mbar_wait(&drained, 0);
+    } else if (warp >= 2) {
+        // epilogue: warp w owns tile rows (TMEM lanes) 32 (w % 4) .. 32 (w % 4) + 31
+        const int q = warp & 3;
+        float* sf = reinterpret_cast<float*>(smem + C::kPipe + (warp - 2) * (C::kWarpF + C::kWarpH));
+        __nv_bfloat16* sh = reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(sf) + C::kWarpF);
+        for (int j = 0; j < my_tiles; ++j) {
+            const int b = j & 1;
+            const int t = (int)blockIdx.x + j * (int)gridDim.x;
+            const int m0 = (t / tiles_n) * kBM + 32 * q, n0 = (t % tiles_n) * C::BN;
+            // warp-uniform decision: the TMEM loads below are warp-collective
+            if (!__all_sync(0xffffffffu, pp_wait(&tfull[b], (unsigned)(j >> 1) & 1u, fail))) {
+                *fail = 1;
+                break;
+            }
+            tc_fence_after();
+            if (ep.mode == kEpiGeluGrad) {
+                // the warp's 32 rows of the pre-activation, coalesced (lane l: columns 4 l .. 4 l + 3)
+                for (int rr = 0; rr < 32; ++rr) {
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (m0 + rr < ep.M) v = *reinterpret_cast<const float4*>(ep.z + (size_t)(m0 + rr) * ep.ldz + n0 + 4 * lane);
+                    *reinterpret_cast<float4*>(sf + rr * C::kLdF + 4 * lane) = v;
+                }
+                __syncwarp();
+            }
+            for (int c0 = 0; c0 < C::BN; c0 += 32) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * C::BN + c0), v);
+                if (ep.mode == kEpiF32) {
+#pragma unroll
+                    for (int i = 0; i < 32; i += 4)
+                        *reinterpret_cast<float4*>(sf + lane * C::kLdF + c0 + i) =
+                            make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                } else if (ep.mode == kEpiBiasGelu) {
+#pragma unroll
+                    for (int i = 0; i < 32; i += 2) {
+                        const float z0 = v[i] + ep.bias[n0 + c0 + i], z1 = v[i + 1] + ep.bias[n0 + c0 + i + 1];
+                        *reinterpret_cast<float2*>(sf + lane * C::kLdF + c0 + i) = make_float2(z0, z1);
+                        *reinterpret_cast<__nv_bfloat162*>(sh + lane * C::kLdH + c0 + i) =
+                            __floats2bfloat162_rn(gelu(z0), gelu(z1));
+                    }
+                } else {  // kEpiGeluGrad: dz = acc * gelu'(z)
+#pragma unroll
+                    for (int i = 0; i < 32; i += 2) {
+                        const float2 z = *reinterpret_cast<const float2*>(sf + lane * C::kLdF + c0 + i);
+                        *reinterpret_cast<__nv_bfloat162*>(sh + lane * C::kLdH + c0 + i) =
+                            __floats2bfloat162_rn(v[i] * gelu_grad(z.x), v[i + 1] * gelu_grad(z.y));
+                    }
+                }
+            }
+            // the accumulator is in registers and staging: hand it back to the MMA issuer
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[b])) : "memory");
+            if (ep.mode != kEpiGeluGrad && ep.c_f32)
+                for (int rr = 0; rr < 32; ++rr)
+                    if (m0 + rr < ep.M)
+                        *reinterpret_cast<float4*>(ep.c_f32 + (size_t)(m0 + rr) * ep.ldc + n0 + 4 * lane) =
+                            *reinterpret_cast<const float4*>(sf + rr * C::kLdF + 4 * lane);
+            if (ep.mode != kEpiF32)
+                for (int rr = 0; rr < 32; rr += 2) {
+                    const int row = rr + (lane >> 4), col = 8 * (lane & 15);
+                    if (m0 + row < ep.M)
+                        *reinterpret_cast<uint4*>(ep.out_bf16 + (size_t)(m0 + row) * ep.ldo + n0 + col) =
+                            *reinterpret_cast<const uint4*>(sh + row * C::kLdH + col);
+                }
+            __syncwarp();  // the staging rows are rewritten by the next tile
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (*fail && tid == 0) {
+        atomicExch(err, 1);
+        // let the loads still in flight land before the CTA's shared memory goes away
+        for (int g = s_consumed; g < s_issued; ++g) mbar_wait(&full[g % kPpStages], (unsigned)(g / kPpStages) & 1u);
+    }
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -342,6 +555,7 @@ cudaError_t gemm_bf16_tn(const void* A, int lda, const void* B, int ldb, int M, 
     if (!gemm_shape_ok(M, N, K) || lda % 8 || ldb % 8 || ((uintptr_t)A & 15) || ((uintptr_t)B & 15))
         return cudaErrorInvalidValue;
     if (ep.mode != kEpiGeluGrad && (ep.ldc % 4 || ((uintptr_t)ep.c_f32 & 15))) return cudaErrorInvalidValue;
+    if (ep.mode == kEpiF32 && !ep.c_f32) return cudaErrorInvalidValue;
     if (ep.mode != kEpiF32 && (ep.ldo % 8 || ((uintptr_t)ep.out_bf16 & 15))) return cudaErrorInvalidValue;
     if (ep.mode == kEpiGeluGrad && (ep.ldz % 4 || ((uintptr_t)ep.z & 15))) return cudaErrorInvalidValue;
     if (!g_sms) {
@@ -350,7 +564,23 @@ cudaError_t gemm_bf16_tn(const void* A, int lda, const void* B, int ldb, int M, 
         cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
         if (g_sms <= 0) g_sms = 1;
     }
-    if ((long long)(M / kBM) * (N / 128) < g_sms) return launch_gemm<64>(A, lda, B, ldb, M, N, K, ep, err, st);
+    const long long tiles = (long long)(M / kBM) * (N / 128);
+    if (tiles < g_sms) return launch_gemm<64>(A, lda, B, ldb, M, N, K, ep, err, st);
+    if (tiles >= 2ll * g_sms && tiles < (1ll << 31)) {
+        // persistent: one CTA per SM, accumulators double-buffered in TMEM
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(k_gemm_pp, cudaFuncAttributeMaxDynamicSharedMemorySize, PpCfg::kSmem);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        CUtensorMap ta, tb;
+        cudaError_t e = make_map(&ta, A, M, K, lda, kBM);
+        if (e == cudaSuccess) e = make_map(&tb, B, N, K, ldb, 128);
+        if (e != cudaSuccess) return e;
+        k_gemm_pp<<<g_sms, kPpThreads, PpCfg::kSmem, st>>>(ta, tb, ep, K, N / 128, (int)tiles, err);
+        return cudaGetLastError();
+    }
     return launch_gemm<128>(A, lda, B, ldb, M, N, K, ep, err, st);
 }
 

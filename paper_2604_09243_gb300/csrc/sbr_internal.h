@@ -272,7 +272,8 @@ enum { kEpiF32 = 0, kEpiBiasGelu = 1, kEpiGeluGrad = 2 };
 struct GemmEpi {
     int mode;                 // kEpi*
     int M;                    // rows of C
-    float* c_f32;             // kEpiF32: C; kEpiBiasGelu: z = acc + bias  (row stride ldc)
+    float* c_f32;             // kEpiF32: C; kEpiBiasGelu: z = acc + bias, or null where no backward pass reads it
+                              // (row stride ldc)
     int ldc;
     __nv_bfloat16* out_bf16;  // kEpiBiasGelu: gelu(z); kEpiGeluGrad: acc * gelu'(z)  (row stride ldo)
     int ldo;

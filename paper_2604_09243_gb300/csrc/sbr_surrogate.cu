@@ -385,7 +385,8 @@ int refresh_bf16(sbr_surrogate* s, int e)
 }
 
 // forward pass of member e on xb[0..M): fills h, z and y (at y + yoff)
-int forward(sbr_surrogate* s, int e, int M, float* yout)
+// keep_z: store the FP32 pre-activations for a backward pass (prediction writes only the BF16 activations)
+int forward(sbr_surrogate* s, int e, int M, float* yout, bool keep_z = true)
 {
     const int D = s->opt.depth;
     k_fourier<<<blocks((long long)M * s->nh, 256), 256, 0, s->stream>>>(s->xb, s->Bf[e], M, s->nh, s->h[0]);
@@ -394,7 +395,7 @@ int forward(sbr_surrogate* s, int e, int M, float* yout)
         memset(&ep, 0, sizeof(ep));
         ep.mode = kEpiBiasGelu;
         ep.M = M;
-        ep.c_f32 = s->z[l];
+        ep.c_f32 = keep_z ? s->z[l] : nullptr;
         ep.ldc = s->N[l];
         ep.out_bf16 = s->h[l + 1];
         ep.ldo = s->N[l];
@@ -815,7 +816,8 @@ int sbr_surrogate_predict(sbr_surrogate* s, const double* x, int64_t n, double* 
     if (!s || !x || n < 1 || (!y_mean && !spread_db)) return SBR_ERR_ARG;
     if (n > (1ll << 31) - 1) return SBR_ERR_ARG;
     SCK(cudaSetDevice(s->device), "cudaSetDevice");
-    const int M = 8192;
+    // prediction batches of 65536 rows: the GEMMs fill the GPU with two or more tiles per SM
+    const int M = (int)std::min<int64_t>(65536, ((n + 127) / 128) * 128);
     int rc = ensure_cap(s, M);
     if (rc != SBR_OK) return rc;
     float* x4 = nullptr;
@@ -837,7 +839,7 @@ int sbr_surrogate_predict(sbr_surrogate* s, const double* x, int64_t n, double* 
         cudaMemsetAsync(s->xb, 0, sizeof(float) * kIn * (size_t)Mp, s->stream);
         cudaMemcpyAsync(s->xb, x4 + kIn * b0, sizeof(float) * kIn * (size_t)cnt, cudaMemcpyDeviceToDevice, s->stream);
         for (int e = 0; e < s->opt.n_members && rc == SBR_OK; ++e)
-            rc = forward(s, e, Mp, s->y + (size_t)e * M * kOut);
+            rc = forward(s, e, Mp, s->y + (size_t)e * M * kOut, false);
         if (rc == SBR_OK)
             k_ens_stats<<<blocks(cnt, 256), 256, 0, s->stream>>>(s->y, s->opt.n_members, (long long)M * kOut, cnt,
                                                                  s->target_scale, dmean + kOut * b0, dspread + b0);

@@ -18,7 +18,9 @@ def G():
     return G
 
 
-@pytest.mark.parametrize("M,N,K,pad", [(128, 128, 64, 0), (256, 384, 512, 0), (1024, 512, 256, 8), (8192, 512, 512, 0)])
+# the last two shapes have two or more 128 x 128 tiles per SM: the persistent kernel (double-buffered TMEM)
+@pytest.mark.parametrize("M,N,K,pad", [(128, 128, 64, 0), (256, 384, 512, 0), (1024, 512, 256, 8), (8192, 512, 512, 0),
+                                       (16384, 512, 256, 8), (32768, 512, 512, 0)])
 def test_tensor_core_gemm(G, M, N, K, pad):
     torch = pytest.importorskip("torch")
     g = torch.Generator().manual_seed(M + N + K)
@@ -88,8 +90,9 @@ def _bf16_network(p, B, x, t, width, depth, nf):
     return loss, np.concatenate([np.concatenate([gw.ravel(), gb]) for gw, gb in grads])
 
 
-@pytest.mark.parametrize("width,depth,nf", [(128, 2, 128), (512, 6, 256)])
-def test_gradients_against_fp64_reference(G, width, depth, nf):
+# 16384 rows: the forward and input-gradient GEMMs of the deep network run the persistent kernel
+@pytest.mark.parametrize("width,depth,nf,n", [(128, 2, 128, 512), (512, 6, 256, 512), (512, 6, 256, 16384)])
+def test_gradients_against_fp64_reference(G, width, depth, nf, n):
     """Loss and gradients of the tensor-core forward and backward against the FP64
     reference network (oracle/mlp.py). The bound comes from BF16 itself: the same
     network with the kernels' BF16 and FP32 roundings (in FP64 otherwise) moves
@@ -98,8 +101,8 @@ def test_gradients_against_fp64_reference(G, width, depth, nf):
     1e-3 per layer back from the output of the rounded network (FP32 sums and
     library functions left)."""
     s = G.Surrogate(0, n_members=1, width=width, depth=depth, n_fourier=nf, fourier_sigma=2.0, seed=3)
-    rng, x = _samples(512, 4)
-    t = rng.normal(0, 1, (512, 4))
+    rng, x = _samples(n, 4)
+    t = rng.normal(0, 1, (n, 4))
     p = s.params(0).astype(np.float64)
     B = s.fourier(0).astype(np.float64)
     loss_g, g = s.grads(x, t)
@@ -127,6 +130,20 @@ def test_gradients_against_fp64_reference(G, width, depth, nf):
         # rounded network do; those differences add up layer by layer on the way back from the output
         assert e_emu <= 1e-3 * (depth - l + 1), (l, e_emu)
         assert e_gpu <= 2.0 * e_bf + 1e-3, (l, e_gpu, e_bf)
+
+
+def test_prediction_batches_agree_bit_for_bit(G):
+    """Every point's forward pass is independent of the others, so predicting
+    20,000 points at once (the persistent GEMM, BF16 activations only) gives the
+    same bits as predicting them 2,000 at a time (the per-tile GEMM)."""
+    s = G.Surrogate(0, n_members=2, width=512, depth=6, n_fourier=256, fourier_sigma=2.0, seed=9)
+    _, x = _samples(20000, 6)
+    y_all, sp_all = s.predict(x)
+    parts = [s.predict(x[i:i + 2000]) for i in range(0, len(x), 2000)]
+    s.close()
+    assert np.all(np.isfinite(y_all))
+    assert np.array_equal(y_all, np.concatenate([p[0] for p in parts]))
+    assert np.array_equal(sp_all, np.concatenate([p[1] for p in parts]))
 
 
 def test_training_reduces_loss_and_ensemble_spread(G):
