@@ -592,7 +592,8 @@ def surrogate_leg(G, torch, dev, ctx=None, scale=0.25, epochs=30):
         out[name] = {k: r[k] for k in ("domain", "training_samples", "rays_per_wavelength", "fourier_sigma",
                                        "served_fraction", "served_median_db_error", "served_within_0.5dB",
                                        "all_median_db_error", "hybrid_vs_plain", "plain_sbr_points_per_s",
-                                       "hybrid_points_per_s", "lattice_served_fraction", "bands", "train_s")}
+                                       "hybrid_points_per_s", "lattice_served_fraction", "lattice_points",
+                                       "lattice_surrogate_s", "bands", "train_s")}
     if own:
         ctx.close()
     return out

@@ -316,7 +316,8 @@ typedef struct {
     int blocks_per_sm;   /* resident 256-thread transport blocks per SM, 1..4 (default: occupancy limit) */
     int stack_depth;     /* traversal stack entries: 32, 64 or 128 (default 64); a query that needs more is
                             reported as a stack overflow (SBR_ERR_STACK_OVERFLOW) */
-    int chunk_rays_log2; /* rays per chunk when opt->chunk_rays is 0: 2^20 .. 2^27 (default 27) */
+    int chunk_rays_log2; /* rays per chunk when opt->chunk_rays is 0: 2^20 .. 2^29 (default 27); a chunk's
+                            two live-ray queues take 192 bytes per ray (about 100 GB at 2^29) */
     int po_item;         /* records per PO block: 512, 1024 or 2048 (default 1024) */
     int bvh_width;       /* 2: binary LBVH; 4: its 4-wide collapse (same boxes, fewer dependent fetches);
                             default 2 */

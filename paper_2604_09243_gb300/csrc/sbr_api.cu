@@ -316,7 +316,7 @@ bool tuning_ok(const sbr_tuning& t)
                       (t.raster == 0 || t.raster == 1);
     return tile && trav && (t.bvh_width == 2 || t.bvh_width == 4) && t.blocks_per_sm >= 1 && t.blocks_per_sm <= 4 &&
            (t.stack_depth == 32 || t.stack_depth == 64 || t.stack_depth == 128) && t.chunk_rays_log2 >= 20 &&
-           t.chunk_rays_log2 <= 27 && (t.po_item == 512 || t.po_item == 1024 || t.po_item == 2048);
+           t.chunk_rays_log2 <= 29 && (t.po_item == 512 || t.po_item == 1024 || t.po_item == 2048);
 }
 
 }  // namespace

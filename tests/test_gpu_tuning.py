@@ -64,7 +64,7 @@ def test_bad_settings_refused(G):
     with G.Context(0) as c:
         before = c.tuning()
         for bad in (dict(tile_w=3), dict(tile_w=64), dict(blocks_per_sm=0), dict(blocks_per_sm=5),
-                    dict(stack_depth=48), dict(po_item=300), dict(chunk_rays_log2=19), dict(chunk_rays_log2=28),
+                    dict(stack_depth=48), dict(po_item=300), dict(chunk_rays_log2=19), dict(chunk_rays_log2=30),
                     dict(bvh_width=3), dict(packet=2), dict(packet=1, bvh_width=4), dict(packet=1, stack_depth=128),
                     dict(silhouette=2), dict(octant=1, bvh_width=4), dict(octant=1, packet=1), dict(octant=2),
                     dict(raster=2), dict(raster=-1)):
