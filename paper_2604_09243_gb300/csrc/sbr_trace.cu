@@ -52,6 +52,19 @@ __device__ __forceinline__ float safe_rcp(float x)
     return __frcp_rn(fabsf(x) > tiny ? x : copysignf(tiny, x));
 }
 
+// Two fused multiply-adds in one packed FP32 instruction: (a.x b.x + c.x,
+// a.y b.y + c.y), each lane rounded once as fmaf rounds it.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
+{
+    float2 r;
+    asm("{\n\t.reg .b64 pa, pb, pc, pr;\n\t"
+        "mov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\tmov.b64 pc, {%6, %7};\n\t"
+        "fma.rn.f32x2 pr, pa, pb, pc;\n\tmov.b64 {%0, %1}, pr;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return r;
+}
+
 // ---------------------------------------------------------------- two-float helpers
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
 {
@@ -422,6 +435,9 @@ __device__ __forceinline__ void closest_hit(const float4* __restrict__ nodes, co
     int stack[kStack];
     const float3 inv = make_float3(safe_rcp(d.x), safe_rcp(d.y), safe_rcp(d.z));
     const float3 oi = make_float3(o.x * inv.x, o.y * inv.y, o.z * inv.z);
+    // the slab distances of a box coordinate pair (lo, hi) of one axis: one packed fma
+    const float2 ix = make_float2(inv.x, inv.x), iy = make_float2(inv.y, inv.y), iz = make_float2(inv.z, inv.z);
+    const float2 mx = make_float2(-oi.x, -oi.x), my = make_float2(-oi.y, -oi.y), mz = make_float2(-oi.z, -oi.z);
     h.t = FLT_MAX;
     h.k = -1;
     h.orig = INT_MAX;
@@ -441,16 +457,13 @@ __device__ __forceinline__ void closest_hit(const float4* __restrict__ nodes, co
             const float4 n0 = __ldg(nd), n1 = __ldg(nd + 1), n2 = __ldg(nd + 2), n3 = __ldg(nd + 3);
             if (kCount) ++nvis;
             const float tmax = h.t;
-            float ax0 = fmaf(n0.x, inv.x, -oi.x), ax1 = fmaf(n0.y, inv.x, -oi.x);
-            float ay0 = fmaf(n0.z, inv.y, -oi.y), ay1 = fmaf(n0.w, inv.y, -oi.y);
-            float az0 = fmaf(n2.x, inv.z, -oi.z), az1 = fmaf(n2.y, inv.z, -oi.z);
-            float bx0 = fmaf(n1.x, inv.x, -oi.x), bx1 = fmaf(n1.y, inv.x, -oi.x);
-            float by0 = fmaf(n1.z, inv.y, -oi.y), by1 = fmaf(n1.w, inv.y, -oi.y);
-            float bz0 = fmaf(n2.z, inv.z, -oi.z), bz1 = fmaf(n2.w, inv.z, -oi.z);
-            float an = fmaxf(fmaxf(fminf(ax0, ax1), fminf(ay0, ay1)), fmaxf(fminf(az0, az1), 0.f));
-            float af = fminf(fminf(fmaxf(ax0, ax1), fmaxf(ay0, ay1)), fminf(fmaxf(az0, az1), tmax));
-            float bn = fmaxf(fmaxf(fminf(bx0, bx1), fminf(by0, by1)), fmaxf(fminf(bz0, bz1), 0.f));
-            float bf = fminf(fminf(fmaxf(bx0, bx1), fmaxf(by0, by1)), fminf(fmaxf(bz0, bz1), tmax));
+            const float2 ax = fma2(make_float2(n0.x, n0.y), ix, mx), ay = fma2(make_float2(n0.z, n0.w), iy, my);
+            const float2 az = fma2(make_float2(n2.x, n2.y), iz, mz), bx = fma2(make_float2(n1.x, n1.y), ix, mx);
+            const float2 by = fma2(make_float2(n1.z, n1.w), iy, my), bz = fma2(make_float2(n2.z, n2.w), iz, mz);
+            float an = fmaxf(fmaxf(fminf(ax.x, ax.y), fminf(ay.x, ay.y)), fmaxf(fminf(az.x, az.y), 0.f));
+            float af = fminf(fminf(fmaxf(ax.x, ax.y), fmaxf(ay.x, ay.y)), fminf(fmaxf(az.x, az.y), tmax));
+            float bn = fmaxf(fmaxf(fminf(bx.x, bx.y), fminf(by.x, by.y)), fmaxf(fminf(bz.x, bz.y), 0.f));
+            float bf = fminf(fminf(fmaxf(bx.x, bx.y), fmaxf(by.x, by.y)), fminf(fmaxf(bz.x, bz.y), tmax));
             const int lref = __float_as_int(n3.x), rref = __float_as_int(n3.y);
             const bool hl = an <= af * kBoxGrow;
             const bool hr = (bn <= bf * kBoxGrow) && (rref != kEmptyRef);
