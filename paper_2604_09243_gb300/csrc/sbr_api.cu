@@ -99,6 +99,10 @@ struct sbr_ctx {
     DevBuf rbig, rbigctr;         // large triangles of a rasterised chunk and their two counters
     long long rbig_cap = 0;
     DevBuf hitlist;               // (ray, aspect) of the rasterised primary hits, read by bounce pass 1
+    // pooled late passes of sbr_trace: the live rays the chunks leave for pass kPoolPass, the trace's aspect
+    // table and ray offsets, each aspect's first record, the pool's counters and work counters
+    DevBuf pool, angall, rayoffall, recofall, poolctr, poolwork;
+    unsigned* pool_host = nullptr;  // pinned copy of the pool's count and flag
     long long rec_total = 0;
     int max_bounces = 0, trace_flags = 0;
     bool has_trace = false;
@@ -398,11 +402,12 @@ void sbr_destroy(sbr_ctx* c)
     cudaStreamSynchronize(c->stream);
     DevBuf* all[] = {&c->xyz, &c->tri, &c->nodes, &c->tris, &c->bvh_scratch, &c->bbox_dev, &c->err_dev, &c->nodes4,
                      &c->angles, &c->rayoff, &c->mask, &c->tilebase, &c->scan_scr, &c->recoff, &c->q0, &c->q1, &c->cover,
-                     &c->nodes_oct, &c->tripos, &c->vis, &c->visfull, &c->hitlist, &c->rbig, &c->rbigctr,
-                     &c->ctr64, &c->ctr32, &c->stats, &c->rec, &c->hit_tri, &c->hit_t, &c->hit_nb, &c->items,
+                     &c->nodes_oct, &c->tripos, &c->pool, &c->angall, &c->rayoffall, &c->recofall, &c->poolctr,
+                     &c->poolwork, &c->vis, &c->visfull, &c->hitlist, &c->rbig, &c->rbigctr, &c->ctr64, &c->ctr32, &c->stats, &c->rec, &c->hit_tri, &c->hit_t, &c->hit_nb, &c->items,
                      &c->itemoff, &c->recbeg, &c->freq, &c->kfreq, &c->partial, &c->E, &c->rcs};
     for (DevBuf* b : all) b->release();
     if (c->host_stage) cudaFreeHost(c->host_stage);
+    if (c->pool_host) cudaFreeHost(c->pool_host);
     if (c->stage_ev) cudaEventDestroy(c->stage_ev);
     for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
     free_plan(c->plan);
@@ -563,6 +568,7 @@ struct TraceRun {
     int flags = 0, max_bounces = 1;
     bool escape = false, hits = false, count = false, timed = false;
     long long chunk_cap = 1ll << 27;
+    int stop_after = -1;  // >= 0: a chunk runs its bounce passes up to this one only (the rest are pooled)
     int n_blocks = 0;
     int64_t n_launch = 0, n_pass = 0;
     size_t n_ev = 0;
@@ -604,10 +610,13 @@ int plan_chunks(sbr_ctx* c, TraceRun& R, std::vector<int64_t>& cut, long long* t
         max_angles = std::max(max_angles, (int)(cut[k + 1] - cut[k]));
     }
     const long long max_tiles = max_chunk / 32;
+    // hit masks and their prefix for the whole trace (a chunk uses its own range): the pooled late passes
+    // find the record slot of a ray of any chunk
+    const long long all_tiles = total / 32;
     CK(c->angles.ensure(sizeof(AngleDev) * (size_t)max_angles), "alloc angles");
     CK(c->rayoff.ensure(sizeof(long long) * (size_t)(max_angles + 1)), "alloc ray offsets");
     CK(c->recoff.ensure(sizeof(unsigned) * (size_t)(max_angles + 1)), "alloc record offsets");
-    CK(c->mask.ensure(sizeof(unsigned) * (size_t)max_tiles), "alloc mask");
+    CK(c->mask.ensure(sizeof(unsigned) * (size_t)all_tiles), "alloc mask");
     if (c->tune.silhouette) CK(c->cover.ensure(sizeof(unsigned) * (size_t)(max_tiles + max_angles)), "alloc cover");
     if (c->tune.raster) {
         CK(c->vis.ensure(sizeof(unsigned long long) * (size_t)max_chunk), "alloc raster keys");
@@ -617,7 +626,7 @@ int plan_chunks(sbr_ctx* c, TraceRun& R, std::vector<int64_t>& cut, long long* t
         CK(c->rbig.ensure(sizeof(int4) * (size_t)c->rbig_cap), "alloc raster triangle list");
         CK(c->rbigctr.ensure(sizeof(unsigned) * 2), "alloc raster triangle counters");
     }
-    CK(c->tilebase.ensure(sizeof(unsigned) * (size_t)max_tiles), "alloc tile base");
+    CK(c->tilebase.ensure(sizeof(unsigned) * (size_t)all_tiles), "alloc tile base");
     CK(c->scan_scr.ensure(scan_scratch_bytes(max_tiles)), "alloc scan scratch");
     CK(c->q0.ensure(sizeof(RayState) * (size_t)max_chunk), "alloc ray queue");
     CK(c->q1.ensure(sizeof(RayState) * (size_t)max_chunk), "alloc ray queue");
@@ -666,6 +675,31 @@ cudaError_t ensure_octant_nodes(sbr_ctx* c, cudaStream_t st)
 // sized for every ray of the chunk being valid. Records go to c->rec from index
 // rec_base on; earlier records are kept. chunk_records reads *hro_out once the
 // stream has passed it.
+// a transport pass; the primary pass includes the rasterisation of its hits
+cudaError_t run_pass(sbr_ctx* c, TraceRun& R, const TraceArgs& t)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (R.timed) {
+        e0 = pool_event(c, R.n_ev);
+        e1 = pool_event(c, R.n_ev + 1);
+        if (!e0 || !e1) return cudaErrorMemoryAllocation;
+        R.n_ev += 2;
+        R.ev_primary.push_back(t.bounce == 0 ? 1 : 0);
+        cudaEventRecord(e0, c->stream);
+    }
+    cudaError_t e = cudaSuccess;
+    if (t.vis && t.bounce == 0) {
+        e = launch_raster(t, (int)c->n_tri, c->vis.as<unsigned long long>(), c->visfull.as<unsigned>(), R.count,
+                          c->n_sms * 16, c->scan_scr.p, c->stream);
+        R.n_launch += 6;  // rasterisation, masks, 3-kernel scan, primary pass of the rasterised rays
+    }
+    if (e == cudaSuccess) e = launch_trace(t, R.n_blocks, R.count, c->tune.stack_depth, c->stream);
+    if (R.timed) cudaEventRecord(e1, c->stream);
+    ++R.n_launch;
+    ++R.n_pass;
+    return e;
+}
+
 int trace_chunk(sbr_ctx* c, TraceRun& R, int64_t a0, int64_t a1, long long rec_base, unsigned** hro_out)
 {
     const int na = (int)(a1 - a0);
@@ -674,29 +708,10 @@ int trace_chunk(sbr_ctx* c, TraceRun& R, int64_t a0, int64_t a1, long long rec_b
                                  tiled_rays(c->ang[(size_t)a1 - 1].grid, c->ang[(size_t)a1 - 1].tw) - base;
     unsigned* q_count = c->ctr32.as<unsigned>();
     unsigned* total_dev = q_count + 2 * (kMaxBounces + 2);
-    // a transport pass; the primary pass includes the rasterisation of its hits
-    auto pass = [&](const TraceArgs& t) -> cudaError_t {
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (R.timed) {
-            e0 = pool_event(c, R.n_ev);
-            e1 = pool_event(c, R.n_ev + 1);
-            if (!e0 || !e1) return cudaErrorMemoryAllocation;
-            R.n_ev += 2;
-            R.ev_primary.push_back(t.bounce == 0 ? 1 : 0);
-            cudaEventRecord(e0, c->stream);
-        }
-        cudaError_t e = cudaSuccess;
-        if (t.vis && t.bounce == 0) {
-            e = launch_raster(t, (int)c->n_tri, c->vis.as<unsigned long long>(), c->visfull.as<unsigned>(), R.count,
-                              c->n_sms * 16, c->scan_scr.p, c->stream);
-            R.n_launch += 6;  // rasterisation, masks, 3-kernel scan, primary pass of the rasterised rays
-        }
-        if (e == cudaSuccess) e = launch_trace(t, R.n_blocks, R.count, c->tune.stack_depth, c->stream);
-        if (R.timed) cudaEventRecord(e1, c->stream);
-        ++R.n_launch;
-        ++R.n_pass;
-        return e;
-    };
+    // the chunk's range of the trace-wide hit masks and their prefix (base is a multiple of 32)
+    unsigned* mask = c->mask.as<unsigned>() + base / 32;
+    unsigned* tilebase = c->tilebase.as<unsigned>() + base / 32;
+    auto pass = [&](const TraceArgs& t) -> cudaError_t { return run_pass(c, R, t); };
     // stage angle table and ray offsets
     const size_t bytes_a = sizeof(AngleDev) * (size_t)na, bytes_o = sizeof(long long) * (size_t)(na + 1);
     char* hs = (char*)stage(c, bytes_a + bytes_o + sizeof(unsigned) * (size_t)(na + 1));
@@ -749,8 +764,8 @@ int trace_chunk(sbr_ctx* c, TraceRun& R, int64_t a0, int64_t a1, long long rec_b
     ta.flags = R.flags;
     ta.visit_limit = (int)std::min<long long>(2 * c->n_tri + 64, 1ll << 30);
     ta.total_rays = chunk_rays;
-    ta.mask = c->mask.as<unsigned>();
-    ta.tile_base = c->tilebase.as<unsigned>();
+    ta.mask = mask;
+    ta.tile_base = tilebase;
     ta.stats = c->stats.as<unsigned long long>();
     if (R.hits) {
         ta.hit_tri = c->hit_tri.as<int>() + (size_t)base * R.max_bounces;
@@ -782,9 +797,9 @@ int trace_chunk(sbr_ctx* c, TraceRun& R, int64_t a0, int64_t a1, long long rec_b
     ta.q_out = qs[0];
     ta.q_out_count = q_count + 1;
     CK(pass(ta), "trace primary");
-    CK(scan_popc(ta.mask, c->tilebase.as<unsigned>(), chunk_rays / 32, total_dev, c->scan_scr.p, c->stream), "scan");
+    CK(scan_popc(ta.mask, tilebase, chunk_rays / 32, total_dev, c->scan_scr.p, c->stream), "scan");
     R.n_launch += 3;
-    CK(launch_angle_offsets(ta.ray_off, c->tilebase.as<unsigned>(), total_dev, na, c->recoff.as<unsigned>(), c->stream),
+    CK(launch_angle_offsets(ta.ray_off, tilebase, total_dev, na, c->recoff.as<unsigned>(), c->stream),
        "angle offsets");
     ++R.n_launch;
     unsigned* hro = (unsigned*)(hs + bytes_a + bytes_o);
@@ -799,7 +814,8 @@ int trace_chunk(sbr_ctx* c, TraceRun& R, int64_t a0, int64_t a1, long long rec_b
         CK(launch_emit_all(ta, R.n_blocks, c->stream), "emit");
         ++R.n_launch;
     } else {
-        const int last_pass = R.escape ? R.max_bounces : R.max_bounces - 1;
+        int last_pass = R.escape ? R.max_bounces : R.max_bounces - 1;
+        if (R.stop_after >= 0) last_pass = std::min(last_pass, R.stop_after);
         for (int b = 1; b <= last_pass; ++b) {
             ta.bounce = b;
             ta.work = c->ctr64.as<unsigned long long>() + b;
@@ -1274,6 +1290,138 @@ int build_plan(sbr_ctx* c, BatchPlan& P)
 }
 
 // sbr_trace and sbr_trace_bistatic (az_el_rx: [n][2] receivers, or null for monostatic)
+// ---------------------------------------------------------------- pooled late passes
+// A trace of several chunks runs bounce passes 1 .. kPoolPass - 1 per chunk;
+// the rays that go on are appended to one pool, and passes kPoolPass .. run
+// over the pool once for all chunks (a late pass holds few rays per chunk, and
+// a launch over few rays leaves most SMs idle while its slowest rays finish).
+// A pooled ray carries its trace-wide aspect index: the pooled passes read the
+// trace's aspect table, its ray offsets, the trace-wide hit masks and each
+// aspect's first record, so every record lands where the chunk reserved it.
+// The pool holds as many rays as a chunk queue; when a chunk's rays do not fit,
+// the pool is traced first and the chunk's rays appended again.
+constexpr int kPoolPass = 2;
+
+struct PoolRun {
+    bool on = false;
+    int64_t n_angles = 0;
+    unsigned cap = 0;
+    std::vector<long long> rec_of;  // per aspect: first record of its chunk
+};
+
+// run the pooled passes over the pool (its ping-pong partner: queue `partner`), then empty it
+int flush_pool(sbr_ctx* c, TraceRun& R, PoolRun& P, RayState* partner)
+{
+    const int last_pass = R.escape ? R.max_bounces : R.max_bounces - 1;
+    const size_t b_rec = sizeof(long long) * (size_t)P.n_angles;
+    long long* hr = (long long*)stage(c, b_rec);
+    if (!hr) return fail(c, SBR_ERR_OOM, "pinned staging allocation failed");
+    memcpy(hr, P.rec_of.data(), b_rec);
+    CK(cudaMemcpyAsync(c->recofall.p, hr, b_rec, cudaMemcpyHostToDevice, c->stream), "copy record bases");
+    CK(cudaEventRecord(c->stage_ev, c->stream), "record staging event");
+    unsigned* ctr = c->poolctr.as<unsigned>();  // [0] pool count, [1] flag, [2 + j] output of pooled pass j
+    CK(cudaMemsetAsync(ctr + 2, 0, sizeof(unsigned) * (kMaxBounces + 2), c->stream), "memset pool counters");
+    CK(cudaMemsetAsync(c->poolwork.p, 0, c->poolwork.cap, c->stream), "memset pool work");
+    TraceArgs ta;
+    memset(&ta, 0, sizeof(ta));
+    ta.wide = c->tune.bvh_width == 4;
+    ta.packet = c->tune.packet;
+    ta.octant = c->tune.octant;
+    ta.n_nodes = c->n_nodes;
+    for (int64_t a = 0; a < P.n_angles; ++a) ta.bistatic |= c->ang[(size_t)a].bistatic ? 1 : 0;
+    if (ta.octant) CK(ensure_octant_nodes(c, c->stream), "octant nodes");
+    ta.nodes = ta.wide ? c->nodes4.as<float4>() : (ta.octant ? c->nodes_oct.as<float4>() : c->nodes.as<float4>());
+    ta.tris = c->tris.as<float4>();
+    ta.tri_nrm = ta.tris + 3 * (size_t)c->n_tri;
+    ta.tri_v12 = ta.tris + 4 * (size_t)c->n_tri;
+    ta.angles = c->angall.as<AngleDev>();
+    ta.ray_off = c->rayoffall.as<long long>();
+    ta.n_angles = (int)P.n_angles;
+    ta.max_bounces = R.max_bounces;
+    ta.flags = R.flags;
+    ta.visit_limit = (int)std::min<long long>(2 * c->n_tri + 64, 1ll << 30);
+    ta.mask = c->mask.as<unsigned>();
+    ta.tile_base = c->tilebase.as<unsigned>();
+    ta.stats = c->stats.as<unsigned long long>();
+    ta.rec = c->rec.as<Record>();
+    ta.rec_of = c->recofall.as<long long>();
+    if (R.hits) {
+        ta.hit_tri = c->hit_tri.as<int>();
+        ta.hit_t = c->hit_t.as<float>();
+        ta.hit_nb = c->hit_nb.as<int>();
+    }
+    RayState* qs[2] = {c->pool.as<RayState>(), partner};
+    for (int b = kPoolPass; b <= last_pass; ++b) {
+        const int j = b - kPoolPass;
+        ta.bounce = b;
+        ta.work = c->poolwork.as<unsigned long long>() + j;
+        ta.q_in = qs[j & 1];
+        ta.q_in_count = j == 0 ? ctr : ctr + 2 + (j - 1);
+        ta.q_out = qs[(j + 1) & 1];
+        ta.q_out_count = ctr + 2 + j;
+        CK(run_pass(c, R, ta), "trace pooled pass");
+    }
+    CK(cudaMemsetAsync(ctr, 0, sizeof(unsigned) * 2, c->stream), "memset pool count");
+    return SBR_OK;
+}
+
+// append the rays chunk [a0, ..) left for pass kPoolPass to the pool, and copy the pool's count and flag to
+// c->pool_host (pinned; *hpc) for the host's next wait
+int pool_append(sbr_ctx* c, TraceRun& R, PoolRun& P, int64_t a0, unsigned** hpc)
+{
+    RayState* qs[2] = {c->q0.as<RayState>(), c->q1.as<RayState>()};
+    const int b = kPoolPass - 1;  // the chunk's last pass wrote queue b & 1, its count at q_count + b + 1
+    unsigned* ctr = c->poolctr.as<unsigned>();
+    CK(launch_pool_append(qs[b & 1], c->ctr32.as<unsigned>() + b + 1, c->pool.as<RayState>(), ctr, P.cap, (int)a0,
+                          ctr + 1, c->n_sms * 4, c->stream),
+       "pool append");
+    R.n_launch += 2;
+    CK(cudaMemcpyAsync(c->pool_host, ctr, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream), "copy pool count");
+    *hpc = c->pool_host;
+    return SBR_OK;
+}
+
+// set up the pool for a trace of the chunks cut (aspects c->ang, grids and ray offsets planned)
+int pool_setup(sbr_ctx* c, TraceRun& R, PoolRun& P, const std::vector<int64_t>& cut)
+{
+    const int64_t n = (int64_t)c->ang.size();
+    const int last_pass = R.escape ? R.max_bounces : R.max_bounces - 1;
+    P.on = cut.size() > 2 && last_pass >= kPoolPass && n <= (1 << 20);
+    if (!P.on) return SBR_OK;
+    P.n_angles = n;
+    P.cap = (unsigned)std::min<size_t>(c->q0.cap / sizeof(RayState), 0xFFFFFFFFu);
+    P.rec_of.assign((size_t)n, 0);
+    CK(c->pool.ensure(sizeof(RayState) * (size_t)P.cap), "alloc ray pool");
+    CK(c->angall.ensure(sizeof(AngleDev) * (size_t)n), "alloc aspect table");
+    CK(c->rayoffall.ensure(sizeof(long long) * (size_t)(n + 1)), "alloc ray offsets");
+    CK(c->recofall.ensure(sizeof(long long) * (size_t)n), "alloc record bases");
+    CK(c->poolctr.ensure(sizeof(unsigned) * (kMaxBounces + 4)), "alloc pool counters");
+    CK(c->poolwork.ensure(sizeof(unsigned long long) * (kMaxBounces + 2)), "alloc pool work counters");
+    if (!c->pool_host && cudaMallocHost((void**)&c->pool_host, 2 * sizeof(unsigned)) != cudaSuccess) {
+        c->pool_host = nullptr;
+        return fail(c, SBR_ERR_OOM, "pinned allocation failed");
+    }
+    const size_t b_a = sizeof(AngleDev) * (size_t)n, b_o = sizeof(long long) * (size_t)(n + 1);
+    char* hs = (char*)stage(c, b_a + b_o);
+    if (!hs) return fail(c, SBR_ERR_OOM, "pinned staging allocation failed");
+    AngleDev* ha = (AngleDev*)hs;
+    long long* ho = (long long*)(hs + b_a);
+    for (int64_t a = 0; a < n; ++a) {
+        const AngleHost& h = c->ang[(size_t)a];
+        ho[a] = h.ray_begin;
+        double rx[2] = {h.rx_az, h.rx_el};
+        ha[a] = to_dev(h.grid, h.ray_begin, h.tw, h.bistatic ? rx : nullptr);
+    }
+    const AngleHost& l = c->ang[(size_t)n - 1];
+    ho[n] = l.ray_begin + tiled_rays(l.grid, l.tw);
+    CK(cudaMemcpyAsync(c->angall.p, ha, b_a, cudaMemcpyHostToDevice, c->stream), "copy aspect table");
+    CK(cudaMemcpyAsync(c->rayoffall.p, ho, b_o, cudaMemcpyHostToDevice, c->stream), "copy ray offsets");
+    CK(cudaMemsetAsync(c->poolctr.p, 0, c->poolctr.cap, c->stream), "memset pool counters");
+    CK(cudaEventRecord(c->stage_ev, c->stream), "record staging event");
+    R.stop_after = kPoolPass - 1;
+    return SBR_OK;
+}
+
 int trace_impl(sbr_ctx* c, const double* az_el, const double* az_el_rx, int64_t n_angles, double ds, double eta,
                int max_bounces, const sbr_trace_opts* opt, sbr_trace_stats* stats)
 {
@@ -1308,14 +1456,42 @@ int trace_impl(sbr_ctx* c, const double* az_el, const double* az_el_rx, int64_t 
     int rc = plan_chunks(c, R, cut, &total, &launched);
     if (rc != SBR_OK) return rc;
     c->rec_total = 0;
-    // the host waits once per chunk: a chunk's records start where the previous chunk's end
+    PoolRun P;
+    rc = pool_setup(c, R, P, cut);
+    if (rc != SBR_OK) return rc;
+    RayState* partner = c->q0.as<RayState>();  // the chunk queue free between chunks (kPoolPass - 1 wrote q1)
+    static_assert(kPoolPass == 2, "the pool's partner queue assumes the chunks stop after bounce pass 1");
+    // the host waits once per chunk: a chunk's records start where the previous chunk's end; a chunk's rays
+    // that the full pool could not take are appended again after the pool is traced
     unsigned* hro = nullptr;
+    unsigned* hpc = nullptr;
+    auto settle = [&](size_t k) -> int {  // after the wait that follows chunk k
+        if (!P.on || !hpc[1]) return SBR_OK;
+        int r = flush_pool(c, R, P, partner);
+        if (r == SBR_OK) r = pool_append(c, R, P, cut[k], &hpc);
+        if (r != SBR_OK) return r;
+        CK(cudaStreamSynchronize(c->stream), "pool sync");
+        return hpc[1] ? fail(c, SBR_ERR_STATE, "sbr_trace: a chunk's live rays do not fit the ray pool") : SBR_OK;
+    };
     for (size_t k = 0; k + 1 < cut.size(); ++k) {
         if (k > 0) {
             CK(cudaStreamSynchronize(c->stream), "trace sync");
             c->rec_total += chunk_records(c, cut[k - 1], cut[k], c->rec_total, hro);
+            rc = settle(k - 1);
+            if (rc != SBR_OK) return rc;
         }
         rc = trace_chunk(c, R, cut[k], cut[k + 1], c->rec_total, &hro);
+        if (rc != SBR_OK) return rc;
+        if (P.on) {
+            for (int64_t a = cut[k]; a < cut[k + 1]; ++a) P.rec_of[(size_t)a] = c->rec_total;
+            rc = pool_append(c, R, P, cut[k], &hpc);
+            if (rc != SBR_OK) return rc;
+        }
+    }
+    if (P.on) {
+        CK(cudaStreamSynchronize(c->stream), "trace sync");
+        rc = settle(cut.size() - 2);
+        if (rc == SBR_OK) rc = flush_pool(c, R, P, partner);
         if (rc != SBR_OK) return rc;
     }
     unsigned long long hs_stats[kStatCount];

@@ -163,6 +163,8 @@ struct TraceArgs {
                                   // misses) and per-aspect all-rays flags
     const unsigned* tile_base;    // [total_rays / 32] exclusive prefix of popcount(mask)
     Record* rec;                  // dense records of this chunk (already offset to the chunk)
+    const long long* rec_of;      // pooled late passes (else null): per aspect, the first record of its
+                                  // chunk; rec is then the record buffer itself
     unsigned long long* work;     // work counter (zeroed before each pass)
     unsigned long long* stats;    // [kStatCount]
     int* hit_tri;                 // optional [total_rays][max_bounces] (RECORD_HITS)
@@ -186,6 +188,11 @@ int trace_blocks_per_sm();
 // the warp-cooperative traversal uses at most 64)
 cudaError_t launch_trace(const TraceArgs& a, int n_blocks, bool count_visits, int stack_depth, cudaStream_t st);
 cudaError_t launch_emit_all(const TraceArgs& a, int n_blocks, cudaStream_t st);
+// Append the *src_count live rays of src to the pool at *pool_count (their
+// aspect index shifted by angle_shift), then advance *pool_count; when they do
+// not fit under cap nothing is copied and *flag becomes 1.
+cudaError_t launch_pool_append(const RayState* src, const unsigned* src_count, RayState* pool, unsigned* pool_count,
+                               unsigned cap, int angle_shift, unsigned* flag, int n_blocks, cudaStream_t st);
 // Silhouette mask of the aspects of a chunk (a.angles, a.ray_off, a.n_angles):
 // sets cover bit (processing layout) of every grid ray whose (u, v) lies in
 // the conservatively widened projected box of some triangle, or the aspect's

@@ -941,7 +941,8 @@ __device__ __forceinline__ void emit(const TraceArgs& a, const Ray& r, bool zero
     const long long tile = g >> 5;
     const unsigned bit = (unsigned)(g & 31);
     const unsigned slot = a.tile_base[tile] + __popc(a.mask[tile] & ((1u << bit) - 1u));
-    float4* p = reinterpret_cast<float4*>(a.rec + slot);
+    Record* rec = a.rec_of ? a.rec + a.rec_of[r.angle] : a.rec;
+    float4* p = reinterpret_cast<float4*>(rec + slot);
     if (zero) {
         __stcs(p + 0, make_float4(0.f, 0.f, 0.f, 0.f));
         __stcs(p + 1, make_float4(0.f, 0.f, 0.f, __int_as_float(ray_id)));
@@ -1863,6 +1864,36 @@ __global__ void __launch_bounds__(kTraceThreads) k_emit_all(const TraceArgs a)
     if (ovf) atomicAdd(a.stats + kStatOverflow, 1ull);
 }
 
+// ---------------------------------------------------------------- pooled late passes
+// The live rays that a chunk's early passes leave for the next pass are
+// appended to a pool shared by the chunks, so that the late passes run once over
+// the rays of every chunk: a late pass holds few rays per chunk, and a launch
+// over few rays leaves most of the GPU idle while its slowest rays finish.
+// A pooled ray's aspect index becomes the trace's (+ angle_shift).
+__global__ void __launch_bounds__(256) k_pool_append(const RayState* __restrict__ src, const unsigned* src_count,
+                                                     RayState* __restrict__ pool, const unsigned* pool_count,
+                                                     unsigned cap, int angle_shift)
+{
+    const unsigned n = *src_count, at = *pool_count;
+    if ((unsigned long long)at + n > cap) return;  // k_pool_commit raises the flag
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4* p = reinterpret_cast<const float4*>(src + i);
+        float4* q = reinterpret_cast<float4*>(pool + at + i);
+#pragma unroll
+        for (int w = 0; w < 5; ++w) __stcs(q + w, __ldcs(p + w));
+        int4 g = __ldcs(reinterpret_cast<const int4*>(p) + 5);
+        g.x += angle_shift;
+        __stcs(reinterpret_cast<int4*>(q) + 5, g);
+    }
+}
+
+__global__ void k_pool_commit(const unsigned* src_count, unsigned* pool_count, unsigned cap, unsigned* flag)
+{
+    const unsigned n = *src_count, at = *pool_count;
+    if ((unsigned long long)at + n > cap) *flag = 1u;
+    else *pool_count = at + n;
+}
+
 __global__ void k_angle_offsets(const long long* ray_off, const unsigned* tile_base, const unsigned* total,
                                 int n_angles, unsigned* rec_off)
 {
@@ -1947,6 +1978,14 @@ cudaError_t launch_emit_all(const TraceArgs& a, int n_blocks, cudaStream_t st)
 {
     if (a.bistatic) k_emit_all<true><<<n_blocks, kTraceThreads, 0, st>>>(a);
     else k_emit_all<false><<<n_blocks, kTraceThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pool_append(const RayState* src, const unsigned* src_count, RayState* pool, unsigned* pool_count,
+                               unsigned cap, int angle_shift, unsigned* flag, int n_blocks, cudaStream_t st)
+{
+    k_pool_append<<<n_blocks, 256, 0, st>>>(src, src_count, pool, pool_count, cap, angle_shift);
+    k_pool_commit<<<1, 1, 0, st>>>(src_count, pool_count, cap, flag);
     return cudaGetLastError();
 }
 

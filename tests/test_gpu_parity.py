@@ -347,6 +347,77 @@ def test_chunked_trace_matches_single_chunk(G, ctx):
     assert np.array_equal(E1, E2)
 
 
+def _hits_fields(G, case, angles, B, chunk_rays, flags=0, sp=1.0):
+    """Trace in a fresh context (its ray queues sized by this trace's chunks)."""
+    with G.Context(0) as c:
+        c.load_mesh(case["xyz"], case["tri"])
+        st = c.trace(angles, sp * case["spacing"], eta=case["eta"], max_bounces=B, offset=case["offset"],
+                     flags=HITS | flags, chunk_rays=chunk_rays)
+        hits = [c.get_hits(a) for a in range(len(angles))]
+        E, R = c.po_integrate([float(case["freqs"][0]), 0.9 * float(case["freqs"][0])], "HH,VV,HV,VH")
+        recs = [c.get_records(a) for a in range(len(angles))]
+    return st, hits, E, R, recs
+
+
+def _assert_same(a, b):
+    sa, ha, Ea, Ra, ra = a
+    sb, hb, Eb, Rb, rb = b
+    for k in ("rays_launched", "ray_bounces", "valid_rays", "stack_overflows", "bounce_hits"):
+        assert sa[k] == sb[k], k
+    for x, y in zip(ha, hb):
+        for u, v in zip(x, y):
+            assert np.array_equal(u, v)
+    for x, y in zip(ra, rb):
+        for k in x:
+            assert np.array_equal(x[k], y[k]), k
+    assert np.array_equal(Ea, Eb) and np.array_equal(Ra, Rb)
+
+
+def test_pooled_late_passes_match_per_chunk_passes(G):
+    """A trace of several chunks runs the bounce passes after the first once
+    over the rays of all chunks (the ray pool). On the aircraft at 1 GHz (ten
+    bounces, 12 aspects in chunks of 2^18 rays) every ray's hits, every record
+    and the fields equal, bit for bit, those of the same aspects traced as one
+    chunk, whose passes all run per chunk."""
+    case = S.aircraft_case(1e9, n_az=360)
+    ang = case["angles"][::30]
+    B = case["max_bounces"]
+    with G.Context(0) as c:
+        c.load_mesh(case["xyz"], case["tri"])
+        n_chunks = c.trace(ang, case["spacing"], eta=case["eta"], max_bounces=2, offset=case["offset"],
+                           chunk_rays=1 << 18)["pass_launches"] // 2
+    assert n_chunks >= 6
+    one = _hits_fields(G, case, ang, B, 0)
+    pooled = _hits_fields(G, case, ang, B, 1 << 18)
+    # per chunk the primary pass and bounce pass 1; passes 2 .. B - 1 once over the pool
+    assert pooled[0]["pass_launches"] == 2 * n_chunks + (B - 2)
+    _assert_same(one, pooled)
+
+
+def test_ray_pool_overflow_flushes_and_keeps_results(G):
+    """When the rays a chunk leaves for the late passes do not fit the pool
+    (which holds as many rays as a chunk), the pool is traced first and the
+    chunk's rays appended again: the trihedral's multi-bounce rays in chunks of
+    2^16 rays overflow it several times, and the hits, records and fields still
+    equal those of one chunk. The escape-required variant (one extra query per
+    ray still hitting) goes through the same pooled passes."""
+    case = S.trihedral_case()
+    ang = case["angles"][::20]
+    # chunks: with B = 2 no pass is pooled, one primary and one bounce pass per chunk
+    with G.Context(0) as c:
+        c.load_mesh(case["xyz"], case["tri"])
+        n_chunks = c.trace(ang, 3 * case["spacing"], eta=case["eta"], max_bounces=2, offset=case["offset"],
+                           chunk_rays=1 << 16)["pass_launches"] // 2
+    assert n_chunks >= 4
+    one = _hits_fields(G, case, ang, 3, 0, sp=3.0)
+    pooled = _hits_fields(G, case, ang, 3, 1 << 16, sp=3.0)
+    # one pooled pass per flush: more than one flush means the pool overflowed
+    assert pooled[0]["pass_launches"] - 2 * n_chunks >= 2
+    _assert_same(one, pooled)
+    esc = G.TRACE_REQUIRE_ESCAPE
+    _assert_same(_hits_fields(G, case, ang, 3, 0, esc, sp=3.0), _hits_fields(G, case, ang, 3, 1 << 16, esc, sp=3.0))
+
+
 def test_many_aspects_match_split_calls(G, ctx):
     """20,000 aspects in one call (a staging upload above the first pinned
     buffer, a PO work list of 20,000 aspect rows expanded on the device) give
