@@ -955,6 +955,8 @@ def run_sbr(args, case, ws, rank, local, pg):
             "clocks": clocks}
     if not args.no_surrogate:
         line["surrogate"] = surrogate_leg(G, torch, local, ctx if args.workload.startswith("aircraft") else None)
+    # the legs below make contexts of their own: free the timed workload's buffers first
+    ctx.close()
     if args.workload != "trihedral" and not args.no_trihedral:
         line["trihedral"] = sweep_value(G, torch, local, S.trihedral_case(), dict(tile_w=4, octant=1), 20, 3, flush)
     if args.batch_requests > 0:
@@ -970,7 +972,6 @@ def run_sbr(args, case, ws, rank, local, pg):
                                           + ("full ray grids" if frac >= 1.0 else
                                              f"a seeded {100 * frac:.3g} % of each aspect's rays")
                                           + f", {b} ray-bounces in {t:.1f} s wall"}
-    ctx.close()
     if rank == 0:
         print(json.dumps(line))
 
