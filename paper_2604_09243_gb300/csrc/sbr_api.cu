@@ -569,6 +569,9 @@ struct TraceRun {
     bool escape = false, hits = false, count = false, timed = false;
     long long chunk_cap = 1ll << 27;
     int stop_after = -1;  // >= 0: a chunk runs its bounce passes up to this one only (the rest are pooled)
+    RayState* pool = nullptr;  // with stop_after: the chunk's last pass appends the rays that go on here
+    unsigned* pool_count = nullptr;
+    unsigned pool_cap = 0;
     int n_blocks = 0;
     int64_t n_launch = 0, n_pass = 0;
     size_t n_ev = 0;
@@ -823,6 +826,12 @@ int trace_chunk(sbr_ctx* c, TraceRun& R, int64_t a0, int64_t a1, long long rec_b
             ta.q_in_count = q_count + b;
             ta.q_out = qs[b & 1];
             ta.q_out_count = q_count + b + 1;
+            if (R.pool && b == last_pass) {  // the rays that go on join the ray pool (those it cannot take: q_out)
+                ta.pool = R.pool;
+                ta.pool_count = R.pool_count;
+                ta.pool_cap = R.pool_cap;
+                ta.angle_shift = (int)a0;
+            }
             CK(pass(ta), "trace bounce");
             ta.hit_list = nullptr;  // only bounce pass 1 reads the list
         }
@@ -1365,20 +1374,38 @@ int flush_pool(sbr_ctx* c, TraceRun& R, PoolRun& P, RayState* partner)
     return SBR_OK;
 }
 
-// append the rays chunk [a0, ..) left for pass kPoolPass to the pool, and copy the pool's count and flag to
-// c->pool_host (pinned; *hpc) for the host's next wait
-int pool_append(sbr_ctx* c, TraceRun& R, PoolRun& P, int64_t a0, unsigned** hpc)
+// after a chunk: copy the pool's count and flag, and the count of the chunk's rays that found the pool full, to
+// c->pool_host (pinned) for the host's next wait
+int pool_note(sbr_ctx* c)
 {
+    const int b = kPoolPass - 1;  // the chunk's last pass: its overflow count at q_count + b + 1
+    CK(cudaMemcpyAsync(c->pool_host, c->poolctr.p, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream),
+       "copy pool count");
+    CK(cudaMemcpyAsync(c->pool_host + 2, c->ctr32.as<unsigned>() + b + 1, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                       c->stream),
+       "copy pool overflow");
+    return SBR_OK;
+}
+
+// after the wait that follows a chunk whose rays did not all fit the pool: trace the full pool, then append the
+// rays the chunk kept in its queue (their aspect index already the trace's)
+int pool_overflow(sbr_ctx* c, TraceRun& R, PoolRun& P, RayState* partner)
+{
+    const int b = kPoolPass - 1;
     RayState* qs[2] = {c->q0.as<RayState>(), c->q1.as<RayState>()};
-    const int b = kPoolPass - 1;  // the chunk's last pass wrote queue b & 1, its count at q_count + b + 1
     unsigned* ctr = c->poolctr.as<unsigned>();
-    CK(launch_pool_append(qs[b & 1], c->ctr32.as<unsigned>() + b + 1, c->pool.as<RayState>(), ctr, P.cap, (int)a0,
-                          ctr + 1, c->n_sms * 4, c->stream),
+    c->pool_host[3] = P.cap;
+    CK(cudaMemcpyAsync(ctr, c->pool_host + 3, sizeof(unsigned), cudaMemcpyHostToDevice, c->stream), "set pool count");
+    int r = flush_pool(c, R, P, partner);
+    if (r != SBR_OK) return r;
+    CK(launch_pool_append(qs[b & 1], c->ctr32.as<unsigned>() + b + 1, c->pool.as<RayState>(), ctr, P.cap, 0, ctr + 1,
+                          c->n_sms * 4, c->stream),
        "pool append");
     R.n_launch += 2;
-    CK(cudaMemcpyAsync(c->pool_host, ctr, 2 * sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream), "copy pool count");
-    *hpc = c->pool_host;
-    return SBR_OK;
+    r = pool_note(c);
+    if (r != SBR_OK) return r;
+    CK(cudaStreamSynchronize(c->stream), "pool sync");
+    return c->pool_host[1] ? fail(c, SBR_ERR_STATE, "sbr_trace: a chunk's live rays do not fit the ray pool") : SBR_OK;
 }
 
 // set up the pool for a trace of the chunks cut (aspects c->ang, grids and ray offsets planned)
@@ -1397,7 +1424,7 @@ int pool_setup(sbr_ctx* c, TraceRun& R, PoolRun& P, const std::vector<int64_t>& 
     CK(c->recofall.ensure(sizeof(long long) * (size_t)n), "alloc record bases");
     CK(c->poolctr.ensure(sizeof(unsigned) * (kMaxBounces + 4)), "alloc pool counters");
     CK(c->poolwork.ensure(sizeof(unsigned long long) * (kMaxBounces + 2)), "alloc pool work counters");
-    if (!c->pool_host && cudaMallocHost((void**)&c->pool_host, 2 * sizeof(unsigned)) != cudaSuccess) {
+    if (!c->pool_host && cudaMallocHost((void**)&c->pool_host, 4 * sizeof(unsigned)) != cudaSuccess) {
         c->pool_host = nullptr;
         return fail(c, SBR_ERR_OOM, "pinned allocation failed");
     }
@@ -1419,6 +1446,9 @@ int pool_setup(sbr_ctx* c, TraceRun& R, PoolRun& P, const std::vector<int64_t>& 
     CK(cudaMemsetAsync(c->poolctr.p, 0, c->poolctr.cap, c->stream), "memset pool counters");
     CK(cudaEventRecord(c->stage_ev, c->stream), "record staging event");
     R.stop_after = kPoolPass - 1;
+    R.pool = c->pool.as<RayState>();
+    R.pool_count = c->poolctr.as<unsigned>();
+    R.pool_cap = P.cap;
     return SBR_OK;
 }
 
@@ -1461,36 +1491,29 @@ int trace_impl(sbr_ctx* c, const double* az_el, const double* az_el_rx, int64_t 
     if (rc != SBR_OK) return rc;
     RayState* partner = c->q0.as<RayState>();  // the chunk queue free between chunks (kPoolPass - 1 wrote q1)
     static_assert(kPoolPass == 2, "the pool's partner queue assumes the chunks stop after bounce pass 1");
-    // the host waits once per chunk: a chunk's records start where the previous chunk's end; a chunk's rays
-    // that the full pool could not take are appended again after the pool is traced
+    // the host waits once per chunk: a chunk's records start where the previous chunk's end; rays that found
+    // the pool full are appended once it has been traced
     unsigned* hro = nullptr;
-    unsigned* hpc = nullptr;
-    auto settle = [&](size_t k) -> int {  // after the wait that follows chunk k
-        if (!P.on || !hpc[1]) return SBR_OK;
-        int r = flush_pool(c, R, P, partner);
-        if (r == SBR_OK) r = pool_append(c, R, P, cut[k], &hpc);
-        if (r != SBR_OK) return r;
-        CK(cudaStreamSynchronize(c->stream), "pool sync");
-        return hpc[1] ? fail(c, SBR_ERR_STATE, "sbr_trace: a chunk's live rays do not fit the ray pool") : SBR_OK;
+    auto settle = [&]() -> int {  // after the wait that follows a chunk
+        if (!P.on || c->pool_host[0] <= P.cap) return SBR_OK;
+        return pool_overflow(c, R, P, partner);
     };
     for (size_t k = 0; k + 1 < cut.size(); ++k) {
         if (k > 0) {
             CK(cudaStreamSynchronize(c->stream), "trace sync");
             c->rec_total += chunk_records(c, cut[k - 1], cut[k], c->rec_total, hro);
-            rc = settle(k - 1);
+            rc = settle();
             if (rc != SBR_OK) return rc;
         }
-        rc = trace_chunk(c, R, cut[k], cut[k + 1], c->rec_total, &hro);
-        if (rc != SBR_OK) return rc;
-        if (P.on) {
+        if (P.on)
             for (int64_t a = cut[k]; a < cut[k + 1]; ++a) P.rec_of[(size_t)a] = c->rec_total;
-            rc = pool_append(c, R, P, cut[k], &hpc);
-            if (rc != SBR_OK) return rc;
-        }
+        rc = trace_chunk(c, R, cut[k], cut[k + 1], c->rec_total, &hro);
+        if (rc == SBR_OK && P.on) rc = pool_note(c);
+        if (rc != SBR_OK) return rc;
     }
     if (P.on) {
         CK(cudaStreamSynchronize(c->stream), "trace sync");
-        rc = settle(cut.size() - 2);
+        rc = settle();
         if (rc == SBR_OK) rc = flush_pool(c, R, P, partner);
         if (rc != SBR_OK) return rc;
     }

@@ -165,6 +165,10 @@ struct TraceArgs {
     Record* rec;                  // dense records of this chunk (already offset to the chunk)
     const long long* rec_of;      // pooled late passes (else null): per aspect, the first record of its
                                   // chunk; rec is then the record buffer itself
+    RayState* pool;               // optional: the pass appends the rays that go on to this ray pool (their
+    unsigned* pool_count;         // aspect index + angle_shift) while it holds fewer than pool_cap; those
+    unsigned pool_cap;            // that find it full go to q_out
+    int angle_shift;
     unsigned long long* work;     // work counter (zeroed before each pass)
     unsigned long long* stats;    // [kStatCount]
     int* hit_tri;                 // optional [total_rays][max_bounces] (RECORD_HITS)

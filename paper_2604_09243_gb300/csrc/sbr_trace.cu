@@ -971,17 +971,37 @@ __device__ __forceinline__ int find_angle(const long long* __restrict__ off, int
     return lo;
 }
 
-// warp-aggregated append to the live-ray queue; every lane of the warp must call it
-__device__ __forceinline__ void push(const TraceArgs& a, bool want, const Ray& r)
+// warp-aggregated append of the lanes of m to queue q; every lane of the warp must call it
+__device__ __forceinline__ void append(RayState* q, unsigned* count, unsigned m, const Ray& r)
 {
-    const unsigned m = __ballot_sync(kFull, want);
-    if (!m) return;
     const int lane = threadIdx.x & 31;
     const int leader = __ffs(m) - 1;
     unsigned base = 0;
-    if (lane == leader) base = atomicAdd(a.q_out_count, (unsigned)__popc(m));
+    if (lane == leader) base = atomicAdd(count, (unsigned)__popc(m));
     base = __shfl_sync(kFull, base, leader);
-    if (want) store_state(a.q_out, base + __popc(m & ((1u << lane) - 1u)), r);
+    if ((m >> lane) & 1u) store_state(q, base + __popc(m & ((1u << lane) - 1u)), r);
+}
+
+// the rays that go on: to the live-ray queue, or to the ray pool while it has room
+__device__ __forceinline__ void push(const TraceArgs& a, bool want, Ray& r)
+{
+    const unsigned m = __ballot_sync(kFull, want);
+    if (!m) return;
+    if (!a.pool) {
+        append(a.q_out, a.q_out_count, m, r);
+        return;
+    }
+    r.angle += a.angle_shift;  // the pool indexes the trace's aspects
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(a.pool_count, (unsigned)__popc(m));
+    base = __shfl_sync(kFull, base, leader);
+    const unsigned idx = base + __popc(m & ((1u << lane) - 1u));
+    const bool fit = want && idx < a.pool_cap;
+    if (fit) store_state(a.pool, idx, r);
+    const unsigned over = __ballot_sync(kFull, want && !fit);
+    if (over) append(a.q_out, a.q_out_count, over, r);  // kept until the pool has been traced
 }
 
 template <bool kCount>
