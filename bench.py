@@ -65,7 +65,7 @@ OPS_PRIMARY_HIT = 185
 # bounce queries of a step. None where no capture of the current kernels exists.
 TRAFFIC_PER_QUERY = {
     # k_bounce, warm L2 (ncu --cache-control none), 36 of the 360 aspects, five identical sweeps, ray pool
-    "aircraft10": [(110.1, {"bvh_width": 2, "octant": 0, "packet": 0})],
+    "aircraft10": [(110.0, {"bvh_width": 2, "octant": 0, "packet": 0})],
 }
 
 

@@ -89,7 +89,8 @@ typedef struct {
     double offset_v; /* same along v */
     int flags;       /* SBR_TRACE_* */
     int chunk_rays;  /* rays per internal batch of aspects (0 = 2^27); bounds the live-ray queue
-                        memory at 192 bytes per ray; an aspect larger than this is refused */
+                        memory at 192 bytes per ray (288 with the ray pool of a trace of several
+                        chunks); an aspect larger than this is refused */
 } sbr_trace_opts;
 
 /* Counters of the last sbr_trace (summed over its angles). */
@@ -213,7 +214,10 @@ int sbr_ray_grid_box(const float* bbox6, double az_deg, double el_deg, double ra
  * trace-integrate decomposition). The records stay in the context until the
  * next sbr_trace or sbr_load_mesh; sbr_po_integrate reads them for any list of
  * frequencies. `opt` may be NULL; `stats` may be NULL (it is filled on return
- * and then the stream is synchronised). max_bounces in 1..128. */
+ * and then the stream is synchronised). max_bounces in 1..128. The aspects
+ * are traced in chunks of at most opt->chunk_rays rays; when there are several,
+ * the bounces after the first run once over the rays of all chunks (a ray pool
+ * the size of a chunk queue), which changes no ray's hits or records. */
 int sbr_trace(sbr_ctx* ctx, const double* az_el_deg, int64_t n_angles, double ray_spacing_m, double margin_eta,
               int max_bounces, const sbr_trace_opts* opt, sbr_trace_stats* stats);
 
@@ -317,7 +321,8 @@ typedef struct {
     int stack_depth;     /* traversal stack entries: 32, 64 or 128 (default 64); a query that needs more is
                             reported as a stack overflow (SBR_ERR_STACK_OVERFLOW) */
     int chunk_rays_log2; /* rays per chunk when opt->chunk_rays is 0: 2^20 .. 2^29 (default 27); a chunk's
-                            two live-ray queues take 192 bytes per ray (about 100 GB at 2^29) */
+                            two live-ray queues take 192 bytes per ray (about 100 GB at 2^29), and
+                            sbr_trace over several chunks adds a ray pool of one queue's size */
     int po_item;         /* records per PO block: 512, 1024 or 2048 (default 1024) */
     int bvh_width;       /* 2: binary LBVH; 4: its 4-wide collapse (same boxes, fewer dependent fetches);
                             default 2 */
