@@ -608,6 +608,26 @@ def test_bistatic_trihedral_multibounce(G, ctx, orc):
                       offset=case["offset"])
 
 
+def test_bistatic_pooled_passes_match_one_chunk(G):
+    """Bistatic aspects in chunks: the pooled late passes keep each aspect's
+    receiver (its visibility queries and radiation toward it), so the trihedral
+    traced in chunks of 2^16 rays gives the hits, records and fields of one
+    chunk, bit for bit."""
+    case = S.trihedral_case()
+    tx = case["angles"][::30]
+    rx = np.stack([np.linspace(20.0, 70.0, len(tx)), np.linspace(25.0, 45.0, len(tx))], 1)
+    out = []
+    for chunk in (0, 1 << 16):
+        with G.Context(0) as c:
+            c.load_mesh(case["xyz"], case["tri"])
+            st = c.trace(tx, 3 * case["spacing"], eta=case["eta"], max_bounces=3, offset=case["offset"], flags=HITS,
+                         chunk_rays=chunk, rx=rx)
+            out.append((st, [c.get_hits(a) for a in range(len(tx))], *c.po_integrate([10e9], "HH,VV,HV,VH"),
+                        [c.get_records(a) for a in range(len(tx))]))
+    assert out[1][0]["pass_launches"] > out[0][0]["pass_launches"]  # several chunks
+    _assert_same(out[0], out[1])
+
+
 def test_bistatic_at_transmitter_matches_monostatic_single_bounce(G, ctx):
     xyz, tri = S.square_plate(1.0, 8)
     ctx.load_mesh(xyz, tri)
