@@ -1310,6 +1310,8 @@ int build_plan(sbr_ctx* c, BatchPlan& P)
 // The pool holds as many rays as a chunk queue; when a chunk's rays do not fit,
 // the pool is traced first and the chunk's rays appended again.
 constexpr int kPoolPass = 2;
+// sbr_run_batch: a group of chunks holds the records of at most this many chunks' worth of rays
+constexpr long long kGroupRecords = 4;
 
 struct PoolRun {
     bool on = false;
@@ -1650,17 +1652,49 @@ int sbr_run_batch(sbr_ctx* c, const sbr_request* req, int64_t n_req, const doubl
         dE = E_out ? c->E.as<double>() : nullptr;
         dR = rcs_out ? c->rcs.as<double>() : nullptr;
     }
-    // each chunk is traced once and integrated for all its requests' frequencies
-    // before the next chunk reuses the record buffer
-    long long valid = 0;
+    // each chunk is traced once and integrated for all its requests' frequencies. Without the ray pool every
+    // chunk is integrated before the next reuses the record buffer; with it, consecutive chunks form a group whose
+    // records stay until the group's pooled late passes have run, and the group is integrated then
+    long long valid = 0, rec_base = 0;
+    size_t g0 = 0;
     CK(cudaMemsetAsync(c->err_dev.as<int>() + 3, 0, sizeof(int), c->stream), "memset po flag");
+    PoolRun P;
+    rc = pool_setup(c, R, P, cut);
+    if (rc != SBR_OK) return rc;
+    RayState* partner = c->q0.as<RayState>();
+    auto close_group = [&](size_t g1) -> int {
+        int r = flush_pool(c, R, P, partner);
+        if (r == SBR_OK) r = po_run(c, pa, cut[g0], cut[g1], f0, nf, row, dE, dR, &R.n_launch);
+        rec_base = 0;
+        g0 = g1;
+        return r;
+    };
     for (size_t k = 0; k + 1 < cut.size(); ++k) {
+        const AngleHost& last = c->ang[(size_t)cut[k + 1] - 1];
+        const long long rays = last.ray_begin + tiled_rays(last.grid, last.tw) - c->ang[(size_t)cut[k]].ray_begin;
+        if (P.on && k > g0 && rec_base + rays > kGroupRecords * R.chunk_cap) {
+            rc = close_group(k);
+            if (rc != SBR_OK) return rc;
+        }
+        if (P.on)
+            for (int64_t a = cut[k]; a < cut[k + 1]; ++a) P.rec_of[(size_t)a] = rec_base;
         unsigned* hro = nullptr;
-        rc = trace_chunk(c, R, cut[k], cut[k + 1], 0, &hro);
+        rc = trace_chunk(c, R, cut[k], cut[k + 1], rec_base, &hro);
+        if (rc == SBR_OK && P.on) rc = pool_note(c);
         if (rc != SBR_OK) return rc;
         CK(cudaStreamSynchronize(c->stream), "trace sync");
-        valid += chunk_records(c, cut[k], cut[k + 1], 0, hro);
-        rc = po_run(c, pa, cut[k], cut[k + 1], f0, nf, row, dE, dR, &R.n_launch);
+        const long long n = chunk_records(c, cut[k], cut[k + 1], rec_base, hro);
+        valid += n;
+        if (P.on) {
+            rec_base += n;
+            if (c->pool_host[0] > P.cap) rc = pool_overflow(c, R, P, partner);
+        } else {
+            rc = po_run(c, pa, cut[k], cut[k + 1], f0, nf, row, dE, dR, &R.n_launch);
+        }
+        if (rc != SBR_OK) return rc;
+    }
+    if (P.on) {
+        rc = close_group(cut.size() - 1);
         if (rc != SBR_OK) return rc;
     }
     if (!out_on_device) {
