@@ -272,9 +272,11 @@ typedef struct {
  * done inside one GPU): every request is traced once (Algorithm 2, Eq. L1-L3
  * with its own spacing) and its frequency-independent ray paths are integrated
  * for all of its frequencies (Eq. po_sum / em6), requests of uneven ray counts
- * packed into chunks of persistent-kernel passes. Chunks are integrated as soon
- * as they are traced, so record memory stays bounded by the chunk size
- * (opt->chunk_rays). Output row r0 + q (r0 = sum of n_freq over the earlier
+ * packed into chunks of persistent-kernel passes. Consecutive chunks form
+ * groups of at most four chunks' worth of records; the bounces after the first
+ * run once over the rays of a group (the ray pool of sbr_trace), and a group is
+ * integrated as soon as it is traced, so record memory stays bounded by a few
+ * chunk sizes (opt->chunk_rays). Output row r0 + q (r0 = sum of n_freq over the earlier
  * requests) holds frequency q of a request: E_re_im [rows][n_pol][2],
  * rcs_dbsm [rows][n_pol], host (out_on_device = 0) or device (1) memory.
  * The call synchronises; it leaves no trace results behind (sbr_po_integrate
