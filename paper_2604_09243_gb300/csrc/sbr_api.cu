@@ -1936,7 +1936,7 @@ int sbr_autotune(sbr_ctx* c, const sbr_request* req, int64_t n_req, const double
         if (p == 2) vals = {32, 16, 8, 4};
         if (p == 3) vals = {32, 64, 128};
         if (p == 4) vals = {512, 1024, 2048};
-        if (p == 5) vals = {22, 24, 25, 26, 27};
+        if (p == 5) vals = {22, 24, 25, 26, 27, 28};
         for (int v : vals) {
             sbr_tuning t = bestt;
             if (p == 0) {
