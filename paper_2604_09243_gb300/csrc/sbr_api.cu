@@ -1301,14 +1301,15 @@ int build_plan(sbr_ctx* c, BatchPlan& P)
 // sbr_trace and sbr_trace_bistatic (az_el_rx: [n][2] receivers, or null for monostatic)
 // ---------------------------------------------------------------- pooled late passes
 // A trace of several chunks runs bounce passes 1 .. kPoolPass - 1 per chunk;
-// the rays that go on are appended to one pool, and passes kPoolPass .. run
-// over the pool once for all chunks (a late pass holds few rays per chunk, and
-// a launch over few rays leaves most SMs idle while its slowest rays finish).
-// A pooled ray carries its trace-wide aspect index: the pooled passes read the
-// trace's aspect table, its ray offsets, the trace-wide hit masks and each
-// aspect's first record, so every record lands where the chunk reserved it.
-// The pool holds as many rays as a chunk queue; when a chunk's rays do not fit,
-// the pool is traced first and the chunk's rays appended again.
+// the last of them appends the rays that go on to one pool, and passes
+// kPoolPass .. run over the pool once for all chunks (a late pass holds few
+// rays per chunk, and a launch over few rays leaves most SMs idle while its
+// slowest rays finish). A pooled ray carries its trace-wide aspect index: the
+// pooled passes read the trace's aspect table, its ray offsets, the trace-wide
+// hit masks and each aspect's first record, so every record lands where the
+// chunk reserved it. The pool holds as many rays as a chunk queue; rays that
+// find it full stay in the chunk's queue, and at the host's next wait the pool
+// is traced and they are appended.
 constexpr int kPoolPass = 2;
 // sbr_run_batch: a group of chunks holds the records of at most this many chunks' worth of rays
 constexpr long long kGroupRecords = 4;
