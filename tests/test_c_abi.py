@@ -36,6 +36,45 @@ def test_c_program_compiles_against_the_header(tmp_path):
     assert os.path.exists(_compile(tmp_path))
 
 
+def test_binding_structs_match_the_header(tmp_path):
+    """Every struct the Python binding passes across the boundary has the
+    size, field offsets and field sizes of its C declaration in the header (a
+    small C program prints sizeof and offsetof; no GPU and no library needed)."""
+    import ctypes as C
+
+    from paper_2604_09243_gb300 import sbr
+
+    gcc = shutil.which("gcc") or pytest.skip("gcc not found")
+    pairs = [("sbr_bvh_opts", sbr.BvhOpts), ("sbr_trace_opts", sbr.TraceOpts), ("sbr_tuning", sbr.Tuning),
+             ("sbr_tune_trial", sbr.TuneTrial), ("sbr_bvh_info", sbr.BvhInfo), ("sbr_trace_stats", sbr.TraceStats),
+             ("sbr_request", sbr.Request), ("sbr_ray_grid", sbr.RayGrid), ("sbr_surrogate_opts", sbr.SurrogateOpts)]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "sbr.h"',
+             "#define F(T, m) printf(\"%s %s %zu %zu\\n\", #T, #m, offsetof(T, m), sizeof(((T*)0)->m))",
+             "int main(void)", "{"]
+    for cname, py in pairs:
+        lines.append(f'    printf("%s size %zu 0\\n", "{cname}", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f"    F({cname}, {f});")
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = str(tmp_path / "layout")
+    r = subprocess.run([gcc, "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                        exe], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        if ln:
+            t, m, a, b = ln.split()
+            got[(t, m)] = (int(a), int(b))
+    for cname, py in pairs:
+        assert got[(cname, "size")][0] == C.sizeof(py), cname
+        for f, _ in py._fields_:
+            d = getattr(py, f)
+            assert got[(cname, f)] == (d.offset, d.size), (cname, f)
+
+
 @pytest.mark.gpu
 def test_c_program_matches_binding_and_closed_form(tmp_path):
     exe = _compile(tmp_path)
