@@ -102,6 +102,7 @@ struct sbr_ctx {
     // pooled late passes of sbr_trace: the live rays the chunks leave for pass kPoolPass, the trace's aspect
     // table and ray offsets, each aspect's first record, the pool's counters and work counters
     DevBuf pool, angall, rayoffall, recofall, poolctr, poolwork;
+    DevBuf poolgroup;  // bucket counts, grouped order and scan scratch of the pooled passes' rays
     unsigned* pool_host = nullptr;  // pinned copy of the pool's count and flag
     long long rec_total = 0;
     int max_bounces = 0, trace_flags = 0;
@@ -403,7 +404,7 @@ void sbr_destroy(sbr_ctx* c)
     DevBuf* all[] = {&c->xyz, &c->tri, &c->nodes, &c->tris, &c->bvh_scratch, &c->bbox_dev, &c->err_dev, &c->nodes4,
                      &c->angles, &c->rayoff, &c->mask, &c->tilebase, &c->scan_scr, &c->recoff, &c->q0, &c->q1, &c->cover,
                      &c->nodes_oct, &c->tripos, &c->pool, &c->angall, &c->rayoffall, &c->recofall, &c->poolctr,
-                     &c->poolwork, &c->vis, &c->visfull, &c->hitlist, &c->rbig, &c->rbigctr, &c->ctr64, &c->ctr32, &c->stats, &c->rec, &c->hit_tri, &c->hit_t, &c->hit_nb, &c->items,
+                     &c->poolwork, &c->poolgroup, &c->vis, &c->visfull, &c->hitlist, &c->rbig, &c->rbigctr, &c->ctr64, &c->ctr32, &c->stats, &c->rec, &c->hit_tri, &c->hit_t, &c->hit_nb, &c->items,
                      &c->itemoff, &c->recbeg, &c->freq, &c->kfreq, &c->partial, &c->E, &c->rcs};
     for (DevBuf* b : all) b->release();
     if (c->host_stage) cudaFreeHost(c->host_stage);
@@ -1319,7 +1320,15 @@ struct PoolRun {
     int64_t n_angles = 0;
     unsigned cap = 0;
     std::vector<long long> rec_of;  // per aspect: first record of its chunk
+    // grouping of each pooled pass's rays by (aspect, triangle left >> tri_shift)
+    int tri_shift = 0;
+    unsigned groups = 1;
+    long long n_buckets = 1;
+    unsigned* counts = nullptr;
+    unsigned* order = nullptr;
+    void* scan_scratch = nullptr;
 };
+constexpr long long kMaxBuckets = 1ll << 22;
 
 // run the pooled passes over the pool (its ping-pong partner: queue `partner`), then empty it
 int flush_pool(sbr_ctx* c, TraceRun& R, PoolRun& P, RayState* partner)
@@ -1371,6 +1380,13 @@ int flush_pool(sbr_ctx* c, TraceRun& R, PoolRun& P, RayState* partner)
         ta.q_in_count = j == 0 ? ctr : ctr + 2 + (j - 1);
         ta.q_out = qs[(j + 1) & 1];
         ta.q_out_count = ctr + 2 + j;
+        // the pass takes its rays grouped by aspect and by the triangle they leave
+        CK(cudaMemsetAsync(P.counts, 0, sizeof(unsigned) * (size_t)P.n_buckets, c->stream), "memset buckets");
+        CK(launch_group_rays(ta.q_in, ta.q_in_count, P.tri_shift, P.groups, P.counts, P.n_buckets, P.order,
+                             P.scan_scratch, c->n_sms * 4, c->stream),
+           "group rays");
+        R.n_launch += 5;
+        ta.q_order = P.order;
         CK(run_pass(c, R, ta), "trace pooled pass");
     }
     CK(cudaMemsetAsync(ctr, 0, sizeof(unsigned) * 2, c->stream), "memset pool count");
@@ -1427,6 +1443,21 @@ int pool_setup(sbr_ctx* c, TraceRun& R, PoolRun& P, const std::vector<int64_t>& 
     CK(c->recofall.ensure(sizeof(long long) * (size_t)n), "alloc record bases");
     CK(c->poolctr.ensure(sizeof(unsigned) * (kMaxBounces + 4)), "alloc pool counters");
     CK(c->poolwork.ensure(sizeof(unsigned long long) * (kMaxBounces + 2)), "alloc pool work counters");
+    while (P.tri_shift < 30) {
+        P.groups = (unsigned)((c->n_tri + (1ll << P.tri_shift) - 1) >> P.tri_shift);
+        if ((long long)P.groups * n <= kMaxBuckets) break;
+        ++P.tri_shift;
+    }
+    P.n_buckets = std::max(1ll, (long long)P.groups * n);
+    {
+        const size_t b_cnt = ((sizeof(unsigned) * (size_t)P.n_buckets + 255) / 256) * 256;
+        const size_t b_ord = ((sizeof(unsigned) * (size_t)P.cap + 255) / 256) * 256;
+        CK(c->poolgroup.ensure(b_cnt + b_ord + scan_scratch_bytes(P.n_buckets)), "alloc ray grouping");
+        char* g = (char*)c->poolgroup.p;
+        P.counts = (unsigned*)g;
+        P.order = (unsigned*)(g + b_cnt);
+        P.scan_scratch = g + b_cnt + b_ord;
+    }
     if (!c->pool_host && cudaMallocHost((void**)&c->pool_host, 4 * sizeof(unsigned)) != cudaSuccess) {
         c->pool_host = nullptr;
         return fail(c, SBR_ERR_OOM, "pinned allocation failed");

@@ -155,6 +155,7 @@ struct TraceArgs {
     int visit_limit;              // upper bound of node + leaf visits of one query (2 n_tri + 64)
     long long total_rays;         // primary: padded ray count of the chunk
     const RayState* q_in;
+    const unsigned* q_order;      // optional: entry i of the pass is q_in[q_order[i]] (rays grouped by place)
     const unsigned* q_in_count;
     RayState* q_out;
     unsigned* q_out_count;
@@ -195,6 +196,14 @@ cudaError_t launch_emit_all(const TraceArgs& a, int n_blocks, cudaStream_t st);
 // Append the *src_count live rays of src to the pool at *pool_count (their
 // aspect index shifted by angle_shift), then advance *pool_count; when they do
 // not fit under cap nothing is copied and *flag becomes 1.
+// Group the *count rays of q by (aspect, triangle left >> tri_shift): bucket
+// b = aspect * groups + (triangle >> tri_shift) of n_buckets; counts
+// (n_buckets + 1 words, zeroed by the caller) becomes the buckets' starts, and
+// order[i] the position in q of the i-th ray in bucket order (within a bucket
+// in no particular order). scratch: scan_scratch_bytes(n_buckets + 1).
+cudaError_t launch_group_rays(const RayState* q, const unsigned* count, int tri_shift, unsigned groups,
+                              unsigned* counts, long long n_buckets, unsigned* order, void* scratch, int n_blocks,
+                              cudaStream_t st);
 cudaError_t launch_pool_append(const RayState* src, const unsigned* src_count, RayState* pool, unsigned* pool_count,
                                unsigned cap, int angle_shift, unsigned* flag, int n_blocks, cudaStream_t st);
 // Silhouette mask of the aspects of a chunk (a.angles, a.ray_off, a.n_angles):

@@ -1839,14 +1839,16 @@ __global__ void __launch_bounds__(kTraceThreads, 4) k_bounce(const TraceArgs a)
             primary_geom(a, e.x, (int)e.y, r.o, r.d, r.last);
             if (kCount) ++nlist;
         }
-        else if (active) load_geom(a.q_in, idx, r);
+        // the pass's i-th entry, in the order of q_order when the rays were grouped by place
+        const unsigned src = (a.q_order && active && !listed) ? __ldcs(a.q_order + idx) : idx;
+        if (active && !listed) load_geom(a.q_in, src, r);
         Hit h;
         const unsigned nvis0 = nvis;
         query<kCount, kStack, kMode>(a, active, r.o, r.d, r.last, h, nvis, ntri, ovf);
         if (kCount) wvis += 32ull * __reduce_max_sync(kFull, nvis - nvis0);
         if (active) {
             if (listed) primary_state(a, e.x, (int)e.y, r);
-            else load_payload(a.q_in, idx, r);
+            else load_payload(a.q_in, src, r);
             const AngleDev& A = a.angles[r.angle];
             ++nq;
             if (h.k < 0) {
@@ -1904,6 +1906,54 @@ __global__ void __launch_bounds__(256) k_pool_append(const RayState* __restrict_
         int4 g = __ldcs(reinterpret_cast<const int4*>(p) + 5);
         g.x += angle_shift;
         __stcs(reinterpret_cast<int4*>(q) + 5, g);
+    }
+}
+
+// Rays grouped by place before a pooled pass: the rays of one aspect that
+// leave neighbouring triangles (the reordered triangles follow the tree's
+// leaves) start close together, in similar directions, and share much of
+// their traversal. A counting sort by bucket with atomic cursors.
+__device__ __forceinline__ unsigned ray_bucket(const RayState* __restrict__ q, unsigned i, int tri_shift,
+                                               unsigned groups)
+{
+    const int4 g = __ldcs(reinterpret_cast<const int4*>(q + i) + 5);  // aspect, ray, triangle left, bounces
+    return (unsigned)g.x * groups + ((unsigned)g.z >> tri_shift);
+}
+
+// Neighbouring queue entries mostly share a bucket (a warp's survivors are
+// appended together), so the lanes of a warp that share one make a single
+// atomic for all of them. The loops run whole warps (every lane reaches the
+// match).
+__global__ void __launch_bounds__(256) k_bucket_count(const RayState* __restrict__ q, const unsigned* count,
+                                                      int tri_shift, unsigned groups, unsigned* counts)
+{
+    const unsigned n = *count;
+    const int lane = threadIdx.x & 31;
+    const unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x - lane; w < n; w += stride) {
+        const unsigned i = w + lane;
+        const unsigned b = i < n ? ray_bucket(q, i, tri_shift, groups) : 0xFFFFFFFFu;
+        const unsigned peers = __match_any_sync(kFull, b);
+        if (i < n && lane == __ffs(peers) - 1) atomicAdd(counts + b, (unsigned)__popc(peers));
+    }
+}
+
+__global__ void __launch_bounds__(256) k_bucket_scatter(const RayState* __restrict__ q, const unsigned* count,
+                                                        int tri_shift, unsigned groups, unsigned* cursor,
+                                                        unsigned* order)
+{
+    const unsigned n = *count;
+    const int lane = threadIdx.x & 31;
+    const unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned w = blockIdx.x * blockDim.x + threadIdx.x - lane; w < n; w += stride) {
+        const unsigned i = w + lane;
+        const unsigned b = i < n ? ray_bucket(q, i, tri_shift, groups) : 0xFFFFFFFFu;
+        const unsigned peers = __match_any_sync(kFull, b);
+        const int leader = __ffs(peers) - 1;
+        unsigned base = 0;
+        if (i < n && lane == leader) base = atomicAdd(cursor + b, (unsigned)__popc(peers));
+        base = __shfl_sync(kFull, base, leader);
+        if (i < n) order[base + __popc(peers & ((1u << lane) - 1u))] = i;
     }
 }
 
@@ -1998,6 +2048,18 @@ cudaError_t launch_emit_all(const TraceArgs& a, int n_blocks, cudaStream_t st)
 {
     if (a.bistatic) k_emit_all<true><<<n_blocks, kTraceThreads, 0, st>>>(a);
     else k_emit_all<false><<<n_blocks, kTraceThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_group_rays(const RayState* q, const unsigned* count, int tri_shift, unsigned groups,
+                              unsigned* counts, long long n_buckets, unsigned* order, void* scratch, int n_blocks,
+                              cudaStream_t st)
+{
+    k_bucket_count<<<n_blocks, 256, 0, st>>>(q, count, tri_shift, groups, counts);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = scan_exclusive_u32(counts, counts, n_buckets, false, nullptr, scratch, st);
+    if (e != cudaSuccess) return e;
+    k_bucket_scatter<<<n_blocks, 256, 0, st>>>(q, count, tri_shift, groups, counts, order);
     return cudaGetLastError();
 }
 
