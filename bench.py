@@ -64,8 +64,8 @@ OPS_PRIMARY_HIT = 185
 # k_bounce launches of one ncu capture, divided by their queries), per workload and setting; scaled by the
 # bounce queries of a step. None where no capture of the current kernels exists.
 TRAFFIC_PER_QUERY = {
-    # k_bounce, warm L2 (ncu --cache-control none), 36 of the 360 aspects, five identical sweeps, ray pool
-    "aircraft10": [(110.0, {"bvh_width": 2, "octant": 0, "packet": 0})],
+    # k_bounce, warm L2 (ncu --cache-control none), 36 of the 360 aspects, five identical sweeps, grouped ray pool
+    "aircraft10": [(116.8, {"bvh_width": 2, "octant": 0, "packet": 0})],
 }
 
 
