@@ -1887,11 +1887,13 @@ __global__ void __launch_bounds__(kTraceThreads) k_emit_all(const TraceArgs a)
 }
 
 // ---------------------------------------------------------------- pooled late passes
-// The live rays that a chunk's early passes leave for the next pass are
-// appended to a pool shared by the chunks, so that the late passes run once over
+// The live rays that a chunk's early passes leave for the next pass go to a
+// pool shared by the chunks (push above), so that the late passes run once over
 // the rays of every chunk: a late pass holds few rays per chunk, and a launch
 // over few rays leaves most of the GPU idle while its slowest rays finish.
-// A pooled ray's aspect index becomes the trace's (+ angle_shift).
+// k_pool_append moves rays that a chunk kept because the pool was full into the
+// pool once it has been traced (their aspect index shifted by angle_shift, 0
+// for rays push already gave the trace's index).
 __global__ void __launch_bounds__(256) k_pool_append(const RayState* __restrict__ src, const unsigned* src_count,
                                                      RayState* __restrict__ pool, const unsigned* pool_count,
                                                      unsigned cap, int angle_shift)
@@ -1912,7 +1914,9 @@ __global__ void __launch_bounds__(256) k_pool_append(const RayState* __restrict_
 // Rays grouped by place before a pooled pass: the rays of one aspect that
 // leave neighbouring triangles (the reordered triangles follow the tree's
 // leaves) start close together, in similar directions, and share much of
-// their traversal. A counting sort by bucket with atomic cursors.
+// their traversal. A counting sort by bucket with atomic cursors; the order
+// within a bucket varies between runs and changes no result, since every ray
+// writes its record to the slot its primary ray reserved.
 __device__ __forceinline__ unsigned ray_bucket(const RayState* __restrict__ q, unsigned i, int tri_shift,
                                                unsigned groups)
 {
