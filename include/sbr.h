@@ -89,8 +89,8 @@ typedef struct {
     double offset_v; /* same along v */
     int flags;       /* SBR_TRACE_* */
     int chunk_rays;  /* rays per internal batch of aspects (0 = 2^27); bounds the live-ray queue
-                        memory at 192 bytes per ray (288 with the ray pool of a trace of several
-                        chunks); an aspect larger than this is refused */
+                        memory at 192 bytes per ray (292 with the ray pool, and its grouping, of a
+                        trace of several chunks); an aspect larger than this is refused */
 } sbr_trace_opts;
 
 /* Counters of the last sbr_trace (summed over its angles). */
